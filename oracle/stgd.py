@@ -1,0 +1,149 @@
+"""Stochastic tensor gradient descent on the implicit whitened tensor, FP64 (oracle).
+
+Section 3.2: the whitened tensor T, the loss Eq. (15), the stochastic update of
+Lemma 3 / Eq. (16); Appendix A (gradient and the alpha0 "shift" terms).
+Test infrastructure only (see the package docstring).
+
+Readings of the paper used here:
+  * Gram coefficient kappa.  Lemma 3 writes (1+theta)/2, Appendix A writes
+    theta; they agree at theta = 1 (the paper's choice).  We use
+    kappa = (1+theta)/2 (Lemma 3).
+  * The factor 3 from differentiating the cubic is absorbed into the step size:
+    the gradient is G = kappa V ((V^T V) o (V^T V)) - T(V, V, I), where column i
+    of T(V, V, I) is T(v_i, v_i, I), and the update is V <- V - beta G.  The
+    matching explicit loss is
+        L~(V) = (kappa/2) sum_ij <v_i, v_j>^3 - <sum_i v_i^(x)3, T>,
+    whose gradient is 3 G when the three views coincide.
+  * The unit-norm constraint of Definition 1 is not enforced during SGD
+    (Section 3.3 reads eigenvalues off the norms).
+  * Lemma 3 contracts views A and B and leaves view C free; with three distinct
+    views (community model) we follow it literally.
+  * "y_B^t" in the alpha0^2 term of Lemma 3 is read as the mean y_B-bar.
+  * y-bar is the full-data mean of each view (computed once).
+  * A step uses the mean of the per-sample updates over a minibatch of b
+    samples (the Gram term once per step); the last, partial minibatch of an
+    epoch is kept and averaged over its own size.
+  * Step size beta_t = beta0 / sqrt(t), t the global step counted from 1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .moments import coefficients
+
+__all__ = [
+    "kappa", "whitened_tensor", "contract", "loss_explicit", "grad_explicit",
+    "grad_implicit", "sgd_step", "sgd_run", "steps_per_epoch",
+]
+
+
+def kappa(theta: float) -> float:
+    """Gram-term coefficient of Lemma 3: (1 + theta) / 2."""
+    return 0.5 * (1.0 + float(theta))
+
+
+def whitened_tensor(YA, YB, YC, ybar3, alpha0: float) -> np.ndarray:
+    """Section 3.2: T = c1 E_t[yA (x) yB (x) yC]
+                        - c2 E_t[yA (x) yB (x) ybC + yA (x) ybB (x) yC + ybA (x) yB (x) yC]
+                        + c3 ybA (x) ybB (x) ybC   (explicit k^3; small k)."""
+    YA, YB, YC = (np.asarray(Y, dtype=np.float64) for Y in (YA, YB, YC))
+    ybA, ybB, ybC = (np.asarray(y, dtype=np.float64) for y in ybar3)
+    n = YA.shape[0]
+    c1, c2, c3 = coefficients(alpha0)
+    E = np.einsum("ti,tj,tk->ijk", YA, YB, YC) / n
+    S = (np.einsum("ti,tj,k->ijk", YA, YB, ybC) + np.einsum("ti,j,tk->ijk", YA, ybB, YC)
+         + np.einsum("i,tj,tk->ijk", ybA, YB, YC)) / n
+    return c1 * E - c2 * S + c3 * np.einsum("i,j,k->ijk", ybA, ybB, ybC)
+
+
+def contract(T: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """Column i = T(v_i, v_i, I): contraction of modes 1 and 2 with v_i."""
+    return np.einsum("abc,ai,bi->ci", T, V, V)
+
+
+def loss_explicit(V: np.ndarray, T: np.ndarray, theta: float) -> float:
+    """L~(V) = (kappa/2) sum_ij <v_i, v_j>^3 - sum_i T(v_i, v_i, v_i)."""
+    G = V.T @ V
+    return 0.5 * kappa(theta) * np.sum(G ** 3) - np.einsum("abc,ai,bi,ci->", T, V, V, V)
+
+
+def grad_explicit(V: np.ndarray, T: np.ndarray, theta: float) -> np.ndarray:
+    """Gradient of L~ with respect to each v_i (all three modes of T)."""
+    G = V.T @ V
+    gram = 3.0 * kappa(theta) * V @ (G ** 2)
+    t = (np.einsum("abc,bi,ci->ai", T, V, V) + np.einsum("abc,ai,ci->bi", T, V, V)
+         + np.einsum("abc,ai,bi->ci", T, V, V))
+    return gram - t
+
+
+def grad_implicit(V, YA, YB, YC, ybar3, theta: float, alpha0: float) -> np.ndarray:
+    """Lemma 3 (Eq. (16)) written per component i, averaged over the minibatch.
+
+    For each i with phi = v_i:
+      data_i = c1 mean_t[<phi,yA_t><phi,yB_t> yC_t] + c3 <phi,ybA><phi,ybB> ybC
+             - c2 mean_t[<phi,yA_t><phi,yB_t>] ybC
+             - c2 <phi,ybB> mean_t[<phi,yA_t> yC_t]
+             - c2 <phi,ybA> mean_t[<phi,yB_t> yC_t]
+      gram_i = sum_j <phi_j, phi>^2 phi_j
+      G[:, i] = kappa gram_i - data_i.
+    The tensor is never formed: only inner products with the samples.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    YA, YB, YC = (np.asarray(Y, dtype=np.float64) for Y in (YA, YB, YC))
+    ybA, ybB, ybC = (np.asarray(y, dtype=np.float64) for y in ybar3)
+    c1, c2, c3 = coefficients(alpha0)
+    kap = kappa(theta)
+    k = V.shape[1]
+    G = np.empty_like(V)
+    for i in range(k):
+        phi = V[:, i]
+        a = YA @ phi
+        b = YB @ phi
+        pa = phi @ ybA
+        pb = phi @ ybB
+        data = (c1 * np.mean((a * b)[:, None] * YC, axis=0)
+                + c3 * pa * pb * ybC
+                - c2 * np.mean(a * b) * ybC
+                - c2 * pb * np.mean(a[:, None] * YC, axis=0)
+                - c2 * pa * np.mean(b[:, None] * YC, axis=0))
+        gram = np.zeros(V.shape[0])
+        for j in range(k):
+            gram += (V[:, j] @ phi) ** 2 * V[:, j]
+        G[:, i] = kap * gram - data
+    return G
+
+
+def sgd_step(V, YA, YB, YC, ybar3, theta: float, beta: float, alpha0: float) -> np.ndarray:
+    """One update of Lemma 3 over a minibatch: V <- V - beta G."""
+    return np.asarray(V, dtype=np.float64) - beta * grad_implicit(V, YA, YB, YC, ybar3,
+                                                                   theta, alpha0)
+
+
+def steps_per_epoch(n: int, b: int) -> int:
+    return (n + b - 1) // b
+
+
+def sgd_run(V0, YA, YB, YC, ybar3, perm: np.ndarray, b: int, beta0: float,
+            theta: float, alpha0: float, snapshot_every: int = 0, max_steps: int = -1):
+    """The STGD loop (Section 3.2): for each epoch e the samples are visited in the
+    order perm[e], in minibatches of b; beta_t = beta0/sqrt(t).
+
+    Returns the final V and, if snapshot_every > 0, the list of V after every
+    snapshot_every-th step.  max_steps >= 0 stops early (bounded CPU samples).
+    """
+    V = np.asarray(V0, dtype=np.float64).copy()
+    YA, YB, YC = (np.asarray(Y, dtype=np.float64) for Y in (YA, YB, YC))
+    n = YA.shape[0]
+    snaps = []
+    t = 0
+    for order in perm:
+        for s in range(0, n, b):
+            if 0 <= max_steps <= t:
+                return V, snaps
+            idx = order[s:s + b]
+            t += 1
+            V = sgd_step(V, YA[idx], YB[idx], YC[idx], ybar3, theta,
+                         beta0 / np.sqrt(t), alpha0)
+            if snapshot_every and t % snapshot_every == 0:
+                snaps.append(V.copy())
+    return V, snaps

@@ -1,0 +1,188 @@
+"""CPU pins of the oracle's stochastic tensor gradient descent (Section 3.2,
+Lemma 3, Appendix A) and post-processing (Section 3.3, Lemma 4)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import moments as om
+from oracle import post, stgd
+from oracle import whiten as ow
+
+
+def _samples(seed, n, k):
+    g = np.random.default_rng(seed)
+    Y = g.standard_normal((n, k)) + 0.3
+    return Y, Y.mean(axis=0)
+
+
+@pytest.mark.parametrize("alpha0,theta", [(0.0, 1.0), (1.0, 1.0), (0.6, 2.5)])
+def test_implicit_gradient_is_third_of_explicit_loss_gradient(alpha0, theta):
+    """Symmetric views: Lemma 3's implicit gradient equals (1/3) grad L~ computed
+    from the explicit whitened tensor (different code path: einsum over T)."""
+    Y, yb = _samples(1, 40, 5)
+    V = np.random.default_rng(2).standard_normal((5, 5))
+    T = stgd.whitened_tensor(Y, Y, Y, (yb, yb, yb), alpha0)
+    G = stgd.grad_implicit(V, Y, Y, Y, (yb, yb, yb), theta, alpha0)
+    np.testing.assert_allclose(3.0 * G, stgd.grad_explicit(V, T, theta), rtol=1e-11, atol=1e-11)
+
+
+def test_explicit_gradient_matches_finite_differences():
+    Y, yb = _samples(3, 30, 4)
+    T = stgd.whitened_tensor(Y, Y, Y, (yb, yb, yb), 1.0)
+    V = np.random.default_rng(4).standard_normal((4, 4))
+    G = stgd.grad_explicit(V, T, 1.0)
+    h = 1e-5
+    FD = np.zeros_like(V)
+    for a, b in itertools.product(range(4), range(4)):
+        E = np.zeros_like(V)
+        E[a, b] = h
+        FD[a, b] = (stgd.loss_explicit(V + E, T, 1.0) - stgd.loss_explicit(V - E, T, 1.0)) / (2 * h)
+    np.testing.assert_allclose(FD, G, rtol=1e-7, atol=1e-7 * np.abs(G).max())
+
+
+def test_three_view_data_term_contracts_modes_one_and_two():
+    """Three distinct views: the data term of Lemma 3 is T(v_i, v_i, I) of the
+    explicit (non-symmetric) whitened tensor."""
+    g = np.random.default_rng(5)
+    YA, YB, YC = (g.standard_normal((25, 4)) + s for s in (0.1, -0.2, 0.3))
+    yb = tuple(Y.mean(axis=0) for Y in (YA, YB, YC))
+    V = g.standard_normal((4, 4))
+    T = stgd.whitened_tensor(YA, YB, YC, yb, 0.8)
+    G0 = stgd.grad_implicit(V, YA, YB, YC, yb, 1.0, 0.8)
+    # Gram part alone from a zero-data problem (alpha0 = 0, all samples zero)
+    Z = np.zeros_like(YA)
+    gram = stgd.grad_implicit(V, Z, Z, Z, (Z[0], Z[0], Z[0]), 1.0, 0.0)
+    np.testing.assert_allclose(gram - G0, stgd.contract(T, V), rtol=1e-11, atol=1e-11)
+
+
+def _orthogonal_atoms(seed, k):
+    """Samples whose empirical third moment is exactly sum_i lam_i u_i^(x)3."""
+    g = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(g.standard_normal((k, k)))
+    lam = g.uniform(1.5, 3.0, k)
+    Y = ((k * lam) ** (1.0 / 3.0) * U).T
+    return Y, U, lam
+
+
+def test_stationary_point_of_orthogonal_tensor():
+    """alpha0 = 0 (c1 = 1): T = sum lam_i u_i^(x)3 and V* = [(lam_i/kappa)^(1/3) u_i]
+    has zero gradient (closed form)."""
+    Y, U, lam = _orthogonal_atoms(6, 5)
+    yb = Y.mean(axis=0)
+    for theta in (1.0, 3.0):
+        Vs = (lam / stgd.kappa(theta)) ** (1.0 / 3.0) * U
+        G = stgd.grad_implicit(Vs, Y, Y, Y, (yb, yb, yb), theta, 0.0)
+        assert np.abs(G).max() < 1e-12
+        np.testing.assert_allclose(post.eigenvalues(Vs, theta), lam, rtol=1e-12)
+
+
+def test_alpha0_zero_is_plain_third_moment():
+    Y, yb = _samples(7, 20, 3)
+    T = stgd.whitened_tensor(Y, Y, Y, (yb, yb, yb), 0.0)
+    brute = np.zeros((3, 3, 3))
+    for y in Y:
+        for a, b, c in itertools.product(range(3), repeat=3):
+            brute[a, b, c] += y[a] * y[b] * y[c] / len(Y)
+    np.testing.assert_allclose(T, brute, atol=1e-12)
+
+
+def test_whitened_tensor_equals_whitened_eq11_on_expected_graph():
+    """Section 3.2's sample form of T (means of each view) equals Eq. (11)
+    multilinearly whitened, M3(W, W, W), when the views coincide (expected graph)."""
+    k, n, a0 = 3, 12, 0.7
+    g = np.random.default_rng(8)
+    Pi = {p: g.dirichlet(np.full(k, a0 / k), size=n) for p in "XABC"}
+    P = g.uniform(0.1, 0.9, size=(k, k))
+    G = {p: Pi["X"] @ P @ Pi[p].T for p in "ABC"}
+    M2 = om.community_second_moment(G["A"], G["B"], G["C"], k, a0)
+    W = ow.whiten_exact(0.5 * (M2 + M2.T), k)["W"]
+    Z_B, Z_C = om.transition_matrices(G["A"], G["B"], G["C"], k)
+    YA, YB, YC = G["A"] @ W, G["B"] @ Z_B.T @ W, G["C"] @ Z_C.T @ W
+    yb = tuple(Y.mean(axis=0) for Y in (YA, YB, YC))
+    T = stgd.whitened_tensor(YA, YB, YC, yb, a0)
+    M3 = om.community_third_moment(G["A"], G["B"], G["C"], k, a0)
+    np.testing.assert_allclose(T, np.einsum("abc,ai,bj,ck->ijk", M3, W, W, W), atol=1e-9)
+
+
+def test_sgd_converges_locally_to_exact_decomposition():
+    """Full-batch STGD started near the decomposition converges to it (error -> 0)."""
+    k = 6
+    Y, U, lam = _orthogonal_atoms(0, k)
+    yb = Y.mean(axis=0)
+    V0 = lam ** (1.0 / 3.0) * U + 0.1 * np.random.default_rng(1).standard_normal((k, k))
+    V, _ = stgd.sgd_run(V0, Y, Y, Y, (yb, yb, yb), np.tile(np.arange(k), (300, 1)), k, 0.2,
+                        1.0, 0.0)
+    assert post.recon_error_from_V(V, 1.0, lam, U) < 1e-6
+    perm, signs, err = post.match_components(V, U)
+    assert err < 1e-5
+
+
+def test_sgd_schedule_steps_and_partial_batch():
+    """beta_t = beta0/sqrt(t) with t counted over the whole run; a partial last
+    batch is one step averaged over its own size."""
+    Y, yb = _samples(9, 10, 3)
+    V0 = np.eye(3)
+    perm = np.stack([np.arange(10), np.arange(10)[::-1]])
+    V, _ = stgd.sgd_run(V0, Y, Y, Y, (yb, yb, yb), perm, 4, 0.01, 1.0, 0.5)
+    Vm = V0.copy()
+    t = 0
+    for order in perm:
+        for s in (0, 4, 8):
+            t += 1
+            idx = order[s:s + 4]
+            Vm = Vm - 0.01 / np.sqrt(t) * stgd.grad_implicit(Vm, Y[idx], Y[idx], Y[idx],
+                                                             (yb, yb, yb), 1.0, 0.5)
+    assert t == 2 * stgd.steps_per_epoch(10, 4) == 6
+    np.testing.assert_allclose(V, Vm, atol=1e-14)
+
+
+def test_unwhiten_recovers_topics_from_population():
+    """Population topic model: whiten M2 = mu diag(a) mu^T, decompose
+    M3(W,W,W) = sum a_i^{-1/2} u_i^(x)3 exactly; Lemma 4 returns mu and alpha/alpha0."""
+    g = np.random.default_rng(10)
+    d, k = 9, 3
+    mu = g.dirichlet(np.ones(d) * 0.7, size=k).T
+    ah = np.array([0.2, 0.3, 0.5])
+    M2 = (mu * ah) @ mu.T
+    wh = ow.whiten_exact(M2, k)
+    Umat = np.sqrt(ah) * (wh["W"].T @ mu)
+    np.testing.assert_allclose(Umat.T @ Umat, np.eye(k), atol=1e-10)
+    lam = ah ** -0.5
+    for theta in (1.0, 2.0):
+        Vs = (lam / stgd.kappa(theta)) ** (1.0 / 3.0) * Umat
+        out = post.unwhiten(Vs, wh["Wplus"], theta, normalize=True)
+        np.testing.assert_allclose(out["mu"], mu, atol=1e-10)
+        np.testing.assert_allclose(out["alpha_hat"], ah, atol=1e-10)
+        np.testing.assert_allclose(out["raw"], mu, atol=1e-10)
+    # sign flip of a component is undone by the simplex normalisation
+    out = post.unwhiten(-Vs, wh["Wplus"], 2.0, normalize=True)
+    np.testing.assert_allclose(out["mu"], mu, atol=1e-10)
+
+
+def test_recon_error_closed_form_matches_explicit_tensor():
+    g = np.random.default_rng(11)
+    k = 4
+    lt, Ut = g.uniform(1, 3, k), g.standard_normal((k, k))
+    lh, Uh = g.uniform(1, 3, k), g.standard_normal((k, k))
+    Ut /= np.linalg.norm(Ut, axis=0)
+    Uh /= np.linalg.norm(Uh, axis=0)
+    Tt = post.tensor_from_components(lt, Ut)
+    Th = post.tensor_from_components(lh, Uh)
+    ref = np.linalg.norm(Th - Tt) / np.linalg.norm(Tt)
+    assert abs(post.recon_error(lh, Uh, lt, Ut) - ref) < 1e-12
+    assert post.recon_error(lt, Ut, lt, Ut) < 1e-7
+
+
+def test_match_components_inverts_permutation_and_signs():
+    g = np.random.default_rng(12)
+    U, _ = np.linalg.qr(g.standard_normal((6, 6)))
+    p = g.permutation(6)
+    s = np.array([1, -1, 1, -1, -1, 1.0])
+    Uh = np.empty_like(U)
+    Uh[:, p] = U * s
+    perm, signs, err = post.match_components(Uh, U)
+    assert err < 1e-12
+    np.testing.assert_array_equal(perm, p)
+    np.testing.assert_array_equal(signs, s)
