@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the online tensor method's hot path on one GB300 (or N replicas).
+
+Workload (one "step" = one pass of the whole hot path over one synthetic
+input): mixed-membership stochastic blockmodel, four parts X, A, B, C of
+5,000 nodes, k = 100 communities, pi ~ Dir(0.01 * 1_100) (alpha0 = 1),
+p = 0.1 within / q = 0.005 across (Bernoulli), three CSR blocks X->A, B, C.
+  whiten (randomised, oversampling 20, 2 power iterations, FP64 eig)
+  -> project the three views -> means -> STGD, minibatch 1,024,
+  beta_t = 1e-2/sqrt(t), theta = 1, 20 epochs (100 steps, one persistent
+  launch) -> unwhiten.
+Metric: whitened samples processed by the SGD per second of whole-path time
+(100,000 samples per step).  Inputs are resident in HBM before timing; the
+L2 is flushed (256 MiB write) between timed steps.  ``e2e`` repeats the
+measurement with the inputs in pinned host memory and the copies inside the
+timed region.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+Multi-GPU: replicas only (one independent decomposition per rank, no
+collective on the data path); value = samples of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "whitened-sample SGD throughput (samples/s) & time-to-1e-3 error vs plain FP32"
+UNIT = "samples/s"
+CFG = dict(workload="mmsb_4x5000_k100_b1024_fp32", n_per=5000, k=100, alpha_i=0.01, p=0.1,
+           q=0.005, oversample=20, power_iters=2, b=1024, epochs=20, beta0=1e-2, theta=1.0,
+           alpha0=1.0, seed=0)
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+
+
+def make_inputs(cfg, rank=0):
+    s = cfg["seed"] + 1000 * rank
+    kt = cfg["k"] + cfg["oversample"]
+    g = synth.mmsb_graph(s, cfg["n_per"], cfg["k"], cfg["alpha_i"], cfg["p"], cfg["q"])
+    return {"G_XA": g["G_XA"], "G_XB": g["G_XB"], "G_XC": g["G_XC"],
+            "S_pairs": synth.gaussian(s + 1, cfg["n_per"], kt),
+            "S_w": synth.gaussian(s + 2, cfg["n_per"], kt),
+            "perm": synth.epoch_permutations(s + 3, cfg["n_per"], cfg["epochs"]),
+            "V0": synth.haar_orthonormal(s + 4, cfg["k"])}
+
+
+def sgd_flops(cfg, views=3):
+    """Algorithmic flops of the STGD launch: per step 2 views x 2k^2 b_s (A = V^T Y)
+    + 2k^2 b_s (Y_C^T B^T) + 4k^3 (Gram term), summed over all steps."""
+    n, b, k = cfg["n_per"], cfg["b"], cfg["k"]
+    sizes = [min(b, n - s) for s in range(0, n, b)] * cfg["epochs"]
+    per_sample = 2 * (views - 1) * k * k + 2 * k * k
+    return sum(per_sample * bs + 4 * k ** 3 for bs in sizes), len(sizes)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+class GpuPath:
+    def __init__(self, otm, torch, cfg, host, device):
+        self.otm, self.torch, self.cfg, self.dev = otm, torch, cfg, device
+        self.host = host
+        self.upload()
+
+    def upload(self, pinned=None):
+        t = self.torch
+        src = pinned if pinned is not None else self.host
+        self.D = {x: self.otm.DeviceCSR.from_host(self.host[x], self.dev) if pinned is None else
+                  self.otm.DeviceCSR(*(a.to(self.dev, non_blocking=True) for a in src[x]),
+                                     self.host[x].shape)
+                  for x in ("G_XA", "G_XB", "G_XC")}
+        for nm in ("S_pairs", "S_w", "perm", "V0"):
+            a = src[nm]
+            setattr(self, nm, (t.from_numpy(np.ascontiguousarray(a)) if pinned is None else a)
+                    .to(self.dev, non_blocking=True))
+
+    def step(self, ev=None):
+        otm, t, c = self.otm, self.torch, self.cfg
+        k = c["k"]
+        if ev:
+            ev["w0"].record()
+        wh = otm.whiten_community(self.D["G_XA"], self.D["G_XB"], self.D["G_XC"], self.S_pairs,
+                                  self.S_w, k, c["power_iters"], c["alpha0"])
+        YA = otm.project(self.D["G_XA"], wh["W"])
+        YB = otm.project(self.D["G_XB"], wh["W_B"])
+        YC = otm.project(self.D["G_XC"], wh["W_C"])
+        yb = t.stack([otm.column_mean(YA), otm.column_mean(YB), otm.column_mean(YC)])
+        V = self.V0.t().contiguous()
+        if ev:
+            ev["s0"].record()
+        otm.sgd_run(V, YA, YB, YC, yb, self.perm, c["epochs"], c["b"], c["beta0"], c["theta"],
+                    c["alpha0"])
+        if ev:
+            ev["s1"].record()
+        out = otm.unwhiten(V, wh["Q"], wh["Cp"], c["theta"], False)
+        return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1309_0787_gb300 import otm
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cfg = dict(CFG)
+    host = make_inputs(cfg, rank)
+    path = GpuPath(otm, torch, cfg, host, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    samples = cfg["n_per"] * cfg["epochs"]
+    flops, nsteps = sgd_flops(cfg)
+
+    for _ in range(args.warmup):
+        path.step()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ev = [{n: torch.cuda.Event(enable_timing=True) for n in ("w0", "s0", "s1", "e1")}
+          for _ in range(args.steps)]
+    l0 = otm.launch_count()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                       # evict the L2 (129 MB) between steps
+        path.step(ev[i])
+        ev[i]["e1"].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    dist_barrier(world)
+    launches = otm.launch_count() - l0
+    clocks = sampler.stop()
+    step_ms = [e["w0"].elapsed_time(e["e1"]) for e in ev]
+    sgd_ms = [e["s0"].elapsed_time(e["s1"]) for e in ev]
+    pre_ms = [e["w0"].elapsed_time(e["s0"]) for e in ev]
+    t_total = sum(step_ms) / 1e3
+    t_max = dist_max(t_total, world)
+
+    # end to end: inputs in pinned host memory, copies inside the timed region
+    pinned = {x: tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                       for a in (host[x].row_ptr, host[x].col, host[x].val))
+              for x in ("G_XA", "G_XB", "G_XC")}
+    for nm in ("S_pairs", "S_w", "perm", "V0"):
+        pinned[nm] = torch.from_numpy(np.ascontiguousarray(host[nm])).pin_memory()
+    h2d = sum(a.numel() * a.element_size() for x in ("G_XA", "G_XB", "G_XC") for a in pinned[x])
+    h2d += sum(pinned[nm].numel() * pinned[nm].element_size()
+               for nm in ("S_pairs", "S_w", "perm", "V0"))
+    res_host = torch.empty(cfg["n_per"], cfg["k"], dtype=torch.float64).pin_memory()
+    lam_host = torch.empty(cfg["k"], dtype=torch.float64).pin_memory()
+    d2h = res_host.numel() * 8 + lam_host.numel() * 8
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for i in range(max(1, args.steps // 2)):
+        flush.fill_(float(i))
+        e_start.record()
+        path.upload(pinned)
+        out = path.step()
+        res_host.copy_(out["comps"], non_blocking=True)
+        lam_host.copy_(out["lambda"], non_blocking=True)
+        e_end.record()
+        torch.cuda.synchronize()
+        e2e_ms += e_start.elapsed_time(e_end)
+    n_e2e = max(1, args.steps // 2)
+    e2e_t = dist_max(e2e_ms / 1e3, world)
+
+    if rank != 0:
+        return None
+    sgd_avg_s = statistics.mean(sgd_ms) / 1e3
+    achieved = flops / sgd_avg_s / 1e12
+    line = {
+        "metric": METRIC, "value": world * samples * args.steps / t_max, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "nodes_per_part": cfg["n_per"], "k": cfg["k"],
+                   "minibatch": cfg["b"], "epochs": cfg["epochs"], "sgd_steps": nsteps,
+                   "samples_per_step": samples, "oversample": cfg["oversample"],
+                   "power_iters": cfg["power_iters"], "alpha0": cfg["alpha0"],
+                   "theta": cfg["theta"], "beta0": cfg["beta0"],
+                   "nnz": [int(host[x].nnz) for x in ("G_XA", "G_XB", "G_XC")],
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "breakdown_ms": {"whiten_project_mean": statistics.mean(pre_ms),
+                         "sgd_run": statistics.mean(sgd_ms),
+                         "unwhiten": statistics.mean(step_ms) - statistics.mean(pre_ms)
+                         - statistics.mean(sgd_ms),
+                         "wall_per_step": 1e3 * wall / args.steps},
+        "roofline": {"kernel": "sgd_cluster_kernel (one launch = all 100 STGD steps)",
+                     "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "algorithmic_flops_per_launch": flops},
+        "e2e": {"value": world * samples * n_e2e / e2e_t, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(cfg, host)
+    return line
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ----------------------------------------------------------------------------
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(v, "").isdigit():
+            return int(os.environ[v])
+    return os.cpu_count() or 1
+
+
+def oracle_sample(cfg, host, sgd_steps):
+    """Time the oracle on the workload: whitening + projection + means once,
+    `sgd_steps` STGD steps, unwhitening.  Returns (seconds per component)."""
+    from oracle import moments as om
+    from oracle import post as opost
+    from oracle import stgd as ostgd
+    from oracle import whiten as ow
+    k = cfg["k"]
+    t0 = time.perf_counter()
+    wh = ow.community_whiten_randomized(host["G_XA"], host["G_XB"], host["G_XC"], k,
+                                        cfg["alpha0"], host["S_pairs"].astype(np.float64),
+                                        host["S_w"].astype(np.float64), cfg["power_iters"])
+    YA = om.as_sparse(host["G_XA"]) @ wh["W"]
+    YB = om.as_sparse(host["G_XB"]) @ wh["W_B"]
+    YC = om.as_sparse(host["G_XC"]) @ wh["W_C"]
+    yb = (YA.mean(axis=0), YB.mean(axis=0), YC.mean(axis=0))
+    t1 = time.perf_counter()
+    V, _ = ostgd.sgd_run(host["V0"], YA, YB, YC, yb, host["perm"], cfg["b"], cfg["beta0"],
+                         cfg["theta"], cfg["alpha0"], max_steps=sgd_steps)
+    t2 = time.perf_counter()
+    opost.unwhiten(V, wh["Wplus"], cfg["theta"], False)
+    t3 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / sgd_steps, t3 - t2
+
+
+def cpu_value(cfg, host, sgd_steps=10):
+    pre, per_step, post = oracle_sample(cfg, host, sgd_steps)
+    _, nsteps = sgd_flops(cfg)
+    full = pre + nsteps * per_step + post
+    samples = cfg["n_per"] * cfg["epochs"]
+    sample = (f"oracle (FP64 NumPy) on the same workload: whitening+projection once "
+              f"({pre:.2f} s), {sgd_steps} of the {nsteps} STGD steps ({per_step * 1e3:.1f} ms "
+              f"each), unwhitening ({post:.2f} s); value = {samples} samples / "
+              f"(pre + {nsteps} x step + post) = {full:.2f} s")
+    return samples / full, sample
+
+
+def cpu_baseline(cfg, host):
+    v, sample = cpu_value(cfg, host)
+    return {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": sample}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cfg = dict(CFG)
+    host = make_inputs(cfg, 0)
+    for _ in range(args.warmup):
+        cpu_value(cfg, host, sgd_steps=2)
+    vals, samples_desc = [], ""
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, samples_desc = cpu_value(cfg, host, sgd_steps=2)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": cfg["workload"], "nodes_per_part": cfg["n_per"],
+                       "k": cfg["k"], "minibatch": cfg["b"], "epochs": cfg["epochs"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(),
+                             "kind": "oracle", "sample": samples_desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        line = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * otm.h -- C ABI of the GB300 (sm_103a) library for the online tensor method of
+ * Huang, Niranjan, Hakeem and Anandkumar, "Online Tensor Methods for Learning
+ * Latent Variable Models" (the paper).
+ *
+ * The library computes the paper's data-parallel hot path on one GPU:
+ *   moments of sparse count data        (Section 2, Eqs. (1)-(2), (9)-(10))
+ *   whitening W with W^T M2 W = I       (Section 3.1; randomised, Section 4.2)
+ *   projection of samples y_t = W^T c_t (Section 3.1, Section 4.1)
+ *   stochastic tensor gradient descent  (Section 3.2, Lemma 3 / Eq. (16))
+ *   unwhitening / post-processing       (Section 3.3, Lemma 4)
+ *
+ * Conventions that hold for every entry point:
+ *   - Every pointer argument is a DEVICE pointer owned by the caller, unless the
+ *     argument's comment says "host".  The library never frees caller memory.
+ *   - Dense matrices are row-major unless stated.  "rows x cols, row-major" means
+ *     element (r, c) is at ptr[r * cols + c].  The k x k component matrix V is
+ *     column-major: component v_i is the contiguous run V[i * k .. i * k + k).
+ *   - Sparse count data use CSR with int32 row_ptr (rows + 1 entries, row_ptr[0]
+ *     = 0, non-decreasing), int32 column indices in [0, cols) and float32 values.
+ *   - Calls are asynchronous on the CUDA stream passed as `stream` (a
+ *     cudaStream_t; NULL = legacy default stream).  Outputs are valid once the
+ *     stream reaches the point of the call.  Calls that return a value to the
+ *     host (documented) synchronise the stream.
+ *   - Scratch memory: calls that need it take `ws` (device) and `ws_bytes`;
+ *     the matching *_workspace() function returns the bytes required.  The
+ *     library itself allocates no device memory.
+ *   - Errors: each call returns an otm_status.  Argument errors are detected on
+ *     the host before any launch (OTM_EINVAL) and leave outputs untouched.
+ *     otm_last_error() returns a message for the calling thread's last error.
+ *     There is no CPU fallback: without a usable GPU the calls fail with
+ *     OTM_ECUDA.
+ */
+#ifndef OTM_H
+#define OTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum otm_status {
+  OTM_OK = 0,
+  OTM_EINVAL = 1,          /* invalid argument (sizes, null pointers, workspace too small) */
+  OTM_ENOTPSD = 2,         /* fewer than k positive eigenvalues: no whitening (Section 3.1) */
+  OTM_ENOMEM = 3,          /* reserved (the library does not allocate) */
+  OTM_ECUDA = 4,           /* a CUDA runtime call or kernel launch failed */
+  OTM_ETIMEOUT = 5,        /* a bounded device-side wait expired */
+  OTM_ENOTCONVERGED = 6    /* an iterative kernel hit its iteration limit */
+} otm_status;
+
+/* CSR sparse matrix (device arrays). */
+typedef struct otm_csr {
+  int64_t rows;
+  int64_t cols;
+  int64_t nnz;
+  const int32_t* row_ptr;  /* rows + 1 */
+  const int32_t* col;      /* nnz */
+  const float* val;        /* nnz */
+} otm_csr;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int otm_version(void);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* otm_last_error(void);
+
+/* Number of kernels this library has launched in this process so far (all
+ * threads, all devices).  A diagnostic for profiling and launch accounting. */
+uint64_t otm_launch_count(void);
+
+/* ------------------------------------------------------------------------ */
+/* Moments (Section 2.1 Eqs. (1)-(2); length normalisation as read for Lemma 1) */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * otm_topic_moments -- per-document statistics and first moments of a corpus.
+ * X: n x d word counts (documents x vocabulary).
+ * Outputs: row_invlen[n] = 1/l_t (0 if l_t = 0), row_w[n] = 1/(l_t (l_t - 1))
+ * (0 if l_t < 2), M1[d] = (1/n) sum_t c_t / l_t (Eq. (1)), delta[d] =
+ * (1/n) sum_t row_w[t] c_t (the diagonal term of Eq. (2)).  FP64 sums.
+ */
+otm_status otm_topic_moments(const otm_csr* X, float* row_invlen, float* row_w,
+                             double* M1, double* delta, void* stream);
+
+/*
+ * otm_topic_m2_apply -- O = M2 S for Eq. (2) without forming M2:
+ *   M2 S = (alpha0+1) [ (1/n) X^T diag(row_w) (X S) - diag(delta) S ]
+ *          - alpha0 M1 (M1^T S).
+ * S: d x m, O: d x m (float32, row-major; O must not alias S).
+ * Scratch: otm_topic_m2_workspace(n, m) bytes.
+ */
+size_t otm_topic_m2_workspace(int64_t n, int64_t m);
+otm_status otm_topic_m2_apply(const otm_csr* X, const float* row_w, const double* M1,
+                              const double* delta, double alpha0, const float* S,
+                              int64_t m, float* O, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * otm_pairs_apply -- O = Pairs(Y1, Y2) S = (1/n_X) G_{X,Y1}^T (G_{X,Y2} S)
+ * (Section 2.2; the sparse core of Eqs. (7)-(8) and (10)).
+ * G1: n_X x n_1, G2: n_X x n_2 (same n_X), S: n_2 x m, O: n_1 x m (float32).
+ * Scratch: otm_pairs_workspace(n_X, m) bytes.
+ */
+size_t otm_pairs_workspace(int64_t n_x, int64_t m);
+otm_status otm_pairs_apply(const otm_csr* G1, const otm_csr* G2, const float* S, int64_t m,
+                           float* O, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Dense kernels of the whitening (Section 4.2: tall-thin QR, short-thin SVD) */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * otm_orthonormalize -- in-place tall-thin QR (Section 4.2 "Tall-thin QR"):
+ * A (rows x m, float32, row-major, rows >= m, m <= 160) is replaced by an
+ * orthonormal basis Q of its column space.  Shifted Cholesky-QR, three passes
+ * (Gram matrices accumulated in FP64).  Scratch: otm_orth_workspace(m).
+ * OTM_ENOTCONVERGED if a Cholesky pivot fails even after the shift.
+ */
+size_t otm_orth_workspace(int64_t m);
+otm_status otm_orthonormalize(float* A, int64_t rows, int64_t m, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/*
+ * otm_syev -- FP64 symmetric eigendecomposition of a small matrix (the
+ * "short-thin SVD" of Section 4.2, Table 3): A (n x n, FP64, row-major, n <= 160,
+ * symmetrised as (A + A^T)/2) -> evals[n] descending, evecs (n x n, row-major,
+ * column j = eigenvector j, sign fixed so its largest-magnitude entry is
+ * positive).  Cyclic Jacobi in FP32 followed by FP64 iterative refinement.
+ * Scratch: otm_syev_workspace(n).  OTM_ENOTCONVERGED if the Jacobi sweeps hit
+ * their limit.
+ */
+size_t otm_syev_workspace(int64_t n);
+otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Whitening (Section 3.1, Section 4.2)                                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * otm_whiten_topic -- randomised whitening of the topic-model M2 (Eq. (2)):
+ * range finder with the caller's random projection S (d x kt, kt = k + p,
+ * k < kt <= 160, kt <= d), power_iters power iterations, tall-thin QR, FP64
+ * eigendecomposition of Omega = Q^T M2 Q, truncation to the k largest.
+ * Outputs: W (d x k, float32) with W^T M2 W = I; Q (d x kt, float32); Cw, Cp
+ * (kt x k, FP64) with W = Q Cw and (W^T)^+ = Q Cp; eig[k] (descending); M1[d];
+ * row_invlen[n], row_w[n] (as otm_topic_moments).  Returns OTM_ENOTPSD if the
+ * k-th eigenvalue is not positive.  Synchronises the stream (the eigenvalue
+ * check).  Scratch: otm_whiten_topic_workspace(n, d, k, kt).
+ */
+size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t k, int64_t kt);
+otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t kt,
+                            int power_iters, double alpha0, float* W, float* Q, double* Cw,
+                            double* Cp, double* eig, double* M1, float* row_invlen,
+                            float* row_w, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * otm_whiten_community -- randomised whitening of the community-model M2
+ * (Eq. (10), Sections 4.1-4.2).  G_XA, G_XB, G_XC: n_X x n_A, n_X x n_B,
+ * n_X x n_C adjacency blocks.  S_pairs (n_B x kt) and S_w (n_A x kt) are the
+ * random projections for the rank-k SVD of Pairs(C,B) and for the range
+ * finder of M2.  Steps: Pairs(C,B) ~ U_C diag(sigma) V_B^T; Z_B = L_B V_B^T,
+ * Z_C = L_C U_C^T (Eqs. (7)-(8) at rank k); the symmetric part of
+ * (alpha0+1) Z_C Pairs(C,B) Z_B^T - alpha0 M1 M1^T applied in factored form;
+ * range finder + QR + FP64 eig as in otm_whiten_topic.
+ * Outputs: W (n_A x k), W_B = Z_B^T W (n_B x k), W_C = Z_C^T W (n_C x k)
+ * (float32), Q (n_A x kt), Cw, Cp (kt x k FP64), eig[k], sigma[k] (singular
+ * values of Pairs(C,B)), M1[n_A] (FP64).  OTM_ENOTPSD as above.  Synchronises
+ * the stream.  Scratch: otm_whiten_community_workspace(n_X, n_A, n_B, n_C, k, kt).
+ */
+size_t otm_whiten_community_workspace(int64_t n_x, int64_t n_a, int64_t n_b, int64_t n_c,
+                                      int64_t k, int64_t kt);
+otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const otm_csr* G_XC,
+                                const float* S_pairs, const float* S_w, int64_t k, int64_t kt,
+                                int power_iters, double alpha0, float* W, float* W_B,
+                                float* W_C, float* Q, double* Cw, double* Cp, double* eig,
+                                double* sigma, double* M1, void* ws, size_t ws_bytes,
+                                void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Projection and means (Section 3.1 "whitened data", Section 4.1)          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * otm_project -- Y = diag(row_scale) X W: y_t = W^T c_t (times row_scale[t]).
+ * X: n x d CSR, W: d x k (float32), row_scale: n floats or NULL (= 1),
+ * Y: n x k (float32).  For topics row_scale = row_invlen (y_t = W^T c_t / l_t).
+ */
+otm_status otm_project(const otm_csr* X, const float* W, int64_t k, const float* row_scale,
+                       float* Y, void* stream);
+
+/*
+ * otm_column_mean -- ybar = (1/n) sum_t Y[t, :] in FP64 (the means y-bar of
+ * Section 3.2).  Y: n x k float32; ybar: k doubles.
+ */
+otm_status otm_column_mean(const float* Y, int64_t n, int64_t k, double* ybar, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Stochastic tensor gradient descent (Section 3.2, Lemma 3, Appendix A)     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * otm_sgd_step -- one STGD update over a minibatch (Lemma 3, Eq. (16)):
+ *   G = kappa V ((V^T V) o (V^T V)) - T_b(V, V, I),   V <- V - beta G,
+ * kappa = (1 + theta)/2, where column i of T_b(V, V, I) is the minibatch mean of
+ * the implicit tensor contraction
+ *   c1 <v_i,yA><v_i,yB> yC - c2 [<v_i,yA><v_i,yB> ybC + <v_i,yA><v_i,ybB> yC
+ *   + <v_i,ybA><v_i,yB> yC] + c3 <v_i,ybA><v_i,ybB> ybC,
+ * c1 = (a0+1)(a0+2)/2, c2 = a0(a0+1)/2, c3 = a0^2.  The tensor is never formed.
+ * V: k x k column-major float32, updated in place.  YA, YB, YC: b x k float32
+ * (may alias each other; equal pointers select the symmetric fast path).
+ * ybar3: 3 x k doubles (ybA, ybB, ybC).  1 <= k <= 128, b >= 1.
+ */
+otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float* YC,
+                        int64_t b, int64_t k, const double* ybar3, double theta, double beta,
+                        double alpha0, void* stream);
+
+/*
+ * otm_sgd_run -- the whole STGD loop in ONE persistent launch (V stays
+ * on-chip between steps, Section 4.3 "device interface").  For epoch e the
+ * samples are visited in the order perm[e * n .. e * n + n) in minibatches of b
+ * (the last one partial), step t = 1, 2, ... uses beta_t = beta0 / sqrt(t).
+ * YA, YB, YC: n x k (may alias); perm: epochs x n int32 (NULL = identity order
+ * every epoch).  If snapshot_every > 0, V after every snapshot_every-th step
+ * is written to V_snap[(t / snapshot_every - 1) * k * k ...] (caller sizes it
+ * for floor(total_steps / snapshot_every) matrices).
+ */
+otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
+                       int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
+                       int64_t b, double beta0, double theta, double alpha0,
+                       int64_t snapshot_every, float* V_snap, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Post-processing (Section 3.3, Lemma 4) and error evaluation               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * otm_unwhiten -- lambda_i = kappa ||v_i||^3; u_i = v_i / ||v_i||;
+ * comps[:, i] = lambda_i (W^T)^+ u_i with (W^T)^+ = Q Cp (Lemma 4).  With
+ * normalize != 0 each column is sign-flipped to a non-negative sum and divided
+ * by its sum (topic-word distributions).  alpha_hat_i = lambda_i^-2 / sum_j
+ * lambda_j^-2.  V: k x k column-major float32; Q: d x kt float32; Cp: kt x k
+ * FP64; comps: d x k FP64 row-major; lambda, alpha_hat: k doubles.
+ * Scratch: otm_unwhiten_workspace(d, k, kt).
+ */
+size_t otm_unwhiten_workspace(int64_t d, int64_t k, int64_t kt);
+otm_status otm_unwhiten(const float* V, int64_t k, const float* Q, int64_t d, int64_t kt,
+                        const double* Cp, double theta, int normalize, double* comps,
+                        double* lambda, double* alpha_hat, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/*
+ * otm_recon_error -- relative reconstruction error of the components in V
+ * against reference components (lam_true[k], U_true: k x k column-major FP64,
+ * unit columns):
+ *   err = || kappa sum_i v_i^(x)3 - sum_j lam_j u_j^(x)3 ||_F / || sum_j lam_j u_j^(x)3 ||_F,
+ * evaluated in closed form from Gram matrices (<x^(x)3, y^(x)3> = <x,y>^3), FP64.
+ * Writes one double to err (device).  Scratch: otm_recon_error_workspace(k).
+ */
+size_t otm_recon_error_workspace(int64_t k);
+otm_status otm_recon_error(const float* V, int64_t k, double theta, const double* U_true,
+                           const double* lam_true, double* err, void* ws, size_t ws_bytes,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OTM_H */

@@ -1,0 +1,119 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/otm.h"
+
+namespace otm {
+
+// Thread-local error message (otm_last_error).
+otm_status set_error(otm_status st, const char* fmt, ...);
+void clear_error();
+
+#define OTM_CHECK_CUDA(expr)                                                       \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return ::otm::set_error(OTM_ECUDA, "%s failed: %s (%s:%d)", #expr,           \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);         \
+  } while (0)
+
+void count_launch();
+
+#define OTM_CHECK_LAUNCH()      \
+  do {                          \
+    ::otm::count_launch();      \
+    OTM_CHECK_CUDA(cudaGetLastError()); \
+  } while (0)
+
+#define OTM_TRY(expr)                  \
+  do {                                 \
+    otm_status s_ = (expr);            \
+    if (s_ != OTM_OK) return s_;       \
+  } while (0)
+
+#define OTM_REQUIRE(cond, ...)                                  \
+  do {                                                          \
+    if (!(cond)) return ::otm::set_error(OTM_EINVAL, __VA_ARGS__); \
+  } while (0)
+
+// Bump allocator over a caller-provided workspace; 256-byte aligned slices.
+struct Workspace {
+  char* base;
+  size_t size;
+  size_t used;
+  Workspace(void* p, size_t n) : base(static_cast<char*>(p)), size(n), used(0) {}
+  template <typename T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    size_t bytes = count * sizeof(T);
+    if (base == nullptr || off + bytes > size) return nullptr;
+    used = off + bytes;
+    return reinterpret_cast<T*>(base + off);
+  }
+};
+
+// Size accounting that mirrors Workspace::take.
+struct WorkspaceSize {
+  size_t used = 0;
+  template <typename T>
+  WorkspaceSize& add(size_t count) {
+    used = ((used + 255) & ~size_t(255)) + count * sizeof(T);
+    return *this;
+  }
+  size_t bytes() const { return used + 256; }
+};
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+otm_status check_csr(const otm_csr* X, const char* name);
+
+// ---- sparse kernels (sparse.cu) ----
+// out[r, :] = row_scale[r] * sum_e val[e] * B[col[e], :]   (gather SpMM)
+otm_status spmm_gather(const otm_csr* X, const float* B, int64_t m, const float* row_scale,
+                       float* out, cudaStream_t st);
+// out[col[e], :] += alpha * row_scale[r] * val[e] * P[r, :]  (scatter SpMM, out pre-zeroed)
+otm_status spmm_scatter(const otm_csr* X, const float* P, int64_t m, const float* row_scale,
+                        float alpha, float* out, cudaStream_t st);
+otm_status topic_moments(const otm_csr* X, float* row_invlen, float* row_w, double* M1,
+                         double* delta, cudaStream_t st);
+// M1[c] = (1/rows) sum_r X[r, c]  (community first moment, Eq. (9))
+otm_status column_sums_scaled(const otm_csr* X, double scale, double* out, cudaStream_t st);
+
+// ---- dense kernels (dense.cu) ----
+// C (m x p, FP64) = alpha * A^T B, A: rows x m, B: rows x p, float32 row-major.
+// If accumulate == 0 C is overwritten, else added to.
+otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t m, int64_t p,
+                          double alpha, double* C, int accumulate, cudaStream_t st);
+// out (rows x p, float32) = A (rows x m, float32) * C (m x p, FP64, rounded to FP32)
+//   [+ rank-one term: - r1_alpha * r1_u[r] * r1_v[c]] [then * colscale[c]]
+otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
+                         float* out, const double* r1_u, const double* r1_v, double r1_alpha,
+                         cudaStream_t st);
+// out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64), FP64 accumulation.
+otm_status gemm_nn_f64(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
+                       double* out, cudaStream_t st);
+// Small FP64 GEMM: C (m x n) = op(A) op(B), op = transpose if flag set.
+otm_status dgemm_small(int ta, int tb, int64_t m, int64_t n, int64_t kk, double alpha,
+                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                       double* C, int64_t ldc, cudaStream_t st);
+size_t orth_workspace(int64_t m);
+otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cudaStream_t st);
+size_t syev_workspace(int64_t n);
+otm_status syev(const double* A, int64_t n, double* evals, double* evecs, Workspace& ws,
+                cudaStream_t st);
+// out[j] = sum_r u[r] * A[r, j]  (FP64 u, float32 A rows x m)
+otm_status vec_tn(const double* u, const float* A, int64_t rows, int64_t m, double* out,
+                  cudaStream_t st);
+// From evals (descending, n) and evecs (n x n): Cw[:, i] = U[:, i] / sqrt(l_i),
+// Cp[:, i] = U[:, i] * sqrt(l_i) for i < k (n x k each, FP64); eig[i] = l_i.
+// Sets *flag (device int) to 1 if l_{k-1} <= 0.
+otm_status whitening_factors(const double* evals, const double* evecs, int64_t n, int64_t k,
+                             double* Cw, double* Cp, double* eig, int* flag, cudaStream_t st);
+
+// ---- whitening composites (whiten.cu) ----
+
+}  // namespace otm

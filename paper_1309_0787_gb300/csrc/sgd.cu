@@ -1,0 +1,504 @@
+// Stochastic tensor gradient descent on the implicit whitened tensor
+// (Section 3.2, Lemma 3 / Eq. (16), Appendix A), fused into one kernel.
+//
+// Per step, for the minibatch Y_b (b samples, three views) and V (k x k):
+//   A_A = V^T Y_A^T, A_B = V^T Y_B^T                         (k x b)
+//   a_A = V^T ybar_A, a_B = V^T ybar_B                        (k)
+//   B   = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B)           (column-broadcast a)
+//   s   = (1/b) sum_t (A_A o A_B)[:, t]
+//   G_data = (1/b) Y_C^T B^T + ybar_C (c3 a_A o a_B - c2 s)^T  (column i = T_b(v_i, v_i, I))
+//   G_gram = V ((V^T V) o (V^T V))
+//   V <- V - beta_t (kappa G_gram - G_data)
+// This is the stacked ("BLAS III", Section 4.3) form of the per-component
+// update of Lemma 3; the k x k x k tensor is never formed.
+//
+// GB300 mapping: one thread-block cluster runs the whole loop of steps (the
+// "device interface" of Section 4.3: V never leaves the chip).  Each CTA of
+// the cluster holds a full copy of V in shared memory and processes a slice
+// of the minibatch in chunks of 32 samples (register-tiled FP32 FMAs for both
+// products).  Partial Y_C^T B^T are reduced column-wise through distributed
+// shared memory: CTA q owns columns [q*cpq, (q+1)*cpq), sums them over the
+// cluster, adds the Gram and mean terms and broadcasts the new columns into
+// every CTA's next-V buffer.  Two cluster barriers per step; no global memory
+// traffic besides the samples.
+#include <cooperative_groups.h>
+
+#include "otm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace otm {
+namespace {
+
+constexpr int TC = 32;        // samples per chunk
+constexpr int THREADS = 256;  // 8 warps
+constexpr int KMAX = 128;
+
+struct SgdArgs {
+  const float* YA;
+  const float* YB;
+  const float* YC;
+  const int32_t* perm;
+  const double* ybar3;
+  float* V;
+  float* V_snap;
+  int64_t n, b, spe, total_steps, snapshot_every;
+  int k;
+  double beta0;
+  float c1, c2, c3, kappa;
+};
+
+struct Layout {
+  int kp, ldk, cpq, nview;
+  size_t off_v0, off_v1, off_u, off_p6, off_small, total_floats;
+};
+
+__host__ __device__ inline Layout make_layout(int k, int CL, bool sym) {
+  Layout L;
+  L.kp = (k + 3) & ~3;
+  L.ldk = L.kp;
+  L.cpq = (k + CL - 1) / CL;
+  L.nview = sym ? 1 : 3;
+  const size_t vsz = (size_t)L.kp * L.ldk;
+  size_t u1 = (size_t)(L.nview + 1) * TC * L.ldk;
+  const size_t u = u1 > vsz ? u1 : vsz;
+  L.off_v0 = 0;
+  L.off_v1 = vsz;
+  L.off_u = 2 * vsz;
+  L.off_p6 = L.off_u + u;
+  L.off_small = L.off_p6 + (size_t)3 * L.cpq * L.ldk;
+  L.total_floats = L.off_small + 6 * (size_t)L.ldk + (size_t)L.cpq + 8;
+  return L;
+}
+
+template <bool SYM, int MT>
+__global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int q = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = a.k;
+  const Layout L = make_layout(k, CL, SYM);
+  const int ldk = L.ldk, kp = L.kp, cpq = L.cpq;
+  float* V0 = sm + L.off_v0;
+  float* V1 = sm + L.off_v1;
+  float* U = sm + L.off_u;
+  float* Ya = U;
+  float* Yb = SYM ? U : U + TC * ldk;
+  float* Yc = SYM ? U : U + 2 * TC * ldk;
+  float* Bt = U + L.nview * TC * ldk;
+  float* Gp = U;  // k x ldk partial Y_C^T B^T (after the chunk loop)
+  float* gd = sm + L.off_p6;              // cpq x ldk
+  float* Hm = gd + cpq * ldk;             // cpq x ldk
+  float* vn = Hm + cpq * ldk;             // cpq x ldk
+  float* aA = sm + L.off_small;
+  float* aB = aA + ldk;
+  float* ybA = aB + ldk;
+  float* ybB = ybA + ldk;
+  float* ybC = ybB + ldk;
+  float* spart = ybC + ldk;
+  float* sown = spart + ldk;
+
+  // ---- initial state: V (zero padded) and the means ----
+  for (int idx = tid; idx < kp * ldk; idx += THREADS) {
+    const int i = idx / ldk, r = idx % ldk;
+    V0[idx] = (i < k && r < k) ? a.V[(int64_t)i * k + r] : 0.f;
+  }
+  for (int r = tid; r < ldk; r += THREADS) {
+    ybA[r] = r < k ? (float)a.ybar3[r] : 0.f;
+    ybB[r] = r < k ? (float)a.ybar3[k + r] : 0.f;
+    ybC[r] = r < k ? (float)a.ybar3[2 * k + r] : 0.f;
+  }
+  const int own_lo = q * cpq, own_hi = min(k, own_lo + cpq);
+  const int64_t bq = (a.b + CL - 1) / CL;
+  __syncthreads();
+
+  // GEMM1 thread mapping: warp w covers components 16w..16w+15 as i = 16w + il + 4j,
+  // lane covers samples t = tl + 8j'.
+  const int tl = lane & 7, il = lane >> 3;
+  const int ibase = 16 * warp + il;
+
+  for (int64_t s = 0; s < a.total_steps; ++s) {
+    float* Vc = (s & 1) ? V1 : V0;
+    float* Vn = (s & 1) ? V0 : V1;
+    const int64_t e = s / a.spe, jb = s % a.spe;
+    const int64_t pos0 = jb * a.b;
+    const int64_t beff = min(a.b, a.n - pos0);
+    const float beta = (float)(a.beta0 / sqrt((double)(s + 1)));
+    const float inv_b = 1.f / (float)beff;
+
+    // phase 1: a_A = V^T ybar_A, a_B = V^T ybar_B, s partial = 0
+    for (int i = warp; i < kp; i += THREADS / 32) {
+      float x = 0.f, y = 0.f;
+      for (int r = lane; r < ldk; r += 32) {
+        const float v = Vc[i * ldk + r];
+        x = fmaf(v, ybA[r], x);
+        y = fmaf(v, ybB[r], y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane == 0) {
+        aA[i] = x;
+        aB[i] = y;
+        spart[i] = 0.f;
+      }
+    }
+    float gacc[MT][4][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) gacc[m][x][y] = 0.f;
+    __syncthreads();
+
+    const int64_t my_lo = (int64_t)q * bq, my_hi = min(beff, my_lo + bq);
+    for (int64_t c0 = my_lo; c0 < my_hi; c0 += TC) {
+      // load the chunk (rows beyond the slice are zero)
+      const int nv4 = ldk / 4;
+      for (int idx = tid; idx < TC * nv4; idx += THREADS) {
+        const int tt = idx / nv4, r4 = idx % nv4;
+        const int64_t p = c0 + tt;
+        float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va, vc = va;
+        const int64_t row =
+            p < my_hi ? (a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p) : -1;
+        // an index outside [0, n) (invalid permutation) reads as a zero sample
+        if (row >= 0 && row < a.n) {
+          const int r = 4 * r4;
+          const float* pa = a.YA + row * k;
+          float t4[4];
+#pragma unroll
+          for (int z = 0; z < 4; ++z) t4[z] = (r + z < k) ? pa[r + z] : 0.f;
+          va = make_float4(t4[0], t4[1], t4[2], t4[3]);
+          if (!SYM) {
+            const float* pb = a.YB + row * k;
+            const float* pc = a.YC + row * k;
+#pragma unroll
+            for (int z = 0; z < 4; ++z) t4[z] = (r + z < k) ? pb[r + z] : 0.f;
+            vb = make_float4(t4[0], t4[1], t4[2], t4[3]);
+#pragma unroll
+            for (int z = 0; z < 4; ++z) t4[z] = (r + z < k) ? pc[r + z] : 0.f;
+            vc = make_float4(t4[0], t4[1], t4[2], t4[3]);
+          }
+        }
+        reinterpret_cast<float4*>(Ya + tt * ldk)[r4] = va;
+        if (!SYM) {
+          reinterpret_cast<float4*>(Yb + tt * ldk)[r4] = vb;
+          reinterpret_cast<float4*>(Yc + tt * ldk)[r4] = vc;
+        }
+      }
+      __syncthreads();
+
+      // GEMM1: A_A, A_B for 4 components x 4 samples per thread, then B
+      if (16 * warp < kp) {
+        float accA[4][4], accB[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            accA[x][y] = 0.f;
+            accB[x][y] = 0.f;
+          }
+        for (int r = 0; r < ldk; r += 4) {
+          float4 v[4], ya[4], yb[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int i = ibase + 4 * j;
+            v[j] = i < kp ? *reinterpret_cast<const float4*>(Vc + i * ldk + r)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            ya[j] = *reinterpret_cast<const float4*>(Ya + (tl + 8 * j) * ldk + r);
+            if (!SYM) yb[j] = *reinterpret_cast<const float4*>(Yb + (tl + 8 * j) * ldk + r);
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+              float t = accA[x][y];
+              t = fmaf(v[x].x, ya[y].x, t);
+              t = fmaf(v[x].y, ya[y].y, t);
+              t = fmaf(v[x].z, ya[y].z, t);
+              t = fmaf(v[x].w, ya[y].w, t);
+              accA[x][y] = t;
+              if (!SYM) {
+                float u = accB[x][y];
+                u = fmaf(v[x].x, yb[y].x, u);
+                u = fmaf(v[x].y, yb[y].y, u);
+                u = fmaf(v[x].z, yb[y].z, u);
+                u = fmaf(v[x].w, yb[y].w, u);
+                accB[x][y] = u;
+              }
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int i = ibase + 4 * x;
+          const float ai = i < kp ? aA[i] : 0.f, bi = i < kp ? aB[i] : 0.f;
+          float ssum = 0.f;
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const float xa = accA[x][y];
+            const float xb = SYM ? xa : accB[x][y];
+            const float pr = xa * xb;
+            ssum += pr;
+            const float bv = a.c1 * pr - a.c2 * (bi * xa + ai * xb);
+            if (i < kp) Bt[(tl + 8 * y) * ldk + i] = bv;
+          }
+          // sum over the 8 sample lanes sharing this component (lane bits 0..2)
+          ssum += __shfl_xor_sync(0xffffffffu, ssum, 1);
+          ssum += __shfl_xor_sync(0xffffffffu, ssum, 2);
+          ssum += __shfl_xor_sync(0xffffffffu, ssum, 4);
+          if (tl == 0 && i < kp) spart[i] += ssum;
+        }
+      }
+      __syncthreads();
+
+      // GEMM2: Gp[r][i] += sum_t Y_C[t][r] B[t][i]; 4 x 4 tiles, MT tiles per thread
+      {
+        const int nt = kp / 4;
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+          const int g = tid + THREADS * m;
+          if (g < nt * nt) {
+            const int r0 = 4 * (g / nt), i0 = 4 * (g % nt);
+#pragma unroll 8
+            for (int tt = 0; tt < TC; ++tt) {
+              const float4 yc = *reinterpret_cast<const float4*>(Yc + tt * ldk + r0);
+              const float4 bt = *reinterpret_cast<const float4*>(Bt + tt * ldk + i0);
+              const float ycv[4] = {yc.x, yc.y, yc.z, yc.w};
+              const float btv[4] = {bt.x, bt.y, bt.z, bt.w};
+#pragma unroll
+              for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) gacc[m][x][y] = fmaf(ycv[x], btv[y], gacc[m][x][y]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // partial results to shared memory: Gp[i][r] (column i contiguous)
+    {
+      const int nt = kp / 4;
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        const int g = tid + THREADS * m;
+        if (g < nt * nt) {
+          const int r0 = 4 * (g / nt), i0 = 4 * (g % nt);
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) Gp[(i0 + y) * ldk + r0 + x] = gacc[m][x][y];
+        }
+      }
+    }
+    cluster.sync();  // partials of every CTA visible cluster-wide
+
+    // phase 6: owned columns -- reduce over the cluster, Gram term, update, broadcast
+    const int nown = own_hi - own_lo;
+    if (tid < nown) {
+      float ss = 0.f;
+      for (int c = 0; c < CL; ++c) ss += cluster.map_shared_rank(spart, c)[own_lo + tid];
+      sown[tid] = ss;
+    }
+    for (int idx = tid; idx < nown * kp; idx += THREADS) {
+      const int jj = idx / kp, r = idx % kp;
+      const int i = own_lo + jj;
+      float g = 0.f;
+      for (int c = 0; c < CL; ++c) g += cluster.map_shared_rank(Gp, c)[i * ldk + r];
+      gd[jj * ldk + r] = g;
+    }
+    for (int idx = tid; idx < nown * kp; idx += THREADS) {
+      const int jj = idx / kp, j = idx % kp;
+      const float* vi = Vc + (own_lo + jj) * ldk;
+      const float* vj = Vc + j * ldk;
+      float h = 0.f;
+      for (int r = 0; r < ldk; r += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(vi + r);
+        const float4 y = *reinterpret_cast<const float4*>(vj + r);
+        h = fmaf(x.x, y.x, h);
+        h = fmaf(x.y, y.y, h);
+        h = fmaf(x.z, y.z, h);
+        h = fmaf(x.w, y.w, h);
+      }
+      Hm[jj * ldk + j] = h * h;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nown * kp; idx += THREADS) {
+      const int jj = idx / kp, r = idx % kp;
+      const int i = own_lo + jj;
+      float g = 0.f;
+      for (int j = 0; j < k; ++j) g = fmaf(Hm[jj * ldk + j], Vc[j * ldk + r], g);
+      const float gdata =
+          gd[jj * ldk + r] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * sown[jj] * inv_b);
+      const float vnew = Vc[i * ldk + r] - beta * (a.kappa * g - gdata);
+      vn[jj * ldk + r] = (r < k) ? vnew : 0.f;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < CL * nown * kp; idx += THREADS) {
+      const int c = idx / (nown * kp), rem = idx % (nown * kp);
+      const int jj = rem / kp, r = rem % kp;
+      cluster.map_shared_rank(Vn, c)[(own_lo + jj) * ldk + r] = vn[jj * ldk + r];
+    }
+    cluster.sync();  // next V complete everywhere; partials may be overwritten
+
+    if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0) {
+      float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
+      for (int idx = tid; idx < nown * k; idx += THREADS) {
+        const int jj = idx / k, r = idx % k;
+        dst[(int64_t)(own_lo + jj) * k + r] = Vn[(own_lo + jj) * ldk + r];
+      }
+    }
+  }
+  const float* Vf = (a.total_steps & 1) ? V1 : V0;
+  for (int idx = tid; idx < (own_hi - own_lo) * k; idx += THREADS) {
+    const int jj = idx / k, r = idx % k;
+    a.V[(int64_t)(own_lo + jj) * k + r] = Vf[(own_lo + jj) * ldk + r];
+  }
+}
+
+template <bool SYM, int MT>
+otm_status launch_mt(const SgdArgs& args, int CL, cudaStream_t st) {
+  const Layout L = make_layout(args.k, CL, SYM);
+  const size_t smem = L.total_floats * sizeof(float);
+  auto kern = sgd_cluster_kernel<SYM, MT>;
+  OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (CL > 8)
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
+  count_launch();
+  return OTM_OK;
+}
+
+template <bool SYM>
+otm_status launch_sym(const SgdArgs& args, int CL, cudaStream_t st) {
+  const int nt = ((args.k + 3) & ~3) / 4;
+  const int MT = (nt * nt + THREADS - 1) / THREADS;
+  switch (MT) {
+    case 1: return launch_mt<SYM, 1>(args, CL, st);
+    case 2: return launch_mt<SYM, 2>(args, CL, st);
+    case 3: return launch_mt<SYM, 3>(args, CL, st);
+    default: return launch_mt<SYM, 4>(args, CL, st);
+  }
+}
+
+// Largest supported cluster size whose shared-memory footprint fits (16, then 8).
+int pick_cluster(int k, bool sym) {
+  static int max_smem = 0;
+  if (max_smem == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (max_smem <= 0) max_smem = 227 * 1024;
+  }
+  for (int CL : {16, 8, 4, 2, 1}) {
+    const Layout L = make_layout(k, CL, sym);
+    if (L.total_floats * sizeof(float) <= (size_t)max_smem) return CL;
+  }
+  return 0;
+}
+
+otm_status run(float* V, const float* YA, const float* YB, const float* YC, int64_t n, int64_t k,
+               const double* ybar3, const int32_t* perm, int64_t epochs, int64_t b,
+               double beta0, double theta, double alpha0, int64_t snapshot_every, float* V_snap,
+               cudaStream_t st) {
+  SgdArgs args;
+  const bool sym = (YA == YB) && (YB == YC);
+  args.YA = YA;
+  args.YB = YB;
+  args.YC = YC;
+  args.perm = perm;
+  args.ybar3 = ybar3;
+  args.V = V;
+  args.V_snap = V_snap;
+  args.n = n;
+  args.b = b;
+  args.spe = (n + b - 1) / b;
+  args.total_steps = args.spe * epochs;
+  args.snapshot_every = snapshot_every;
+  args.k = (int)k;
+  args.beta0 = beta0;
+  const double a0 = alpha0;
+  args.c1 = (float)((a0 + 1.0) * (a0 + 2.0) / 2.0);
+  args.c2 = (float)(a0 * (a0 + 1.0) / 2.0);
+  args.c3 = (float)(a0 * a0);
+  args.kappa = (float)(0.5 * (1.0 + theta));
+  int CL = pick_cluster((int)k, sym);
+  if (CL == 0) return set_error(OTM_EINVAL, "sgd: k=%lld does not fit shared memory", (long long)k);
+  // honour the device's limit on active clusters of this size
+  static int cl16_ok = -1;
+  if (CL == 16 && cl16_ok < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = make_layout((int)k, 16, sym).total_floats * sizeof(float);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    auto kern = sgd_cluster_kernel<false, 4>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cfg.dynamicSmemBytes);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int nclusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    cl16_ok = (e == cudaSuccess && nclusters > 0) ? 1 : 0;
+    cudaGetLastError();
+  }
+  if (CL == 16 && cl16_ok == 0) CL = 8;
+  return sym ? launch_sym<true>(args, CL, st) : launch_sym<false>(args, CL, st);
+}
+
+}  // namespace
+}  // namespace otm
+
+using namespace otm;
+
+extern "C" {
+
+otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float* YC, int64_t b,
+                        int64_t k, const double* ybar3, double theta, double beta,
+                        double alpha0, void* stream) {
+  clear_error();
+  OTM_REQUIRE(V && YA && YB && YC && ybar3, "otm_sgd_step: null pointer");
+  OTM_REQUIRE(k >= 1 && k <= KMAX, "otm_sgd_step: k=%lld outside [1, %d]", (long long)k, KMAX);
+  OTM_REQUIRE(b >= 1, "otm_sgd_step: b must be >= 1");
+  return run(V, YA, YB, YC, b, k, ybar3, nullptr, 1, b, beta, theta, alpha0, 0, nullptr,
+             as_stream(stream));
+}
+
+otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
+                       int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
+                       int64_t b, double beta0, double theta, double alpha0,
+                       int64_t snapshot_every, float* V_snap, void* stream) {
+  clear_error();
+  OTM_REQUIRE(V && YA && YB && YC && ybar3, "otm_sgd_run: null pointer");
+  OTM_REQUIRE(k >= 1 && k <= KMAX, "otm_sgd_run: k=%lld outside [1, %d]", (long long)k, KMAX);
+  OTM_REQUIRE(n >= 1 && b >= 1 && epochs >= 0, "otm_sgd_run: need n >= 1, b >= 1, epochs >= 0");
+  OTM_REQUIRE(snapshot_every >= 0, "otm_sgd_run: snapshot_every must be >= 0");
+  OTM_REQUIRE(snapshot_every == 0 || V_snap, "otm_sgd_run: V_snap required for snapshots");
+  if (epochs == 0) return OTM_OK;
+  return run(V, YA, YB, YC, n, k, ybar3, perm, epochs, b, beta0, theta, alpha0, snapshot_every,
+             V_snap, as_stream(stream));
+}
+
+}  // extern "C"

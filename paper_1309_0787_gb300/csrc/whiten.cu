@@ -1,0 +1,364 @@
+// Whitening (Section 3.1) by the randomised low-rank method of Section 4.2.
+//
+// Topic model: M2 of Eq. (2) is applied implicitly, M2 S = (a0+1)[(1/n) X^T
+// diag(w) (X S) - diag(delta) S] - a0 M1 (M1^T S), i.e. one gather SpMM, one
+// scatter SpMM and a fused diagonal/rank-one epilogue; the d x d matrix is
+// never formed.
+//
+// Community model: Pairs(C,B) = (1/n_X) G_XC^T G_XB gets a rank-k randomised
+// SVD (the pseudo-inverses of Eqs. (7)-(8)); Z_B, Z_C and M2 of Eq. (10) are
+// then kept in factored form (Section 4.1, "we avoid products of sizes
+// O(n) x O(n)"): with L = [L_C | L_B] (n_A x 2k) and K = U_C^T Pairs(C,B) V_B,
+//   sym(M2) X = L [ (a0+1)/2 K (L_B^T X) ; (a0+1)/2 K^T (L_C^T X) ] - a0 M1 (M1^T X).
+//
+// Both then run the same range finder: Q = orth(M2 S); q times Q = orth(M2 Q);
+// Omega = Q^T M2 Q; FP64 eigendecomposition; W = Q U_k Lambda_k^{-1/2}.
+#include "otm_internal.cuh"
+
+namespace otm {
+namespace {
+
+__global__ void topic_m2_epilogue_kernel(float* __restrict__ O, const float* __restrict__ S,
+                                         const double* __restrict__ delta,
+                                         const double* __restrict__ M1,
+                                         const double* __restrict__ u, int64_t d, int64_t m,
+                                         double a0) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d * m) return;
+  const int64_t r = idx / m, j = idx % m;
+  const double v = (a0 + 1.0) * ((double)O[idx] - delta[r] * (double)S[idx]) - a0 * M1[r] * u[j];
+  O[idx] = (float)v;
+}
+
+__global__ void concat2_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                               int64_t rows, int64_t k, float* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * 2 * k) return;
+  const int64_t r = idx / (2 * k), c = idx % (2 * k);
+  out[idx] = c < k ? A[r * k + c] : B[r * k + c - k];
+}
+
+__global__ void scale_cols_mod_kernel(float* __restrict__ L, int64_t rows, int64_t k,
+                                      const double* __restrict__ ev) {
+  // L is rows x 2k; column c is divided by sigma_{c mod k} = sqrt(ev[c mod k]).
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * 2 * k) return;
+  const int64_t c = idx % (2 * k);
+  L[idx] = (float)((double)L[idx] / sqrt(ev[c % k]));
+}
+
+__global__ void sqrt_vec_kernel(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = sqrt(a[i] > 0.0 ? a[i] : 0.0);
+}
+
+// First k columns of an n x n row-major matrix -> n x k.
+__global__ void take_cols_kernel(const double* __restrict__ a, int64_t n, int64_t k,
+                                 double* __restrict__ b) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * k) return;
+  b[idx] = a[(idx / k) * n + idx % k];
+}
+
+inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+struct TopicOp {
+  const otm_csr* X;
+  const float* row_w;
+  const double* M1;
+  const double* delta;
+  double a0;
+  float* P;   // n x m scratch
+  double* u;  // m scratch
+  otm_status apply(const float* S, int64_t m, float* O, cudaStream_t st) const {
+    const int64_t n = X->rows, d = X->cols;
+    OTM_TRY(spmm_gather(X, S, m, row_w, P, st));
+    OTM_CHECK_CUDA(cudaMemsetAsync(O, 0, sizeof(float) * d * m, st));
+    OTM_TRY(spmm_scatter(X, P, m, nullptr, (float)(1.0 / (double)(n > 0 ? n : 1)), O, st));
+    OTM_TRY(vec_tn(M1, S, d, m, u, st));
+    topic_m2_epilogue_kernel<<<blocks_for(d * m), 256, 0, st>>>(O, S, delta, M1, u, d, m, a0);
+    OTM_CHECK_LAUNCH();
+    return OTM_OK;
+  }
+};
+
+struct CommunityOp {
+  const float* L;   // n_A x 2k  ([L_C | L_B])
+  const double* K;  // k x k
+  const double* M1; // n_A
+  int64_t n_a, k;
+  double a0;
+  double* ab;    // 2k x m scratch
+  double* coef;  // 2k x m scratch
+  double* u;     // m scratch
+  otm_status apply(const float* X, int64_t m, float* O, cudaStream_t st) const {
+    OTM_TRY(gemm_tn_f64acc(L, X, n_a, 2 * k, m, 1.0, ab, 0, st));  // [L_C^T X ; L_B^T X]
+    OTM_TRY(vec_tn(M1, X, n_a, m, u, st));
+    const double s = 0.5 * (a0 + 1.0);
+    // top rows multiply L_C: s K (L_B^T X); bottom rows multiply L_B: s K^T (L_C^T X)
+    OTM_TRY(dgemm_small(0, 0, k, m, k, s, K, k, ab + k * m, m, 0.0, coef, m, st));
+    OTM_TRY(dgemm_small(1, 0, k, m, k, s, K, k, ab, m, 0.0, coef + k * m, m, st));
+    OTM_TRY(gemm_nn_small(L, n_a, 2 * k, coef, m, O, M1, u, a0, st));
+    return OTM_OK;
+  }
+};
+
+// Range finder + QR + eig + whitening factors, shared by both models.
+template <class Op>
+otm_status range_finder(const Op& op, int64_t d, const float* S, int64_t k, int64_t kt,
+                        int power_iters, float* W, float* Q, double* Cw, double* Cp, double* eig,
+                        Workspace& ws, cudaStream_t st, int* flag) {
+  float* O = ws.take<float>(d * kt);
+  double* Om = ws.take<double>(kt * kt);
+  double* ev = ws.take<double>(kt);
+  double* evec = ws.take<double>(kt * kt);
+  if (!O || !Om || !ev || !evec) return set_error(OTM_EINVAL, "whiten: workspace too small");
+  const size_t mark = ws.used;
+  OTM_TRY(op.apply(S, kt, Q, st));
+  OTM_TRY(orthonormalize(Q, d, kt, ws, st));
+  ws.used = mark;
+  for (int it = 0; it < power_iters; ++it) {
+    OTM_TRY(op.apply(Q, kt, O, st));
+    OTM_CHECK_CUDA(cudaMemcpyAsync(Q, O, sizeof(float) * d * kt, cudaMemcpyDeviceToDevice, st));
+    OTM_TRY(orthonormalize(Q, d, kt, ws, st));
+    ws.used = mark;
+  }
+  OTM_TRY(op.apply(Q, kt, O, st));
+  OTM_TRY(gemm_tn_f64acc(Q, O, d, kt, kt, 1.0, Om, 0, st));
+  OTM_TRY(syev(Om, kt, ev, evec, ws, st));
+  ws.used = mark;
+  OTM_TRY(whitening_factors(ev, evec, kt, k, Cw, Cp, eig, flag, st));
+  OTM_TRY(gemm_nn_small(Q, d, kt, Cw, k, W, nullptr, nullptr, 0.0, st));
+  return OTM_OK;
+}
+
+otm_status read_flag(int* flag, cudaStream_t st, int* out) {
+  OTM_CHECK_CUDA(cudaMemcpyAsync(out, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
+  return OTM_OK;
+}
+
+size_t range_finder_ws(int64_t d, int64_t kt) {
+  WorkspaceSize w;
+  w.add<float>(d * kt).add<double>(kt * kt).add<double>(kt).add<double>(kt * kt);
+  const size_t inner = orth_workspace(kt) > syev_workspace(kt) ? orth_workspace(kt)
+                                                                  : syev_workspace(kt);
+  return w.bytes() + inner;
+}
+
+otm_status pairs_apply_ws(const otm_csr* G1, const otm_csr* G2, const float* S, int64_t m,
+                          float* O, float* tmp, cudaStream_t st) {
+  const int64_t nx = G1->rows;
+  OTM_TRY(spmm_gather(G2, S, m, nullptr, tmp, st));
+  OTM_CHECK_CUDA(cudaMemsetAsync(O, 0, sizeof(float) * G1->cols * m, st));
+  OTM_TRY(spmm_scatter(G1, tmp, m, nullptr, (float)(1.0 / (double)(nx > 0 ? nx : 1)), O, st));
+  return OTM_OK;
+}
+
+}  // namespace
+}  // namespace otm
+
+using namespace otm;
+
+extern "C" {
+
+size_t otm_topic_m2_workspace(int64_t n, int64_t m) {
+  WorkspaceSize w;
+  w.add<float>(n * m).add<double>(m);
+  return w.bytes();
+}
+
+otm_status otm_topic_m2_apply(const otm_csr* X, const float* row_w, const double* M1,
+                              const double* delta, double alpha0, const float* S, int64_t m,
+                              float* O, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  OTM_TRY(check_csr(X, "otm_topic_m2_apply"));
+  OTM_REQUIRE(m >= 1 && row_w && M1 && delta && S && O, "otm_topic_m2_apply: bad arguments");
+  OTM_REQUIRE(S != O, "otm_topic_m2_apply: O must not alias S");
+  Workspace w(ws, ws_bytes);
+  TopicOp op{X, row_w, M1, delta, alpha0, w.take<float>(X->rows * m), w.take<double>(m)};
+  OTM_REQUIRE(op.P && op.u, "otm_topic_m2_apply: workspace too small (need %zu bytes)",
+              otm_topic_m2_workspace(X->rows, m));
+  return op.apply(S, m, O, as_stream(stream));
+}
+
+size_t otm_pairs_workspace(int64_t n_x, int64_t m) {
+  WorkspaceSize w;
+  w.add<float>(n_x * m);
+  return w.bytes();
+}
+
+otm_status otm_pairs_apply(const otm_csr* G1, const otm_csr* G2, const float* S, int64_t m,
+                           float* O, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  OTM_TRY(check_csr(G1, "otm_pairs_apply G1"));
+  OTM_TRY(check_csr(G2, "otm_pairs_apply G2"));
+  OTM_REQUIRE(G1->rows == G2->rows, "otm_pairs_apply: G1 and G2 need the same rows (n_X)");
+  OTM_REQUIRE(m >= 1 && S && O, "otm_pairs_apply: bad arguments");
+  Workspace w(ws, ws_bytes);
+  float* tmp = w.take<float>(G2->rows * m);
+  OTM_REQUIRE(tmp, "otm_pairs_apply: workspace too small");
+  return pairs_apply_ws(G1, G2, S, m, O, tmp, as_stream(stream));
+}
+
+size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t k, int64_t kt) {
+  (void)k;
+  WorkspaceSize w;
+  w.add<double>(d).add<float>(n * kt).add<double>(kt).add<int>(1);
+  return w.bytes() + range_finder_ws(d, kt);
+}
+
+otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t kt,
+                            int power_iters, double alpha0, float* W, float* Q, double* Cw,
+                            double* Cp, double* eig, double* M1, float* row_invlen,
+                            float* row_w, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  OTM_TRY(check_csr(X, "otm_whiten_topic"));
+  OTM_REQUIRE(k >= 1 && kt > k && kt <= 160 && kt <= X->cols,
+              "otm_whiten_topic: need 1 <= k < kt <= min(160, d) (k=%lld kt=%lld d=%lld)",
+              (long long)k, (long long)kt, (long long)X->cols);
+  OTM_REQUIRE(X->rows >= 1, "otm_whiten_topic: empty corpus");
+  OTM_REQUIRE(power_iters >= 0 && power_iters <= 16, "otm_whiten_topic: power_iters in [0,16]");
+  OTM_REQUIRE(alpha0 >= 0.0, "otm_whiten_topic: alpha0 must be >= 0");
+  OTM_REQUIRE(S && W && Q && Cw && Cp && eig && M1 && row_invlen && row_w,
+              "otm_whiten_topic: null output");
+  OTM_REQUIRE(ws_bytes >= otm_whiten_topic_workspace(X->rows, X->cols, k, kt),
+              "otm_whiten_topic: workspace too small (need %zu bytes)",
+              otm_whiten_topic_workspace(X->rows, X->cols, k, kt));
+  cudaStream_t st = as_stream(stream);
+  Workspace w(ws, ws_bytes);
+  double* delta = w.take<double>(X->cols);
+  float* P = w.take<float>(X->rows * kt);
+  double* u = w.take<double>(kt);
+  int* flag = w.take<int>(1);
+  OTM_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  OTM_TRY(topic_moments(X, row_invlen, row_w, M1, delta, st));
+  TopicOp op{X, row_w, M1, delta, alpha0, P, u};
+  OTM_TRY(range_finder(op, X->cols, S, k, kt, power_iters, W, Q, Cw, Cp, eig, w, st, flag));
+  int h = 0;
+  OTM_TRY(read_flag(flag, st, &h));
+  if (h) return set_error(OTM_ENOTPSD, "otm_whiten_topic: fewer than k positive eigenvalues");
+  return OTM_OK;
+}
+
+size_t otm_whiten_community_workspace(int64_t n_x, int64_t n_a, int64_t n_b, int64_t n_c,
+                                      int64_t k, int64_t kt) {
+  WorkspaceSize w;
+  w.add<float>(n_c * kt).add<float>(n_b * kt).add<float>(n_x * (kt > 2 * k ? kt : 2 * k));
+  w.add<double>(kt * kt).add<double>(kt).add<double>(kt * kt);  // BB, ev, evec
+  w.add<double>(kt * k).add<double>(kt * k).add<double>(kt * k).add<double>(k);  // Ub, Cv, Cu, s2
+  w.add<float>(n_c * k).add<float>(n_b * k);                      // U_C, V_B
+  w.add<float>(n_x * k).add<float>(n_x * k).add<float>(n_a * 2 * k);  // CU, BV, L
+  w.add<double>(k * k);                                           // K
+  w.add<double>(2 * k * kt).add<double>(2 * k * kt).add<double>(kt);  // ab, coef, u
+  w.add<double>(2 * k * k).add<int>(2);                            // LW, flags
+  const size_t a = w.bytes();
+  const size_t inner = orth_workspace(kt) > syev_workspace(kt) ? orth_workspace(kt)
+                                                                  : syev_workspace(kt);
+  const size_t b = range_finder_ws(n_a, kt);
+  return a + (b > inner ? b : inner);
+}
+
+otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const otm_csr* G_XC,
+                                const float* S_pairs, const float* S_w, int64_t k, int64_t kt,
+                                int power_iters, double alpha0, float* W, float* W_B,
+                                float* W_C, float* Q, double* Cw, double* Cp, double* eig,
+                                double* sigma, double* M1, void* ws, size_t ws_bytes,
+                                void* stream) {
+  clear_error();
+  OTM_TRY(check_csr(G_XA, "otm_whiten_community G_XA"));
+  OTM_TRY(check_csr(G_XB, "otm_whiten_community G_XB"));
+  OTM_TRY(check_csr(G_XC, "otm_whiten_community G_XC"));
+  const int64_t nx = G_XA->rows, na = G_XA->cols, nb = G_XB->cols, nc = G_XC->cols;
+  OTM_REQUIRE(G_XB->rows == nx && G_XC->rows == nx && nx >= 1,
+              "otm_whiten_community: blocks must share the same (non-empty) X rows");
+  OTM_REQUIRE(k >= 1 && kt > k && kt <= 160 && kt <= na && kt <= nb && kt <= nc && 2 * k <= 256,
+              "otm_whiten_community: need 1 <= k < kt <= min(160, n_A, n_B, n_C)");
+  OTM_REQUIRE(power_iters >= 0 && power_iters <= 16,
+              "otm_whiten_community: power_iters in [0,16]");
+  OTM_REQUIRE(alpha0 >= 0.0, "otm_whiten_community: alpha0 must be >= 0");
+  OTM_REQUIRE(S_pairs && S_w && W && W_B && W_C && Q && Cw && Cp && eig && sigma && M1,
+              "otm_whiten_community: null argument");
+  const size_t need = otm_whiten_community_workspace(nx, na, nb, nc, k, kt);
+  OTM_REQUIRE(ws_bytes >= need, "otm_whiten_community: workspace too small (need %zu bytes)",
+              need);
+  cudaStream_t st = as_stream(stream);
+  Workspace w(ws, ws_bytes);
+  float* Yc = w.take<float>(nc * kt);
+  float* Zb = w.take<float>(nb * kt);
+  float* tmp = w.take<float>(nx * (kt > 2 * k ? kt : 2 * k));
+  double* BB = w.take<double>(kt * kt);
+  double* ev = w.take<double>(kt);
+  double* evec = w.take<double>(kt * kt);
+  double* Ub = w.take<double>(kt * k);
+  double* Cv = w.take<double>(kt * k);
+  double* Cu = w.take<double>(kt * k);
+  double* s2 = w.take<double>(k);
+  float* U_C = w.take<float>(nc * k);
+  float* V_B = w.take<float>(nb * k);
+  float* CU = w.take<float>(nx * k);
+  float* BV = w.take<float>(nx * k);
+  float* L = w.take<float>(na * 2 * k);
+  double* K = w.take<double>(k * k);
+  double* ab = w.take<double>(2 * k * kt);
+  double* coef = w.take<double>(2 * k * kt);
+  double* u = w.take<double>(kt);
+  double* LW = w.take<double>(2 * k * k);
+  int* flags = w.take<int>(2);
+  OTM_CHECK_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), st));
+  const size_t mark = w.used;
+
+  // 1. rank-k randomised SVD of Pairs(C,B) ~ U_C diag(sigma) V_B^T
+  OTM_TRY(pairs_apply_ws(G_XC, G_XB, S_pairs, kt, Yc, tmp, st));
+  OTM_TRY(orthonormalize(Yc, nc, kt, w, st));
+  w.used = mark;
+  for (int it = 0; it < power_iters; ++it) {
+    OTM_TRY(pairs_apply_ws(G_XB, G_XC, Yc, kt, Zb, tmp, st));
+    OTM_TRY(orthonormalize(Zb, nb, kt, w, st));
+    w.used = mark;
+    OTM_TRY(pairs_apply_ws(G_XC, G_XB, Zb, kt, Yc, tmp, st));
+    OTM_TRY(orthonormalize(Yc, nc, kt, w, st));
+    w.used = mark;
+  }
+  OTM_TRY(pairs_apply_ws(G_XB, G_XC, Yc, kt, Zb, tmp, st));  // B^T = Pairs(B,C) Q
+  OTM_TRY(gemm_tn_f64acc(Zb, Zb, nb, kt, kt, 1.0, BB, 0, st));
+  OTM_TRY(syev(BB, kt, ev, evec, w, st));
+  w.used = mark;
+  take_cols_kernel<<<blocks_for(kt * k), 256, 0, st>>>(evec, kt, k, Ub);
+  OTM_CHECK_LAUNCH();
+  OTM_TRY(whitening_factors(ev, evec, kt, k, Cv, Cu, s2, flags + 1, st));  // Cv = Ub / sigma
+  sqrt_vec_kernel<<<blocks_for(k), 256, 0, st>>>(s2, sigma, k);
+  OTM_CHECK_LAUNCH();
+  OTM_TRY(gemm_nn_small(Yc, nc, kt, Ub, k, U_C, nullptr, nullptr, 0.0, st));
+  OTM_TRY(gemm_nn_small(Zb, nb, kt, Cv, k, V_B, nullptr, nullptr, 0.0, st));
+
+  // 2. factors of Z_B, Z_C and the middle matrix K
+  OTM_TRY(spmm_gather(G_XC, U_C, k, nullptr, CU, st));
+  OTM_TRY(spmm_gather(G_XB, V_B, k, nullptr, BV, st));
+  concat2_kernel<<<blocks_for(nx * 2 * k), 256, 0, st>>>(BV, CU, nx, k, tmp);
+  OTM_CHECK_LAUNCH();
+  OTM_CHECK_CUDA(cudaMemsetAsync(L, 0, sizeof(float) * na * 2 * k, st));
+  OTM_TRY(spmm_scatter(G_XA, tmp, 2 * k, nullptr, (float)(1.0 / (double)nx), L, st));
+  scale_cols_mod_kernel<<<blocks_for(na * 2 * k), 256, 0, st>>>(L, na, k, s2);
+  OTM_CHECK_LAUNCH();
+  OTM_TRY(gemm_tn_f64acc(CU, BV, nx, k, k, 1.0 / (double)nx, K, 0, st));
+  OTM_TRY(column_sums_scaled(G_XA, 1.0 / (double)nx, M1, st));
+
+  // 3. range-finder whitening of sym(M2)
+  CommunityOp op{L, K, M1, na, k, alpha0, ab, coef, u};
+  OTM_TRY(range_finder(op, na, S_w, k, kt, power_iters, W, Q, Cw, Cp, eig, w, st, flags));
+
+  // 4. other views: W_B = Z_B^T W = V_B (L_B^T W), W_C = Z_C^T W = U_C (L_C^T W)
+  OTM_TRY(gemm_tn_f64acc(L, W, na, 2 * k, k, 1.0, LW, 0, st));
+  OTM_TRY(gemm_nn_small(V_B, nb, k, LW + k * k, k, W_B, nullptr, nullptr, 0.0, st));
+  OTM_TRY(gemm_nn_small(U_C, nc, k, LW, k, W_C, nullptr, nullptr, 0.0, st));
+
+  int h[2] = {0, 0};
+  OTM_CHECK_CUDA(cudaMemcpyAsync(h, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (h[1]) return set_error(OTM_ENOTPSD, "otm_whiten_community: Pairs(C,B) has rank < k");
+  if (h[0]) return set_error(OTM_ENOTPSD, "otm_whiten_community: fewer than k positive eigenvalues");
+  return OTM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,332 @@
+"""Python binding of the C ABI in ``include/otm.h`` (argument marshalling only).
+
+Every function takes and returns PyTorch CUDA tensors and forwards to the
+entry point of the same name in ``_build/libotm.so`` on the current CUDA
+stream.  All arithmetic runs in the library's CUDA kernels; there is no
+fallback: if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libotm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libotm.so not built ({LIB_PATH}); run python -m paper_1309_0787_gb300.build")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+c_i64 = ctypes.c_int64
+c_f64 = ctypes.c_double
+c_vp = ctypes.c_void_p
+c_sz = ctypes.c_size_t
+
+
+class OtmCsr(ctypes.Structure):
+    _fields_ = [("rows", c_i64), ("cols", c_i64), ("nnz", c_i64), ("row_ptr", c_vp),
+                ("col", c_vp), ("val", c_vp)]
+
+
+_P = ctypes.POINTER(OtmCsr)
+
+# entry point -> argument types (every entry returns int status unless listed below)
+_SIGS = {
+    "otm_version": [],
+    "otm_last_error": [],
+    "otm_launch_count": [],
+    "otm_topic_moments": [_P, c_vp, c_vp, c_vp, c_vp, c_vp],
+    "otm_topic_m2_workspace": [c_i64, c_i64],
+    "otm_topic_m2_apply": [_P, c_vp, c_vp, c_vp, c_f64, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_pairs_workspace": [c_i64, c_i64],
+    "otm_pairs_apply": [_P, _P, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_orth_workspace": [c_i64],
+    "otm_orthonormalize": [c_vp, c_i64, c_i64, c_vp, c_sz, c_vp],
+    "otm_syev_workspace": [c_i64],
+    "otm_syev": [c_vp, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp],
+    "otm_whiten_topic_workspace": [c_i64, c_i64, c_i64, c_i64],
+    "otm_whiten_topic": [_P, c_vp, c_i64, c_i64, ctypes.c_int, c_f64, c_vp, c_vp, c_vp, c_vp,
+                         c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
+    "otm_whiten_community_workspace": [c_i64, c_i64, c_i64, c_i64, c_i64, c_i64],
+    "otm_whiten_community": [_P, _P, _P, c_vp, c_vp, c_i64, c_i64, ctypes.c_int, c_f64, c_vp,
+                             c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
+    "otm_project": [_P, c_vp, c_i64, c_vp, c_vp, c_vp],
+    "otm_column_mean": [c_vp, c_i64, c_i64, c_vp, c_vp],
+    "otm_sgd_step": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_f64, c_f64, c_f64, c_vp],
+    "otm_sgd_run": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64, c_i64, c_f64,
+                    c_f64, c_f64, c_i64, c_vp, c_vp],
+    "otm_unwhiten_workspace": [c_i64, c_i64, c_i64],
+    "otm_unwhiten": [c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_f64, ctypes.c_int, c_vp, c_vp,
+                     c_vp, c_vp, c_sz, c_vp],
+    "otm_recon_error_workspace": [c_i64],
+    "otm_recon_error": [c_vp, c_i64, c_f64, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
+}
+_RESTYPE = {"otm_last_error": ctypes.c_char_p, "otm_version": ctypes.c_int,
+            "otm_launch_count": ctypes.c_uint64}
+
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _RESTYPE.get(_name, c_sz if _name.endswith("_workspace") else ctypes.c_int)
+
+STATUS = {0: "OTM_OK", 1: "OTM_EINVAL", 2: "OTM_ENOTPSD", 3: "OTM_ENOMEM", 4: "OTM_ECUDA",
+          5: "OTM_ETIMEOUT", 6: "OTM_ENOTCONVERGED"}
+
+
+class OtmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(st: int) -> None:
+    if st != 0:
+        raise OtmError(st, _lib.otm_last_error().decode())
+
+
+def version() -> int:
+    return _lib.otm_version()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(_lib.otm_launch_count())
+
+
+def _stream():
+    return c_vp(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return c_vp(t.data_ptr())
+
+
+def _need(t, dtype, shape, name):
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _ws(nbytes: int, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+class DeviceCSR:
+    """CSR matrix resident on the GPU (int32 row_ptr/col, float32 values)."""
+
+    def __init__(self, row_ptr, col, val, shape):
+        self.row_ptr, self.col, self.val = row_ptr, col, val
+        self.shape = (int(shape[0]), int(shape[1]))
+        self._desc = OtmCsr(self.shape[0], self.shape[1], int(col.numel()),
+                            row_ptr.data_ptr(), col.data_ptr() if col.numel() else 0,
+                            val.data_ptr() if val.numel() else 0)
+
+    @classmethod
+    def from_host(cls, csr, device="cuda"):
+        rp = torch.as_tensor(csr.row_ptr, dtype=torch.int32).to(device)
+        col = torch.as_tensor(csr.col, dtype=torch.int32).to(device)
+        val = torch.as_tensor(csr.val, dtype=torch.float32).to(device)
+        return cls(rp, col, val, csr.shape)
+
+    @property
+    def nnz(self):
+        return int(self.col.numel())
+
+    @property
+    def device(self):
+        return self.row_ptr.device
+
+    def ref(self):
+        return ctypes.byref(self._desc)
+
+
+# --------------------------------------------------------------------------
+def topic_moments(X: DeviceCSR) -> dict:
+    n, d = X.shape
+    dev = X.device
+    out = {"row_invlen": torch.empty(n, dtype=torch.float32, device=dev),
+           "row_w": torch.empty(n, dtype=torch.float32, device=dev),
+           "M1": torch.empty(d, dtype=torch.float64, device=dev),
+           "delta": torch.empty(d, dtype=torch.float64, device=dev)}
+    _check(_lib.otm_topic_moments(X.ref(), _ptr(out["row_invlen"]), _ptr(out["row_w"]),
+                                  _ptr(out["M1"]), _ptr(out["delta"]), _stream()))
+    return out
+
+
+def topic_m2_apply(X: DeviceCSR, moments: dict, alpha0: float, S):
+    n, d = X.shape
+    m = S.shape[1]
+    _need(S, torch.float32, (d, m), "S")
+    O = torch.empty_like(S)
+    ws = _ws(_lib.otm_topic_m2_workspace(n, m), S.device)
+    _check(_lib.otm_topic_m2_apply(X.ref(), _ptr(moments["row_w"]), _ptr(moments["M1"]),
+                                   _ptr(moments["delta"]), float(alpha0), _ptr(S), m, _ptr(O),
+                                   _ptr(ws), ws.numel(), _stream()))
+    return O
+
+
+def pairs_apply(G1: DeviceCSR, G2: DeviceCSR, S):
+    m = S.shape[1]
+    _need(S, torch.float32, (G2.shape[1], m), "S")
+    O = torch.empty(G1.shape[1], m, dtype=torch.float32, device=S.device)
+    ws = _ws(_lib.otm_pairs_workspace(G1.shape[0], m), S.device)
+    _check(_lib.otm_pairs_apply(G1.ref(), G2.ref(), _ptr(S), m, _ptr(O), _ptr(ws), ws.numel(),
+                                _stream()))
+    return O
+
+
+def orthonormalize(A):
+    rows, m = A.shape
+    _need(A, torch.float32, (rows, m), "A")
+    ws = _ws(_lib.otm_orth_workspace(m), A.device)
+    _check(_lib.otm_orthonormalize(_ptr(A), rows, m, _ptr(ws), ws.numel(), _stream()))
+    return A
+
+
+def syev(A):
+    n = A.shape[0]
+    _need(A, torch.float64, (n, n), "A")
+    ev = torch.empty(n, dtype=torch.float64, device=A.device)
+    vec = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    ws = _ws(_lib.otm_syev_workspace(n), A.device)
+    _check(_lib.otm_syev(_ptr(A), n, _ptr(ev), _ptr(vec), _ptr(ws), ws.numel(), _stream()))
+    return ev, vec
+
+
+def whiten_topic(X: DeviceCSR, S, k: int, power_iters: int, alpha0: float) -> dict:
+    n, d = X.shape
+    kt = S.shape[1]
+    _need(S, torch.float32, (d, kt), "S")
+    dev = S.device
+    f32, f64 = torch.float32, torch.float64
+    o = {"W": torch.empty(d, k, dtype=f32, device=dev), "Q": torch.empty(d, kt, dtype=f32, device=dev),
+         "Cw": torch.empty(kt, k, dtype=f64, device=dev), "Cp": torch.empty(kt, k, dtype=f64, device=dev),
+         "eig": torch.empty(k, dtype=f64, device=dev), "M1": torch.empty(d, dtype=f64, device=dev),
+         "row_invlen": torch.empty(n, dtype=f32, device=dev),
+         "row_w": torch.empty(n, dtype=f32, device=dev)}
+    ws = _ws(_lib.otm_whiten_topic_workspace(n, d, k, kt), dev)
+    _check(_lib.otm_whiten_topic(X.ref(), _ptr(S), k, kt, int(power_iters), float(alpha0),
+                                 _ptr(o["W"]), _ptr(o["Q"]), _ptr(o["Cw"]), _ptr(o["Cp"]),
+                                 _ptr(o["eig"]), _ptr(o["M1"]), _ptr(o["row_invlen"]),
+                                 _ptr(o["row_w"]), _ptr(ws), ws.numel(), _stream()))
+    return o
+
+
+def whiten_community(G_XA: DeviceCSR, G_XB: DeviceCSR, G_XC: DeviceCSR, S_pairs, S_w, k: int,
+                     power_iters: int, alpha0: float) -> dict:
+    nx, na = G_XA.shape
+    nb, nc = G_XB.shape[1], G_XC.shape[1]
+    kt = S_w.shape[1]
+    _need(S_w, torch.float32, (na, kt), "S_w")
+    _need(S_pairs, torch.float32, (nb, kt), "S_pairs")
+    dev = S_w.device
+    f32, f64 = torch.float32, torch.float64
+    o = {"W": torch.empty(na, k, dtype=f32, device=dev), "W_B": torch.empty(nb, k, dtype=f32, device=dev),
+         "W_C": torch.empty(nc, k, dtype=f32, device=dev), "Q": torch.empty(na, kt, dtype=f32, device=dev),
+         "Cw": torch.empty(kt, k, dtype=f64, device=dev), "Cp": torch.empty(kt, k, dtype=f64, device=dev),
+         "eig": torch.empty(k, dtype=f64, device=dev), "sigma": torch.empty(k, dtype=f64, device=dev),
+         "M1": torch.empty(na, dtype=f64, device=dev)}
+    ws = _ws(_lib.otm_whiten_community_workspace(nx, na, nb, nc, k, kt), dev)
+    _check(_lib.otm_whiten_community(G_XA.ref(), G_XB.ref(), G_XC.ref(), _ptr(S_pairs), _ptr(S_w),
+                                     k, kt, int(power_iters), float(alpha0), _ptr(o["W"]),
+                                     _ptr(o["W_B"]), _ptr(o["W_C"]), _ptr(o["Q"]), _ptr(o["Cw"]),
+                                     _ptr(o["Cp"]), _ptr(o["eig"]), _ptr(o["sigma"]),
+                                     _ptr(o["M1"]), _ptr(ws), ws.numel(), _stream()))
+    return o
+
+
+def project(X: DeviceCSR, W, row_scale=None):
+    n, d = X.shape
+    k = W.shape[1]
+    _need(W, torch.float32, (d, k), "W")
+    if row_scale is not None:
+        _need(row_scale, torch.float32, (n,), "row_scale")
+    Y = torch.empty(n, k, dtype=torch.float32, device=W.device)
+    _check(_lib.otm_project(X.ref(), _ptr(W), k, _ptr(row_scale), _ptr(Y), _stream()))
+    return Y
+
+
+def column_mean(Y):
+    n, k = Y.shape
+    _need(Y, torch.float32, (n, k), "Y")
+    yb = torch.empty(k, dtype=torch.float64, device=Y.device)
+    _check(_lib.otm_column_mean(_ptr(Y), n, k, _ptr(yb), _stream()))
+    return yb
+
+
+def sgd_step(V, YA, YB, YC, ybar3, theta: float, beta: float, alpha0: float):
+    k = V.shape[0]
+    b = YA.shape[0]
+    _need(V, torch.float32, (k, k), "V")
+    for nm, Y in (("YA", YA), ("YB", YB), ("YC", YC)):
+        _need(Y, torch.float32, (b, k), nm)
+    _need(ybar3, torch.float64, (3, k), "ybar3")
+    _check(_lib.otm_sgd_step(_ptr(V), _ptr(YA), _ptr(YB), _ptr(YC), b, k, _ptr(ybar3),
+                             float(theta), float(beta), float(alpha0), _stream()))
+    return V
+
+
+def sgd_run(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, theta: float,
+            alpha0: float, snapshot_every: int = 0):
+    """V is k x k column-major as stored (V[i] = component i); updated in place.
+    Returns the snapshot tensor (steps // snapshot_every, k, k) or None."""
+    k = V.shape[0]
+    n = YA.shape[0]
+    _need(V, torch.float32, (k, k), "V")
+    for nm, Y in (("YA", YA), ("YB", YB), ("YC", YC)):
+        _need(Y, torch.float32, (n, k), nm)
+    _need(ybar3, torch.float64, (3, k), "ybar3")
+    if perm is not None:
+        _need(perm, torch.int32, (epochs, n), "perm")
+    steps = ((n + b - 1) // b) * epochs
+    snaps = None
+    if snapshot_every:
+        snaps = torch.empty(max(steps // snapshot_every, 1), k, k, dtype=torch.float32,
+                            device=V.device)
+    _check(_lib.otm_sgd_run(_ptr(V), _ptr(YA), _ptr(YB), _ptr(YC), n, k, _ptr(ybar3),
+                            _ptr(perm), int(epochs), int(b), float(beta0), float(theta),
+                            float(alpha0), int(snapshot_every), _ptr(snaps), _stream()))
+    return snaps
+
+
+def unwhiten(V, Q, Cp, theta: float, normalize: bool) -> dict:
+    k = V.shape[0]
+    d, kt = Q.shape
+    _need(V, torch.float32, (k, k), "V")
+    _need(Q, torch.float32, (d, kt), "Q")
+    _need(Cp, torch.float64, (kt, k), "Cp")
+    dev = V.device
+    o = {"comps": torch.empty(d, k, dtype=torch.float64, device=dev),
+         "lambda": torch.empty(k, dtype=torch.float64, device=dev),
+         "alpha_hat": torch.empty(k, dtype=torch.float64, device=dev)}
+    ws = _ws(_lib.otm_unwhiten_workspace(d, k, kt), dev)
+    _check(_lib.otm_unwhiten(_ptr(V), k, _ptr(Q), d, kt, _ptr(Cp), float(theta), int(bool(normalize)),
+                             _ptr(o["comps"]), _ptr(o["lambda"]), _ptr(o["alpha_hat"]), _ptr(ws),
+                             ws.numel(), _stream()))
+    return o
+
+
+def recon_error(V, U_true, lam_true, theta: float):
+    """U_true: k x k with U_true[j] = unit component j (column-major storage)."""
+    k = V.shape[0]
+    _need(V, torch.float32, (k, k), "V")
+    _need(U_true, torch.float64, (k, k), "U_true")
+    _need(lam_true, torch.float64, (k,), "lam_true")
+    err = torch.empty(1, dtype=torch.float64, device=V.device)
+    ws = _ws(_lib.otm_recon_error_workspace(k), V.device)
+    _check(_lib.otm_recon_error(_ptr(V), k, float(theta), _ptr(U_true), _ptr(lam_true), _ptr(err),
+                                _ptr(ws), ws.numel(), _stream()))
+    return err
+
+
+ENTRY_POINTS = tuple(_SIGS)

@@ -1,0 +1,27 @@
+"""Helpers shared by the GPU parity tests (no arithmetic of the method)."""
+import numpy as np
+
+
+def rel(a, b):
+    """Normwise relative difference ||a - b|| / ||b||."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def align_signs(A, B):
+    """Flip the columns of A to best match B (eigenvector sign ambiguity)."""
+    s = np.sign(np.sum(np.asarray(A) * np.asarray(B), axis=0))
+    s[s == 0] = 1.0
+    return np.asarray(A) * s
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def grad_rel_err(G, G64, V, theta, kappa_gram_data):
+    """Survey tolerance metric: ||G - G64||_F / (||kappa G_gram||_F + ||G_data||_F)."""
+    gram, data = kappa_gram_data
+    return float(np.linalg.norm(G - G64) / (np.linalg.norm(gram) + np.linalg.norm(data)))
