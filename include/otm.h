@@ -114,9 +114,12 @@ otm_status otm_pairs_apply(const otm_csr* G1, const otm_csr* G2, const float* S,
 /*
  * otm_orthonormalize -- in-place tall-thin QR (Section 4.2 "Tall-thin QR"):
  * A (rows x m, float32, row-major, rows >= m, m <= 160) is replaced by an
- * orthonormal basis Q of its column space.  Shifted Cholesky-QR, three passes
- * (Gram matrices accumulated in FP64).  Scratch: otm_orth_workspace(m).
- * OTM_ENOTCONVERGED if a Cholesky pivot fails even after the shift.
+ * orthonormal basis Q of a space containing its column space (exactly its
+ * column space when A has full rank).  Cholesky-QR, two shifted passes then
+ * two plain ones (Gram matrices accumulated in FP64); numerically
+ * rank-deficient directions are completed with orthonormalised rounding
+ * noise.  Scratch: otm_orth_workspace(m).  OTM_ENOTCONVERGED if the Gram
+ * matrix is not finite.  Synchronises the stream.
  */
 size_t otm_orth_workspace(int64_t m);
 otm_status otm_orthonormalize(float* A, int64_t rows, int64_t m, void* ws, size_t ws_bytes,
@@ -147,8 +150,9 @@ otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, vo
  * Outputs: W (d x k, float32) with W^T M2 W = I; Q (d x kt, float32); Cw, Cp
  * (kt x k, FP64) with W = Q Cw and (W^T)^+ = Q Cp; eig[k] (descending); M1[d];
  * row_invlen[n], row_w[n] (as otm_topic_moments).  Returns OTM_ENOTPSD if the
- * k-th eigenvalue is not positive.  Synchronises the stream (the eigenvalue
- * check).  Scratch: otm_whiten_topic_workspace(n, d, k, kt).
+ * k-th eigenvalue is not above 1e-5 times the largest (not positive, or not
+ * resolvable at the float32 accuracy of the range finder).  Synchronises the
+ * stream (the eigenvalue check).  Scratch: otm_whiten_topic_workspace(n, d, k, kt).
  */
 size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t k, int64_t kt);
 otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t kt,
@@ -164,7 +168,8 @@ otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t
  * finder of M2.  Steps: Pairs(C,B) ~ U_C diag(sigma) V_B^T; Z_B = L_B V_B^T,
  * Z_C = L_C U_C^T (Eqs. (7)-(8) at rank k); the symmetric part of
  * (alpha0+1) Z_C Pairs(C,B) Z_B^T - alpha0 M1 M1^T applied in factored form;
- * range finder + QR + FP64 eig as in otm_whiten_topic.
+ * range finder + QR + FP64 eig as in otm_whiten_topic.  OTM_ENOTPSD also when
+ * sigma_k^2 <= 1e-5 sigma_1^2 (Pairs(C,B) numerically of rank < k).
  * Outputs: W (n_A x k), W_B = Z_B^T W (n_B x k), W_C = Z_C^T W (n_C x k)
  * (float32), Q (n_A x kt), Cw, Cp (kt x k FP64), eig[k], sigma[k] (singular
  * values of Pairs(C,B)), M1[n_A] (FP64).  OTM_ENOTPSD as above.  Synchronises

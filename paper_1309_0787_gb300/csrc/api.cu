@@ -78,28 +78,44 @@ otm_status otm_column_mean(const float* Y, int64_t n, int64_t k, double* ybar, v
   return OTM_OK;
 }
 
-size_t otm_orth_workspace(int64_t m) { return orth_workspace(m); }
+size_t otm_orth_workspace(int64_t m) { return orth_workspace(m) + 256; }
 
 otm_status otm_orthonormalize(float* A, int64_t rows, int64_t m, void* ws, size_t ws_bytes,
                               void* stream) {
   clear_error();
   OTM_REQUIRE(A && m >= 1 && m <= 160 && rows >= m,
               "otm_orthonormalize: need A != NULL, 1 <= m <= 160, rows >= m");
-  OTM_REQUIRE(ws_bytes >= orth_workspace(m), "otm_orthonormalize: workspace too small");
+  OTM_REQUIRE(ws_bytes >= otm_orth_workspace(m), "otm_orthonormalize: workspace too small");
+  cudaStream_t st = as_stream(stream);
   Workspace w(ws, ws_bytes);
-  return orthonormalize(A, rows, m, w, as_stream(stream));
+  int* flag = w.take<int>(1);
+  OTM_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  OTM_TRY(orthonormalize(A, rows, m, w, st, flag));
+  int h = 0;
+  OTM_CHECK_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (h) return set_error(OTM_ENOTCONVERGED, "otm_orthonormalize: non-finite Gram matrix");
+  return OTM_OK;
 }
 
-size_t otm_syev_workspace(int64_t n) { return syev_workspace(n); }
+size_t otm_syev_workspace(int64_t n) { return syev_workspace(n) + 256; }
 
 otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, void* ws,
                     size_t ws_bytes, void* stream) {
   clear_error();
   OTM_REQUIRE(A && evals && evecs && n >= 1 && n <= 160,
               "otm_syev: need non-null arguments and 1 <= n <= 160");
-  OTM_REQUIRE(ws_bytes >= syev_workspace(n), "otm_syev: workspace too small");
+  OTM_REQUIRE(ws_bytes >= otm_syev_workspace(n), "otm_syev: workspace too small");
+  cudaStream_t st = as_stream(stream);
   Workspace w(ws, ws_bytes);
-  return syev(A, n, evals, evecs, w, as_stream(stream));
+  int* flag = w.take<int>(1);
+  OTM_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  OTM_TRY(syev(A, n, evals, evecs, w, st, flag));
+  int h = 0;
+  OTM_CHECK_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (h) return set_error(OTM_ENOTCONVERGED, "otm_syev: Jacobi sweep limit reached");
+  return OTM_OK;
 }
 
 }  // extern "C"

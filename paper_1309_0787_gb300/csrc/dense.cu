@@ -98,16 +98,15 @@ __global__ void __launch_bounds__(256) gemm_nn_small_kernel(
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int j = 0; j < NN_PMAX / 32; ++j) acc[a][j] = 0.f;
+  const int pp = 32 * ncj;  // columns staged (p rounded up to the column groups)
   for (int64_t k0 = 0; k0 < m; k0 += NN_K) {
-    for (int idx = threadIdx.x; idx < NN_R * NN_K; idx += 256) {
-      const int rr = idx / NN_K, kk = idx % NN_K;
-      const int64_t r = r0 + rr, k = k0 + kk;
-      As[rr][kk] = (r < rows && k < m) ? A[r * m + k] : 0.f;
+    for (int rr = rg; rr < NN_R; rr += 8) {
+      const int64_t r = r0 + rr, k = k0 + cg;
+      As[rr][cg] = (r < rows && k < m) ? A[r * m + k] : 0.f;
     }
-    for (int idx = threadIdx.x; idx < NN_K * NN_PMAX; idx += 256) {
-      const int kk = idx / NN_PMAX, c = idx % NN_PMAX;
+    for (int kk = rg; kk < NN_K; kk += 8) {
       const int64_t k = k0 + kk;
-      Cs[kk][c] = (k < m && c < p) ? (float)C[k * p + c] : 0.f;
+      for (int c = cg; c < pp; c += 32) Cs[kk][c] = (k < m && c < p) ? (float)C[k * p + c] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -176,36 +175,38 @@ __global__ void __launch_bounds__(256) gemm_nn_f64_kernel(const float* __restric
   }
 }
 
-// Small FP64 GEMM, C = alpha op(A) op(B) + beta C, 16 x 16 tiles, one output
-// per thread.  A is m x kk (or kk x m when ta), B is kk x n (or n x kk when tb).
-__global__ void __launch_bounds__(256) dgemm_small_kernel(int ta, int tb, int64_t m, int64_t n,
-                                                          int64_t kk, double alpha,
-                                                          const double* __restrict__ A,
-                                                          int64_t lda,
-                                                          const double* __restrict__ B,
-                                                          int64_t ldb, double beta, double* C,
-                                                          int64_t ldc) {
-  __shared__ double As[16][17];
-  __shared__ double Bs[16][17];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t i = (int64_t)blockIdx.y * 16 + ty, j = (int64_t)blockIdx.x * 16 + tx;
+// Small FP64 GEMM, C = alpha op(A) op(B) + beta C, 8 x 8 tiles, one output
+// per thread (many small blocks: the FP64 rate per SM is low, so the work is
+// spread over as many SMs as possible).  A is m x kk (or kk x m when ta), B is
+// kk x n (or n x kk when tb).
+__global__ void __launch_bounds__(64) dgemm_small_kernel(int ta, int tb, int64_t m, int64_t n,
+                                                         int64_t kk, double alpha,
+                                                         const double* __restrict__ A,
+                                                         int64_t lda,
+                                                         const double* __restrict__ B,
+                                                         int64_t ldb, double beta, double* C,
+                                                         int64_t ldc) {
+  __shared__ double As[8][9];
+  __shared__ double Bs[8][9];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int64_t i = (int64_t)blockIdx.y * 8 + ty, j = (int64_t)blockIdx.x * 8 + tx;
   double acc = 0.0;
-  for (int64_t k0 = 0; k0 < kk; k0 += 16) {
+  for (int64_t k0 = 0; k0 < kk; k0 += 8) {
     {
-      const int64_t ii = (int64_t)blockIdx.y * 16 + ty, k = k0 + tx;
+      const int64_t k = k0 + tx;
       double v = 0.0;
-      if (ii < m && k < kk) v = ta ? A[k * lda + ii] : A[ii * lda + k];
+      if (i < m && k < kk) v = ta ? A[k * lda + i] : A[i * lda + k];
       As[ty][tx] = v;
     }
     {
-      const int64_t k = k0 + ty, jj = (int64_t)blockIdx.x * 16 + tx;
+      const int64_t k = k0 + ty;
       double v = 0.0;
-      if (k < kk && jj < n) v = tb ? B[jj * ldb + k] : B[k * ldb + jj];
+      if (k < kk && j < n) v = tb ? B[j * ldb + k] : B[k * ldb + j];
       Bs[ty][tx] = v;
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc = fma(As[ty][q], Bs[q][tx], acc);
+    for (int q = 0; q < 8; ++q) acc = fma(As[ty][q], Bs[q][tx], acc);
     __syncthreads();
   }
   if (i < m && j < n) C[i * ldc + j] = alpha * acc + (beta != 0.0 ? beta * C[i * ldc + j] : 0.0);
@@ -231,69 +232,78 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 // (u = 2^-24), which keeps the factorisation positive definite for Gram
 // matrices of ill-conditioned A (shifted Cholesky-QR: Fukaya, Kannan,
 // Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 42, 2020).
+// Pivots below 10 u trace(G) (numerically rank-deficient A) are raised to
+// that floor: the matching columns of Q become normalised rounding noise,
+// which the following passes orthonormalise -- still a valid orthonormal
+// basis of a space containing range(A).  Only a non-finite pivot is an error.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G, int n,
                                                         double shift_scale,
                                                         double* __restrict__ Rinv,
                                                         int* __restrict__ flag) {
   extern __shared__ float sm[];
-  float* L = sm;              // n x n, lower triangle used
-  float* Li = sm + n * n;     // n x n, inverse of L (lower)
-  __shared__ float s_shift;
+  const int ldn = n | 1;       // odd row stride: column walks are bank-conflict free
+  float* L = sm;               // n x ldn, lower triangle used (diagonal kept in dg)
+  float* Li = sm + n * ldn;    // n x ldn, inverse of L (lower)
+  float* dg = Li + n * ldn;    // n, diagonal of L
+  __shared__ float s_shift, s_floor;
   __shared__ int s_bad;
-  const int tid = threadIdx.x, T = blockDim.x;
-  if (tid == 0) {
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = T >> 5;
+  if (warp == 0) {
     double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += G[i * n + i];
-    s_shift = (float)(shift_scale * (double)n * 5.9604644775390625e-8 * tr);
-    s_bad = 0;
+    for (int i = lane; i < n; i += 32) tr += G[(int64_t)i * n + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (lane == 0) {
+      s_shift = (float)(shift_scale * (double)n * 5.9604644775390625e-8 * tr);
+      s_floor = (float)(10.0 * 5.9604644775390625e-8 * tr) + 1e-30f;
+      s_bad = 0;
+    }
   }
   __syncthreads();
-  for (int idx = tid; idx < n * n; idx += T) {
-    const int i = idx / n, j = idx % n;
-    float v = (float)(0.5 * (G[i * n + j] + G[j * n + i]));
-    if (i == j) v += s_shift;
-    L[idx] = v;
-    Li[idx] = 0.f;
-  }
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) {
+      float v = (float)(0.5 * (G[(int64_t)i * n + j] + G[(int64_t)j * n + i]));
+      if (i == j) v += s_shift;
+      L[i * ldn + j] = v;
+      Li[i * ldn + j] = 0.f;
+    }
   __syncthreads();
-  // right-looking Cholesky, column by column
+  // right-looking Cholesky; every thread derives the pivot itself (no extra barrier)
   for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const float d = L[j * n + j];
-      if (!(d > 0.f)) {
-        s_bad = 1;
-        L[j * n + j] = 1.f;
-      } else {
-        L[j * n + j] = sqrtf(d);
-      }
+    float d = L[j * ldn + j];
+    if (!isfinite(d)) {
+      if (tid == 0) s_bad = 1;
+      d = 1.f;
     }
+    const float djj = sqrtf(fmaxf(d, s_floor));
+    if (tid == 0) dg[j] = djj;
+    for (int i = j + 1 + tid; i < n; i += T) L[i * ldn + j] /= djj;
     __syncthreads();
-    const float djj = L[j * n + j];
-    for (int i = j + 1 + tid; i < n; i += T) L[i * n + j] /= djj;
-    __syncthreads();
-    const int rem = n - j - 1;
-    for (int idx = tid; idx < rem * rem; idx += T) {
-      const int i = j + 1 + idx / rem, l = j + 1 + idx % rem;
-      if (l <= i) L[i * n + l] -= L[i * n + j] * L[l * n + j];
+    for (int i = j + 1 + warp; i < n; i += nw) {
+      const float lij = L[i * ldn + j];
+      for (int l = j + 1 + lane; l <= i; l += 32) L[i * ldn + l] -= lij * L[l * ldn + j];
     }
     __syncthreads();
   }
-  // inverse of lower-triangular L: column c by forward substitution (thread per column)
-  for (int c = tid; c < n; c += T) {
-    Li[c * n + c] = 1.f / L[c * n + c];
+  // inverse of L, one warp per column: forward substitution with warp dot products
+  for (int c = warp; c < n; c += nw) {
+    if (lane == 0) Li[c * ldn + c] = 1.f / dg[c];
+    __syncwarp();
     for (int i = c + 1; i < n; ++i) {
-      float s = 0.f;
-      for (int l = c; l < i; ++l) s = fmaf(L[i * n + l], Li[l * n + c], s);
-      Li[i * n + c] = -s / L[i * n + i];
+      float sacc = 0.f;
+      for (int l = c + lane; l < i; l += 32) sacc = fmaf(L[i * ldn + l], Li[l * ldn + c], sacc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) Li[i * ldn + c] = -sacc / dg[i];
+      __syncwarp();
     }
   }
   __syncthreads();
   // Rinv = (L^T)^{-1} = (L^{-1})^T
-  for (int idx = tid; idx < n * n; idx += T) {
-    const int i = idx / n, j = idx % n;
-    Rinv[idx] = (double)Li[j * n + i];
-  }
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) Rinv[(int64_t)i * n + j] = (double)Li[j * ldn + i];
   if (tid == 0 && s_bad) *flag = 1;
 }
 
@@ -301,6 +311,9 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict
 // Cyclic Jacobi (FP32, one CTA), round-robin parallel ordering: each round
 // applies n/2 disjoint rotations, first to columns (A J, V J) then to rows
 // (J^T A).  Rotation angle from the 2 x 2 symmetric Schur decomposition.
+// Stops when off(A) <= 1e-6 ||A||_F, or when a sweep no longer halves off(A)
+// once it is below 1e-3 ||A||_F (the float32 rounding floor); the FP64
+// refinement that follows supplies the remaining accuracy.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int rr_member(int pos, int round, int np) {
   // circle method: position 0 fixed, the others rotate by `round`
@@ -312,52 +325,53 @@ __global__ void __launch_bounds__(1024) jacobi_f32_kernel(const double* __restri
                                                           int max_sweeps, double* __restrict__ V_out,
                                                           int* __restrict__ flag) {
   extern __shared__ float sm[];
-  float* A = sm;              // n x n
-  float* V = sm + n * n;      // n x n, columns = eigenvectors
-  float* cs = V + n * n;      // [np/2] cos, [np/2] sin
-  int* pq = reinterpret_cast<int*>(cs + n + 2);  // [np/2] p, [np/2] q
-  __shared__ float s_red[32];
-  __shared__ int s_done;
-  const int tid = threadIdx.x, T = blockDim.x;
+  const int ldn = n | 1;
   const int np = n + (n & 1), half = np / 2;
-  for (int idx = tid; idx < n * n; idx += T) {
-    const int i = idx / n, j = idx % n;
-    A[idx] = (float)(0.5 * (A0[i * n + j] + A0[j * n + i]));
-    V[idx] = (i == j) ? 1.f : 0.f;
-  }
-  __syncthreads();
+  float* A = sm;                 // n x ldn
+  float* V = sm + n * ldn;       // n x ldn, columns = eigenvectors
+  float* cs = V + n * ldn;       // [half] cos, [half] sin
+  int* pq = reinterpret_cast<int*>(cs + 2 * half);  // [half] p, [half] q
+  __shared__ float s_red[2][32];
+  __shared__ int s_done;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = T >> 5;
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) {
+      A[i * ldn + j] = (float)(0.5 * (A0[(int64_t)i * n + j] + A0[(int64_t)j * n + i]));
+      V[i * ldn + j] = (i == j) ? 1.f : 0.f;
+    }
+  float off_prev = 3.0e38f;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    // convergence test: off(A)^2 <= tol^2 * ||A||_F^2
+    __syncthreads();
     float off = 0.f, tot = 0.f;
-    for (int idx = tid; idx < n * n; idx += T) {
-      const float v = A[idx] * A[idx];
-      tot += v;
-      if (idx / n != idx % n) off += v;
-    }
+    for (int i = warp; i < n; i += nw)
+      for (int j = lane; j < n; j += 32) {
+        const float v = A[i * ldn + j] * A[i * ldn + j];
+        tot += v;
+        if (i != j) off += v;
+      }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_xor_sync(0xffffffffu, off, o);
       tot += __shfl_xor_sync(0xffffffffu, tot, o);
     }
-    if ((tid & 31) == 0) s_red[tid >> 5] = off;
-    __syncthreads();
-    if (tid == 0) {
-      float o2 = 0.f;
-      for (int w = 0; w < (T + 31) / 32; ++w) o2 += s_red[w];
-      s_red[0] = o2;
+    if (lane == 0) {
+      s_red[0][warp] = off;
+      s_red[1][warp] = tot;
     }
     __syncthreads();
-    const float off_all = s_red[0];
-    __syncthreads();
-    if ((tid & 31) == 0) s_red[tid >> 5] = tot;
-    __syncthreads();
     if (tid == 0) {
-      float t2 = 0.f;
-      for (int w = 0; w < (T + 31) / 32; ++w) t2 += s_red[w];
-      s_done = (off_all <= 1e-11f * t2) ? 1 : 0;
+      float o2 = 0.f, t2 = 0.f;
+      for (int w = 0; w < nw; ++w) {
+        o2 += s_red[0][w];
+        t2 += s_red[1][w];
+      }
+      s_done = (o2 <= 1e-12f * t2) || (o2 <= 1e-6f * t2 && o2 > 0.25f * off_prev);
+      s_red[0][0] = o2;
     }
     __syncthreads();
+    off_prev = s_red[0][0];
     if (s_done) break;
     for (int round = 0; round < np - 1; ++round) {
       if (tid < half) {
@@ -365,9 +379,9 @@ __global__ void __launch_bounds__(1024) jacobi_f32_kernel(const double* __restri
         if (p > q) { const int t = p; p = q; q = t; }
         float c = 1.f, s = 0.f;
         if (q < n) {
-          const float apq = A[p * n + q];
-          const float app = A[p * n + p], aqq = A[q * n + q];
-          if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq))) {
+          const float apq = A[p * ldn + q];
+          const float app = A[p * ldn + p], aqq = A[q * ldn + q];
+          if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-8f * sqrtf(fabsf(app * aqq))) {
             const float tau = (aqq - app) / (2.f * apq);
             const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + t * t);
@@ -380,137 +394,135 @@ __global__ void __launch_bounds__(1024) jacobi_f32_kernel(const double* __restri
         pq[half + tid] = q;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int idx = tid; idx < half * n; idx += T) {
-        const int w = idx / n, r = idx % n;
+      // columns: A <- A J, V <- V J   (warp per pair, lanes over rows)
+      for (int w = warp; w < half; w += nw) {
         const int p = pq[w], q = pq[half + w];
-        if (q >= n) continue;
         const float c = cs[w], s = cs[half + w];
-        if (s == 0.f) continue;
-        const float ap = A[r * n + p], aq = A[r * n + q];
-        A[r * n + p] = c * ap - s * aq;
-        A[r * n + q] = s * ap + c * aq;
-        const float vp = V[r * n + p], vq = V[r * n + q];
-        V[r * n + p] = c * vp - s * vq;
-        V[r * n + q] = s * vp + c * vq;
+        if (q >= n || s == 0.f) continue;
+        for (int r = lane; r < n; r += 32) {
+          const float ap = A[r * ldn + p], aq = A[r * ldn + q];
+          A[r * ldn + p] = c * ap - s * aq;
+          A[r * ldn + q] = s * ap + c * aq;
+          const float vp = V[r * ldn + p], vq = V[r * ldn + q];
+          V[r * ldn + p] = c * vp - s * vq;
+          V[r * ldn + q] = s * vp + c * vq;
+        }
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int idx = tid; idx < half * n; idx += T) {
-        const int w = idx / n, col = idx % n;
+      // rows: A <- J^T A  (warp per pair, lanes over columns); the rotated
+      // off-diagonal pair is zero by construction of the angle
+      for (int w = warp; w < half; w += nw) {
         const int p = pq[w], q = pq[half + w];
-        if (q >= n) continue;
         const float c = cs[w], s = cs[half + w];
-        if (s == 0.f) continue;
-        const float ap = A[p * n + col], aq = A[q * n + col];
-        A[p * n + col] = c * ap - s * aq;
-        A[q * n + col] = s * ap + c * aq;
-      }
-      __syncthreads();
-      if (tid < half) {
-        const int p = pq[tid], q = pq[half + tid];
-        if (q < n && cs[half + tid] != 0.f) {
-          A[p * n + q] = 0.f;
-          A[q * n + p] = 0.f;
+        if (q >= n || s == 0.f) continue;
+        for (int col = lane; col < n; col += 32) {
+          const float ap = A[p * ldn + col], aq = A[q * ldn + col];
+          float np_ = c * ap - s * aq, nq_ = s * ap + c * aq;
+          if (col == q) np_ = 0.f;
+          if (col == p) nq_ = 0.f;
+          A[p * ldn + col] = np_;
+          A[q * ldn + col] = nq_;
         }
       }
       __syncthreads();
     }
   }
-  for (int idx = tid; idx < n * n; idx += T) V_out[idx] = (double)V[idx];
+  __syncthreads();
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) V_out[(int64_t)i * n + j] = (double)V[i * ldn + j];
   if (tid == 0 && sweep >= max_sweeps) *flag = 2;
 }
 
-// One step of the FP64 refinement: from S = X^T A X and P = X^T X build
-// lambda_i = S_ii / P_ii  [= S_ii / (1 - R_ii), R = I - P: Rayleigh quotients] and
-// E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) (i != j, separated),
-//      = R_ij / 2 otherwise,
-// so that X <- X + X E.  One CTA (n <= 160).
-__global__ void __launch_bounds__(1024) refine_e_kernel(const double* __restrict__ S,
-                                                        const double* __restrict__ P,
-                                                        const double* __restrict__ A, int n,
-                                                        double* __restrict__ E,
-                                                        double* __restrict__ lam_out) {
-  extern __shared__ double dsm[];
-  double* lam = dsm;  // n
-  __shared__ double s_red[3][32];
-  __shared__ double s_delta;
-  const int tid = threadIdx.x, T = blockDim.x;
-  for (int i = tid; i < n; i += T) lam[i] = S[i * n + i] / P[i * n + i];
-  __syncthreads();
-  // delta = 2 (||S - diag(lam)||_F + ||A||_F ||R||_F)
-  double a = 0.0, b = 0.0, c = 0.0;
-  for (int idx = tid; idx < n * n; idx += T) {
-    const int i = idx / n, j = idx % n;
-    const double sd = S[idx] - (i == j ? lam[i] : 0.0);
-    const double rr = (i == j ? 1.0 : 0.0) - P[idx];
-    a += sd * sd;
-    b += A[idx] * A[idx];
-    c += rr * rr;
-  }
+// FP64 refinement (Ogita & Aishima), step 1 of 2, one CTA: Rayleigh quotients
+// lambda_i = S_ii / P_ii (= S_ii / (1 - R_ii) with R = I - P) and the cluster
+// threshold delta = 2 (||S - diag(lambda)||_F + ||A||_F ||R||_F) (norms in
+// float32: only their magnitude matters).
+__global__ void __launch_bounds__(1024) refine_lambda_kernel(const double* __restrict__ S,
+                                                             const double* __restrict__ P,
+                                                             const double* __restrict__ A, int n,
+                                                             double* __restrict__ lam,
+                                                             double* __restrict__ delta) {
+  __shared__ float s_red[3][32];
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += T) lam[i] = S[(int64_t)i * n + i] / P[(int64_t)i * n + i];
+  float a = 0.f, b = 0.f, c = 0.f;
+  for (int i = warp; i < n; i += T / 32)
+    for (int j = lane; j < n; j += 32) {
+      const int64_t idx = (int64_t)i * n + j;
+      const float sd = (i == j) ? 0.f : (float)S[idx];
+      const float rr = (float)((i == j ? 1.0 : 0.0) - P[idx]);
+      const float aa = (float)A[idx];
+      a = fmaf(sd, sd, a);
+      b = fmaf(aa, aa, b);
+      c = fmaf(rr, rr, c);
+    }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
     c += __shfl_xor_sync(0xffffffffu, c, o);
   }
-  if ((tid & 31) == 0) {
-    s_red[0][tid >> 5] = a;
-    s_red[1][tid >> 5] = b;
-    s_red[2][tid >> 5] = c;
+  if (lane == 0) {
+    s_red[0][warp] = a;
+    s_red[1][warp] = b;
+    s_red[2][warp] = c;
   }
   __syncthreads();
   if (tid == 0) {
-    double x = 0.0, y = 0.0, z = 0.0;
-    for (int w = 0; w < (T + 31) / 32; ++w) {
+    float x = 0.f, y = 0.f, z = 0.f;
+    for (int w = 0; w < T / 32; ++w) {
       x += s_red[0][w];
       y += s_red[1][w];
       z += s_red[2][w];
     }
-    s_delta = 2.0 * (sqrt(x) + sqrt(y) * sqrt(z));
+    *delta = 2.0 * (sqrt((double)x) + sqrt((double)y) * sqrt((double)z));
   }
-  __syncthreads();
-  const double delta = s_delta;
-  for (int idx = tid; idx < n * n; idx += T) {
-    const int i = idx / n, j = idx % n;
-    const double rij = (i == j ? 1.0 : 0.0) - P[idx];
-    double e;
-    if (i == j) {
-      e = 0.5 * rij;
-    } else {
-      const double gap = lam[j] - lam[i];
-      e = (fabs(gap) > delta) ? (S[idx] + lam[j] * rij) / gap : 0.5 * rij;
-    }
-    E[idx] = e;
-  }
-  for (int i = tid; i < n; i += T) lam_out[i] = lam[i];
 }
 
-// Sort eigenpairs descending, fix signs (largest-magnitude entry positive).
+// Step 2 of 2, many CTAs: E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)
+// for separated eigenvalues, R_ij / 2 inside clusters and on the diagonal, so
+// that X <- X + X E.
+__global__ void refine_e_kernel(const double* __restrict__ S, const double* __restrict__ P,
+                                const double* __restrict__ lam,
+                                const double* __restrict__ delta, int n,
+                                double* __restrict__ E) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  const double rij = (i == j ? 1.0 : 0.0) - P[idx];
+  double e = 0.5 * rij;
+  if (i != j) {
+    const double gap = lam[j] - lam[i];
+    if (fabs(gap) > *delta) e = (S[idx] + lam[j] * rij) / gap;
+  }
+  E[idx] = e;
+}
+
+// Sort eigenpairs descending and fix signs (largest-magnitude entry positive);
+// one warp per eigenpair.
 __global__ void __launch_bounds__(1024) eig_finalize_kernel(const double* __restrict__ lam,
                                                             const double* __restrict__ X, int n,
                                                             double* __restrict__ evals,
                                                             double* __restrict__ evecs) {
-  extern __shared__ int ism[];
-  int* dest = ism;  // n
-  const int tid = threadIdx.x, T = blockDim.x;
-  for (int i = tid; i < n; i += T) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nw) {
+    const double li = lam[i];
     int rank = 0;
-    for (int j = 0; j < n; ++j)
-      if (lam[j] > lam[i] || (lam[j] == lam[i] && j < i)) ++rank;
-    dest[i] = rank;
-  }
-  __syncthreads();
-  for (int i = tid; i < n; i += T) {
     double best = 0.0;
-    for (int r = 0; r < n; ++r) {
-      const double v = X[r * n + i];
+    for (int j = lane; j < n; j += 32) {
+      if (lam[j] > li || (lam[j] == li && j < i)) ++rank;
+      const double v = X[(int64_t)j * n + i];
       if (fabs(v) > fabs(best)) best = v;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rank += __shfl_xor_sync(0xffffffffu, rank, o);
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      if (fabs(ob) > fabs(best) || (fabs(ob) == fabs(best) && ob > best)) best = ob;
+    }
     const double sgn = best < 0.0 ? -1.0 : 1.0;
-    const int c = dest[i];
-    evals[c] = lam[i];
-    for (int r = 0; r < n; ++r) evecs[r * n + c] = sgn * X[r * n + i];
+    if (lane == 0) evals[rank] = li;
+    for (int r = lane; r < n; r += 32) evecs[(int64_t)r * n + rank] = sgn * X[(int64_t)r * n + i];
   }
 }
 
@@ -520,7 +532,9 @@ __global__ void whitening_factors_kernel(const double* __restrict__ evals,
                                          double* __restrict__ eig, int* __restrict__ flag) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < k) eig[idx] = evals[idx];
-  if (idx == 0 && !(evals[k - 1] > 0.0)) *flag = 1;
+  // the k-th eigenvalue must be positive and resolvable above the float32
+  // accuracy of the range finder that produced the matrix
+  if (idx == 0 && !(evals[k - 1] > 1e-5 * fabs(evals[0]))) *flag = 1;
   if (idx >= n * k) return;
   const int64_t r = idx / k, i = idx % k;
   const double l = evals[i];
@@ -551,9 +565,11 @@ otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t 
                           double alpha, double* C, int accumulate, cudaStream_t st) {
   if (!accumulate) OTM_CHECK_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * m * p, st));
   if (rows == 0 || m == 0 || p == 0) return OTM_OK;
+  // about two blocks per SM, but at least 256 rows per block: every block adds
+  // its tile to C with FP64 atomics, so fewer, longer splits mean less contention
   const int64_t tiles = ((m + TN_T - 1) / TN_T) * ((p + TN_T - 1) / TN_T);
   int64_t splits = (2 * num_sms() + tiles - 1) / tiles;
-  const int64_t max_splits = (rows + TN_R - 1) / TN_R;
+  const int64_t max_splits = (rows + 255) / 256;
   splits = splits < 1 ? 1 : (splits > max_splits ? max_splits : splits);
   int64_t rps = (rows + splits - 1) / splits;
   rps = (rps + TN_R - 1) / TN_R * TN_R;
@@ -589,8 +605,8 @@ otm_status dgemm_small(int ta, int tb, int64_t m, int64_t n, int64_t kk, double 
                        const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                        double* C, int64_t ldc, cudaStream_t st) {
   if (m == 0 || n == 0) return OTM_OK;
-  dim3 grid((unsigned)((n + 15) / 16), (unsigned)((m + 15) / 16));
-  dgemm_small_kernel<<<grid, 256, 0, st>>>(ta, tb, m, n, kk, alpha, A, lda, B, ldb, beta, C, ldc);
+  dim3 grid((unsigned)((n + 7) / 8), (unsigned)((m + 7) / 8));
+  dgemm_small_kernel<<<grid, 64, 0, st>>>(ta, tb, m, n, kk, alpha, A, lda, B, ldb, beta, C, ldc);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }
@@ -607,44 +623,48 @@ otm_status vec_tn(const double* u, const float* A, int64_t rows, int64_t m, doub
 
 size_t orth_workspace(int64_t m) {
   WorkspaceSize w;
-  w.add<double>(m * m).add<double>(m * m).add<int>(1);
+  w.add<double>(m * m).add<double>(m * m);
   return w.bytes();
 }
 
-otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cudaStream_t st) {
+otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cudaStream_t st,
+                          int* dflag) {
   if (m > 160) return set_error(OTM_EINVAL, "orthonormalize: m=%lld > 160", (long long)m);
   if (rows < m) return set_error(OTM_EINVAL, "orthonormalize: rows < m");
   double* G = ws.take<double>(m * m);
   double* Rinv = ws.take<double>(m * m);
-  int* flag = ws.take<int>(1);
-  if (!G || !Rinv || !flag) return set_error(OTM_EINVAL, "orthonormalize: workspace too small");
-  OTM_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  const size_t smem = 2 * sizeof(float) * m * m;
+  if (!G || !Rinv) return set_error(OTM_EINVAL, "orthonormalize: workspace too small");
+  const size_t smem = sizeof(float) * (2 * m * (m | 1) + m);
   OTM_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-  for (int pass = 0; pass < 3; ++pass) {
+  // two shifted passes bring kappa(A) down to where plain Cholesky-QR2 is stable
+  for (int pass = 0; pass < 4; ++pass) {
     OTM_TRY(gemm_tn_f64acc(A, A, rows, m, m, 1.0, G, 0, st));
-    chol_inv_kernel<<<1, 1024, smem, st>>>(G, (int)m, pass == 0 ? 11.0 : 0.0, Rinv, flag);
+    chol_inv_kernel<<<1, 1024, smem, st>>>(G, (int)m, pass < 2 ? 11.0 : 0.0, Rinv, dflag);
     OTM_CHECK_LAUNCH();
     OTM_TRY(gemm_nn_small(A, rows, m, Rinv, m, A, nullptr, nullptr, 0.0, st));
   }
-  int h = 0;
-  OTM_CHECK_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (h) return set_error(OTM_ENOTCONVERGED, "orthonormalize: Cholesky pivot failed");
   return OTM_OK;
 }
 
 size_t syev_workspace(int64_t n) {
   WorkspaceSize w;
-  for (int i = 0; i < 6; ++i) w.add<double>(n * n);
-  w.add<double>(n).add<int>(1);
+  for (int i = 0; i < 7; ++i) w.add<double>(n * n);
+  w.add<double>(n).add<double>(1);
   return w.bytes();
 }
 
-otm_status syev(const double* A, int64_t n, double* evals, double* evecs, Workspace& ws,
-                cudaStream_t st) {
+__global__ void symmetrize_kernel(const double* __restrict__ A, int64_t n, double* __restrict__ B) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  B[idx] = 0.5 * (A[i * n + j] + A[j * n + i]);
+}
+
+otm_status syev(const double* A_in, int64_t n, double* evals, double* evecs, Workspace& ws,
+                cudaStream_t st, int* dflag) {
   if (n < 1 || n > 160) return set_error(OTM_EINVAL, "syev: n=%lld outside [1, 160]", (long long)n);
+  double* A = ws.take<double>(n * n);
   double* X = ws.take<double>(n * n);
   double* Xn = ws.take<double>(n * n);
   double* AX = ws.take<double>(n * n);
@@ -652,38 +672,36 @@ otm_status syev(const double* A, int64_t n, double* evals, double* evecs, Worksp
   double* P = ws.take<double>(n * n);
   double* E = ws.take<double>(n * n);
   double* lam = ws.take<double>(n);
-  int* flag = ws.take<int>(1);
-  if (!flag) return set_error(OTM_EINVAL, "syev: workspace too small");
-  OTM_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  const int np = (int)(n + (n & 1));
-  const size_t smem = sizeof(float) * (2 * n * n + n + 2) + sizeof(int) * np + 16;
+  double* delta = ws.take<double>(1);
+  if (!delta) return set_error(OTM_EINVAL, "syev: workspace too small");
+  const unsigned nb = (unsigned)((n * n + 255) / 256);
+  symmetrize_kernel<<<nb, 256, 0, st>>>(A_in, n, A);
+  OTM_CHECK_LAUNCH();
+  const int64_t ldn = n | 1, half = (n + (n & 1)) / 2;
+  const size_t smem = sizeof(float) * (2 * n * ldn + 2 * half) + sizeof(int) * 2 * half + 16;
   OTM_CHECK_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  jacobi_f32_kernel<<<1, 1024, smem, st>>>(A, (int)n, 40, X, flag);
+  jacobi_f32_kernel<<<1, 1024, smem, st>>>(A, (int)n, 40, X, dflag);
   OTM_CHECK_LAUNCH();
-  const int iters = 3;
+  // FP64 refinement: quadratic convergence from the float32 eigenvectors
+  const int iters = 4;
   for (int it = 0; it < iters; ++it) {
-    // AX = A X, S = X^T (A X), P = X^T X   (A read symmetrically: A^T = A assumed after
-    // symmetrisation; use (A + A^T)/2 X = 0.5 A X + 0.5 A^T X)
-    OTM_TRY(dgemm_small(0, 0, n, n, n, 0.5, A, n, X, n, 0.0, AX, n, st));
-    OTM_TRY(dgemm_small(1, 0, n, n, n, 0.5, A, n, X, n, 1.0, AX, n, st));
+    OTM_TRY(dgemm_small(0, 0, n, n, n, 1.0, A, n, X, n, 0.0, AX, n, st));
     OTM_TRY(dgemm_small(1, 0, n, n, n, 1.0, X, n, AX, n, 0.0, S, n, st));
     OTM_TRY(dgemm_small(1, 0, n, n, n, 1.0, X, n, X, n, 0.0, P, n, st));
-    refine_e_kernel<<<1, 1024, sizeof(double) * n, st>>>(S, P, A, (int)n, E, lam);
+    refine_lambda_kernel<<<1, 1024, 0, st>>>(S, P, A, (int)n, lam, delta);
     OTM_CHECK_LAUNCH();
-    copy_f64_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(X, Xn, n * n);
+    refine_e_kernel<<<nb, 256, 0, st>>>(S, P, lam, delta, (int)n, E);
+    OTM_CHECK_LAUNCH();
+    copy_f64_kernel<<<nb, 256, 0, st>>>(X, Xn, n * n);
     OTM_CHECK_LAUNCH();
     OTM_TRY(dgemm_small(0, 0, n, n, n, 1.0, X, n, E, n, 1.0, Xn, n, st));
     double* t = X;
     X = Xn;
     Xn = t;
   }
-  eig_finalize_kernel<<<1, 256, sizeof(int) * n, st>>>(lam, X, (int)n, evals, evecs);
+  eig_finalize_kernel<<<1, 1024, 0, st>>>(lam, X, (int)n, evals, evecs);
   OTM_CHECK_LAUNCH();
-  int h = 0;
-  OTM_CHECK_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (h) return set_error(OTM_ENOTCONVERGED, "syev: Jacobi sweep limit reached");
   return OTM_OK;
 }
 

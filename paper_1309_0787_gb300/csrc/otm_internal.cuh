@@ -101,10 +101,13 @@ otm_status dgemm_small(int ta, int tb, int64_t m, int64_t n, int64_t kk, double 
                        const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                        double* C, int64_t ldc, cudaStream_t st);
 size_t orth_workspace(int64_t m);
-otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cudaStream_t st);
+// Device-side failure flags: *dflag is set to 1 (QR: non-finite Gram matrix) or
+// 2 (eigensolver: Jacobi sweep limit); callers zero it and check it once.
+otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cudaStream_t st,
+                          int* dflag);
 size_t syev_workspace(int64_t n);
 otm_status syev(const double* A, int64_t n, double* evals, double* evecs, Workspace& ws,
-                cudaStream_t st);
+                cudaStream_t st, int* dflag);
 // out[j] = sum_r u[r] * A[r, j]  (FP64 u, float32 A rows x m)
 otm_status vec_tn(const double* u, const float* A, int64_t rows, int64_t m, double* out,
                   cudaStream_t st);

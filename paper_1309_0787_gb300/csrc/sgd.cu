@@ -71,11 +71,10 @@ __host__ __device__ inline Layout make_layout(int k, int CL, bool sym) {
   return L;
 }
 
-template <bool SYM, int MT>
+template <bool SYM, int MT, int CL>
 __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cluster = cg::this_cluster();
-  const int CL = (int)cluster.num_blocks();
   const int q = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k;
@@ -263,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
         for (int m = 0; m < MT; ++m) {
           const int g = tid + THREADS * m;
           if (g < nt * nt) {
-            const int r0 = 4 * (g / nt), i0 = 4 * (g % nt);
+            const int r0 = 4 * (g % nt), i0 = 4 * (g / nt);
 #pragma unroll 8
             for (int tt = 0; tt < TC; ++tt) {
               const float4 yc = *reinterpret_cast<const float4*>(Yc + tt * ldk + r0);
@@ -288,11 +287,11 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
       for (int m = 0; m < MT; ++m) {
         const int g = tid + THREADS * m;
         if (g < nt * nt) {
-          const int r0 = 4 * (g / nt), i0 = 4 * (g % nt);
+          const int r0 = 4 * (g % nt), i0 = 4 * (g / nt);
 #pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) Gp[(i0 + y) * ldk + r0 + x] = gacc[m][x][y];
+          for (int y = 0; y < 4; ++y)
+            *reinterpret_cast<float4*>(Gp + (i0 + y) * ldk + r0) =
+                make_float4(gacc[m][0][y], gacc[m][1][y], gacc[m][2][y], gacc[m][3][y]);
         }
       }
     }
@@ -301,15 +300,23 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
     // phase 6: owned columns -- reduce over the cluster, Gram term, update, broadcast
     const int nown = own_hi - own_lo;
     if (tid < nown) {
+      float part[CL];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) part[c] = cluster.map_shared_rank(spart, c)[own_lo + tid];
       float ss = 0.f;
-      for (int c = 0; c < CL; ++c) ss += cluster.map_shared_rank(spart, c)[own_lo + tid];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) ss += part[c];
       sown[tid] = ss;
     }
     for (int idx = tid; idx < nown * kp; idx += THREADS) {
       const int jj = idx / kp, r = idx % kp;
       const int i = own_lo + jj;
+      float part[CL];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) part[c] = cluster.map_shared_rank(Gp, c)[i * ldk + r];
       float g = 0.f;
-      for (int c = 0; c < CL; ++c) g += cluster.map_shared_rank(Gp, c)[i * ldk + r];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) g += part[c];
       gd[jj * ldk + r] = g;
     }
     for (int idx = tid; idx < nown * kp; idx += THREADS) {
@@ -339,10 +346,11 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
       vn[jj * ldk + r] = (r < k) ? vnew : 0.f;
     }
     __syncthreads();
-    for (int idx = tid; idx < CL * nown * kp; idx += THREADS) {
-      const int c = idx / (nown * kp), rem = idx % (nown * kp);
-      const int jj = rem / kp, r = rem % kp;
-      cluster.map_shared_rank(Vn, c)[(own_lo + jj) * ldk + r] = vn[jj * ldk + r];
+    for (int idx = tid; idx < nown * kp; idx += THREADS) {
+      const int jj = idx / kp, r = idx % kp;
+      const float v = vn[jj * ldk + r];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) cluster.map_shared_rank(Vn, c)[(own_lo + jj) * ldk + r] = v;
     }
     cluster.sync();  // next V complete everywhere; partials may be overwritten
 
@@ -361,11 +369,11 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
   }
 }
 
-template <bool SYM, int MT>
-otm_status launch_mt(const SgdArgs& args, int CL, cudaStream_t st) {
+template <bool SYM, int MT, int CL>
+otm_status launch_cl(const SgdArgs& args, cudaStream_t st) {
   const Layout L = make_layout(args.k, CL, SYM);
   const size_t smem = L.total_floats * sizeof(float);
-  auto kern = sgd_cluster_kernel<SYM, MT>;
+  auto kern = sgd_cluster_kernel<SYM, MT, CL>;
   OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (CL > 8)
     OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -384,6 +392,17 @@ otm_status launch_mt(const SgdArgs& args, int CL, cudaStream_t st) {
   OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
   count_launch();
   return OTM_OK;
+}
+
+template <bool SYM, int MT>
+otm_status launch_mt(const SgdArgs& args, int CL, cudaStream_t st) {
+  switch (CL) {
+    case 16: return launch_cl<SYM, MT, 16>(args, st);
+    case 8: return launch_cl<SYM, MT, 8>(args, st);
+    case 4: return launch_cl<SYM, MT, 4>(args, st);
+    case 2: return launch_cl<SYM, MT, 2>(args, st);
+    default: return launch_cl<SYM, MT, 1>(args, st);
+  }
 }
 
 template <bool SYM>
@@ -455,7 +474,7 @@ otm_status run(float* V, const float* YA, const float* YB, const float* YC, int6
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    auto kern = sgd_cluster_kernel<false, 4>;
+    auto kern = sgd_cluster_kernel<false, 4, 16>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)cfg.dynamicSmemBytes);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -107,7 +107,7 @@ struct CommunityOp {
 template <class Op>
 otm_status range_finder(const Op& op, int64_t d, const float* S, int64_t k, int64_t kt,
                         int power_iters, float* W, float* Q, double* Cw, double* Cp, double* eig,
-                        Workspace& ws, cudaStream_t st, int* flag) {
+                        Workspace& ws, cudaStream_t st, int* flags) {
   float* O = ws.take<float>(d * kt);
   double* Om = ws.take<double>(kt * kt);
   double* ev = ws.take<double>(kt);
@@ -115,26 +115,35 @@ otm_status range_finder(const Op& op, int64_t d, const float* S, int64_t k, int6
   if (!O || !Om || !ev || !evec) return set_error(OTM_EINVAL, "whiten: workspace too small");
   const size_t mark = ws.used;
   OTM_TRY(op.apply(S, kt, Q, st));
-  OTM_TRY(orthonormalize(Q, d, kt, ws, st));
+  OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2));
   ws.used = mark;
   for (int it = 0; it < power_iters; ++it) {
     OTM_TRY(op.apply(Q, kt, O, st));
     OTM_CHECK_CUDA(cudaMemcpyAsync(Q, O, sizeof(float) * d * kt, cudaMemcpyDeviceToDevice, st));
-    OTM_TRY(orthonormalize(Q, d, kt, ws, st));
+    OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2));
     ws.used = mark;
   }
   OTM_TRY(op.apply(Q, kt, O, st));
   OTM_TRY(gemm_tn_f64acc(Q, O, d, kt, kt, 1.0, Om, 0, st));
-  OTM_TRY(syev(Om, kt, ev, evec, ws, st));
+  OTM_TRY(syev(Om, kt, ev, evec, ws, st, flags + 2));
   ws.used = mark;
-  OTM_TRY(whitening_factors(ev, evec, kt, k, Cw, Cp, eig, flag, st));
+  OTM_TRY(whitening_factors(ev, evec, kt, k, Cw, Cp, eig, flags, st));
   OTM_TRY(gemm_nn_small(Q, d, kt, Cw, k, W, nullptr, nullptr, 0.0, st));
   return OTM_OK;
 }
 
-otm_status read_flag(int* flag, cudaStream_t st, int* out) {
-  OTM_CHECK_CUDA(cudaMemcpyAsync(out, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+// Flag slots written by the device: [0] k-th eigenvalue of M2 not resolvable,
+// [1] Pairs(C,B) of numerical rank < k, [2] QR / eigensolver failure.
+constexpr int kFlags = 4;
+
+otm_status check_flags(int* flags, cudaStream_t st, const char* who) {
+  int h[kFlags] = {0, 0, 0, 0};
+  OTM_CHECK_CUDA(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, st));
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (h[2]) return set_error(OTM_ENOTCONVERGED, "%s: QR or eigensolver failed (non-finite data or "
+                             "Jacobi sweep limit)", who);
+  if (h[1]) return set_error(OTM_ENOTPSD, "%s: Pairs(C,B) has numerical rank < k", who);
+  if (h[0]) return set_error(OTM_ENOTPSD, "%s: fewer than k resolvable positive eigenvalues", who);
   return OTM_OK;
 }
 
@@ -204,7 +213,7 @@ otm_status otm_pairs_apply(const otm_csr* G1, const otm_csr* G2, const float* S,
 size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t k, int64_t kt) {
   (void)k;
   WorkspaceSize w;
-  w.add<double>(d).add<float>(n * kt).add<double>(kt).add<int>(1);
+  w.add<double>(d).add<float>(n * kt).add<double>(kt).add<int>(kFlags);
   return w.bytes() + range_finder_ws(d, kt);
 }
 
@@ -230,15 +239,12 @@ otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t
   double* delta = w.take<double>(X->cols);
   float* P = w.take<float>(X->rows * kt);
   double* u = w.take<double>(kt);
-  int* flag = w.take<int>(1);
-  OTM_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  int* flags = w.take<int>(kFlags);
+  OTM_CHECK_CUDA(cudaMemsetAsync(flags, 0, kFlags * sizeof(int), st));
   OTM_TRY(topic_moments(X, row_invlen, row_w, M1, delta, st));
   TopicOp op{X, row_w, M1, delta, alpha0, P, u};
-  OTM_TRY(range_finder(op, X->cols, S, k, kt, power_iters, W, Q, Cw, Cp, eig, w, st, flag));
-  int h = 0;
-  OTM_TRY(read_flag(flag, st, &h));
-  if (h) return set_error(OTM_ENOTPSD, "otm_whiten_topic: fewer than k positive eigenvalues");
-  return OTM_OK;
+  OTM_TRY(range_finder(op, X->cols, S, k, kt, power_iters, W, Q, Cw, Cp, eig, w, st, flags));
+  return check_flags(flags, st, "otm_whiten_topic");
 }
 
 size_t otm_whiten_community_workspace(int64_t n_x, int64_t n_a, int64_t n_b, int64_t n_c,
@@ -251,7 +257,7 @@ size_t otm_whiten_community_workspace(int64_t n_x, int64_t n_a, int64_t n_b, int
   w.add<float>(n_x * k).add<float>(n_x * k).add<float>(n_a * 2 * k);  // CU, BV, L
   w.add<double>(k * k);                                           // K
   w.add<double>(2 * k * kt).add<double>(2 * k * kt).add<double>(kt);  // ab, coef, u
-  w.add<double>(2 * k * k).add<int>(2);                            // LW, flags
+  w.add<double>(2 * k * k).add<int>(kFlags);                       // LW, flags
   const size_t a = w.bytes();
   const size_t inner = orth_workspace(kt) > syev_workspace(kt) ? orth_workspace(kt)
                                                                   : syev_workspace(kt);
@@ -304,25 +310,25 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
   double* coef = w.take<double>(2 * k * kt);
   double* u = w.take<double>(kt);
   double* LW = w.take<double>(2 * k * k);
-  int* flags = w.take<int>(2);
-  OTM_CHECK_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), st));
+  int* flags = w.take<int>(kFlags);
+  OTM_CHECK_CUDA(cudaMemsetAsync(flags, 0, kFlags * sizeof(int), st));
   const size_t mark = w.used;
 
   // 1. rank-k randomised SVD of Pairs(C,B) ~ U_C diag(sigma) V_B^T
   OTM_TRY(pairs_apply_ws(G_XC, G_XB, S_pairs, kt, Yc, tmp, st));
-  OTM_TRY(orthonormalize(Yc, nc, kt, w, st));
+  OTM_TRY(orthonormalize(Yc, nc, kt, w, st, flags + 2));
   w.used = mark;
   for (int it = 0; it < power_iters; ++it) {
     OTM_TRY(pairs_apply_ws(G_XB, G_XC, Yc, kt, Zb, tmp, st));
-    OTM_TRY(orthonormalize(Zb, nb, kt, w, st));
+    OTM_TRY(orthonormalize(Zb, nb, kt, w, st, flags + 2));
     w.used = mark;
     OTM_TRY(pairs_apply_ws(G_XC, G_XB, Zb, kt, Yc, tmp, st));
-    OTM_TRY(orthonormalize(Yc, nc, kt, w, st));
+    OTM_TRY(orthonormalize(Yc, nc, kt, w, st, flags + 2));
     w.used = mark;
   }
   OTM_TRY(pairs_apply_ws(G_XB, G_XC, Yc, kt, Zb, tmp, st));  // B^T = Pairs(B,C) Q
   OTM_TRY(gemm_tn_f64acc(Zb, Zb, nb, kt, kt, 1.0, BB, 0, st));
-  OTM_TRY(syev(BB, kt, ev, evec, w, st));
+  OTM_TRY(syev(BB, kt, ev, evec, w, st, flags + 2));
   w.used = mark;
   take_cols_kernel<<<blocks_for(kt * k), 256, 0, st>>>(evec, kt, k, Ub);
   OTM_CHECK_LAUNCH();
@@ -353,12 +359,7 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
   OTM_TRY(gemm_nn_small(V_B, nb, k, LW + k * k, k, W_B, nullptr, nullptr, 0.0, st));
   OTM_TRY(gemm_nn_small(U_C, nc, k, LW, k, W_C, nullptr, nullptr, 0.0, st));
 
-  int h[2] = {0, 0};
-  OTM_CHECK_CUDA(cudaMemcpyAsync(h, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (h[1]) return set_error(OTM_ENOTPSD, "otm_whiten_community: Pairs(C,B) has rank < k");
-  if (h[0]) return set_error(OTM_ENOTPSD, "otm_whiten_community: fewer than k positive eigenvalues");
-  return OTM_OK;
+  return check_flags(flags, st, "otm_whiten_community");
 }
 
 }  // extern "C"
