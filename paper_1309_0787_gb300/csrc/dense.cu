@@ -226,7 +226,12 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 
 // ---------------------------------------------------------------------------
 // Cholesky of G (+ shift) and the inverse of its upper factor R = L^T.
-// One CTA, FP32 in shared memory (n <= 160).  Output Rinv (n x n, FP64,
+// One CTA of 256 threads, FP32 in shared memory (n <= 160), blocked by 8
+// columns: one warp factors each 8 x 8 diagonal block in registers (shuffles,
+// no barrier), the panel below is solved against the block's inverse, and
+// the trailing matrix takes a rank-8 update -- three barriers per block
+// column instead of two per column.  L^{-1} is then formed by blocked forward
+// substitution (two barriers per block row).  Output Rinv (n x n, FP64,
 // row-major, upper triangular) so that Q = A Rinv.
 // shift_scale > 0 adds shift_scale * n * u * trace(G) to the diagonal
 // (u = 2^-24), which keeps the factorisation positive definite for Gram
@@ -237,19 +242,23 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 // which the following passes orthonormalise -- still a valid orthonormal
 // basis of a space containing range(A).  Only a non-finite pivot is an error.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G, int n,
+constexpr int CH_T = 256, CH_B = 8;
+
+__global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict__ G, int n,
                                                         double shift_scale,
                                                         double* __restrict__ Rinv,
                                                         int* __restrict__ flag) {
   extern __shared__ float sm[];
   const int ldn = n | 1;       // odd row stride: column walks are bank-conflict free
-  float* L = sm;               // n x ldn, lower triangle used (diagonal kept in dg)
-  float* Li = sm + n * ldn;    // n x ldn, inverse of L (lower)
-  float* dg = Li + n * ldn;    // n, diagonal of L
+  const int nblk = (n + CH_B - 1) / CH_B;
+  float* L = sm;                         // n x ldn (lower triangle)
+  float* X = L + n * ldn;                // n x ldn, X = L^{-1} (lower triangle)
+  float* Dinv = X + n * ldn;             // nblk x 8 x 8, inverses of the diagonal blocks
+  float* tmp = Dinv + nblk * 64;         // 8 x n scratch
   __shared__ float s_shift, s_floor;
   __shared__ int s_bad;
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = T >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = CH_T / 32;
   if (warp == 0) {
     double tr = 0.0;
     for (int i = lane; i < n; i += 32) tr += G[(int64_t)i * n + i];
@@ -262,48 +271,138 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict
     }
   }
   __syncthreads();
-  for (int i = warp; i < n; i += nw)
-    for (int j = lane; j < n; j += 32) {
+  for (int i = warp; i < n; i += NW)
+    for (int j = lane; j <= i; j += 32) {
       float v = (float)(0.5 * (G[(int64_t)i * n + j] + G[(int64_t)j * n + i]));
       if (i == j) v += s_shift;
       L[i * ldn + j] = v;
-      Li[i * ldn + j] = 0.f;
     }
   __syncthreads();
-  // right-looking Cholesky; every thread derives the pivot itself (no extra barrier)
-  for (int j = 0; j < n; ++j) {
-    float d = L[j * ldn + j];
-    if (!isfinite(d)) {
-      if (tid == 0) s_bad = 1;
-      d = 1.f;
-    }
-    const float djj = sqrtf(fmaxf(d, s_floor));
-    if (tid == 0) dg[j] = djj;
-    for (int i = j + 1 + tid; i < n; i += T) L[i * ldn + j] /= djj;
-    __syncthreads();
-    for (int i = j + 1 + warp; i < n; i += nw) {
-      const float lij = L[i * ldn + j];
-      for (int l = j + 1 + lane; l <= i; l += 32) L[i * ldn + l] -= lij * L[l * ldn + j];
-    }
-    __syncthreads();
-  }
-  // inverse of L, one warp per column: forward substitution with warp dot products
-  for (int c = warp; c < n; c += nw) {
-    if (lane == 0) Li[c * ldn + c] = 1.f / dg[c];
-    __syncwarp();
-    for (int i = c + 1; i < n; ++i) {
-      float sacc = 0.f;
-      for (int l = c + lane; l < i; l += 32) sacc = fmaf(L[i * ldn + l], Li[l * ldn + c], sacc);
+
+  for (int J = 0; J < nblk; ++J) {
+    const int j0 = J * CH_B, jb = min(CH_B, n - j0);
+    // (1) factor the diagonal block: lane r holds row j0 + r
+    if (warp == 0) {
+      float a[CH_B];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) Li[i * ldn + c] = -sacc / dg[i];
+      for (int c = 0; c < CH_B; ++c)
+        a[c] = (lane < jb && c <= lane) ? L[(j0 + lane) * ldn + j0 + c] : 0.f;
+#pragma unroll
+      for (int c = 0; c < CH_B; ++c) {
+        if (c < jb) {
+          float d = __shfl_sync(0xffffffffu, a[c], c);
+          if (!isfinite(d)) {
+            if (lane == 0) s_bad = 1;
+            d = 1.f;
+          }
+          const float piv = sqrtf(fmaxf(d, s_floor));
+          if (lane == c) a[c] = piv;
+          if (lane > c) a[c] /= piv;
+#pragma unroll
+          for (int kk = c + 1; kk < CH_B; ++kk) {
+            const float lkc = __shfl_sync(0xffffffffu, a[c], kk);
+            if (kk < jb && lane >= kk && lane < jb) a[kk] -= a[c] * lkc;
+          }
+        }
+      }
+      if (lane < jb) {
+#pragma unroll
+        for (int c = 0; c < CH_B; ++c)
+          if (c <= lane) L[(j0 + lane) * ldn + j0 + c] = a[c];
+      }
       __syncwarp();
+      // inverse of the diagonal block (lower triangular), lane c owns column c
+      float* D = Dinv + J * 64;
+      if (lane < jb) {
+        float x[CH_B];
+#pragma unroll
+        for (int r = 0; r < CH_B; ++r) {
+          float v = 0.f;
+          if (r == lane) v = 1.f / L[(j0 + r) * ldn + j0 + r];
+          if (r > lane && r < jb) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int l2 = 0; l2 < CH_B; ++l2)
+              if (l2 >= lane && l2 < r) sacc = fmaf(L[(j0 + r) * ldn + j0 + l2], x[l2], sacc);
+            v = -sacc / L[(j0 + r) * ldn + j0 + r];
+          }
+          x[r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < CH_B; ++r) D[r * CH_B + lane] = x[r];
+      }
+      if (lane >= jb && lane < CH_B) {
+#pragma unroll
+        for (int r = 0; r < CH_B; ++r) D[r * CH_B + lane] = 0.f;
+      }
     }
+    __syncthreads();
+    // (2) panel: L_iJ = A_iJ L_JJ^{-T} for the rows below the block
+    {
+      const float* D = Dinv + J * 64;
+      for (int i = j0 + jb + tid; i < n; i += CH_T) {
+        float a[CH_B], l[CH_B];
+#pragma unroll
+        for (int c = 0; c < CH_B; ++c) a[c] = c < jb ? L[i * ldn + j0 + c] : 0.f;
+#pragma unroll
+        for (int c = 0; c < CH_B; ++c) {
+          float v = 0.f;
+#pragma unroll
+          for (int m2 = 0; m2 <= c; ++m2) v = fmaf(a[m2], D[c * CH_B + m2], v);
+          l[c] = v;
+        }
+#pragma unroll
+        for (int c = 0; c < CH_B; ++c)
+          if (c < jb) L[i * ldn + j0 + c] = l[c];
+      }
+    }
+    __syncthreads();
+    // (3) trailing rank-jb update of the lower triangle
+    for (int i = j0 + jb + warp; i < n; i += NW) {
+      float li[CH_B];
+#pragma unroll
+      for (int c = 0; c < CH_B; ++c) li[c] = c < jb ? L[i * ldn + j0 + c] : 0.f;
+      for (int l2 = j0 + jb + lane; l2 <= i; l2 += 32) {
+        float acc = L[i * ldn + l2];
+#pragma unroll
+        for (int c = 0; c < CH_B; ++c)
+          if (c < jb) acc = fmaf(-li[c], L[l2 * ldn + j0 + c], acc);
+        L[i * ldn + l2] = acc;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  // Rinv = (L^T)^{-1} = (L^{-1})^T
-  for (int i = warp; i < n; i += nw)
-    for (int j = lane; j < n; j += 32) Rinv[(int64_t)i * n + j] = (double)Li[j * ldn + i];
+
+  // X = L^{-1} by block rows: X_II = Dinv_I,
+  // X_IJ = -Dinv_I sum_{K < I} L_IK X_KJ  for the columns left of block I
+  for (int I = 0; I < nblk; ++I) {
+    const int i0 = I * CH_B, ib = min(CH_B, n - i0);
+    // tmp[r][c] = sum_{m=c}^{i0-1} L[i0+r][m] X[m][c], c < i0
+    for (int idx = tid; idx < ib * i0; idx += CH_T) {
+      const int r = idx / i0, c = idx % i0;
+      float sacc = 0.f;
+      for (int m2 = c; m2 < i0; ++m2) sacc = fmaf(L[(i0 + r) * ldn + m2], X[m2 * ldn + c], sacc);
+      tmp[r * n + c] = sacc;
+    }
+    __syncthreads();
+    const float* D = Dinv + I * 64;
+    for (int idx = tid; idx < ib * (i0 + ib); idx += CH_T) {
+      const int r = idx / (i0 + ib), c = idx % (i0 + ib);
+      float v;
+      if (c < i0) {
+        v = 0.f;
+        for (int r2 = 0; r2 <= r; ++r2) v = fmaf(-D[r * CH_B + r2], tmp[r2 * n + c], v);
+      } else {
+        v = D[r * CH_B + (c - i0)];
+      }
+      X[(i0 + r) * ldn + c] = v;
+    }
+    __syncthreads();
+  }
+  // Rinv = (L^T)^{-1} = (L^{-1})^T, zero below the diagonal
+  for (int i = warp; i < n; i += NW)
+    for (int j = lane; j < n; j += 32)
+      Rinv[(int64_t)i * n + j] = j >= i ? (double)X[j * ldn + i] : 0.0;
   if (tid == 0 && s_bad) *flag = 1;
 }
 
@@ -433,6 +532,231 @@ __global__ void __launch_bounds__(1024) jacobi_f32_kernel(const double* __restri
   if (tid == 0 && sweep >= max_sweeps) *flag = 2;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 starting eigenvectors for the FP64 refinement, one CTA of 256 threads
+// (n <= 160), all in shared memory:
+//  1. Householder reduction to tridiagonal form T = H^T A H (classical
+//     two-sided reflections v, tau; three barriers per column);
+//  2. every eigenvalue of T by bisection on Sturm counts (thread per
+//     eigenvalue);
+//  3. eigenvectors of T from twisted factorisations (the forward LDL^T and
+//     backward UDU^T factorisations of T - lambda I, twisted where the
+//     diagonal of the twisted factorisation is smallest; Parlett & Dhillon,
+//     "Relatively robust representations of symmetric tridiagonals", 2000),
+//     one thread per eigenvector, Gram-Schmidt inside groups of eigenvalues
+//     closer than 1e-4 ||T||;
+//  4. back-transformation X = H Z with one thread per column (no barriers).
+// Output: X (n x n FP64, row-major, column i = eigenvector i, eigenvalues
+// ascending).  fac: 2 n^2 floats of global scratch for the factorisations.
+// ---------------------------------------------------------------------------
+constexpr int TE_T = 256;
+
+__device__ __forceinline__ float block_sum_f(float v, float* red, int tid) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < TE_T / 32; ++w) t += red[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restrict__ A0, int n,
+                                                           double* __restrict__ X_out,
+                                                           float* __restrict__ fac) {
+  extern __shared__ float sm[];
+  const int ldn = n | 1;
+  float* Ah = sm;               // n x ldn: the matrix, then the reflectors (column j, rows > j)
+  float* Z = Ah + n * ldn;      // n x ldn: eigenvectors of T, then of A
+  float* d = Z + n * ldn;       // n  diagonal of T
+  float* e = d + n;             // n  off-diagonal of T (e[j] couples j and j+1)
+  float* tau = e + n;           // n
+  float* P = tau + n;           // n  p = tau A v
+  float* lam = P + n;           // n  eigenvalues of T (ascending)
+  __shared__ float red[2][TE_T / 32];
+  __shared__ float s_alpha, s_tau, s_v0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = TE_T / 32;
+  for (int i = warp; i < n; i += NW)
+    for (int j = lane; j < n; j += 32)
+      Ah[i * ldn + j] = (float)(0.5 * (A0[(int64_t)i * n + j] + A0[(int64_t)j * n + i]));
+  __syncthreads();
+
+  // 1. Householder tridiagonalisation
+  for (int j = 0; j + 2 < n; ++j) {
+    const int r0 = j + 1;  // first row of the column part x = A[r0:, j]
+    float part = 0.f;
+    for (int r = r0 + tid; r < n; r += TE_T) part += Ah[r * ldn + j] * Ah[r * ldn + j];
+    const float sigma = block_sum_f(part, red[0], tid);
+    const float x0 = Ah[r0 * ldn + j];
+    float alpha, tj, v0;
+    if (sigma <= 1e-36f) {
+      alpha = x0;
+      tj = 0.f;
+      v0 = 0.f;
+    } else {
+      alpha = -copysignf(sqrtf(sigma), x0);
+      v0 = x0 - alpha;
+      tj = 1.f / (sigma - x0 * alpha);  // 2 / (v^T v), v^T v = 2 (sigma - x0 alpha)
+    }
+    // p = tau A_trail v  (thread per trailing row), and p^T v
+    float pv = 0.f;
+    for (int i = r0 + tid; i < n; i += TE_T) {
+      float acc = Ah[i * ldn + r0] * v0;
+      for (int c = r0 + 1; c < n; ++c) acc = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], acc);
+      const float pi = tj * acc;
+      P[i] = pi;
+      pv = fmaf(pi, i == r0 ? v0 : Ah[i * ldn + j], pv);
+    }
+    const float ptv = block_sum_f(pv, red[1], tid);  // includes a barrier: P complete
+    const float K = 0.5f * tj * ptv;
+    // A_trail -= v w^T + w v^T, w = p - K v
+    for (int i = r0 + warp; i < n; i += NW) {
+      const float vi = i == r0 ? v0 : Ah[i * ldn + j];
+      const float wi = P[i] - K * vi;
+      for (int c = r0 + lane; c < n; c += 32) {
+        const float vc = c == r0 ? v0 : Ah[c * ldn + j];
+        const float wc = P[c] - K * vc;
+        Ah[i * ldn + c] -= vi * wc + wi * vc;
+      }
+    }
+    if (tid == 0) {
+      d[j] = Ah[j * ldn + j];
+      e[j] = alpha;
+      tau[j] = tj;
+    }
+    __syncthreads();
+    if (tid == 0) Ah[r0 * ldn + j] = v0;  // reflector kept in place for step 4
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = Ah[(n - 2) * ldn + n - 2];
+      e[n - 2] = Ah[(n - 1) * ldn + n - 2];
+    }
+    d[n - 1] = Ah[(n - 1) * ldn + n - 1];
+    e[n - 1] = 0.f;
+  }
+  __syncthreads();
+
+  // 2. bisection: thread i finds the i-th smallest eigenvalue
+  float tnorm = 0.f, glo = 3.0e38f, ghi = -3.0e38f;
+  for (int k = 0; k < n; ++k) {
+    const float off = (k > 0 ? fabsf(e[k - 1]) : 0.f) + (k + 1 < n ? fabsf(e[k]) : 0.f);
+    glo = fminf(glo, d[k] - off);
+    ghi = fmaxf(ghi, d[k] + off);
+    tnorm = fmaxf(tnorm, fabsf(d[k]) + off);
+  }
+  const float pad = 1e-6f * tnorm + 1e-30f;
+  glo -= pad;
+  ghi += pad;
+  const float piv_min = 1e-30f + 1e-12f * tnorm;
+  if (tid < n) {
+    float lo = glo, hi = ghi;
+    for (int it = 0; it < 32; ++it) {
+      const float mid = 0.5f * (lo + hi);
+      int cnt = 0;
+      float q = d[0] - mid;
+      if (fabsf(q) < piv_min) q = -piv_min;
+      cnt += q < 0.f;
+      for (int k = 1; k < n; ++k) {
+        q = d[k] - mid - e[k - 1] * e[k - 1] / q;
+        if (fabsf(q) < piv_min) q = -piv_min;
+        cnt += q < 0.f;
+      }
+      if (cnt > tid) hi = mid; else lo = mid;
+    }
+    lam[tid] = 0.5f * (lo + hi);
+  }
+  __syncthreads();
+
+  // 3. eigenvectors of T by twisted factorisation (thread per eigenvector)
+  if (tid < n) {
+    const float mu = lam[tid];
+    float* Dp = fac;                      // [k * n + tid]
+    float* Dm = fac + (int64_t)n * n;
+    float q = d[0] - mu;
+    if (fabsf(q) < piv_min) q = piv_min;
+    Dp[tid] = q;
+    for (int k = 1; k < n; ++k) {
+      q = d[k] - mu - e[k - 1] * e[k - 1] / q;
+      if (fabsf(q) < piv_min) q = piv_min;
+      Dp[(int64_t)k * n + tid] = q;
+    }
+    q = d[n - 1] - mu;
+    if (fabsf(q) < piv_min) q = piv_min;
+    Dm[(int64_t)(n - 1) * n + tid] = q;
+    for (int k = n - 2; k >= 0; --k) {
+      q = d[k] - mu - e[k] * e[k] / q;
+      if (fabsf(q) < piv_min) q = piv_min;
+      Dm[(int64_t)k * n + tid] = q;
+    }
+    int rt = 0;
+    float best = 3.0e38f;
+    for (int k = 0; k < n; ++k) {
+      const float g = fabsf(Dp[(int64_t)k * n + tid] + Dm[(int64_t)k * n + tid] - (d[k] - mu));
+      if (g < best) { best = g; rt = k; }
+    }
+    float z = 1.f, nrm = 1.f;
+    Z[rt * ldn + tid] = 1.f;
+    for (int k = rt - 1; k >= 0; --k) {
+      z = -(e[k] / Dp[(int64_t)k * n + tid]) * z;
+      Z[k * ldn + tid] = z;
+      nrm = fmaf(z, z, nrm);
+    }
+    z = 1.f;
+    for (int k = rt + 1; k < n; ++k) {
+      z = -(e[k - 1] / Dm[(int64_t)k * n + tid]) * z;
+      Z[k * ldn + tid] = z;
+      nrm = fmaf(z, z, nrm);
+    }
+    const float inv = rsqrtf(nrm);
+    for (int k = 0; k < n; ++k) Z[k * ldn + tid] *= inv;
+  }
+  __syncthreads();
+  // Gram-Schmidt inside groups of close eigenvalues (warp 0; groups are rare)
+  if (warp == 0) {
+    const float ctol = 1e-4f * tnorm;
+    for (int i = 1; i < n; ++i) {
+      int j0 = i - 1;
+      if (lam[i] - lam[j0] > ctol) continue;
+      while (j0 > 0 && lam[i] - lam[j0 - 1] <= ctol) --j0;
+      for (int jj = j0; jj < i; ++jj) {
+        float dot = 0.f;
+        for (int k = lane; k < n; k += 32) dot = fmaf(Z[k * ldn + jj], Z[k * ldn + i], dot);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        for (int k = lane; k < n; k += 32) Z[k * ldn + i] -= dot * Z[k * ldn + jj];
+        __syncwarp();
+      }
+      float nn = 0.f;
+      for (int k = lane; k < n; k += 32) nn = fmaf(Z[k * ldn + i], Z[k * ldn + i], nn);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
+      for (int k = lane; k < n; k += 32) Z[k * ldn + i] *= inv;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // 4. back-transformation X = H_0 ... H_{n-3} Z, thread per column
+  for (int c = tid; c < n; c += TE_T) {
+    for (int j = n - 3; j >= 0; --j) {
+      const float tj = tau[j];
+      if (tj == 0.f) continue;
+      float w = 0.f;
+      for (int r = j + 1; r < n; ++r) w = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w);
+      w *= tj;
+      for (int r = j + 1; r < n; ++r) Z[r * ldn + c] = fmaf(-w, Ah[r * ldn + j], Z[r * ldn + c]);
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < n; i += NW)
+    for (int j = lane; j < n; j += 32) X_out[(int64_t)i * n + j] = (double)Z[i * ldn + j];
+}
+
 // FP64 refinement (Ogita & Aishima), step 1 of 2, one CTA: Rayleigh quotients
 // lambda_i = S_ii / P_ii (= S_ii / (1 - R_ii) with R = I - P) and the cluster
 // threshold delta = 2 (||S - diag(lambda)||_F + ||A||_F ||R||_F) (norms in
@@ -503,7 +827,8 @@ __global__ void refine_e_kernel(const double* __restrict__ S, const double* __re
 __global__ void __launch_bounds__(1024) eig_finalize_kernel(const double* __restrict__ lam,
                                                             const double* __restrict__ X, int n,
                                                             double* __restrict__ evals,
-                                                            double* __restrict__ evecs) {
+                                                            double* __restrict__ evecs,
+                                                            int* __restrict__ flag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = warp; i < n; i += nw) {
     const double li = lam[i];
@@ -521,7 +846,10 @@ __global__ void __launch_bounds__(1024) eig_finalize_kernel(const double* __rest
       if (fabs(ob) > fabs(best) || (fabs(ob) == fabs(best) && ob > best)) best = ob;
     }
     const double sgn = best < 0.0 ? -1.0 : 1.0;
-    if (lane == 0) evals[rank] = li;
+    if (lane == 0) {
+      evals[rank] = li;
+      if (!isfinite(li)) *flag = 2;  // non-finite input or breakdown
+    }
     for (int r = lane; r < n; r += 32) evecs[(int64_t)r * n + rank] = sgn * X[(int64_t)r * n + i];
   }
 }
@@ -634,13 +962,14 @@ otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cuda
   double* G = ws.take<double>(m * m);
   double* Rinv = ws.take<double>(m * m);
   if (!G || !Rinv) return set_error(OTM_EINVAL, "orthonormalize: workspace too small");
-  const size_t smem = sizeof(float) * (2 * m * (m | 1) + m);
+  const size_t smem =
+      sizeof(float) * (2 * m * (m | 1) + ((m + CH_B - 1) / CH_B) * 64 + CH_B * m);
   OTM_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   // two shifted passes bring kappa(A) down to where plain Cholesky-QR2 is stable
   for (int pass = 0; pass < 4; ++pass) {
     OTM_TRY(gemm_tn_f64acc(A, A, rows, m, m, 1.0, G, 0, st));
-    chol_inv_kernel<<<1, 1024, smem, st>>>(G, (int)m, pass < 2 ? 11.0 : 0.0, Rinv, dflag);
+    chol_inv_kernel<<<1, CH_T, smem, st>>>(G, (int)m, pass < 2 ? 11.0 : 0.0, Rinv, dflag);
     OTM_CHECK_LAUNCH();
     OTM_TRY(gemm_nn_small(A, rows, m, Rinv, m, A, nullptr, nullptr, 0.0, st));
   }
@@ -650,7 +979,7 @@ otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cuda
 size_t syev_workspace(int64_t n) {
   WorkspaceSize w;
   for (int i = 0; i < 7; ++i) w.add<double>(n * n);
-  w.add<double>(n).add<double>(1);
+  w.add<double>(n).add<double>(1).add<float>(2 * n * n);
   return w.bytes();
 }
 
@@ -673,15 +1002,16 @@ otm_status syev(const double* A_in, int64_t n, double* evals, double* evecs, Wor
   double* E = ws.take<double>(n * n);
   double* lam = ws.take<double>(n);
   double* delta = ws.take<double>(1);
-  if (!delta) return set_error(OTM_EINVAL, "syev: workspace too small");
+  float* fac = ws.take<float>(2 * n * n);
+  if (!fac) return set_error(OTM_EINVAL, "syev: workspace too small");
   const unsigned nb = (unsigned)((n * n + 255) / 256);
   symmetrize_kernel<<<nb, 256, 0, st>>>(A_in, n, A);
   OTM_CHECK_LAUNCH();
-  const int64_t ldn = n | 1, half = (n + (n & 1)) / 2;
-  const size_t smem = sizeof(float) * (2 * n * ldn + 2 * half) + sizeof(int) * 2 * half + 16;
-  OTM_CHECK_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel,
+  const int64_t ldn = n | 1;
+  const size_t smem = sizeof(float) * (2 * n * ldn + 5 * n);
+  OTM_CHECK_CUDA(cudaFuncSetAttribute(tridiag_eig_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  jacobi_f32_kernel<<<1, 1024, smem, st>>>(A, (int)n, 40, X, dflag);
+  tridiag_eig_kernel<<<1, TE_T, smem, st>>>(A, (int)n, X, fac);
   OTM_CHECK_LAUNCH();
   // FP64 refinement: quadratic convergence from the float32 eigenvectors
   const int iters = 4;
@@ -700,7 +1030,7 @@ otm_status syev(const double* A_in, int64_t n, double* evals, double* evecs, Wor
     X = Xn;
     Xn = t;
   }
-  eig_finalize_kernel<<<1, 1024, 0, st>>>(lam, X, (int)n, evals, evecs);
+  eig_finalize_kernel<<<1, 1024, 0, st>>>(lam, X, (int)n, evals, evecs, dflag);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }
