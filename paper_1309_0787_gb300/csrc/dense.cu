@@ -24,6 +24,24 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int TN_T = 64, TN_R = 32;
 
+// Each thread stages 8 elements of A and 8 of B per 32-row slab: thread t
+// covers slab rows rr = (t >> 4) + 16 q (q = 0, 1) and tile columns
+// cc = 4 (t & 15) .. +3.  Loads for the next slab are issued into registers
+// before the current slab is multiplied (software pipelining).
+__device__ __forceinline__ void tn_load(const float* __restrict__ X, int64_t ld, int64_t r0,
+                                        int64_t r_end, int64_t c0, int64_t cmax, int t,
+                                        float (&v)[2][4]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int64_t r = r0 + (t >> 4) + 16 * q;
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const int64_t c = c0 + 4 * (t & 15) + z;
+      v[q][z] = (r < r_end && c < cmax) ? __ldg(X + r * ld + c) : 0.f;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ A,
                                                       const float* __restrict__ B, int64_t rows,
                                                       int64_t m, int64_t p, double alpha,
@@ -31,7 +49,8 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
                                                       int64_t rows_per_split) {
   __shared__ float As[TN_R][TN_T];
   __shared__ float Bs[TN_R][TN_T];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * TN_T, j0 = (int64_t)blockIdx.y * TN_T;
   const int64_t r_begin = (int64_t)blockIdx.z * rows_per_split;
   const int64_t r_end = min(rows, r_begin + rows_per_split);
@@ -40,14 +59,22 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) accd[a][b] = 0.0;
+  float va[2][4], vb[2][4];
+  tn_load(A, m, r_begin, r_end, i0, m, t, va);
+  tn_load(B, p, r_begin, r_end, j0, p, t, vb);
   for (int64_t r0 = r_begin; r0 < r_end; r0 += TN_R) {
-    for (int idx = threadIdx.x; idx < TN_R * TN_T; idx += 256) {
-      const int rr = idx / TN_T, cc = idx % TN_T;
-      const int64_t r = r0 + rr;
-      As[rr][cc] = (r < r_end && i0 + cc < m) ? A[r * m + i0 + cc] : 0.f;
-      Bs[rr][cc] = (r < r_end && j0 + cc < p) ? B[r * p + j0 + cc] : 0.f;
-    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        As[ty + 16 * q][4 * tx + z] = va[q][z];
+        Bs[ty + 16 * q][4 * tx + z] = vb[q][z];
+      }
     __syncthreads();
+    if (r0 + TN_R < r_end) {  // prefetch the next slab while this one is multiplied
+      tn_load(A, m, r0 + TN_R, r_end, i0, m, t, va);
+      tn_load(B, p, r0 + TN_R, r_end, j0, p, t, vb);
+    }
     float acc[4][4] = {};
 #pragma unroll 8
     for (int rr = 0; rr < TN_R; ++rr) {
@@ -81,6 +108,8 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
 // out (rows x p) = A (rows x m) * C (m x p, FP64 staged as float32)
 //                  - r1_alpha * r1_u[r] * r1_v[c]   (optional rank-one term)
 // One block owns 32 whole rows (all p <= 256 columns), so A may alias out.
+// Staging loads of a K-chunk are all issued into registers before they are
+// stored to shared memory.
 // ---------------------------------------------------------------------------
 constexpr int NN_R = 32, NN_K = 32, NN_PMAX = 256;
 
@@ -98,15 +127,28 @@ __global__ void __launch_bounds__(256) gemm_nn_small_kernel(
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int j = 0; j < NN_PMAX / 32; ++j) acc[a][j] = 0.f;
-  const int pp = 32 * ncj;  // columns staged (p rounded up to the column groups)
   for (int64_t k0 = 0; k0 < m; k0 += NN_K) {
-    for (int rr = rg; rr < NN_R; rr += 8) {
-      const int64_t r = r0 + rr, k = k0 + cg;
-      As[rr][cg] = (r < rows && k < m) ? A[r * m + k] : 0.f;
+    float av[4], cv[4][NN_PMAX / 32];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t r = r0 + rg + 8 * q, k = k0 + cg;
+      av[q] = (r < rows && k < m) ? A[r * m + k] : 0.f;
     }
-    for (int kk = rg; kk < NN_K; kk += 8) {
-      const int64_t k = k0 + kk;
-      for (int c = cg; c < pp; c += 32) Cs[kk][c] = (k < m && c < p) ? (float)C[k * p + c] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t k = k0 + rg + 8 * q;
+#pragma unroll
+      for (int j = 0; j < NN_PMAX / 32; ++j) {
+        const int64_t c = cg + 32 * j;
+        cv[q][j] = (j < ncj && k < m && c < p) ? (float)__ldg(C + k * p + c) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      As[rg + 8 * q][cg] = av[q];
+#pragma unroll
+      for (int j = 0; j < NN_PMAX / 32; ++j)
+        if (j < ncj) Cs[rg + 8 * q][cg + 32 * j] = cv[q][j];
     }
     __syncthreads();
 #pragma unroll 4
@@ -186,27 +228,30 @@ __global__ void __launch_bounds__(64) dgemm_small_kernel(int ta, int tb, int64_t
                                                          const double* __restrict__ B,
                                                          int64_t ldb, double beta, double* C,
                                                          int64_t ldc) {
-  __shared__ double As[8][9];
-  __shared__ double Bs[8][9];
+  constexpr int KC = 32;
+  __shared__ double As[8][KC + 1];
+  __shared__ double Bs[KC][9];
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
   const int64_t i = (int64_t)blockIdx.y * 8 + ty, j = (int64_t)blockIdx.x * 8 + tx;
   double acc = 0.0;
-  for (int64_t k0 = 0; k0 < kk; k0 += 8) {
-    {
-      const int64_t k = k0 + tx;
-      double v = 0.0;
-      if (i < m && k < kk) v = ta ? A[k * lda + i] : A[i * lda + k];
-      As[ty][tx] = v;
+  for (int64_t k0 = 0; k0 < kk; k0 += KC) {
+    double av[KC / 8], bv[KC / 8];
+#pragma unroll
+    for (int q = 0; q < KC / 8; ++q) {
+      // A tile: row ii = blockIdx.y*8 + ty, k = k0 + tx + 8q ; B tile: k = k0 + ty + 8q, col jj
+      const int64_t ka = k0 + tx + 8 * q, ii = (int64_t)blockIdx.y * 8 + ty;
+      av[q] = (ii < m && ka < kk) ? (ta ? A[ka * lda + ii] : A[ii * lda + ka]) : 0.0;
+      const int64_t kb = k0 + ty + 8 * q, jj = (int64_t)blockIdx.x * 8 + tx;
+      bv[q] = (kb < kk && jj < n) ? (tb ? B[jj * ldb + kb] : B[kb * ldb + jj]) : 0.0;
     }
-    {
-      const int64_t k = k0 + ty;
-      double v = 0.0;
-      if (k < kk && j < n) v = tb ? B[j * ldb + k] : B[k * ldb + j];
-      Bs[ty][tx] = v;
+#pragma unroll
+    for (int q = 0; q < KC / 8; ++q) {
+      As[ty][tx + 8 * q] = av[q];
+      Bs[ty + 8 * q][tx] = bv[q];
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc = fma(As[ty][q], Bs[q][tx], acc);
+    for (int q = 0; q < KC; ++q) acc = fma(As[ty][q], Bs[q][tx], acc);
     __syncthreads();
   }
   if (i < m && j < n) C[i * ldc + j] = alpha * acc + (beta != 0.0 ? beta * C[i * ldc + j] : 0.0);
@@ -715,28 +760,63 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
     for (int k = 0; k < n; ++k) Z[k * ldn + tid] *= inv;
   }
   __syncthreads();
-  // Gram-Schmidt inside groups of close eigenvalues (warp 0; groups are rare)
+  // Gram-Schmidt inside groups of close eigenvalues (warp 0; groups are rare).
+  // A repeated eigenvalue makes the twisted factorisation return the same
+  // vector for every member; when Gram-Schmidt leaves less than half of a
+  // vector, it is regenerated by two inverse-iteration solves with the stored
+  // LDL^T factors of T - lambda I from a fixed pseudo-random start, and
+  // orthogonalised again.
   if (warp == 0) {
     const float ctol = 1e-4f * tnorm;
     for (int i = 1; i < n; ++i) {
       int j0 = i - 1;
       if (lam[i] - lam[j0] > ctol) continue;
       while (j0 > 0 && lam[i] - lam[j0 - 1] <= ctol) --j0;
-      for (int jj = j0; jj < i; ++jj) {
-        float dot = 0.f;
-        for (int k = lane; k < n; k += 32) dot = fmaf(Z[k * ldn + jj], Z[k * ldn + i], dot);
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        for (int jj = j0; jj < i; ++jj) {
+          float dot = 0.f;
+          for (int k = lane; k < n; k += 32) dot = fmaf(Z[k * ldn + jj], Z[k * ldn + i], dot);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        for (int k = lane; k < n; k += 32) Z[k * ldn + i] -= dot * Z[k * ldn + jj];
+          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          for (int k = lane; k < n; k += 32) Z[k * ldn + i] -= dot * Z[k * ldn + jj];
+          __syncwarp();
+        }
+        float nn = 0.f;
+        for (int k = lane; k < n; k += 32) nn = fmaf(Z[k * ldn + i], Z[k * ldn + i], nn);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        if (nn > 0.25f || attempt == 1) {
+          const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
+          for (int k = lane; k < n; k += 32) Z[k * ldn + i] *= inv;
+          __syncwarp();
+          break;
+        }
+        // regenerate: x = (L D L^T)^{-2} r, L D L^T = T - lambda_i I (forward factors of column i)
+        if (lane == 0) {
+          const float* Dp = fac;
+          for (int k = 0; k < n; ++k)
+            Z[k * ldn + i] = sinf(12.9898f * (float)(k + 1) + 78.233f * (float)(i + 1));
+          for (int rep = 0; rep < 2; ++rep) {
+            float y = Z[i];  // row 0
+            for (int k = 1; k < n; ++k) {
+              const float lk = e[k - 1] / Dp[(int64_t)(k - 1) * n + i];
+              y = Z[k * ldn + i] - lk * y;
+              Z[k * ldn + i] = y;
+            }
+            for (int k = 0; k < n; ++k) Z[k * ldn + i] /= Dp[(int64_t)k * n + i];
+            float x = Z[(n - 1) * ldn + i], sq = x * x;
+            for (int k = n - 2; k >= 0; --k) {
+              const float lk = e[k] / Dp[(int64_t)k * n + i];
+              x = Z[k * ldn + i] - lk * x;
+              Z[k * ldn + i] = x;
+              sq = fmaf(x, x, sq);
+            }
+            const float inv = sq > 0.f ? rsqrtf(sq) : 0.f;
+            for (int k = 0; k < n; ++k) Z[k * ldn + i] *= inv;
+          }
+        }
         __syncwarp();
       }
-      float nn = 0.f;
-      for (int k = lane; k < n; k += 32) nn = fmaf(Z[k * ldn + i], Z[k * ldn + i], nn);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-      const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
-      for (int k = lane; k < n; k += 32) Z[k * ldn + i] *= inv;
-      __syncwarp();
     }
   }
   __syncthreads();
