@@ -241,6 +241,45 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
                        int64_t snapshot_every, float* V_snap, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Precision form of the STGD (not in the paper: BF16 / FP8 tensor cores)     */
+/* ------------------------------------------------------------------------ */
+
+#define OTM_PREC_BF16 1
+#define OTM_PREC_FP8 2 /* e4m3 */
+
+/*
+ * otm_quantize_samples -- store whitened samples for the low-precision STGD.
+ * Y: n x k float32 (row-major), 1 <= k <= 128.  Yq: n x ldq elements with
+ * ldq = k rounded up to a multiple of 16, zero padded; BF16 (2 bytes each) or
+ * FP8 e4m3 (1 byte each) per `precision`.  FP8 rows are scaled by one factor
+ * per sample, scales[t] = max_r |Y[t][r]| / 448 (1 for an all-zero row), so
+ * Y[t] ~ scales[t] * Yq[t]; BF16 writes scales[t] = 1 when scales != NULL.
+ */
+otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precision, void* Yq,
+                                float* scales, void* stream);
+
+/*
+ * otm_sgd_run_lp -- otm_sgd_run (the Lemma 3 update, same schedule and
+ * arguments) with the two sample products on the tensor cores: A = Y V in
+ * BF16 or FP8 from samples stored by otm_quantize_samples (YA, YB, YC with
+ * their per-sample scales sA, sB, sC, NULL = 1; equal pointers select the
+ * symmetric path), V re-quantised every step with one scale per component,
+ * B = c1 A_A o A_B - c2 (...) quantised with one scale per component per 128
+ * samples, FP32 accumulation in tensor memory; V, the Gram term, the mean
+ * terms and the update stay FP32.  ybar3 are the FP64 means of the unquantised
+ * samples.  1 <= k <= 128 (three distinct views: k <= 112 in BF16).
+ * Scratch: otm_sgd_run_lp_workspace() bytes.  Synchronises the stream;
+ * returns OTM_ETIMEOUT if a bounded wait on the tensor cores expired.
+ */
+size_t otm_sgd_run_lp_workspace(void);
+otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* YC,
+                          const float* sA, const float* sB, const float* sC, int64_t n, int64_t k,
+                          const double* ybar3, const int32_t* perm, int64_t epochs, int64_t b,
+                          double beta0, double theta, double alpha0, int precision,
+                          int64_t snapshot_every, float* V_snap, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Post-processing (Section 3.3, Lemma 4) and error evaluation               */
 /* ------------------------------------------------------------------------ */
 

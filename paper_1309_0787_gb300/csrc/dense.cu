@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
                                                       const float* __restrict__ B, int64_t rows,
                                                       int64_t m, int64_t p, double alpha,
                                                       double* __restrict__ C,
-                                                      int64_t rows_per_split) {
+                                                      int64_t rows_per_split,
+                                                      const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ float As[TN_R][TN_T];
   __shared__ float Bs[TN_R][TN_T];
   const int t = threadIdx.x;
@@ -115,7 +117,9 @@ constexpr int NN_R = 32, NN_K = 32, NN_PMAX = 256;
 
 __global__ void __launch_bounds__(256) gemm_nn_small_kernel(
     const float* A, int64_t rows, int64_t m, const double* __restrict__ C, int64_t p, float* out,
-    const double* __restrict__ r1_u, const double* __restrict__ r1_v, double r1_alpha) {
+    const double* __restrict__ r1_u, const double* __restrict__ r1_v, double r1_alpha,
+    const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ float As[NN_R][NN_K + 1];
   __shared__ float Cs[NN_K][NN_PMAX];
   const int cg = threadIdx.x & 31;   // column group: columns cg + 32 j
@@ -292,8 +296,30 @@ constexpr int CH_T = 256, CH_B = 8;
 __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict__ G, int n,
                                                         double shift_scale,
                                                         double* __restrict__ Rinv,
-                                                        int* __restrict__ flag) {
+                                                        int* __restrict__ flag, int* skip,
+                                                        float check_tol) {
   extern __shared__ float sm[];
+  // conditional pass: nothing to do once the columns are orthonormal to check_tol
+  if (skip && *skip) return;
+  if (check_tol > 0.f) {
+    __shared__ float s_dev[CH_T / 32];
+    float dev = 0.f;
+    for (int idx = threadIdx.x; idx < n * n; idx += CH_T) {
+      const int i = idx / n, j = idx % n;
+      dev = fmaxf(dev, fabsf((float)G[idx] - (i == j ? 1.f : 0.f)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if ((threadIdx.x & 31) == 0) s_dev[threadIdx.x >> 5] = dev;
+    __syncthreads();
+    float mx = 0.f;
+#pragma unroll
+    for (int w = 0; w < CH_T / 32; ++w) mx = fmaxf(mx, s_dev[w]);
+    if (mx <= check_tol) {
+      if (threadIdx.x == 0) *skip = 1;
+      return;
+    }
+  }
   const int ldn = n | 1;       // odd row stride: column walks are bank-conflict free
   const int nblk = (n + CH_B - 1) / CH_B;
   float* L = sm;                         // n x ldn (lower triangle)
@@ -970,7 +996,8 @@ int num_sms() {
 }  // namespace
 
 otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t m, int64_t p,
-                          double alpha, double* C, int accumulate, cudaStream_t st) {
+                          double alpha, double* C, int accumulate, cudaStream_t st,
+                          const int* skip) {
   if (!accumulate) OTM_CHECK_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * m * p, st));
   if (rows == 0 || m == 0 || p == 0) return OTM_OK;
   // about two blocks per SM, but at least 256 rows per block: every block adds
@@ -984,18 +1011,18 @@ otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t 
   splits = (rows + rps - 1) / rps;
   dim3 grid((unsigned)((m + TN_T - 1) / TN_T), (unsigned)((p + TN_T - 1) / TN_T),
             (unsigned)splits);
-  gemm_tn_kernel<<<grid, 256, 0, st>>>(A, B, rows, m, p, alpha, C, rps);
+  gemm_tn_kernel<<<grid, 256, 0, st>>>(A, B, rows, m, p, alpha, C, rps, skip);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }
 
 otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
                          float* out, const double* r1_u, const double* r1_v, double r1_alpha,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int* skip) {
   if (p > NN_PMAX) return set_error(OTM_EINVAL, "gemm_nn_small: p=%lld > %d", (long long)p, NN_PMAX);
   if (rows == 0 || p == 0) return OTM_OK;
   gemm_nn_small_kernel<<<(unsigned)((rows + NN_R - 1) / NN_R), 256, 0, st>>>(
-      A, rows, m, C, p, out, r1_u, r1_v, r1_alpha);
+      A, rows, m, C, p, out, r1_u, r1_v, r1_alpha, skip);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }
@@ -1031,7 +1058,7 @@ otm_status vec_tn(const double* u, const float* A, int64_t rows, int64_t m, doub
 
 size_t orth_workspace(int64_t m) {
   WorkspaceSize w;
-  w.add<double>(m * m).add<double>(m * m);
+  w.add<double>(m * m).add<double>(m * m).add<int>(1);
   return w.bytes();
 }
 
@@ -1041,17 +1068,23 @@ otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cuda
   if (rows < m) return set_error(OTM_EINVAL, "orthonormalize: rows < m");
   double* G = ws.take<double>(m * m);
   double* Rinv = ws.take<double>(m * m);
-  if (!G || !Rinv) return set_error(OTM_EINVAL, "orthonormalize: workspace too small");
+  int* skip = ws.take<int>(1);
+  if (!G || !Rinv || !skip) return set_error(OTM_EINVAL, "orthonormalize: workspace too small");
   const size_t smem =
       sizeof(float) * (2 * m * (m | 1) + ((m + CH_B - 1) / CH_B) * 64 + CH_B * m);
   OTM_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-  // two shifted passes bring kappa(A) down to where plain Cholesky-QR2 is stable
+  OTM_CHECK_CUDA(cudaMemsetAsync(skip, 0, sizeof(int), st));
+  // pass 0: shifted (ill-conditioned input); pass 1: plain Cholesky-QR; passes
+  // 2-3 run only while the columns are not yet orthonormal to 1e-5 (the test
+  // and the skip happen on the device, without a host round trip)
   for (int pass = 0; pass < 4; ++pass) {
-    OTM_TRY(gemm_tn_f64acc(A, A, rows, m, m, 1.0, G, 0, st));
-    chol_inv_kernel<<<1, CH_T, smem, st>>>(G, (int)m, pass < 2 ? 11.0 : 0.0, Rinv, dflag);
+    const int* sk = pass >= 2 ? skip : nullptr;
+    OTM_TRY(gemm_tn_f64acc(A, A, rows, m, m, 1.0, G, 0, st, sk));
+    chol_inv_kernel<<<1, CH_T, smem, st>>>(G, (int)m, pass == 0 ? 11.0 : 0.0, Rinv, dflag,
+                                           pass >= 2 ? skip : nullptr, pass >= 2 ? 1e-5f : 0.f);
     OTM_CHECK_LAUNCH();
-    OTM_TRY(gemm_nn_small(A, rows, m, Rinv, m, A, nullptr, nullptr, 0.0, st));
+    OTM_TRY(gemm_nn_small(A, rows, m, Rinv, m, A, nullptr, nullptr, 0.0, st, sk));
   }
   return OTM_OK;
 }
@@ -1094,7 +1127,7 @@ otm_status syev(const double* A_in, int64_t n, double* evals, double* evecs, Wor
   tridiag_eig_kernel<<<1, TE_T, smem, st>>>(A, (int)n, X, fac);
   OTM_CHECK_LAUNCH();
   // FP64 refinement: quadratic convergence from the float32 eigenvectors
-  const int iters = 4;
+  const int iters = 6;
   for (int it = 0; it < iters; ++it) {
     OTM_TRY(dgemm_small(0, 0, n, n, n, 1.0, A, n, X, n, 0.0, AX, n, st));
     OTM_TRY(dgemm_small(1, 0, n, n, n, 1.0, X, n, AX, n, 0.0, S, n, st));

@@ -87,12 +87,13 @@ otm_status column_sums_scaled(const otm_csr* X, double scale, double* out, cudaS
 // C (m x p, FP64) = alpha * A^T B, A: rows x m, B: rows x p, float32 row-major.
 // If accumulate == 0 C is overwritten, else added to.
 otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t m, int64_t p,
-                          double alpha, double* C, int accumulate, cudaStream_t st);
+                          double alpha, double* C, int accumulate, cudaStream_t st,
+                          const int* skip = nullptr);
 // out (rows x p, float32) = A (rows x m, float32) * C (m x p, FP64, rounded to FP32)
 //   [+ rank-one term: - r1_alpha * r1_u[r] * r1_v[c]] [then * colscale[c]]
 otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
                          float* out, const double* r1_u, const double* r1_v, double r1_alpha,
-                         cudaStream_t st);
+                         cudaStream_t st, const int* skip = nullptr);
 // out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64), FP64 accumulation.
 otm_status gemm_nn_f64(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
                        double* out, cudaStream_t st);

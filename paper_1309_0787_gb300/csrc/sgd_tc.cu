@@ -1,0 +1,755 @@
+// Precision form of the fused STGD step (Section 3.2, Lemma 3) on the
+// fifth-generation tensor cores.  The two products of the stacked update,
+//   A = Y_b V        (samples x components, K = coordinates; views A and B)
+//   G = Y_C^T B      (coordinates x components, K = samples)
+// run as tcgen05.mma in BF16 (kind::f16) or FP8 e4m3 (kind::f8f6f4) with
+// FP32 accumulators in tensor memory; B = c1 A_A o A_B - c2 (a_B o A_A +
+// a_A o A_B) is formed in registers between them.  The FP32 master V, the
+// Gram term V((V^T V) o (V^T V)), the mean terms and the update stay in FP32
+// as in the FP32 kernel (sgd.cu), and so does the organisation: one
+// thread-block cluster runs all steps, the minibatch is split over its CTAs,
+// partial G are summed column-wise through distributed shared memory, and V
+// never leaves the chip.
+//
+// Scaling: samples are stored quantised with one scale per sample (FP8; BF16
+// stores scale 1); V is re-quantised every step with one scale per component;
+// B with one scale per component per 128-sample tile.  Every scale is applied
+// to the FP32 accumulator in the epilogues:
+//   A[t][i] = s_t sigma_i D1[t][i],   G[r][i] = sum over tiles of beta_i D2[r][i].
+//
+// Operand layouts in shared memory (no swizzle; 8-row x 16-byte core
+// matrices; LBO = stride between cores along K, SBO = along M/N):
+//   sample tile: core (tg, rg) = 8 samples x 16 B of coordinates at
+//                (tg * CR + rg) * 128 with CR = KP * esize / 16; read K-major
+//                (M = samples, K = coordinates) by the first product and
+//                MN-major (M = coordinates, K = samples) by the second;
+//   V image:     core (ng, rg) = 8 components x 16 B of coordinates, K-major;
+//   B image:     core (tg, ng) = 8 samples x 16 B of components, MN-major.
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "otm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace otm {
+namespace {
+
+constexpr int TILE = 128;        // samples per MMA tile (M of the first product)
+constexpr int KP = 128;          // padded coordinates (M of the second product)
+constexpr int TC_THREADS = 256;  // 8 warps: 2 warps per 32-lane TMEM quarter
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int TC_KMAX = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t sdesc(const void* base, uint32_t lbo, uint32_t sbo) {
+  const uint32_t a = smem_u32(base);
+  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t amaj, uint32_t bmaj,
+                                                  uint32_t M, uint32_t N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (amaj << 15) | (bmaj << 16) | ((N >> 3) << 17) |
+         ((M >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t acc) {
+  if constexpr (FP8) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(mbar)));
+}
+
+// Bounded wait on an mbarrier phase (about a second); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < (1u << 24) && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(phase));
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+
+// Quantise 16 FP32 values into one 16-byte core row (8 bf16 = 16 B covers only
+// 8 values, so BF16 writes two rows; see the callers).
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d) {
+  const __nv_fp8x4_e4m3 q(make_float4(a, b, c, d));
+  return *reinterpret_cast<const uint32_t*>(&q);
+}
+
+struct TcArgs {
+  const uint8_t* YA;  // quantised samples, row stride ldq elements
+  const uint8_t* YB;
+  const uint8_t* YC;
+  const float* sA;    // per-sample scales (null = 1)
+  const float* sB;
+  const float* sC;
+  const int32_t* perm;
+  const double* ybar3;
+  float* V;
+  float* V_snap;
+  int* err;
+  int64_t n, b, spe, total_steps, snapshot_every;
+  int k, ldq;
+  double beta0;
+  float c1, c2, c3, kappa;
+};
+
+struct TcLayout {
+  int np, ldk, cpq, nview, esize, cr, cb;
+  size_t y_bytes, b_bytes, v_bytes;
+  size_t off_b, off_v, off_f;
+  // float offsets inside the FP32 region
+  size_t vm, gd, hm, vn, aA, aB, ybA, ybB, ybC, vsc, bsc, spw, spart, sown, sAt, sBt, sCt,
+      amax, nfloat;
+  size_t total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int k, int CL, bool sym, int esize) {
+  TcLayout L;
+  L.np = (k + 15) & ~15;
+  L.ldk = (k + 3) & ~3;
+  L.cpq = (k + CL - 1) / CL;
+  L.nview = sym ? 1 : 3;
+  L.esize = esize;
+  L.cr = KP * esize / 16;
+  L.cb = L.np * esize / 16;
+  L.y_bytes = (size_t)TILE * KP * esize;
+  L.b_bytes = (size_t)TILE * L.np * esize;
+  L.v_bytes = (size_t)L.np * KP * esize;
+  L.off_b = L.y_bytes * L.nview;
+  size_t region = L.off_b + L.b_bytes;
+  const size_t gp = (size_t)L.np * KP * 4;  // partial G (FP32) reuses the sample images
+  if (region < gp) region = gp;
+  L.off_v = (region + 1023) & ~(size_t)1023;
+  L.off_f = (L.off_v + L.v_bytes + 1023) & ~(size_t)1023;
+  size_t f = 0;
+  L.vm = f; f += (size_t)k * L.ldk;
+  L.gd = f; f += (size_t)L.cpq * L.ldk;
+  L.hm = f; f += (size_t)L.cpq * L.ldk;
+  L.vn = f; f += (size_t)L.cpq * L.ldk;
+  L.aA = f; f += L.np;
+  L.aB = f; f += L.np;
+  L.ybA = f; f += L.ldk;
+  L.ybB = f; f += L.ldk;
+  L.ybC = f; f += L.ldk;
+  L.vsc = f; f += L.np;
+  L.bsc = f; f += L.np;
+  L.spw = f; f += 4 * (size_t)L.np;
+  L.spart = f; f += L.np;
+  L.sown = f; f += L.cpq + 4;
+  L.sAt = f; f += TILE;
+  L.sBt = f; f += TILE;
+  L.sCt = f; f += TILE;
+  L.amax = f; f += L.np;
+  L.nfloat = f;
+  L.total = L.off_f + f * 4 + 64;
+  return L;
+}
+
+template <bool FP8, bool SYM, int CL>
+__global__ void __launch_bounds__(TC_THREADS, 1) sgd_tc_kernel(TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  constexpr int ES = FP8 ? 1 : 2;
+  constexpr int KSTEP = FP8 ? 32 : 16;            // K of one MMA
+  constexpr uint32_t FMT = FP8 ? 0u : 1u;         // E4M3 / BF16
+  constexpr float QMAX = FP8 ? 448.f : 1.f;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quad = warp & 3, half = warp >> 2;
+  const int k = a.k;
+  const TcLayout L = tc_layout(k, CL, SYM, ES);
+  const int np = L.np, ldk = L.ldk, cpq = L.cpq, CR = L.cr, CB = L.cb;
+  uint8_t* Yimg = smem;                        // nview x y_bytes
+  uint8_t* Bimg = smem + L.off_b;
+  uint8_t* Vimg = smem + L.off_v;
+  float* Gp = reinterpret_cast<float*>(smem);  // np x KP, after the last product
+  float* F = reinterpret_cast<float*>(smem + L.off_f);
+  float* Vm = F + L.vm;
+  float* gd = F + L.gd;
+  float* Hm = F + L.hm;
+  float* vn = F + L.vn;
+  float* aA = F + L.aA;
+  float* aB = F + L.aB;
+  float* ybA = F + L.ybA;
+  float* ybB = F + L.ybB;
+  float* ybC = F + L.ybC;
+  float* vsc = F + L.vsc;
+  float* bsc = F + L.bsc;
+  float* spw = F + L.spw;
+  float* spart = F + L.spart;
+  float* sown = F + L.sown;
+  float* sAt = F + L.sAt;
+  float* sBt = F + L.sBt;
+  float* sCt = F + L.sCt;
+  unsigned* amax = reinterpret_cast<unsigned*>(F + L.amax);
+
+  // ---- set-up: TMEM, mbarrier, V master, means ----
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_abort = 0;
+  }
+  for (int idx = tid; idx < k * ldk; idx += TC_THREADS) {
+    const int i = idx / ldk, r = idx % ldk;
+    Vm[idx] = r < k ? a.V[(int64_t)i * k + r] : 0.f;
+  }
+  for (int r = tid; r < ldk; r += TC_THREADS) {
+    ybA[r] = r < k ? (float)a.ybar3[r] : 0.f;
+    ybB[r] = r < k ? (float)a.ybar3[k + r] : 0.f;
+    ybC[r] = r < k ? (float)a.ybar3[2 * k + r] : 0.f;
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+  const uint32_t colA = 0, colB = SYM ? 0 : 128, colG = 256;
+  const int own_lo = q * cpq, own_hi = min(k, own_lo + cpq);
+  const int64_t bq = (a.b + CL - 1) / CL;
+  const int nchunk = np / 16;
+  uint32_t phase = 0;
+
+  for (int64_t s = 0; s < a.total_steps; ++s) {
+    const int64_t e = s / a.spe, jb = s % a.spe;
+    const int64_t pos0 = jb * a.b;
+    const int64_t beff = min(a.b, a.n - pos0);
+    const float beta = (float)(a.beta0 / sqrt((double)(s + 1)));
+    const float inv_b = 1.f / (float)beff;
+
+    // -- per-step: a_A, a_B, V scales, V image --
+    for (int i = warp; i < np; i += TC_THREADS / 32) {
+      float x = 0.f, y = 0.f, m = 0.f;
+      if (i < k)
+        for (int r = lane; r < k; r += 32) {
+          const float v = Vm[i * ldk + r];
+          x = fmaf(v, ybA[r], x);
+          y = fmaf(v, ybB[r], y);
+          m = fmaxf(m, fabsf(v));
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      }
+      if (lane == 0) {
+        aA[i] = x;
+        aB[i] = y;
+        vsc[i] = FP8 ? (m > 0.f ? m / QMAX : 1.f) : 1.f;
+        spart[i] = 0.f;
+      }
+      if (lane < 4) spw[lane * np + i] = 0.f;
+    }
+    __syncthreads();
+    // V image: 16-byte core rows of (component i, coordinate group rg)
+    for (int idx = tid; idx < np * CR; idx += TC_THREADS) {
+      const int i = idx / CR, rg = idx % CR;
+      const int r0 = rg * (16 / ES);
+      const float inv = 1.f / vsc[i];
+      float v[16];
+#pragma unroll
+      for (int z = 0; z < 16 / ES; ++z) {
+        const int r = r0 + z;
+        v[z] = (i < k && r < k) ? Vm[i * ldk + r] * inv : 0.f;
+      }
+      uint4 w;
+      if constexpr (FP8) {
+        w.x = pack_e4m3(v[0], v[1], v[2], v[3]);
+        w.y = pack_e4m3(v[4], v[5], v[6], v[7]);
+        w.z = pack_e4m3(v[8], v[9], v[10], v[11]);
+        w.w = pack_e4m3(v[12], v[13], v[14], v[15]);
+      } else {
+        w.x = pack_bf16(v[0], v[1]);
+        w.y = pack_bf16(v[2], v[3]);
+        w.z = pack_bf16(v[4], v[5]);
+        w.w = pack_bf16(v[6], v[7]);
+      }
+      *reinterpret_cast<uint4*>(Vimg + ((size_t)((i >> 3) * CR + rg) << 7) + ((i & 7) << 4)) = w;
+    }
+
+    // per-thread accumulators of the second product (this thread's TMEM lane,
+    // chunks c = half, half + 2, ...)
+    float gacc[4][16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) gacc[c][j] = 0.f;
+
+    const int64_t my_lo = (int64_t)q * bq, my_hi = min(beff, my_lo + bq);
+    for (int64_t t0 = my_lo; t0 < my_hi; t0 += TILE) {
+      // -- sample tile(s) into the operand images --
+      for (int idx = tid; idx < TILE * CR; idx += TC_THREADS) {
+        const int t = idx / CR, rg = idx % CR;
+        const int64_t p = t0 + t;
+        int64_t row = p < my_hi ? (a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p) : -1;
+        if (row >= a.n) row = -1;
+        const int c0 = rg * (16 / ES);
+        const size_t off = ((size_t)((t >> 3) * CR + rg) << 7) + ((t & 7) << 4);
+        const bool in = row >= 0 && c0 < a.ldq;
+        const size_t goff = (size_t)row * a.ldq * ES + (size_t)c0 * ES;
+        const uint4 z4 = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(Yimg + off) =
+            in ? *reinterpret_cast<const uint4*>(a.YA + goff) : z4;
+        if (!SYM) {
+          *reinterpret_cast<uint4*>(Yimg + L.y_bytes + off) =
+              in ? *reinterpret_cast<const uint4*>(a.YB + goff) : z4;
+          *reinterpret_cast<uint4*>(Yimg + 2 * L.y_bytes + off) =
+              in ? *reinterpret_cast<const uint4*>(a.YC + goff) : z4;
+        }
+        if (rg == 0) {
+          sAt[t] = row >= 0 ? (a.sA ? a.sA[row] : 1.f) : 0.f;
+          sBt[t] = row >= 0 ? (a.sB ? a.sB[row] : 1.f) : 0.f;
+          sCt[t] = row >= 0 ? (a.sC ? a.sC[row] : 1.f) : 0.f;
+        }
+        if (FP8 && idx < np) amax[idx] = 0u;
+      }
+      fence_async_smem();
+      tc_before();
+      __syncthreads();
+      tc_after();
+      // -- first product: D1 = Y_tile V^T (K-major operands) --
+      if (tid == 0 && !s_abort) {
+        const uint32_t id1 = make_idesc(FMT, 0, 0, TILE, (uint32_t)np);
+        for (int v = 0; v < (SYM ? 1 : 2); ++v) {
+          const uint8_t* Y = Yimg + v * L.y_bytes;
+          const uint32_t col = v == 0 ? colA : colB;
+          for (int ks = 0; ks < KP / KSTEP; ++ks) {
+            const uint64_t da = sdesc(Y + ks * 256, 128, (uint32_t)CR * 128);
+            const uint64_t db = sdesc(Vimg + ks * 256, 128, (uint32_t)CR * 128);
+            mma<FP8>(tmem + col, da, db, id1, ks > 0 ? 1u : 0u);
+          }
+        }
+        mma_commit(&mbar);
+      }
+      if (!mbar_wait(&mbar, phase) && lane == 0) {
+        s_abort = 1;
+        atomicExch(a.err, 1);
+      }
+      phase ^= 1u;
+      tc_after();
+      // -- epilogue 1: B = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B), per-column s --
+      {
+        const int t = 32 * quad + lane;
+        const float sa = sAt[t], sb = sBt[t], sc = sCt[t];
+        float bv[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int ch = half + 2 * c;
+          if (ch < nchunk) {
+            float xa[16], xb[16];
+            tmem_ld16(tmem + lane_base + colA + 16 * ch, xa);
+            if (!SYM) tmem_ld16(tmem + lane_base + colB + 16 * ch, xb);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = 16 * ch + j;
+              const float va = xa[j] * sa * vsc[i];
+              const float vb = SYM ? va : xb[j] * sb * vsc[i];
+              const float pr = va * vb;
+              bv[c][j] = sc * (a.c1 * pr - a.c2 * (aB[i] * va + aA[i] * vb));
+              float ps = pr;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
+              if (lane == 0) spw[quad * np + i] += ps;
+              if (FP8) {
+                float m = fabsf(bv[c][j]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) atomicMax(&amax[i], __float_as_uint(m));
+              }
+            }
+          }
+        }
+        if (FP8) {
+          __syncthreads();
+          if (tid < np) bsc[tid] = amax[tid] > 0u ? __uint_as_float(amax[tid]) / QMAX : 1.f;
+          __syncthreads();
+        }
+        // B image (MN-major: core (tg, ng) = 8 samples x 16 B of components)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int ch = half + 2 * c;
+          if (ch < nchunk) {
+            float w[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) w[j] = FP8 ? bv[c][j] / bsc[16 * ch + j] : bv[c][j];
+            if constexpr (FP8) {
+              uint4 u;
+              u.x = pack_e4m3(w[0], w[1], w[2], w[3]);
+              u.y = pack_e4m3(w[4], w[5], w[6], w[7]);
+              u.z = pack_e4m3(w[8], w[9], w[10], w[11]);
+              u.w = pack_e4m3(w[12], w[13], w[14], w[15]);
+              *reinterpret_cast<uint4*>(Bimg + ((size_t)((t >> 3) * CB + ch) << 7) +
+                                        ((t & 7) << 4)) = u;
+            } else {
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                uint4 u;
+                u.x = pack_bf16(w[8 * hh + 0], w[8 * hh + 1]);
+                u.y = pack_bf16(w[8 * hh + 2], w[8 * hh + 3]);
+                u.z = pack_bf16(w[8 * hh + 4], w[8 * hh + 5]);
+                u.w = pack_bf16(w[8 * hh + 6], w[8 * hh + 7]);
+                *reinterpret_cast<uint4*>(Bimg + ((size_t)((t >> 3) * CB + 2 * ch + hh) << 7) +
+                                          ((t & 7) << 4)) = u;
+              }
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      tc_before();
+      __syncthreads();
+      tc_after();
+      // -- second product: D2 = Y_C^T B (MN-major operands) --
+      if (tid == 0 && !s_abort) {
+        const uint32_t id2 = make_idesc(FMT, 1, 1, KP, (uint32_t)np);
+        const uint8_t* YC = Yimg + (SYM ? 0 : 2 * L.y_bytes);
+        for (int ks = 0; ks < TILE / KSTEP; ++ks) {
+          const uint64_t da =
+              sdesc(YC + (size_t)ks * (KSTEP / 8) * CR * 128, (uint32_t)CR * 128, 128);
+          const uint64_t db =
+              sdesc(Bimg + (size_t)ks * (KSTEP / 8) * CB * 128, (uint32_t)CB * 128, 128);
+          mma<FP8>(tmem + colG, da, db, id2, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(&mbar);
+      }
+      if (!mbar_wait(&mbar, phase) && lane == 0) {
+        s_abort = 1;
+        atomicExch(a.err, 1);
+      }
+      phase ^= 1u;
+      tc_after();
+      // -- epilogue 2: accumulate beta_i D2[r][i] for this thread's coordinate r --
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ch = half + 2 * c;
+        if (ch < nchunk) {
+          float x[16];
+          tmem_ld16(tmem + lane_base + colG + 16 * ch, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) gacc[c][j] = fmaf(x[j], FP8 ? bsc[16 * ch + j] : 1.f, gacc[c][j]);
+        }
+      }
+      tc_before();
+      __syncthreads();  // operand images free for the next tile
+      tc_after();
+    }
+    // partial G to shared memory, column i contiguous: Gp[i * KP + r]
+    {
+      const int r = 32 * quad + lane;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ch = half + 2 * c;
+        if (ch < nchunk) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) Gp[(16 * ch + j) * KP + r] = gacc[c][j];
+        }
+      }
+      for (int i = tid; i < np; i += TC_THREADS)
+        spart[i] = spw[i] + spw[np + i] + spw[2 * np + i] + spw[3 * np + i];
+    }
+    cluster.sync();  // partial products of every CTA visible
+
+    // -- owned columns: cluster sums, Gram term, update (FP32) --
+    const int nown = own_hi - own_lo;
+    if (tid < nown) {
+      float part[CL];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) part[c] = cluster.map_shared_rank(spart, c)[own_lo + tid];
+      float ss = 0.f;
+#pragma unroll
+      for (int c = 0; c < CL; ++c) ss += part[c];
+      sown[tid] = ss;
+    }
+    for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
+      const int jj = idx / k, r = idx % k;
+      float part[CL];
+#pragma unroll
+      for (int c = 0; c < CL; ++c) part[c] = cluster.map_shared_rank(Gp, c)[(own_lo + jj) * KP + r];
+      float g = 0.f;
+#pragma unroll
+      for (int c = 0; c < CL; ++c) g += part[c];
+      gd[jj * ldk + r] = g;
+    }
+    for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
+      const int jj = idx / k, j = idx % k;
+      const float* vi = Vm + (own_lo + jj) * ldk;
+      const float* vj = Vm + j * ldk;
+      float h = 0.f;
+      for (int r = 0; r < ldk; r += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(vi + r);
+        const float4 y = *reinterpret_cast<const float4*>(vj + r);
+        h = fmaf(x.x, y.x, h);
+        h = fmaf(x.y, y.y, h);
+        h = fmaf(x.z, y.z, h);
+        h = fmaf(x.w, y.w, h);
+      }
+      Hm[jj * ldk + j] = h * h;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
+      const int jj = idx / k, r = idx % k;
+      const int i = own_lo + jj;
+      float g = 0.f;
+      for (int j = 0; j < k; ++j) g = fmaf(Hm[jj * ldk + j], Vm[j * ldk + r], g);
+      const float gdata =
+          gd[jj * ldk + r] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * sown[jj] * inv_b);
+      vn[jj * ldk + r] = Vm[i * ldk + r] - beta * (a.kappa * g - gdata);
+    }
+    cluster.sync();  // every owner's new columns ready; all reads of V and Gp done
+    // pull the new V from the owners
+    for (int idx = tid; idx < k * k; idx += TC_THREADS) {
+      const int i = idx / k, r = idx % k;
+      const int owner = i / cpq, jj = i % cpq;
+      Vm[i * ldk + r] = cluster.map_shared_rank(vn, owner)[jj * ldk + r];
+    }
+    __syncthreads();
+    if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0) {
+      float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
+      for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
+        const int jj = idx / k, r = idx % k;
+        dst[(int64_t)(own_lo + jj) * k + r] = Vm[(own_lo + jj) * ldk + r];
+      }
+    }
+  }
+  for (int idx = tid; idx < (own_hi - own_lo) * k; idx += TC_THREADS) {
+    const int jj = idx / k, r = idx % k;
+    a.V[(int64_t)(own_lo + jj) * k + r] = Vm[(own_lo + jj) * ldk + r];
+  }
+  // the cluster must not exit while others still read this CTA's shared memory
+  cluster.sync();
+  tc_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// quantise rows: FP8 -> per-row scale amax/448; BF16 -> scale 1.  Output row
+// stride ldq (zero padded).
+template <bool FP8>
+__global__ void quantize_rows_kernel(const float* __restrict__ Y, int64_t n, int k, int ldq,
+                                     uint8_t* __restrict__ Yq, float* __restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= n) return;
+  const float* y = Y + r * k;
+  float m = 0.f;
+  for (int c = lane; c < k; c += 32) m = fmaxf(m, fabsf(y[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float sc = FP8 ? (m > 0.f ? m / 448.f : 1.f) : 1.f;
+  const float inv = 1.f / sc;
+  for (int c = lane; c < ldq; c += 32) {
+    const float v = c < k ? y[c] * inv : 0.f;
+    if constexpr (FP8) {
+      const __nv_fp8_e4m3 q(v);
+      Yq[r * ldq + c] = *reinterpret_cast<const uint8_t*>(&q);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      reinterpret_cast<__nv_bfloat16*>(Yq)[r * ldq + c] = h;
+    }
+  }
+  if (lane == 0 && scale) scale[r] = sc;
+}
+
+template <bool FP8, bool SYM, int CL>
+otm_status launch_tc(const TcArgs& args, cudaStream_t st) {
+  const TcLayout L = tc_layout(args.k, CL, SYM, FP8 ? 1 : 2);
+  auto kern = sgd_tc_kernel<FP8, SYM, CL>;
+  OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  if (CL > 8)
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(TC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = L.total;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
+  count_launch();
+  return OTM_OK;
+}
+
+template <bool FP8, bool SYM>
+otm_status launch_tc_cl(const TcArgs& args, int CL, cudaStream_t st) {
+  switch (CL) {
+    case 16: return launch_tc<FP8, SYM, 16>(args, st);
+    case 8: return launch_tc<FP8, SYM, 8>(args, st);
+    case 4: return launch_tc<FP8, SYM, 4>(args, st);
+    case 2: return launch_tc<FP8, SYM, 2>(args, st);
+    default: return launch_tc<FP8, SYM, 1>(args, st);
+  }
+}
+
+int max_smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (v <= 0) v = 227 * 1024;
+  }
+  return v;
+}
+
+}  // namespace
+}  // namespace otm
+
+using namespace otm;
+
+extern "C" {
+
+otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precision, void* Yq,
+                                float* scales, void* stream) {
+  clear_error();
+  OTM_REQUIRE(Y && Yq && n >= 1 && k >= 1 && k <= TC_KMAX, "otm_quantize_samples: bad arguments");
+  OTM_REQUIRE(precision == OTM_PREC_BF16 || precision == OTM_PREC_FP8,
+              "otm_quantize_samples: precision must be OTM_PREC_BF16 or OTM_PREC_FP8");
+  OTM_REQUIRE(precision == OTM_PREC_BF16 || scales, "otm_quantize_samples: FP8 needs scales");
+  const int ldq = (int)((k + 15) & ~15);
+  cudaStream_t st = as_stream(stream);
+  const unsigned grid = (unsigned)((n + 7) / 8);
+  if (precision == OTM_PREC_FP8)
+    quantize_rows_kernel<true><<<grid, 256, 0, st>>>(Y, n, (int)k, ldq, (uint8_t*)Yq, scales);
+  else
+    quantize_rows_kernel<false><<<grid, 256, 0, st>>>(Y, n, (int)k, ldq, (uint8_t*)Yq, scales);
+  OTM_CHECK_LAUNCH();
+  return OTM_OK;
+}
+
+size_t otm_sgd_run_lp_workspace(void) { return 256; }
+
+otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* YC,
+                          const float* sA, const float* sB, const float* sC, int64_t n, int64_t k,
+                          const double* ybar3, const int32_t* perm, int64_t epochs, int64_t b,
+                          double beta0, double theta, double alpha0, int precision,
+                          int64_t snapshot_every, float* V_snap, void* ws, size_t ws_bytes,
+                          void* stream) {
+  clear_error();
+  OTM_REQUIRE(V && YA && YB && YC && ybar3, "otm_sgd_run_lp: null pointer");
+  OTM_REQUIRE(k >= 1 && k <= TC_KMAX, "otm_sgd_run_lp: k=%lld outside [1, %d]", (long long)k,
+              TC_KMAX);
+  OTM_REQUIRE(n >= 1 && b >= 1 && epochs >= 0, "otm_sgd_run_lp: need n >= 1, b >= 1, epochs >= 0");
+  OTM_REQUIRE(precision == OTM_PREC_BF16 || precision == OTM_PREC_FP8,
+              "otm_sgd_run_lp: precision must be OTM_PREC_BF16 or OTM_PREC_FP8");
+  OTM_REQUIRE(snapshot_every >= 0 && (snapshot_every == 0 || V_snap),
+              "otm_sgd_run_lp: V_snap required for snapshots");
+  OTM_REQUIRE(ws && ws_bytes >= otm_sgd_run_lp_workspace(), "otm_sgd_run_lp: workspace too small");
+  if (epochs == 0) return OTM_OK;
+  const bool fp8 = precision == OTM_PREC_FP8;
+  const bool sym = (YA == YB) && (YB == YC);
+  const int esize = fp8 ? 1 : 2;
+  // largest cluster (16, 8, ...) whose CTAs each hold at most a few tiles and
+  // whose shared-memory footprint fits
+  int CL = 0;
+  for (int c : {8, 16, 4, 2, 1}) {
+    if (tc_layout((int)k, c, sym, esize).total <= (size_t)max_smem_optin()) {
+      CL = c;
+      break;
+    }
+  }
+  OTM_REQUIRE(CL > 0, "otm_sgd_run_lp: k=%lld does not fit shared memory with %s views",
+              (long long)k, sym ? "one" : "three");
+  if (b > 8 * TILE && CL == 8 && tc_layout((int)k, 16, sym, esize).total <= (size_t)max_smem_optin())
+    CL = 16;
+  cudaStream_t st = as_stream(stream);
+  int* err = static_cast<int*>(ws);
+  OTM_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  TcArgs args;
+  args.YA = static_cast<const uint8_t*>(YA);
+  args.YB = static_cast<const uint8_t*>(YB);
+  args.YC = static_cast<const uint8_t*>(YC);
+  args.sA = sA;
+  args.sB = sB;
+  args.sC = sC;
+  args.perm = perm;
+  args.ybar3 = ybar3;
+  args.V = V;
+  args.V_snap = V_snap;
+  args.err = err;
+  args.n = n;
+  args.b = b;
+  args.spe = (n + b - 1) / b;
+  args.total_steps = args.spe * epochs;
+  args.snapshot_every = snapshot_every;
+  args.k = (int)k;
+  args.ldq = (int)((k + 15) & ~15);
+  args.beta0 = beta0;
+  args.c1 = (float)((alpha0 + 1.0) * (alpha0 + 2.0) / 2.0);
+  args.c2 = (float)(alpha0 * (alpha0 + 1.0) / 2.0);
+  args.c3 = (float)(alpha0 * alpha0);
+  args.kappa = (float)(0.5 * (1.0 + theta));
+  otm_status s_;
+  if (fp8)
+    s_ = sym ? launch_tc_cl<true, true>(args, CL, st) : launch_tc_cl<true, false>(args, CL, st);
+  else
+    s_ = sym ? launch_tc_cl<false, true>(args, CL, st) : launch_tc_cl<false, false>(args, CL, st);
+  if (s_ != OTM_OK) return s_;
+  int h = 0;
+  OTM_CHECK_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (h) return set_error(OTM_ETIMEOUT, "otm_sgd_run_lp: a tensor-core wait timed out");
+  return OTM_OK;
+}
+
+}  // extern "C"

@@ -58,6 +58,10 @@ _SIGS = {
     "otm_sgd_step": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_f64, c_f64, c_f64, c_vp],
     "otm_sgd_run": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64, c_i64, c_f64,
                     c_f64, c_f64, c_i64, c_vp, c_vp],
+    "otm_quantize_samples": [c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp, c_vp],
+    "otm_sgd_run_lp_workspace": [],
+    "otm_sgd_run_lp": [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64,
+                       c_i64, c_f64, c_f64, c_f64, ctypes.c_int, c_i64, c_vp, c_vp, c_sz, c_vp],
     "otm_unwhiten_workspace": [c_i64, c_i64, c_i64],
     "otm_unwhiten": [c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_f64, ctypes.c_int, c_vp, c_vp,
                      c_vp, c_vp, c_sz, c_vp],
@@ -296,6 +300,47 @@ def sgd_run(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, theta
     _check(_lib.otm_sgd_run(_ptr(V), _ptr(YA), _ptr(YB), _ptr(YC), n, k, _ptr(ybar3),
                             _ptr(perm), int(epochs), int(b), float(beta0), float(theta),
                             float(alpha0), int(snapshot_every), _ptr(snaps), _stream()))
+    return snaps
+
+
+PREC_BF16 = 1
+PREC_FP8 = 2
+
+
+def quantize_samples(Y, precision: int):
+    """Samples for the tensor-core STGD: returns (Yq, scales), Yq n x ldq
+    (ldq = k rounded up to 16) BF16 or FP8 e4m3 stored as bytes, scales n."""
+    n, k = Y.shape
+    _need(Y, torch.float32, (n, k), "Y")
+    ldq = (k + 15) // 16 * 16
+    es = 2 if precision == PREC_BF16 else 1
+    Yq = torch.empty(n, ldq * es, dtype=torch.uint8, device=Y.device)
+    sc = torch.empty(n, dtype=torch.float32, device=Y.device)
+    _check(_lib.otm_quantize_samples(_ptr(Y), n, k, int(precision), _ptr(Yq), _ptr(sc), _stream()))
+    return Yq, sc
+
+
+def sgd_run_lp(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, theta: float,
+               alpha0: float, precision: int, snapshot_every: int = 0):
+    """Tensor-core STGD.  YA/YB/YC are (Yq, scales) pairs from quantize_samples
+    (pass the same pair three times for symmetric views)."""
+    k = V.shape[0]
+    n = YA[0].shape[0]
+    _need(V, torch.float32, (k, k), "V")
+    _need(ybar3, torch.float64, (3, k), "ybar3")
+    if perm is not None:
+        _need(perm, torch.int32, (epochs, n), "perm")
+    steps = ((n + b - 1) // b) * epochs
+    snaps = None
+    if snapshot_every:
+        snaps = torch.empty(max(steps // snapshot_every, 1), k, k, dtype=torch.float32,
+                            device=V.device)
+    ws = _ws(_lib.otm_sgd_run_lp_workspace(), V.device)
+    _check(_lib.otm_sgd_run_lp(_ptr(V), _ptr(YA[0]), _ptr(YB[0]), _ptr(YC[0]), _ptr(YA[1]),
+                               _ptr(YB[1]), _ptr(YC[1]), n, k, _ptr(ybar3), _ptr(perm),
+                               int(epochs), int(b), float(beta0), float(theta), float(alpha0),
+                               int(precision), int(snapshot_every), _ptr(snaps), _ptr(ws),
+                               ws.numel(), _stream()))
     return snaps
 
 

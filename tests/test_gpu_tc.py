@@ -1,0 +1,95 @@
+"""GPU parity of the tensor-core (BF16 / FP8) STGD against the FP64 oracle.
+
+The low-precision path quantises the samples, V and B (per-sample and
+per-component scales) and accumulates in FP32; the oracle computes Lemma 3 in
+FP64 from the unquantised samples.  Tolerance: 2e-2 normwise relative
+(||G - G64||_F / (||kappa G_gram||_F + ||G_data||_F)) for BF16; FP8 e4m3
+(3 mantissa bits) is measured and held to 6e-2.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import stgd as ostgd
+from tests._util import rel, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def otm():
+    from paper_1309_0787_gb300 import otm as _otm
+    return _otm
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def _grad_err(otm, prec, k, b, sym, a0, seed):
+    g = np.random.default_rng(seed)
+    Ys = [(g.standard_normal((b, k)) * 0.5 + 0.2 * s).astype(np.float32) for s in (1, -1, 0.5)]
+    if sym:
+        Ys = [Ys[0]] * 3
+    yb = np.stack([Y.astype(np.float64).mean(axis=0) for Y in Ys])
+    V0 = (synth.haar_orthonormal(seed + 1, k) * np.float32(1.2)).astype(np.float32)
+    qs = [otm.quantize_samples(_dev(Y), prec) for Y in (Ys[:1] if sym else Ys)]
+    if sym:
+        qs = qs * 3
+    Vd = _dev(V0.T.copy())
+    otm.sgd_run_lp(Vd, qs[0], qs[1], qs[2], _dev(yb), None, 1, b, 1.0, 1.0, a0, prec)
+    torch.cuda.synchronize()
+    V64 = V0.astype(np.float64)
+    G = ostgd.grad_implicit(V64, *[Y.astype(np.float64) for Y in Ys], tuple(yb), 1.0, a0)
+    gram = V64 @ (V64.T @ V64) ** 2
+    Gk = V64 - to_np(Vd).T.astype(np.float64)
+    return np.linalg.norm(Gk - G) / (np.linalg.norm(gram) + np.linalg.norm(gram - G))
+
+
+@pytest.mark.parametrize("k,b,sym,a0", [(100, 1024, False, 1.0), (100, 1024, True, 1.0),
+                                        (10, 256, True, 1.0), (17, 100, False, 0.5),
+                                        (64, 2000, True, 0.0), (128, 512, True, 1.0)])
+def test_tc_bf16_gradient(otm, k, b, sym, a0):
+    err = _grad_err(otm, otm.PREC_BF16, k, b, sym, a0, 3 * k + b)
+    assert err < 2e-2, err
+
+
+@pytest.mark.parametrize("k,b,sym,a0", [(100, 1024, False, 1.0), (100, 1024, True, 1.0),
+                                        (33, 300, False, 1.0), (128, 1024, True, 1.0)])
+def test_tc_fp8_gradient(otm, k, b, sym, a0):
+    err = _grad_err(otm, otm.PREC_FP8, k, b, sym, a0, 5 * k + b)
+    assert err < 6e-2, err
+
+
+def test_tc_bf16_run_tracks_fp32_run(otm):
+    """Several epochs with permutations: the BF16 iterate stays close to the
+    FP32 oracle iterate (errors do not accumulate beyond the per-step level)."""
+    k, n, b, epochs = 16, 2000, 256, 4
+    o = synth.orthogonal_samples(7, k, n, 0.05)
+    Y = o["Y"]
+    yb = Y.astype(np.float64).mean(axis=0)
+    perm = synth.epoch_permutations(8, n, epochs)
+    V0 = synth.haar_orthonormal(9, k)
+    q = otm.quantize_samples(_dev(Y), otm.PREC_BF16)
+    Vd = _dev(V0.T.copy())
+    snaps = otm.sgd_run_lp(Vd, q, q, q, _dev(np.stack([yb] * 3)), _dev(perm), epochs, b, 5e-3,
+                           1.0, 0.0, otm.PREC_BF16, snapshot_every=8)
+    torch.cuda.synchronize()
+    Vo, so = ostgd.sgd_run(V0, Y, Y, Y, (yb, yb, yb), perm, b, 5e-3, 1.0, 0.0, snapshot_every=8)
+    assert rel(to_np(Vd).T, Vo) < 2e-2
+    assert snaps.shape[0] == len(so)
+
+
+def test_quantize_samples_roundtrip(otm):
+    g = np.random.default_rng(1)
+    Y = (g.standard_normal((300, 37)) * np.exp(g.standard_normal((300, 1)))).astype(np.float32)
+    qb, sb = otm.quantize_samples(_dev(Y), otm.PREC_BF16)
+    qf, sf = otm.quantize_samples(_dev(Y), otm.PREC_FP8)
+    torch.cuda.synchronize()
+    yb = to_np(qb.view(torch.bfloat16).float())[:, :37]
+    assert np.abs(yb - Y).max() <= 2 ** -8 * np.abs(Y).max()
+    yf = to_np(qf.view(torch.float8_e4m3fn).float())[:, :37] * to_np(sf)[:, None]
+    # e4m3: 3 mantissa bits -> relative rounding error <= 2^-4 of each value's scale
+    assert np.all(np.abs(yf - Y) <= 2 ** -4 * np.abs(Y) + 2 ** -9 * to_np(sf)[:, None] * 448)
+    assert np.all(to_np(qb)[:, 74:] == 0) and np.all(to_np(qf)[:, 37:] == 0)
