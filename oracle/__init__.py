@@ -27,4 +27,4 @@ other than itself (brute-force counts, closed forms, library routines, finite
 differences, exact recovery).  The paper's real-dataset tables are not
 reproduced (their data are absent): parity unpinned for those numbers only.
 """
-from . import moments, whiten, stgd, post  # noqa: F401
+from . import moments, whiten, stgd, post, warmstart  # noqa: F401

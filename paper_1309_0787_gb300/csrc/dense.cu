@@ -20,7 +20,8 @@ namespace {
 // ---------------------------------------------------------------------------
 // C (m x p, FP64) (+)= alpha * A^T B.  A: rows x m, B: rows x p (float32).
 // Block: 64 x 64 output tile, 256 threads (4 x 4 each).  Rows are split over
-// gridDim.z; inside a block 32-row slabs are summed in FP32, slabs in FP64.
+// gridDim.z (at least 256 rows per block); a block sums its rows in FP32 and
+// adds its tile to C in FP64.
 // ---------------------------------------------------------------------------
 constexpr int TN_T = 64, TN_R = 32;
 
@@ -56,28 +57,24 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
   const int64_t i0 = (int64_t)blockIdx.x * TN_T, j0 = (int64_t)blockIdx.y * TN_T;
   const int64_t r_begin = (int64_t)blockIdx.z * rows_per_split;
   const int64_t r_end = min(rows, r_begin + rows_per_split);
-  double accd[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) accd[a][b] = 0.0;
+  // FP32 sums over this block's rows (<= a few hundred), FP64 across blocks
+  float acc[4][4] = {};
   float va[2][4], vb[2][4];
   tn_load(A, m, r_begin, r_end, i0, m, t, va);
   tn_load(B, p, r_begin, r_end, j0, p, t, vb);
   for (int64_t r0 = r_begin; r0 < r_end; r0 += TN_R) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int z = 0; z < 4; ++z) {
-        As[ty + 16 * q][4 * tx + z] = va[q][z];
-        Bs[ty + 16 * q][4 * tx + z] = vb[q][z];
-      }
+    for (int q = 0; q < 2; ++q) {
+      *reinterpret_cast<float4*>(&As[ty + 16 * q][4 * tx]) =
+          make_float4(va[q][0], va[q][1], va[q][2], va[q][3]);
+      *reinterpret_cast<float4*>(&Bs[ty + 16 * q][4 * tx]) =
+          make_float4(vb[q][0], vb[q][1], vb[q][2], vb[q][3]);
+    }
     __syncthreads();
     if (r0 + TN_R < r_end) {  // prefetch the next slab while this one is multiplied
       tn_load(A, m, r0 + TN_R, r_end, i0, m, t, va);
       tn_load(B, p, r0 + TN_R, r_end, j0, p, t, vb);
     }
-    float acc[4][4] = {};
 #pragma unroll 8
     for (int rr = 0; rr < TN_R; ++rr) {
       float a[4], b[4];
@@ -91,10 +88,6 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
     }
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) accd[x][y] += (double)acc[x][y];
     __syncthreads();
   }
 #pragma unroll
@@ -102,12 +95,12 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
       const int64_t i = i0 + ty + 16 * x, j = j0 + tx + 16 * y;
-      if (i < m && j < p) atomicAdd(&C[i * p + j], alpha * accd[x][y]);
+      if (i < m && j < p) atomicAdd(&C[i * p + j], alpha * (double)acc[x][y]);
     }
 }
 
 // ---------------------------------------------------------------------------
-// out (rows x p) = A (rows x m) * C (m x p, FP64 staged as float32)
+// out (rows x p) = A (rows x m) * C (m x p, float32)
 //                  - r1_alpha * r1_u[r] * r1_v[c]   (optional rank-one term)
 // One block owns 32 whole rows (all p <= 256 columns), so A may alias out.
 // Staging loads of a K-chunk are all issued into registers before they are
@@ -116,7 +109,7 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
 constexpr int NN_R = 32, NN_K = 32, NN_PMAX = 256;
 
 __global__ void __launch_bounds__(256) gemm_nn_small_kernel(
-    const float* A, int64_t rows, int64_t m, const double* __restrict__ C, int64_t p, float* out,
+    const float* A, int64_t rows, int64_t m, const float* __restrict__ C, int64_t p, float* out,
     const double* __restrict__ r1_u, const double* __restrict__ r1_v, double r1_alpha,
     const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -144,7 +137,7 @@ __global__ void __launch_bounds__(256) gemm_nn_small_kernel(
 #pragma unroll
       for (int j = 0; j < NN_PMAX / 32; ++j) {
         const int64_t c = cg + 32 * j;
-        cv[q][j] = (j < ncj && k < m && c < p) ? (float)__ldg(C + k * p + c) : 0.f;
+        cv[q][j] = (j < ncj && k < m && c < p) ? __ldg(C + k * p + c) : 0.f;
       }
     }
 #pragma unroll
@@ -277,10 +270,10 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 // Cholesky of G (+ shift) and the inverse of its upper factor R = L^T.
 // One CTA of 256 threads, FP32 in shared memory (n <= 160), blocked by 8
 // columns: one warp factors each 8 x 8 diagonal block in registers (shuffles,
-// no barrier), the panel below is solved against the block's inverse, and
-// the trailing matrix takes a rank-8 update -- three barriers per block
-// column instead of two per column.  L^{-1} is then formed by blocked forward
-// substitution (two barriers per block row).  Output Rinv (n x n, FP64,
+// no barrier), every row of the panel below solves against it by forward
+// substitution, and the trailing matrix takes a rank-8 update -- three
+// barriers per block column instead of two per column.  L^{-1} is then formed
+// by blocked forward substitution (two barriers per block row).  Output Rinv (n x n, float32,
 // row-major, upper triangular) so that Q = A Rinv.
 // shift_scale > 0 adds shift_scale * n * u * trace(G) to the diagonal
 // (u = 2^-24), which keeps the factorisation positive definite for Gram
@@ -295,7 +288,7 @@ constexpr int CH_T = 256, CH_B = 8;
 
 __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict__ G, int n,
                                                         double shift_scale,
-                                                        double* __restrict__ Rinv,
+                                                        float* __restrict__ Rinv,
                                                         int* __restrict__ flag, int* skip,
                                                         float check_tol) {
   extern __shared__ float sm[];
@@ -322,10 +315,10 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
   }
   const int ldn = n | 1;       // odd row stride: column walks are bank-conflict free
   const int nblk = (n + CH_B - 1) / CH_B;
-  float* L = sm;                         // n x ldn (lower triangle)
-  float* X = L + n * ldn;                // n x ldn, X = L^{-1} (lower triangle)
-  float* Dinv = X + n * ldn;             // nblk x 8 x 8, inverses of the diagonal blocks
-  float* tmp = Dinv + nblk * 64;         // 8 x n scratch
+  float* L = sm;                 // n x ldn (lower triangle)
+  float* X = L + n * ldn;        // n x ldn, X = L^{-1} (lower triangle)
+  float* rdg = X + n * ldn;      // n reciprocal pivots 1 / L_jj
+  float* tmp = rdg + n;          // 8 x n scratch
   __shared__ float s_shift, s_floor;
   __shared__ int s_bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -352,7 +345,7 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
 
   for (int J = 0; J < nblk; ++J) {
     const int j0 = J * CH_B, jb = min(CH_B, n - j0);
-    // (1) factor the diagonal block: lane r holds row j0 + r
+    // (1) factor the diagonal block in warp 0: lane r holds row j0 + r
     if (warp == 0) {
       float a[CH_B];
 #pragma unroll
@@ -366,9 +359,12 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
             if (lane == 0) s_bad = 1;
             d = 1.f;
           }
-          const float piv = sqrtf(fmaxf(d, s_floor));
-          if (lane == c) a[c] = piv;
-          if (lane > c) a[c] /= piv;
+          const float pinv = rsqrtf(fmaxf(d, s_floor));
+          if (lane == c) {
+            a[c] = fmaxf(d, s_floor) * pinv;
+            rdg[j0 + c] = pinv;
+          }
+          if (lane > c) a[c] *= pinv;
 #pragma unroll
           for (int kk = c + 1; kk < CH_B; ++kk) {
             const float lkc = __shfl_sync(0xffffffffu, a[c], kk);
@@ -381,50 +377,20 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
         for (int c = 0; c < CH_B; ++c)
           if (c <= lane) L[(j0 + lane) * ldn + j0 + c] = a[c];
       }
-      __syncwarp();
-      // inverse of the diagonal block (lower triangular), lane c owns column c
-      float* D = Dinv + J * 64;
-      if (lane < jb) {
-        float x[CH_B];
-#pragma unroll
-        for (int r = 0; r < CH_B; ++r) {
-          float v = 0.f;
-          if (r == lane) v = 1.f / L[(j0 + r) * ldn + j0 + r];
-          if (r > lane && r < jb) {
-            float sacc = 0.f;
-#pragma unroll
-            for (int l2 = 0; l2 < CH_B; ++l2)
-              if (l2 >= lane && l2 < r) sacc = fmaf(L[(j0 + r) * ldn + j0 + l2], x[l2], sacc);
-            v = -sacc / L[(j0 + r) * ldn + j0 + r];
-          }
-          x[r] = v;
-        }
-#pragma unroll
-        for (int r = 0; r < CH_B; ++r) D[r * CH_B + lane] = x[r];
-      }
-      if (lane >= jb && lane < CH_B) {
-#pragma unroll
-        for (int r = 0; r < CH_B; ++r) D[r * CH_B + lane] = 0.f;
-      }
     }
     __syncthreads();
-    // (2) panel: L_iJ = A_iJ L_JJ^{-T} for the rows below the block
-    {
-      const float* D = Dinv + J * 64;
-      for (int i = j0 + jb + tid; i < n; i += CH_T) {
-        float a[CH_B], l[CH_B];
+    // (2) panel: row i below the block solves l L_JJ^T = a by forward substitution
+    for (int i = j0 + jb + tid; i < n; i += CH_T) {
+      float l[CH_B];
 #pragma unroll
-        for (int c = 0; c < CH_B; ++c) a[c] = c < jb ? L[i * ldn + j0 + c] : 0.f;
+      for (int c = 0; c < CH_B; ++c) {
+        if (c < jb) {
+          float v = L[i * ldn + j0 + c];
 #pragma unroll
-        for (int c = 0; c < CH_B; ++c) {
-          float v = 0.f;
-#pragma unroll
-          for (int m2 = 0; m2 <= c; ++m2) v = fmaf(a[m2], D[c * CH_B + m2], v);
-          l[c] = v;
+          for (int m2 = 0; m2 < c; ++m2) v = fmaf(-l[m2], L[(j0 + c) * ldn + j0 + m2], v);
+          l[c] = v * rdg[j0 + c];
+          L[i * ldn + j0 + c] = l[c];
         }
-#pragma unroll
-        for (int c = 0; c < CH_B; ++c)
-          if (c < jb) L[i * ldn + j0 + c] = l[c];
       }
     }
     __syncthreads();
@@ -444,36 +410,43 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
     __syncthreads();
   }
 
-  // X = L^{-1} by block rows: X_II = Dinv_I,
-  // X_IJ = -Dinv_I sum_{K < I} L_IK X_KJ  for the columns left of block I
+  // X = L^{-1} by block rows: tmp = L_{I,<I} X_{<I}, then forward substitution
+  // with L_II for every column (unit right-hand sides inside the block)
   for (int I = 0; I < nblk; ++I) {
     const int i0 = I * CH_B, ib = min(CH_B, n - i0);
-    // tmp[r][c] = sum_{m=c}^{i0-1} L[i0+r][m] X[m][c], c < i0
     for (int idx = tid; idx < ib * i0; idx += CH_T) {
       const int r = idx / i0, c = idx % i0;
-      float sacc = 0.f;
-      for (int m2 = c; m2 < i0; ++m2) sacc = fmaf(L[(i0 + r) * ldn + m2], X[m2 * ldn + c], sacc);
-      tmp[r * n + c] = sacc;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int m2 = c;
+      for (; m2 + 3 < i0; m2 += 4) {
+        s0 = fmaf(L[(i0 + r) * ldn + m2], X[m2 * ldn + c], s0);
+        s1 = fmaf(L[(i0 + r) * ldn + m2 + 1], X[(m2 + 1) * ldn + c], s1);
+        s2 = fmaf(L[(i0 + r) * ldn + m2 + 2], X[(m2 + 2) * ldn + c], s2);
+        s3 = fmaf(L[(i0 + r) * ldn + m2 + 3], X[(m2 + 3) * ldn + c], s3);
+      }
+      for (; m2 < i0; ++m2) s0 = fmaf(L[(i0 + r) * ldn + m2], X[m2 * ldn + c], s0);
+      tmp[r * n + c] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
-    const float* D = Dinv + I * 64;
-    for (int idx = tid; idx < ib * (i0 + ib); idx += CH_T) {
-      const int r = idx / (i0 + ib), c = idx % (i0 + ib);
-      float v;
-      if (c < i0) {
-        v = 0.f;
-        for (int r2 = 0; r2 <= r; ++r2) v = fmaf(-D[r * CH_B + r2], tmp[r2 * n + c], v);
-      } else {
-        v = D[r * CH_B + (c - i0)];
+    for (int c = tid; c < i0 + ib; c += CH_T) {
+      float x[CH_B];
+#pragma unroll
+      for (int r = 0; r < CH_B; ++r) {
+        if (r < ib) {
+          float v = c < i0 ? -tmp[r * n + c] : (c - i0 == r ? 1.f : 0.f);
+#pragma unroll
+          for (int r2 = 0; r2 < r; ++r2) v = fmaf(-L[(i0 + r) * ldn + i0 + r2], x[r2], v);
+          x[r] = v * rdg[i0 + r];
+          X[(i0 + r) * ldn + c] = x[r];
+        }
       }
-      X[(i0 + r) * ldn + c] = v;
     }
     __syncthreads();
   }
   // Rinv = (L^T)^{-1} = (L^{-1})^T, zero below the diagonal
   for (int i = warp; i < n; i += NW)
     for (int j = lane; j < n; j += 32)
-      Rinv[(int64_t)i * n + j] = j >= i ? (double)X[j * ldn + i] : 0.0;
+      Rinv[(int64_t)i * n + j] = j >= i ? X[j * ldn + i] : 0.f;
   if (tid == 0 && s_bad) *flag = 1;
 }
 
@@ -671,14 +644,29 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
       v0 = x0 - alpha;
       tj = 1.f / (sigma - x0 * alpha);  // 2 / (v^T v), v^T v = 2 (sigma - x0 alpha)
     }
-    // p = tau A_trail v  (thread per trailing row), and p^T v
+    // p = tau A_trail v (two threads per trailing row, interleaved columns,
+    // two accumulators each), and p^T v
     float pv = 0.f;
-    for (int i = r0 + tid; i < n; i += TE_T) {
-      float acc = Ah[i * ldn + r0] * v0;
-      for (int c = r0 + 1; c < n; ++c) acc = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], acc);
-      const float pi = tj * acc;
-      P[i] = pi;
-      pv = fmaf(pi, i == r0 ? v0 : Ah[i * ldn + j], pv);
+    for (int base = r0; base < n; base += TE_T >> 1) {  // trip count uniform per block
+      const int i = base + (tid >> 1);
+      const int hh = tid & 1;
+      float a0 = 0.f, a1 = 0.f;
+      if (i < n) {
+        int c = r0 + 1 + hh;
+        for (; c + 2 < n; c += 4) {
+          a0 = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], a0);
+          a1 = fmaf(Ah[i * ldn + c + 2], Ah[(c + 2) * ldn + j], a1);
+        }
+        for (; c < n; c += 2) a0 = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], a0);
+        if (hh == 0) a0 = fmaf(Ah[i * ldn + r0], v0, a0);
+      }
+      float acc = a0 + a1;
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (i < n && hh == 0) {
+        const float pi = tj * acc;
+        P[i] = pi;
+        pv = fmaf(pi, i == r0 ? v0 : Ah[i * ldn + j], pv);
+      }
     }
     const float ptv = block_sum_f(pv, red[1], tid);  // includes a barrier: P complete
     const float K = 0.5f * tj * ptv;
@@ -725,14 +713,14 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   const float piv_min = 1e-30f + 1e-12f * tnorm;
   if (tid < n) {
     float lo = glo, hi = ghi;
-    for (int it = 0; it < 32; ++it) {
+    for (int it = 0; it < 28; ++it) {
       const float mid = 0.5f * (lo + hi);
       int cnt = 0;
       float q = d[0] - mid;
       if (fabsf(q) < piv_min) q = -piv_min;
       cnt += q < 0.f;
       for (int k = 1; k < n; ++k) {
-        q = d[k] - mid - e[k - 1] * e[k - 1] / q;
+        q = d[k] - mid - __fdividef(e[k - 1] * e[k - 1], q);
         if (fabsf(q) < piv_min) q = -piv_min;
         cnt += q < 0.f;
       }
@@ -847,15 +835,28 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   }
   __syncthreads();
 
-  // 4. back-transformation X = H_0 ... H_{n-3} Z, thread per column
-  for (int c = tid; c < n; c += TE_T) {
+  // 4. back-transformation X = H_0 ... H_{n-3} Z: two threads per column (rows
+  // interleaved, partial dot products combined by a shuffle), no barriers
+  for (int base = 0; base < n; base += TE_T >> 1) {  // trip count uniform per block
+    const int c = base + (tid >> 1), hh = tid & 1;
     for (int j = n - 3; j >= 0; --j) {
-      const float tj = tau[j];
+      const float tj = tau[j];  // uniform across the pair
       if (tj == 0.f) continue;
-      float w = 0.f;
-      for (int r = j + 1; r < n; ++r) w = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w);
+      float w0 = 0.f, w1 = 0.f;
+      if (c < n) {
+        int r = j + 1 + hh;
+        for (; r + 2 < n; r += 4) {
+          w0 = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w0);
+          w1 = fmaf(Ah[(r + 2) * ldn + j], Z[(r + 2) * ldn + c], w1);
+        }
+        for (; r < n; r += 2) w0 = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w0);
+      }
+      float w = w0 + w1;
+      w += __shfl_xor_sync(0xffffffffu, w, 1);
       w *= tj;
-      for (int r = j + 1; r < n; ++r) Z[r * ldn + c] = fmaf(-w, Ah[r * ldn + j], Z[r * ldn + c]);
+      if (c < n)
+        for (int r = j + 1 + hh; r < n; r += 2)
+          Z[r * ldn + c] = fmaf(-w, Ah[r * ldn + j], Z[r * ldn + c]);
     }
   }
   __syncthreads();
@@ -963,7 +964,8 @@ __global__ void __launch_bounds__(1024) eig_finalize_kernel(const double* __rest
 __global__ void whitening_factors_kernel(const double* __restrict__ evals,
                                          const double* __restrict__ evecs, int64_t n, int64_t k,
                                          double* __restrict__ Cw, double* __restrict__ Cp,
-                                         double* __restrict__ eig, int* __restrict__ flag) {
+                                         double* __restrict__ eig, int* __restrict__ flag,
+                                         float* __restrict__ Cw32) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < k) eig[idx] = evals[idx];
   // the k-th eigenvalue must be positive and resolvable above the float32
@@ -975,6 +977,7 @@ __global__ void whitening_factors_kernel(const double* __restrict__ evals,
   const double s = l > 0.0 ? sqrt(l) : 1.0;
   Cw[idx] = evecs[r * n + i] / s;
   Cp[idx] = evecs[r * n + i] * s;
+  if (Cw32) Cw32[idx] = (float)(evecs[r * n + i] / s);
 }
 
 __global__ void copy_f64_kernel(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
@@ -1016,7 +1019,7 @@ otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t 
   return OTM_OK;
 }
 
-otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
+otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const float* C, int64_t p,
                          float* out, const double* r1_u, const double* r1_v, double r1_alpha,
                          cudaStream_t st, const int* skip) {
   if (p > NN_PMAX) return set_error(OTM_EINVAL, "gemm_nn_small: p=%lld > %d", (long long)p, NN_PMAX);
@@ -1058,7 +1061,7 @@ otm_status vec_tn(const double* u, const float* A, int64_t rows, int64_t m, doub
 
 size_t orth_workspace(int64_t m) {
   WorkspaceSize w;
-  w.add<double>(m * m).add<double>(m * m).add<int>(1);
+  w.add<double>(m * m).add<float>(m * m).add<int>(1);
   return w.bytes();
 }
 
@@ -1067,11 +1070,10 @@ otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cuda
   if (m > 160) return set_error(OTM_EINVAL, "orthonormalize: m=%lld > 160", (long long)m);
   if (rows < m) return set_error(OTM_EINVAL, "orthonormalize: rows < m");
   double* G = ws.take<double>(m * m);
-  double* Rinv = ws.take<double>(m * m);
+  float* Rinv = ws.take<float>(m * m);
   int* skip = ws.take<int>(1);
   if (!G || !Rinv || !skip) return set_error(OTM_EINVAL, "orthonormalize: workspace too small");
-  const size_t smem =
-      sizeof(float) * (2 * m * (m | 1) + ((m + CH_B - 1) / CH_B) * 64 + CH_B * m);
+  const size_t smem = sizeof(float) * (2 * m * (m | 1) + m + CH_B * m);
   OTM_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   OTM_CHECK_CUDA(cudaMemsetAsync(skip, 0, sizeof(int), st));
@@ -1149,10 +1151,23 @@ otm_status syev(const double* A_in, int64_t n, double* evals, double* evecs, Wor
 }
 
 otm_status whitening_factors(const double* evals, const double* evecs, int64_t n, int64_t k,
-                             double* Cw, double* Cp, double* eig, int* flag, cudaStream_t st) {
+                             double* Cw, double* Cp, double* eig, int* flag, cudaStream_t st,
+                             float* Cw32) {
   const int64_t tot = n * k > k ? n * k : k;
   whitening_factors_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(evals, evecs, n, k, Cw,
-                                                                           Cp, eig, flag);
+                                                                           Cp, eig, flag, Cw32);
+  OTM_CHECK_LAUNCH();
+  return OTM_OK;
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+otm_status f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
+  if (n <= 0) return OTM_OK;
+  f64_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }

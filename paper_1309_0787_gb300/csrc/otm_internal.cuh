@@ -89,11 +89,12 @@ otm_status column_sums_scaled(const otm_csr* X, double scale, double* out, cudaS
 otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t m, int64_t p,
                           double alpha, double* C, int accumulate, cudaStream_t st,
                           const int* skip = nullptr);
-// out (rows x p, float32) = A (rows x m, float32) * C (m x p, FP64, rounded to FP32)
+// out (rows x p, float32) = A (rows x m, float32) * C (m x p, float32)
 //   [+ rank-one term: - r1_alpha * r1_u[r] * r1_v[c]] [then * colscale[c]]
-otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
+otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const float* C, int64_t p,
                          float* out, const double* r1_u, const double* r1_v, double r1_alpha,
                          cudaStream_t st, const int* skip = nullptr);
+otm_status f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 // out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64), FP64 accumulation.
 otm_status gemm_nn_f64(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
                        double* out, cudaStream_t st);
@@ -116,7 +117,8 @@ otm_status vec_tn(const double* u, const float* A, int64_t rows, int64_t m, doub
 // Cp[:, i] = U[:, i] * sqrt(l_i) for i < k (n x k each, FP64); eig[i] = l_i.
 // Sets *flag (device int) to 1 if l_{k-1} <= 0.
 otm_status whitening_factors(const double* evals, const double* evecs, int64_t n, int64_t k,
-                             double* Cw, double* Cp, double* eig, int* flag, cudaStream_t st);
+                             double* Cw, double* Cp, double* eig, int* flag, cudaStream_t st,
+                             float* Cw32 = nullptr);
 
 // ---- whitening composites (whiten.cu) ----
 

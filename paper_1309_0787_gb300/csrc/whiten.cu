@@ -54,10 +54,10 @@ __global__ void sqrt_vec_kernel(const double* __restrict__ a, double* __restrict
 
 // First k columns of an n x n row-major matrix -> n x k.
 __global__ void take_cols_kernel(const double* __restrict__ a, int64_t n, int64_t k,
-                                 double* __restrict__ b) {
+                                 float* __restrict__ b) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * k) return;
-  b[idx] = a[(idx / k) * n + idx % k];
+  b[idx] = (float)a[(idx / k) * n + idx % k];
 }
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -91,6 +91,7 @@ struct CommunityOp {
   double* ab;    // 2k x m scratch
   double* coef;  // 2k x m scratch
   double* u;     // m scratch
+  float* coef32; // 2k x m scratch
   otm_status apply(const float* X, int64_t m, float* O, cudaStream_t st) const {
     OTM_TRY(gemm_tn_f64acc(L, X, n_a, 2 * k, m, 1.0, ab, 0, st));  // [L_C^T X ; L_B^T X]
     OTM_TRY(vec_tn(M1, X, n_a, m, u, st));
@@ -98,7 +99,8 @@ struct CommunityOp {
     // top rows multiply L_C: s K (L_B^T X); bottom rows multiply L_B: s K^T (L_C^T X)
     OTM_TRY(dgemm_small(0, 0, k, m, k, s, K, k, ab + k * m, m, 0.0, coef, m, st));
     OTM_TRY(dgemm_small(1, 0, k, m, k, s, K, k, ab, m, 0.0, coef + k * m, m, st));
-    OTM_TRY(gemm_nn_small(L, n_a, 2 * k, coef, m, O, M1, u, a0, st));
+    OTM_TRY(f64_to_f32(coef, coef32, 2 * k * m, st));
+    OTM_TRY(gemm_nn_small(L, n_a, 2 * k, coef32, m, O, M1, u, a0, st));
     return OTM_OK;
   }
 };
@@ -112,7 +114,9 @@ otm_status range_finder(const Op& op, int64_t d, const float* S, int64_t k, int6
   double* Om = ws.take<double>(kt * kt);
   double* ev = ws.take<double>(kt);
   double* evec = ws.take<double>(kt * kt);
-  if (!O || !Om || !ev || !evec) return set_error(OTM_EINVAL, "whiten: workspace too small");
+  float* Cw32 = ws.take<float>(kt * k);
+  if (!O || !Om || !ev || !evec || !Cw32)
+    return set_error(OTM_EINVAL, "whiten: workspace too small");
   const size_t mark = ws.used;
   OTM_TRY(op.apply(S, kt, Q, st));
   OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2));
@@ -127,8 +131,8 @@ otm_status range_finder(const Op& op, int64_t d, const float* S, int64_t k, int6
   OTM_TRY(gemm_tn_f64acc(Q, O, d, kt, kt, 1.0, Om, 0, st));
   OTM_TRY(syev(Om, kt, ev, evec, ws, st, flags + 2));
   ws.used = mark;
-  OTM_TRY(whitening_factors(ev, evec, kt, k, Cw, Cp, eig, flags, st));
-  OTM_TRY(gemm_nn_small(Q, d, kt, Cw, k, W, nullptr, nullptr, 0.0, st));
+  OTM_TRY(whitening_factors(ev, evec, kt, k, Cw, Cp, eig, flags, st, Cw32));
+  OTM_TRY(gemm_nn_small(Q, d, kt, Cw32, k, W, nullptr, nullptr, 0.0, st));
   return OTM_OK;
 }
 
@@ -150,6 +154,7 @@ otm_status check_flags(int* flags, cudaStream_t st, const char* who) {
 size_t range_finder_ws(int64_t d, int64_t kt) {
   WorkspaceSize w;
   w.add<float>(d * kt).add<double>(kt * kt).add<double>(kt).add<double>(kt * kt);
+  w.add<float>(kt * 160);
   const size_t inner = orth_workspace(kt) > syev_workspace(kt) ? orth_workspace(kt)
                                                                   : syev_workspace(kt);
   return w.bytes() + inner;
@@ -252,7 +257,8 @@ size_t otm_whiten_community_workspace(int64_t n_x, int64_t n_a, int64_t n_b, int
   WorkspaceSize w;
   w.add<float>(n_c * kt).add<float>(n_b * kt).add<float>(n_x * (kt > 2 * k ? kt : 2 * k));
   w.add<double>(kt * kt).add<double>(kt).add<double>(kt * kt);  // BB, ev, evec
-  w.add<double>(kt * k).add<double>(kt * k).add<double>(kt * k).add<double>(k);  // Ub, Cv, Cu, s2
+  w.add<float>(kt * k).add<double>(kt * k).add<double>(kt * k).add<double>(k);  // Ub, Cv, Cu, s2
+  w.add<float>(kt * k).add<float>(2 * k * kt).add<float>(2 * k * k);  // Cv32, coef32, LW32
   w.add<float>(n_c * k).add<float>(n_b * k);                      // U_C, V_B
   w.add<float>(n_x * k).add<float>(n_x * k).add<float>(n_a * 2 * k);  // CU, BV, L
   w.add<double>(k * k);                                           // K
@@ -296,7 +302,7 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
   double* BB = w.take<double>(kt * kt);
   double* ev = w.take<double>(kt);
   double* evec = w.take<double>(kt * kt);
-  double* Ub = w.take<double>(kt * k);
+  float* Ub = w.take<float>(kt * k);
   double* Cv = w.take<double>(kt * k);
   double* Cu = w.take<double>(kt * k);
   double* s2 = w.take<double>(k);
@@ -310,6 +316,9 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
   double* coef = w.take<double>(2 * k * kt);
   double* u = w.take<double>(kt);
   double* LW = w.take<double>(2 * k * k);
+  float* Cv32 = w.take<float>(kt * k);
+  float* coef32 = w.take<float>(2 * k * kt);
+  float* LW32 = w.take<float>(2 * k * k);
   int* flags = w.take<int>(kFlags);
   OTM_CHECK_CUDA(cudaMemsetAsync(flags, 0, kFlags * sizeof(int), st));
   const size_t mark = w.used;
@@ -332,11 +341,11 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
   w.used = mark;
   take_cols_kernel<<<blocks_for(kt * k), 256, 0, st>>>(evec, kt, k, Ub);
   OTM_CHECK_LAUNCH();
-  OTM_TRY(whitening_factors(ev, evec, kt, k, Cv, Cu, s2, flags + 1, st));  // Cv = Ub / sigma
+  OTM_TRY(whitening_factors(ev, evec, kt, k, Cv, Cu, s2, flags + 1, st, Cv32));  // Ub / sigma
   sqrt_vec_kernel<<<blocks_for(k), 256, 0, st>>>(s2, sigma, k);
   OTM_CHECK_LAUNCH();
   OTM_TRY(gemm_nn_small(Yc, nc, kt, Ub, k, U_C, nullptr, nullptr, 0.0, st));
-  OTM_TRY(gemm_nn_small(Zb, nb, kt, Cv, k, V_B, nullptr, nullptr, 0.0, st));
+  OTM_TRY(gemm_nn_small(Zb, nb, kt, Cv32, k, V_B, nullptr, nullptr, 0.0, st));
 
   // 2. factors of Z_B, Z_C and the middle matrix K
   OTM_TRY(spmm_gather(G_XC, U_C, k, nullptr, CU, st));
@@ -351,13 +360,14 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
   OTM_TRY(column_sums_scaled(G_XA, 1.0 / (double)nx, M1, st));
 
   // 3. range-finder whitening of sym(M2)
-  CommunityOp op{L, K, M1, na, k, alpha0, ab, coef, u};
+  CommunityOp op{L, K, M1, na, k, alpha0, ab, coef, u, coef32};
   OTM_TRY(range_finder(op, na, S_w, k, kt, power_iters, W, Q, Cw, Cp, eig, w, st, flags));
 
   // 4. other views: W_B = Z_B^T W = V_B (L_B^T W), W_C = Z_C^T W = U_C (L_C^T W)
   OTM_TRY(gemm_tn_f64acc(L, W, na, 2 * k, k, 1.0, LW, 0, st));
-  OTM_TRY(gemm_nn_small(V_B, nb, k, LW + k * k, k, W_B, nullptr, nullptr, 0.0, st));
-  OTM_TRY(gemm_nn_small(U_C, nc, k, LW, k, W_C, nullptr, nullptr, 0.0, st));
+  OTM_TRY(f64_to_f32(LW, LW32, 2 * k * k, st));
+  OTM_TRY(gemm_nn_small(V_B, nb, k, LW32 + k * k, k, W_B, nullptr, nullptr, 0.0, st));
+  OTM_TRY(gemm_nn_small(U_C, nc, k, LW32, k, W_C, nullptr, nullptr, 0.0, st));
 
   return check_flags(flags, st, "otm_whiten_community");
 }
