@@ -280,6 +280,61 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
                           void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched form: many independent decompositions in one persistent launch   */
+/* (not in the paper)                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* One decomposition problem (symmetric views); all pointers are device
+ * pointers.  Its `restarts` independent chains start from V[r * k * k ...]
+ * (restart r, k x k, component-contiguous) and are updated in place. */
+typedef struct otm_problem {
+  int64_t n, k, b, epochs;   /* samples, components (1..128), minibatch, epochs */
+  const void* Yq;            /* n x ldq samples from otm_quantize_samples */
+  const float* scales;       /* per-sample scales or NULL */
+  const int32_t* perm;       /* epochs x n sample orders or NULL */
+  const double* ybar3;       /* 3 x k means (the same mean three times) */
+  float* V;                  /* restarts x k x k, in/out */
+  int64_t restarts;
+  double beta0, theta, alpha0;
+} otm_problem;
+
+/* A prepared batch: filled by otm_sgd_batched_prepare, read by the launch. */
+typedef struct otm_batch_plan {
+  int32_t nitems;     /* chains = sum of restarts */
+  int32_t cluster;    /* CTAs per chain chosen by the autotuner (or given) */
+  int32_t precision;
+  int32_t max_k;
+  int32_t grid_clusters;  /* clusters in the persistent grid */
+  int32_t reserved;
+  int64_t smem_bytes;
+  void* ws;
+  size_t ws_bytes;
+} otm_batch_plan;
+
+/*
+ * otm_sgd_batched_prepare -- expands the problems into chains (one per
+ * restart), orders them by cost (steps x (b k^2 + k^3), longest first) and
+ * uploads the work list to the workspace (otm_sgd_batched_workspace(chains)
+ * bytes, kept alive until the last launch).  cluster = 0 runs the autotuner:
+ * a short trial launch (at most 4 steps per chain, on scratch V) for each
+ * cluster size whose shared-memory footprint fits the largest k; the fastest
+ * is kept (cached per precision, largest k and chain count).  Synchronises
+ * the stream.  Each chain runs the Lemma 3 schedule of otm_sgd_run_lp.
+ *
+ * otm_sgd_batched_launch -- ONE persistent launch running every chain of the
+ * plan: as many clusters as fit on the GPU take chains from the work list
+ * until it is empty.  Asynchronous and free of host synchronisation, so it can
+ * be captured in a CUDA graph.  otm_sgd_batched_check reads the plan's
+ * timeout flag (synchronises; OTM_ETIMEOUT if a tensor-core wait expired).
+ */
+size_t otm_sgd_batched_workspace(int64_t nitems);
+otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int precision,
+                                   int cluster, void* ws, size_t ws_bytes, otm_batch_plan* plan,
+                                   void* stream);
+otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream);
+otm_status otm_sgd_batched_check(const otm_batch_plan* plan, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Post-processing (Section 3.3, Lemma 4) and error evaluation               */
 /* ------------------------------------------------------------------------ */
 

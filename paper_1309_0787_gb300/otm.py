@@ -33,6 +33,23 @@ class OtmCsr(ctypes.Structure):
 
 _P = ctypes.POINTER(OtmCsr)
 
+
+class OtmProblem(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("k", c_i64), ("b", c_i64), ("epochs", c_i64), ("Yq", c_vp),
+                ("scales", c_vp), ("perm", c_vp), ("ybar3", c_vp), ("V", c_vp),
+                ("restarts", c_i64), ("beta0", c_f64), ("theta", c_f64), ("alpha0", c_f64)]
+
+
+class OtmBatchPlan(ctypes.Structure):
+    _fields_ = [("nitems", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_k", ctypes.c_int32),
+                ("grid_clusters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("smem_bytes", c_i64), ("ws", c_vp), ("ws_bytes", c_sz)]
+
+
+_PP = ctypes.POINTER(OtmProblem)
+_BP = ctypes.POINTER(OtmBatchPlan)
+
 # entry point -> argument types (every entry returns int status unless listed below)
 _SIGS = {
     "otm_version": [],
@@ -62,6 +79,11 @@ _SIGS = {
     "otm_sgd_run_lp_workspace": [],
     "otm_sgd_run_lp": [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64,
                        c_i64, c_f64, c_f64, c_f64, ctypes.c_int, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_sgd_batched_workspace": [c_i64],
+    "otm_sgd_batched_prepare": [_PP, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_vp, c_sz, _BP,
+                                c_vp],
+    "otm_sgd_batched_launch": [_BP, c_vp],
+    "otm_sgd_batched_check": [_BP, c_vp],
     "otm_unwhiten_workspace": [c_i64, c_i64, c_i64],
     "otm_unwhiten": [c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_f64, ctypes.c_int, c_vp, c_vp,
                      c_vp, c_vp, c_sz, c_vp],
@@ -342,6 +364,57 @@ def sgd_run_lp(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, th
                                int(precision), int(snapshot_every), _ptr(snaps), _ptr(ws),
                                ws.numel(), _stream()))
     return snaps
+
+
+class SgdBatch:
+    """Many independent tensor-core STGD chains in one persistent launch.
+
+    problems: list of dicts with keys Yq, scales (from quantize_samples), ybar3
+    (3 x k float64), V (restarts x k x k float32, updated in place), perm
+    (epochs x n int32 or None), epochs, b, beta0, theta, alpha0.  The
+    referenced tensors must stay alive while the batch is used.  ``launch()``
+    is asynchronous and capturable in a CUDA graph; ``check()`` synchronises
+    and raises if a device wait timed out."""
+
+    def __init__(self, problems, precision: int, cluster: int = 0):
+        arr = (OtmProblem * len(problems))()
+        dev = None
+        for i, p in enumerate(problems):
+            V = p["V"]
+            r, k, k2 = V.shape
+            if k != k2:
+                raise ValueError("V must be restarts x k x k")
+            n = p["Yq"].shape[0]
+            _need(V, torch.float32, (r, k, k), "V")
+            _need(p["ybar3"], torch.float64, (3, k), "ybar3")
+            if p.get("perm") is not None:
+                _need(p["perm"], torch.int32, (p["epochs"], n), "perm")
+            arr[i] = OtmProblem(n, k, int(p["b"]), int(p["epochs"]), _ptr(p["Yq"]),
+                                _ptr(p.get("scales")), _ptr(p.get("perm")), _ptr(p["ybar3"]),
+                                _ptr(V), r, float(p["beta0"]), float(p["theta"]),
+                                float(p["alpha0"]))
+            dev = V.device
+        nitems = sum(int(p["V"].shape[0]) for p in problems)
+        self.ws = _ws(_lib.otm_sgd_batched_workspace(nitems), dev)
+        self.plan = OtmBatchPlan()
+        self._problems = arr
+        _check(_lib.otm_sgd_batched_prepare(arr, len(problems), int(precision), int(cluster),
+                                            _ptr(self.ws), self.ws.numel(),
+                                            ctypes.byref(self.plan), _stream()))
+
+    @property
+    def cluster(self) -> int:
+        return int(self.plan.cluster)
+
+    @property
+    def nitems(self) -> int:
+        return int(self.plan.nitems)
+
+    def launch(self) -> None:
+        _check(_lib.otm_sgd_batched_launch(ctypes.byref(self.plan), _stream()))
+
+    def check(self) -> None:
+        _check(_lib.otm_sgd_batched_check(ctypes.byref(self.plan), _stream()))
 
 
 def unwhiten(V, Q, Cp, theta: float, normalize: bool) -> dict:
