@@ -141,6 +141,26 @@ size_t otm_syev_workspace(int64_t n);
 otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, void* ws,
                     size_t ws_bytes, void* stream);
 
+/*
+ * otm_syev_noalloc -- otm_syev without a caller workspace, for callers that
+ * cannot allocate device memory (a host whose framework's memory pool owns the
+ * GPU, an interface that passes only data pointers, or a loop that must not
+ * call cudaMalloc / cudaFree because they synchronise the device).  The paper
+ * has no counterpart: this is a packaging of the same eigendecomposition.
+ * Arguments and results are those of otm_syev; n must be at most 160
+ * (OTM_EINVAL with a message otherwise).
+ * Scratch: a fixed 2 MiB array inside the library, present on every GPU on
+ * which the library is loaded until the process exits.  The call allocates
+ * nothing.  The first call on a device looks up the array's address on that
+ * device (the current device; `stream` must belong to it); make that first
+ * call before any stream capture begins.  All calls on one device share the
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and give wrong results, so serialise them.  Synchronises the
+ * stream.
+ */
+otm_status otm_syev_noalloc(const double* A, int64_t n, double* evals, double* evecs,
+                            void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Whitening (Section 3.1, Section 4.2)                                     */
 /* ------------------------------------------------------------------------ */

@@ -64,6 +64,7 @@ _SIGS = {
     "otm_orthonormalize": [c_vp, c_i64, c_i64, c_vp, c_sz, c_vp],
     "otm_syev_workspace": [c_i64],
     "otm_syev": [c_vp, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp],
+    "otm_syev_noalloc": [c_vp, c_i64, c_vp, c_vp, c_vp],
     "otm_whiten_topic_workspace": [c_i64, c_i64, c_i64, c_i64],
     "otm_whiten_topic": [_P, c_vp, c_i64, c_i64, ctypes.c_int, c_f64, c_vp, c_vp, c_vp, c_vp,
                          c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
@@ -227,6 +228,17 @@ def syev(A):
     ws = _ws(_lib.otm_syev_workspace(n), A.device)
     _check(_lib.otm_syev(_ptr(A), n, _ptr(ev), _ptr(vec), _ptr(ws), ws.numel(), _stream()))
     return ev, vec
+
+
+def syev_noalloc(A, evals, evecs) -> None:
+    """otm_syev_noalloc: the library allocates nothing (scratch is a fixed
+    array inside it, n <= 160); the caller provides the outputs evals (n,
+    float64) and evecs (n x n, float64)."""
+    n = A.shape[0]
+    _need(A, torch.float64, (n, n), "A")
+    _need(evals, torch.float64, (n,), "evals")
+    _need(evecs, torch.float64, (n, n), "evecs")
+    _check(_lib.otm_syev_noalloc(_ptr(A), n, _ptr(evals), _ptr(evecs), _stream()))
 
 
 def whiten_topic(X: DeviceCSR, S, k: int, power_iters: int, alpha0: float) -> dict:
