@@ -12,7 +12,10 @@ when U recovers the components.  Test infrastructure only.
 
 MLP: x (4 k^2) -> GELU(W1 x + b1) (512) -> GELU(W2 h1 + b2) (512) -> W3 h2 + b3
 (k^2, read row-major as the k x k matrix M whose columns are Gram-Schmidt'ed).
-GELU(z) = z Phi(z) (exact, Phi the standard normal CDF).
+GELU(z) = z Phi(z) (exact, Phi the standard normal CDF).  The input is the
+concatenated sketches scaled to unit root-mean-square (mlp_input).  Training:
+the batch-mean loss, its gradient through Gram-Schmidt and the MLP, and Adam
+(Kingma & Ba 2015, Algorithm 1).
 """
 from __future__ import annotations
 
@@ -25,7 +28,8 @@ from .stgd import kappa, whitened_tensor
 
 __all__ = ["sketch", "sketches", "gelu", "gelu_grad", "init_params", "mlp_forward",
            "mlp_backward", "gram_schmidt", "gram_schmidt_backward", "tensor_eval",
-           "warmstart_loss", "warmstart_loss_grad", "initial_components"]
+           "warmstart_loss", "warmstart_loss_grad", "initial_components", "mlp_input",
+           "adam_step", "batch_loss_and_grad", "infer"]
 
 
 def sketch(T: np.ndarray, theta: np.ndarray) -> np.ndarray:
@@ -125,3 +129,42 @@ def initial_components(U0: np.ndarray, T: np.ndarray, theta: float) -> np.ndarra
     t = np.einsum("abc,ai,bi,ci->i", T, U0, U0, U0)
     s = np.where(t < 0, -1.0, 1.0)
     return (U0 * s) * (np.abs(t) / kappa(theta)) ** (1.0 / 3.0)
+
+
+def mlp_input(S: np.ndarray) -> np.ndarray:
+    """Network input of one instance: vec(S_1, ..., S_J) (row-major) scaled so
+    that its root-mean-square is 1."""
+    x = np.asarray(S, dtype=np.float64).reshape(-1)
+    return x * math.sqrt(x.size) / np.linalg.norm(x)
+
+
+def adam_step(p, g, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1); returns (p, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def batch_loss_and_grad(params: dict, X: np.ndarray, Ustar: np.ndarray, lam: np.ndarray,
+                        k: int):
+    """Batch-mean warm-start loss of the network outputs and its parameter
+    gradient.  X: B x d_in inputs, Ustar: B x k x k (columns u*_i), lam: B x k."""
+    out, cache = mlp_forward(X, params)
+    B = X.shape[0]
+    dout = np.zeros_like(out)
+    loss = 0.0
+    for b in range(B):
+        U, R = gram_schmidt(out[b].reshape(k, k))
+        loss += warmstart_loss(U, lam[b], Ustar[b]) / B
+        dU = warmstart_loss_grad(U, lam[b], Ustar[b])
+        dout[b] = gram_schmidt_backward(U, R, dU).reshape(-1) / B
+    return loss, mlp_backward(dout, params, cache)
+
+
+def infer(params: dict, X: np.ndarray, k: int) -> np.ndarray:
+    """Orthonormal initial directions U0 (B x k x k, columns) for inputs X."""
+    out, _ = mlp_forward(X, params)
+    return np.stack([gram_schmidt(o.reshape(k, k))[0] for o in out])

@@ -20,6 +20,15 @@ Generators:
   * :func:`haar_orthonormal`    -- Haar-random orthonormal k x k matrix (the
                                    random initial components of the SGD).
   * :func:`epoch_permutations`  -- per-epoch sample orders for the SGD.
+  * :func:`whitened_lda_instances` / :func:`whitened_lda_samples` --
+                                   decomposition instances of an exact-mixture
+                                   LDA model drawn directly in whitened
+                                   coordinates (training and evaluation data
+                                   of the learned warm start).  The samples
+                                   come from a counter-based generator
+                                   (:func:`philox4x32`, Marsaglia-Tsang gamma
+                                   draws) that the CUDA library implements
+                                   from the same published definitions.
 
 All generators use NumPy's PCG64 bit generator seeded with the given integer,
 so both sides see bit-identical inputs.
@@ -31,6 +40,8 @@ import numpy as np
 __all__ = [
     "rng", "CSR", "lda_corpus", "mmsb_graph", "orthogonal_samples", "gaussian",
     "haar_orthonormal", "epoch_permutations", "csr_from_dense", "csr_to_dense",
+    "philox4x32", "bits_to_unit", "whitened_lda_instances", "whitened_lda_samples",
+    "unit_vectors",
 ]
 
 
@@ -190,3 +201,138 @@ def epoch_permutations(seed: int, n: int, epochs: int) -> np.ndarray:
     """epochs x n int32 array; row e is the sample order of epoch e."""
     g = rng(seed)
     return np.stack([g.permutation(n) for _ in range(epochs)]).astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+# "Parallel random numbers: as easy as 1, 2, 3", SC 2011).
+# ---------------------------------------------------------------------------
+_PHILOX_M0 = np.uint64(0xD2511F53)
+_PHILOX_M1 = np.uint64(0xCD9E8D57)
+_PHILOX_W0 = np.uint32(0x9E3779B9)
+_PHILOX_W1 = np.uint32(0xBB67AE85)
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32(c0, c1, c2, c3, k0, k1, rounds: int = 10):
+    """Philox4x32 with `rounds` rounds on uint32 counters (arrays broadcast)
+    and a 2 x 32-bit key.  Returns the four uint32 output words."""
+    c = [np.asarray(x, dtype=np.uint32) for x in np.broadcast_arrays(c0, c1, c2, c3)]
+    k0 = np.uint32(k0)
+    k1 = np.uint32(k1)
+    with np.errstate(over="ignore"):
+        for r in range(rounds):
+            if r > 0:
+                k0 = np.uint32(k0 + _PHILOX_W0)
+                k1 = np.uint32(k1 + _PHILOX_W1)
+            p0 = _PHILOX_M0 * c[0].astype(np.uint64)
+            p1 = _PHILOX_M1 * c[2].astype(np.uint64)
+            hi0 = (p0 >> np.uint64(32)).astype(np.uint32)
+            lo0 = (p0 & _MASK32).astype(np.uint32)
+            hi1 = (p1 >> np.uint64(32)).astype(np.uint32)
+            lo1 = (p1 & _MASK32).astype(np.uint32)
+            c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]
+    return c
+
+
+def bits_to_unit(x) -> np.ndarray:
+    """uint32 -> float32 uniform strictly inside (0, 1): ((x >> 9) + 0.5) * 2^-23
+    (every step exact in float32)."""
+    return ((np.asarray(x, dtype=np.uint32) >> np.uint32(9)).astype(np.float32)
+            + np.float32(0.5)) * np.float32(2.0 ** -23)
+
+
+# Marsaglia-Tsang attempts per gamma draw; after that many rejections (a
+# probability below 1e-20) the draw takes the mode-like value d.
+GAMMA_ATTEMPTS = 16
+
+
+def _log_gamma_draws(alpha: np.ndarray, t: np.ndarray, c: np.ndarray, inst: int, key):
+    """log of Gamma(alpha_c) draws for samples t (vector) and components c,
+    Marsaglia & Tsang, "A simple method for generating gamma variables"
+    (ACM TOMS 2000), with the alpha < 1 boost G(a) = G(a + 1) U^(1/a).
+    Counter (t, c, instance, attempt), key (seed lo, seed hi).  float32."""
+    f = np.float32
+    T, C = np.meshgrid(t.astype(np.uint32), c.astype(np.uint32), indexing="ij")
+    a = alpha.astype(np.float32)[None, :] * np.ones_like(T, dtype=np.float32)
+    small = a < f(1)
+    ab = np.where(small, a + f(1), a).astype(np.float32)
+    d = (ab - f(1.0 / 3.0)).astype(np.float32)
+    cc = (f(1) / np.sqrt(f(9) * d)).astype(np.float32)
+    logg = np.log(d).astype(np.float32)          # fallback value log(d)
+    done = np.zeros(T.shape, dtype=bool)
+    boost_u = None
+    for att in range(GAMMA_ATTEMPTS):
+        r = philox4x32(T, C, np.uint32(inst), np.uint32(att), key[0], key[1])
+        if att == 0:
+            boost_u = bits_to_unit(r[3])
+        u1 = bits_to_unit(r[0])
+        u2 = bits_to_unit(r[1])
+        x = (np.sqrt(f(-2) * np.log(u1)) * np.cos(f(2 * np.pi) * u2)).astype(np.float32)
+        v = (f(1) + cc * x).astype(np.float32)
+        ok = v > f(0)
+        v3 = (v * v * v).astype(np.float32)
+        u = bits_to_unit(r[2])
+        with np.errstate(invalid="ignore", divide="ignore"):
+            lv3 = np.log(np.where(ok, v3, f(1))).astype(np.float32)
+            acc = ok & (np.log(u) < f(0.5) * x * x + d - d * v3 + d * lv3)
+        new = acc & ~done
+        logg = np.where(new, (np.log(d) + lv3).astype(np.float32), logg)
+        done |= acc
+        if done.all():
+            break
+    logg = np.where(small, logg + np.log(boost_u) / a, logg).astype(np.float32)
+    return logg
+
+
+def unit_vectors(seed: int, count: int, k: int) -> np.ndarray:
+    """count x k random unit vectors (float32), e.g. the sketch directions."""
+    g = rng(seed).standard_normal((count, k))
+    return (g / np.linalg.norm(g, axis=1, keepdims=True)).astype(np.float32)
+
+
+def whitened_lda_instances(seed: int, nb: int, k: int, alpha0_range=(0.5, 2.0),
+                           concentration: float = 4.0) -> dict:
+    """Parameters of nb exact-mixture LDA instances in whitened coordinates.
+
+    Per instance: alpha0 ~ U[alpha0_range], alpha = alpha0 * pi with
+    pi ~ Dir(concentration * 1_k), U* Haar-random orthonormal, and the whitened
+    topic vectors m_i = sqrt(alpha0 / alpha_i) u*_i (columns of m).  A sample
+    is y = m h with h ~ Dir(alpha); the Dirichlet moment identities then give
+    (alpha0 + 1) E[y y^T] - alpha0 ybar ybar^T = I and a whitened third moment
+    sum_i lam_i u*_i^(x)3 with lam_i = sqrt(alpha0 / alpha_i).
+    """
+    g = rng(seed)
+    a0 = g.uniform(alpha0_range[0], alpha0_range[1], size=nb)
+    pi = g.dirichlet(np.full(k, concentration), size=nb)
+    alpha = a0[:, None] * pi
+    U = np.stack([_haar(g, k) for _ in range(nb)])
+    lam = np.sqrt(a0[:, None] / alpha)
+    m = U * lam[:, None, :]
+    return {"alpha0": a0, "alpha": alpha, "U": U, "lam": lam,
+            "m": m.astype(np.float32), "alpha32": alpha.astype(np.float32)}
+
+
+def whitened_lda_samples(inst: dict, n: int, seed: int, first: int = 0,
+                         count: int | None = None) -> np.ndarray:
+    """Samples y_t = m h_t, h_t ~ Dir(alpha) of instances first .. first+count-1
+    (count x n x k float32) from the counter-based generator: counter (t, c,
+    instance, attempt), key (seed lo, seed hi); h = exp(L - max L) / sum exp(L
+    - max L) with L the log-gamma draws; y accumulated in float32 in component
+    order."""
+    nb = inst["m"].shape[0] if count is None else count
+    k = inst["m"].shape[1]
+    key = (np.uint32(seed & 0xFFFFFFFF), np.uint32((seed >> 32) & 0xFFFFFFFF))
+    out = np.empty((nb, n, k), dtype=np.float32)
+    t = np.arange(n, dtype=np.uint32)
+    c = np.arange(k, dtype=np.uint32)
+    for j in range(nb):
+        i = first + j
+        L = _log_gamma_draws(inst["alpha32"][i], t, c, i, key)
+        e = np.exp(L - L.max(axis=1, keepdims=True)).astype(np.float32)
+        h = (e / e.sum(axis=1, keepdims=True, dtype=np.float32)).astype(np.float32)
+        y = np.zeros((n, k), dtype=np.float32)
+        for cc in range(k):
+            y = (y + h[:, cc:cc + 1] * inst["m"][i][:, cc][None, :]).astype(np.float32)
+        out[j] = y
+    return out

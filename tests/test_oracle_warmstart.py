@@ -86,3 +86,51 @@ def test_sketch_and_initial_components_on_orthogonal_tensor():
     V0 = ws.initial_components(-Us, T, 1.0)
     Vs = (lam / stgd.kappa(1.0)) ** (1 / 3) * Us
     np.testing.assert_allclose(V0, Vs, atol=1e-12)
+
+
+def test_batch_loss_and_grad_finite_differences():
+    """The composite training gradient (MLP -> Gram-Schmidt -> loss, batch
+    mean) equals central differences of the composite loss."""
+    k, B = 3, 2
+    p = ws.init_params(4, 2 * k * k, 6, k * k)
+    g = np.random.default_rng(5)
+    X = g.standard_normal((B, 2 * k * k))
+    Us = np.stack([np.linalg.qr(g.standard_normal((k, k)))[0] for _ in range(B)])
+    lam = g.uniform(0.5, 2.0, (B, k))
+    _, grads = ws.batch_loss_and_grad(p, X, Us, lam, k)
+    for key in ("W1", "b2", "W3"):
+        def f(v, key=key):
+            q = dict(p)
+            q[key] = v
+            return ws.batch_loss_and_grad(q, X, Us, lam, k)[0]
+        np.testing.assert_allclose(grads[key], _fd(f, p[key]), rtol=1e-5, atol=1e-8)
+
+
+def test_adam_matches_first_steps_by_hand():
+    """Adam's bias correction: the first step moves every coordinate by
+    lr * sign(g) (up to eps), the second by lr * mh / sqrt(vh) written out."""
+    p = np.array([1.0, -2.0, 0.5])
+    g1 = np.array([0.3, -4.0, 1e-3])
+    p1, m, v = ws.adam_step(p, g1, np.zeros(3), np.zeros(3), 1, 0.01)
+    np.testing.assert_allclose(p1, p - 0.01 * np.sign(g1), atol=1e-7)
+    g2 = np.array([-0.1, 2.0, 1e-3])
+    p2, _, _ = ws.adam_step(p1, g2, m, v, 2, 0.01)
+    mh = (0.9 * 0.1 * g1 + 0.1 * g2) / (1 - 0.81)
+    vh = (0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2) / (1 - 0.999 ** 2)
+    np.testing.assert_allclose(p2, p1 - 0.01 * mh / (np.sqrt(vh) + 1e-8), rtol=1e-12)
+
+
+def test_mlp_input_unit_rms():
+    S = np.random.default_rng(6).standard_normal((4, 5, 5)) * 7.0
+    x = ws.mlp_input(S)
+    assert x.shape == (100,)
+    np.testing.assert_allclose(np.sqrt((x ** 2).mean()), 1.0, rtol=1e-12)
+    np.testing.assert_allclose(x / x[0], S.reshape(-1) / S.reshape(-1)[0], rtol=1e-12)
+
+
+def test_infer_orthonormal_columns():
+    k = 4
+    p = ws.init_params(7, 8, 6, k * k)
+    U0 = ws.infer(p, np.random.default_rng(8).standard_normal((3, 8)), k)
+    for U in U0:
+        np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-12)
