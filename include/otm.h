@@ -355,6 +355,164 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream);
 otm_status otm_sgd_batched_check(const otm_batch_plan* plan, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Learned warm start (not in the paper)                                     */
+/* ------------------------------------------------------------------------ */
+/*
+ * A small MLP maps J <= 4 sketches of the whitened tensor of Section 3.2,
+ * S_j = T(I, I, theta_j) (k x k each, k <= 64), to an initial component
+ * matrix.  The network is x -> GELU(W1 x + b1) -> GELU(W2 h1 + b2) -> W3 h2 + b3
+ * (exact GELU z Phi(z)), x = vec(S_1..S_J) scaled to unit root-mean-square;
+ * its output (k^2) is read row-major as a k x k matrix M whose columns are
+ * orthonormalised by Gram-Schmidt (U0 = GS(M)); v_i = sign(t_i) (|t_i| /
+ * kappa)^(1/3) u_i with t_i = T(u_i, u_i, u_i) (the stationary scaling of
+ * Lemma 3).  Training minimises the batch mean of
+ *   L(U) = - sum_i T*(u_i, u_i, u_i)^2 / sum_j lam_j^2,
+ * T* = sum_j lam_j u*_j^(x)3 the instance's known decomposition, with Adam
+ * (Kingma & Ba 2015).  Weights are FP32 masters with BF16 copies; the dense
+ * products run on tcgen05 tensor cores with FP32 accumulation.
+ * Matrices of one instance are k x k row-major (U[a * k + i] = entry a of
+ * column u_i) unless stated; batches are contiguous.
+ */
+
+/* Network descriptor; every buffer is caller-owned device memory.
+ * d_in, width, d_out: multiples of 8 (d_in = J k^2, d_out = k^2).
+ * Parameter order (otm_mlp_param_count elements): W1 (width x d_in, row-major),
+ * b1 (width), W2 (width x width), b2, W3 (d_out x width), b3 (d_out). */
+typedef struct otm_mlp {
+  int64_t d_in, width, d_out;
+  float* p;        /* FP32 master parameters */
+  void* p16;       /* BF16 copy of p (same order) */
+  void* w2t16;     /* BF16 W2^T (width x width) */
+  void* w3t16;     /* BF16 W3^T (width x d_out) */
+  float* grad;     /* FP32 gradient (same order as p), written by the backward pass */
+  float* adam_m;   /* Adam first and second moments (same order; zero before step 1) */
+  float* adam_v;
+} otm_mlp;
+
+int64_t otm_mlp_param_count(int64_t d_in, int64_t width, int64_t d_out);
+
+/* Refresh p16, w2t16 and w3t16 from p (after the caller writes p). */
+otm_status otm_mlp_sync_weights(const otm_mlp* net, void* stream);
+
+/*
+ * otm_mlp_forward -- out (batch x d_out, FP32) for BF16 inputs x16 (batch x
+ * d_in); batch a multiple of 8.  Leaves the activations in ws for
+ * otm_mlp_backward.  otm_mlp_backward -- net->grad from dL/d(out) (batch x
+ * d_out, FP32) and the cache of the preceding forward call on the same ws.
+ * Scratch: otm_mlp_workspace(net, batch) bytes.
+ */
+size_t otm_mlp_workspace(const otm_mlp* net, int64_t batch);
+otm_status otm_mlp_forward(const otm_mlp* net, const void* x16, int64_t batch, float* out,
+                           void* ws, size_t ws_bytes, void* stream);
+otm_status otm_mlp_backward(const otm_mlp* net, const void* x16, int64_t batch, const float* dout,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* One Adam update of p from grad (step t >= 1), then the BF16 copies. */
+otm_status otm_adam_step(const otm_mlp* net, double lr, double b1, double b2, double eps, int64_t t,
+                         void* stream);
+
+/*
+ * otm_gram_schmidt -- M (nb x k x k) = U R column by column (classical
+ * Gram-Schmidt applied twice per column, FP32); R upper triangular with
+ * positive diagonal.  otm_gram_schmidt_backward -- dL/dM = (dU + U
+ * copyltu(-dU^T U)) R^{-T}, copyltu(A) = tril(A) + tril(A, -1)^T.
+ * otm_ws_loss_grad -- loss[b] = L(U_b) and dU = scale * dL/dU
+ * (column i = -6 T*(u_i,u_i,u_i) T*(u_i,u_i,I) / sum lam^2); Ustar nb x k x k
+ * (columns u*_j), lam nb x k.  k <= 64.
+ */
+otm_status otm_gram_schmidt(const float* M, int64_t nb, int64_t k, float* U, float* R,
+                            void* stream);
+otm_status otm_gram_schmidt_backward(const float* U, const float* R, const float* dU, int64_t nb,
+                                     int64_t k, float* dM, void* stream);
+otm_status otm_ws_loss_grad(const float* U, const float* Ustar, const float* lam, int64_t nb,
+                            int64_t k, double scale, float* loss, float* dU, void* stream);
+
+/*
+ * otm_ws_train_step -- forward, Gram-Schmidt, loss (loss[b] per instance,
+ * FP32), backward through Gram-Schmidt and the MLP (dL/dout scaled by
+ * 1/batch: the gradient of the batch mean), then Adam step t with learning
+ * rate lr (b1 = 0.9, b2 = 0.999, eps = 1e-8).  otm_ws_infer -- U0 (batch x k x k)
+ * = GS(MLP(x16)).  Scratch of both: otm_ws_train_workspace(net, batch).
+ * Asynchronous; otm_ws_check(ws) reports a timed-out tensor-core wait.
+ */
+size_t otm_ws_train_workspace(const otm_mlp* net, int64_t batch);
+otm_status otm_ws_train_step(const otm_mlp* net, const void* x16, const float* Ustar,
+                             const float* lam, int64_t batch, int64_t k, double lr, int64_t t,
+                             float* loss, void* ws, size_t ws_bytes, void* stream);
+otm_status otm_ws_infer(const otm_mlp* net, const void* x16, int64_t batch, int64_t k, float* U0,
+                        void* ws, size_t ws_bytes, void* stream);
+otm_status otm_ws_check(const void* ws, void* stream);
+
+/*
+ * otm_ws_sketch -- J sketches S_j = T(I, I, theta_j) of the symmetric whitened
+ * tensor of Section 3.2 per instance, from samples Y (nb x n x k) with the
+ * instance's alpha0 (nb, host-order device array):
+ *   S = c1 P - c2 <theta,ybar> Q - c2 (m ybar^T + ybar m^T) + c3 <theta,ybar> ybar ybar^T,
+ *   Q = Y^T Y / n, P = Y^T diag(Y theta) Y / n, m = Q theta.
+ * Q and P_j are BF16 tensor-core products with FP32 accumulation.
+ * thetas: J x k; S (optional): nb x J x k x k FP32; x16: nb x J k^2 BF16
+ * network inputs (unit root-mean-square).  Scratch: otm_ws_sketch_workspace.
+ */
+size_t otm_ws_sketch_workspace(int64_t nb, int64_t n, int64_t k, int J);
+otm_status otm_ws_sketch(const float* Y, int64_t nb, int64_t n, int64_t k, const double* alpha0,
+                         const float* thetas, int J, float* S, void* x16, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/*
+ * otm_ws_canonicalize -- the canonical frame of each instance: E (nb x k x k,
+ * columns) = eigenvectors of the symmetric part of S_1 (cyclic Jacobi, FP32),
+ * ordered by descending eigenvalue (evals, nb x k, optional) with each
+ * vector's largest-magnitude entry positive; x16 (nb x J k^2, BF16) =
+ * vec(E^T S_j E) scaled to unit root-mean-square.  S: nb x J x k x k.
+ * otm_ws_rotate -- out = E U (transpose = 0) or E^T U (transpose = 1) per
+ * instance (out must not alias U).  k <= 64.
+ */
+otm_status otm_ws_canonicalize(const float* S, int64_t nb, int64_t k, int J, float* E,
+                               float* evals, void* x16, void* stream);
+otm_status otm_ws_rotate(const float* E, const float* U, int64_t nb, int64_t k, int transpose,
+                         float* out, void* stream);
+
+/*
+ * otm_ws_init_components -- V0 (nb x k x k, component i contiguous, the STGD
+ * layout) from orthonormal directions U0 (nb x k x k, columns) and samples Y:
+ * v_i = sign(t_i) (|t_i| / kappa)^(1/3) u_i, kappa = (1 + theta) / 2,
+ * t_i = c1 E[(y.u_i)^3] - 3 c2 E[(y.u_i)^2] (ybar.u_i) + c3 (ybar.u_i)^3.
+ * Scratch: otm_ws_init_workspace(nb, n, k).
+ */
+size_t otm_ws_init_workspace(int64_t nb, int64_t n, int64_t k);
+otm_status otm_ws_init_components(const float* U0, const float* Y, int64_t nb, int64_t n,
+                                  int64_t k, const double* alpha0, double theta, float* V0,
+                                  void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * otm_ws_generate -- samples of exact-mixture LDA instances in whitened
+ * coordinates (training and evaluation data): y_t = m h_t, h_t ~ Dir(alpha)
+ * for instances first .. first + nb - 1.  m: nb x k x k (row-major, column i
+ * the whitened topic vector sqrt(alpha0/alpha_i) u*_i), alpha: nb x k, Y: nb x
+ * n x k.  Gamma draws by Marsaglia & Tsang (ACM TOMS 2000) on Philox4x32-10
+ * counters (t, c, instance, attempt) with key seed (Salmon et al., SC 2011);
+ * h = exp(L - max L) / sum exp(L - max L) from the log-gamma draws L.
+ */
+otm_status otm_ws_generate(const float* m, const float* alpha, int64_t nb, int64_t n, int64_t k,
+                           uint64_t seed, int64_t first, float* Y, void* stream);
+
+/*
+ * otm_gemm_bf16 -- C[z] = alpha A[z] B[z]^T for z < batch on the tensor cores
+ * (tcgen05, TMA-fed, FP32 accumulation).  A: M x K, B: N x K, BF16 row-major
+ * with leading dimensions lda, ldb and batch strides (elements); K, lda, ldb
+ * and the strides multiples of 8, A and B 16-byte aligned.  epilogue 0: C
+ * (FP32, ldc, strideC; optional) and H (BF16, ldh, strideH; optional) =
+ * result; 1: result + bias[col]; 2: C = result + bias, H = GELU(C).  Scratch:
+ * otm_gemm_bf16_workspace() bytes (its first int is set if a wait timed out).
+ */
+size_t otm_gemm_bf16_workspace(void);
+otm_status otm_gemm_bf16(const void* A, const void* B, int64_t M, int64_t N, int64_t K,
+                         int64_t batch, int64_t lda, int64_t ldb, int64_t strideA, int64_t strideB,
+                         int epilogue, float alpha, const float* bias, float* C, int64_t ldc,
+                         int64_t strideC, void* H, int64_t ldh, int64_t strideH, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Post-processing (Section 3.3, Lemma 4) and error evaluation               */
 /* ------------------------------------------------------------------------ */
 

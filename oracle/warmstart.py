@@ -15,7 +15,11 @@ MLP: x (4 k^2) -> GELU(W1 x + b1) (512) -> GELU(W2 h1 + b2) (512) -> W3 h2 + b3
 GELU(z) = z Phi(z) (exact, Phi the standard normal CDF).  The input is the
 concatenated sketches scaled to unit root-mean-square (mlp_input).  Training:
 the batch-mean loss, its gradient through Gram-Schmidt and the MLP, and Adam
-(Kingma & Ba 2015, Algorithm 1).
+(Kingma & Ba 2015, Algorithm 1).  The network works in a canonical frame: the
+eigenvectors E of the first sketch (canonical_frame); its input is the
+sketches E^T S_j E and its output directions are rotated back by E, so the
+map it learns does not depend on the arbitrary orientation of the whitened
+coordinates.
 """
 from __future__ import annotations
 
@@ -29,7 +33,8 @@ from .stgd import kappa, whitened_tensor
 __all__ = ["sketch", "sketches", "gelu", "gelu_grad", "init_params", "mlp_forward",
            "mlp_backward", "gram_schmidt", "gram_schmidt_backward", "tensor_eval",
            "warmstart_loss", "warmstart_loss_grad", "initial_components", "mlp_input",
-           "adam_step", "batch_loss_and_grad", "infer"]
+           "adam_step", "batch_loss_and_grad", "infer", "canonical_frame",
+           "canonical_input"]
 
 
 def sketch(T: np.ndarray, theta: np.ndarray) -> np.ndarray:
@@ -168,3 +173,21 @@ def infer(params: dict, X: np.ndarray, k: int) -> np.ndarray:
     """Orthonormal initial directions U0 (B x k x k, columns) for inputs X."""
     out, _ = mlp_forward(X, params)
     return np.stack([gram_schmidt(o.reshape(k, k))[0] for o in out])
+
+
+def canonical_frame(S1: np.ndarray):
+    """Eigenvectors of the symmetric part of S1 (library eigh), ordered by
+    descending eigenvalue, each with its largest-magnitude entry positive."""
+    w, V = np.linalg.eigh(0.5 * (S1 + S1.T))
+    order = np.argsort(-w, kind="stable")
+    E = V[:, order]
+    idx = np.argmax(np.abs(E), axis=0)
+    E = E * np.where(E[idx, np.arange(E.shape[1])] < 0, -1.0, 1.0)
+    return E, w[order]
+
+
+def canonical_input(S: np.ndarray):
+    """Network input in the canonical frame of S[0] and the frame E:
+    mlp_input([E^T S_j E]_j)."""
+    E, _ = canonical_frame(S[0])
+    return mlp_input(np.stack([E.T @ Sj @ E for Sj in S])), E

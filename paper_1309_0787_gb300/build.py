@@ -18,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libotm.so")
-HEADERS = [os.path.join(SRC, "otm_internal.cuh"),
-           os.path.join(os.path.dirname(HERE), "include", "otm.h")]
+HEADERS = [os.path.join(SRC, f) for f in sorted(os.listdir(SRC)) if f.endswith(".cuh")] + [
+    os.path.join(os.path.dirname(HERE), "include", "otm.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -122,4 +122,15 @@ otm_status whitening_factors(const double* evals, const double* evecs, int64_t n
 
 // ---- whitening composites (whiten.cu) ----
 
+// ---- tensor-core GEMM (gemm_tc.cu) ----
+// C[z] = alpha A[z] B[z]^T (BF16 row-major operands, K-major; FP32 accumulate).
+// mode 0: C = acc (FP32, optional) and H = bf16(acc) (optional);
+// mode 1: as 0 with + bias[col]; mode 2: C = acc + bias (pre-activation, optional),
+// H = bf16(GELU(C)).  K, lda, ldb, batch strides multiples of 8.  *err is set
+// non-zero if a device wait timed out.
+otm_status gemm_bf16_nt(const void* A, const void* B, int64_t M, int64_t N, int64_t K,
+                        int64_t batch, int64_t lda, int64_t ldb, int64_t sA, int64_t sB, int mode,
+                        float alpha, const float* bias, float* C, int64_t ldc, int64_t sC, void* H,
+                        int64_t ldh, int64_t sH, int* err, cudaStream_t st);
+
 }  // namespace otm

@@ -35,6 +35,7 @@
 #include <cuda_fp8.h>
 
 #include "otm_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -47,84 +48,7 @@ constexpr int TC_THREADS = 256;  // 8 warps: 2 warps per 32-lane TMEM quarter
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int TC_KMAX = 128;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t sdesc(const void* base, uint32_t lbo, uint32_t sbo) {
-  const uint32_t a = smem_u32(base);
-  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t amaj, uint32_t bmaj,
-                                                  uint32_t M, uint32_t N) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | (amaj << 15) | (bmaj << 16) | ((N >> 3) << 17) |
-         ((M >> 4) << 24);
-}
-
-template <bool FP8>
-__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
-                                    uint32_t acc) {
-  if constexpr (FP8) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-      smem_u32(mbar)));
-}
-
-// Bounded wait on an mbarrier phase (about a second); false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < (1u << 24) && !done; ++it) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(phase));
-  }
-  return done != 0;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
-
-// Quantise 16 FP32 values into one 16-byte core row (8 bf16 = 16 B covers only
-// 8 values, so BF16 writes two rows; see the callers).
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-__device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d) {
-  const __nv_fp8x4_e4m3 q(make_float4(a, b, c, d));
-  return *reinterpret_cast<const uint32_t*>(&q);
-}
+using namespace tc;
 
 struct TcArgs {
   const uint8_t* YA;  // quantised samples, row stride ldq elements

@@ -47,6 +47,13 @@ class OtmBatchPlan(ctypes.Structure):
                 ("smem_bytes", c_i64), ("ws", c_vp), ("ws_bytes", c_sz)]
 
 
+class OtmMlp(ctypes.Structure):
+    _fields_ = [("d_in", c_i64), ("width", c_i64), ("d_out", c_i64), ("p", c_vp), ("p16", c_vp),
+                ("w2t16", c_vp), ("w3t16", c_vp), ("grad", c_vp), ("adam_m", c_vp),
+                ("adam_v", c_vp)]
+
+
+_MP = ctypes.POINTER(OtmMlp)
 _PP = ctypes.POINTER(OtmProblem)
 _BP = ctypes.POINTER(OtmBatchPlan)
 
@@ -85,6 +92,33 @@ _SIGS = {
                                 c_vp],
     "otm_sgd_batched_launch": [_BP, c_vp],
     "otm_sgd_batched_check": [_BP, c_vp],
+    "otm_mlp_param_count": [c_i64, c_i64, c_i64],
+    "otm_mlp_sync_weights": [_MP, c_vp],
+    "otm_mlp_workspace": [_MP, c_i64],
+    "otm_mlp_forward": [_MP, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_mlp_backward": [_MP, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_adam_step": [_MP, c_f64, c_f64, c_f64, c_f64, c_i64, c_vp],
+    "otm_gram_schmidt": [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp],
+    "otm_gram_schmidt_backward": [c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp],
+    "otm_ws_loss_grad": [c_vp, c_vp, c_vp, c_i64, c_i64, c_f64, c_vp, c_vp, c_vp],
+    "otm_ws_train_workspace": [_MP, c_i64],
+    "otm_ws_train_step": [_MP, c_vp, c_vp, c_vp, c_i64, c_i64, c_f64, c_i64, c_vp, c_vp, c_sz,
+                          c_vp],
+    "otm_ws_infer": [_MP, c_vp, c_i64, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_ws_check": [c_vp, c_vp],
+    "otm_ws_canonicalize": [c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp, c_vp, c_vp],
+    "otm_ws_rotate": [c_vp, c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp],
+    "otm_ws_sketch_workspace": [c_i64, c_i64, c_i64, ctypes.c_int],
+    "otm_ws_sketch": [c_vp, c_i64, c_i64, c_i64, c_vp, c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_sz,
+                      c_vp],
+    "otm_ws_init_workspace": [c_i64, c_i64, c_i64],
+    "otm_ws_init_components": [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_f64, c_vp, c_vp, c_sz,
+                               c_vp],
+    "otm_ws_generate": [c_vp, c_vp, c_i64, c_i64, c_i64, ctypes.c_uint64, c_i64, c_vp, c_vp],
+    "otm_gemm_bf16_workspace": [],
+    "otm_gemm_bf16": [c_vp, c_vp, c_i64, c_i64, c_i64, c_i64, c_i64, c_i64, c_i64, c_i64,
+                      ctypes.c_int, ctypes.c_float, c_vp, c_vp, c_i64, c_i64, c_vp, c_i64, c_i64,
+                      c_vp, c_sz, c_vp],
     "otm_unwhiten_workspace": [c_i64, c_i64, c_i64],
     "otm_unwhiten": [c_vp, c_i64, c_vp, c_i64, c_i64, c_vp, c_f64, ctypes.c_int, c_vp, c_vp,
                      c_vp, c_vp, c_sz, c_vp],
@@ -92,7 +126,7 @@ _SIGS = {
     "otm_recon_error": [c_vp, c_i64, c_f64, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
 }
 _RESTYPE = {"otm_last_error": ctypes.c_char_p, "otm_version": ctypes.c_int,
-            "otm_launch_count": ctypes.c_uint64}
+            "otm_launch_count": ctypes.c_uint64, "otm_mlp_param_count": c_i64}
 
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -427,6 +461,203 @@ class SgdBatch:
 
     def check(self) -> None:
         _check(_lib.otm_sgd_batched_check(ctypes.byref(self.plan), _stream()))
+
+
+# ---- learned warm start -------------------------------------------------
+
+def gemm_bf16(A, B, epilogue: int = 0, alpha: float = 1.0, bias=None, want_c: bool = True,
+              want_h: bool = False):
+    """C = alpha A B^T (+ bias, GELU) for BF16 A (batch x M x K or M x K) and B
+    (batch x N x K or N x K).  Returns (C float32 or None, H bfloat16 or None)."""
+    batched = A.dim() == 3
+    A3 = A if batched else A.unsqueeze(0)
+    B3 = B if batched else B.unsqueeze(0)
+    nb, M, K = A3.shape
+    N = B3.shape[1]
+    _need(A3, torch.bfloat16, (nb, M, K), "A")
+    _need(B3, torch.bfloat16, (nb, N, K), "B")
+    C = torch.empty(nb, M, N, dtype=torch.float32, device=A.device) if want_c else None
+    H = torch.empty(nb, M, N, dtype=torch.bfloat16, device=A.device) if want_h else None
+    ws = _ws(_lib.otm_gemm_bf16_workspace(), A.device)
+    _check(_lib.otm_gemm_bf16(_ptr(A3), _ptr(B3), M, N, K, nb, K, K, M * K, N * K, int(epilogue),
+                              float(alpha), _ptr(bias), _ptr(C), N, M * N, _ptr(H), N, M * N,
+                              _ptr(ws), ws.numel(), _stream()))
+    _check(_lib.otm_ws_check(_ptr(ws), _stream()))
+    if not batched:
+        C = None if C is None else C[0]
+        H = None if H is None else H[0]
+    return C, H
+
+
+def gram_schmidt(M):
+    nb, k, _ = M.shape
+    _need(M, torch.float32, (nb, k, k), "M")
+    U = torch.empty_like(M)
+    R = torch.empty_like(M)
+    _check(_lib.otm_gram_schmidt(_ptr(M), nb, k, _ptr(U), _ptr(R), _stream()))
+    return U, R
+
+
+def gram_schmidt_backward(U, R, dU):
+    nb, k, _ = U.shape
+    for t, nm in ((U, "U"), (R, "R"), (dU, "dU")):
+        _need(t, torch.float32, (nb, k, k), nm)
+    dM = torch.empty_like(U)
+    _check(_lib.otm_gram_schmidt_backward(_ptr(U), _ptr(R), _ptr(dU), nb, k, _ptr(dM), _stream()))
+    return dM
+
+
+def ws_loss_grad(U, Ustar, lam, scale: float = 1.0):
+    nb, k, _ = U.shape
+    _need(U, torch.float32, (nb, k, k), "U")
+    _need(Ustar, torch.float32, (nb, k, k), "Ustar")
+    _need(lam, torch.float32, (nb, k), "lam")
+    loss = torch.empty(nb, dtype=torch.float32, device=U.device)
+    dU = torch.empty_like(U)
+    _check(_lib.otm_ws_loss_grad(_ptr(U), _ptr(Ustar), _ptr(lam), nb, k, float(scale), _ptr(loss),
+                                 _ptr(dU), _stream()))
+    return loss, dU
+
+
+def ws_generate(m, alpha, n: int, seed: int, first: int = 0):
+    """Samples (nb x n x k float32) of whitened exact-mixture LDA instances."""
+    nb, k, _ = m.shape
+    _need(m, torch.float32, (nb, k, k), "m")
+    _need(alpha, torch.float32, (nb, k), "alpha")
+    Y = torch.empty(nb, n, k, dtype=torch.float32, device=m.device)
+    _check(_lib.otm_ws_generate(_ptr(m), _ptr(alpha), nb, int(n), k, int(seed), int(first),
+                                _ptr(Y), _stream()))
+    return Y
+
+
+def ws_sketch(Y, alpha0, thetas, want_s: bool = True):
+    """(S: nb x J x k x k float32 or None, x16: nb x J k^2 bfloat16)."""
+    nb, n, k = Y.shape
+    J = thetas.shape[0]
+    _need(Y, torch.float32, (nb, n, k), "Y")
+    _need(alpha0, torch.float64, (nb,), "alpha0")
+    _need(thetas, torch.float32, (J, k), "thetas")
+    S = torch.empty(nb, J, k, k, dtype=torch.float32, device=Y.device) if want_s else None
+    x16 = torch.empty(nb, J * k * k, dtype=torch.bfloat16, device=Y.device)
+    ws = _ws(_lib.otm_ws_sketch_workspace(nb, n, k, J), Y.device)
+    _check(_lib.otm_ws_sketch(_ptr(Y), nb, n, k, _ptr(alpha0), _ptr(thetas), J, _ptr(S), _ptr(x16),
+                              _ptr(ws), ws.numel(), _stream()))
+    _check(_lib.otm_ws_check(_ptr(ws), _stream()))
+    return S, x16
+
+
+def ws_canonicalize(S):
+    """(E: nb x k x k, evals: nb x k, x16: nb x J k^2 bfloat16) of the sketches
+    S (nb x J x k x k)."""
+    nb, J, k, _ = S.shape
+    _need(S, torch.float32, (nb, J, k, k), "S")
+    E = torch.empty(nb, k, k, dtype=torch.float32, device=S.device)
+    ev = torch.empty(nb, k, dtype=torch.float32, device=S.device)
+    x16 = torch.empty(nb, J * k * k, dtype=torch.bfloat16, device=S.device)
+    _check(_lib.otm_ws_canonicalize(_ptr(S), nb, k, J, _ptr(E), _ptr(ev), _ptr(x16), _stream()))
+    return E, ev, x16
+
+
+def ws_rotate(E, U, transpose: bool = False):
+    nb, k, _ = E.shape
+    _need(E, torch.float32, (nb, k, k), "E")
+    _need(U, torch.float32, (nb, k, k), "U")
+    out = torch.empty_like(U)
+    _check(_lib.otm_ws_rotate(_ptr(E), _ptr(U), nb, k, int(bool(transpose)), _ptr(out), _stream()))
+    return out
+
+
+def ws_init_components(U0, Y, alpha0, theta: float):
+    nb, n, k = Y.shape
+    _need(U0, torch.float32, (nb, k, k), "U0")
+    _need(alpha0, torch.float64, (nb,), "alpha0")
+    V0 = torch.empty(nb, k, k, dtype=torch.float32, device=Y.device)
+    ws = _ws(_lib.otm_ws_init_workspace(nb, n, k), Y.device)
+    _check(_lib.otm_ws_init_components(_ptr(U0), _ptr(Y), nb, n, k, _ptr(alpha0), float(theta),
+                                       _ptr(V0), _ptr(ws), ws.numel(), _stream()))
+    return V0
+
+
+class Mlp:
+    """Warm-start network: FP32 master parameters (same order as
+    otm_mlp_param_count), BF16 copies, gradient and Adam moments on the GPU."""
+
+    def __init__(self, d_in: int, width: int, d_out: int, params, device="cuda"):
+        self.d_in, self.width, self.d_out = d_in, width, d_out
+        P = int(_lib.otm_mlp_param_count(d_in, width, d_out))
+        self.p = torch.as_tensor(params, dtype=torch.float32).reshape(-1).to(device).contiguous()
+        if self.p.numel() != P:
+            raise ValueError(f"expected {P} parameters, got {self.p.numel()}")
+        self.p16 = torch.empty(P, dtype=torch.bfloat16, device=device)
+        self.w2t16 = torch.empty(width * width, dtype=torch.bfloat16, device=device)
+        self.w3t16 = torch.empty(width * d_out, dtype=torch.bfloat16, device=device)
+        self.grad = torch.zeros(P, dtype=torch.float32, device=device)
+        self.m = torch.zeros(P, dtype=torch.float32, device=device)
+        self.v = torch.zeros(P, dtype=torch.float32, device=device)
+        self.t = 0
+        self.desc = OtmMlp(d_in, width, d_out, _ptr(self.p), _ptr(self.p16), _ptr(self.w2t16),
+                           _ptr(self.w3t16), _ptr(self.grad), _ptr(self.m), _ptr(self.v))
+        self._ws = {}
+        _check(_lib.otm_mlp_sync_weights(ctypes.byref(self.desc), _stream()))
+
+    def _workspace(self, kind: str, batch: int):
+        key = (kind, batch)
+        if key not in self._ws:
+            fn = _lib.otm_mlp_workspace if kind == "mlp" else _lib.otm_ws_train_workspace
+            self._ws[key] = _ws(fn(ctypes.byref(self.desc), batch), self.p.device)
+        return self._ws[key]
+
+    def forward(self, x16):
+        B = x16.shape[0]
+        _need(x16, torch.bfloat16, (B, self.d_in), "x16")
+        out = torch.empty(B, self.d_out, dtype=torch.float32, device=x16.device)
+        ws = self._workspace("mlp", B)
+        _check(_lib.otm_mlp_forward(ctypes.byref(self.desc), _ptr(x16), B, _ptr(out), _ptr(ws),
+                                    ws.numel(), _stream()))
+        return out
+
+    def backward(self, x16, dout):
+        """net.grad from dL/dout; uses the cache of the last forward(x16)."""
+        B = x16.shape[0]
+        _need(dout, torch.float32, (B, self.d_out), "dout")
+        ws = self._workspace("mlp", B)
+        _check(_lib.otm_mlp_backward(ctypes.byref(self.desc), _ptr(x16), B, _ptr(dout), _ptr(ws),
+                                     ws.numel(), _stream()))
+        _check(_lib.otm_ws_check(_ptr(ws), _stream()))
+        return self.grad
+
+    def adam(self, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+        self.t += 1
+        _check(_lib.otm_adam_step(ctypes.byref(self.desc), float(lr), float(b1), float(b2),
+                                  float(eps), self.t, _stream()))
+
+    def train_step(self, x16, Ustar, lam, k: int, lr: float):
+        """One training step; returns the per-instance losses (device)."""
+        B = x16.shape[0]
+        _need(x16, torch.bfloat16, (B, self.d_in), "x16")
+        _need(Ustar, torch.float32, (B, k, k), "Ustar")
+        _need(lam, torch.float32, (B, k), "lam")
+        loss = torch.empty(B, dtype=torch.float32, device=x16.device)
+        ws = self._workspace("train", B)
+        self.t += 1
+        _check(_lib.otm_ws_train_step(ctypes.byref(self.desc), _ptr(x16), _ptr(Ustar), _ptr(lam),
+                                      B, k, float(lr), self.t, _ptr(loss), _ptr(ws), ws.numel(),
+                                      _stream()))
+        return loss
+
+    def infer(self, x16, k: int):
+        B = x16.shape[0]
+        _need(x16, torch.bfloat16, (B, self.d_in), "x16")
+        U0 = torch.empty(B, k, k, dtype=torch.float32, device=x16.device)
+        ws = self._workspace("train", B)
+        _check(_lib.otm_ws_infer(ctypes.byref(self.desc), _ptr(x16), B, k, _ptr(U0), _ptr(ws),
+                                 ws.numel(), _stream()))
+        return U0
+
+    def check(self, batch: int) -> None:
+        for key, ws in self._ws.items():
+            if key[1] == batch:
+                _check(_lib.otm_ws_check(_ptr(ws), _stream()))
 
 
 def unwhiten(V, Q, Cp, theta: float, normalize: bool) -> dict:

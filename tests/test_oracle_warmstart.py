@@ -134,3 +134,19 @@ def test_infer_orthonormal_columns():
     U0 = ws.infer(p, np.random.default_rng(8).standard_normal((3, 8)), k)
     for U in U0:
         np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-12)
+
+
+def test_canonical_frame_diagonalises_first_sketch():
+    g = np.random.default_rng(9)
+    A = g.standard_normal((6, 6))
+    S = np.stack([A + A.T, g.standard_normal((6, 6))])
+    E, w = ws.canonical_frame(S[0])
+    D = E.T @ S[0] @ E
+    np.testing.assert_allclose(D, np.diag(np.diag(D)), atol=1e-12)
+    np.testing.assert_allclose(np.diag(D), w, atol=1e-12)
+    assert np.all(np.diff(w) <= 0)
+    idx = np.argmax(np.abs(E), axis=0)
+    assert np.all(E[idx, np.arange(6)] > 0)
+    x, E2 = ws.canonical_input(S)
+    np.testing.assert_array_equal(E, E2)
+    np.testing.assert_allclose(np.linalg.norm(x), np.linalg.norm(ws.mlp_input(S)), rtol=1e-12)
