@@ -1,30 +1,41 @@
 // Precision form of the fused STGD step (Section 3.2, Lemma 3) on the
-// fifth-generation tensor cores.  The two products of the stacked update,
-//   A = Y_b V        (samples x components, K = coordinates; views A and B)
-//   G = Y_C^T B      (coordinates x components, K = samples)
-// run as tcgen05.mma in BF16 (kind::f16) or FP8 e4m3 (kind::f8f6f4) with
-// FP32 accumulators in tensor memory; B = c1 A_A o A_B - c2 (a_B o A_A +
-// a_A o A_B) is formed in registers between them.  The FP32 master V, the
-// Gram term V((V^T V) o (V^T V)), the mean terms and the update stay in FP32
-// as in the FP32 kernel (sgd.cu), and so does the organisation: one
-// thread-block cluster runs all steps, the minibatch is split over its CTAs,
-// partial G are summed column-wise through distributed shared memory, and V
-// never leaves the chip.
+// fifth-generation tensor cores.  Per step, for the components i a CTA owns:
+//   A = Y_b V_own            (samples x owned components, K = coordinates)
+//   B = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B)      (registers)
+//   G_data = Y_C^T B / b + ybar_C (c3 a_A o a_B - c2 s / b)^T
+//   H = V^T V_own,  G_gram = V (H o H)                  (Gram term)
+//   V_own <- V_own - beta_t (kappa G_gram - G_data)
+// Every product runs as tcgen05.mma (BF16: kind::f16; FP8 e4m3: kind::f8f6f4
+// for the two data products) with FP32 accumulators in tensor memory; the
+// master V and all sums stay FP32.
+//
+// Organisation (one thread-block cluster per decomposition): CTA q owns N
+// consecutive components (N a multiple of 16) and streams every sample tile
+// of the minibatch, so no partial product is ever reduced across CTAs.  After
+// its update a CTA writes the BF16 image of its new columns into every CTA's
+// V image (double-buffered, one cluster barrier per step).  Sample tiles
+// arrive by cp.async into a ring of shared-memory stages, up to NS - 1 tiles
+// ahead (across step boundaries); with three or more stages the first product
+// of tile n + 1 is issued before the epilogue of tile n so that its latency
+// is hidden.  One thread issues every MMA; completion is signalled by
+// tcgen05.commit to mbarriers whose waits are bounded.
 //
 // Scaling: samples are stored quantised with one scale per sample (FP8; BF16
-// stores scale 1); V is re-quantised every step with one scale per component;
-// B with one scale per component per 128-sample tile.  Every scale is applied
-// to the FP32 accumulator in the epilogues:
-//   A[t][i] = s_t sigma_i D1[t][i],   G[r][i] = sum over tiles of beta_i D2[r][i].
+// stores scale 1); the owned rows of V are re-quantised every step with one
+// scale per component (FP8); B with one scale per component per 128-sample
+// tile (FP8).  Scales are applied to the FP32 accumulators in the epilogues.
+// The Gram term always uses the BF16 image of V.
 //
 // Operand layouts in shared memory (no swizzle; 8-row x 16-byte core
 // matrices; LBO = stride between cores along K, SBO = along M/N):
 //   sample tile: core (tg, rg) = 8 samples x 16 B of coordinates at
-//                (tg * CR + rg) * 128 with CR = KP * esize / 16; read K-major
-//                (M = samples, K = coordinates) by the first product and
-//                MN-major (M = coordinates, K = samples) by the second;
-//   V image:     core (ng, rg) = 8 components x 16 B of coordinates, K-major;
-//   B image:     core (tg, ng) = 8 samples x 16 B of components, MN-major.
+//                (tg * CR + rg) * 128, CR = KP * esize / 16; read K-major by
+//                the first product and MN-major (M = coordinates) by the second;
+//   V image:     core (ng, rg) = 8 components x 16 B of coordinates (BF16,
+//                128 rows): K-major for A = Y V_own and H = V^T V_own, MN-major
+//                (M = coordinates, K = components) for G_gram = V (H o H);
+//   B image:     core (tg, ng) = 8 samples x 16 B of owned components, MN-major;
+//   H image:     core (jg, ng) = 8 components j x 16 B of owned components.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -42,13 +53,15 @@ namespace cg = cooperative_groups;
 namespace otm {
 namespace {
 
-constexpr int TILE = 128;        // samples per MMA tile (M of the first product)
+using namespace tc;
+
+constexpr int TILE = 128;        // samples per tile (M of the first product)
 constexpr int KP = 128;          // padded coordinates (M of the second product)
-constexpr int TC_THREADS = 256;  // 8 warps: 2 warps per 32-lane TMEM quarter
+constexpr int VROWS = 128;       // rows of the V image (components, zero padded)
+constexpr int TC_THREADS = 256;  // 8 warps: two per 32-lane TMEM quarter
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int TC_KMAX = 128;
-
-using namespace tc;
+constexpr int NMBAR = 5;         // mbarriers: first product x2, second x2, Gram
 
 struct TcArgs {
   const uint8_t* YA;  // quantised samples, row stride ldq elements
@@ -68,449 +81,643 @@ struct TcArgs {
   float c1, c2, c3, kappa;
 };
 
+__host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
+
+// Components per CTA for k and a cluster of cl CTAs.
+__host__ __device__ inline int own_cols(int k, int cl) {
+  return round16((round16(k) + cl - 1) / cl);
+}
+
 struct TcLayout {
-  int np, ldk, cpq, nview, esize, cr, cb;
-  size_t y_bytes, b_bytes, v_bytes;
-  size_t off_b, off_v, off_f;
-  // float offsets inside the FP32 region
-  size_t vm, gd, hm, vn, aA, aB, ybA, ybB, ybC, vsc, bsc, spw, spart, sown, sAt, sBt, sCt,
-      amax, nfloat;
+  int N, nv, NS, es, CR, CRb, CBn, CBh;
+  bool dbl;
+  size_t y_view, y_stage, off_v[2], off_vq, off_b[2], off_h, off_f;
+  size_t vm, ybA, ybB, ybC, aA, aB, vsc, bsc, amax, spw, red, ssc, nfloat;
   size_t total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int k, int CL, bool sym, int esize) {
+__host__ __device__ inline size_t al128(size_t x) { return (x + 127) & ~(size_t)127; }
+
+__host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, bool dbl) {
   TcLayout L;
-  L.np = (k + 15) & ~15;
-  L.ldk = (k + 3) & ~3;
-  L.cpq = (k + CL - 1) / CL;
-  L.nview = sym ? 1 : 3;
-  L.esize = esize;
-  L.cr = KP * esize / 16;
-  L.cb = L.np * esize / 16;
-  L.y_bytes = (size_t)TILE * KP * esize;
-  L.b_bytes = (size_t)TILE * L.np * esize;
-  L.v_bytes = (size_t)L.np * KP * esize;
-  L.off_b = L.y_bytes * L.nview;
-  size_t region = L.off_b + L.b_bytes;
-  const size_t gp = (size_t)L.np * KP * 4;  // partial G (FP32) reuses the sample images
-  if (region < gp) region = gp;
-  L.off_v = (region + 1023) & ~(size_t)1023;
-  L.off_f = (L.off_v + L.v_bytes + 1023) & ~(size_t)1023;
+  L.N = N;
+  L.nv = sym ? 1 : 3;
+  L.NS = NS;
+  L.es = es;
+  L.dbl = dbl;
+  L.CR = KP * es / 16;
+  L.CRb = KP * 2 / 16;
+  L.CBn = N * es / 16;
+  L.CBh = N * 2 / 16;
+  L.y_view = (size_t)TILE * KP * es;
+  L.y_stage = L.nv * L.y_view;
+  const size_t v_bytes = (size_t)VROWS * KP * 2;
+  L.off_v[0] = NS * L.y_stage;
+  L.off_v[1] = dbl ? L.off_v[0] + v_bytes : L.off_v[0];
+  L.off_vq = L.off_v[1] + v_bytes;
+  const size_t vq_bytes = es == 1 ? (size_t)N * KP : 0;
+  const size_t b_bytes = (size_t)TILE * N * es;
+  L.off_b[0] = al128(L.off_vq + vq_bytes);
+  L.off_b[1] = L.off_b[0] + b_bytes;
+  L.off_h = L.off_b[0];  // the H image reuses both B images (free by then)
+  size_t end = L.off_b[1] + b_bytes;
+  const size_t h_bytes = (size_t)VROWS * N * 2;
+  if (L.off_h + h_bytes > end) end = L.off_h + h_bytes;
+  L.off_f = al128(end);
   size_t f = 0;
-  L.vm = f; f += (size_t)k * L.ldk;
-  L.gd = f; f += (size_t)L.cpq * L.ldk;
-  L.hm = f; f += (size_t)L.cpq * L.ldk;
-  L.vn = f; f += (size_t)L.cpq * L.ldk;
-  L.aA = f; f += L.np;
-  L.aB = f; f += L.np;
-  L.ybA = f; f += L.ldk;
-  L.ybB = f; f += L.ldk;
-  L.ybC = f; f += L.ldk;
-  L.vsc = f; f += L.np;
-  L.bsc = f; f += L.np;
-  L.spw = f; f += 4 * (size_t)L.np;
-  L.spart = f; f += L.np;
-  L.sown = f; f += L.cpq + 4;
-  L.sAt = f; f += TILE;
-  L.sBt = f; f += TILE;
-  L.sCt = f; f += TILE;
-  L.amax = f; f += L.np;
+  L.vm = f;   f += (size_t)N * KP;
+  L.ybA = f;  f += KP;
+  L.ybB = f;  f += KP;
+  L.ybC = f;  f += KP;
+  L.aA = f;   f += N;
+  L.aB = f;   f += N;
+  L.vsc = f;  f += N;
+  L.bsc = f;  f += 2 * (size_t)N;
+  L.amax = f; f += 2 * (size_t)N;
+  L.spw = f;  f += 4 * (size_t)N;
+  L.red = f;  f += 12 * (size_t)N;
+  L.ssc = f;  f += (size_t)NS * 3 * TILE;
   L.nfloat = f;
   L.total = L.off_f + f * 4 + 64;
   return L;
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most `pending` of this thread's most recent groups are in flight
+__device__ __forceinline__ void cp_async_wait(int pending) {
+  switch (pending) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+  }
+}
+__device__ __forceinline__ void fence_async_cluster() {
+  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+
 struct TcCtx {
-  uint64_t* mbar;
+  uint64_t* mbar;  // NMBAR barriers
   int* abort;
   uint32_t tmem;
-  uint32_t phase;
+  uint32_t ph;     // phase bits: 0-1 first product slots, 2-3 second, 4 Gram
 };
 
-// One STGD chain (one decomposition) with V on-chip, run by one cluster.
-// TMEM and the mbarrier are set up by the caller; the chain ends with a
-// cluster barrier so that the caller may reuse shared memory afterwards.
-template <bool FP8, bool SYM, int CL>
-__device__ __forceinline__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx) {
+// Sample tile n of step s into ring stage `stage` (cp.async, zero fill outside
+// the minibatch).  Thread tid copies half of sample tid / 2's coordinates.
+template <bool FP8, bool SYM>
+__device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, uint8_t* smem,
+                                          float* F, int64_t s, int n_tile, int stage) {
+  constexpr int ES = FP8 ? 1 : 2;
+  const int tid = threadIdx.x;
+  const int t = tid >> 1, hs = tid & 1;
+  const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
+  const int64_t beff = min(a.b, a.n - pos0);
+  const int64_t p = (int64_t)n_tile * TILE + t;
+  int64_t row = -1;
+  if (p < beff) row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
+  if (row >= a.n) row = -1;
+  const int half = L.CR / 2;
+  uint8_t* Ys = smem + (size_t)stage * L.y_stage;
+  for (int v = 0; v < L.nv; ++v) {
+    const uint8_t* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+    uint8_t* dst = Ys + v * L.y_view + ((size_t)(t >> 3) * L.CR << 7) + ((t & 7) << 4);
+    for (int c = 0; c < half; ++c) {
+      const int rg = hs * half + c;
+      const int c0 = rg * (16 / ES);
+      const bool in = row >= 0 && c0 < a.ldq;
+      const uint8_t* src = in ? Yg + ((size_t)row * a.ldq + c0) * ES : Yg;
+      cp_async16(dst + ((size_t)rg << 7), src, in ? 16u : 0u);
+    }
+    if (hs == 0) {
+      const float* sv = v == 0 ? a.sA : (v == 1 ? a.sB : a.sC);
+      F[L.ssc + ((size_t)stage * 3 + v) * TILE + t] = row >= 0 ? (sv ? sv[row] : 1.f) : 0.f;
+    }
+  }
+  cp_async_commit();
+}
+
+// One STGD chain (one decomposition), run by one cluster; TMEM and the
+// mbarriers are set up by the caller.  Ends with a cluster barrier so that the
+// caller may reuse shared memory afterwards.
+template <bool FP8, bool SYM>
+__device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool dbl) {
   constexpr int ES = FP8 ? 1 : 2;
   constexpr int KSTEP = FP8 ? 32 : 16;            // K of one MMA
   constexpr uint32_t FMT = FP8 ? 0u : 1u;         // E4M3 / BF16
   constexpr float QMAX = FP8 ? 448.f : 1.f;
+  constexpr int NVD = SYM ? 1 : 2;                // views through the first product
   cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
   const int q = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int quad = warp & 3, half = warp >> 2;
+  const int qd = warp & 3, hf = warp >> 2;
   const int k = a.k;
-  const TcLayout L = tc_layout(k, CL, SYM, ES);
-  const int np = L.np, ldk = L.ldk, cpq = L.cpq, CR = L.cr, CB = L.cb;
-  uint8_t* Yimg = smem;                        // nview x y_bytes
-  uint8_t* Bimg = smem + L.off_b;
-  uint8_t* Vimg = smem + L.off_v;
-  float* Gp = reinterpret_cast<float*>(smem);  // np x KP, after the last product
+  const int N = own_cols(k, CL);
+  const TcLayout L = tc_layout(N, SYM, ES, NS, dbl);
+  const int own_lo = q * N;
+  const bool active = own_lo < k;
+  const int nch = N / 16;
   float* F = reinterpret_cast<float*>(smem + L.off_f);
   float* Vm = F + L.vm;
-  float* gd = F + L.gd;
-  float* Hm = F + L.hm;
-  float* vn = F + L.vn;
-  float* aA = F + L.aA;
-  float* aB = F + L.aB;
   float* ybA = F + L.ybA;
   float* ybB = F + L.ybB;
   float* ybC = F + L.ybC;
+  float* aA = F + L.aA;
+  float* aB = F + L.aB;
   float* vsc = F + L.vsc;
   float* bsc = F + L.bsc;
-  float* spw = F + L.spw;
-  float* spart = F + L.spart;
-  float* sown = F + L.sown;
-  float* sAt = F + L.sAt;
-  float* sBt = F + L.sBt;
-  float* sCt = F + L.sCt;
   unsigned* amax = reinterpret_cast<unsigned*>(F + L.amax);
-  uint64_t& mbar = *cx.mbar;
+  float* spw = F + L.spw;
+  float* red = F + L.red;
+  uint8_t* Vimg0 = smem + L.off_v[0];
+  uint8_t* Vimg1 = smem + L.off_v[1];
+  uint8_t* Vq = smem + L.off_vq;
+  uint8_t* Bimg0 = smem + L.off_b[0];
+  uint8_t* Bimg1 = smem + L.off_b[1];
+  uint8_t* Himg = smem + L.off_h;
+  uint64_t* mb = cx.mbar;
   int& s_abort = *cx.abort;
+  const uint32_t tmem = cx.tmem;
+  uint32_t ph = cx.ph;
+  const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+  const uint32_t colD2b = (uint32_t)(2 * NVD * N);
+  const uint32_t colH = 0, colGG = (uint32_t)N;
+  const int ks1 = (k + KSTEP - 1) / KSTEP;  // coordinate steps of the first product
+  const int kg16 = (k + 15) / 16;           // 16-steps of the Gram products
+  const size_t own_off = ((size_t)(own_lo >> 3) * L.CRb) << 7;
 
-  for (int idx = tid; idx < k * ldk; idx += TC_THREADS) {
-    const int i = idx / ldk, r = idx % ldk;
-    Vm[idx] = r < k ? a.V[(int64_t)i * k + r] : 0.f;
+  // ---- initial state: owned FP32 rows, BF16 image of all rows, means ----
+  for (int idx = tid; idx < N * KP; idx += TC_THREADS) {
+    const int i = idx / KP, r = idx % KP, c = own_lo + i;
+    Vm[idx] = (c < k && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
   }
-  for (int r = tid; r < ldk; r += TC_THREADS) {
+  for (int idx = tid; idx < VROWS * L.CRb; idx += TC_THREADS) {
+    const int c = idx / L.CRb, rg = idx % L.CRb;
+    float v[8];
+#pragma unroll
+    for (int z = 0; z < 8; ++z) {
+      const int r = rg * 8 + z;
+      v[z] = (c < k && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
+    }
+    uint4 w;
+    w.x = pack_bf16(v[0], v[1]);
+    w.y = pack_bf16(v[2], v[3]);
+    w.z = pack_bf16(v[4], v[5]);
+    w.w = pack_bf16(v[6], v[7]);
+    const size_t off = (((size_t)(c >> 3) * L.CRb + rg) << 7) + ((c & 7) << 4);
+    *reinterpret_cast<uint4*>(Vimg0 + off) = w;
+    if (dbl) *reinterpret_cast<uint4*>(Vimg1 + off) = w;
+  }
+  for (int r = tid; r < KP; r += TC_THREADS) {
     ybA[r] = r < k ? (float)a.ybar3[r] : 0.f;
     ybB[r] = r < k ? (float)a.ybar3[k + r] : 0.f;
     ybC[r] = r < k ? (float)a.ybar3[2 * k + r] : 0.f;
   }
+  for (int i = tid; i < 2 * N; i += TC_THREADS) amax[i] = 0u;
   __syncthreads();
-  const uint32_t tmem = cx.tmem;
-  const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-  const uint32_t colA = 0, colB = SYM ? 0 : 128, colG = 256;
-  const int own_lo = q * cpq, own_hi = min(k, own_lo + cpq);
-  const int64_t bq = (a.b + CL - 1) / CL;
-  const int nchunk = np / 16;
-  uint32_t phase = cx.phase;
+  for (int i = warp; i < N; i += TC_THREADS / 32) {
+    float x = 0.f, y = 0.f, m = 0.f;
+    for (int r = lane; r < KP; r += 32) {
+      const float v = Vm[i * KP + r];
+      x = fmaf(v, ybA[r], x);
+      y = fmaf(v, ybB[r], y);
+      m = fmaxf(m, fabsf(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      aA[i] = x;
+      aB[i] = y;
+      vsc[i] = FP8 ? (m > 0.f ? m / QMAX : 1.f) : 1.f;
+    }
+  }
+  __syncthreads();
 
+  // FP8: owned rows of V quantised with one scale per component (K-major)
+  auto build_vq = [&]() {
+    for (int idx = tid; idx < N * L.CR; idx += TC_THREADS) {
+      const int i = idx / L.CR, rg = idx % L.CR;
+      const float inv = 1.f / vsc[i];
+      const float* vr = Vm + i * KP + rg * 16;
+      uint4 w;
+      w.x = pack_e4m3(vr[0] * inv, vr[1] * inv, vr[2] * inv, vr[3] * inv);
+      w.y = pack_e4m3(vr[4] * inv, vr[5] * inv, vr[6] * inv, vr[7] * inv);
+      w.z = pack_e4m3(vr[8] * inv, vr[9] * inv, vr[10] * inv, vr[11] * inv);
+      w.w = pack_e4m3(vr[12] * inv, vr[13] * inv, vr[14] * inv, vr[15] * inv);
+      *reinterpret_cast<uint4*>(Vq + (((size_t)(i >> 3) * L.CR + rg) << 7) + ((i & 7) << 4)) = w;
+    }
+  };
+  if (FP8) build_vq();
+  fence_async_smem();
+  cluster.sync();
+
+  // bounded mbarrier wait by every thread (phases tracked identically)
+  auto wait_mb = [&](int idx) {
+    if (!mbar_wait_or_abort(&mb[idx], (ph >> idx) & 1u, &s_abort) && lane == 0) {
+      s_abort = 1;
+      atomicExch(a.err, 1);
+    }
+    ph ^= 1u << idx;
+    tc_after();
+  };
+
+  // ---- tile loader: the global sequence of (step, tile), NS - 1 ahead ----
+  int64_t ld_s = 0;
+  int ld_n = 0;
+  int64_t issued = 0;
+  auto tiles_of = [&](int64_t s) {
+    const int64_t pos0 = (s % a.spe) * a.b;
+    return (int)((min(a.b, a.n - pos0) + TILE - 1) / TILE);
+  };
+  auto issue_one = [&]() {
+    if (ld_s >= a.total_steps) return;
+    load_tile<FP8, SYM>(a, L, smem, F, ld_s, ld_n, (int)(issued % NS));
+    ++issued;
+    if (++ld_n >= tiles_of(ld_s)) {
+      ld_n = 0;
+      ++ld_s;
+    }
+  };
+  auto wait_tile = [&](int64_t g) {
+    const int64_t pend = issued - 1 - g;
+    cp_async_wait(pend < 0 ? 0 : (pend > 3 ? 3 : (int)pend));
+    fence_async_smem();
+    tc_before();
+    __syncthreads();
+    tc_after();
+  };
+  if (active)
+    for (int i = 0; i < NS - 1; ++i) issue_one();
+
+  int cur = 0;
+  int64_t gbase = 0;
+  const bool early = NS >= 3;
   for (int64_t s = 0; s < a.total_steps; ++s) {
-    const int64_t e = s / a.spe, jb = s % a.spe;
-    const int64_t pos0 = jb * a.b;
+    const int64_t pos0 = (s % a.spe) * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
+    const int nt = (int)((beff + TILE - 1) / TILE);
     const float beta = (float)(a.beta0 / sqrt((double)(s + 1)));
     const float inv_b = 1.f / (float)beff;
+    uint8_t* Vc = cur ? Vimg1 : Vimg0;
+    uint8_t* Vn = dbl ? (cur ? Vimg0 : Vimg1) : Vc;
 
-    // -- per-step: a_A, a_B, V scales, V image --
-    for (int i = warp; i < np; i += TC_THREADS / 32) {
-      float x = 0.f, y = 0.f, m = 0.f;
-      if (i < k)
-        for (int r = lane; r < k; r += 32) {
-          const float v = Vm[i * ldk + r];
-          x = fmaf(v, ybA[r], x);
-          y = fmaf(v, ybB[r], y);
-          m = fmaxf(m, fabsf(v));
-        }
+    if (active) {
+      float spart[8][8];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_xor_sync(0xffffffffu, x, o);
-        y += __shfl_xor_sync(0xffffffffu, y, o);
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      }
-      if (lane == 0) {
-        aA[i] = x;
-        aB[i] = y;
-        vsc[i] = FP8 ? (m > 0.f ? m / QMAX : 1.f) : 1.f;
-        spart[i] = 0.f;
-      }
-      if (lane < 4) spw[lane * np + i] = 0.f;
-    }
-    __syncthreads();
-    // V image: 16-byte core rows of (component i, coordinate group rg)
-    for (int idx = tid; idx < np * CR; idx += TC_THREADS) {
-      const int i = idx / CR, rg = idx % CR;
-      const int r0 = rg * (16 / ES);
-      const float inv = 1.f / vsc[i];
-      float v[16];
+      for (int c = 0; c < 8; ++c)
 #pragma unroll
-      for (int z = 0; z < 16 / ES; ++z) {
-        const int r = r0 + z;
-        v[z] = (i < k && r < k) ? Vm[i * ldk + r] * inv : 0.f;
-      }
-      uint4 w;
-      if constexpr (FP8) {
-        w.x = pack_e4m3(v[0], v[1], v[2], v[3]);
-        w.y = pack_e4m3(v[4], v[5], v[6], v[7]);
-        w.z = pack_e4m3(v[8], v[9], v[10], v[11]);
-        w.w = pack_e4m3(v[12], v[13], v[14], v[15]);
-      } else {
-        w.x = pack_bf16(v[0], v[1]);
-        w.y = pack_bf16(v[2], v[3]);
-        w.z = pack_bf16(v[4], v[5]);
-        w.w = pack_bf16(v[6], v[7]);
-      }
-      *reinterpret_cast<uint4*>(Vimg + ((size_t)((i >> 3) * CR + rg) << 7) + ((i & 7) << 4)) = w;
-    }
+        for (int j = 0; j < 8; ++j) spart[c][j] = 0.f;
+      float gacc[FP8 ? 4 : 1][8];
+#pragma unroll
+      for (int c = 0; c < (FP8 ? 4 : 1); ++c)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gacc[c][j] = 0.f;
 
-    // per-thread accumulators of the second product (this thread's TMEM lane,
-    // chunks c = half, half + 2, ...)
-    float gacc[4][16];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int j = 0; j < 16; ++j) gacc[c][j] = 0.f;
-
-    const int64_t my_lo = (int64_t)q * bq, my_hi = min(beff, my_lo + bq);
-    for (int64_t t0 = my_lo; t0 < my_hi; t0 += TILE) {
-      // -- sample tile(s) into the operand images --
-      for (int idx = tid; idx < TILE * CR; idx += TC_THREADS) {
-        const int t = idx / CR, rg = idx % CR;
-        const int64_t p = t0 + t;
-        int64_t row = p < my_hi ? (a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p) : -1;
-        if (row >= a.n) row = -1;
-        const int c0 = rg * (16 / ES);
-        const size_t off = ((size_t)((t >> 3) * CR + rg) << 7) + ((t & 7) << 4);
-        const bool in = row >= 0 && c0 < a.ldq;
-        const size_t goff = (size_t)row * a.ldq * ES + (size_t)c0 * ES;
-        const uint4 z4 = make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4*>(Yimg + off) =
-            in ? *reinterpret_cast<const uint4*>(a.YA + goff) : z4;
-        if (!SYM) {
-          *reinterpret_cast<uint4*>(Yimg + L.y_bytes + off) =
-              in ? *reinterpret_cast<const uint4*>(a.YB + goff) : z4;
-          *reinterpret_cast<uint4*>(Yimg + 2 * L.y_bytes + off) =
-              in ? *reinterpret_cast<const uint4*>(a.YC + goff) : z4;
-        }
-        if (rg == 0) {
-          sAt[t] = row >= 0 ? (a.sA ? a.sA[row] : 1.f) : 0.f;
-          sBt[t] = row >= 0 ? (a.sB ? a.sB[row] : 1.f) : 0.f;
-          sCt[t] = row >= 0 ? (a.sC ? a.sC[row] : 1.f) : 0.f;
-        }
-        if (FP8 && idx < np) amax[idx] = 0u;
-      }
-      fence_async_smem();
-      tc_before();
-      __syncthreads();
-      tc_after();
-      // -- first product: D1 = Y_tile V^T (K-major operands) --
-      if (tid == 0 && !s_abort) {
-        const uint32_t id1 = make_idesc(FMT, 0, 0, TILE, (uint32_t)np);
-        for (int v = 0; v < (SYM ? 1 : 2); ++v) {
-          const uint8_t* Y = Yimg + v * L.y_bytes;
-          const uint32_t col = v == 0 ? colA : colB;
-          for (int ks = 0; ks < KP / KSTEP; ++ks) {
-            const uint64_t da = sdesc(Y + ks * 256, 128, (uint32_t)CR * 128);
-            const uint64_t db = sdesc(Vimg + ks * 256, 128, (uint32_t)CR * 128);
-            mma<FP8>(tmem + col, da, db, id1, ks > 0 ? 1u : 0u);
+      // first product A = Y V_own of tile n (thread 0)
+      auto gemm1 = [&](int n) {
+        const int slot = n & 1;
+        const uint8_t* Ys = smem + (size_t)((gbase + n) % NS) * L.y_stage;
+        const uint32_t id = make_idesc(FMT, 0, 0, TILE, (uint32_t)N);
+        for (int v = 0; v < NVD; ++v) {
+          const uint8_t* Y = Ys + v * L.y_view;
+          for (int ks = 0; ks < ks1; ++ks) {
+            const uint64_t da = sdesc(Y + ks * 256, 128, (uint32_t)L.CR * 128);
+            const uint64_t db = FP8 ? sdesc(Vq + ks * 256, 128, (uint32_t)L.CR * 128)
+                                    : sdesc(Vc + own_off + ks * 256, 128, (uint32_t)L.CRb * 128);
+            mma<FP8>(tmem + (uint32_t)((slot * NVD + v) * N), da, db, id, ks > 0 ? 1u : 0u);
           }
         }
-        mma_commit(&mbar);
-      }
-      if (!mbar_wait(&mbar, phase) && lane == 0) {
-        s_abort = 1;
-        atomicExch(a.err, 1);
-      }
-      phase ^= 1u;
-      tc_after();
-      // -- epilogue 1: B = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B), per-column s --
-      {
-        const int t = 32 * quad + lane;
-        const float sa = sAt[t], sb = sBt[t], sc = sCt[t];
-        float bv[4][16];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int ch = half + 2 * c;
-          if (ch < nchunk) {
-            float xa[16], xb[16];
-            tmem_ld16(tmem + lane_base + colA + 16 * ch, xa);
-            if (!SYM) tmem_ld16(tmem + lane_base + colB + 16 * ch, xb);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int i = 16 * ch + j;
-              const float va = xa[j] * sa * vsc[i];
-              const float vb = SYM ? va : xb[j] * sb * vsc[i];
-              const float pr = va * vb;
-              bv[c][j] = sc * (a.c1 * pr - a.c2 * (aB[i] * va + aA[i] * vb));
-              float ps = pr;
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
-              if (lane == 0) spw[quad * np + i] += ps;
-              if (FP8) {
-                float m = fabsf(bv[c][j]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                if (lane == 0) atomicMax(&amax[i], __float_as_uint(m));
-              }
-            }
-          }
-        }
-        if (FP8) {
-          __syncthreads();
-          if (tid < np) bsc[tid] = amax[tid] > 0u ? __uint_as_float(amax[tid]) / QMAX : 1.f;
-          __syncthreads();
-        }
-        // B image (MN-major: core (tg, ng) = 8 samples x 16 B of components)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int ch = half + 2 * c;
-          if (ch < nchunk) {
-            float w[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) w[j] = FP8 ? bv[c][j] / bsc[16 * ch + j] : bv[c][j];
-            if constexpr (FP8) {
-              uint4 u;
-              u.x = pack_e4m3(w[0], w[1], w[2], w[3]);
-              u.y = pack_e4m3(w[4], w[5], w[6], w[7]);
-              u.z = pack_e4m3(w[8], w[9], w[10], w[11]);
-              u.w = pack_e4m3(w[12], w[13], w[14], w[15]);
-              *reinterpret_cast<uint4*>(Bimg + ((size_t)((t >> 3) * CB + ch) << 7) +
-                                        ((t & 7) << 4)) = u;
-            } else {
-#pragma unroll
-              for (int hh = 0; hh < 2; ++hh) {
-                uint4 u;
-                u.x = pack_bf16(w[8 * hh + 0], w[8 * hh + 1]);
-                u.y = pack_bf16(w[8 * hh + 2], w[8 * hh + 3]);
-                u.z = pack_bf16(w[8 * hh + 4], w[8 * hh + 5]);
-                u.w = pack_bf16(w[8 * hh + 6], w[8 * hh + 7]);
-                *reinterpret_cast<uint4*>(Bimg + ((size_t)((t >> 3) * CB + 2 * ch + hh) << 7) +
-                                          ((t & 7) << 4)) = u;
-              }
-            }
-          }
-        }
-      }
-      fence_async_smem();
-      tc_before();
-      __syncthreads();
-      tc_after();
-      // -- second product: D2 = Y_C^T B (MN-major operands) --
-      if (tid == 0 && !s_abort) {
-        const uint32_t id2 = make_idesc(FMT, 1, 1, KP, (uint32_t)np);
-        const uint8_t* YC = Yimg + (SYM ? 0 : 2 * L.y_bytes);
+        mma_commit(&mb[slot]);
+      };
+      // second product G += Y_C^T B of tile n (thread 0)
+      auto gemm2 = [&](int n) {
+        const int slot = n & 1;
+        const uint8_t* Ys = smem + (size_t)((gbase + n) % NS) * L.y_stage;
+        const uint8_t* YC = Ys + (SYM ? 0 : 2 * L.y_view);
+        const uint8_t* Bi = slot ? Bimg1 : Bimg0;
+        const uint32_t id = make_idesc(FMT, 1, 1, KP, (uint32_t)N);
+        const uint32_t col = colD2b + (FP8 ? (uint32_t)(slot * N) : 0u);
         for (int ks = 0; ks < TILE / KSTEP; ++ks) {
           const uint64_t da =
-              sdesc(YC + (size_t)ks * (KSTEP / 8) * CR * 128, (uint32_t)CR * 128, 128);
+              sdesc(YC + (size_t)ks * (KSTEP / 8) * L.CR * 128, (uint32_t)L.CR * 128, 128);
           const uint64_t db =
-              sdesc(Bimg + (size_t)ks * (KSTEP / 8) * CB * 128, (uint32_t)CB * 128, 128);
-          mma<FP8>(tmem + colG, da, db, id2, ks > 0 ? 1u : 0u);
+              sdesc(Bi + (size_t)ks * (KSTEP / 8) * L.CBn * 128, (uint32_t)L.CBn * 128, 128);
+          mma<FP8>(tmem + col, da, db, id, (FP8 ? ks > 0 : (n > 0 || ks > 0)) ? 1u : 0u);
         }
-        mma_commit(&mbar);
+        mma_commit(&mb[2 + slot]);
+      };
+      // FP8: per-tile second product, scaled by the tile's B scales
+      auto epi2 = [&](int n) {
+        const int slot = n & 1;
+#pragma unroll
+        for (int c = 0; c < (FP8 ? 4 : 1); ++c) {
+          if (c < nch) {
+            const int c0 = 16 * c + 8 * hf;
+            float x[8];
+            tmem_ld8(tmem + lane_base + colD2b + (uint32_t)(slot * N + c0), x);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) gacc[c][j] = fmaf(x[j], bsc[slot * N + c0 + j], gacc[c][j]);
+          }
+        }
+      };
+
+      if (early) {
+        wait_tile(gbase);
+        if (tid == 0 && !s_abort) gemm1(0);
       }
-      if (!mbar_wait(&mbar, phase) && lane == 0) {
-        s_abort = 1;
-        atomicExch(a.err, 1);
+      for (int n = 0; n < nt; ++n) {
+        const int64_t g = gbase + n;
+        const int slot = n & 1;
+        if (early && n + 1 < nt) {
+          wait_tile(g + 1);
+          if (tid == 0 && !s_abort) gemm1(n + 1);
+        }
+        if (n >= 1) {
+          wait_mb(2 + ((n - 1) & 1));
+          if (FP8) epi2(n - 1);
+        }
+        while (issued <= g + NS - 1 && ld_s < a.total_steps) issue_one();
+        if (!early) {
+          wait_tile(g);
+          if (tid == 0 && !s_abort) gemm1(n);
+        }
+        wait_mb(slot);
+
+        // -- epilogue 1: B = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B) --
+        {
+          const int t = 32 * qd + lane;
+          const float* ss = F + L.ssc + (size_t)(g % NS) * 3 * TILE;
+          const float sa = ss[t], sb = SYM ? sa : ss[TILE + t], sc = SYM ? sa : ss[2 * TILE + t];
+          uint8_t* Bi = slot ? Bimg1 : Bimg0;
+          if (FP8) {
+            // pass 1: B column maxima over the tile (and the sums s_i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              if (c < nch) {
+                const int c0 = 16 * c + 8 * hf;
+                float xa[8], xb[8];
+                tmem_ld8(tmem + lane_base + (uint32_t)(slot * NVD * N + c0), xa);
+                if (!SYM) tmem_ld8(tmem + lane_base + (uint32_t)((slot * NVD + 1) * N + c0), xb);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const int i = c0 + j;
+                  const float va = xa[j] * sa * vsc[i];
+                  const float vb = SYM ? va : xb[j] * sb * vsc[i];
+                  const float pr = va * vb;
+                  spart[c][j] += pr;
+                  float m = fabsf(sc * (a.c1 * pr - a.c2 * (aB[i] * va + aA[i] * vb)));
+#pragma unroll
+                  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                  if (lane == 0) atomicMax(&amax[slot * N + i], __float_as_uint(m));
+                }
+              }
+            }
+            tc_before();
+            __syncthreads();
+            tc_after();
+            if (tid < N) {
+              const unsigned m = amax[slot * N + tid];
+              bsc[slot * N + tid] = m ? __uint_as_float(m) / QMAX : 1.f;
+              amax[slot * N + tid] = 0u;
+            }
+            __syncthreads();
+          }
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (c < nch) {
+              const int c0 = 16 * c + 8 * hf;
+              float xa[8], xb[8];
+              tmem_ld8(tmem + lane_base + (uint32_t)(slot * NVD * N + c0), xa);
+              if (!SYM) tmem_ld8(tmem + lane_base + (uint32_t)((slot * NVD + 1) * N + c0), xb);
+              float w[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int i = c0 + j;
+                const float va = xa[j] * sa * vsc[i];
+                const float vb = SYM ? va : xb[j] * sb * vsc[i];
+                const float pr = va * vb;
+                if (!FP8) spart[c][j] += pr;
+                const float b = sc * (a.c1 * pr - a.c2 * (aB[i] * va + aA[i] * vb));
+                w[j] = FP8 ? b / bsc[slot * N + i] : b;
+              }
+              if constexpr (FP8) {
+                uint2 u;
+                u.x = pack_e4m3(w[0], w[1], w[2], w[3]);
+                u.y = pack_e4m3(w[4], w[5], w[6], w[7]);
+                *reinterpret_cast<uint2*>(Bi + ((((size_t)(t >> 3) * L.CBn + c) << 7) +
+                                                ((t & 7) << 4) + 8 * hf)) = u;
+              } else {
+                uint4 u;
+                u.x = pack_bf16(w[0], w[1]);
+                u.y = pack_bf16(w[2], w[3]);
+                u.z = pack_bf16(w[4], w[5]);
+                u.w = pack_bf16(w[6], w[7]);
+                *reinterpret_cast<uint4*>(Bi + ((((size_t)(t >> 3) * L.CBn + (c0 >> 3)) << 7) +
+                                                ((t & 7) << 4))) = u;
+              }
+            }
+          }
+        }
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        tc_after();
+        if (tid == 0 && !s_abort) gemm2(n);
       }
-      phase ^= 1u;
+      wait_mb(2 + ((nt - 1) & 1));
+      if (FP8) epi2(nt - 1);
+
+      // s_i = sum over the minibatch of A_A o A_B (per owned component)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c < nch) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float v = spart[c][j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) spw[qd * N + 16 * c + 8 * hf + j] = v;
+          }
+        }
+      }
+      // -- Gram term: H = V^T V_own, then G_gram = V (H o H) --
+      tc_before();
+      __syncthreads();
       tc_after();
-      // -- epilogue 2: accumulate beta_i D2[r][i] for this thread's coordinate r --
+      if (tid == 0 && !s_abort) {
+        const uint32_t id = make_idesc(1, 0, 0, VROWS, (uint32_t)N);
+        for (int ks = 0; ks < kg16; ++ks) {
+          const uint64_t da = sdesc(Vc + ks * 256, 128, (uint32_t)L.CRb * 128);
+          const uint64_t db = sdesc(Vc + own_off + ks * 256, 128, (uint32_t)L.CRb * 128);
+          mma<false>(tmem + colH, da, db, id, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(&mb[4]);
+      }
+      wait_mb(4);
+      {
+        const int j = 32 * qd + lane;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int ch = half + 2 * c;
-        if (ch < nchunk) {
-          float x[16];
-          tmem_ld16(tmem + lane_base + colG + 16 * ch, x);
+        for (int c = 0; c < 8; ++c) {
+          if (c < nch) {
+            const int c0 = 16 * c + 8 * hf;
+            float x[8];
+            tmem_ld8(tmem + lane_base + colH + (uint32_t)c0, x);
+            uint4 u;
+            u.x = pack_bf16(x[0] * x[0], x[1] * x[1]);
+            u.y = pack_bf16(x[2] * x[2], x[3] * x[3]);
+            u.z = pack_bf16(x[4] * x[4], x[5] * x[5]);
+            u.w = pack_bf16(x[6] * x[6], x[7] * x[7]);
+            *reinterpret_cast<uint4*>(Himg + ((((size_t)(j >> 3) * L.CBh + (c0 >> 3)) << 7) +
+                                              ((j & 7) << 4))) = u;
+          }
+        }
+      }
+      fence_async_smem();
+      tc_before();
+      __syncthreads();
+      tc_after();
+      if (tid == 0 && !s_abort) {
+        const uint32_t id = make_idesc(1, 1, 1, KP, (uint32_t)N);
+        for (int ks = 0; ks < kg16; ++ks) {
+          const uint64_t da =
+              sdesc(Vc + (size_t)ks * 2 * L.CRb * 128, (uint32_t)L.CRb * 128, 128);
+          const uint64_t db =
+              sdesc(Himg + (size_t)ks * 2 * L.CBh * 128, (uint32_t)L.CBh * 128, 128);
+          mma<false>(tmem + colGG, da, db, id, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(&mb[4]);
+      }
+      wait_mb(4);
+
+      // -- update of the owned columns (thread = coordinate r) --
+      {
+        const int r = 32 * qd + lane;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) gacc[c][j] = fmaf(x[j], FP8 ? bsc[16 * ch + j] : 1.f, gacc[c][j]);
+        for (int c = 0; c < 8; ++c) {
+          if (c < nch) {
+            const int c0 = 16 * c + 8 * hf;
+            float gg[8], gd[8];
+            tmem_ld8(tmem + lane_base + colGG + (uint32_t)c0, gg);
+            if constexpr (FP8) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) gd[j] = gacc[c < 4 ? c : 0][j];
+            } else {
+              tmem_ld8(tmem + lane_base + colD2b + (uint32_t)c0, gd);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int i = c0 + j, comp = own_lo + i;
+              float vnew = 0.f;
+              if (comp < k && r < k) {
+                const float s_i = spw[i] + spw[N + i] + spw[2 * N + i] + spw[3 * N + i];
+                const float gdata =
+                    gd[j] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * s_i * inv_b);
+                vnew = Vm[i * KP + r] - beta * (a.kappa * gg[j] - gdata);
+                Vm[i * KP + r] = vnew;
+              }
+              if (comp < VROWS)
+                *reinterpret_cast<__nv_bfloat16*>(
+                    Vn + ((((size_t)(comp >> 3) * L.CRb + (r >> 3)) << 7) + ((comp & 7) << 4) +
+                          ((r & 7) << 1))) = __float2bfloat16_rn(vnew);
+              float x = vnew * ybA[r], y = vnew * ybB[r], m = fabsf(vnew);
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                y += __shfl_xor_sync(0xffffffffu, y, o);
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+              }
+              if (lane == 0) {
+                red[qd * N + i] = x;
+                red[(4 + qd) * N + i] = y;
+                red[(8 + qd) * N + i] = m;
+              }
+            }
+          }
         }
       }
       tc_before();
-      __syncthreads();  // operand images free for the next tile
+      __syncthreads();
       tc_after();
-    }
-    // partial G to shared memory, column i contiguous: Gp[i * KP + r]
-    {
-      const int r = 32 * quad + lane;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int ch = half + 2 * c;
-        if (ch < nchunk) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) Gp[(16 * ch + j) * KP + r] = gacc[c][j];
+      if (tid < N) {
+        const int i = tid;
+        aA[i] = red[i] + red[N + i] + red[2 * N + i] + red[3 * N + i];
+        aB[i] = red[4 * N + i] + red[5 * N + i] + red[6 * N + i] + red[7 * N + i];
+        const float m = fmaxf(fmaxf(red[8 * N + i], red[9 * N + i]),
+                              fmaxf(red[10 * N + i], red[11 * N + i]));
+        vsc[i] = FP8 ? (m > 0.f ? m / QMAX : 1.f) : 1.f;
+      }
+      if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0) {
+        float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
+        for (int idx = tid; idx < N * k; idx += TC_THREADS) {
+          const int i = idx / k, r = idx % k;
+          if (own_lo + i < k) dst[(int64_t)(own_lo + i) * k + r] = Vm[i * KP + r];
         }
       }
-      for (int i = tid; i < np; i += TC_THREADS)
-        spart[i] = spw[i] + spw[np + i] + spw[2 * np + i] + spw[3 * np + i];
+      __syncthreads();
+      if (FP8) build_vq();
     }
-    cluster.sync();  // partial products of every CTA visible
 
-    // -- owned columns: cluster sums, Gram term, update (FP32) --
-    const int nown = own_hi - own_lo;
-    if (tid < nown) {
-      float part[CL];
-#pragma unroll
-      for (int c = 0; c < CL; ++c) part[c] = cluster.map_shared_rank(spart, c)[own_lo + tid];
-      float ss = 0.f;
-#pragma unroll
-      for (int c = 0; c < CL; ++c) ss += part[c];
-      sown[tid] = ss;
-    }
-    for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
-      const int jj = idx / k, r = idx % k;
-      float part[CL];
-#pragma unroll
-      for (int c = 0; c < CL; ++c) part[c] = cluster.map_shared_rank(Gp, c)[(own_lo + jj) * KP + r];
-      float g = 0.f;
-#pragma unroll
-      for (int c = 0; c < CL; ++c) g += part[c];
-      gd[jj * ldk + r] = g;
-    }
-    for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
-      const int jj = idx / k, j = idx % k;
-      const float* vi = Vm + (own_lo + jj) * ldk;
-      const float* vj = Vm + j * ldk;
-      float h = 0.f;
-      for (int r = 0; r < ldk; r += 4) {
-        const float4 x = *reinterpret_cast<const float4*>(vi + r);
-        const float4 y = *reinterpret_cast<const float4*>(vj + r);
-        h = fmaf(x.x, y.x, h);
-        h = fmaf(x.y, y.y, h);
-        h = fmaf(x.z, y.z, h);
-        h = fmaf(x.w, y.w, h);
+    // -- the new owned rows into every CTA's V image --
+    if (CL > 1) {
+      if (!dbl) cluster.sync();  // single image: every CTA has finished reading it
+      if (active) {
+        for (int idx = tid; idx < N * L.CRb; idx += TC_THREADS) {
+          const int i = idx / L.CRb, rg = idx % L.CRb, comp = own_lo + i;
+          if (comp >= VROWS) continue;
+          const size_t off = (((size_t)(comp >> 3) * L.CRb + rg) << 7) + ((comp & 7) << 4);
+          const uint4 w = *reinterpret_cast<const uint4*>(Vn + off);
+          for (int c = 0; c < CL; ++c)
+            if (c != q) *reinterpret_cast<uint4*>(cluster.map_shared_rank(Vn + off, c)) = w;
+        }
       }
-      Hm[jj * ldk + j] = h * h;
+      fence_async_cluster();
     }
-    __syncthreads();
-    for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
-      const int jj = idx / k, r = idx % k;
-      const int i = own_lo + jj;
-      float g = 0.f;
-      for (int j = 0; j < k; ++j) g = fmaf(Hm[jj * ldk + j], Vm[j * ldk + r], g);
-      const float gdata =
-          gd[jj * ldk + r] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * sown[jj] * inv_b);
-      vn[jj * ldk + r] = Vm[i * ldk + r] - beta * (a.kappa * g - gdata);
-    }
-    cluster.sync();  // every owner's new columns ready; all reads of V and Gp done
-    // pull the new V from the owners
-    for (int idx = tid; idx < k * k; idx += TC_THREADS) {
+    fence_async_smem();
+    cluster.sync();
+    fence_async_smem();
+    if (dbl) cur ^= 1;
+    gbase += nt;
+  }
+  cp_async_wait(0);
+  if (active) {
+    for (int idx = tid; idx < N * k; idx += TC_THREADS) {
       const int i = idx / k, r = idx % k;
-      const int owner = i / cpq, jj = i % cpq;
-      Vm[i * ldk + r] = cluster.map_shared_rank(vn, owner)[jj * ldk + r];
-    }
-    __syncthreads();
-    if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0) {
-      float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
-      for (int idx = tid; idx < nown * k; idx += TC_THREADS) {
-        const int jj = idx / k, r = idx % k;
-        dst[(int64_t)(own_lo + jj) * k + r] = Vm[(own_lo + jj) * ldk + r];
-      }
+      if (own_lo + i < k) a.V[(int64_t)(own_lo + i) * k + r] = Vm[i * KP + r];
     }
   }
-  for (int idx = tid; idx < (own_hi - own_lo) * k; idx += TC_THREADS) {
-    const int jj = idx / k, r = idx % k;
-    a.V[(int64_t)(own_lo + jj) * k + r] = Vm[(own_lo + jj) * ldk + r];
-  }
-  cx.phase = phase;
-  // no CTA may leave (or reuse its shared memory) while others still read it
+  cx.ph = ph;
   cluster.sync();
 }
 
-template <bool FP8, bool SYM, int CL>
 __device__ __forceinline__ void tc_setup(TcCtx& cx, uint64_t* mbar, uint32_t* tmem_base,
                                          int* s_abort) {
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_base)),
-                 "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
+  if (warp == 0) tmem_alloc(tmem_base, TMEM_COLS);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
+    for (int i = 0; i < NMBAR; ++i) mbar_init(&mbar[i], 1);
+    mbar_fence_init();
     *s_abort = 0;
   }
   tc_before();
@@ -519,55 +726,59 @@ __device__ __forceinline__ void tc_setup(TcCtx& cx, uint64_t* mbar, uint32_t* tm
   cx.mbar = mbar;
   cx.abort = s_abort;
   cx.tmem = *tmem_base;
-  cx.phase = 0;
+  cx.ph = 0;
 }
 
-__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+// Frees TMEM; after a timeout, first waits (bounded) for this CTA's MMAs.
+__device__ __forceinline__ void tc_teardown(TcCtx& cx) {
+  if (threadIdx.x == 0 && *cx.abort) {
+    mma_commit(&cx.mbar[4]);
+    mbar_wait(&cx.mbar[4], (cx.ph >> 4) & 1u);
+  }
   tc_before();
   __syncthreads();
-  if ((threadIdx.x >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(cx.tmem, TMEM_COLS);
 }
 
-template <bool FP8, bool SYM, int CL>
-__global__ void __launch_bounds__(TC_THREADS, 1) sgd_tc_kernel(TcArgs a) {
+template <bool FP8, bool SYM>
+__global__ void __launch_bounds__(TC_THREADS, 1) sgd_tc_kernel(TcArgs a, int NS, int dbl) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[NMBAR];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   TcCtx cx;
-  tc_setup<FP8, SYM, CL>(cx, &mbar, &tmem_base, &s_abort);
-  tc_chain<FP8, SYM, CL>(a, smem, cx);
-  tc_teardown(cx.tmem);
+  tc_setup(cx, mbar, &tmem_base, &s_abort);
+  tc_chain<FP8, SYM>(a, smem, cx, NS, dbl != 0);
+  tc_teardown(cx);
 }
 
 // Persistent batched form: every cluster takes (problem, restart) chains from
 // a cost-ordered work list until it is exhausted.  Cluster rank 0 claims the
 // next item with one atomic and broadcasts it through distributed shared memory.
-template <bool FP8, bool SYM, int CL>
-__global__ void __launch_bounds__(TC_THREADS, 1) sgd_tc_batched_kernel(const TcArgs* __restrict__ items,
-                                                                       int nitems, int* counter) {
+template <bool FP8>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    sgd_tc_batched_kernel(const TcArgs* __restrict__ items, int nitems, int* counter, int NS,
+                          int dbl) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[NMBAR];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   __shared__ int s_item;
   cg::cluster_group cluster = cg::this_cluster();
   TcCtx cx;
-  tc_setup<FP8, SYM, CL>(cx, &mbar, &tmem_base, &s_abort);
+  tc_setup(cx, mbar, &tmem_base, &s_abort);
   while (true) {
     if (cluster.block_rank() == 0 && threadIdx.x == 0) {
       const int it = atomicAdd(counter, 1);
-#pragma unroll
-      for (int c = 0; c < CL; ++c) *cluster.map_shared_rank(&s_item, c) = it;
+      for (int c = 0; c < (int)cluster.num_blocks(); ++c) *cluster.map_shared_rank(&s_item, c) = it;
     }
     cluster.sync();
     const int it = s_item;
     if (it >= nitems) break;
     const TcArgs a = items[it];
-    tc_chain<FP8, SYM, CL>(a, smem, cx);
+    tc_chain<FP8, true>(a, smem, cx, NS, dbl != 0);
   }
-  tc_teardown(cx.tmem);
+  tc_teardown(cx);
 }
 
 // quantise rows: FP8 -> per-row scale amax/448; BF16 -> scale 1.  Output row
@@ -598,114 +809,113 @@ __global__ void quantize_rows_kernel(const float* __restrict__ Y, int64_t n, int
   if (lane == 0 && scale) scale[r] = sc;
 }
 
-template <bool FP8, bool SYM, int CL>
-otm_status launch_tc(const TcArgs& args, cudaStream_t st) {
-  const TcLayout L = tc_layout(args.k, CL, SYM, FP8 ? 1 : 2);
-  auto kern = sgd_tc_kernel<FP8, SYM, CL>;
-  OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-  if (CL > 8)
-    OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL, 1, 1);
-  cfg.blockDim = dim3(TC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = L.total;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
-  count_launch();
-  return OTM_OK;
+int max_smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (v <= 0) v = 227 * 1024;
+  }
+  return v;
+}
+
+// Launch shape of one chain: cluster size, owned components per CTA, sample
+// stages, single or double V image, dynamic shared memory.
+struct TcPlan {
+  int CL, N, NS;
+  bool dbl;
+  size_t smem;
+};
+
+// The first configuration (deepest pipeline, double-buffered V image first)
+// whose tensor memory, registers and shared memory fit; false if none does.
+bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
+  const int N = own_cols(k, CL);
+  if (N > 128 || (fp8 && N > 64)) return false;
+  const int nvd = sym ? 1 : 2;
+  if ((2 * nvd + (fp8 ? 2 : 1)) * N > (int)TMEM_COLS) return false;
+  const size_t lim = (size_t)max_smem_optin() - 1024;  // static shared variables
+  const int order[8][2] = {{1, 4}, {1, 3}, {0, 4}, {0, 3}, {1, 2}, {0, 2}, {1, 1}, {0, 1}};
+  for (const auto& o : order) {
+    const bool dbl = o[0] != 0;
+    if (dbl && CL == 1) continue;
+    const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, o[1], dbl);
+    if (L.total <= lim) {
+      *out = {CL, N, o[1], dbl, L.total};
+      return true;
+    }
+  }
+  return false;
+}
+
+// Single chain: the smallest power-of-two cluster giving every CTA at most 16
+// components (more CTAs per chain shorten each step), growing if needed.
+bool tc_plan_single(int k, bool sym, bool fp8, TcPlan* out) {
+  int CL = 1;
+  while (CL < 16 && CL * 16 < round16(k)) CL *= 2;
+  for (; CL <= 16; CL *= 2)
+    if (tc_plan(k, sym, fp8, CL, out)) return true;
+  return false;
 }
 
 template <bool FP8, bool SYM>
-otm_status launch_tc_cl(const TcArgs& args, int CL, cudaStream_t st) {
-  switch (CL) {
-    case 16: return launch_tc<FP8, SYM, 16>(args, st);
-    case 8: return launch_tc<FP8, SYM, 8>(args, st);
-    case 4: return launch_tc<FP8, SYM, 4>(args, st);
-    case 2: return launch_tc<FP8, SYM, 2>(args, st);
-    default: return launch_tc<FP8, SYM, 1>(args, st);
-  }
-}
-
-// configure = set the kernel's shared-memory / cluster attributes first (done by
-// the prepare call, so that the launch itself issues stream work only)
-template <bool FP8, int CL>
-otm_status launch_batched_cl(const TcArgs* items, int nitems, int* counter, size_t smem,
-                             int nclusters, cudaStream_t st, bool configure) {
-  auto kern = sgd_tc_batched_kernel<FP8, true, CL>;
-  if (configure) {
-    OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (CL > 8)
-      OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  }
-  if (nitems == 0) return OTM_OK;
+otm_status launch_tc(const TcArgs& args, const TcPlan& P, cudaStream_t st) {
+  auto kern = sgd_tc_kernel<FP8, SYM>;
+  OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+  if (P.CL > 8)
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL * nclusters, 1, 1);
+  cfg.gridDim = dim3(P.CL, 1, 1);
   cfg.blockDim = dim3(TC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = P.smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.x = P.CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, items, nitems, counter));
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args, P.NS, (int)P.dbl));
   count_launch();
   return OTM_OK;
 }
 
-template <bool FP8>
-otm_status launch_batched(int CL, const TcArgs* items, int nitems, int* counter, size_t smem,
-                          int nclusters, cudaStream_t st, bool configure) {
-  switch (CL) {
-    case 16: return launch_batched_cl<FP8, 16>(items, nitems, counter, smem, nclusters, st, configure);
-    case 8: return launch_batched_cl<FP8, 8>(items, nitems, counter, smem, nclusters, st, configure);
-    case 4: return launch_batched_cl<FP8, 4>(items, nitems, counter, smem, nclusters, st, configure);
-    case 2: return launch_batched_cl<FP8, 2>(items, nitems, counter, smem, nclusters, st, configure);
-    default: return launch_batched_cl<FP8, 1>(items, nitems, counter, smem, nclusters, st, configure);
-  }
-}
-
-// clusters of the batched kernel that can be resident at once (persistent grid)
-template <bool FP8, int CL>
-int resident_clusters_cl(size_t smem) {
-  auto kern = sgd_tc_batched_kernel<FP8, true, CL>;
+cudaLaunchConfig_t batched_cfg(const TcPlan& P, int nclusters, cudaStream_t st,
+                               cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.gridDim = dim3(P.CL * nclusters, 1, 1);
   cfg.blockDim = dim3(TC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr[1];
+  cfg.dynamicSmemBytes = P.smem;
+  cfg.stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.x = P.CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n <= 0) {
-    cudaGetLastError();
-    n = 0;
-  }
-  return n;
+  return cfg;
 }
 
+// configure = set the kernel's shared-memory / cluster attributes (done by the
+// prepare call, so that the launch itself issues stream work only)
 template <bool FP8>
-int resident_clusters(int CL, size_t smem) {
-  switch (CL) {
-    case 16: return resident_clusters_cl<FP8, 16>(smem);
-    case 8: return resident_clusters_cl<FP8, 8>(smem);
-    case 4: return resident_clusters_cl<FP8, 4>(smem);
-    case 2: return resident_clusters_cl<FP8, 2>(smem);
-    default: return resident_clusters_cl<FP8, 1>(smem);
+otm_status launch_batched(const TcPlan& P, const TcArgs* items, int nitems, int* counter,
+                          int nclusters, cudaStream_t st, bool configure) {
+  auto kern = sgd_tc_batched_kernel<FP8>;
+  if (configure) {
+    OTM_CHECK_CUDA(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+    if (P.CL > 8)
+      OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   }
+  if (nitems == 0) return OTM_OK;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = batched_cfg(P, nclusters, st, attr);
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, items, nitems, counter, P.NS, (int)P.dbl));
+  count_launch();
+  return OTM_OK;
 }
 
 int num_sms_tc() {
@@ -719,28 +929,24 @@ int num_sms_tc() {
   return v;
 }
 
-// Persistent grid: as many clusters as are resident at once (the occupancy
-// query; one CTA per SM if it is unavailable).  Call after the kernel's
-// attributes are set.
-int batched_clusters(bool fp8, int CL, size_t smem) {
-  const int n = fp8 ? resident_clusters<true>(CL, smem) : resident_clusters<false>(CL, smem);
-  return n > 0 ? n : std::max(1, num_sms_tc() / CL);
+// Clusters of the batched kernel resident at once (the persistent grid); call
+// after the attributes are set.  One CTA per SM if the query fails.
+int batched_clusters(bool fp8, const TcPlan& P) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = batched_cfg(P, 1, nullptr, attr);
+  int n = 0;
+  const cudaError_t e = fp8 ? cudaOccupancyMaxActiveClusters(&n, sgd_tc_batched_kernel<true>, &cfg)
+                            : cudaOccupancyMaxActiveClusters(&n, sgd_tc_batched_kernel<false>, &cfg);
+  if (e != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = std::max(1, num_sms_tc() / P.CL);
+  }
+  return n;
 }
 
-// autotuner cache: (precision, max k, cluster candidates tried) -> chosen size
+// autotuner cache: (precision, max k, chains) -> chosen cluster size
 std::mutex g_tune_mu;
 std::map<long long, int> g_tune_cache;
-
-int max_smem_optin() {
-  static int v = 0;
-  if (v == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (v <= 0) v = 227 * 1024;
-  }
-  return v;
-}
 
 }  // namespace
 }  // namespace otm
@@ -788,20 +994,10 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   if (epochs == 0) return OTM_OK;
   const bool fp8 = precision == OTM_PREC_FP8;
   const bool sym = (YA == YB) && (YB == YC);
-  const int esize = fp8 ? 1 : 2;
-  // largest cluster (16, 8, ...) whose CTAs each hold at most a few tiles and
-  // whose shared-memory footprint fits
-  int CL = 0;
-  for (int c : {8, 16, 4, 2, 1}) {
-    if (tc_layout((int)k, c, sym, esize).total <= (size_t)max_smem_optin()) {
-      CL = c;
-      break;
-    }
-  }
-  OTM_REQUIRE(CL > 0, "otm_sgd_run_lp: k=%lld does not fit shared memory with %s views",
-              (long long)k, sym ? "one" : "three");
-  if (b > 8 * TILE && CL == 8 && tc_layout((int)k, 16, sym, esize).total <= (size_t)max_smem_optin())
-    CL = 16;
+  TcPlan P;
+  OTM_REQUIRE(tc_plan_single((int)k, sym, fp8, &P),
+              "otm_sgd_run_lp: k=%lld does not fit on chip with %s views", (long long)k,
+              sym ? "one" : "three");
   cudaStream_t st = as_stream(stream);
   int* err = static_cast<int*>(ws);
   OTM_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -831,9 +1027,9 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   args.kappa = (float)(0.5 * (1.0 + theta));
   otm_status s_;
   if (fp8)
-    s_ = sym ? launch_tc_cl<true, true>(args, CL, st) : launch_tc_cl<true, false>(args, CL, st);
+    s_ = sym ? launch_tc<true, true>(args, P, st) : launch_tc<true, false>(args, P, st);
   else
-    s_ = sym ? launch_tc_cl<false, true>(args, CL, st) : launch_tc_cl<false, false>(args, CL, st);
+    s_ = sym ? launch_tc<false, true>(args, P, st) : launch_tc<false, false>(args, P, st);
   if (s_ != OTM_OK) return s_;
   int h = 0;
   OTM_CHECK_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -917,13 +1113,18 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 64 * sizeof(int), st));
   // feasible cluster sizes: shared memory for the largest k
   std::vector<int> cands;
-  for (int c : {1, 2, 4, 8, 16})
-    if (tc_layout(max_k, c, true, fp8 ? 1 : 2).total + 1024 <= (size_t)max_smem_optin())
-      cands.push_back(c);  // 1 KiB left for the kernel's static shared variables
-  OTM_REQUIRE(!cands.empty(), "otm_sgd_batched_prepare: k=%d does not fit shared memory", max_k);
+  for (int c : {1, 2, 4, 8, 16}) {
+    TcPlan Pc;
+    // every CTA of the cluster must own components of the largest problem
+    if ((c - 1) * own_cols(max_k, c) >= round16(max_k)) continue;
+    if (tc_plan(max_k, true, fp8, c, &Pc)) cands.push_back(c);
+  }
+  OTM_REQUIRE(!cands.empty() || cluster != 0,
+              "otm_sgd_batched_prepare: k=%d does not fit shared memory", max_k);
   int chosen = cluster;
   if (chosen != 0) {
-    OTM_REQUIRE(std::find(cands.begin(), cands.end(), chosen) != cands.end(),
+    TcPlan Pc;
+    OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pc),
                 "otm_sgd_batched_prepare: cluster %d does not fit k=%d", chosen, max_k);
   } else {
     // autotune: time a short trial (<= 4 steps per chain, on scratch V) for every
@@ -949,20 +1150,19 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
       OTM_CHECK_CUDA(cudaEventCreate(&e1));
       float best = 3.0e38f;
       for (int c : cands) {
-        const size_t smem = tc_layout(max_k, c, true, fp8 ? 1 : 2).total;
+        TcPlan Pc;
+        tc_plan(max_k, true, fp8, c, &Pc);
         float tot = 0.f;
         // set attributes (zero-item launch) before the occupancy query
-        otm_status s1 = fp8 ? launch_batched<true>(c, trial_items, 0, hdr + 8, smem, 1, st, true)
-                            : launch_batched<false>(c, trial_items, 0, hdr + 8, smem, 1, st, true);
+        otm_status s1 = fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true)
+                            : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true);
         if (s1 != OTM_OK) return s1;
-        const int ncl = std::min(batched_clusters(fp8, c, smem), ntrial);
+        const int ncl = std::min(batched_clusters(fp8, Pc), ntrial);
         for (int rep = 0; rep < 2; ++rep) {
           OTM_CHECK_CUDA(cudaMemsetAsync(hdr + 8, 0, sizeof(int), st));
           OTM_CHECK_CUDA(cudaEventRecord(e0, st));
-          otm_status s2 = fp8 ? launch_batched<true>(c, trial_items, ntrial, hdr + 8, smem, ncl,
-                                                     st, false)
-                              : launch_batched<false>(c, trial_items, ntrial, hdr + 8, smem, ncl,
-                                                      st, false);
+          otm_status s2 = fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false)
+                              : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false);
           if (s2 != OTM_OK) return s2;
           OTM_CHECK_CUDA(cudaEventRecord(e1, st));
           OTM_CHECK_CUDA(cudaEventSynchronize(e1));
@@ -981,10 +1181,11 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
       g_tune_cache[key] = chosen;
     }
   }
+  TcPlan Pch;
+  OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pch), "otm_sgd_batched_prepare: no plan");
   {
-    const size_t smem = tc_layout(max_k, chosen, true, fp8 ? 1 : 2).total;
-    otm_status s3 = fp8 ? launch_batched<true>(chosen, dev_items, 0, hdr, smem, 1, st, true)
-                        : launch_batched<false>(chosen, dev_items, 0, hdr, smem, 1, st, true);
+    otm_status s3 = fp8 ? launch_batched<true>(Pch, dev_items, 0, hdr, 1, st, true)
+                        : launch_batched<false>(Pch, dev_items, 0, hdr, 1, st, true);
     if (s3 != OTM_OK) return s3;
   }
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -992,9 +1193,8 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   plan->cluster = chosen;
   plan->precision = precision;
   plan->max_k = max_k;
-  plan->smem_bytes = (int64_t)tc_layout(max_k, chosen, true, fp8 ? 1 : 2).total;
-  plan->grid_clusters =
-      std::min(batched_clusters(fp8, chosen, (size_t)plan->smem_bytes), nitems);
+  plan->smem_bytes = (int64_t)Pch.smem;
+  plan->grid_clusters = std::min(batched_clusters(fp8, Pch), nitems);
   plan->ws = ws;
   plan->ws_bytes = ws_bytes;
   return OTM_OK;
@@ -1009,12 +1209,13 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
   int* hdr = w.take<int>(64);
   TcArgs* dev_items = w.take<TcArgs>(plan->nitems);
   OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 2 * sizeof(int), st));
-  const int c = plan->cluster;
-  return plan->precision == OTM_PREC_FP8
-             ? launch_batched<true>(c, dev_items, plan->nitems, hdr, (size_t)plan->smem_bytes,
-                                    plan->grid_clusters, st, false)
-             : launch_batched<false>(c, dev_items, plan->nitems, hdr, (size_t)plan->smem_bytes,
-                                     plan->grid_clusters, st, false);
+  const bool fp8 = plan->precision == OTM_PREC_FP8;
+  TcPlan P;
+  OTM_REQUIRE(tc_plan(plan->max_k, true, fp8, plan->cluster, &P) &&
+                  (int64_t)P.smem == plan->smem_bytes,
+              "otm_sgd_batched_launch: plan does not match this library");
+  return fp8 ? launch_batched<true>(P, dev_items, plan->nitems, hdr, plan->grid_clusters, st, false)
+             : launch_batched<false>(P, dev_items, plan->nitems, hdr, plan->grid_clusters, st, false);
 }
 
 otm_status otm_sgd_batched_check(const otm_batch_plan* plan, void* stream) {
