@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
     const int64_t e = s / a.spe, jb = s % a.spe;
     const int64_t pos0 = jb * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
-    const float beta = (float)(a.beta0 / sqrt((double)(s + 1)));
+    const float beta = (float)a.beta0 / sqrtf((float)(s + 1));
     const float inv_b = 1.f / (float)beff;
 
     // phase 1: a_A = V^T ybar_A, a_B = V^T ybar_B, s partial = 0

@@ -91,7 +91,7 @@ __host__ __device__ inline int own_cols(int k, int cl) {
 struct TcLayout {
   int N, nv, NS, es, CR, CRb, CBn, CBh;
   bool dbl;
-  size_t y_view, y_stage, off_v[2], off_vq, off_b[2], off_h, off_f;
+  size_t y_view, y_stage, off_v[2], off_vq, off_yb, off_b[2], off_h, off_f;
   size_t vm, ybA, ybB, ybC, aA, aB, vsc, bsc, amax, spw, red, ssc, nfloat;
   size_t total;
 };
@@ -117,7 +117,8 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   L.off_vq = L.off_v[1] + v_bytes;
   const size_t vq_bytes = es == 1 ? (size_t)N * KP : 0;
   const size_t b_bytes = (size_t)TILE * N * es;
-  L.off_b[0] = al128(L.off_vq + vq_bytes);
+  L.off_yb = al128(L.off_vq + vq_bytes);   // 16 rows: ybar_A, ybar_B, zeros (BF16)
+  L.off_b[0] = al128(L.off_yb + (size_t)16 * KP * 2);
   L.off_b[1] = L.off_b[0] + b_bytes;
   L.off_h = L.off_b[0];  // the H image reuses both B images (free by then)
   size_t end = L.off_b[1] + b_bytes;
@@ -135,7 +136,7 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   L.bsc = f;  f += 2 * (size_t)N;
   L.amax = f; f += 2 * (size_t)N;
   L.spw = f;  f += 4 * (size_t)N;
-  L.red = f;  f += 12 * (size_t)N;
+  L.red = f;  f += 4 * (size_t)N;
   L.ssc = f;  f += (size_t)NS * 3 * TILE;
   L.nfloat = f;
   L.total = L.off_f + f * 4 + 64;
@@ -156,6 +157,11 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
                "r"(bytes)
                : "memory");
 }
@@ -180,20 +186,17 @@ struct TcCtx {
   uint32_t ph;     // phase bits: 0-1 first product slots, 2-3 second, 4 Gram
 };
 
-// Sample tile n of step s into ring stage `stage` (cp.async, zero fill outside
-// the minibatch).  Thread tid copies half of sample tid / 2's coordinates.
+// Sample tile into ring stage `stage` by cp.async (zero fill outside the
+// minibatch); thread tid copies half of sample tid / 2's coordinates and its
+// scales.  raw: the permutation entry of that sample (-1 outside the
+// minibatch), loaded one issue earlier so that its latency is hidden.
 template <bool FP8, bool SYM>
 __device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, uint8_t* smem,
-                                          float* F, int64_t s, int n_tile, int stage) {
+                                          float* F, int raw, int stage) {
   constexpr int ES = FP8 ? 1 : 2;
   const int tid = threadIdx.x;
   const int t = tid >> 1, hs = tid & 1;
-  const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
-  const int64_t beff = min(a.b, a.n - pos0);
-  const int64_t p = (int64_t)n_tile * TILE + t;
-  int64_t row = -1;
-  if (p < beff) row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
-  if (row >= a.n) row = -1;
+  const int64_t row = (raw >= 0 && raw < a.n) ? raw : -1;
   const int half = L.CR / 2;
   uint8_t* Ys = smem + (size_t)stage * L.y_stage;
   for (int v = 0; v < L.nv; ++v) {
@@ -208,7 +211,11 @@ __device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, ui
     }
     if (hs == 0) {
       const float* sv = v == 0 ? a.sA : (v == 1 ? a.sB : a.sC);
-      F[L.ssc + ((size_t)stage * 3 + v) * TILE + t] = row >= 0 ? (sv ? sv[row] : 1.f) : 0.f;
+      float* sd = F + L.ssc + ((size_t)stage * 3 + v) * TILE + t;
+      if (sv)
+        cp_async4(sd, row >= 0 ? sv + row : sv, row >= 0 ? 4u : 0u);
+      else
+        *sd = row >= 0 ? 1.f : 0.f;
     }
   }
   cp_async_commit();
@@ -292,26 +299,34 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     ybC[r] = r < k ? (float)a.ybar3[2 * k + r] : 0.f;
   }
   for (int i = tid; i < 2 * N; i += TC_THREADS) amax[i] = 0u;
-  __syncthreads();
-  for (int i = warp; i < N; i += TC_THREADS / 32) {
-    float x = 0.f, y = 0.f, m = 0.f;
-    for (int r = lane; r < KP; r += 32) {
-      const float v = Vm[i * KP + r];
-      x = fmaf(v, ybA[r], x);
-      y = fmaf(v, ybB[r], y);
-      m = fmaxf(m, fabsf(v));
-    }
+  // ybar image: rows 0, 1 = ybar_A, ybar_B (BF16, K-major like V), rows 2..15 zero
+  uint8_t* Ybimg = smem + L.off_yb;
+  for (int idx = tid; idx < 16 * L.CRb; idx += TC_THREADS) {
+    const int c = idx / L.CRb, rg = idx % L.CRb;
+    float v[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_xor_sync(0xffffffffu, x, o);
-      y += __shfl_xor_sync(0xffffffffu, y, o);
-      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int z = 0; z < 8; ++z) {
+      const int r = rg * 8 + z;
+      v[z] = (r < k && c < 2) ? (float)a.ybar3[c * k + r] : 0.f;
     }
-    if (lane == 0) {
-      aA[i] = x;
-      aB[i] = y;
-      vsc[i] = FP8 ? (m > 0.f ? m / QMAX : 1.f) : 1.f;
+    uint4 w;
+    w.x = pack_bf16(v[0], v[1]);
+    w.y = pack_bf16(v[2], v[3]);
+    w.z = pack_bf16(v[4], v[5]);
+    w.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(Ybimg + (((size_t)(c >> 3) * L.CRb + rg) << 7) + ((c & 7) << 4)) = w;
+  }
+  __syncthreads();
+  if (FP8) {
+    for (int i = warp; i < N; i += TC_THREADS / 32) {
+      float m = 0.f;
+      for (int r = lane; r < KP; r += 32) m = fmaxf(m, fabsf(Vm[i * KP + r]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) vsc[i] = m > 0.f ? m / QMAX : 1.f;
     }
+  } else {
+    for (int i = tid; i < N; i += TC_THREADS) vsc[i] = 1.f;
   }
   __syncthreads();
 
@@ -343,22 +358,41 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     tc_after();
   };
 
-  // ---- tile loader: the global sequence of (step, tile), NS - 1 ahead ----
-  int64_t ld_s = 0;
-  int ld_n = 0;
+  // ---- tile loader: the global sequence of (step, tile) ----
+  // W = how many tiles back the second product is waited for before its sample
+  // stage is refilled (two with four stages, so that wait is never exposed)
+  const int W = NS >= 4 ? 2 : 1;
+  const bool early = NS - W >= 2;  // the next tile is resident one tile ahead
+  int64_t ld_s = 0, ld_e = 0, ld_jb = 0;  // step, epoch, minibatch of the next tile to issue
+  int ld_n = 0, ld_nt = 0, ld_stage = 0;
   int64_t issued = 0;
-  auto tiles_of = [&](int64_t s) {
-    const int64_t pos0 = (s % a.spe) * a.b;
-    return (int)((min(a.b, a.n - pos0) + TILE - 1) / TILE);
+  auto tiles_of = [&](int64_t jb) {
+    return (int)((min(a.b, a.n - jb * a.b) + TILE - 1) / TILE);
   };
+  auto row_raw = [&](int64_t e, int64_t jb, int n_tile) {
+    const int t = tid >> 1;
+    const int64_t pos0 = jb * a.b;
+    const int64_t p = (int64_t)n_tile * TILE + t;
+    if (p >= min(a.b, a.n - pos0)) return -1;
+    return a.perm ? a.perm[e * a.n + pos0 + p] : (int)(pos0 + p);
+  };
+  ld_nt = a.total_steps > 0 ? tiles_of(0) : 0;
+  int next_raw = a.total_steps > 0 ? row_raw(0, 0, 0) : -1;
   auto issue_one = [&]() {
     if (ld_s >= a.total_steps) return;
-    load_tile<FP8, SYM>(a, L, smem, F, ld_s, ld_n, (int)(issued % NS));
+    load_tile<FP8, SYM>(a, L, smem, F, next_raw, ld_stage);
     ++issued;
-    if (++ld_n >= tiles_of(ld_s)) {
+    if (++ld_stage == NS) ld_stage = 0;
+    if (++ld_n >= ld_nt) {
       ld_n = 0;
       ++ld_s;
+      if (++ld_jb == a.spe) {
+        ld_jb = 0;
+        ++ld_e;
+      }
+      ld_nt = tiles_of(ld_jb);
     }
+    if (ld_s < a.total_steps) next_raw = row_raw(ld_e, ld_jb, ld_n);
   };
   auto wait_tile = [&](int64_t g) {
     const int64_t pend = issued - 1 - g;
@@ -369,16 +403,18 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     tc_after();
   };
   if (active)
-    for (int i = 0; i < NS - 1; ++i) issue_one();
+    for (int i = 0; i < NS - W; ++i) issue_one();
 
+  const uint32_t colY = colD2b + (uint32_t)((FP8 ? 2 : 1) * N);
   int cur = 0;
   int64_t gbase = 0;
-  const bool early = NS >= 3;
+  int gstage = 0;  // ring stage of the step's first tile
+  int64_t jb = 0;  // minibatch index within the epoch
   for (int64_t s = 0; s < a.total_steps; ++s) {
-    const int64_t pos0 = (s % a.spe) * a.b;
+    const int64_t pos0 = jb * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
     const int nt = (int)((beff + TILE - 1) / TILE);
-    const float beta = (float)(a.beta0 / sqrt((double)(s + 1)));
+    const float beta = (float)a.beta0 / sqrtf((float)(s + 1));
     const float inv_b = 1.f / (float)beff;
     uint8_t* Vc = cur ? Vimg1 : Vimg0;
     uint8_t* Vn = dbl ? (cur ? Vimg0 : Vimg1) : Vc;
@@ -395,37 +431,36 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
 #pragma unroll
         for (int j = 0; j < 8; ++j) gacc[c][j] = 0.f;
 
-      // first product A = Y V_own of tile n (thread 0)
-      auto gemm1 = [&](int n) {
-        const int slot = n & 1;
-        const uint8_t* Ys = smem + (size_t)((gbase + n) % NS) * L.y_stage;
-        const uint32_t id = make_idesc(FMT, 0, 0, TILE, (uint32_t)N);
+      // descriptors (the start address is the low 14-bit field, in 16-byte units)
+      const uint64_t dV_own = sdesc(Vc + own_off, 128, (uint32_t)L.CRb * 128);
+      const uint64_t dVq = sdesc(Vq, 128, (uint32_t)L.CR * 128);
+      const uint32_t id1 = make_idesc(FMT, 0, 0, TILE, (uint32_t)N);
+      const uint32_t id2 = make_idesc(FMT, 1, 1, KP, (uint32_t)N);
+
+      // first product A = Y V_own of the tile in stage st (thread 0)
+      auto gemm1 = [&](int slot, int st) {
+        const uint8_t* Ys = smem + (size_t)st * L.y_stage;
         for (int v = 0; v < NVD; ++v) {
-          const uint8_t* Y = Ys + v * L.y_view;
-          for (int ks = 0; ks < ks1; ++ks) {
-            const uint64_t da = sdesc(Y + ks * 256, 128, (uint32_t)L.CR * 128);
-            const uint64_t db = FP8 ? sdesc(Vq + ks * 256, 128, (uint32_t)L.CR * 128)
-                                    : sdesc(Vc + own_off + ks * 256, 128, (uint32_t)L.CRb * 128);
-            mma<FP8>(tmem + (uint32_t)((slot * NVD + v) * N), da, db, id, ks > 0 ? 1u : 0u);
-          }
+          const uint64_t dY = sdesc(Ys + v * L.y_view, 128, (uint32_t)L.CR * 128);
+          const uint64_t dB = FP8 ? dVq : dV_own;
+          for (int ks = 0; ks < ks1; ++ks)
+            mma<FP8>(tmem + (uint32_t)((slot * NVD + v) * N), dY + (uint64_t)(16 * ks),
+                     dB + (uint64_t)(16 * ks), id1, ks > 0 ? 1u : 0u);
         }
         mma_commit(&mb[slot]);
       };
-      // second product G += Y_C^T B of tile n (thread 0)
-      auto gemm2 = [&](int n) {
+      // second product G += Y_C^T B of tile n in stage st (thread 0)
+      auto gemm2 = [&](int n, int st) {
         const int slot = n & 1;
-        const uint8_t* Ys = smem + (size_t)((gbase + n) % NS) * L.y_stage;
-        const uint8_t* YC = Ys + (SYM ? 0 : 2 * L.y_view);
-        const uint8_t* Bi = slot ? Bimg1 : Bimg0;
-        const uint32_t id = make_idesc(FMT, 1, 1, KP, (uint32_t)N);
+        const uint8_t* YC = smem + (size_t)st * L.y_stage + (SYM ? 0 : 2 * L.y_view);
+        const uint64_t dA = sdesc(YC, (uint32_t)L.CR * 128, 128);
+        const uint64_t dB = sdesc(slot ? Bimg1 : Bimg0, (uint32_t)L.CBn * 128, 128);
         const uint32_t col = colD2b + (FP8 ? (uint32_t)(slot * N) : 0u);
-        for (int ks = 0; ks < TILE / KSTEP; ++ks) {
-          const uint64_t da =
-              sdesc(YC + (size_t)ks * (KSTEP / 8) * L.CR * 128, (uint32_t)L.CR * 128, 128);
-          const uint64_t db =
-              sdesc(Bi + (size_t)ks * (KSTEP / 8) * L.CBn * 128, (uint32_t)L.CBn * 128, 128);
-          mma<FP8>(tmem + col, da, db, id, (FP8 ? ks > 0 : (n > 0 || ks > 0)) ? 1u : 0u);
-        }
+        const uint64_t stepA = (uint64_t)((KSTEP / 8) * L.CR * 8);   // (KSTEP/8) core groups
+        const uint64_t stepB = (uint64_t)((KSTEP / 8) * L.CBn * 8);  // in 16-byte units
+        for (int ks = 0; ks < TILE / KSTEP; ++ks)
+          mma<FP8>(tmem + col, dA + stepA * ks, dB + stepB * ks, id2,
+                   (FP8 ? ks > 0 : (n > 0 || ks > 0)) ? 1u : 0u);
         mma_commit(&mb[2 + slot]);
       };
       // FP8: per-tile second product, scaled by the tile's B scales
@@ -443,32 +478,58 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         }
       };
 
+      // a_A = V^T ybar_A, a_B = V^T ybar_B for every component (one MMA, N = 16)
+      if (tid == 0 && !s_abort) {
+        const uint64_t dA = sdesc(Vc, 128, (uint32_t)L.CRb * 128);
+        const uint64_t dB = sdesc(Ybimg, 128, (uint32_t)L.CRb * 128);
+        const uint32_t id = make_idesc(1, 0, 0, VROWS, 16);
+        for (int ks = 0; ks < kg16; ++ks)
+          mma<false>(tmem + colY, dA + (uint64_t)(16 * ks), dB + (uint64_t)(16 * ks), id,
+                     ks > 0 ? 1u : 0u);
+        mma_commit(&mb[4]);
+      }
+      int st = gstage;  // stage of tile g
       if (early) {
         wait_tile(gbase);
-        if (tid == 0 && !s_abort) gemm1(0);
+        if (tid == 0 && !s_abort) gemm1(0, st);
       }
+      wait_mb(4);
+      if (hf == 0) {  // lanes = components: keep the owned ones
+        float x[8];
+        tmem_ld8(tmem + lane_base + colY, x);
+        const int j = 32 * qd + lane;
+        if (j >= own_lo && j < own_lo + N) {
+          aA[j - own_lo] = x[0];
+          aB[j - own_lo] = SYM ? x[0] : x[1];
+        }
+      }
+      tc_before();
+      __syncthreads();
+      tc_after();
+
       for (int n = 0; n < nt; ++n) {
         const int64_t g = gbase + n;
         const int slot = n & 1;
+        const int st_next = st + 1 == NS ? 0 : st + 1;
         if (early && n + 1 < nt) {
           wait_tile(g + 1);
-          if (tid == 0 && !s_abort) gemm1(n + 1);
+          if (tid == 0 && !s_abort) gemm1((n + 1) & 1, st_next);
         }
-        if (n >= 1) {
-          wait_mb(2 + ((n - 1) & 1));
-          if (FP8) epi2(n - 1);
+        if (n >= W) {
+          wait_mb(2 + ((n - W) & 1));
+          if (FP8) epi2(n - W);
         }
-        while (issued <= g + NS - 1 && ld_s < a.total_steps) issue_one();
+        while (issued <= g + NS - W && ld_s < a.total_steps) issue_one();
         if (!early) {
           wait_tile(g);
-          if (tid == 0 && !s_abort) gemm1(n);
+          if (tid == 0 && !s_abort) gemm1(slot, st);
         }
         wait_mb(slot);
 
         // -- epilogue 1: B = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B) --
         {
           const int t = 32 * qd + lane;
-          const float* ss = F + L.ssc + (size_t)(g % NS) * 3 * TILE;
+          const float* ss = F + L.ssc + (size_t)st * 3 * TILE;
           const float sa = ss[t], sb = SYM ? sa : ss[TILE + t], sc = SYM ? sa : ss[2 * TILE + t];
           uint8_t* Bi = slot ? Bimg1 : Bimg0;
           if (FP8) {
@@ -544,10 +605,13 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         tc_before();
         __syncthreads();
         tc_after();
-        if (tid == 0 && !s_abort) gemm2(n);
+        if (tid == 0 && !s_abort) gemm2(n, st);
+        st = st_next;
       }
-      wait_mb(2 + ((nt - 1) & 1));
-      if (FP8) epi2(nt - 1);
+      for (int n = nt - W < 0 ? 0 : nt - W; n < nt; ++n) {
+        wait_mb(2 + (n & 1));
+        if (FP8) epi2(n);
+      }
 
       // s_i = sum over the minibatch of A_A o A_B (per owned component)
 #pragma unroll
@@ -567,12 +631,11 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       __syncthreads();
       tc_after();
       if (tid == 0 && !s_abort) {
+        const uint64_t dA = sdesc(Vc, 128, (uint32_t)L.CRb * 128);
         const uint32_t id = make_idesc(1, 0, 0, VROWS, (uint32_t)N);
-        for (int ks = 0; ks < kg16; ++ks) {
-          const uint64_t da = sdesc(Vc + ks * 256, 128, (uint32_t)L.CRb * 128);
-          const uint64_t db = sdesc(Vc + own_off + ks * 256, 128, (uint32_t)L.CRb * 128);
-          mma<false>(tmem + colH, da, db, id, ks > 0 ? 1u : 0u);
-        }
+        for (int ks = 0; ks < kg16; ++ks)
+          mma<false>(tmem + colH, dA + (uint64_t)(16 * ks), dV_own + (uint64_t)(16 * ks), id,
+                     ks > 0 ? 1u : 0u);
         mma_commit(&mb[4]);
       }
       wait_mb(4);
@@ -599,14 +662,12 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       __syncthreads();
       tc_after();
       if (tid == 0 && !s_abort) {
+        const uint64_t dA = sdesc(Vc, (uint32_t)L.CRb * 128, 128);
+        const uint64_t dB = sdesc(Himg, (uint32_t)L.CBh * 128, 128);
         const uint32_t id = make_idesc(1, 1, 1, KP, (uint32_t)N);
-        for (int ks = 0; ks < kg16; ++ks) {
-          const uint64_t da =
-              sdesc(Vc + (size_t)ks * 2 * L.CRb * 128, (uint32_t)L.CRb * 128, 128);
-          const uint64_t db =
-              sdesc(Himg + (size_t)ks * 2 * L.CBh * 128, (uint32_t)L.CBh * 128, 128);
-          mma<false>(tmem + colGG, da, db, id, ks > 0 ? 1u : 0u);
-        }
+        for (int ks = 0; ks < kg16; ++ks)
+          mma<false>(tmem + colGG, dA + (uint64_t)(2 * L.CRb * 8 * ks),
+                     dB + (uint64_t)(2 * L.CBh * 8 * ks), id, ks > 0 ? 1u : 0u);
         mma_commit(&mb[4]);
       }
       wait_mb(4);
@@ -629,29 +690,24 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int i = c0 + j, comp = own_lo + i;
-              float vnew = 0.f;
-              if (comp < k && r < k) {
-                const float s_i = spw[i] + spw[N + i] + spw[2 * N + i] + spw[3 * N + i];
-                const float gdata =
-                    gd[j] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * s_i * inv_b);
-                vnew = Vm[i * KP + r] - beta * (a.kappa * gg[j] - gdata);
-                Vm[i * KP + r] = vnew;
-              }
-              if (comp < VROWS)
+              if (comp < k) {
+                float vnew = 0.f;
+                if (r < k) {
+                  const float s_i = spw[i] + spw[N + i] + spw[2 * N + i] + spw[3 * N + i];
+                  const float gdata =
+                      gd[j] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * s_i * inv_b);
+                  vnew = Vm[i * KP + r] - beta * (a.kappa * gg[j] - gdata);
+                  Vm[i * KP + r] = vnew;
+                }
                 *reinterpret_cast<__nv_bfloat16*>(
                     Vn + ((((size_t)(comp >> 3) * L.CRb + (r >> 3)) << 7) + ((comp & 7) << 4) +
                           ((r & 7) << 1))) = __float2bfloat16_rn(vnew);
-              float x = vnew * ybA[r], y = vnew * ybB[r], m = fabsf(vnew);
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) {
-                x += __shfl_xor_sync(0xffffffffu, x, o);
-                y += __shfl_xor_sync(0xffffffffu, y, o);
-                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
               }
-              if (lane == 0) {
-                red[qd * N + i] = x;
-                red[(4 + qd) * N + i] = y;
-                red[(8 + qd) * N + i] = m;
+              if (FP8) {
+                float m = (comp < k && r < k) ? fabsf(Vm[i * KP + r]) : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) red[qd * N + i] = m;
               }
             }
           }
@@ -660,13 +716,9 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       tc_before();
       __syncthreads();
       tc_after();
-      if (tid < N) {
-        const int i = tid;
-        aA[i] = red[i] + red[N + i] + red[2 * N + i] + red[3 * N + i];
-        aB[i] = red[4 * N + i] + red[5 * N + i] + red[6 * N + i] + red[7 * N + i];
-        const float m = fmaxf(fmaxf(red[8 * N + i], red[9 * N + i]),
-                              fmaxf(red[10 * N + i], red[11 * N + i]));
-        vsc[i] = FP8 ? (m > 0.f ? m / QMAX : 1.f) : 1.f;
+      if (FP8 && tid < N) {
+        const float m = fmaxf(fmaxf(red[tid], red[N + tid]), fmaxf(red[2 * N + tid], red[3 * N + tid]));
+        vsc[tid] = m > 0.f ? m / QMAX : 1.f;
       }
       if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0) {
         float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
@@ -683,9 +735,9 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     if (CL > 1) {
       if (!dbl) cluster.sync();  // single image: every CTA has finished reading it
       if (active) {
-        for (int idx = tid; idx < N * L.CRb; idx += TC_THREADS) {
+        const int nrow = min(N, k - own_lo);
+        for (int idx = tid; idx < nrow * L.CRb; idx += TC_THREADS) {
           const int i = idx / L.CRb, rg = idx % L.CRb, comp = own_lo + i;
-          if (comp >= VROWS) continue;
           const size_t off = (((size_t)(comp >> 3) * L.CRb + rg) << 7) + ((comp & 7) << 4);
           const uint4 w = *reinterpret_cast<const uint4*>(Vn + off);
           for (int c = 0; c < CL; ++c)
@@ -699,6 +751,8 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     fence_async_smem();
     if (dbl) cur ^= 1;
     gbase += nt;
+    gstage = (int)((gstage + nt) % NS);
+    if (++jb == a.spe) jb = 0;
   }
   cp_async_wait(0);
   if (active) {
@@ -834,7 +888,7 @@ bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
   const int N = own_cols(k, CL);
   if (N > 128 || (fp8 && N > 64)) return false;
   const int nvd = sym ? 1 : 2;
-  if ((2 * nvd + (fp8 ? 2 : 1)) * N > (int)TMEM_COLS) return false;
+  if ((2 * nvd + (fp8 ? 2 : 1)) * N + 16 > (int)TMEM_COLS) return false;
   const size_t lim = (size_t)max_smem_optin() - 1024;  // static shared variables
   const int order[8][2] = {{1, 4}, {1, 3}, {0, 4}, {0, 3}, {1, 2}, {0, 2}, {1, 1}, {0, 1}};
   for (const auto& o : order) {
