@@ -156,6 +156,61 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+REF_STEPS, REF_BETA0 = 10000, 0.02   # full-batch reference run (see convergence())
+
+
+def convergence(otm, torch, path, cfg, fp32_step_ms):
+    """Time-to-1e-3 of the plain FP32 STGD and of the BF16 precision form on the
+    bench's whitened samples.  Error = relative reconstruction error of the
+    iterate (snapshot after every epoch) against a reference solution on the
+    same samples: REF_STEPS full-batch FP32 steps (beta_t = REF_BETA0/sqrt(t))
+    continued from the FP32 run's final iterate; its residual gradient is
+    reported.  Untimed except for the BF16 run's own step time."""
+    c, k = cfg, cfg["k"]
+    n = c["n_per"]
+    spe = (n + c["b"] - 1) // c["b"]
+    wh = otm.whiten_community(path.D["G_XA"], path.D["G_XB"], path.D["G_XC"], path.S_pairs,
+                              path.S_w, k, c["power_iters"], c["alpha0"])
+    Y = [otm.project(path.D[x], wh[w]) for x, w in (("G_XA", "W"), ("G_XB", "W_B"),
+                                                   ("G_XC", "W_C"))]
+    yb = torch.stack([otm.column_mean(y) for y in Y])
+    V32 = path.V0.t().contiguous()
+    snap32 = otm.sgd_run(V32, *Y, yb, path.perm, c["epochs"], c["b"], c["beta0"], c["theta"],
+                         c["alpha0"], snapshot_every=spe)
+    q = [otm.quantize_samples(y, otm.PREC_BF16) for y in Y]
+    V16 = path.V0.t().contiguous()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    snap16 = otm.sgd_run_lp(V16, *q, yb, path.perm, c["epochs"], c["b"], c["beta0"], c["theta"],
+                            c["alpha0"], otm.PREC_BF16, snapshot_every=spe)
+    e1.record()
+    torch.cuda.synchronize()
+    bf16_step_ms = e0.elapsed_time(e1) / (spe * c["epochs"])
+    Vref = V32.clone()
+    otm.sgd_run(Vref, *Y, yb, None, REF_STEPS, n, REF_BETA0, c["theta"], c["alpha0"])
+    # residual gradient at the reference: one tiny full-batch step
+    Vg = Vref.clone()
+    h = 1e-3
+    otm.sgd_step(Vg, *Y, yb, c["theta"], h, c["alpha0"])
+    grad_rel = float(((Vref - Vg) / h).norm() / Vref.norm())
+    nr = Vref.double().norm(dim=1)
+    kappa = 0.5 * (1.0 + c["theta"])
+    lam = (kappa * nr ** 3).contiguous()
+    U = (Vref.double() / nr[:, None]).contiguous()
+
+    def report(snaps, step_ms):
+        errs = [float(otm.recon_error(snaps[i].contiguous(), U, lam, c["theta"])[0])
+                for i in range(snaps.shape[0])]
+        hit = next((i for i, e in enumerate(errs) if e <= 1e-3), None)
+        return {"epochs_to_1e-3": None if hit is None else hit + 1,
+                "seconds_to_1e-3": None if hit is None else (hit + 1) * spe * step_ms / 1e3,
+                "step_ms": step_ms, "error_by_epoch": [round(e, 6) for e in errs]}
+    return {"reference": f"{REF_STEPS} full-batch FP32 steps, beta0 {REF_BETA0}, "
+                         "from the FP32 run's final iterate",
+            "reference_grad_rel": grad_rel,
+            "fp32": report(snap32, fp32_step_ms), "bf16": report(snap16, bf16_step_ms)}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_1309_0787_gb300 import otm
@@ -257,6 +312,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    line["time_to_1e-3"] = convergence(otm, torch, path, cfg, statistics.mean(sgd_ms) / nsteps)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(cfg, host)
     return line

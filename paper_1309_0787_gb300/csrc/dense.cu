@@ -1066,7 +1066,7 @@ size_t orth_workspace(int64_t m) {
 }
 
 otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cudaStream_t st,
-                          int* dflag) {
+                          int* dflag, int passes) {
   if (m > 160) return set_error(OTM_EINVAL, "orthonormalize: m=%lld > 160", (long long)m);
   if (rows < m) return set_error(OTM_EINVAL, "orthonormalize: rows < m");
   double* G = ws.take<double>(m * m);
@@ -1080,7 +1080,7 @@ otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cuda
   // pass 0: shifted (ill-conditioned input); pass 1: plain Cholesky-QR; passes
   // 2-3 run only while the columns are not yet orthonormal to 1e-5 (the test
   // and the skip happen on the device, without a host round trip)
-  for (int pass = 0; pass < 4; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     const int* sk = pass >= 2 ? skip : nullptr;
     OTM_TRY(gemm_tn_f64acc(A, A, rows, m, m, 1.0, G, 0, st, sk));
     chol_inv_kernel<<<1, CH_T, smem, st>>>(G, (int)m, pass == 0 ? 11.0 : 0.0, Rinv, dflag,
