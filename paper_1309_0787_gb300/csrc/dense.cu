@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(1024) jacobi_f32_kernel(const double* __restri
 // Output: X (n x n FP64, row-major, column i = eigenvector i, eigenvalues
 // ascending).  fac: 2 n^2 floats of global scratch for the factorisations.
 // ---------------------------------------------------------------------------
-constexpr int TE_T = 256;
+constexpr int TE_T = 1024;
 
 __device__ __forceinline__ float block_sum_f(float v, float* red, int tid) {
 #pragma unroll
@@ -711,22 +711,35 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   glo -= pad;
   ghi += pad;
   const float piv_min = 1e-30f + 1e-12f * tnorm;
-  if (tid < n) {
+  // multisection: G lanes per eigenvalue evaluate the Sturm count at G interior
+  // points of the current interval, which then shrinks by G + 1 (9 rounds of
+  // 9 for G = 8, 13 rounds of 5 for G = 4: below 2^-28 of the Gershgorin range)
+  const int G = n <= TE_T / 8 ? 8 : 4;
+  const int rounds = G == 8 ? 9 : 13;
+  {
+    const int i = tid / G, sub = tid % G;
+    const int gbase = (lane / G) * G;  // first lane of this eigenvalue's group
     float lo = glo, hi = ghi;
-    for (int it = 0; it < 28; ++it) {
-      const float mid = 0.5f * (lo + hi);
+    for (int it = 0; it < rounds; ++it) {
+      const float w = (hi - lo) / (float)(G + 1);
+      const float x = lo + w * (float)(sub + 1);
       int cnt = 0;
-      float q = d[0] - mid;
+      float q = d[0] - x;
       if (fabsf(q) < piv_min) q = -piv_min;
       cnt += q < 0.f;
       for (int k = 1; k < n; ++k) {
-        q = d[k] - mid - __fdividef(e[k - 1] * e[k - 1], q);
+        q = d[k] - x - __fdividef(e[k - 1] * e[k - 1], q);
         if (fabsf(q) < piv_min) q = -piv_min;
         cnt += q < 0.f;
       }
-      if (cnt > tid) hi = mid; else lo = mid;
+      // first interior point with more than i eigenvalues below it
+      const unsigned m = (__ballot_sync(0xffffffffu, cnt > i) >> gbase) & ((1u << G) - 1u);
+      const int first = m ? __ffs(m) - 1 : G;
+      const float nlo = lo + w * (float)first;
+      hi = first < G ? lo + w * (float)(first + 1) : hi;
+      lo = nlo;
     }
-    lam[tid] = 0.5f * (lo + hi);
+    if (i < n && sub == 0) lam[i] = 0.5f * (lo + hi);
   }
   __syncthreads();
 
@@ -835,28 +848,21 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   }
   __syncthreads();
 
-  // 4. back-transformation X = H_0 ... H_{n-3} Z: two threads per column (rows
-  // interleaved, partial dot products combined by a shuffle), no barriers
-  for (int base = 0; base < n; base += TE_T >> 1) {  // trip count uniform per block
-    const int c = base + (tid >> 1), hh = tid & 1;
+  // 4. back-transformation X = H_0 ... H_{n-3} Z: G threads per column (rows
+  // interleaved, partial dot products combined by shuffles); columns are
+  // independent, so no barriers
+  for (int base = 0; base < n; base += TE_T / G) {  // trip count uniform per block
+    const int c = base + tid / G, sub = tid % G;
     for (int j = n - 3; j >= 0; --j) {
-      const float tj = tau[j];  // uniform across the pair
+      const float tj = tau[j];  // uniform across the block
       if (tj == 0.f) continue;
-      float w0 = 0.f, w1 = 0.f;
-      if (c < n) {
-        int r = j + 1 + hh;
-        for (; r + 2 < n; r += 4) {
-          w0 = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w0);
-          w1 = fmaf(Ah[(r + 2) * ldn + j], Z[(r + 2) * ldn + c], w1);
-        }
-        for (; r < n; r += 2) w0 = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w0);
-      }
-      float w = w0 + w1;
-      w += __shfl_xor_sync(0xffffffffu, w, 1);
+      float w = 0.f;
+      if (c < n)
+        for (int r = j + 1 + sub; r < n; r += G) w = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w);
+      for (int o = 1; o < G; o <<= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
       w *= tj;
       if (c < n)
-        for (int r = j + 1 + hh; r < n; r += 2)
-          Z[r * ldn + c] = fmaf(-w, Ah[r * ldn + j], Z[r * ldn + c]);
+        for (int r = j + 1 + sub; r < n; r += G) Z[r * ldn + c] = fmaf(-w, Ah[r * ldn + j], Z[r * ldn + c]);
     }
   }
   __syncthreads();
@@ -1129,7 +1135,7 @@ otm_status syev(const double* A_in, int64_t n, double* evals, double* evecs, Wor
   tridiag_eig_kernel<<<1, TE_T, smem, st>>>(A, (int)n, X, fac);
   OTM_CHECK_LAUNCH();
   // FP64 refinement: quadratic convergence from the float32 eigenvectors
-  const int iters = 6;
+  const int iters = 4;
   for (int it = 0; it < iters; ++it) {
     OTM_TRY(dgemm_small(0, 0, n, n, n, 1.0, A, n, X, n, 0.0, AX, n, st));
     OTM_TRY(dgemm_small(1, 0, n, n, n, 1.0, X, n, AX, n, 0.0, S, n, st));
