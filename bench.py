@@ -43,6 +43,10 @@ CFG = dict(workload="mmsb_4x5000_k100_b1024_fp32", n_per=5000, k=100, alpha_i=0.
            q=0.005, oversample=20, power_iters=2, b=1024, epochs=20, beta0=1e-2, theta=1.0,
            alpha0=1.0, seed=0)
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+# DRAM bytes (read + write) per launch of sgd_cluster_kernel on this workload, from the ncu
+# capture summarised in profiles/sgd_cluster_kernel_mmsb_k100.md (reset to None whenever the
+# kernel changes)
+SGD_CLUSTER_TRAFFIC = 6508032
 
 
 def make_inputs(cfg, rank=0):
@@ -304,7 +308,7 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": {"kernel": "sgd_cluster_kernel (one launch = all 100 STGD steps)",
                      "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": SGD_CLUSTER_TRAFFIC,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "algorithmic_flops_per_launch": flops},
         "e2e": {"value": world * samples * n_e2e / e2e_t, "unit": UNIT,
@@ -404,6 +408,110 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------
+# Batched form: many independent decompositions in one persistent launch
+# ----------------------------------------------------------------------------
+BATCHED = dict(ks=(16, 32, 64, 128), b_exp=(6, 12), pool=4, epochs=8, sigma=1e-2, beta0=5e-3,
+               theta=1.0, seed=0)
+BF16_PEAK_TFLOPS = 1891.5   # MEASURED_PEAKS.json bf16_tflops (burst; cuBLAS 8192^3)
+
+
+def run_batched(args):
+    """Whitened orthogonal-tensor problems (y = w_h^{-1/2} u_h + sigma eps, alpha0 = 0),
+    k ~ U{16, 32, 64, 128}, b = 2^U{6..12}, a pool of 4 b samples per problem,
+    8 epochs, `restarts` Haar-random starts each; all chains in one persistent
+    BF16 tensor-core launch captured in a CUDA graph.  Flops per step of one
+    chain (symmetric views): 2 k^2 b (A = Y V) + 2 k^2 b (Y^T B) + 4 k^3 (Gram).
+    The plain FP32 kernel, looped chain by chain, is timed on the first
+    problems' first restart and extrapolated per sample."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    dev = torch.device("cuda", 0)
+    c = dict(BATCHED)
+    g = np.random.default_rng(c["seed"])
+    probs, flops, samples, chains = [], 0, 0, 0
+    for p in range(args.problems):
+        k = int(g.choice(c["ks"]))
+        b = 2 ** int(g.integers(c["b_exp"][0], c["b_exp"][1] + 1))
+        n = c["pool"] * b
+        o = synth.orthogonal_samples(c["seed"] + 100 + p, k, n, c["sigma"])
+        Y = torch.from_numpy(o["Y"]).to(dev)
+        Yq, sc = otm.quantize_samples(Y, otm.PREC_BF16)
+        yb = Y.double().mean(0)
+        V0 = np.stack([synth.haar_orthonormal(c["seed"] + 10000 + 16 * p + r, k).T
+                       for r in range(args.restarts)])
+        probs.append({"Y": Y, "Yq": Yq, "scales": sc, "ybar3": torch.stack([yb] * 3).contiguous(),
+                      "perm": torch.from_numpy(synth.epoch_permutations(c["seed"] + 50000 + p, n,
+                                                                        c["epochs"])).to(dev),
+                      "V0": torch.from_numpy(np.ascontiguousarray(V0)).to(dev),
+                      "V": torch.from_numpy(np.ascontiguousarray(V0)).to(dev),
+                      "epochs": c["epochs"], "b": b, "beta0": c["beta0"], "theta": c["theta"],
+                      "alpha0": 0.0, "k": k, "n": n})
+        steps = (n // b) * c["epochs"]
+        flops += args.restarts * steps * (4 * k * k * b + 4 * k ** 3)
+        samples += args.restarts * steps * b
+        chains += args.restarts
+    batch = otm.SgdBatch(probs, otm.PREC_BF16, cluster=args.cluster)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batch.launch()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    batch.check()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    l0 = otm.launch_count()
+    for e0, e1 in ev:
+        e0.record()
+        graph.replay()
+        e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    batch.check()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t = statistics.mean(ms) / 1e3
+    # the plain FP32 kernel looped over chains (first restart of the first problems)
+    nloop = min(8, len(probs))
+    lsamples, lt = 0, 0.0
+    for p in probs[:nloop]:
+        V = p["V0"][0].contiguous()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        otm.sgd_run(V, p["Y"], p["Y"], p["Y"], p["ybar3"], p["perm"], p["epochs"], p["b"],
+                    p["beta0"], p["theta"], p["alpha0"])
+        e1.record()
+        torch.cuda.synchronize()
+        lt += e0.elapsed_time(e1) / 1e3
+        lsamples += (p["n"] // p["b"]) * p["epochs"] * p["b"]
+    achieved = flops / t / 1e12
+    return {"metric": "batched STGD throughput (samples/s), BF16 tensor cores, one persistent launch",
+            "value": samples / t, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"batched_{args.problems}x{args.restarts}_orthogonal",
+                       "problems": args.problems, "restarts": args.restarts, "chains": chains,
+                       "k_choices": list(c["ks"]), "minibatch": "2^U{6..12}",
+                       "pool": "4 b samples", "epochs": c["epochs"], "cluster": batch.cluster,
+                       "l2": "inputs larger than L2" if samples > 0 else None,
+                       "k_256": "not supported yet (k <= 128)"},
+            "roofline": {"kernel": "sgd_tc_batched_kernel", "bound": "tensor",
+                         "achieved": achieved, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / BF16_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)",
+                         "algorithmic_flops_per_launch": flops},
+            "vs_plain_fp32_loop": {"samples_per_s": lsamples / lt, "chains_timed": nloop,
+                                   "speedup": (samples / t) / (lsamples / lt)},
+            # one persistent kernel per graph replay (graph replays bypass the library's
+            # host-side launch counter)
+            "gpu_launches": args.steps,
+            "clocks": clocks}
+
+
+# ----------------------------------------------------------------------------
 def dist_barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -427,11 +535,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="mmsb", choices=["mmsb", "batched"],
+                    help="mmsb: the default pipeline line; batched: the batched form")
+    ap.add_argument("--problems", type=int, default=512)
+    ap.add_argument("--restarts", type=int, default=8)
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="batched: CTAs per chain (0 = autotune)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.workload == "batched":
+        line = run_batched(args) if rank == 0 else None
+    elif args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
         if world > 1:
