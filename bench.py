@@ -43,9 +43,9 @@ CFG = dict(workload="mmsb_4x5000_k100_b1024_fp32", n_per=5000, k=100, alpha_i=0.
            q=0.005, oversample=20, power_iters=2, b=1024, epochs=20, beta0=1e-2, theta=1.0,
            alpha0=1.0, seed=0)
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
-# DRAM bytes (read + write) per launch of sgd_cluster_kernel on this workload, from the ncu
-# capture summarised in profiles/sgd_cluster_kernel_mmsb_k100.md (reset to None whenever the
-# kernel changes)
+# DRAM bytes (read + write) per launch of sgd_cluster_kernel on this workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command; to be reset to None
+# whenever the kernel changes
 SGD_CLUSTER_TRAFFIC = 6508032
 
 
