@@ -512,6 +512,187 @@ def run_batched(args):
 
 
 # ----------------------------------------------------------------------------
+# Learned warm start: time to 1e-3 reconstruction error on held-out instances
+# ----------------------------------------------------------------------------
+WARM = dict(k=64, J=4, width=512, n_train=2000, ntr=32768, batch=256, train_epochs=2,
+            lr=3e-4, n_test=8192, nte=16, beta0=0.02, epochs=300, ref_steps=3000,
+            bf16_epochs=100, seed=0)
+
+
+def run_warmstart(args):
+    """Exact-mixture LDA instances in whitened coordinates (alpha0 ~ U[0.5, 2]).  The
+    network (canonical frame of the first sketch + MLP started at the identity) is
+    trained on `ntr` generated instances; on `nte` held-out instances full-batch
+    STGD (b = n, beta_t = beta0/sqrt(t)) runs from (a) a Haar-random start, FP32
+    (the paper's method), (b) the learned start, FP32, (c) the learned start,
+    BF16 tensor cores, (d) the learned start, BF16 for `bf16_epochs` then FP32.
+    Error after every epoch = relative reconstruction error against a reference:
+    `ref_steps` FP32 full-batch steps from the learned start.  Reported per method:
+    fraction of instances reaching 1e-3 within `epochs`, median epochs and median
+    seconds (epochs x measured step time)."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    c = dict(WARM)
+    if args.k:
+        c["k"] = args.k
+    k, J, h = c["k"], c["J"], c["width"]
+    din, dout = J * k * k, k * k
+    dev = torch.device("cuda", 0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    inst = synth.whitened_lda_instances(c["seed"], c["ntr"] + c["nte"], k)
+    th = torch.from_numpy(synth.unit_vectors(c["seed"] + 1, J, k)).to(dev)
+    m = torch.from_numpy(inst["m"]).to(dev)
+    al = torch.from_numpy(inst["alpha32"]).to(dev)
+    a0 = torch.from_numpy(inst["alpha0"]).to(dev)
+    Us = torch.from_numpy(inst["U"].astype(np.float32)).to(dev)
+    lam = torch.from_numpy(inst["lam"].astype(np.float32)).to(dev)
+    # training data: generate, sketch, canonical frame (in chunks)
+    X = torch.empty(c["ntr"], din, dtype=torch.bfloat16, device=dev)
+    E = torch.empty(c["ntr"], k, k, dtype=torch.float32, device=dev)
+    e0, e1 = ev(), ev()
+    e0.record()
+    for c0 in range(0, c["ntr"], 512):
+        c1 = min(c0 + 512, c["ntr"])
+        Y = otm.ws_generate(m[c0:c1].contiguous(), al[c0:c1].contiguous(), c["n_train"],
+                            c["seed"] + 2, first=c0)
+        S, _ = otm.ws_sketch(Y, a0[c0:c1].contiguous(), th)
+        Ec, _, Xc = otm.ws_canonicalize(S)
+        X[c0:c1] = Xc
+        E[c0:c1] = Ec
+    e1.record()
+    torch.cuda.synchronize()
+    gen_ms = e0.elapsed_time(e1)
+    Ut = otm.ws_rotate(E, Us[:c["ntr"]].contiguous(), transpose=True)
+    # network, started at the canonical frame (b3 = vec(I), W3 small)
+    g = np.random.default_rng(c["seed"] + 3)
+    W1 = g.standard_normal((h, din)) / np.sqrt(din)
+    W2 = g.standard_normal((h, h)) / np.sqrt(h)
+    W3 = 0.01 * g.standard_normal((dout, h)) / np.sqrt(h)
+    params = np.concatenate([W1.ravel(), np.zeros(h), W2.ravel(), np.zeros(h), W3.ravel(),
+                             np.eye(k).ravel()]).astype(np.float32)
+    net = otm.Mlp(din, h, dout, params)
+    B = c["batch"]
+    steps = c["train_epochs"] * c["ntr"] // B
+    losses = []
+    e0.record()
+    for st in range(steps):
+        i0 = (st * B) % c["ntr"]
+        l = net.train_step(X[i0:i0 + B], Ut[i0:i0 + B], lam[i0:i0 + B], k, c["lr"])
+        if st % max(1, steps // 8) == 0 or st == steps - 1:
+            losses.append(l)
+    e1.record()
+    torch.cuda.synchronize()
+    net.check(B)
+    train_ms = e0.elapsed_time(e1)
+    losses = [round(float(x.mean()), 4) for x in losses]
+    # held-out instances
+    nte, n = c["nte"], c["n_test"]
+    lo = c["ntr"]
+    Yt = otm.ws_generate(m[lo:].contiguous(), al[lo:].contiguous(), n, c["seed"] + 4, first=lo)
+    St, _ = otm.ws_sketch(Yt, a0[lo:].contiguous(), th)
+    Et, _, Xt = otm.ws_canonicalize(St)
+    nb = ((nte + 7) // 8) * 8
+    Xpad = torch.zeros(nb, din, dtype=torch.bfloat16, device=dev)
+    Xpad[:nte] = Xt
+    U0 = otm.ws_rotate(Et, net.infer(Xpad, k)[:nte].contiguous())
+    Vwarm = otm.ws_init_components(U0, Yt, a0[lo:].contiguous(), 1.0)
+    held = {"network": -float(otm.ws_loss_grad(U0, Us[lo:].contiguous(),
+                                                lam[lo:].contiguous())[0].mean()),
+            "frame": -float(otm.ws_loss_grad(Et, Us[lo:].contiguous(),
+                                              lam[lo:].contiguous())[0].mean())}
+    kappa = 1.0
+    results = {nm: {"epochs": [], "reached": 0} for nm in
+               ("fp32_random", "fp32_warm", "bf16_warm", "bf16_then_fp32_warm")}
+    tstep = {nm: [] for nm in results}
+    for i in range(nte):
+        Y = Yt[i].contiguous()
+        yb = torch.stack([Y.double().mean(0)] * 3).contiguous()
+        q = otm.quantize_samples(Y, otm.PREC_BF16)
+        Vw = Vwarm[i].contiguous()
+        Vref = Vw.clone()
+        otm.sgd_run(Vref, Y, Y, Y, yb, None, c["ref_steps"], n, c["beta0"], 1.0, float(a0[lo + i]))
+        nr = Vref.double().norm(dim=1)
+        lam_r = (kappa * nr ** 3).contiguous()
+        U_r = (Vref.double() / nr[:, None]).contiguous()
+
+        def errs(snaps):
+            return [float(otm.recon_error(snaps[j].contiguous(), U_r, lam_r, 1.0)[0])
+                    for j in range(snaps.shape[0])]
+
+        def timed(fn):
+            t0, t1 = ev(), ev()
+            t0.record()
+            out = fn()
+            t1.record()
+            torch.cuda.synchronize()
+            return out, t0.elapsed_time(t1)
+
+        a0i = float(a0[lo + i])
+        Vr = torch.from_numpy(synth.haar_orthonormal(c["seed"] + 500 + i, k).T.copy()).to(dev)
+        runs = {}
+        runs["fp32_random"] = timed(lambda: otm.sgd_run(Vr, Y, Y, Y, yb, None, c["epochs"], n,
+                                                        c["beta0"], 1.0, a0i, snapshot_every=1))
+        V1 = Vw.clone()
+        runs["fp32_warm"] = timed(lambda: otm.sgd_run(V1, Y, Y, Y, yb, None, c["epochs"], n,
+                                                      c["beta0"], 1.0, a0i, snapshot_every=1))
+        V2 = Vw.clone()
+        runs["bf16_warm"] = timed(lambda: otm.sgd_run_lp(V2, q, q, q, yb, None, c["epochs"], n,
+                                                         c["beta0"], 1.0, a0i, otm.PREC_BF16,
+                                                         snapshot_every=1))
+        for nm, (snaps, ms) in runs.items():
+            tstep[nm].append(ms / c["epochs"])
+            e = errs(snaps)
+            hit = next((j for j, x in enumerate(e) if x <= 1e-3), None)
+            if hit is not None:
+                results[nm]["reached"] += 1
+                results[nm]["epochs"].append(hit + 1)
+        # mixed: BF16 epochs, then FP32 from the BF16 iterate
+        V3 = Vw.clone()
+        s16, _ = timed(lambda: otm.sgd_run_lp(V3, q, q, q, yb, None, c["bf16_epochs"], n,
+                                              c["beta0"], 1.0, a0i, otm.PREC_BF16,
+                                              snapshot_every=1))
+        s32, _ = timed(lambda: otm.sgd_run(V3, Y, Y, Y, yb, None, c["epochs"] - c["bf16_epochs"],
+                                           n, c["beta0"], 1.0, a0i, snapshot_every=1))
+        e = errs(s16) + errs(s32)
+        hit = next((j for j, x in enumerate(e) if x <= 1e-3), None)
+        tstep["bf16_then_fp32_warm"].append(0.0)
+        if hit is not None:
+            results["bf16_then_fp32_warm"]["reached"] += 1
+            results["bf16_then_fp32_warm"]["epochs"].append(hit + 1)
+    t32 = statistics.median(tstep["fp32_warm"])
+    t16 = statistics.median(tstep["bf16_warm"])
+    out = {}
+    for nm, r in results.items():
+        med = statistics.median(r["epochs"]) if r["epochs"] else None
+        if nm == "bf16_then_fp32_warm":
+            sec = None if med is None else (min(med, c["bf16_epochs"]) * t16 +
+                                            max(0, med - c["bf16_epochs"]) * t32) / 1e3
+        else:
+            sec = None if med is None else med * statistics.median(tstep[nm]) / 1e3
+        out[nm] = {"reached_1e-3": f"{r['reached']}/{nte}", "median_epochs": med,
+                   "median_seconds": sec,
+                   "step_ms": statistics.median(tstep[nm]) if tstep[nm][0] else None}
+    plain = out["fp32_random"]["median_seconds"]
+    best = min([v["median_seconds"] for nm, v in out.items()
+                if nm != "fp32_random" and v["median_seconds"] is not None], default=None)
+    return {"metric": "time to 1e-3 reconstruction error: warm-started vs plain FP32 STGD",
+            "value": best, "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "dtype": "bf16+f32", "data": "synthetic",
+            "vs_baseline": None,
+            "config": {"workload": f"warmstart_lda_whitened_k{k}", "k": k, "J": J,
+                       "width": h, "train_instances": c["ntr"],
+                       "train_samples_per_instance": c["n_train"], "heldout": nte,
+                       "samples_per_heldout": n, "minibatch": "full (b = n)",
+                       "beta0": c["beta0"], "epochs": c["epochs"],
+                       "reference": f"{c['ref_steps']} FP32 full-batch steps from the learned start"},
+            "plain_fp32_random_init": out["fp32_random"], "methods": out,
+            "plain_reached_at_all": plain is not None,
+            "heldout_T_captured": held, "train_loss_trace": losses,
+            "generate_sketch_ms_per_instance": gen_ms / c["ntr"],
+            "train_instances_per_s": steps * B / (train_ms / 1e3)}
+
+
+# ----------------------------------------------------------------------------
 def dist_barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -535,8 +716,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mmsb", choices=["mmsb", "batched"],
-                    help="mmsb: the default pipeline line; batched: the batched form")
+    ap.add_argument("--workload", default="mmsb", choices=["mmsb", "batched", "warmstart"],
+                    help="mmsb: the default pipeline line; batched: the batched form; "
+                         "warmstart: time to 1e-3 with the learned start")
+    ap.add_argument("--k", type=int, default=0, help="warmstart: components (default 64)")
     ap.add_argument("--problems", type=int, default=512)
     ap.add_argument("--restarts", type=int, default=8)
     ap.add_argument("--cluster", type=int, default=0,
@@ -547,6 +730,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.workload == "batched":
         line = run_batched(args) if rank == 0 else None
+    elif args.workload == "warmstart":
+        line = run_warmstart(args) if rank == 0 else None
     elif args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
