@@ -269,7 +269,7 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
 
 /*
  * otm_quantize_samples -- store whitened samples for the low-precision STGD.
- * Y: n x k float32 (row-major), 1 <= k <= 128.  Yq: n x ldq elements with
+ * Y: n x k float32 (row-major), 1 <= k <= 256.  Yq: n x ldq elements with
  * ldq = k rounded up to a multiple of 16, zero padded; BF16 (2 bytes each) or
  * FP8 e4m3 (1 byte each) per `precision`.  FP8 rows are scaled by one factor
  * per sample, scales[t] = max_r |Y[t][r]| / 448 (1 for an all-zero row), so
@@ -285,9 +285,11 @@ otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precis
  * their per-sample scales sA, sB, sC, NULL = 1; equal pointers select the
  * symmetric path), V re-quantised every step with one scale per component,
  * B = c1 A_A o A_B - c2 (...) quantised with one scale per component per 128
- * samples, FP32 accumulation in tensor memory; V, the Gram term, the mean
- * terms and the update stay FP32.  ybar3 are the FP64 means of the unquantised
- * samples.  1 <= k <= 128 (three distinct views: k <= 112 in BF16).
+ * samples, FP32 accumulation in tensor memory; the Gram term V((V^T V) o 2)
+ * and a_A = V^T ybar_A, a_B = V^T ybar_B run as BF16 tensor-core products of
+ * the BF16 image of V; the master V, the mean terms and the update stay FP32.
+ * ybar3 are the FP64 means of the unquantised samples.  1 <= k <= 256
+ * (k > 128: symmetric views only).
  * Scratch: otm_sgd_run_lp_workspace() bytes.  Synchronises the stream;
  * returns OTM_ETIMEOUT if a bounded wait on the tensor cores expired.
  */
@@ -306,9 +308,10 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
 
 /* One decomposition problem (symmetric views); all pointers are device
  * pointers.  Its `restarts` independent chains start from V[r * k * k ...]
- * (restart r, k x k, component-contiguous) and are updated in place. */
+ * (restart r, k x k, component-contiguous) and are updated in place.
+ * k <= 256. */
 typedef struct otm_problem {
-  int64_t n, k, b, epochs;   /* samples, components (1..128), minibatch, epochs */
+  int64_t n, k, b, epochs;   /* samples, components (1..256), minibatch, epochs */
   const void* Yq;            /* n x ldq samples from otm_quantize_samples */
   const float* scales;       /* per-sample scales or NULL */
   const int32_t* perm;       /* epochs x n sample orders or NULL */
@@ -320,12 +323,14 @@ typedef struct otm_problem {
 
 /* A prepared batch: filled by otm_sgd_batched_prepare, read by the launch. */
 typedef struct otm_batch_plan {
-  int32_t nitems;     /* chains = sum of restarts */
-  int32_t cluster;    /* CTAs per chain chosen by the autotuner (or given) */
+  int32_t nitems;         /* chains = sum of restarts */
+  int32_t cluster;        /* CTAs per chain (k <= 128), chosen by the autotuner or given */
   int32_t precision;
-  int32_t max_k;
-  int32_t grid_clusters;  /* clusters in the persistent grid */
-  int32_t reserved;
+  int32_t max_k;          /* largest k <= 128 */
+  int32_t grid_clusters;  /* clusters in the persistent grid (k <= 128) */
+  int32_t nitems_wide;    /* chains with 128 < k <= 256 (second launch, 16-CTA clusters) */
+  int32_t grid_clusters_wide;
+  int32_t max_k_wide;
   int64_t smem_bytes;
   void* ws;
   size_t ws_bytes;
@@ -341,9 +346,10 @@ typedef struct otm_batch_plan {
  * is kept (cached per precision, largest k and chain count).  Synchronises
  * the stream.  Each chain runs the Lemma 3 schedule of otm_sgd_run_lp.
  *
- * otm_sgd_batched_launch -- ONE persistent launch running every chain of the
- * plan: as many clusters as fit on the GPU take chains from the work list
- * until it is empty.  Asynchronous and free of host synchronisation, so it can
+ * otm_sgd_batched_launch -- one persistent launch running every chain with
+ * k <= 128 (and, if the plan has any, a second one for 128 < k <= 256, whose
+ * chains use 16-CTA clusters): as many clusters as fit on the GPU take chains
+ * from the work list until it is empty.  Asynchronous and free of host synchronisation, so it can
  * be captured in a CUDA graph.  otm_sgd_batched_check reads the plan's
  * timeout flag (synchronises; OTM_ETIMEOUT if a tensor-core wait expired).
  */

@@ -56,11 +56,11 @@ namespace {
 using namespace tc;
 
 constexpr int TILE = 128;        // samples per tile (M of the first product)
-constexpr int KP = 128;          // padded coordinates (M of the second product)
-constexpr int VROWS = 128;       // rows of the V image (components, zero padded)
+// Coordinates and components are padded to KPc = 128 (k <= 128) or 256 (k <= 256);
+// products whose M runs over coordinates or components are issued per 128-row block.
 constexpr int TC_THREADS = 256;  // 8 warps: two per 32-lane TMEM quarter
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int TC_KMAX = 128;
+constexpr int TC_KMAX = 256;
 constexpr int NMBAR = 5;         // mbarriers: first product x2, second x2, Gram
 
 struct TcArgs {
@@ -89,7 +89,7 @@ __host__ __device__ inline int own_cols(int k, int cl) {
 }
 
 struct TcLayout {
-  int N, nv, NS, es, CR, CRb, CBn, CBh;
+  int N, nv, NS, es, KPc, CR, CRb, CBn, CBh;
   bool dbl;
   size_t y_view, y_stage, off_v[2], off_vq, off_yb, off_b[2], off_h, off_f;
   size_t vm, ybA, ybB, ybC, aA, aB, vsc, bsc, amax, spw, red, ssc, nfloat;
@@ -98,8 +98,13 @@ struct TcLayout {
 
 __host__ __device__ inline size_t al128(size_t x) { return (x + 127) & ~(size_t)127; }
 
-__host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, bool dbl) {
+// KPc: 128 or 256 padded coordinates; the second B image exists only with four
+// stages (where the second product is waited for two tiles later)
+__host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, bool dbl,
+                                              int KPc) {
   TcLayout L;
+  const int KP = KPc;
+  L.KPc = KPc;
   L.N = N;
   L.nv = sym ? 1 : 3;
   L.NS = NS;
@@ -111,19 +116,24 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   L.CBh = N * 2 / 16;
   L.y_view = (size_t)TILE * KP * es;
   L.y_stage = L.nv * L.y_view;
-  const size_t v_bytes = (size_t)VROWS * KP * 2;
+  const size_t v_bytes = (size_t)KP * KP * 2;  // KPc rows (components) x KPc coordinates
   L.off_v[0] = NS * L.y_stage;
   L.off_v[1] = dbl ? L.off_v[0] + v_bytes : L.off_v[0];
   L.off_vq = L.off_v[1] + v_bytes;
   const size_t vq_bytes = es == 1 ? (size_t)N * KP : 0;
   const size_t b_bytes = (size_t)TILE * N * es;
-  L.off_yb = al128(L.off_vq + vq_bytes);   // 16 rows: ybar_A, ybar_B, zeros (BF16)
-  L.off_b[0] = al128(L.off_yb + (size_t)16 * KP * 2);
-  L.off_b[1] = L.off_b[0] + b_bytes;
+  // the B images, the H image and the ybar image (16 rows: ybar_A, ybar_B, zeros;
+  // rebuilt at the start of every step) share one region: they are live at
+  // different times of a step
+  L.off_b[0] = al128(L.off_vq + vq_bytes);
+  L.off_b[1] = NS >= 4 ? L.off_b[0] + b_bytes : L.off_b[0];
+  L.off_yb = L.off_b[0];
   L.off_h = L.off_b[0];  // the H image reuses both B images (free by then)
   size_t end = L.off_b[1] + b_bytes;
-  const size_t h_bytes = (size_t)VROWS * N * 2;
+  const size_t h_bytes = (size_t)KP * N * 2;
   if (L.off_h + h_bytes > end) end = L.off_h + h_bytes;
+  const size_t yb_bytes = (size_t)16 * KP * 2;
+  if (L.off_yb + yb_bytes > end) end = L.off_yb + yb_bytes;
   L.off_f = al128(end);
   size_t f = 0;
   L.vm = f;   f += (size_t)N * KP;
@@ -237,8 +247,10 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int qd = warp & 3, hf = warp >> 2;
   const int k = a.k;
+  const int KPc = k <= 128 ? 128 : 256;  // padded coordinates / components
+  const int MB = KPc / 128;               // 128-row blocks
   const int N = own_cols(k, CL);
-  const TcLayout L = tc_layout(N, SYM, ES, NS, dbl);
+  const TcLayout L = tc_layout(N, SYM, ES, NS, dbl, KPc);
   const int own_lo = q * N;
   const bool active = own_lo < k;
   const int nch = N / 16;
@@ -265,18 +277,23 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   const uint32_t tmem = cx.tmem;
   uint32_t ph = cx.ph;
   const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+  // TMEM columns: first product (2 slots x views), second product per coordinate block
+  // (two slots each for FP8), the means (16), G_gram per coordinate block; H per
+  // component block reuses the first product's columns
   const uint32_t colD2b = (uint32_t)(2 * NVD * N);
-  const uint32_t colH = 0, colGG = (uint32_t)N;
+  const uint32_t d2w = (uint32_t)((FP8 ? 2 : 1) * N);
+  const uint32_t colY = colD2b + (uint32_t)MB * d2w;
+  const uint32_t colGGb = MB == 1 ? (uint32_t)N : colY + 16;
   const int ks1 = (k + KSTEP - 1) / KSTEP;  // coordinate steps of the first product
   const int kg16 = (k + 15) / 16;           // 16-steps of the Gram products
   const size_t own_off = ((size_t)(own_lo >> 3) * L.CRb) << 7;
 
   // ---- initial state: owned FP32 rows, BF16 image of all rows, means ----
-  for (int idx = tid; idx < N * KP; idx += TC_THREADS) {
-    const int i = idx / KP, r = idx % KP, c = own_lo + i;
+  for (int idx = tid; idx < N * KPc; idx += TC_THREADS) {
+    const int i = idx / KPc, r = idx % KPc, c = own_lo + i;
     Vm[idx] = (c < k && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
   }
-  for (int idx = tid; idx < VROWS * L.CRb; idx += TC_THREADS) {
+  for (int idx = tid; idx < KPc * L.CRb; idx += TC_THREADS) {
     const int c = idx / L.CRb, rg = idx % L.CRb;
     float v[8];
 #pragma unroll
@@ -293,34 +310,37 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     *reinterpret_cast<uint4*>(Vimg0 + off) = w;
     if (dbl) *reinterpret_cast<uint4*>(Vimg1 + off) = w;
   }
-  for (int r = tid; r < KP; r += TC_THREADS) {
+  for (int r = tid; r < KPc; r += TC_THREADS) {
     ybA[r] = r < k ? (float)a.ybar3[r] : 0.f;
     ybB[r] = r < k ? (float)a.ybar3[k + r] : 0.f;
     ybC[r] = r < k ? (float)a.ybar3[2 * k + r] : 0.f;
   }
   for (int i = tid; i < 2 * N; i += TC_THREADS) amax[i] = 0u;
-  // ybar image: rows 0, 1 = ybar_A, ybar_B (BF16, K-major like V), rows 2..15 zero
   uint8_t* Ybimg = smem + L.off_yb;
-  for (int idx = tid; idx < 16 * L.CRb; idx += TC_THREADS) {
-    const int c = idx / L.CRb, rg = idx % L.CRb;
-    float v[8];
+  // ybar image: rows 0, 1 = ybar_A, ybar_B (BF16, K-major like V), rows 2..15 zero
+  auto build_ybar_image = [&]() {
+    for (int idx = tid; idx < 16 * L.CRb; idx += TC_THREADS) {
+      const int c = idx / L.CRb, rg = idx % L.CRb;
+      float v[8];
 #pragma unroll
-    for (int z = 0; z < 8; ++z) {
-      const int r = rg * 8 + z;
-      v[z] = (r < k && c < 2) ? (float)a.ybar3[c * k + r] : 0.f;
+      for (int z = 0; z < 8; ++z) {
+        const int r = rg * 8 + z;
+        v[z] = (r < k && c < 2) ? (c == 0 ? ybA[r] : ybB[r]) : 0.f;
+      }
+      uint4 w;
+      w.x = pack_bf16(v[0], v[1]);
+      w.y = pack_bf16(v[2], v[3]);
+      w.z = pack_bf16(v[4], v[5]);
+      w.w = pack_bf16(v[6], v[7]);
+      *reinterpret_cast<uint4*>(Ybimg + (((size_t)(c >> 3) * L.CRb + rg) << 7) + ((c & 7) << 4)) =
+          w;
     }
-    uint4 w;
-    w.x = pack_bf16(v[0], v[1]);
-    w.y = pack_bf16(v[2], v[3]);
-    w.z = pack_bf16(v[4], v[5]);
-    w.w = pack_bf16(v[6], v[7]);
-    *reinterpret_cast<uint4*>(Ybimg + (((size_t)(c >> 3) * L.CRb + rg) << 7) + ((c & 7) << 4)) = w;
-  }
+  };
   __syncthreads();
   if (FP8) {
     for (int i = warp; i < N; i += TC_THREADS / 32) {
       float m = 0.f;
-      for (int r = lane; r < KP; r += 32) m = fmaxf(m, fabsf(Vm[i * KP + r]));
+      for (int r = lane; r < KPc; r += 32) m = fmaxf(m, fabsf(Vm[i * KPc + r]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       if (lane == 0) vsc[i] = m > 0.f ? m / QMAX : 1.f;
@@ -335,7 +355,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     for (int idx = tid; idx < N * L.CR; idx += TC_THREADS) {
       const int i = idx / L.CR, rg = idx % L.CR;
       const float inv = 1.f / vsc[i];
-      const float* vr = Vm + i * KP + rg * 16;
+      const float* vr = Vm + i * KPc + rg * 16;
       uint4 w;
       w.x = pack_e4m3(vr[0] * inv, vr[1] * inv, vr[2] * inv, vr[3] * inv);
       w.y = pack_e4m3(vr[4] * inv, vr[5] * inv, vr[6] * inv, vr[7] * inv);
@@ -405,7 +425,6 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   if (active)
     for (int i = 0; i < NS - W; ++i) issue_one();
 
-  const uint32_t colY = colD2b + (uint32_t)((FP8 ? 2 : 1) * N);
   int cur = 0;
   int64_t gbase = 0;
   int gstage = 0;  // ring stage of the step's first tile
@@ -425,17 +444,19 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       for (int c = 0; c < 8; ++c)
 #pragma unroll
         for (int j = 0; j < 8; ++j) spart[c][j] = 0.f;
-      float gacc[FP8 ? 4 : 1][8];
+      float gacc[FP8 ? 2 : 1][FP8 ? 4 : 1][8];
 #pragma unroll
-      for (int c = 0; c < (FP8 ? 4 : 1); ++c)
+      for (int u = 0; u < (FP8 ? 2 : 1); ++u)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) gacc[c][j] = 0.f;
+        for (int c = 0; c < (FP8 ? 4 : 1); ++c)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) gacc[u][c][j] = 0.f;
 
       // descriptors (the start address is the low 14-bit field, in 16-byte units)
       const uint64_t dV_own = sdesc(Vc + own_off, 128, (uint32_t)L.CRb * 128);
       const uint64_t dVq = sdesc(Vq, 128, (uint32_t)L.CR * 128);
       const uint32_t id1 = make_idesc(FMT, 0, 0, TILE, (uint32_t)N);
-      const uint32_t id2 = make_idesc(FMT, 1, 1, KP, (uint32_t)N);
+      const uint32_t id2 = make_idesc(FMT, 1, 1, 128, (uint32_t)N);
 
       // first product A = Y V_own of the tile in stage st (thread 0)
       auto gemm1 = [&](int slot, int st) {
@@ -453,36 +474,52 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       auto gemm2 = [&](int n, int st) {
         const int slot = n & 1;
         const uint8_t* YC = smem + (size_t)st * L.y_stage + (SYM ? 0 : 2 * L.y_view);
-        const uint64_t dA = sdesc(YC, (uint32_t)L.CR * 128, 128);
         const uint64_t dB = sdesc(slot ? Bimg1 : Bimg0, (uint32_t)L.CBn * 128, 128);
-        const uint32_t col = colD2b + (FP8 ? (uint32_t)(slot * N) : 0u);
         const uint64_t stepA = (uint64_t)((KSTEP / 8) * L.CR * 8);   // (KSTEP/8) core groups
         const uint64_t stepB = (uint64_t)((KSTEP / 8) * L.CBn * 8);  // in 16-byte units
-        for (int ks = 0; ks < TILE / KSTEP; ++ks)
-          mma<FP8>(tmem + col, dA + stepA * ks, dB + stepB * ks, id2,
-                   (FP8 ? ks > 0 : (n > 0 || ks > 0)) ? 1u : 0u);
+        for (int mbk = 0; mbk < MB; ++mbk) {  // 128 coordinates = 1024 ES bytes along M
+          const uint64_t dA = sdesc(YC + (size_t)mbk * 1024 * ES, (uint32_t)L.CR * 128, 128);
+          const uint32_t col = colD2b + (uint32_t)mbk * d2w + (FP8 ? (uint32_t)(slot * N) : 0u);
+          for (int ks = 0; ks < TILE / KSTEP; ++ks)
+            mma<FP8>(tmem + col, dA + stepA * ks, dB + stepB * ks, id2,
+                     (FP8 ? ks > 0 : (n > 0 || ks > 0)) ? 1u : 0u);
+        }
         mma_commit(&mb[2 + slot]);
       };
       // FP8: per-tile second product, scaled by the tile's B scales
       auto epi2 = [&](int n) {
         const int slot = n & 1;
 #pragma unroll
-        for (int c = 0; c < (FP8 ? 4 : 1); ++c) {
-          if (c < nch) {
-            const int c0 = 16 * c + 8 * hf;
-            float x[8];
-            tmem_ld8(tmem + lane_base + colD2b + (uint32_t)(slot * N + c0), x);
+        for (int u = 0; u < (FP8 ? 2 : 1); ++u) {
+          if (u < MB) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) gacc[c][j] = fmaf(x[j], bsc[slot * N + c0 + j], gacc[c][j]);
+            for (int c = 0; c < (FP8 ? 4 : 1); ++c) {
+              if (c < nch) {
+                const int c0 = 16 * c + 8 * hf;
+                float x[8];
+                tmem_ld8(tmem + lane_base + colD2b + (uint32_t)u * d2w + (uint32_t)(slot * N + c0),
+                         x);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  gacc[u][c][j] = fmaf(x[j], bsc[slot * N + c0 + j], gacc[u][c][j]);
+              }
+            }
           }
         }
       };
 
-      // a_A = V^T ybar_A, a_B = V^T ybar_B for every component (one MMA, N = 16)
+      // a_A = V^T ybar_A, a_B = V^T ybar_B for the 128 components of the block holding
+      // the owned ones (one MMA chain, N = 16)
+      const int mbo = own_lo >> 7;
+      build_ybar_image();
+      fence_async_smem();
+      tc_before();
+      __syncthreads();
+      tc_after();
       if (tid == 0 && !s_abort) {
-        const uint64_t dA = sdesc(Vc, 128, (uint32_t)L.CRb * 128);
+        const uint64_t dA = sdesc(Vc + (((size_t)mbo * 16 * L.CRb) << 7), 128, (uint32_t)L.CRb * 128);
         const uint64_t dB = sdesc(Ybimg, 128, (uint32_t)L.CRb * 128);
-        const uint32_t id = make_idesc(1, 0, 0, VROWS, 16);
+        const uint32_t id = make_idesc(1, 0, 0, 128, 16);
         for (int ks = 0; ks < kg16; ++ks)
           mma<false>(tmem + colY, dA + (uint64_t)(16 * ks), dB + (uint64_t)(16 * ks), id,
                      ks > 0 ? 1u : 0u);
@@ -497,7 +534,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       if (hf == 0) {  // lanes = components: keep the owned ones
         float x[8];
         tmem_ld8(tmem + lane_base + colY, x);
-        const int j = 32 * qd + lane;
+        const int j = mbo * 128 + 32 * qd + lane;
         if (j >= own_lo && j < own_lo + N) {
           aA[j - own_lo] = x[0];
           aB[j - own_lo] = SYM ? x[0] : x[1];
@@ -631,22 +668,25 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       __syncthreads();
       tc_after();
       if (tid == 0 && !s_abort) {
-        const uint64_t dA = sdesc(Vc, 128, (uint32_t)L.CRb * 128);
-        const uint32_t id = make_idesc(1, 0, 0, VROWS, (uint32_t)N);
-        for (int ks = 0; ks < kg16; ++ks)
-          mma<false>(tmem + colH, dA + (uint64_t)(16 * ks), dV_own + (uint64_t)(16 * ks), id,
-                     ks > 0 ? 1u : 0u);
+        const uint32_t id = make_idesc(1, 0, 0, 128, (uint32_t)N);
+        for (int mbk = 0; mbk < MB; ++mbk) {  // components j in blocks of 128 rows
+          const uint64_t dA =
+              sdesc(Vc + (((size_t)mbk * 16 * L.CRb) << 7), 128, (uint32_t)L.CRb * 128);
+          for (int ks = 0; ks < kg16; ++ks)
+            mma<false>(tmem + (uint32_t)(mbk * N), dA + (uint64_t)(16 * ks),
+                       dV_own + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
+        }
         mma_commit(&mb[4]);
       }
       wait_mb(4);
-      {
-        const int j = 32 * qd + lane;
+      for (int mbk = 0; mbk < MB; ++mbk) {
+        const int j = mbk * 128 + 32 * qd + lane;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           if (c < nch) {
             const int c0 = 16 * c + 8 * hf;
             float x[8];
-            tmem_ld8(tmem + lane_base + colH + (uint32_t)c0, x);
+            tmem_ld8(tmem + lane_base + (uint32_t)(mbk * N + c0), x);
             uint4 u;
             u.x = pack_bf16(x[0] * x[0], x[1] * x[1]);
             u.y = pack_bf16(x[2] * x[2], x[3] * x[3]);
@@ -662,30 +702,35 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       __syncthreads();
       tc_after();
       if (tid == 0 && !s_abort) {
-        const uint64_t dA = sdesc(Vc, (uint32_t)L.CRb * 128, 128);
         const uint64_t dB = sdesc(Himg, (uint32_t)L.CBh * 128, 128);
-        const uint32_t id = make_idesc(1, 1, 1, KP, (uint32_t)N);
-        for (int ks = 0; ks < kg16; ++ks)
-          mma<false>(tmem + colGG, dA + (uint64_t)(2 * L.CRb * 8 * ks),
-                     dB + (uint64_t)(2 * L.CBh * 8 * ks), id, ks > 0 ? 1u : 0u);
+        const uint32_t id = make_idesc(1, 1, 1, 128, (uint32_t)N);
+        for (int mbk = 0; mbk < MB; ++mbk) {  // coordinates in blocks of 128 (2048 bytes)
+          const uint64_t dA = sdesc(Vc + (size_t)mbk * 2048, (uint32_t)L.CRb * 128, 128);
+          for (int ks = 0; ks < kg16; ++ks)
+            mma<false>(tmem + colGGb + (uint32_t)(mbk * N), dA + (uint64_t)(2 * L.CRb * 8 * ks),
+                       dB + (uint64_t)(2 * L.CBh * 8 * ks), id, ks > 0 ? 1u : 0u);
+        }
         mma_commit(&mb[4]);
       }
       wait_mb(4);
 
-      // -- update of the owned columns (thread = coordinate r) --
-      {
-        const int r = 32 * qd + lane;
+      // -- update of the owned columns (thread = coordinate r, per 128-row block) --
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c < nch) {
-            const int c0 = 16 * c + 8 * hf;
+      for (int c = 0; c < 8; ++c) {
+        if (c < nch) {
+          const int c0 = 16 * c + 8 * hf;
+          float mcol[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) mcol[j] = 0.f;
+          for (int mbk = 0; mbk < MB; ++mbk) {
+            const int r = mbk * 128 + 32 * qd + lane;
             float gg[8], gd[8];
-            tmem_ld8(tmem + lane_base + colGG + (uint32_t)c0, gg);
+            tmem_ld8(tmem + lane_base + colGGb + (uint32_t)(mbk * N + c0), gg);
             if constexpr (FP8) {
 #pragma unroll
-              for (int j = 0; j < 8; ++j) gd[j] = gacc[c < 4 ? c : 0][j];
+              for (int j = 0; j < 8; ++j) gd[j] = gacc[mbk & 1][c < 4 ? c : 0][j];
             } else {
-              tmem_ld8(tmem + lane_base + colD2b + (uint32_t)c0, gd);
+              tmem_ld8(tmem + lane_base + colD2b + (uint32_t)mbk * d2w + (uint32_t)c0, gd);
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -696,19 +741,23 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
                   const float s_i = spw[i] + spw[N + i] + spw[2 * N + i] + spw[3 * N + i];
                   const float gdata =
                       gd[j] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * s_i * inv_b);
-                  vnew = Vm[i * KP + r] - beta * (a.kappa * gg[j] - gdata);
-                  Vm[i * KP + r] = vnew;
+                  vnew = Vm[i * KPc + r] - beta * (a.kappa * gg[j] - gdata);
+                  Vm[i * KPc + r] = vnew;
                 }
                 *reinterpret_cast<__nv_bfloat16*>(
                     Vn + ((((size_t)(comp >> 3) * L.CRb + (r >> 3)) << 7) + ((comp & 7) << 4) +
                           ((r & 7) << 1))) = __float2bfloat16_rn(vnew);
+                mcol[j] = fmaxf(mcol[j], fabsf(vnew));
               }
-              if (FP8) {
-                float m = (comp < k && r < k) ? fabsf(Vm[i * KP + r]) : 0.f;
+            }
+          }
+          if (FP8) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                if (lane == 0) red[qd * N + i] = m;
-              }
+            for (int j = 0; j < 8; ++j) {
+              float m = mcol[j];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+              if (lane == 0) red[qd * N + c0 + j] = m;
             }
           }
         }
@@ -724,7 +773,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
         for (int idx = tid; idx < N * k; idx += TC_THREADS) {
           const int i = idx / k, r = idx % k;
-          if (own_lo + i < k) dst[(int64_t)(own_lo + i) * k + r] = Vm[i * KP + r];
+          if (own_lo + i < k) dst[(int64_t)(own_lo + i) * k + r] = Vm[i * KPc + r];
         }
       }
       __syncthreads();
@@ -758,7 +807,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   if (active) {
     for (int idx = tid; idx < N * k; idx += TC_THREADS) {
       const int i = idx / k, r = idx % k;
-      if (own_lo + i < k) a.V[(int64_t)(own_lo + i) * k + r] = Vm[i * KP + r];
+      if (own_lo + i < k) a.V[(int64_t)(own_lo + i) * k + r] = Vm[i * KPc + r];
     }
   }
   cx.ph = ph;
@@ -886,15 +935,18 @@ struct TcPlan {
 // whose tensor memory, registers and shared memory fit; false if none does.
 bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
   const int N = own_cols(k, CL);
+  const int KPc = k <= 128 ? 128 : 256, MB = KPc / 128;
   if (N > 128 || (fp8 && N > 64)) return false;
+  if (MB > 1 && 128 % N != 0) return false;  // owned rows inside one 128-row block
   const int nvd = sym ? 1 : 2;
-  if ((2 * nvd + (fp8 ? 2 : 1)) * N + 16 > (int)TMEM_COLS) return false;
+  if (2 * nvd * N + MB * (fp8 ? 2 : 1) * N + 16 + (MB > 1 ? MB * N : 0) > (int)TMEM_COLS)
+    return false;
   const size_t lim = (size_t)max_smem_optin() - 1024;  // static shared variables
   const int order[8][2] = {{1, 4}, {1, 3}, {0, 4}, {0, 3}, {1, 2}, {0, 2}, {1, 1}, {0, 1}};
   for (const auto& o : order) {
     const bool dbl = o[0] != 0;
     if (dbl && CL == 1) continue;
-    const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, o[1], dbl);
+    const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, o[1], dbl, KPc);
     if (L.total <= lim) {
       *out = {CL, N, o[1], dbl, L.total};
       return true;
@@ -1149,12 +1201,29 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   OTM_REQUIRE(ws_bytes >= otm_sgd_batched_workspace(nitems),
               "otm_sgd_batched_prepare: workspace too small (need %zu bytes)",
               otm_sgd_batched_workspace(nitems));
-  // longest chains first: the tail of the persistent loop is then short ones
+  // two groups, each its own persistent launch: k <= 128 (autotuned cluster) first,
+  // then k > 128 (256 padded coordinates, 16-CTA clusters); longest chains first
+  // within a group, so that the tail of each persistent loop holds short ones
   std::vector<int> order(nitems);
   for (int i = 0; i < nitems; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const bool wx = items[x].k > 128, wy = items[y].k > 128;
+    if (wx != wy) return wy;
+    return cost[x] > cost[y];
+  });
   std::vector<TcArgs> sorted(nitems);
   for (int i = 0; i < nitems; ++i) sorted[i] = items[order[i]];
+  int n_wide = 0, max_k_wide = 0;
+  max_k = 0;
+  for (const TcArgs& a : sorted) {
+    if (a.k > 128) {
+      ++n_wide;
+      max_k_wide = std::max(max_k_wide, a.k);
+    } else {
+      max_k = std::max(max_k, a.k);
+    }
+  }
+  const int n_narrow = nitems - n_wide;
   Workspace w(ws, ws_bytes);
   int* hdr = w.take<int>(64);
   TcArgs* dev_items = w.take<TcArgs>(nitems);
@@ -1162,6 +1231,10 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   float* scratchV = w.take<float>((size_t)std::min(nitems, 512) * TC_KMAX * TC_KMAX);
   cudaStream_t st = as_stream(stream);
   for (int i = 0; i < nitems; ++i) sorted[i].err = hdr + 1;
+  TcPlan Pw{};
+  if (n_wide > 0)
+    OTM_REQUIRE(tc_plan(max_k_wide, true, fp8, 16, &Pw),
+                "otm_sgd_batched_prepare: k=%d does not fit on chip", max_k_wide);
   OTM_CHECK_CUDA(cudaMemcpyAsync(dev_items, sorted.data(), sizeof(TcArgs) * nitems,
                                  cudaMemcpyHostToDevice, st));
   OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 64 * sizeof(int), st));
@@ -1169,14 +1242,16 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   std::vector<int> cands;
   for (int c : {1, 2, 4, 8, 16}) {
     TcPlan Pc;
+    if (n_narrow == 0) break;
     // every CTA of the cluster must own components of the largest problem
     if ((c - 1) * own_cols(max_k, c) >= round16(max_k)) continue;
     if (tc_plan(max_k, true, fp8, c, &Pc)) cands.push_back(c);
   }
-  OTM_REQUIRE(!cands.empty() || cluster != 0,
+  OTM_REQUIRE(n_narrow == 0 || !cands.empty() || cluster != 0,
               "otm_sgd_batched_prepare: k=%d does not fit shared memory", max_k);
-  int chosen = cluster;
-  if (chosen != 0) {
+  int chosen = n_narrow == 0 ? 16 : cluster;
+  if (n_narrow == 0) {
+  } else if (chosen != 0) {
     TcPlan Pc;
     OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pc),
                 "otm_sgd_batched_prepare: cluster %d does not fit k=%d", chosen, max_k);
@@ -1190,7 +1265,7 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
       if (f != g_tune_cache.end()) chosen = f->second;
     }
     if (chosen == 0) {
-      const int ntrial = std::min(nitems, 512);
+      const int ntrial = std::min(n_narrow, 512);
       std::vector<TcArgs> trial(sorted.begin(), sorted.begin() + ntrial);
       for (int i = 0; i < ntrial; ++i) {
         trial[i].V = scratchV + (size_t)i * TC_KMAX * TC_KMAX;
@@ -1235,12 +1310,17 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
       g_tune_cache[key] = chosen;
     }
   }
-  TcPlan Pch;
-  OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pch), "otm_sgd_batched_prepare: no plan");
-  {
+  TcPlan Pch{};
+  if (n_narrow > 0) {
+    OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pch), "otm_sgd_batched_prepare: no plan");
     otm_status s3 = fp8 ? launch_batched<true>(Pch, dev_items, 0, hdr, 1, st, true)
                         : launch_batched<false>(Pch, dev_items, 0, hdr, 1, st, true);
     if (s3 != OTM_OK) return s3;
+  }
+  if (n_wide > 0) {
+    otm_status s4 = fp8 ? launch_batched<true>(Pw, dev_items, 0, hdr, 1, st, true)
+                        : launch_batched<false>(Pw, dev_items, 0, hdr, 1, st, true);
+    if (s4 != OTM_OK) return s4;
   }
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
   plan->nitems = nitems;
@@ -1248,7 +1328,10 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   plan->precision = precision;
   plan->max_k = max_k;
   plan->smem_bytes = (int64_t)Pch.smem;
-  plan->grid_clusters = std::min(batched_clusters(fp8, Pch), nitems);
+  plan->grid_clusters = n_narrow > 0 ? std::min(batched_clusters(fp8, Pch), n_narrow) : 0;
+  plan->nitems_wide = n_wide;
+  plan->max_k_wide = max_k_wide;
+  plan->grid_clusters_wide = n_wide > 0 ? std::min(batched_clusters(fp8, Pw), n_wide) : 0;
   plan->ws = ws;
   plan->ws_bytes = ws_bytes;
   return OTM_OK;
@@ -1256,20 +1339,36 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
 
 otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
   clear_error();
-  OTM_REQUIRE(plan && plan->ws && plan->nitems >= 1 && plan->grid_clusters >= 1,
+  OTM_REQUIRE(plan && plan->ws && plan->nitems >= 1 && plan->nitems_wide >= 0 &&
+                  plan->nitems_wide <= plan->nitems,
               "otm_sgd_batched_launch: invalid plan");
+  const int n_wide = plan->nitems_wide, n_narrow = plan->nitems - n_wide;
   cudaStream_t st = as_stream(stream);
   Workspace w(plan->ws, plan->ws_bytes);
   int* hdr = w.take<int>(64);
   TcArgs* dev_items = w.take<TcArgs>(plan->nitems);
-  OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 2 * sizeof(int), st));
+  OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 3 * sizeof(int), st));  // counters and the flag
   const bool fp8 = plan->precision == OTM_PREC_FP8;
-  TcPlan P;
-  OTM_REQUIRE(tc_plan(plan->max_k, true, fp8, plan->cluster, &P) &&
-                  (int64_t)P.smem == plan->smem_bytes,
-              "otm_sgd_batched_launch: plan does not match this library");
-  return fp8 ? launch_batched<true>(P, dev_items, plan->nitems, hdr, plan->grid_clusters, st, false)
-             : launch_batched<false>(P, dev_items, plan->nitems, hdr, plan->grid_clusters, st, false);
+  if (n_narrow > 0) {
+    TcPlan P;
+    OTM_REQUIRE(tc_plan(plan->max_k, true, fp8, plan->cluster, &P) &&
+                    (int64_t)P.smem == plan->smem_bytes && plan->grid_clusters >= 1,
+                "otm_sgd_batched_launch: plan does not match this library");
+    OTM_TRY(fp8 ? launch_batched<true>(P, dev_items, n_narrow, hdr, plan->grid_clusters, st,
+                                       false)
+                : launch_batched<false>(P, dev_items, n_narrow, hdr, plan->grid_clusters, st,
+                                        false));
+  }
+  if (n_wide > 0) {
+    TcPlan P;
+    OTM_REQUIRE(tc_plan(plan->max_k_wide, true, fp8, 16, &P) && plan->grid_clusters_wide >= 1,
+                "otm_sgd_batched_launch: plan does not match this library");
+    OTM_TRY(fp8 ? launch_batched<true>(P, dev_items + n_narrow, n_wide, hdr + 2,
+                                       plan->grid_clusters_wide, st, false)
+                : launch_batched<false>(P, dev_items + n_narrow, n_wide, hdr + 2,
+                                        plan->grid_clusters_wide, st, false));
+  }
+  return OTM_OK;
 }
 
 otm_status otm_sgd_batched_check(const otm_batch_plan* plan, void* stream) {

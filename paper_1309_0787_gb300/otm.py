@@ -43,7 +43,8 @@ class OtmProblem(ctypes.Structure):
 class OtmBatchPlan(ctypes.Structure):
     _fields_ = [("nitems", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_k", ctypes.c_int32),
-                ("grid_clusters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("grid_clusters", ctypes.c_int32), ("nitems_wide", ctypes.c_int32),
+                ("grid_clusters_wide", ctypes.c_int32), ("max_k_wide", ctypes.c_int32),
                 ("smem_bytes", c_i64), ("ws", c_vp), ("ws_bytes", c_sz)]
 
 

@@ -86,6 +86,23 @@ def test_batched_mixed_sizes_autotuned(otm, prec_name):
             assert rel(to_np(p["V"][r]), to_np(Vs)) < tol
 
 
+def test_batched_two_groups_beyond_128(otm):
+    """Problems with k <= 128 and k > 128 in one batch (two persistent launches):
+    every chain matches its own single-chain run."""
+    prec = otm.PREC_BF16
+    specs = [(71, 48, 800, 128, 2, 2), (72, 200, 1024, 256, 1, 2), (73, 256, 1024, 512, 1, 1)]
+    probs = [_problem(otm, s, k, n, b, e, r, 5e-3, prec) for s, k, n, b, e, r in specs]
+    batch = otm.SgdBatch(probs, prec)
+    assert batch.nitems == 5 and batch.plan.nitems_wide == 3
+    batch.launch()
+    batch.check()
+    for p in probs:
+        for r in range(p["V0"].shape[0]):
+            Vs = _single(otm, p, r, prec)
+            torch.cuda.synchronize()
+            assert rel(to_np(p["V"][r]), to_np(Vs)) < 1e-2
+
+
 def test_batched_tracks_oracle(otm):
     """Batched BF16 chains against the FP64 oracle run of Lemma 3."""
     prec = otm.PREC_BF16

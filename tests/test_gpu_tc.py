@@ -93,3 +93,22 @@ def test_quantize_samples_roundtrip(otm):
     # e4m3: 3 mantissa bits -> relative rounding error <= 2^-4 of each value's scale
     assert np.all(np.abs(yf - Y) <= 2 ** -4 * np.abs(Y) + 2 ** -9 * to_np(sf)[:, None] * 448)
     assert np.all(to_np(qb)[:, 74:] == 0) and np.all(to_np(qf)[:, 37:] == 0)
+
+
+@pytest.mark.parametrize("k,b,prec_name,tol", [(200, 512, "PREC_BF16", 2e-2),
+                                               (256, 1024, "PREC_BF16", 2e-2),
+                                               (256, 512, "PREC_FP8", 6e-2)])
+def test_tc_gradient_beyond_128_components(otm, k, b, prec_name, tol):
+    """k > 128: 256 padded coordinates, products per 128-row block (symmetric views)."""
+    err = _grad_err(otm, getattr(otm, prec_name), k, b, True, 1.0, 7 * k + b)
+    assert err < tol, err
+
+
+def test_tc_three_views_beyond_128_rejected(otm):
+    k, n = 160, 64
+    Y = torch.zeros(n, k, device="cuda")
+    q = [otm.quantize_samples(Y + i, otm.PREC_BF16) for i in range(3)]
+    V = torch.zeros(k, k, device="cuda")
+    yb = torch.zeros(3, k, dtype=torch.float64, device="cuda")
+    with pytest.raises(otm.OtmError):
+        otm.sgd_run_lp(V, q[0], q[1], q[2], yb, None, 1, 32, 1e-2, 1.0, 1.0, otm.PREC_BF16)
