@@ -16,23 +16,30 @@
 // "device interface" of Section 4.3: V never leaves the chip).  Each CTA of
 // the cluster holds a full copy of V in shared memory and processes a slice
 // of the minibatch in chunks of 32 samples (register-tiled FP32 FMAs for both
-// products).  Partial Y_C^T B^T are reduced column-wise through distributed
+// products; the next chunk arrives by cp.async while one is computed, and the
+// next step's row indices are fetched a step ahead).  Partial Y_C^T B^T are reduced column-wise through distributed
 // shared memory: CTA q owns columns [q*cpq, (q+1)*cpq), sums them over the
 // cluster, adds the Gram and mean terms and broadcasts the new columns into
-// every CTA's next-V buffer.  Two cluster barriers per step; no global memory
-// traffic besides the samples.
+// every CTA's next-V buffer together with their means a_A, a_B.  Two cluster
+// barriers per step; no global memory traffic besides the samples.
 #include <cooperative_groups.h>
 
 #include "otm_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace otm {
 namespace {
 
+using tc::cp_async16;
+using tc::cp_async_commit;
+using tc::cp_async_wait;
+
 constexpr int TC = 32;        // samples per chunk
 constexpr int THREADS = 256;  // 8 warps
 constexpr int KMAX = 128;
+constexpr int RB = 4 * THREADS;  // staged row indices per CTA and step
 
 struct SgdArgs {
   const float* YA;
@@ -50,68 +57,112 @@ struct SgdArgs {
 
 struct Layout {
   int kp, ldk, cpq, nview;
-  size_t off_v0, off_v1, off_u, off_p6, off_small, total_floats;
+  int64_t bq;  // samples of a minibatch per CTA
+  int nrows;   // of which the row indices are staged in shared memory
+  int nbuf;    // sample-chunk buffers: 2 (load the next chunk during this one) or 1
+  size_t off_v0, off_v1, off_u, off_p6, off_small, off_rows, total_floats;
 };
 
-__host__ __device__ inline Layout make_layout(int k, int CL, bool sym) {
+// Shared memory (floats): V twice (current / next), the sample chunks (nbuf
+// buffers of nview x TC samples; two where they fit) and B, the owner buffers, the means (a_A, a_B
+// double-buffered by step parity), and the row indices of this CTA's slice of
+// the current and the next minibatch (the first RB of them; a longer slice reads
+// the rest of its indices from the permutation as it goes).
+__host__ __device__ inline Layout make_layout(int k, int CL, bool sym, int64_t b, int nbuf) {
   Layout L;
   L.kp = (k + 3) & ~3;
   L.ldk = L.kp;
   L.cpq = (k + CL - 1) / CL;
   L.nview = sym ? 1 : 3;
+  L.bq = (b + CL - 1) / CL;
+  L.nrows = (int)(L.bq < RB ? L.bq : RB);
   const size_t vsz = (size_t)L.kp * L.ldk;
-  size_t u1 = (size_t)(L.nview + 1) * TC * L.ldk;
+  L.nbuf = nbuf;
+  size_t u1 = (size_t)(nbuf * L.nview + 1) * TC * L.ldk;
   const size_t u = u1 > vsz ? u1 : vsz;
   L.off_v0 = 0;
   L.off_v1 = vsz;
   L.off_u = 2 * vsz;
   L.off_p6 = L.off_u + u;
   L.off_small = L.off_p6 + (size_t)3 * L.cpq * L.ldk;
-  L.total_floats = L.off_small + 6 * (size_t)L.ldk + (size_t)L.cpq + 8;
+  L.off_rows = L.off_small + 8 * (size_t)L.ldk + (size_t)L.cpq + 8;
+  L.total_floats = L.off_rows + 2 * (size_t)L.nrows + 4;
   return L;
 }
 
 template <bool SYM, int MT, int CL>
-__global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a, int nbuf) {
   extern __shared__ __align__(16) float sm[];
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k;
-  const Layout L = make_layout(k, CL, SYM);
+  const Layout L = make_layout(k, CL, SYM, a.b, nbuf);
   const int ldk = L.ldk, kp = L.kp, cpq = L.cpq;
   float* V0 = sm + L.off_v0;
   float* V1 = sm + L.off_v1;
   float* U = sm + L.off_u;
-  float* Ya = U;
-  float* Yb = SYM ? U : U + TC * ldk;
-  float* Yc = SYM ? U : U + 2 * TC * ldk;
-  float* Bt = U + L.nview * TC * ldk;
+  float* Bt = U + nbuf * L.nview * TC * ldk;
   float* Gp = U;  // k x ldk partial Y_C^T B^T (after the chunk loop)
   float* gd = sm + L.off_p6;              // cpq x ldk
   float* Hm = gd + cpq * ldk;             // cpq x ldk
   float* vn = Hm + cpq * ldk;             // cpq x ldk
-  float* aA = sm + L.off_small;
-  float* aB = aA + ldk;
-  float* ybA = aB + ldk;
+  float* aAb = sm + L.off_small;          // [2][ldk] by step parity
+  float* aBb = aAb + 2 * ldk;             // [2][ldk]
+  float* ybA = aBb + 2 * ldk;
   float* ybB = ybA + ldk;
   float* ybC = ybB + ldk;
   float* spart = ybC + ldk;
   float* sown = spart + ldk;
+  int* srow = reinterpret_cast<int*>(sm + L.off_rows);  // [2][nrows] by step parity
 
   // ---- initial state: V (zero padded) and the means ----
   for (int idx = tid; idx < kp * ldk; idx += THREADS) {
     const int i = idx / ldk, r = idx % ldk;
     V0[idx] = (i < k && r < k) ? a.V[(int64_t)i * k + r] : 0.f;
+    V1[idx] = 0.f;  // padding rows stay zero; owners fill the rest
   }
+  for (int r = tid; r < 4 * ldk; r += THREADS) aAb[r] = 0.f;  // a_A, a_B, both parities
   for (int r = tid; r < ldk; r += THREADS) {
     ybA[r] = r < k ? (float)a.ybar3[r] : 0.f;
     ybB[r] = r < k ? (float)a.ybar3[k + r] : 0.f;
     ybC[r] = r < k ? (float)a.ybar3[2 * k + r] : 0.f;
   }
   const int own_lo = q * cpq, own_hi = min(k, own_lo + cpq);
-  const int64_t bq = (a.b + CL - 1) / CL;
+  const int64_t bq = L.bq;
+  // row index of sample p of this CTA's slice of step s (-1 outside the minibatch)
+  auto row_of = [&](int64_t s, int64_t p) -> int {
+    const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
+    const int64_t lo = (int64_t)q * bq + p;
+    if (lo >= min(a.b, a.n - pos0) || p >= bq) return -1;
+    return a.perm ? a.perm[e * a.n + pos0 + lo] : (int)(pos0 + lo);
+  };
+  const int nrows = L.nrows;
+  for (int p = tid; p < nrows; p += THREADS) srow[p] = a.total_steps > 0 ? row_of(0, p) : -1;
+  cluster.sync();  // zeroed buffers before any remote write
+  // a_A, a_B of the initial V (later steps receive them from the owners)
+  for (int i = warp; i < kp; i += THREADS / 32) {
+    float x = 0.f, y = 0.f;
+    for (int r = lane; r < ldk; r += 32) {
+      const float v = V0[i * ldk + r];
+      x = fmaf(v, ybA[r], x);
+      y = fmaf(v, ybB[r], y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) {
+      aAb[i] = x;
+      aBb[i] = y;
+    }
+  }
   __syncthreads();
+  // rows 16-byte aligned: chunks arrive by cp.async while the previous one is used
+  const bool vec_rows = (k & 3) == 0 && ((reinterpret_cast<uintptr_t>(a.YA) |
+                                          reinterpret_cast<uintptr_t>(a.YB) |
+                                          reinterpret_cast<uintptr_t>(a.YC)) & 15) == 0;
 
   // GEMM1 thread mapping: warp w covers components 16w..16w+15 as i = 16w + il + 4j,
   // lane covers samples t = tl + 8j'.
@@ -121,31 +172,22 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
   for (int64_t s = 0; s < a.total_steps; ++s) {
     float* Vc = (s & 1) ? V1 : V0;
     float* Vn = (s & 1) ? V0 : V1;
-    const int64_t e = s / a.spe, jb = s % a.spe;
-    const int64_t pos0 = jb * a.b;
+    const int64_t pos0 = (s % a.spe) * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
     const float beta = (float)a.beta0 / sqrtf((float)(s + 1));
     const float inv_b = 1.f / (float)beff;
-
-    // phase 1: a_A = V^T ybar_A, a_B = V^T ybar_B, s partial = 0
-    for (int i = warp; i < kp; i += THREADS / 32) {
-      float x = 0.f, y = 0.f;
-      for (int r = lane; r < ldk; r += 32) {
-        const float v = Vc[i * ldk + r];
-        x = fmaf(v, ybA[r], x);
-        y = fmaf(v, ybB[r], y);
-      }
+    const int par = (int)(s & 1);
+    const float* aA = aAb + par * ldk;  // means of this step's V, from the owners
+    const float* aB = aBb + par * ldk;
+    const int* rows = srow + par * nrows;
+    // the next step's row indices: loaded now, stored at the end of the step
+    int pre[4];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_xor_sync(0xffffffffu, x, o);
-        y += __shfl_xor_sync(0xffffffffu, y, o);
-      }
-      if (lane == 0) {
-        aA[i] = x;
-        aB[i] = y;
-        spart[i] = 0.f;
-      }
+    for (int j = 0; j < 4; ++j) {
+      const int p = tid + THREADS * j;
+      pre[j] = (s + 1 < a.total_steps && p < nrows) ? row_of(s + 1, p) : -1;
     }
+    for (int i = tid; i < kp; i += THREADS) spart[i] = 0.f;
     float gacc[MT][4][4];
 #pragma unroll
     for (int m = 0; m < MT; ++m)
@@ -153,44 +195,59 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) gacc[m][x][y] = 0.f;
-    __syncthreads();
 
-    const int64_t my_lo = (int64_t)q * bq, my_hi = min(beff, my_lo + bq);
-    for (int64_t c0 = my_lo; c0 < my_hi; c0 += TC) {
-      // load the chunk (rows beyond the slice are zero)
+    const int64_t my_lo = (int64_t)q * bq;
+    const int64_t nmy = max((int64_t)0, min(beff, my_lo + bq) - my_lo);
+    const int nchunk = (int)((nmy + TC - 1) / TC);
+    // chunk c of the slice into buffer `buf` (rows beyond the slice are zero; an
+    // index outside [0, n), i.e. an invalid permutation, reads as a zero sample)
+    auto load_chunk = [&](int c, int buf) {
+      float* Yd = U + (size_t)buf * L.nview * TC * ldk;
+      const int c0 = c * TC;
       const int nv4 = ldk / 4;
-      for (int idx = tid; idx < TC * nv4; idx += THREADS) {
-        const int tt = idx / nv4, r4 = idx % nv4;
-        const int64_t p = c0 + tt;
-        float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va, vc = va;
-        const int64_t row =
-            p < my_hi ? (a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p) : -1;
-        // an index outside [0, n) (invalid permutation) reads as a zero sample
-        if (row >= 0 && row < a.n) {
-          const int r = 4 * r4;
-          const float* pa = a.YA + row * k;
-          float t4[4];
-#pragma unroll
-          for (int z = 0; z < 4; ++z) t4[z] = (r + z < k) ? pa[r + z] : 0.f;
-          va = make_float4(t4[0], t4[1], t4[2], t4[3]);
-          if (!SYM) {
-            const float* pb = a.YB + row * k;
-            const float* pc = a.YC + row * k;
-#pragma unroll
-            for (int z = 0; z < 4; ++z) t4[z] = (r + z < k) ? pb[r + z] : 0.f;
-            vb = make_float4(t4[0], t4[1], t4[2], t4[3]);
-#pragma unroll
-            for (int z = 0; z < 4; ++z) t4[z] = (r + z < k) ? pc[r + z] : 0.f;
-            vc = make_float4(t4[0], t4[1], t4[2], t4[3]);
+      if (vec_rows) {
+        for (int idx = tid; idx < TC * nv4; idx += THREADS) {
+          const int tt = idx / nv4, r4 = idx % nv4;
+          const int p = c0 + tt;
+          const int row = p < nmy ? (p < nrows ? rows[p] : row_of(s, p)) : -1;
+          const bool ok = row >= 0 && row < a.n;
+          for (int v = 0; v < L.nview; ++v) {
+            const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+            cp_async16(Yd + ((size_t)v * TC + tt) * ldk + 4 * r4,
+                       ok ? Yg + (int64_t)row * k + 4 * r4 : Yg, ok ? 16u : 0u);
           }
         }
-        reinterpret_cast<float4*>(Ya + tt * ldk)[r4] = va;
-        if (!SYM) {
-          reinterpret_cast<float4*>(Yb + tt * ldk)[r4] = vb;
-          reinterpret_cast<float4*>(Yc + tt * ldk)[r4] = vc;
+        cp_async_commit();
+      } else {
+        for (int idx = tid; idx < TC * nv4; idx += THREADS) {
+          const int tt = idx / nv4, r4 = idx % nv4;
+          const int p = c0 + tt;
+          const int row = p < nmy ? (p < nrows ? rows[p] : row_of(s, p)) : -1;
+          for (int v = 0; v < L.nview; ++v) {
+            const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+            float t4[4] = {0.f, 0.f, 0.f, 0.f};
+            if (row >= 0 && row < a.n) {
+              const int r = 4 * r4;
+#pragma unroll
+              for (int z = 0; z < 4; ++z) t4[z] = (r + z < k) ? Yg[(int64_t)row * k + r + z] : 0.f;
+            }
+            reinterpret_cast<float4*>(Yd + ((size_t)v * TC + tt) * ldk)[r4] =
+                make_float4(t4[0], t4[1], t4[2], t4[3]);
+          }
         }
       }
+    };
+    if (nbuf == 2 && nchunk > 0) load_chunk(0, 0);
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const int buf = nbuf == 2 ? (ch & 1) : 0;
+      const bool ahead = nbuf == 2 && ch + 1 < nchunk;
+      if (ahead) load_chunk(ch + 1, buf ^ 1);
+      if (nbuf == 1) load_chunk(ch, 0);
+      if (vec_rows) cp_async_wait(ahead ? 1 : 0);
       __syncthreads();
+      const float* Ya = U + (size_t)buf * L.nview * TC * ldk;
+      const float* Yb = SYM ? Ya : Ya + TC * ldk;
+      const float* Yc = SYM ? Ya : Ya + 2 * TC * ldk;
 
       // GEMM1: A_A, A_B for 4 components x 4 samples per thread, then B
       if (16 * warp < kp) {
@@ -352,7 +409,32 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
 #pragma unroll
       for (int c = 0; c < CL; ++c) cluster.map_shared_rank(Vn, c)[(own_lo + jj) * ldk + r] = v;
     }
-    cluster.sync();  // next V complete everywhere; partials may be overwritten
+    // means of the new owned columns for the next step, to every CTA
+    for (int jj = warp; jj < nown; jj += THREADS / 32) {
+      float x = 0.f, y = 0.f;
+      for (int r = lane; r < kp; r += 32) {
+        x = fmaf(vn[jj * ldk + r], ybA[r], x);
+        y = fmaf(vn[jj * ldk + r], ybB[r], y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane < CL) {
+        cluster.map_shared_rank(aAb, lane)[(par ^ 1) * ldk + own_lo + jj] = x;
+        cluster.map_shared_rank(aBb, lane)[(par ^ 1) * ldk + own_lo + jj] = y;
+      }
+    }
+    {
+      int* rows_next = srow + (par ^ 1) * nrows;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int p = tid + THREADS * j;
+        if (p < nrows) rows_next[p] = pre[j];
+      }
+    }
+    cluster.sync();  // next V and means complete everywhere; partials may be overwritten
 
     if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0) {
       float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
@@ -370,8 +452,8 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a) {
 }
 
 template <bool SYM, int MT, int CL>
-otm_status launch_cl(const SgdArgs& args, cudaStream_t st) {
-  const Layout L = make_layout(args.k, CL, SYM);
+otm_status launch_cl(const SgdArgs& args, int nbuf, cudaStream_t st) {
+  const Layout L = make_layout(args.k, CL, SYM, args.b, nbuf);
   const size_t smem = L.total_floats * sizeof(float);
   auto kern = sgd_cluster_kernel<SYM, MT, CL>;
   OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -389,36 +471,38 @@ otm_status launch_cl(const SgdArgs& args, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args, nbuf));
   count_launch();
   return OTM_OK;
 }
 
 template <bool SYM, int MT>
-otm_status launch_mt(const SgdArgs& args, int CL, cudaStream_t st) {
+otm_status launch_mt(const SgdArgs& args, int CL, int nbuf, cudaStream_t st) {
   switch (CL) {
-    case 16: return launch_cl<SYM, MT, 16>(args, st);
-    case 8: return launch_cl<SYM, MT, 8>(args, st);
-    case 4: return launch_cl<SYM, MT, 4>(args, st);
-    case 2: return launch_cl<SYM, MT, 2>(args, st);
-    default: return launch_cl<SYM, MT, 1>(args, st);
+    case 16: return launch_cl<SYM, MT, 16>(args, nbuf, st);
+    case 8: return launch_cl<SYM, MT, 8>(args, nbuf, st);
+    case 4: return launch_cl<SYM, MT, 4>(args, nbuf, st);
+    case 2: return launch_cl<SYM, MT, 2>(args, nbuf, st);
+    default: return launch_cl<SYM, MT, 1>(args, nbuf, st);
   }
 }
 
 template <bool SYM>
-otm_status launch_sym(const SgdArgs& args, int CL, cudaStream_t st) {
+otm_status launch_sym(const SgdArgs& args, int CL, int nbuf, cudaStream_t st) {
   const int nt = ((args.k + 3) & ~3) / 4;
   const int MT = (nt * nt + THREADS - 1) / THREADS;
   switch (MT) {
-    case 1: return launch_mt<SYM, 1>(args, CL, st);
-    case 2: return launch_mt<SYM, 2>(args, CL, st);
-    case 3: return launch_mt<SYM, 3>(args, CL, st);
-    default: return launch_mt<SYM, 4>(args, CL, st);
+    case 1: return launch_mt<SYM, 1>(args, CL, nbuf, st);
+    case 2: return launch_mt<SYM, 2>(args, CL, nbuf, st);
+    case 3: return launch_mt<SYM, 3>(args, CL, nbuf, st);
+    default: return launch_mt<SYM, 4>(args, CL, nbuf, st);
   }
 }
 
-// Largest supported cluster size whose shared-memory footprint fits (16, then 8).
-int pick_cluster(int k, bool sym) {
+// Largest supported cluster size whose shared-memory footprint fits (16, then
+// 8, ...), with two sample-chunk buffers where they fit and one otherwise;
+// *nbuf receives the buffer count.
+int pick_cluster(int k, bool sym, int64_t b, int max_cl, int* nbuf) {
   static int max_smem = 0;
   if (max_smem == 0) {
     int dev = 0;
@@ -426,10 +510,15 @@ int pick_cluster(int k, bool sym) {
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (max_smem <= 0) max_smem = 227 * 1024;
   }
-  for (int CL : {16, 8, 4, 2, 1}) {
-    const Layout L = make_layout(k, CL, sym);
-    if (L.total_floats * sizeof(float) <= (size_t)max_smem) return CL;
-  }
+  for (int CL : {16, 8, 4, 2, 1})
+    for (int nb : {2, 1}) {
+      if (CL > max_cl) continue;
+      const Layout L = make_layout(k, CL, sym, b, nb);
+      if (L.total_floats * sizeof(float) <= (size_t)max_smem) {
+        *nbuf = nb;
+        return CL;
+      }
+    }
   return 0;
 }
 
@@ -458,7 +547,8 @@ otm_status run(float* V, const float* YA, const float* YB, const float* YC, int6
   args.c2 = (float)(a0 * (a0 + 1.0) / 2.0);
   args.c3 = (float)(a0 * a0);
   args.kappa = (float)(0.5 * (1.0 + theta));
-  int CL = pick_cluster((int)k, sym);
+  int nbuf = 1;
+  int CL = pick_cluster((int)k, sym, b, 16, &nbuf);
   if (CL == 0) return set_error(OTM_EINVAL, "sgd: k=%lld does not fit shared memory", (long long)k);
   // honour the device's limit on active clusters of this size
   static int cl16_ok = -1;
@@ -466,7 +556,7 @@ otm_status run(float* V, const float* YA, const float* YB, const float* YC, int6
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
     cfg.blockDim = dim3(THREADS, 1, 1);
-    cfg.dynamicSmemBytes = make_layout((int)k, 16, sym).total_floats * sizeof(float);
+    cfg.dynamicSmemBytes = make_layout((int)k, 16, sym, b, nbuf).total_floats * sizeof(float);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;
@@ -483,8 +573,9 @@ otm_status run(float* V, const float* YA, const float* YB, const float* YC, int6
     cl16_ok = (e == cudaSuccess && nclusters > 0) ? 1 : 0;
     cudaGetLastError();
   }
-  if (CL == 16 && cl16_ok == 0) CL = 8;
-  return sym ? launch_sym<true>(args, CL, st) : launch_sym<false>(args, CL, st);
+  if (CL == 16 && cl16_ok == 0) CL = pick_cluster((int)k, sym, b, 8, &nbuf);
+  if (CL == 0) return set_error(OTM_EINVAL, "sgd: k=%lld does not fit shared memory", (long long)k);
+  return sym ? launch_sym<true>(args, CL, nbuf, st) : launch_sym<false>(args, CL, nbuf, st);
 }
 
 }  // namespace

@@ -232,6 +232,30 @@ def test_sgd_run_identity_order_and_three_views(otm):
     assert rel(to_np(Vd).T, Vo) < 1e-5
 
 
+@pytest.mark.parametrize("k,offset", [(100, 0), (128, 0), (37, 0), (64, 1)])
+def test_sgd_run_large_batches_three_views(otm, k, offset):
+    """Minibatches of 20000 samples (a CTA's slice is longer than its staged row
+    indices), a partial last batch, three views; k = 128 runs with one sample
+    buffer, k = 37 and views that are not 16-byte aligned take scalar loads."""
+    n, b, epochs = 45000, 20000, 1
+    g = np.random.default_rng(k + offset)
+    Ys = [(g.standard_normal((n, k)) * 0.05 + 0.1 * g.standard_normal(k)).astype(np.float32)
+          for _ in range(3)]
+    yb = np.stack([Y.astype(np.float64).mean(axis=0) for Y in Ys])
+    perm = synth.epoch_permutations(k + 3, n, epochs)
+    V0 = synth.haar_orthonormal(k + 4, k)
+    Vd = _dev(V0.T.copy())
+    views = []
+    for Y in Ys:
+        buf = torch.zeros(n * k + offset, device="cuda", dtype=torch.float32)
+        buf[offset:] = _dev(Y).reshape(-1)
+        views.append(buf[offset:].view(n, k))
+    otm.sgd_run(Vd, *views, _dev(yb), _dev(perm), epochs, b, 5e-2, 1.0, 1.0)
+    torch.cuda.synchronize()
+    Vo, _ = ostgd.sgd_run(V0, *Ys, tuple(yb), perm, b, 5e-2, 1.0, 1.0)
+    assert rel(to_np(Vd).T, Vo) < 1e-5
+
+
 # ----------------------------------------------------------------------------
 # post-processing and the error measure
 # ----------------------------------------------------------------------------
