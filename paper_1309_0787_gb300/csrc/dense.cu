@@ -268,13 +268,19 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 
 // ---------------------------------------------------------------------------
 // Cholesky of G (+ shift) and the inverse of its upper factor R = L^T.
-// One CTA of 256 threads, FP32 in shared memory (n <= 160), blocked by 8
-// columns: one warp factors each 8 x 8 diagonal block in registers (shuffles,
-// no barrier), every row of the panel below solves against it by forward
-// substitution, and the trailing matrix takes a rank-8 update -- three
-// barriers per block column instead of two per column.  L^{-1} is then formed
-// by blocked forward substitution (two barriers per block row).  Output Rinv (n x n, float32,
-// row-major, upper triangular) so that Q = A Rinv.
+// One CTA of 1024 threads, FP32 in shared memory (n <= 160), right-looking
+// and blocked by 8 columns, with L^{-1} built in the same sweep.  Block J:
+//  (a) one warp factors the 8 x 8 diagonal block L_JJ in registers and
+//      inverts it (lane c solves for column c of L_JJ^{-1});
+//  (b) the block row J of X = L^{-1} is finished: X_J = L_JJ^{-1} B_J, where
+//      B starts as the identity and has taken the updates of earlier blocks;
+//  (c) the panel below, L_{>J,J} = A_{>J,J} L_JJ^{-T} (row by row, in parallel
+//      with (b));
+//  (d) every row i below takes one rank-8 update over its columns 0..i: the
+//      trailing Cholesky matrix (columns past the block) and B (columns up to
+//      the block), B_{i,:} -= L_{i,J} X_J.
+// Three barriers per block column.  Output Rinv (n x n, float32, row-major,
+// upper triangular) so that Q = A Rinv.
 // shift_scale > 0 adds shift_scale * n * u * trace(G) to the diagonal
 // (u = 2^-24), which keeps the factorisation positive definite for Gram
 // matrices of ill-conditioned A (shifted Cholesky-QR: Fukaya, Kannan,
@@ -283,8 +289,13 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 // that floor: the matching columns of Q become normalised rounding noise,
 // which the following passes orthonormalise -- still a valid orthonormal
 // basis of a space containing range(A).  Only a non-finite pivot is an error.
+// G is read from its lower triangle (it is the symmetric product A^T A).
 // ---------------------------------------------------------------------------
-constexpr int CH_T = 256, CH_B = 8;
+constexpr int CH_T = 1024, CH_B = 8;
+
+__host__ __device__ inline size_t chol_smem_floats(int n) {
+  return (size_t)2 * n * (n | 1) + (size_t)(CH_B + 1) * n + 2 * CH_B * CH_B;
+}
 
 __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict__ G, int n,
                                                         double shift_scale,
@@ -292,37 +303,40 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
                                                         int* __restrict__ flag, int* skip,
                                                         float check_tol) {
   extern __shared__ float sm[];
+  __shared__ float s_red[CH_T / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = CH_T / 32;
   // conditional pass: nothing to do once the columns are orthonormal to check_tol
   if (skip && *skip) return;
   if (check_tol > 0.f) {
-    __shared__ float s_dev[CH_T / 32];
     float dev = 0.f;
-    for (int idx = threadIdx.x; idx < n * n; idx += CH_T) {
+    for (int idx = tid; idx < n * n; idx += CH_T) {
       const int i = idx / n, j = idx % n;
       dev = fmaxf(dev, fabsf((float)G[idx] - (i == j ? 1.f : 0.f)));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
-    if ((threadIdx.x & 31) == 0) s_dev[threadIdx.x >> 5] = dev;
+    if (lane == 0) s_red[warp] = dev;
     __syncthreads();
     float mx = 0.f;
 #pragma unroll
-    for (int w = 0; w < CH_T / 32; ++w) mx = fmaxf(mx, s_dev[w]);
+    for (int w = 0; w < NW; ++w) mx = fmaxf(mx, s_red[w]);
     if (mx <= check_tol) {
-      if (threadIdx.x == 0) *skip = 1;
+      if (tid == 0) *skip = 1;
       return;
     }
+    __syncthreads();  // s_red is reused below
   }
-  const int ldn = n | 1;       // odd row stride: column walks are bank-conflict free
+  const int ldn = n | 1;         // odd row stride: column walks are bank-conflict free
   const int nblk = (n + CH_B - 1) / CH_B;
-  float* L = sm;                 // n x ldn (lower triangle)
-  float* X = L + n * ldn;        // n x ldn, X = L^{-1} (lower triangle)
+  float* L = sm;                 // n x ldn: G, then L (lower triangle)
+  float* X = L + n * ldn;        // n x ldn: B, then X = L^{-1} (lower triangle)
   float* rdg = X + n * ldn;      // n reciprocal pivots 1 / L_jj
-  float* tmp = rdg + n;          // 8 x n scratch
+  float* PT = rdg + n;           // 8 x n: the current panel, transposed
+  float* Ljj = PT + CH_B * n;    // 8 x 8 diagonal block
+  float* Dinv = Ljj + CH_B * CH_B;  // 8 x 8 its inverse
   __shared__ float s_shift, s_floor;
   __shared__ int s_bad;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = CH_T / 32;
   if (warp == 0) {
     double tr = 0.0;
     for (int i = lane; i < n; i += 32) tr += G[(int64_t)i * n + i];
@@ -335,17 +349,21 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
     }
   }
   __syncthreads();
-  for (int i = warp; i < n; i += NW)
-    for (int j = lane; j <= i; j += 32) {
-      float v = (float)(0.5 * (G[(int64_t)i * n + j] + G[(int64_t)j * n + i]));
+#pragma unroll 4
+  for (int idx = tid; idx < n * n; idx += CH_T) {
+    const int i = idx / n, j = idx % n;
+    if (j <= i) {
+      float v = (float)G[idx];
       if (i == j) v += s_shift;
       L[i * ldn + j] = v;
     }
+    X[i * ldn + j] = i == j ? 1.f : 0.f;
+  }
   __syncthreads();
 
   for (int J = 0; J < nblk; ++J) {
-    const int j0 = J * CH_B, jb = min(CH_B, n - j0);
-    // (1) factor the diagonal block in warp 0: lane r holds row j0 + r
+    const int j0 = J * CH_B, jb = min(CH_B, n - j0), je = j0 + jb;
+    // (a) factor and invert the diagonal block in warp 0: lane r holds row j0 + r
     if (warp == 0) {
       float a[CH_B];
 #pragma unroll
@@ -372,72 +390,83 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
           }
         }
       }
-      if (lane < jb) {
+      if (lane < CH_B) {
 #pragma unroll
-        for (int c = 0; c < CH_B; ++c)
-          if (c <= lane) L[(j0 + lane) * ldn + j0 + c] = a[c];
+        for (int c = 0; c < CH_B; ++c) {
+          const float v = (lane < jb && c <= lane) ? a[c] : 0.f;
+          Ljj[lane * CH_B + c] = v;
+          if (lane < jb && c <= lane) L[(j0 + lane) * ldn + j0 + c] = v;
+        }
+      }
+      __syncwarp();
+      // column c of L_JJ^{-1} by forward substitution
+      if (lane < CH_B) {
+        const int c = lane;
+        float y[CH_B];
+#pragma unroll
+        for (int r = 0; r < CH_B; ++r) {
+          float v = r == c ? 1.f : 0.f;
+#pragma unroll
+          for (int m = 0; m < r; ++m) v = fmaf(-Ljj[r * CH_B + m], y[m], v);
+          y[r] = (r < jb && r >= c) ? v * rdg[j0 + (r < jb ? r : 0)] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < CH_B; ++r) Dinv[r * CH_B + c] = y[r];
       }
     }
     __syncthreads();
-    // (2) panel: row i below the block solves l L_JJ^T = a by forward substitution
-    for (int i = j0 + jb + tid; i < n; i += CH_T) {
-      float l[CH_B];
+    // (b) block row J of X: threads [0, je) take one column each
+    if (tid < je) {
+      const int c = tid;
+      float bcol[CH_B];
 #pragma unroll
-      for (int c = 0; c < CH_B; ++c) {
-        if (c < jb) {
-          float v = L[i * ldn + j0 + c];
+      for (int m = 0; m < CH_B; ++m) bcol[m] = m < jb ? X[(j0 + m) * ldn + c] : 0.f;
 #pragma unroll
-          for (int m2 = 0; m2 < c; ++m2) v = fmaf(-l[m2], L[(j0 + c) * ldn + j0 + m2], v);
-          l[c] = v * rdg[j0 + c];
-          L[i * ldn + j0 + c] = l[c];
+      for (int r = 0; r < CH_B; ++r) {
+        if (r < jb) {
+          float v = 0.f;
+#pragma unroll
+          for (int m = 0; m <= r; ++m) v = fmaf(Dinv[r * CH_B + m], bcol[m], v);
+          X[(j0 + r) * ldn + c] = v;
+        }
+      }
+    }
+    // (c) panel rows i >= je: threads [CH_T/2, ...) take one row each
+    {
+      const int i = je + (tid - CH_T / 2);
+      if (tid >= CH_T / 2 && i < n) {
+        float arow[CH_B];
+#pragma unroll
+        for (int m = 0; m < CH_B; ++m) arow[m] = m < jb ? L[i * ldn + j0 + m] : 0.f;
+#pragma unroll
+        for (int c = 0; c < CH_B; ++c) {
+          float v = 0.f;
+#pragma unroll
+          for (int m = 0; m <= c; ++m) v = fmaf(arow[m], Dinv[c * CH_B + m], v);
+          if (c < jb) L[i * ldn + j0 + c] = v;
+          PT[c * n + i] = c < jb ? v : 0.f;
         }
       }
     }
     __syncthreads();
-    // (3) trailing rank-jb update of the lower triangle
-    for (int i = j0 + jb + warp; i < n; i += NW) {
+    // (d) rank-8 update of rows i >= je over columns 0..i: B for columns < je,
+    // the trailing Cholesky matrix for columns je..i
+    for (int i = je + warp; i < n; i += NW) {
       float li[CH_B];
 #pragma unroll
-      for (int c = 0; c < CH_B; ++c) li[c] = c < jb ? L[i * ldn + j0 + c] : 0.f;
-      for (int l2 = j0 + jb + lane; l2 <= i; l2 += 32) {
-        float acc = L[i * ldn + l2];
+      for (int m = 0; m < CH_B; ++m) li[m] = PT[m * n + i];
+      for (int c = lane; c <= i; c += 32) {
+        if (c < je) {
+          float acc = X[i * ldn + c];
 #pragma unroll
-        for (int c = 0; c < CH_B; ++c)
-          if (c < jb) acc = fmaf(-li[c], L[l2 * ldn + j0 + c], acc);
-        L[i * ldn + l2] = acc;
-      }
-    }
-    __syncthreads();
-  }
-
-  // X = L^{-1} by block rows: tmp = L_{I,<I} X_{<I}, then forward substitution
-  // with L_II for every column (unit right-hand sides inside the block)
-  for (int I = 0; I < nblk; ++I) {
-    const int i0 = I * CH_B, ib = min(CH_B, n - i0);
-    for (int idx = tid; idx < ib * i0; idx += CH_T) {
-      const int r = idx / i0, c = idx % i0;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int m2 = c;
-      for (; m2 + 3 < i0; m2 += 4) {
-        s0 = fmaf(L[(i0 + r) * ldn + m2], X[m2 * ldn + c], s0);
-        s1 = fmaf(L[(i0 + r) * ldn + m2 + 1], X[(m2 + 1) * ldn + c], s1);
-        s2 = fmaf(L[(i0 + r) * ldn + m2 + 2], X[(m2 + 2) * ldn + c], s2);
-        s3 = fmaf(L[(i0 + r) * ldn + m2 + 3], X[(m2 + 3) * ldn + c], s3);
-      }
-      for (; m2 < i0; ++m2) s0 = fmaf(L[(i0 + r) * ldn + m2], X[m2 * ldn + c], s0);
-      tmp[r * n + c] = (s0 + s1) + (s2 + s3);
-    }
-    __syncthreads();
-    for (int c = tid; c < i0 + ib; c += CH_T) {
-      float x[CH_B];
+          for (int m = 0; m < CH_B; ++m)
+            if (m < jb) acc = fmaf(-li[m], X[(j0 + m) * ldn + c], acc);
+          X[i * ldn + c] = acc;
+        } else {
+          float acc = L[i * ldn + c];
 #pragma unroll
-      for (int r = 0; r < CH_B; ++r) {
-        if (r < ib) {
-          float v = c < i0 ? -tmp[r * n + c] : (c - i0 == r ? 1.f : 0.f);
-#pragma unroll
-          for (int r2 = 0; r2 < r; ++r2) v = fmaf(-L[(i0 + r) * ldn + i0 + r2], x[r2], v);
-          x[r] = v * rdg[i0 + r];
-          X[(i0 + r) * ldn + c] = x[r];
+          for (int m = 0; m < CH_B; ++m) acc = fmaf(-li[m], PT[m * n + c], acc);
+          L[i * ldn + c] = acc;
         }
       }
     }
@@ -1079,7 +1108,7 @@ otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cuda
   float* Rinv = ws.take<float>(m * m);
   int* skip = ws.take<int>(1);
   if (!G || !Rinv || !skip) return set_error(OTM_EINVAL, "orthonormalize: workspace too small");
-  const size_t smem = sizeof(float) * (2 * m * (m | 1) + m + CH_B * m);
+  const size_t smem = sizeof(float) * chol_smem_floats((int)m);
   OTM_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
   OTM_CHECK_CUDA(cudaMemsetAsync(skip, 0, sizeof(int), st));
