@@ -130,12 +130,15 @@ otm_status otm_orthonormalize(float* A, int64_t rows, int64_t m, void* ws, size_
  * "short-thin SVD" of Section 4.2, Table 3): A (n x n, FP64, row-major, n <= 160,
  * symmetrised as (A + A^T)/2) -> evals[n] descending, evecs (n x n, row-major,
  * column j = eigenvector j, sign fixed so its largest-magnitude entry is
- * positive).  Cyclic Jacobi in FP32 followed by FP64 iterative refinement:
- * eigenvalues separated from their neighbours by more than ~1e-5 ||A|| are
- * FP64-accurate (~1e-13 ||A||); closer groups get an FP64-exact invariant
- * subspace and eigenvalues to ~1e-9 ||A||.  Scratch: otm_syev_workspace(n).
- * OTM_ENOTCONVERGED if the Jacobi sweeps hit their limit.  Synchronises the
- * stream.
+ * positive).  A float32 start (Householder tridiagonalisation, multisection
+ * bisection, eigenvectors from twisted factorisations) is refined in FP64
+ * (Ogita-Aishima iteration, one cooperative launch over all SMs) until the
+ * correction is below 1e-10 in every entry, at most 8 times: eigenvalues
+ * separated from their neighbours by more than ~1e-5 ||A|| are FP64-accurate
+ * (~1e-13 ||A||); closer groups get an FP64-exact invariant subspace and
+ * eigenvalues to ~1e-9 ||A||.  Scratch: otm_syev_workspace(n).
+ * OTM_ENOTCONVERGED on a non-finite eigenvalue, or if the refinement's grid
+ * barrier timed out.  Synchronises the stream.
  */
 size_t otm_syev_workspace(int64_t n);
 otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, void* ws,

@@ -114,7 +114,8 @@ otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, vo
   int h = 0;
   OTM_CHECK_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (h) return set_error(OTM_ENOTCONVERGED, "otm_syev: non-finite eigenvalues");
+  if (h)
+    return set_error(OTM_ENOTCONVERGED, "otm_syev: non-finite eigenvalues or refinement failure");
   return OTM_OK;
 }
 

@@ -480,137 +480,13 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Cyclic Jacobi (FP32, one CTA), round-robin parallel ordering: each round
-// applies n/2 disjoint rotations, first to columns (A J, V J) then to rows
-// (J^T A).  Rotation angle from the 2 x 2 symmetric Schur decomposition.
-// Stops when off(A) <= 1e-6 ||A||_F, or when a sweep no longer halves off(A)
-// once it is below 1e-3 ||A||_F (the float32 rounding floor); the FP64
-// refinement that follows supplies the remaining accuracy.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int rr_member(int pos, int round, int np) {
-  // circle method: position 0 fixed, the others rotate by `round`
-  if (pos == 0) return 0;
-  return 1 + (pos - 1 + round) % (np - 1);
-}
-
-__global__ void __launch_bounds__(1024) jacobi_f32_kernel(const double* __restrict__ A0, int n,
-                                                          int max_sweeps, double* __restrict__ V_out,
-                                                          int* __restrict__ flag) {
-  extern __shared__ float sm[];
-  const int ldn = n | 1;
-  const int np = n + (n & 1), half = np / 2;
-  float* A = sm;                 // n x ldn
-  float* V = sm + n * ldn;       // n x ldn, columns = eigenvectors
-  float* cs = V + n * ldn;       // [half] cos, [half] sin
-  int* pq = reinterpret_cast<int*>(cs + 2 * half);  // [half] p, [half] q
-  __shared__ float s_red[2][32];
-  __shared__ int s_done;
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = T >> 5;
-  for (int i = warp; i < n; i += nw)
-    for (int j = lane; j < n; j += 32) {
-      A[i * ldn + j] = (float)(0.5 * (A0[(int64_t)i * n + j] + A0[(int64_t)j * n + i]));
-      V[i * ldn + j] = (i == j) ? 1.f : 0.f;
-    }
-  float off_prev = 3.0e38f;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    __syncthreads();
-    float off = 0.f, tot = 0.f;
-    for (int i = warp; i < n; i += nw)
-      for (int j = lane; j < n; j += 32) {
-        const float v = A[i * ldn + j] * A[i * ldn + j];
-        tot += v;
-        if (i != j) off += v;
-      }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if (lane == 0) {
-      s_red[0][warp] = off;
-      s_red[1][warp] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float o2 = 0.f, t2 = 0.f;
-      for (int w = 0; w < nw; ++w) {
-        o2 += s_red[0][w];
-        t2 += s_red[1][w];
-      }
-      s_done = (o2 <= 1e-12f * t2) || (o2 <= 1e-6f * t2 && o2 > 0.25f * off_prev);
-      s_red[0][0] = o2;
-    }
-    __syncthreads();
-    off_prev = s_red[0][0];
-    if (s_done) break;
-    for (int round = 0; round < np - 1; ++round) {
-      if (tid < half) {
-        int p = rr_member(tid, round, np), q = rr_member(np - 1 - tid, round, np);
-        if (p > q) { const int t = p; p = q; q = t; }
-        float c = 1.f, s = 0.f;
-        if (q < n) {
-          const float apq = A[p * ldn + q];
-          const float app = A[p * ldn + p], aqq = A[q * ldn + q];
-          if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-8f * sqrtf(fabsf(app * aqq))) {
-            const float tau = (aqq - app) / (2.f * apq);
-            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + t * t);
-            s = t * c;
-          }
-        }
-        cs[tid] = c;
-        cs[half + tid] = s;
-        pq[tid] = p;
-        pq[half + tid] = q;
-      }
-      __syncthreads();
-      // columns: A <- A J, V <- V J   (warp per pair, lanes over rows)
-      for (int w = warp; w < half; w += nw) {
-        const int p = pq[w], q = pq[half + w];
-        const float c = cs[w], s = cs[half + w];
-        if (q >= n || s == 0.f) continue;
-        for (int r = lane; r < n; r += 32) {
-          const float ap = A[r * ldn + p], aq = A[r * ldn + q];
-          A[r * ldn + p] = c * ap - s * aq;
-          A[r * ldn + q] = s * ap + c * aq;
-          const float vp = V[r * ldn + p], vq = V[r * ldn + q];
-          V[r * ldn + p] = c * vp - s * vq;
-          V[r * ldn + q] = s * vp + c * vq;
-        }
-      }
-      __syncthreads();
-      // rows: A <- J^T A  (warp per pair, lanes over columns); the rotated
-      // off-diagonal pair is zero by construction of the angle
-      for (int w = warp; w < half; w += nw) {
-        const int p = pq[w], q = pq[half + w];
-        const float c = cs[w], s = cs[half + w];
-        if (q >= n || s == 0.f) continue;
-        for (int col = lane; col < n; col += 32) {
-          const float ap = A[p * ldn + col], aq = A[q * ldn + col];
-          float np_ = c * ap - s * aq, nq_ = s * ap + c * aq;
-          if (col == q) np_ = 0.f;
-          if (col == p) nq_ = 0.f;
-          A[p * ldn + col] = np_;
-          A[q * ldn + col] = nq_;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-  for (int i = warp; i < n; i += nw)
-    for (int j = lane; j < n; j += 32) V_out[(int64_t)i * n + j] = (double)V[i * ldn + j];
-  if (tid == 0 && sweep >= max_sweeps) *flag = 2;
-}
-
-// ---------------------------------------------------------------------------
-// FP32 starting eigenvectors for the FP64 refinement, one CTA of 256 threads
+// FP32 starting eigenvectors for the FP64 refinement, one CTA of 1024 threads
 // (n <= 160), all in shared memory:
 //  1. Householder reduction to tridiagonal form T = H^T A H (classical
-//     two-sided reflections v, tau; three barriers per column);
-//  2. every eigenvalue of T by bisection on Sturm counts (thread per
+//     two-sided reflections v, tau; eight threads per row for p = tau A v, a
+//     warp per row and lanes over columns for the rank-2 update; the next
+//     column's norm is summed during the update, so two barriers per column);
+//  2. every eigenvalue of T by multisection on Sturm counts (G threads per
 //     eigenvalue);
 //  3. eigenvectors of T from twisted factorisations (the forward LDL^T and
 //     backward UDU^T factorisations of T - lambda I, twisted where the
@@ -618,20 +494,25 @@ __global__ void __launch_bounds__(1024) jacobi_f32_kernel(const double* __restri
 //     "Relatively robust representations of symmetric tridiagonals", 2000),
 //     one thread per eigenvector, Gram-Schmidt inside groups of eigenvalues
 //     closer than 1e-4 ||T||;
-//  4. back-transformation X = H Z with one thread per column (no barriers).
+//  4. back-transformation X = H Z by blocks of 8 reflectors in compact WY
+//     form, eight threads per four columns (no barriers between blocks).
 // Output: X (n x n FP64, row-major, column i = eigenvector i, eigenvalues
 // ascending).  fac: 2 n^2 floats of global scratch for the factorisations.
 // ---------------------------------------------------------------------------
 constexpr int TE_T = 1024;
+constexpr int TE_CW = 5;  // columns per lane, rows per warp in the rank-2 update (n <= 160)
 
+static_assert(TE_T == 32 * 32, "block sums read one partial per lane");
+
+// Sum of v over the block (every thread gets it); one barrier.
 __device__ __forceinline__ float block_sum_f(float v, float* red, int tid) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((tid & 31) == 0) red[tid >> 5] = v;
   __syncthreads();
-  float t = 0.f;
+  float t = red[tid & 31];
 #pragma unroll
-  for (int w = 0; w < TE_T / 32; ++w) t += red[w];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   return t;
 }
 
@@ -647,21 +528,30 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   float* tau = e + n;           // n
   float* P = tau + n;           // n  p = tau A v
   float* lam = P + n;           // n  eigenvalues of T (ascending)
+  float* Tw = lam + n;          // 64 per block of 8 reflectors: T_b of the compact WY form
   __shared__ float red[2][TE_T / 32];
   __shared__ float s_alpha, s_tau, s_v0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = TE_T / 32;
-  for (int i = warp; i < n; i += NW)
-    for (int j = lane; j < n; j += 32)
-      Ah[i * ldn + j] = (float)(0.5 * (A0[(int64_t)i * n + j] + A0[(int64_t)j * n + i]));
+  // A0 is symmetric (the caller symmetrises it): coalesced row-major reads
+#pragma unroll 4
+  for (int idx = tid; idx < n * n; idx += TE_T) Ah[(idx / n) * ldn + idx % n] = (float)A0[idx];
   __syncthreads();
 
   // 1. Householder tridiagonalisation
+  __shared__ float s_sig[NW];  // per-warp squares of the next column, from the update
   for (int j = 0; j + 2 < n; ++j) {
     const int r0 = j + 1;  // first row of the column part x = A[r0:, j]
-    float part = 0.f;
-    for (int r = r0 + tid; r < n; r += TE_T) part += Ah[r * ldn + j] * Ah[r * ldn + j];
-    const float sigma = block_sum_f(part, red[0], tid);
+    float sigma;
+    if (j == 0) {
+      float part = 0.f;
+      for (int r = r0 + tid; r < n; r += TE_T) part += Ah[r * ldn + j] * Ah[r * ldn + j];
+      sigma = block_sum_f(part, red[0], tid);
+    } else {
+      sigma = s_sig[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sigma += __shfl_xor_sync(0xffffffffu, sigma, o);
+    }
     const float x0 = Ah[r0 * ldn + j];
     float alpha, tj, v0;
     if (sigma <= 1e-36f) {
@@ -669,29 +559,36 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
       tj = 0.f;
       v0 = 0.f;
     } else {
-      alpha = -copysignf(sqrtf(sigma), x0);
+      // fast square root and reciprocal (a few ulp): this is a float32 start
+      // for the FP64 refinement, and tau stays consistent with v
+      alpha = -copysignf(sigma * rsqrtf(sigma), x0);
       v0 = x0 - alpha;
-      tj = 1.f / (sigma - x0 * alpha);  // 2 / (v^T v), v^T v = 2 (sigma - x0 alpha)
+      tj = __fdividef(1.f, sigma - x0 * alpha);  // 2 / (v^T v), v^T v = 2 (sigma - x0 alpha)
     }
-    // p = tau A_trail v (two threads per trailing row, interleaved columns,
+    // p = tau A_trail v (eight threads per trailing row, interleaved columns,
     // two accumulators each), and p^T v
     float pv = 0.f;
-    for (int base = r0; base < n; base += TE_T >> 1) {  // trip count uniform per block
-      const int i = base + (tid >> 1);
-      const int hh = tid & 1;
+    for (int base = r0; base < n; base += TE_T >> 3) {  // trip count uniform per block
+      const int i = base + (tid >> 3);
+      const int sub = tid & 7;
       float a0 = 0.f, a1 = 0.f;
       if (i < n) {
-        int c = r0 + 1 + hh;
-        for (; c + 2 < n; c += 4) {
-          a0 = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], a0);
-          a1 = fmaf(Ah[i * ldn + c + 2], Ah[(c + 2) * ldn + j], a1);
+        int c = r0 + sub;
+        if (sub == 0) {
+          a0 = Ah[i * ldn + r0] * v0;
+          c += 8;
         }
-        for (; c < n; c += 2) a0 = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], a0);
-        if (hh == 0) a0 = fmaf(Ah[i * ldn + r0], v0, a0);
+        for (; c + 8 < n; c += 16) {
+          a0 = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], a0);
+          a1 = fmaf(Ah[i * ldn + c + 8], Ah[(c + 8) * ldn + j], a1);
+        }
+        if (c < n) a0 = fmaf(Ah[i * ldn + c], Ah[c * ldn + j], a0);
       }
       float acc = a0 + a1;
       acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      if (i < n && hh == 0) {
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      if (i < n && sub == 0) {
         const float pi = tj * acc;
         P[i] = pi;
         pv = fmaf(pi, i == r0 ? v0 : Ah[i * ldn + j], pv);
@@ -699,16 +596,35 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
     }
     const float ptv = block_sum_f(pv, red[1], tid);  // includes a barrier: P complete
     const float K = 0.5f * tj * ptv;
-    // A_trail -= v w^T + w v^T, w = p - K v
-    for (int i = r0 + warp; i < n; i += NW) {
-      const float vi = i == r0 ? v0 : Ah[i * ldn + j];
-      const float wi = P[i] - K * vi;
-      for (int c = r0 + lane; c < n; c += 32) {
-        const float vc = c == r0 ? v0 : Ah[c * ldn + j];
-        const float wc = P[c] - K * vc;
-        Ah[i * ldn + c] -= vi * wc + wi * vc;
+    // A_trail -= v w^T + w v^T, w = p - K v; the squares of the updated column
+    // r0 below its diagonal are the next step's sigma
+    float sq = 0.f;
+    float vcs[TE_CW], wcs[TE_CW];  // v_c, w_c of this lane's columns c = r0 + lane + 32 t
+#pragma unroll
+    for (int t = 0; t < TE_CW; ++t) {
+      const int c = r0 + lane + 32 * t;
+      const float vc = c < n ? (c == r0 ? v0 : Ah[c * ldn + j]) : 0.f;
+      vcs[t] = vc;
+      wcs[t] = c < n ? P[c] - K * vc : 0.f;
+    }
+#pragma unroll
+    for (int t2 = 0; t2 < TE_CW; ++t2) {
+      const int i = r0 + warp + NW * t2;
+      if (i < n) {
+        const float vi = i == r0 ? v0 : Ah[i * ldn + j];
+        const float wi = P[i] - K * vi;
+#pragma unroll
+        for (int t = 0; t < TE_CW; ++t) {
+          const int c = r0 + lane + 32 * t;
+          if (c < n) {
+            const float nv = Ah[i * ldn + c] - (vi * wcs[t] + wi * vcs[t]);
+            Ah[i * ldn + c] = nv;
+            if (t == 0 && lane == 0 && i > r0) sq = fmaf(nv, nv, sq);
+          }
+        }
       }
     }
+    if (lane == 0) s_sig[warp] = sq;  // column r0 is handled by lane 0 only
     if (tid == 0) {
       d[j] = Ah[j * ldn + j];
       e[j] = alpha;
@@ -728,14 +644,24 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   }
   __syncthreads();
 
-  // 2. bisection: thread i finds the i-th smallest eigenvalue
+  // 2. bisection: thread i finds the i-th smallest eigenvalue.  Gershgorin
+  // bounds per warp (lanes over rows, shuffle min / max); e2 = e^2 (in P).
+  float* e2 = P;
+  for (int k = tid; k < n; k += TE_T) e2[k] = e[k] * e[k];
   float tnorm = 0.f, glo = 3.0e38f, ghi = -3.0e38f;
-  for (int k = 0; k < n; ++k) {
+  for (int k = lane; k < n; k += 32) {
     const float off = (k > 0 ? fabsf(e[k - 1]) : 0.f) + (k + 1 < n ? fabsf(e[k]) : 0.f);
     glo = fminf(glo, d[k] - off);
     ghi = fmaxf(ghi, d[k] + off);
     tnorm = fmaxf(tnorm, fabsf(d[k]) + off);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fminf(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmaxf(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+    tnorm = fmaxf(tnorm, __shfl_xor_sync(0xffffffffu, tnorm, o));
+  }
+  __syncthreads();  // e2 complete
   const float pad = 1e-6f * tnorm + 1e-30f;
   glo -= pad;
   ghi += pad;
@@ -745,7 +671,7 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   // 9 for G = 8, 13 rounds of 5 for G = 4: below 2^-28 of the Gershgorin range)
   const int G = n <= TE_T / 8 ? 8 : 4;
   const int rounds = G == 8 ? 9 : 13;
-  {
+  if ((warp * 32) / G < n) {  // warps holding at least one eigenvalue (ballots are warp-wide)
     const int i = tid / G, sub = tid % G;
     const int gbase = (lane / G) * G;  // first lane of this eigenvalue's group
     float lo = glo, hi = ghi;
@@ -757,7 +683,7 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
       if (fabsf(q) < piv_min) q = -piv_min;
       cnt += q < 0.f;
       for (int k = 1; k < n; ++k) {
-        q = d[k] - x - __fdividef(e[k - 1] * e[k - 1], q);
+        q = d[k] - x - __fdividef(e2[k - 1], q);
         if (fabsf(q) < piv_min) q = -piv_min;
         cnt += q < 0.f;
       }
@@ -772,43 +698,49 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   }
   __syncthreads();
 
-  // 3. eigenvectors of T by twisted factorisation (thread per eigenvector)
+  // 3. eigenvectors of T by twisted factorisation (thread per eigenvector).
+  // The forward pivots Dp go to this thread's column of Z (and to global
+  // scratch for the regeneration below); the backward pivots Dm to global
+  // scratch, with the twist index found in the same backward pass.
   if (tid < n) {
     const float mu = lam[tid];
-    float* Dp = fac;                      // [k * n + tid]
+    float* Dpg = fac;                     // [k * n + tid]
     float* Dm = fac + (int64_t)n * n;
     float q = d[0] - mu;
     if (fabsf(q) < piv_min) q = piv_min;
-    Dp[tid] = q;
+    Z[tid] = q;
+    Dpg[tid] = q;
     for (int k = 1; k < n; ++k) {
-      q = d[k] - mu - e[k - 1] * e[k - 1] / q;
+      q = d[k] - mu - __fdividef(e2[k - 1], q);
       if (fabsf(q) < piv_min) q = piv_min;
-      Dp[(int64_t)k * n + tid] = q;
+      Z[k * ldn + tid] = q;
+      Dpg[(int64_t)k * n + tid] = q;
     }
     q = d[n - 1] - mu;
     if (fabsf(q) < piv_min) q = piv_min;
     Dm[(int64_t)(n - 1) * n + tid] = q;
+    int rt = n - 1;
+    float best = fabsf(Z[(n - 1) * ldn + tid] + q - (d[n - 1] - mu));
     for (int k = n - 2; k >= 0; --k) {
-      q = d[k] - mu - e[k] * e[k] / q;
+      q = d[k] - mu - __fdividef(e2[k], q);
       if (fabsf(q) < piv_min) q = piv_min;
       Dm[(int64_t)k * n + tid] = q;
-    }
-    int rt = 0;
-    float best = 3.0e38f;
-    for (int k = 0; k < n; ++k) {
-      const float g = fabsf(Dp[(int64_t)k * n + tid] + Dm[(int64_t)k * n + tid] - (d[k] - mu));
-      if (g < best) { best = g; rt = k; }
+      const float g = fabsf(Z[k * ldn + tid] + q - (d[k] - mu));
+      if (g <= best) {  // ties go to the smaller index
+        best = g;
+        rt = k;
+      }
     }
     float z = 1.f, nrm = 1.f;
-    Z[rt * ldn + tid] = 1.f;
     for (int k = rt - 1; k >= 0; --k) {
-      z = -(e[k] / Dp[(int64_t)k * n + tid]) * z;
+      z = -__fdividef(e[k], Z[k * ldn + tid]) * z;  // Dp_k, then overwritten by z
       Z[k * ldn + tid] = z;
       nrm = fmaf(z, z, nrm);
     }
+    Z[rt * ldn + tid] = 1.f;
     z = 1.f;
     for (int k = rt + 1; k < n; ++k) {
-      z = -(e[k - 1] / Dm[(int64_t)k * n + tid]) * z;
+      z = -__fdividef(e[k - 1], Dm[(int64_t)k * n + tid]) * z;
       Z[k * ldn + tid] = z;
       nrm = fmaf(z, z, nrm);
     }
@@ -877,21 +809,118 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   }
   __syncthreads();
 
-  // 4. back-transformation X = H_0 ... H_{n-3} Z: G threads per column (rows
-  // interleaved, partial dot products combined by shuffles); columns are
-  // independent, so no barriers
-  for (int base = 0; base < n; base += TE_T / G) {  // trip count uniform per block
-    const int c = base + tid / G, sub = tid % G;
-    for (int j = n - 3; j >= 0; --j) {
-      const float tj = tau[j];  // uniform across the block
-      if (tj == 0.f) continue;
-      float w = 0.f;
-      if (c < n)
-        for (int r = j + 1 + sub; r < n; r += G) w = fmaf(Ah[r * ldn + j], Z[r * ldn + c], w);
-      for (int o = 1; o < G; o <<= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      w *= tj;
-      if (c < n)
-        for (int r = j + 1 + sub; r < n; r += G) Z[r * ldn + c] = fmaf(-w, Ah[r * ldn + j], Z[r * ldn + c]);
+  // 4. back-transformation X = H_0 ... H_{n-3} Z in blocks of 8 reflectors:
+  // H_{8b} ... H_{8b+7} = I - V_b T_b V_b^T (compact WY form, T_b upper
+  // triangular: Schreiber & Van Loan, SIAM J. Sci. Stat. Comput. 10, 1989),
+  // blocks applied last to first as Z -= V_b (T_b (V_b^T Z)).  Reflector j
+  // is column j of Ah below the diagonal (rows > j).
+  const int nr = n >= 3 ? n - 2 : 0;
+  const int nb = (nr + 7) / 8;
+  // keep only the reflectors in Ah (entries below the diagonal of columns < nr)
+  for (int idx = tid; idx < n * n; idx += TE_T) {
+    const int r = idx / n, c = idx % n;
+    if (c >= nr || r <= c) Ah[r * ldn + c] = 0.f;
+  }
+  __syncthreads();
+  // (i) T_b[r][i] holds v_r^T v_i (r < i) ...
+  for (int pidx = warp; pidx < nb * 28; pidx += NW) {
+    const int b = pidx / 28, pr = pidx % 28;
+    int a = 0, c = pr;  // pair (a, c), a < c, row-major over the strict upper triangle
+    while (c >= 7 - a) {
+      c -= 7 - a;
+      ++a;
+    }
+    c += a + 1;
+    const int ja = 8 * b + a, jc = 8 * b + c;
+    float dot = 0.f;
+    if (jc < nr)
+      for (int r = jc + 1 + lane; r < n; r += 32) dot = fmaf(Ah[r * ldn + ja], Ah[r * ldn + jc], dot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if (lane == 0) Tw[b * 64 + a * 8 + c] = dot;
+  }
+  __syncthreads();
+  // ... (ii) then T_b itself, one thread per block (columns in order, rows ascending)
+  if (tid < nb) {
+    float* T = Tw + tid * 64;
+    for (int i = 0; i < 8; ++i) {
+      const int ji = 8 * tid + i;
+      const float ti = ji < nr ? tau[ji] : 0.f;
+      // T[m][i] (m < i) still holds v_m^T v_i where row r reads it: rows ascend
+      for (int r = 0; r < i; ++r) {
+        float acc = 0.f;
+        for (int m = r; m < i; ++m) acc = fmaf(T[r * 8 + m], T[m * 8 + i], acc);
+        T[r * 8 + i] = -ti * acc;
+      }
+      T[i * 8 + i] = ti;
+      for (int r = i + 1; r < 8; ++r) T[r * 8 + i] = 0.f;
+    }
+  }
+  __syncthreads();
+  // (iii) 8 threads (rows interleaved by 8) per group of 4 columns c = cbase +
+  // g + 32 q, so that each reflector entry loaded serves four columns; 256
+  // threads; columns are independent, so no barriers
+  if (tid < 256) {
+    constexpr int CPT = 4;
+    const int sub = tid & 7, g = tid >> 3;
+    for (int cbase = 0; cbase < n; cbase += 32 * CPT) {
+      for (int b = nb - 1; b >= 0; --b) {
+        const int j0 = 8 * b, cnt = min(8, nr - j0);  // reflectors in this block
+        const float* T = Tw + b * 64;
+        float w[CPT][8];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q)
+#pragma unroll
+          for (int m = 0; m < 8; ++m) w[q][m] = 0.f;
+        // first row of this thread's interleave that is > j0
+        const int rs = j0 + 1 + ((sub - (j0 + 1)) & 7);
+        for (int r = rs; r < n; r += 8) {
+          float v[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) v[m] = m < cnt ? Ah[r * ldn + j0 + m] : 0.f;
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) {
+            const int c = cbase + g + 32 * q;
+            const float z = c < n ? Z[r * ldn + c] : 0.f;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) w[q][m] = fmaf(v[m], z, w[q][m]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < CPT; ++q)
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            w[q][m] += __shfl_xor_sync(0xffffffffu, w[q][m], 1);
+            w[q][m] += __shfl_xor_sync(0xffffffffu, w[q][m], 2);
+            w[q][m] += __shfl_xor_sync(0xffffffffu, w[q][m], 4);
+          }
+        // y = T w in place (row r of T reads w[m] for m >= r only)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = r; m < 8; ++m) acc = fmaf(T[r * 8 + m], w[q][m], acc);
+            w[q][r] = acc;
+          }
+        }
+        for (int r = rs; r < n; r += 8) {
+          float v[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) v[m] = m < cnt ? Ah[r * ldn + j0 + m] : 0.f;
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) {
+            const int c = cbase + g + 32 * q;
+            if (c < n) {
+              float z = Z[r * ldn + c];
+#pragma unroll
+              for (int m = 0; m < 8; ++m) z = fmaf(-v[m], w[q][m], z);
+              Z[r * ldn + c] = z;
+            }
+          }
+        }
+      }
     }
   }
   __syncthreads();
@@ -899,86 +928,350 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
     for (int j = lane; j < n; j += 32) X_out[(int64_t)i * n + j] = (double)Z[i * ldn + j];
 }
 
-// FP64 refinement (Ogita & Aishima), step 1 of 2, one CTA: Rayleigh quotients
-// lambda_i = S_ii / P_ii (= S_ii / (1 - R_ii) with R = I - P) and the cluster
-// threshold delta = 2 (||S - diag(lambda)||_F + ||A||_F ||R||_F) (norms in
-// float32: only their magnitude matters).
-__global__ void __launch_bounds__(1024) refine_lambda_kernel(const double* __restrict__ S,
-                                                             const double* __restrict__ P,
-                                                             const double* __restrict__ A, int n,
-                                                             double* __restrict__ lam,
-                                                             double* __restrict__ delta) {
-  __shared__ float s_red[3][32];
-  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < n; i += T) lam[i] = S[(int64_t)i * n + i] / P[(int64_t)i * n + i];
-  float a = 0.f, b = 0.f, c = 0.f;
-  for (int i = warp; i < n; i += T / 32)
-    for (int j = lane; j < n; j += 32) {
-      const int64_t idx = (int64_t)i * n + j;
-      const float sd = (i == j) ? 0.f : (float)S[idx];
-      const float rr = (float)((i == j ? 1.0 : 0.0) - P[idx]);
-      const float aa = (float)A[idx];
-      a = fmaf(sd, sd, a);
-      b = fmaf(aa, aa, b);
-      c = fmaf(rr, rr, c);
-    }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-  }
-  if (lane == 0) {
-    s_red[0][warp] = a;
-    s_red[1][warp] = b;
-    s_red[2][warp] = c;
+// ---------------------------------------------------------------------------
+// FP64 refinement of the float32 eigenvectors (Ogita & Aishima, "Iterative
+// refinement for symmetric eigenvalue decomposition", Japan J. Indust. Appl.
+// Math. 35, 2018), one cooperative kernel over the whole GPU.  Per iteration:
+//   AX = A X;  S = X^T AX,  P = X^T X  (R = I - P);
+//   lambda_i = S_ii / P_ii,
+//   delta = 2 (||S - diag(S)||_F + ||A||_F ||R||_F);
+//   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) where
+//          |lambda_j - lambda_i| > delta, else R_ij / 2 (clusters, diagonal);
+//   X <- X + X E,
+// stopping once max |E_ij| <= REFINE_TOL (the next correction would be of
+// order REFINE_TOL^2 ||A|| / gap, below FP64 rounding) or after REFINE_MAX
+// iterations.  The eigenvalues are the last Rayleigh quotients; the pairs are
+// then sorted descending and each vector signed so that its largest-magnitude
+// entry is positive.  The FP64 products are spread over every SM (output
+// tiles whose operand rows / columns are staged in shared memory, the k range
+// split over the CTA's warps; S and P only on the upper block triangle);
+// phases are separated by a grid barrier whose wait is bounded (on time-out
+// the kernel sets the failure flag and returns).  Data written inside the
+// kernel is read with L2 loads (__ldcg).
+// ---------------------------------------------------------------------------
+constexpr int RF_T = 256;
+constexpr int REFINE_MAX = 8;
+constexpr double REFINE_TOL = 1e-10;
+constexpr long long GRID_WAIT_CYCLES = 4000000000LL;  // about 2 s
+constexpr int RF_MAX_GRID = 1024;  // per-CTA partial slots per quantity
+constexpr int RF_NMAX = 160;
+constexpr int PT_COLS = (RF_NMAX * 8 + RF_T - 1) / RF_T;  // panel entries per thread (n x 8)
+constexpr int PT_ROWS = (RF_NMAX * 4 + RF_T - 1) / RF_T;  // (4 x n)
+
+struct RefineArgs {
+  const double* A;   // n x n symmetric
+  double* X;         // n x n: the starting vectors
+  double* Xn;        // n x n scratch
+  double* AX;        // n x n scratch: A X, kept up to date as X changes
+  double* AXn;       // n x n scratch
+  double* S;         // n x n scratch
+  double* P;         // n x n scratch
+  double* E;         // n x n scratch
+  double* lam;       // n
+  double* part;      // 4 x RF_MAX_GRID per-CTA partials: ||A||^2, ||S - diag S||^2, ||R||^2, max|E|
+  unsigned* bar;     // barrier counter (zero on entry)
+  int* flag;         // 2: non-finite eigenvalue; 3: barrier time-out
+  double* evals;     // n, descending
+  double* evecs;     // n x n, column i = eigenvector i
+  int n;
+};
+
+// Grid-wide barrier for a cooperative launch (all CTAs resident): one
+// counter, to which CTA 0 adds 2^31 - (gridDim.x - 1) and every other CTA 1,
+// so that bit 31 flips once all have arrived; arrival is a release, the wait
+// an acquire.  The counter starts at zero and is never reset.  False if the
+// wait timed out (the failure flag is then set).
+__device__ bool grid_barrier(unsigned* count, int* flag) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+    unsigned old, v;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(count), "r"(add) : "memory");
+    const long long t0 = clock64();
+    do {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (((v ^ old) & 0x80000000u) != 0u) break;
+      if (clock64() - t0 > GRID_WAIT_CYCLES) {
+        atomicExch(flag, 3);
+        ok = 0;
+        break;
+      }
+    } while (true);
+    s_ok = ok;
   }
   __syncthreads();
-  if (tid == 0) {
-    float x = 0.f, y = 0.f, z = 0.f;
-    for (int w = 0; w < T / 32; ++w) {
-      x += s_red[0][w];
-      y += s_red[1][w];
-      z += s_red[2][w];
+  return s_ok != 0;
+}
+
+// Sum (is_max: maximum) of v over the block, to every thread.
+__device__ __forceinline__ double block_reduce_d(double v, double* red, bool is_max) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmax(v, u) : v + u;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = red[0];
+#pragma unroll
+  for (int w = 1; w < RF_T / 32; ++w) t = is_max ? fmax(t, red[w]) : t + red[w];
+  return t;
+}
+
+// Sum (is_max: maximum) of the per-CTA partials slot[0, gridDim.x), reduced by
+// every warp in the same order (so every CTA gets the same value); the first
+// 256 partials are loaded at once.
+__device__ __forceinline__ double grid_total(const double* slot, bool is_max) {
+  const int lane = threadIdx.x & 31, G = (int)gridDim.x;
+  double v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = lane + 32 * q < G ? __ldcg(slot + lane + 32 * q) : 0.0;
+  double t = v[0];
+#pragma unroll
+  for (int q = 1; q < 8; ++q) t = is_max ? fmax(t, v[q]) : t + v[q];
+  for (int b = lane + 256; b < G; b += 32) {
+    const double u = __ldcg(slot + b);
+    t = is_max ? fmax(t, u) : t + u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_xor_sync(0xffffffffu, t, o);
+    t = is_max ? fmax(t, u) : t + u;
+  }
+  return t;
+}
+
+// Operand staging: every load of a panel is issued before its stores, so a
+// panel costs one L2 round trip.
+struct Cols8 {  // columns [c0, c0 + 8) of an n x n matrix as n x 8
+  double v[PT_COLS];
+};
+struct Rows4 {  // rows [r0, r0 + 4) as 4 x n
+  double v[PT_ROWS];
+};
+__device__ __forceinline__ void load_cols8(Cols8& p, const double* M, int c0, int n) {
+#pragma unroll
+  for (int t = 0; t < PT_COLS; ++t) {
+    const int idx = threadIdx.x + t * RF_T, k = idx >> 3, c = idx & 7;
+    p.v[t] = (k < n && c0 + c < n) ? __ldcg(M + k * n + c0 + c) : 0.0;
+  }
+}
+__device__ __forceinline__ void store_cols8(double* dst, const Cols8& p, int n) {
+#pragma unroll
+  for (int t = 0; t < PT_COLS; ++t) {
+    const int idx = threadIdx.x + t * RF_T;
+    if (idx < n * 8) dst[idx] = p.v[t];
+  }
+}
+__device__ __forceinline__ void load_rows4(Rows4& p, const double* M, int r0, int n) {
+#pragma unroll
+  for (int t = 0; t < PT_ROWS; ++t) {
+    const int idx = threadIdx.x + t * RF_T, r = idx / n, k = idx % n;
+    p.v[t] = (r < 4 && r0 + r < n) ? __ldcg(M + (r0 + r) * n + k) : 0.0;
+  }
+}
+__device__ __forceinline__ void store_rows4(double* dst, const Rows4& p, int n) {
+#pragma unroll
+  for (int t = 0; t < PT_ROWS; ++t) {
+    const int idx = threadIdx.x + t * RF_T;
+    if (idx < 4 * n) dst[idx] = p.v[t];
+  }
+}
+
+// C[i][j] = (Add ? Add[i][j] : 0) + sum_k L[i][k] R[k][j] over 4 x 8 output
+// tiles, and when L2 is given also C2 = L2 + L2 R (same R): a tile's 4 rows of
+// L (and L2) and 8 columns of R are staged in shared memory, the k range is
+// split over 8 warps and the partial sums added by warp 0.
+__device__ void gemm_tiles_4x8(const double* L, const double* R, const double* Add, double* C,
+                               const double* L2, double* C2, int n, double* sm) {
+  const int ntr = (n + 3) / 4, ntc = (n + 7) / 8, items = ntr * ntc;
+  double* sl = sm;            // 4 x n
+  double* sl2 = sl + 4 * n;   // 4 x n
+  double* sr = sl2 + 4 * n;   // n x 8
+  double* part = sr + 8 * n;  // 8 x 32 x 2
+  const int ks = threadIdx.x >> 5, o = threadIdx.x & 31, ty = o >> 3, tx = o & 7;
+  const bool two = L2 != nullptr;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int i0 = (item / ntc) * 4, j0 = (item % ntc) * 8;
+    Rows4 pl, pl2;
+    Cols8 pr;
+    load_rows4(pl, L, i0, n);
+    if (two) load_rows4(pl2, L2, i0, n);
+    load_cols8(pr, R, j0, n);
+    store_rows4(sl, pl, n);
+    if (two) store_rows4(sl2, pl2, n);
+    store_cols8(sr, pr, n);
+    __syncthreads();
+    double acc = 0.0, acc2 = 0.0;
+    if (two) {
+      for (int k = ks; k < n; k += 8) {
+        const double r = sr[k * 8 + tx];
+        acc = fma(sl[ty * n + k], r, acc);
+        acc2 = fma(sl2[ty * n + k], r, acc2);
+      }
+    } else {
+      for (int k = ks; k < n; k += 8) acc = fma(sl[ty * n + k], sr[k * 8 + tx], acc);
     }
-    *delta = 2.0 * (sqrt((double)x) + sqrt((double)y) * sqrt((double)z));
+    part[(ks * 32 + o) * 2] = acc;
+    part[(ks * 32 + o) * 2 + 1] = acc2;
+    __syncthreads();
+    if (ks == 0) {
+      double t = 0.0, t2 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        t += part[(q * 32 + o) * 2];
+        t2 += part[(q * 32 + o) * 2 + 1];
+      }
+      const int i = i0 + ty, j = j0 + tx;
+      if (i < n && j < n) {
+        C[i * n + j] = (Add ? __ldcg(Add + i * n + j) : 0.0) + t;
+        if (two) C2[i * n + j] = __ldcg(L2 + i * n + j) + t2;
+      }
+    }
+    __syncthreads();  // shared buffers are reused by the next item
   }
 }
 
-// Step 2 of 2, many CTAs: E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)
-// for separated eigenvalues, R_ij / 2 inside clusters and on the diagonal, so
-// that X <- X + X E.
-__global__ void refine_e_kernel(const double* __restrict__ S, const double* __restrict__ P,
-                                const double* __restrict__ lam,
-                                const double* __restrict__ delta, int n,
-                                double* __restrict__ E) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * n) return;
-  const int i = (int)(idx / n), j = (int)(idx % n);
-  const double rij = (i == j ? 1.0 : 0.0) - P[idx];
-  double e = 0.5 * rij;
-  if (i != j) {
-    const double gap = lam[j] - lam[i];
-    if (fabs(gap) > *delta) e = (S[idx] + lam[j] * rij) / gap;
+__global__ void __launch_bounds__(RF_T) refine_kernel(RefineArgs a) {
+  extern __shared__ double rsm[];
+  __shared__ double red[RF_T / 32];
+  const int n = a.n;
+  const int tid = threadIdx.x;
+  const int gtid = blockIdx.x * RF_T + tid, gthreads = gridDim.x * RF_T;
+  double* pA2 = a.part;
+  double* pS = a.part + RF_MAX_GRID;
+  double* pR = a.part + 2 * RF_MAX_GRID;
+  double* pE = a.part + 3 * RF_MAX_GRID;
+  // ||A||_F^2
+  {
+    double v = 0.0;
+    for (int idx = gtid; idx < n * n; idx += gthreads) v = fma(a.A[idx], a.A[idx], v);
+    const double t = block_reduce_d(v, red, false);
+    if (tid == 0) pA2[blockIdx.x] = t;
   }
-  E[idx] = e;
-}
-
-// Sort eigenpairs descending and fix signs (largest-magnitude entry positive);
-// one warp per eigenpair.
-__global__ void __launch_bounds__(1024) eig_finalize_kernel(const double* __restrict__ lam,
-                                                            const double* __restrict__ X, int n,
-                                                            double* __restrict__ evals,
-                                                            double* __restrict__ evecs,
-                                                            int* __restrict__ flag) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < n; i += nw) {
-    const double li = lam[i];
+  double* X = a.X;
+  double* Xn = a.Xn;
+  double* AX = a.AX;
+  double* AXn = a.AXn;
+  const int nb8 = (n + 7) / 8, npairs = nb8 * (nb8 + 1) / 2;
+  gemm_tiles_4x8(a.A, X, nullptr, AX, nullptr, nullptr, n, rsm);  // AX = A X
+  if (!grid_barrier(a.bar, a.flag)) return;
+  for (int it = 0; it < REFINE_MAX; ++it) {
+    // S = X^T AX and P = X^T X on the upper block triangle (both symmetric),
+    // lambda, and the two norms
+    double s_off = 0.0, r2 = 0.0;
+    {
+      double* xi = rsm;          // n x 8: X columns of block bi
+      double* axj = xi + 8 * n;  // n x 8: AX columns of block bj
+      double* xj = axj + 8 * n;  // n x 8: X columns of block bj
+      double* part = xj + 8 * n; // 4 x 64 x 2
+      const int ks = tid >> 6, o = tid & 63, ty = o >> 3, tx = o & 7;
+      for (int item = blockIdx.x; item < npairs; item += gridDim.x) {
+        int bi = 0, rem = item;  // item -> (bi, bj), bi <= bj, row-major
+        while (rem >= nb8 - bi) {
+          rem -= nb8 - bi;
+          ++bi;
+        }
+        const int bj = bi + rem;
+        Cols8 p1, p2, p3;
+        load_cols8(p1, X, 8 * bi, n);
+        load_cols8(p2, AX, 8 * bj, n);
+        load_cols8(p3, X, 8 * bj, n);
+        store_cols8(xi, p1, n);
+        store_cols8(axj, p2, n);
+        store_cols8(xj, p3, n);
+        __syncthreads();
+        double sv = 0.0, pv = 0.0;
+        for (int k = ks; k < n; k += 4) {
+          const double x = xi[k * 8 + ty];
+          sv = fma(x, axj[k * 8 + tx], sv);
+          pv = fma(x, xj[k * 8 + tx], pv);
+        }
+        part[(ks * 64 + o) * 2] = sv;
+        part[(ks * 64 + o) * 2 + 1] = pv;
+        __syncthreads();
+        if (ks == 0) {
+          double st = 0.0, pt = 0.0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            st += part[(q * 64 + o) * 2];
+            pt += part[(q * 64 + o) * 2 + 1];
+          }
+          const int i = 8 * bi + ty, j = 8 * bj + tx;
+          if (i < n && j < n) {
+            a.S[i * n + j] = st;
+            a.P[i * n + j] = pt;
+            const double w = bi == bj ? 1.0 : 2.0;  // mirrored entries count twice
+            const double rr = (i == j ? 1.0 : 0.0) - pt;
+            r2 = fma(w * rr, rr, r2);
+            if (i != j) s_off = fma(w * st, st, s_off);
+            else a.lam[i] = st / pt;
+            if (bi != bj) {
+              a.S[j * n + i] = st;
+              a.P[j * n + i] = pt;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    {
+      const double t1 = block_reduce_d(s_off, red, false);
+      const double t2 = block_reduce_d(r2, red, false);
+      if (tid == 0) {
+        pS[blockIdx.x] = t1;
+        pR[blockIdx.x] = t2;
+      }
+    }
+    if (!grid_barrier(a.bar, a.flag)) return;
+    // E and its largest entry
+    {
+      const double ts = grid_total(pS, false), ta = grid_total(pA2, false),
+                   tr = grid_total(pR, false);
+      const double delta = 2.0 * (sqrt(ts) + sqrt(ta) * sqrt(tr));
+      double mx = 0.0;
+      for (int idx = gtid; idx < n * n; idx += gthreads) {
+        const int i = idx / n, j = idx % n;
+        const double rij = (i == j ? 1.0 : 0.0) - __ldcg(a.P + idx);
+        double e = 0.5 * rij;
+        if (i != j) {
+          const double lj = __ldcg(a.lam + j), gap = lj - __ldcg(a.lam + i);
+          if (fabs(gap) > delta) e = (__ldcg(a.S + idx) + lj * rij) / gap;
+        }
+        a.E[idx] = e;
+        mx = fmax(mx, fabs(e));
+      }
+      const double t = block_reduce_d(mx, red, true);
+      if (tid == 0) pE[blockIdx.x] = t;
+    }
+    if (!grid_barrier(a.bar, a.flag)) return;
+    // X <- X + X E, and AX <- AX + (AX) E = A X for the next iteration (not
+    // needed after the last one)
+    const bool last = grid_total(pE, true) <= REFINE_TOL;
+    gemm_tiles_4x8(X, a.E, X, Xn, last ? nullptr : AX, AXn, n, rsm);
+    if (!grid_barrier(a.bar, a.flag)) return;
+    double* t = X;
+    X = Xn;
+    Xn = t;
+    t = AX;
+    AX = AXn;
+    AXn = t;
+    if (last) break;
+  }
+  // sort descending, fix signs: one warp per eigenpair
+  const int lane = tid & 31;
+  for (int i = gtid >> 5; i < n; i += gthreads >> 5) {
+    const double li = __ldcg(a.lam + i);
     int rank = 0;
     double best = 0.0;
     for (int j = lane; j < n; j += 32) {
-      if (lam[j] > li || (lam[j] == li && j < i)) ++rank;
-      const double v = X[(int64_t)j * n + i];
+      const double lj = __ldcg(a.lam + j);
+      if (lj > li || (lj == li && j < i)) ++rank;
+      const double v = __ldcg(X + j * n + i);
       if (fabs(v) > fabs(best)) best = v;
     }
 #pragma unroll
@@ -989,10 +1282,10 @@ __global__ void __launch_bounds__(1024) eig_finalize_kernel(const double* __rest
     }
     const double sgn = best < 0.0 ? -1.0 : 1.0;
     if (lane == 0) {
-      evals[rank] = li;
-      if (!isfinite(li)) *flag = 2;  // non-finite input or breakdown
+      a.evals[rank] = li;
+      if (!isfinite(li)) atomicExch(a.flag, 2);  // non-finite input or breakdown
     }
-    for (int r = lane; r < n; r += 32) evecs[(int64_t)r * n + rank] = sgn * X[(int64_t)r * n + i];
+    for (int r = lane; r < n; r += 32) a.evecs[r * n + rank] = sgn * __ldcg(X + r * n + i);
   }
 }
 
@@ -1013,11 +1306,6 @@ __global__ void whitening_factors_kernel(const double* __restrict__ evals,
   Cw[idx] = evecs[r * n + i] / s;
   Cp[idx] = evecs[r * n + i] * s;
   if (Cw32) Cw32[idx] = (float)(evecs[r * n + i] / s);
-}
-
-__global__ void copy_f64_kernel(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = a[i];
 }
 
 int num_sms() {
@@ -1126,10 +1414,26 @@ otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cuda
   return OTM_OK;
 }
 
+// One CTA per SM (the cooperative launch needs every CTA resident), at most
+// RF_MAX_GRID.
+unsigned refine_grid() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (sms[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = v > 0 ? (v < RF_MAX_GRID ? v : RF_MAX_GRID) : 1;
+  }
+  return (unsigned)sms[dev];
+}
+
 size_t syev_workspace(int64_t n) {
   WorkspaceSize w;
-  for (int i = 0; i < 7; ++i) w.add<double>(n * n);
-  w.add<double>(n).add<double>(1).add<float>(2 * n * n);
+  for (int i = 0; i < 8; ++i) w.add<double>(n * n);
+  w.add<double>(n).add<double>(4 * RF_MAX_GRID);
+  w.add<unsigned>(1).add<float>(2 * n * n);
   return w.bytes();
 }
 
@@ -1147,41 +1451,32 @@ otm_status syev(const double* A_in, int64_t n, double* evals, double* evecs, Wor
   double* X = ws.take<double>(n * n);
   double* Xn = ws.take<double>(n * n);
   double* AX = ws.take<double>(n * n);
+  double* AXn = ws.take<double>(n * n);
   double* S = ws.take<double>(n * n);
   double* P = ws.take<double>(n * n);
   double* E = ws.take<double>(n * n);
   double* lam = ws.take<double>(n);
-  double* delta = ws.take<double>(1);
+  double* part = ws.take<double>(4 * RF_MAX_GRID);
+  unsigned* bar = ws.take<unsigned>(1);
   float* fac = ws.take<float>(2 * n * n);
   if (!fac) return set_error(OTM_EINVAL, "syev: workspace too small");
   const unsigned nb = (unsigned)((n * n + 255) / 256);
   symmetrize_kernel<<<nb, 256, 0, st>>>(A_in, n, A);
   OTM_CHECK_LAUNCH();
   const int64_t ldn = n | 1;
-  const size_t smem = sizeof(float) * (2 * n * ldn + 5 * n);
+  const size_t smem = sizeof(float) * (2 * n * ldn + 5 * n + 64 * ((n + 5) / 8));
   OTM_CHECK_CUDA(cudaFuncSetAttribute(tridiag_eig_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   tridiag_eig_kernel<<<1, TE_T, smem, st>>>(A, (int)n, X, fac);
   OTM_CHECK_LAUNCH();
   // FP64 refinement: quadratic convergence from the float32 eigenvectors
-  const int iters = 4;
-  for (int it = 0; it < iters; ++it) {
-    OTM_TRY(dgemm_small(0, 0, n, n, n, 1.0, A, n, X, n, 0.0, AX, n, st));
-    OTM_TRY(dgemm_small(1, 0, n, n, n, 1.0, X, n, AX, n, 0.0, S, n, st));
-    OTM_TRY(dgemm_small(1, 0, n, n, n, 1.0, X, n, X, n, 0.0, P, n, st));
-    refine_lambda_kernel<<<1, 1024, 0, st>>>(S, P, A, (int)n, lam, delta);
-    OTM_CHECK_LAUNCH();
-    refine_e_kernel<<<nb, 256, 0, st>>>(S, P, lam, delta, (int)n, E);
-    OTM_CHECK_LAUNCH();
-    copy_f64_kernel<<<nb, 256, 0, st>>>(X, Xn, n * n);
-    OTM_CHECK_LAUNCH();
-    OTM_TRY(dgemm_small(0, 0, n, n, n, 1.0, X, n, E, n, 1.0, Xn, n, st));
-    double* t = X;
-    X = Xn;
-    Xn = t;
-  }
-  eig_finalize_kernel<<<1, 1024, 0, st>>>(lam, X, (int)n, evals, evecs, dflag);
-  OTM_CHECK_LAUNCH();
+  RefineArgs ra{A, X, Xn, AX, AXn, S, P, E, lam, part, bar, dflag, evals, evecs, (int)n};
+  OTM_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
+  void* kargs[] = {&ra};
+  const size_t rsmem = sizeof(double) * (24 * n + 4 * 64 * 2);  // the largest phase (S, P)
+  OTM_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)refine_kernel, dim3(refine_grid()),
+                                             dim3(RF_T), kargs, rsmem, st));
+  count_launch();
   return OTM_OK;
 }
 

@@ -104,7 +104,8 @@ otm_status dgemm_small(int ta, int tb, int64_t m, int64_t n, int64_t kk, double 
                        double* C, int64_t ldc, cudaStream_t st);
 size_t orth_workspace(int64_t m);
 // Device-side failure flags: *dflag is set to 1 (QR: non-finite Gram matrix) or
-// 2 (eigensolver: non-finite eigenvalues); callers zero it and check it once.
+// 2 (eigensolver: non-finite eigenvalues) or 3 (eigensolver: the refinement's grid
+// barrier timed out); callers zero it and check it once.
 // passes: Cholesky-QR passes (pass 0 shifted, pass 1 plain, passes 2-3 only while
 // the basis is not yet orthonormal to 1e-5); 2 suffices for the intermediate
 // bases of a power iteration, whose span is all that matters.

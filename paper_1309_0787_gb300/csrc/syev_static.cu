@@ -21,7 +21,7 @@ namespace otm {
 namespace {
 
 constexpr int64_t NOALLOC_MAX_N = 160;
-constexpr size_t SCRATCH_BYTES = size_t(2) << 20;  // 2 MiB; n = 160 needs about 1.64 MB
+constexpr size_t SCRATCH_BYTES = size_t(2) << 20;  // 2 MiB; n = 160 needs about 1.88 MB
 constexpr int MAX_DEVICES = 64;
 
 // Device scratch of otm_syev_noalloc.  In host code this name only stands for
@@ -81,7 +81,8 @@ otm_status otm_syev_noalloc(const double* A, int64_t n, double* evals, double* e
   int h = 0;
   OTM_CHECK_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (h) return set_error(OTM_ENOTCONVERGED, "otm_syev_noalloc: non-finite eigenvalues");
+  if (h)
+    return set_error(OTM_ENOTCONVERGED, "otm_syev_noalloc: non-finite eigenvalues or refinement failure");
   return OTM_OK;
 }
 
