@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a, int 
             accA[x][y] = 0.f;
             accB[x][y] = 0.f;
           }
+#pragma unroll 2
         for (int r = 0; r < ldk; r += 4) {
           float4 v[4], ya[4], yb[4];
 #pragma unroll
@@ -376,38 +377,71 @@ __global__ void __launch_bounds__(THREADS, 1) sgd_cluster_kernel(SgdArgs a, int 
       for (int c = 0; c < CL; ++c) g += part[c];
       gd[jj * ldk + r] = g;
     }
+    // H[jj][j] = (v_i . v_j)^2 (thread per entry, four partial sums)
     for (int idx = tid; idx < nown * kp; idx += THREADS) {
       const int jj = idx / kp, j = idx % kp;
       const float* vi = Vc + (own_lo + jj) * ldk;
       const float* vj = Vc + j * ldk;
-      float h = 0.f;
+      float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f;
+#pragma unroll 5
       for (int r = 0; r < ldk; r += 4) {
         const float4 x = *reinterpret_cast<const float4*>(vi + r);
         const float4 y = *reinterpret_cast<const float4*>(vj + r);
-        h = fmaf(x.x, y.x, h);
-        h = fmaf(x.y, y.y, h);
-        h = fmaf(x.z, y.z, h);
-        h = fmaf(x.w, y.w, h);
+        h0 = fmaf(x.x, y.x, h0);
+        h1 = fmaf(x.y, y.y, h1);
+        h2 = fmaf(x.z, y.z, h2);
+        h3 = fmaf(x.w, y.w, h3);
       }
+      const float h = (h0 + h1) + (h2 + h3);
       Hm[jj * ldk + j] = h * h;
     }
     __syncthreads();
-    for (int idx = tid; idx < nown * kp; idx += THREADS) {
-      const int jj = idx / kp, r = idx % kp;
+    // Gram term G = V (H o H) and the update: thread per (column, 4 coordinates)
+    for (int idx = tid; idx < nown * (kp / 4); idx += THREADS) {
+      const int jj = idx / (kp / 4), r = 4 * (idx % (kp / 4));
       const int i = own_lo + jj;
-      float g = 0.f;
-      for (int j = 0; j < k; ++j) g = fmaf(Hm[jj * ldk + j], Vc[j * ldk + r], g);
-      const float gdata =
-          gd[jj * ldk + r] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * sown[jj] * inv_b);
-      const float vnew = Vc[i * ldk + r] - beta * (a.kappa * g - gdata);
-      vn[jj * ldk + r] = (r < k) ? vnew : 0.f;
+      float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < k; j += 2) {
+        const float ha = Hm[jj * ldk + j], hb = Hm[jj * ldk + j + 1];
+        const float4 va = *reinterpret_cast<const float4*>(Vc + j * ldk + r);
+        const float4 vb = *reinterpret_cast<const float4*>(Vc + (j + 1) * ldk + r);
+        g0.x = fmaf(ha, va.x, g0.x);
+        g0.y = fmaf(ha, va.y, g0.y);
+        g0.z = fmaf(ha, va.z, g0.z);
+        g0.w = fmaf(ha, va.w, g0.w);
+        g1.x = fmaf(hb, vb.x, g1.x);
+        g1.y = fmaf(hb, vb.y, g1.y);
+        g1.z = fmaf(hb, vb.z, g1.z);
+        g1.w = fmaf(hb, vb.w, g1.w);
+      }
+      if (j < k) {
+        const float ha = Hm[jj * ldk + j];
+        const float4 va = *reinterpret_cast<const float4*>(Vc + j * ldk + r);
+        g0.x = fmaf(ha, va.x, g0.x);
+        g0.y = fmaf(ha, va.y, g0.y);
+        g0.z = fmaf(ha, va.z, g0.z);
+        g0.w = fmaf(ha, va.w, g0.w);
+      }
+      const float gg[4] = {g0.x + g1.x, g0.y + g1.y, g0.z + g1.z, g0.w + g1.w};
+      const float mean_term = a.c3 * aA[i] * aB[i] - a.c2 * sown[jj] * inv_b;
+      float out[4];
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        const float gdata = gd[jj * ldk + r + z] * inv_b + ybC[r + z] * mean_term;
+        const float vnew = Vc[i * ldk + r + z] - beta * (a.kappa * gg[z] - gdata);
+        out[z] = (r + z < k) ? vnew : 0.f;
+      }
+      *reinterpret_cast<float4*>(vn + jj * ldk + r) = make_float4(out[0], out[1], out[2], out[3]);
     }
     __syncthreads();
-    for (int idx = tid; idx < nown * kp; idx += THREADS) {
-      const int jj = idx / kp, r = idx % kp;
-      const float v = vn[jj * ldk + r];
+    for (int idx = tid; idx < nown * (kp / 4); idx += THREADS) {
+      const int jj = idx / (kp / 4), r = 4 * (idx % (kp / 4));
+      const float4 v = *reinterpret_cast<const float4*>(vn + jj * ldk + r);
 #pragma unroll
-      for (int c = 0; c < CL; ++c) cluster.map_shared_rank(Vn, c)[(own_lo + jj) * ldk + r] = v;
+      for (int c = 0; c < CL; ++c)
+        *reinterpret_cast<float4*>(cluster.map_shared_rank(Vn, c) + (own_lo + jj) * ldk + r) = v;
     }
     // means of the new owned columns for the next step, to every CTA
     for (int jj = warp; jj < nown; jj += THREADS / 32) {
