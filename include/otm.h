@@ -263,6 +263,26 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
                        int64_t b, double beta0, double theta, double alpha0,
                        int64_t snapshot_every, float* V_snap, void* stream);
 
+/*
+ * otm_sgd_set_form -- which FP32 kernel otm_sgd_step / otm_sgd_run use, for
+ * the whole process (no paper counterpart; a performance choice with the same
+ * results up to FP32 summation order):
+ *   0 (default)  chosen by size: the grid form for k <= 128 and
+ *                256 <= b <= 32 x (SM count), the cluster form otherwise;
+ *   1            the cluster form: one thread-block cluster of up to 16 CTAs
+ *                keeps V in shared memory, the minibatch split over its CTAs,
+ *                partial products reduced through distributed shared memory;
+ *   2            the grid form: one cooperative launch of up to one CTA per SM,
+ *                the minibatch split over all of them, partial products
+ *                reduced through L2 by the owners of the columns, two grid
+ *                barriers per step (k <= 128, 16 <= b <= 32 x SMs, else
+ *                OTM_EINVAL from the run).  It takes its scratch with
+ *                cudaMallocAsync on the stream and frees it after the launch.
+ *                On a barrier time-out the affected columns of V are NaN.
+ * OTM_EINVAL for another value.
+ */
+otm_status otm_sgd_set_form(int form);
+
 /* ------------------------------------------------------------------------ */
 /* Precision form of the STGD (not in the paper: BF16 / FP8 tensor cores)     */
 /* ------------------------------------------------------------------------ */

@@ -12,6 +12,7 @@
 // low on this part, so no FP64 loop runs inside a single CTA).
 #include <math.h>
 
+#include "grid_sync.cuh"
 #include "otm_internal.cuh"
 
 namespace otm {
@@ -952,7 +953,6 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
 constexpr int RF_T = 256;
 constexpr int REFINE_MAX = 8;
 constexpr double REFINE_TOL = 1e-10;
-constexpr long long GRID_WAIT_CYCLES = 4000000000LL;  // about 2 s
 constexpr int RF_MAX_GRID = 1024;  // per-CTA partial slots per quantity
 constexpr int RF_NMAX = 160;
 constexpr int PT_COLS = (RF_NMAX * 8 + RF_T - 1) / RF_T;  // panel entries per thread (n x 8)
@@ -975,36 +975,6 @@ struct RefineArgs {
   double* evecs;     // n x n, column i = eigenvector i
   int n;
 };
-
-// Grid-wide barrier for a cooperative launch (all CTAs resident): one
-// counter, to which CTA 0 adds 2^31 - (gridDim.x - 1) and every other CTA 1,
-// so that bit 31 flips once all have arrived; arrival is a release, the wait
-// an acquire.  The counter starts at zero and is never reset.  False if the
-// wait timed out (the failure flag is then set).
-__device__ bool grid_barrier(unsigned* count, int* flag) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
-    unsigned old, v;
-    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;"
-                 : "=r"(old) : "l"(count), "r"(add) : "memory");
-    const long long t0 = clock64();
-    do {
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
-      if (((v ^ old) & 0x80000000u) != 0u) break;
-      if (clock64() - t0 > GRID_WAIT_CYCLES) {
-        atomicExch(flag, 3);
-        ok = 0;
-        break;
-      }
-    } while (true);
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 // Sum (is_max: maximum) of v over the block, to every thread.
 __device__ __forceinline__ double block_reduce_d(double v, double* red, bool is_max) {
@@ -1159,7 +1129,7 @@ __global__ void __launch_bounds__(RF_T) refine_kernel(RefineArgs a) {
   double* AXn = a.AXn;
   const int nb8 = (n + 7) / 8, npairs = nb8 * (nb8 + 1) / 2;
   gemm_tiles_4x8(a.A, X, nullptr, AX, nullptr, nullptr, n, rsm);  // AX = A X
-  if (!grid_barrier(a.bar, a.flag)) return;
+  if (!grid_barrier(a.bar, a.flag, 3)) return;
   for (int it = 0; it < REFINE_MAX; ++it) {
     // S = X^T AX and P = X^T X on the upper block triangle (both symmetric),
     // lambda, and the two norms
@@ -1227,7 +1197,7 @@ __global__ void __launch_bounds__(RF_T) refine_kernel(RefineArgs a) {
         pR[blockIdx.x] = t2;
       }
     }
-    if (!grid_barrier(a.bar, a.flag)) return;
+    if (!grid_barrier(a.bar, a.flag, 3)) return;
     // E and its largest entry
     {
       const double ts = grid_total(pS, false), ta = grid_total(pA2, false),
@@ -1248,12 +1218,12 @@ __global__ void __launch_bounds__(RF_T) refine_kernel(RefineArgs a) {
       const double t = block_reduce_d(mx, red, true);
       if (tid == 0) pE[blockIdx.x] = t;
     }
-    if (!grid_barrier(a.bar, a.flag)) return;
+    if (!grid_barrier(a.bar, a.flag, 3)) return;
     // X <- X + X E, and AX <- AX + (AX) E = A X for the next iteration (not
     // needed after the last one)
     const bool last = grid_total(pE, true) <= REFINE_TOL;
     gemm_tiles_4x8(X, a.E, X, Xn, last ? nullptr : AX, AXn, n, rsm);
-    if (!grid_barrier(a.bar, a.flag)) return;
+    if (!grid_barrier(a.bar, a.flag, 3)) return;
     double* t = X;
     X = Xn;
     Xn = t;

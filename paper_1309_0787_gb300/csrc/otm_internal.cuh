@@ -102,6 +102,15 @@ otm_status gemm_nn_f64(const float* A, int64_t rows, int64_t m, const double* C,
 otm_status dgemm_small(int ta, int tb, int64_t m, int64_t n, int64_t kk, double alpha,
                        const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                        double* C, int64_t ldc, cudaStream_t st);
+// FP32 STGD (Lemma 3) as one cooperative launch over many SMs (sgd_grid.cu):
+// the minibatch split over up to one CTA per SM, partial products reduced
+// through L2 by the owners of the columns; same arguments and results as
+// otm_sgd_run.  Applicable for k <= 128 and 16 <= b <= 32 x (SM count).
+bool sgd_grid_applicable(int64_t k, int64_t b);
+otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
+                        int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
+                        int64_t b, double beta0, double theta, double alpha0,
+                        int64_t snapshot_every, float* V_snap, cudaStream_t st);
 size_t orth_workspace(int64_t m);
 // Device-side failure flags: *dflag is set to 1 (QR: non-finite Gram matrix) or
 // 2 (eigensolver: non-finite eigenvalues) or 3 (eigensolver: the refinement's grid

@@ -22,6 +22,8 @@
 // cluster, adds the Gram and mean terms and broadcasts the new columns into
 // every CTA's next-V buffer together with their means a_A, a_B.  Two cluster
 // barriers per step; no global memory traffic besides the samples.
+#include <atomic>
+
 #include <cooperative_groups.h>
 
 #include "otm_internal.cuh"
@@ -556,10 +558,23 @@ int pick_cluster(int k, bool sym, int64_t b, int max_cl, int* nbuf) {
   return 0;
 }
 
+// Which form runs otm_sgd_step / otm_sgd_run: 0 = chosen by size, 1 = the
+// cluster form (this file), 2 = the grid form (sgd_grid.cu).
+std::atomic<int> g_sgd_form{0};
+// The grid form is chosen for minibatches of at least this many samples.
+constexpr int64_t GRID_AUTO_MIN_B = 256;
+
 otm_status run(float* V, const float* YA, const float* YB, const float* YC, int64_t n, int64_t k,
                const double* ybar3, const int32_t* perm, int64_t epochs, int64_t b,
                double beta0, double theta, double alpha0, int64_t snapshot_every, float* V_snap,
                cudaStream_t st) {
+  const int form = g_sgd_form.load();
+  const bool grid_ok = sgd_grid_applicable(k, b);
+  if (form == 2 && !grid_ok)
+    return set_error(OTM_EINVAL, "sgd: the grid form needs k <= 128 and 16 <= b <= 32 x SMs");
+  if (form == 2 || (form == 0 && grid_ok && b >= GRID_AUTO_MIN_B))
+    return sgd_grid_run(V, YA, YB, YC, n, k, ybar3, perm, epochs, b, beta0, theta, alpha0,
+                        snapshot_every, V_snap, st);
   SgdArgs args;
   const bool sym = (YA == YB) && (YB == YC);
   args.YA = YA;
@@ -628,6 +643,13 @@ otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float*
   OTM_REQUIRE(b >= 1, "otm_sgd_step: b must be >= 1");
   return run(V, YA, YB, YC, b, k, ybar3, nullptr, 1, b, beta, theta, alpha0, 0, nullptr,
              as_stream(stream));
+}
+
+otm_status otm_sgd_set_form(int form) {
+  clear_error();
+  OTM_REQUIRE(form >= 0 && form <= 2, "otm_sgd_set_form: form must be 0, 1 or 2");
+  g_sgd_form.store(form);
+  return OTM_OK;
 }
 
 otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,

@@ -82,6 +82,7 @@ _SIGS = {
     "otm_project": [_P, c_vp, c_i64, c_vp, c_vp, c_vp],
     "otm_column_mean": [c_vp, c_i64, c_i64, c_vp, c_vp],
     "otm_sgd_step": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_f64, c_f64, c_f64, c_vp],
+    "otm_sgd_set_form": [ctypes.c_int],
     "otm_sgd_run": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64, c_i64, c_f64,
                     c_f64, c_f64, c_i64, c_vp, c_vp],
     "otm_quantize_samples": [c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp, c_vp],
@@ -335,6 +336,14 @@ def column_mean(Y):
     yb = torch.empty(k, dtype=torch.float64, device=Y.device)
     _check(_lib.otm_column_mean(_ptr(Y), n, k, _ptr(yb), _stream()))
     return yb
+
+
+SGD_FORM_AUTO, SGD_FORM_CLUSTER, SGD_FORM_GRID = 0, 1, 2
+
+
+def sgd_set_form(form: int) -> None:
+    """otm_sgd_set_form: which FP32 kernel sgd_step / sgd_run use (process-wide)."""
+    _check(_lib.otm_sgd_set_form(int(form)))
 
 
 def sgd_step(V, YA, YB, YC, ybar3, theta: float, beta: float, alpha0: float):
