@@ -29,9 +29,13 @@ namespace otm {
 namespace {
 
 constexpr int GT = 256;       // threads per CTA
-constexpr int G_SAMPLES = 8;  // target samples per CTA per step
+constexpr int G_SAMPLES = 6;  // target samples per CTA per step
 constexpr int G_SMAX = 32;    // at most this many samples per CTA per step
 constexpr int G_KMAX = 128;
+constexpr int G_MAXGRID = 160;  // CTAs at most (the owners' sums load G / 8 partials at once)
+constexpr int VQ = (G_KMAX * (G_KMAX + 4) / 4 + GT - 1) / GT;  // float4 of V per thread
+constexpr int YQ = (3 * G_SMAX * (G_KMAX / 4) + GT - 1) / GT;  // float4 of samples per thread
+constexpr int RQ = G_MAXGRID / 8;                              // partials per thread
 
 struct GridArgs {
   const float* YA;
@@ -49,13 +53,14 @@ struct GridArgs {
   int* flag;      // barrier time-out
   int64_t n, b, spe, total_steps, snapshot_every;
   int k, S;
+  int vec;        // sample rows are 16-byte aligned (k % 4 == 0, aligned bases)
   double beta0;
   float c1, c2, c3, kappa;
 };
 
 struct GLayout {
   int kp, ld, nview, S;
-  size_t off_v, off_y, off_b, off_p, off_yb, off_a, off_red, off_h, off_g, total;
+  size_t off_v, off_y, off_b, off_p, off_yb, off_a, off_red, off_h, total;
 };
 
 // Shared memory (floats).  Rows of V and of the samples have stride ld, an odd
@@ -74,9 +79,8 @@ __host__ __device__ inline GLayout g_layout(int k, bool sym, int S) {
   L.off_p = f;   f += (size_t)S * L.kp;             // A_A o A_B [t][i]
   L.off_yb = f;  f += 3 * (size_t)L.ld;             // ybar_A, ybar_B, ybar_C
   L.off_a = f;   f += 2 * (size_t)L.kp;             // a_A, a_B
-  L.off_red = f; f += 8 * (size_t)L.kp;             // 8 partial rows
+  L.off_red = f; f += 16 * (size_t)L.kp;            // 8 partial rows of Y_C^T B^T, 8 of G_gram
   L.off_h = f;   f += (size_t)L.kp;                 // (v_i . v_j)^2 of an owned column i
-  L.off_g = f;   f += (size_t)L.kp;                 // G_data column
   L.total = f;
   return L;
 }
@@ -99,6 +103,7 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_red[2][GT / 32];
   __shared__ float s_si;
+  __shared__ int s_row[2][G_SMAX];  // sample rows of this CTA, by step parity (-1: none)
   const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k;
   const GLayout L = g_layout(k, SYM, a.S);
@@ -113,8 +118,8 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
   float* aA = sm + L.off_a;
   float* aB = aA + kp;
   float* red = sm + L.off_red;
+  float* redg = red + 8 * kp;
   float* hs = sm + L.off_h;
-  float* gd = sm + L.off_g;
   // on a barrier time-out the owned columns of V are set to NaN (the caller
   // sees the failure in the result) and the CTA returns
   auto fail = [&]() {
@@ -142,6 +147,17 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
       a.means[(size_t)q * kp + i] = 0.f;
     }
   }
+  // row of sample t of this CTA in step s (-1 outside the minibatch or for an
+  // index outside [0, n), which reads as a zero sample)
+  auto row_of = [&](int64_t s, int t) -> int {
+    if (s >= a.total_steps) return -1;
+    const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
+    const int64_t beff = min(a.b, a.n - pos0), p = (int64_t)g * S + t;
+    if (p >= beff) return -1;
+    const int64_t row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
+    return (row >= 0 && row < a.n) ? (int)row : -1;
+  };
+  if (tid < S) s_row[0][tid] = row_of(0, tid);
   __syncthreads();
   for (int i = warp; i < kp; i += GT / 32) {  // a_A, a_B of the initial V
     float x = 0.f, y = 0.f;
@@ -164,31 +180,59 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     const int par = (int)(s & 1);
     float* Vnext = a.Vg + (size_t)(par ^ 1) * kp * ld;
     float* Mnext = a.means + (size_t)(par ^ 1) * 2 * kp;
-    if (s > 0) {  // the iterate the owners wrote in the previous step
-      const float4* src = reinterpret_cast<const float4*>(a.Vg + (size_t)par * kp * ld);
-      float4* dst = reinterpret_cast<float4*>(Vs);
-      for (int idx = tid; idx < kp * ld / 4; idx += GT) dst[idx] = __ldcg(src + idx);
-      const float* msrc = a.means + (size_t)par * 2 * kp;
-      for (int idx = tid; idx < 2 * kp; idx += GT) aA[idx] = __ldcg(msrc + idx);  // aA, aB
-    }
-    const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
+    const int64_t pos0 = (s % a.spe) * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
-    const int64_t t0 = (int64_t)g * S;
-    const int ns = (int)max((int64_t)0, min((int64_t)S, beff - t0));
-    // this CTA's samples (rows outside the minibatch, or an index outside
-    // [0, n), read as zero samples)
-    for (int idx = tid; idx < L.nview * S * kq; idx += GT) {
-      const int v = idx / (S * kq), rem = idx % (S * kq), t = rem / kq, r = 4 * (rem % kq);
-      const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
-      int64_t row = -1;
-      if (t < ns) row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + t0 + t] : pos0 + t0 + t;
-      float y4[4] = {0.f, 0.f, 0.f, 0.f};
-      if (row >= 0 && row < a.n) {
+    // the iterate the owners wrote in the previous step, its means and this
+    // CTA's samples: every load is issued before any store
+    {
+      float4 vv[VQ], yy[YQ];
+      const int nv4 = s > 0 ? kp * ld / 4 : 0;
+      const float4* src = reinterpret_cast<const float4*>(a.Vg + (size_t)par * kp * ld);
 #pragma unroll
-        for (int z = 0; z < 4; ++z) y4[z] = r + z < k ? __ldg(Yg + row * k + r + z) : 0.f;
+      for (int c = 0; c < VQ; ++c) {
+        const int idx = tid + c * GT;
+        if (idx < nv4) vv[c] = __ldcg(src + idx);
       }
-      *reinterpret_cast<float4*>(Ys + ((size_t)v * S + t) * ld + r) =
-          make_float4(y4[0], y4[1], y4[2], y4[3]);
+      const int ny = L.nview * S * kq;
+#pragma unroll
+      for (int c = 0; c < YQ; ++c) {
+        const int idx = tid + c * GT;
+        yy[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < ny) {
+          const int v = idx / (S * kq), rem = idx % (S * kq), t = rem / kq, r = 4 * (rem % kq);
+          const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+          const int row = s_row[par][t];
+          if (row >= 0) {
+            const float* src_y = Yg + (int64_t)row * k + r;
+            if (a.vec) {
+              yy[c] = __ldg(reinterpret_cast<const float4*>(src_y));
+            } else {
+              yy[c].x = __ldg(src_y);
+              yy[c].y = r + 1 < k ? __ldg(src_y + 1) : 0.f;
+              yy[c].z = r + 2 < k ? __ldg(src_y + 2) : 0.f;
+              yy[c].w = r + 3 < k ? __ldg(src_y + 3) : 0.f;
+            }
+          }
+        }
+      }
+      if (s > 0) {
+        const float* msrc = a.means + (size_t)par * 2 * kp;
+        for (int idx = tid; idx < 2 * kp; idx += GT) aA[idx] = __ldcg(msrc + idx);  // aA, aB
+      }
+      float4* dst = reinterpret_cast<float4*>(Vs);
+#pragma unroll
+      for (int c = 0; c < VQ; ++c) {
+        const int idx = tid + c * GT;
+        if (idx < nv4) dst[idx] = vv[c];
+      }
+#pragma unroll
+      for (int c = 0; c < YQ; ++c) {
+        const int idx = tid + c * GT;
+        if (idx < ny) {
+          const int v = idx / (S * kq), rem = idx % (S * kq), t = rem / kq, r = 4 * (rem % kq);
+          *reinterpret_cast<float4*>(Ys + ((size_t)v * S + t) * ld + r) = yy[c];
+        }
+      }
     }
     __syncthreads();
 
@@ -256,60 +300,64 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     const float beta = (float)a.beta0 / sqrtf((float)(s + 1));
     const float inv_b = 1.f / (float)beff;
     for (int i = g; i < k; i += G) {
-      {
-        const int h = tid >> 5, q = tid & 31;  // 8 groups of partials x 32 float4 columns
-        for (int q4 = q; q4 < kq; q4 += 32) {
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-          for (int gg = h; gg < G; gg += 8) {
-            const float4 p = __ldcg(
-                reinterpret_cast<const float4*>(a.part + ((size_t)gg * kp + i) * ld + 4 * q4));
-            acc.x += p.x;
-            acc.y += p.y;
-            acc.z += p.z;
-            acc.w += p.w;
-          }
-          *reinterpret_cast<float4*>(red + h * kp + 4 * q4) = acc;
-        }
-        if (warp == 0) {
-          float v = 0.f;
-          for (int gg = lane; gg < G; gg += 32) v += __ldcg(a.spart + (size_t)gg * kp + i);
+      // the partials of column i are loaded first; the Gram term, which needs
+      // only V, is computed while they are in flight
+      const int h = tid >> 5, q = tid & 31;  // 8 groups x 32 float4 columns (kq <= 32)
+      float4 p[RQ];
+      if (q < kq) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) s_si = v;
-        }
-        for (int j = tid; j < kp; j += GT) {  // (v_i . v_j)^2
-          const float* vi = Vs + (size_t)i * ld;
-          const float* vj = Vs + (size_t)j * ld;
-          float h0 = 0.f, h1 = 0.f;
-          for (int r = 0; r < kp; r += 8) {
-            h0 = dot4(*reinterpret_cast<const float4*>(vi + r),
-                      *reinterpret_cast<const float4*>(vj + r), h0);
-            if (r + 4 < kp)
-              h1 = dot4(*reinterpret_cast<const float4*>(vi + r + 4),
-                        *reinterpret_cast<const float4*>(vj + r + 4), h1);
-          }
-          const float hv = h0 + h1;
-          hs[j] = hv * hv;
+        for (int c = 0; c < RQ; ++c) {
+          const int gg = h + 8 * c;
+          p[c] = gg < G ? __ldcg(reinterpret_cast<const float4*>(
+                              a.part + ((size_t)gg * kp + i) * ld + 4 * q))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
-      __syncthreads();
-      for (int r = tid; r < kp; r += GT) {
-        float t = 0.f;
+      float sv[G_MAXGRID / 32];
+      if (warp == 0) {
 #pragma unroll
-        for (int h = 0; h < 8; ++h) t += red[h * kp + r];
-        gd[r] = t;
+        for (int c = 0; c < G_MAXGRID / 32; ++c) {
+          const int gg = lane + 32 * c;
+          sv[c] = gg < G ? __ldcg(a.spart + (size_t)gg * kp + i) : 0.f;
+        }
+      }
+      for (int j = tid; j < kp; j += GT) {  // (v_i . v_j)^2
+        const float* vi = Vs + (size_t)i * ld;
+        const float* vj = Vs + (size_t)j * ld;
+        float h0 = 0.f, h1 = 0.f;
+        for (int r = 0; r < kp; r += 8) {
+          h0 = dot4(*reinterpret_cast<const float4*>(vi + r),
+                    *reinterpret_cast<const float4*>(vj + r), h0);
+          if (r + 4 < kp)
+            h1 = dot4(*reinterpret_cast<const float4*>(vi + r + 4),
+                      *reinterpret_cast<const float4*>(vj + r + 4), h1);
+        }
+        const float hv = h0 + h1;
+        hs[j] = hv * hv;
       }
       __syncthreads();
-      // Gram term: 8 groups of components j, 4 coordinates per thread
-      {
-        const int h = tid >> 5, q = tid & 31;
-        for (int q4 = q; q4 < kq; q4 += 32) {
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int j = h; j < k; j += 8)
-            fma4(acc, hs[j], *reinterpret_cast<const float4*>(Vs + (size_t)j * ld + 4 * q4));
-          *reinterpret_cast<float4*>(red + h * kp + 4 * q4) = acc;
+      if (q < kq) {  // Gram term, components j = h (mod 8)
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = h; j < k; j += 8)
+          fma4(acc, hs[j], *reinterpret_cast<const float4*>(Vs + (size_t)j * ld + 4 * q));
+        *reinterpret_cast<float4*>(redg + h * kp + 4 * q) = acc;
+        float4 t = p[0];
+#pragma unroll
+        for (int c = 1; c < RQ; ++c) {
+          t.x += p[c].x;
+          t.y += p[c].y;
+          t.z += p[c].z;
+          t.w += p[c].w;
         }
+        *reinterpret_cast<float4*>(red + h * kp + 4 * q) = t;
+      }
+      if (warp == 0) {
+        float v = sv[0];
+#pragma unroll
+        for (int c = 1; c < G_MAXGRID / 32; ++c) v += sv[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_si = v;
       }
       __syncthreads();
       {
@@ -317,10 +365,13 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
         const float mean_term = a.c3 * aA[i] * aB[i] - a.c2 * si * inv_b;
         float x = 0.f, y = 0.f;
         for (int r = tid; r < kp; r += GT) {
-          float gg = 0.f;
+          float gg = 0.f, gdr = 0.f;
 #pragma unroll
-          for (int h = 0; h < 8; ++h) gg += red[h * kp + r];
-          const float gdata = gd[r] * inv_b + ybC[r] * mean_term;
+          for (int hh = 0; hh < 8; ++hh) {
+            gg += redg[hh * kp + r];
+            gdr += red[hh * kp + r];
+          }
+          const float gdata = gdr * inv_b + ybC[r] * mean_term;
           const float v = r < k ? Vs[(size_t)i * ld + r] - beta * (a.kappa * gg - gdata) : 0.f;
           Vnext[(size_t)i * ld + r] = v;
           x = fmaf(v, ybA[r], x);
@@ -354,6 +405,7 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
         __syncthreads();  // shared scratch is reused by the next owned column
       }
     }
+    if (tid < S) s_row[par ^ 1][tid] = row_of(s + 1, tid);
     if (!grid_barrier(a.bar, a.flag, 1)) {
       fail();
       return;
@@ -389,7 +441,8 @@ otm_status launch_grid(GridArgs& args, int G, cudaStream_t st) {
 }  // namespace
 
 bool sgd_grid_applicable(int64_t k, int64_t b) {
-  return k >= 1 && k <= G_KMAX && b >= 2 * G_SAMPLES && b <= (int64_t)G_SMAX * grid_sms();
+  const int64_t gmax = std::min<int64_t>(grid_sms(), G_MAXGRID);
+  return k >= 1 && k <= G_KMAX && b >= 16 && b <= (int64_t)G_SMAX * gmax;
 }
 
 otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
@@ -399,7 +452,7 @@ otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float*
   if (!sgd_grid_applicable(k, b)) return set_error(OTM_EINVAL, "sgd grid form: k or b out of range");
   const bool sym = (YA == YB) && (YB == YC);
   const int64_t want = (b + G_SAMPLES - 1) / G_SAMPLES;
-  const int G = (int)std::min<int64_t>(grid_sms(), want);
+  const int G = (int)std::min<int64_t>(std::min<int64_t>(grid_sms(), G_MAXGRID), want);
   const int S = (int)((b + G - 1) / G);
   if (S > G_SMAX) return set_error(OTM_EINVAL, "sgd grid form: minibatch too large for the grid");
   GridArgs args;
@@ -417,6 +470,8 @@ otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float*
   args.snapshot_every = snapshot_every;
   args.k = (int)k;
   args.S = S;
+  args.vec = (k % 4 == 0) && ((reinterpret_cast<uintptr_t>(YA) | reinterpret_cast<uintptr_t>(YB) |
+                                reinterpret_cast<uintptr_t>(YC)) & 15) == 0;
   args.beta0 = beta0;
   args.c1 = (float)((alpha0 + 1.0) * (alpha0 + 2.0) / 2.0);
   args.c2 = (float)(alpha0 * (alpha0 + 1.0) / 2.0);
