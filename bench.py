@@ -43,10 +43,10 @@ CFG = dict(workload="mmsb_4x5000_k100_b1024_fp32", n_per=5000, k=100, alpha_i=0.
            q=0.005, oversample=20, power_iters=2, b=1024, epochs=20, beta0=1e-2, theta=1.0,
            alpha0=1.0, seed=0)
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
-# DRAM bytes (read + write) per launch of sgd_cluster_kernel on this workload, from one ncu
+# DRAM bytes (read + write) per launch of the STGD kernel on this workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command; to be reset to None
 # whenever the kernel changes
-SGD_CLUSTER_TRAFFIC = 6541056
+SGD_KERNEL_TRAFFIC = 6989568
 
 
 def make_inputs(cfg, rank=0):
@@ -305,10 +305,10 @@ def run_gpu(args, rank, world, local_rank):
                          "unwhiten": statistics.mean(step_ms) - statistics.mean(pre_ms)
                          - statistics.mean(sgd_ms),
                          "wall_per_step": 1e3 * wall / args.steps},
-        "roofline": {"kernel": "sgd_cluster_kernel (one launch = all 100 STGD steps)",
+        "roofline": {"kernel": "sgd_grid_kernel (one cooperative launch = all 100 STGD steps)",
                      "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
-                     "traffic": SGD_CLUSTER_TRAFFIC,
+                     "traffic": SGD_KERNEL_TRAFFIC,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "algorithmic_flops_per_launch": flops},
         "e2e": {"value": world * samples * n_e2e / e2e_t, "unit": UNIT,
