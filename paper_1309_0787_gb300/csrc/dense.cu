@@ -20,7 +20,8 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // C (m x p, FP64) (+)= alpha * A^T B.  A: rows x m, B: rows x p (float32).
-// Block: 64 x 64 output tile, 256 threads (4 x 4 each).  Rows are split over
+// Block: 64 x 64 output tile, 256 threads (4 x 4 consecutive rows and columns
+// each, read from shared memory as float4).  Rows are split over
 // gridDim.z (at least 256 rows per block); a block sums its rows in FP32 and
 // adds its tile to C in FP64.
 // ---------------------------------------------------------------------------
@@ -51,8 +52,8 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
                                                       int64_t rows_per_split,
                                                       const int* __restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ float As[TN_R][TN_T];
-  __shared__ float Bs[TN_R][TN_T];
+  __shared__ __align__(16) float As[TN_R][TN_T];
+  __shared__ __align__(16) float Bs[TN_R][TN_T];
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * TN_T, j0 = (int64_t)blockIdx.y * TN_T;
@@ -78,12 +79,9 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
     }
 #pragma unroll 8
     for (int rr = 0; rr < TN_R; ++rr) {
-      float a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[rr][ty + 16 * q];
-        b[q] = Bs[rr][tx + 16 * q];
-      }
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[rr][4 * ty]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[rr][4 * tx]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -95,7 +93,7 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const float* __restrict__ 
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
-      const int64_t i = i0 + ty + 16 * x, j = j0 + tx + 16 * y;
+      const int64_t i = i0 + 4 * ty + x, j = j0 + 4 * tx + y;
       if (i < m && j < p) atomicAdd(&C[i * p + j], alpha * (double)acc[x][y]);
     }
 }
@@ -271,17 +269,18 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 // Cholesky of G (+ shift) and the inverse of its upper factor R = L^T.
 // One CTA of 1024 threads, FP32 in shared memory (n <= 160), right-looking
 // and blocked by 8 columns, with L^{-1} built in the same sweep.  Block J:
-//  (a) one warp factors the 8 x 8 diagonal block L_JJ in registers and
-//      inverts it (lane c solves for column c of L_JJ^{-1});
-//  (b) the block row J of X = L^{-1} is finished: X_J = L_JJ^{-1} B_J, where
-//      B starts as the identity and has taken the updates of earlier blocks;
-//  (c) the panel below, L_{>J,J} = A_{>J,J} L_JJ^{-T} (row by row, in parallel
-//      with (b));
+//  (a) one warp factors the 8 x 8 diagonal block L_JJ in registers;
+//  (b) the block row J of X = L^{-1} is finished: X_J = L_JJ^{-1} B_J by
+//      forward substitution, where B starts as the identity and has taken the
+//      updates of earlier blocks;
+//  (c) the panel below, L_{>J,J} = A_{>J,J} L_JJ^{-T} (row by row by forward
+//      substitution, in parallel with (b));
 //  (d) every row i below takes one rank-8 update over its columns 0..i: the
 //      trailing Cholesky matrix (columns past the block) and B (columns up to
 //      the block), B_{i,:} -= L_{i,J} X_J.
-// Three barriers per block column.  Output Rinv (n x n, float32, row-major,
-// upper triangular) so that Q = A Rinv.
+// Look-ahead: while warps 1.. run (d), warp 0 updates and factors the next
+// diagonal block, so two barriers per block column.  Output Rinv (n x n,
+// float32, row-major, upper triangular) so that Q = A Rinv.
 // shift_scale > 0 adds shift_scale * n * u * trace(G) to the diagonal
 // (u = 2^-24), which keeps the factorisation positive definite for Gram
 // matrices of ill-conditioned A (shifted Cholesky-QR: Fukaya, Kannan,
@@ -295,7 +294,7 @@ __global__ void vec_tn_kernel(const double* __restrict__ u, const float* __restr
 constexpr int CH_T = 1024, CH_B = 8;
 
 __host__ __device__ inline size_t chol_smem_floats(int n) {
-  return (size_t)2 * n * (n | 1) + (size_t)(CH_B + 1) * n + 2 * CH_B * CH_B;
+  return (size_t)2 * n * (n | 1) + (size_t)(CH_B + 1) * n + CH_B * CH_B;
 }
 
 __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict__ G, int n,
@@ -335,7 +334,6 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
   float* rdg = X + n * ldn;      // n reciprocal pivots 1 / L_jj
   float* PT = rdg + n;           // 8 x n: the current panel, transposed
   float* Ljj = PT + CH_B * n;    // 8 x 8 diagonal block
-  float* Dinv = Ljj + CH_B * CH_B;  // 8 x 8 its inverse
   __shared__ float s_shift, s_floor;
   __shared__ int s_bad;
   if (warp == 0) {
@@ -362,112 +360,127 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(const double* __restrict
   }
   __syncthreads();
 
-  for (int J = 0; J < nblk; ++J) {
-    const int j0 = J * CH_B, jb = min(CH_B, n - j0), je = j0 + jb;
-    // (a) factor and invert the diagonal block in warp 0: lane r holds row j0 + r
-    if (warp == 0) {
-      float a[CH_B];
+  // (a) factor the diagonal block starting at j0 in warp 0: lane r holds row
+  // j0 + r in a[] (already updated); writes L, Ljj and the reciprocal pivots
+  auto factor_diag = [&](int j0, float (&a)[CH_B]) {
+    const int jb = min(CH_B, n - j0);
 #pragma unroll
-      for (int c = 0; c < CH_B; ++c)
-        a[c] = (lane < jb && c <= lane) ? L[(j0 + lane) * ldn + j0 + c] : 0.f;
-#pragma unroll
-      for (int c = 0; c < CH_B; ++c) {
-        if (c < jb) {
-          float d = __shfl_sync(0xffffffffu, a[c], c);
-          if (!isfinite(d)) {
-            if (lane == 0) s_bad = 1;
-            d = 1.f;
-          }
-          const float pinv = rsqrtf(fmaxf(d, s_floor));
-          if (lane == c) {
-            a[c] = fmaxf(d, s_floor) * pinv;
-            rdg[j0 + c] = pinv;
-          }
-          if (lane > c) a[c] *= pinv;
-#pragma unroll
-          for (int kk = c + 1; kk < CH_B; ++kk) {
-            const float lkc = __shfl_sync(0xffffffffu, a[c], kk);
-            if (kk < jb && lane >= kk && lane < jb) a[kk] -= a[c] * lkc;
-          }
+    for (int c = 0; c < CH_B; ++c) {
+      if (c < jb) {
+        float d = __shfl_sync(0xffffffffu, a[c], c);
+        if (!isfinite(d)) {
+          if (lane == 0) s_bad = 1;
+          d = 1.f;
         }
-      }
-      if (lane < CH_B) {
-#pragma unroll
-        for (int c = 0; c < CH_B; ++c) {
-          const float v = (lane < jb && c <= lane) ? a[c] : 0.f;
-          Ljj[lane * CH_B + c] = v;
-          if (lane < jb && c <= lane) L[(j0 + lane) * ldn + j0 + c] = v;
+        const float pinv = rsqrtf(fmaxf(d, s_floor));
+        if (lane == c) {
+          a[c] = fmaxf(d, s_floor) * pinv;
+          rdg[j0 + c] = pinv;
         }
-      }
-      __syncwarp();
-      // column c of L_JJ^{-1} by forward substitution
-      if (lane < CH_B) {
-        const int c = lane;
-        float y[CH_B];
+        if (lane > c) a[c] *= pinv;
 #pragma unroll
-        for (int r = 0; r < CH_B; ++r) {
-          float v = r == c ? 1.f : 0.f;
-#pragma unroll
-          for (int m = 0; m < r; ++m) v = fmaf(-Ljj[r * CH_B + m], y[m], v);
-          y[r] = (r < jb && r >= c) ? v * rdg[j0 + (r < jb ? r : 0)] : 0.f;
+        for (int kk = c + 1; kk < CH_B; ++kk) {
+          const float lkc = __shfl_sync(0xffffffffu, a[c], kk);
+          if (kk < jb && lane >= kk && lane < jb) a[kk] -= a[c] * lkc;
         }
-#pragma unroll
-        for (int r = 0; r < CH_B; ++r) Dinv[r * CH_B + c] = y[r];
       }
     }
-    __syncthreads();
-    // (b) block row J of X: threads [0, je) take one column each
+    if (lane < CH_B) {
+#pragma unroll
+      for (int c = 0; c < CH_B; ++c) {
+        const float v = (lane < jb && c <= lane) ? a[c] : 0.f;
+        Ljj[lane * CH_B + c] = v;
+        if (lane < jb && c <= lane) L[(j0 + lane) * ldn + j0 + c] = v;
+      }
+    }
+  };
+  if (warp == 0) {
+    float a[CH_B];
+#pragma unroll
+    for (int c = 0; c < CH_B; ++c) a[c] = (lane < min(CH_B, n) && c <= lane) ? L[lane * ldn + c] : 0.f;
+    factor_diag(0, a);
+  }
+  __syncthreads();
+
+  for (int J = 0; J < nblk; ++J) {
+    const int j0 = J * CH_B, jb = min(CH_B, n - j0), je = j0 + jb;
+    // (b) block row J of X = L_JJ^{-1} B_J by forward substitution: threads
+    // [0, je) take one column each
     if (tid < je) {
       const int c = tid;
-      float bcol[CH_B];
-#pragma unroll
-      for (int m = 0; m < CH_B; ++m) bcol[m] = m < jb ? X[(j0 + m) * ldn + c] : 0.f;
+      float x[CH_B];
 #pragma unroll
       for (int r = 0; r < CH_B; ++r) {
         if (r < jb) {
-          float v = 0.f;
+          float v = X[(j0 + r) * ldn + c];
 #pragma unroll
-          for (int m = 0; m <= r; ++m) v = fmaf(Dinv[r * CH_B + m], bcol[m], v);
-          X[(j0 + r) * ldn + c] = v;
+          for (int m = 0; m < r; ++m) v = fmaf(-Ljj[r * CH_B + m], x[m], v);
+          x[r] = v * rdg[j0 + r];
         }
       }
+#pragma unroll
+      for (int r = 0; r < CH_B; ++r)
+        if (r < jb) X[(j0 + r) * ldn + c] = x[r];
     }
-    // (c) panel rows i >= je: threads [CH_T/2, ...) take one row each
+    // (c) panel rows i >= je, l L_JJ^T = a by forward substitution: threads
+    // [CH_T/2, ...) take one row each
     {
       const int i = je + (tid - CH_T / 2);
       if (tid >= CH_T / 2 && i < n) {
-        float arow[CH_B];
-#pragma unroll
-        for (int m = 0; m < CH_B; ++m) arow[m] = m < jb ? L[i * ldn + j0 + m] : 0.f;
+        float l[CH_B];
 #pragma unroll
         for (int c = 0; c < CH_B; ++c) {
-          float v = 0.f;
+          float v = c < jb ? L[i * ldn + j0 + c] : 0.f;
 #pragma unroll
-          for (int m = 0; m <= c; ++m) v = fmaf(arow[m], Dinv[c * CH_B + m], v);
-          if (c < jb) L[i * ldn + j0 + c] = v;
-          PT[c * n + i] = c < jb ? v : 0.f;
+          for (int m = 0; m < c; ++m) v = fmaf(-l[m], Ljj[c * CH_B + m], v);
+          l[c] = c < jb ? v * rdg[j0 + c] : 0.f;
+          if (c < jb) L[i * ldn + j0 + c] = l[c];
+          PT[c * n + i] = l[c];
         }
       }
     }
     __syncthreads();
     // (d) rank-8 update of rows i >= je over columns 0..i: B for columns < je,
-    // the trailing Cholesky matrix for columns je..i
-    for (int i = je + warp; i < n; i += NW) {
-      float li[CH_B];
+    // the trailing Cholesky matrix for columns je..i.  Look-ahead: warp 0
+    // updates the next diagonal block (rows and columns je .. je + 7) and
+    // factors it at once; warps 1.. update everything else.
+    const int je2 = min(je + CH_B, n);
+    if (warp == 0) {
+      if (je < n) {
+        float a[CH_B];
+        const int i = je + lane;
 #pragma unroll
-      for (int m = 0; m < CH_B; ++m) li[m] = PT[m * n + i];
-      for (int c = lane; c <= i; c += 32) {
-        if (c < je) {
-          float acc = X[i * ldn + c];
+        for (int c = 0; c < CH_B; ++c) {
+          float acc = 0.f;
+          if (i < je2 && c <= lane) {
+            acc = L[i * ldn + je + c];
 #pragma unroll
-          for (int m = 0; m < CH_B; ++m)
-            if (m < jb) acc = fmaf(-li[m], X[(j0 + m) * ldn + c], acc);
-          X[i * ldn + c] = acc;
-        } else {
-          float acc = L[i * ldn + c];
+            for (int m = 0; m < CH_B; ++m) acc = fmaf(-PT[m * n + i], PT[m * n + je + c], acc);
+          }
+          a[c] = acc;
+        }
+        factor_diag(je, a);
+      }
+    } else {
+      for (int i = je + warp - 1; i < n; i += NW - 1) {
+        float li[CH_B];
 #pragma unroll
-          for (int m = 0; m < CH_B; ++m) acc = fmaf(-li[m], PT[m * n + c], acc);
-          L[i * ldn + c] = acc;
+        for (int m = 0; m < CH_B; ++m) li[m] = PT[m * n + i];
+        // columns je .. min(i, je2 - 1) of rows in the next diagonal block are warp 0's
+        const int c_skip_hi = i < je2 ? i : je - 1;
+        for (int c = lane; c <= i; c += 32) {
+          if (c < je) {
+            float acc = X[i * ldn + c];
+#pragma unroll
+            for (int m = 0; m < CH_B; ++m)
+              if (m < jb) acc = fmaf(-li[m], X[(j0 + m) * ldn + c], acc);
+            X[i * ldn + c] = acc;
+          } else if (c > c_skip_hi || c >= je2) {
+            float acc = L[i * ldn + c];
+#pragma unroll
+            for (int m = 0; m < CH_B; ++m) acc = fmaf(-li[m], PT[m * n + c], acc);
+            L[i * ldn + c] = acc;
+          }
         }
       }
     }
@@ -1296,11 +1309,11 @@ otm_status gemm_tn_f64acc(const float* A, const float* B, int64_t rows, int64_t 
                           const int* skip) {
   if (!accumulate) OTM_CHECK_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * m * p, st));
   if (rows == 0 || m == 0 || p == 0) return OTM_OK;
-  // about two blocks per SM, but at least 256 rows per block: every block adds
+  // about two blocks per SM, but at least 128 rows per block: every block adds
   // its tile to C with FP64 atomics, so fewer, longer splits mean less contention
   const int64_t tiles = ((m + TN_T - 1) / TN_T) * ((p + TN_T - 1) / TN_T);
   int64_t splits = (2 * num_sms() + tiles - 1) / tiles;
-  const int64_t max_splits = (rows + 255) / 256;
+  const int64_t max_splits = (rows + 127) / 128;
   splits = splits < 1 ? 1 : (splits > max_splits ? max_splits : splits);
   int64_t rps = (rows + splits - 1) / splits;
   rps = (rps + TN_R - 1) / TN_R * TN_R;
