@@ -116,8 +116,9 @@ size_t orth_workspace(int64_t m);
 // 2 (eigensolver: non-finite eigenvalues) or 3 (eigensolver: the refinement's grid
 // barrier timed out); callers zero it and check it once.
 // passes: Cholesky-QR passes (pass 0 shifted, pass 1 plain, passes 2-3 only while
-// the basis is not yet orthonormal to 1e-5); 2 suffices for the intermediate
-// bases of a power iteration, whose span is all that matters.
+// the basis is not yet orthonormal to 1e-5); the one shifted pass suffices for
+// the intermediate bases of a power iteration, whose span is all that matters
+// (it leaves a well-conditioned, not an orthonormal, basis).
 otm_status orthonormalize(float* A, int64_t rows, int64_t m, Workspace& ws, cudaStream_t st,
                           int* dflag, int passes = 4);
 size_t syev_workspace(int64_t n);

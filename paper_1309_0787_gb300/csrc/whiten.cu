@@ -118,15 +118,16 @@ otm_status range_finder(const Op& op, int64_t d, const float* S, int64_t k, int6
   if (!O || !Om || !ev || !evec || !Cw32)
     return set_error(OTM_EINVAL, "whiten: workspace too small");
   const size_t mark = ws.used;
-  // intermediate bases need only be well conditioned (two passes); the last
+  // intermediate bases need only be well conditioned -- the next product
+  // depends on their span alone -- so one shifted Cholesky-QR pass; the last
   // one is orthonormalised fully
   OTM_TRY(op.apply(S, kt, Q, st));
-  OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2, power_iters > 0 ? 2 : 4));
+  OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2, power_iters > 0 ? 1 : 4));
   ws.used = mark;
   for (int it = 0; it < power_iters; ++it) {
     OTM_TRY(op.apply(Q, kt, O, st));
     OTM_CHECK_CUDA(cudaMemcpyAsync(Q, O, sizeof(float) * d * kt, cudaMemcpyDeviceToDevice, st));
-    OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2, it + 1 < power_iters ? 2 : 4));
+    OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2, it + 1 < power_iters ? 1 : 4));
     ws.used = mark;
   }
   OTM_TRY(op.apply(Q, kt, O, st));
@@ -327,14 +328,14 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
 
   // 1. rank-k randomised SVD of Pairs(C,B) ~ U_C diag(sigma) V_B^T
   OTM_TRY(pairs_apply_ws(G_XC, G_XB, S_pairs, kt, Yc, tmp, st));
-  OTM_TRY(orthonormalize(Yc, nc, kt, w, st, flags + 2, power_iters > 0 ? 2 : 4));
+  OTM_TRY(orthonormalize(Yc, nc, kt, w, st, flags + 2, power_iters > 0 ? 1 : 4));
   w.used = mark;
   for (int it = 0; it < power_iters; ++it) {
     OTM_TRY(pairs_apply_ws(G_XB, G_XC, Yc, kt, Zb, tmp, st));
-    OTM_TRY(orthonormalize(Zb, nb, kt, w, st, flags + 2, 2));
+    OTM_TRY(orthonormalize(Zb, nb, kt, w, st, flags + 2, 1));
     w.used = mark;
     OTM_TRY(pairs_apply_ws(G_XC, G_XB, Zb, kt, Yc, tmp, st));
-    OTM_TRY(orthonormalize(Yc, nc, kt, w, st, flags + 2, it + 1 < power_iters ? 2 : 4));
+    OTM_TRY(orthonormalize(Yc, nc, kt, w, st, flags + 2, it + 1 < power_iters ? 1 : 4));
     w.used = mark;
   }
   OTM_TRY(pairs_apply_ws(G_XB, G_XC, Yc, kt, Zb, tmp, st));  // B^T = Pairs(B,C) Q
