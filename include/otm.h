@@ -351,9 +351,10 @@ typedef struct otm_batch_plan {
   int32_t precision;
   int32_t max_k;          /* largest k <= 128 */
   int32_t grid_clusters;  /* clusters in the persistent grid (k <= 128) */
-  int32_t nitems_wide;    /* chains with 128 < k <= 256 (second launch, 16-CTA clusters) */
+  int32_t nitems_wide;    /* chains with 128 < k <= 256 (second launch) */
   int32_t grid_clusters_wide;
   int32_t max_k_wide;
+  int32_t cluster_wide;   /* CTAs per chain with k > 128: 8 or 16, by the same trial */
   int64_t smem_bytes;
   void* ws;
   size_t ws_bytes;
@@ -371,7 +372,8 @@ typedef struct otm_batch_plan {
  *
  * otm_sgd_batched_launch -- one persistent launch running every chain with
  * k <= 128 (and, if the plan has any, a second one for 128 < k <= 256, whose
- * chains use 16-CTA clusters): as many clusters as fit on the GPU take chains
+ * chains use 8- or 16-CTA clusters and keep their FP32 master rows in the
+ * workspace instead of shared memory): as many clusters as fit on the GPU take chains
  * from the work list until it is empty.  Asynchronous and free of host synchronisation, so it can
  * be captured in a CUDA graph.  otm_sgd_batched_check reads the plan's
  * timeout flag (synchronises; OTM_ETIMEOUT if a tensor-core wait expired).

@@ -91,6 +91,7 @@ __host__ __device__ inline int own_cols(int k, int cl) {
 struct TcLayout {
   int N, nv, NS, es, KPc, CR, CRb, CBn, CBh;
   bool dbl;
+  bool vmg;  // the FP32 master rows live in global scratch (KPc = 256: shared memory is short)
   size_t y_view, y_stage, off_v[2], off_vq, off_yb, off_b[2], off_h, off_f;
   size_t vm, ybA, ybB, ybC, aA, aB, vsc, bsc, amax, spw, red, ssc, nfloat;
   size_t total;
@@ -110,6 +111,7 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   L.NS = NS;
   L.es = es;
   L.dbl = dbl;
+  L.vmg = KPc > 128;
   L.CR = KP * es / 16;
   L.CRb = KP * 2 / 16;
   L.CBn = N * es / 16;
@@ -136,7 +138,7 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   if (L.off_yb + yb_bytes > end) end = L.off_yb + yb_bytes;
   L.off_f = al128(end);
   size_t f = 0;
-  L.vm = f;   f += (size_t)N * KP;
+  L.vm = f;   f += L.vmg ? 0 : (size_t)N * KP;
   L.ybA = f;  f += KP;
   L.ybB = f;  f += KP;
   L.ybC = f;  f += KP;
@@ -215,7 +217,8 @@ __device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, ui
 // mbarriers are set up by the caller.  Ends with a cluster barrier so that the
 // caller may reuse shared memory afterwards.
 template <bool FP8, bool SYM>
-__device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool dbl) {
+__device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool dbl,
+                         float* vm_cta) {
   constexpr int ES = FP8 ? 1 : 2;
   constexpr int KSTEP = FP8 ? 32 : 16;            // K of one MMA
   constexpr uint32_t FMT = FP8 ? 0u : 1u;         // E4M3 / BF16
@@ -235,7 +238,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   const bool active = own_lo < k;
   const int nch = N / 16;
   float* F = reinterpret_cast<float*>(smem + L.off_f);
-  float* Vm = F + L.vm;
+  float* Vm = L.vmg ? vm_cta : F + L.vm;  // owned rows [N][KPc]
   float* ybA = F + L.ybA;
   float* ybB = F + L.ybB;
   float* ybC = F + L.ybC;
@@ -824,14 +827,16 @@ __device__ __forceinline__ void tc_teardown(TcCtx& cx) {
 }
 
 template <bool FP8, bool SYM>
-__global__ void __launch_bounds__(TC_THREADS, 1) sgd_tc_kernel(TcArgs a, int NS, int dbl) {
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    sgd_tc_kernel(TcArgs a, int NS, int dbl, float* vms, int vm_stride) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar[NMBAR];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   TcCtx cx;
   tc_setup(cx, mbar, &tmem_base, &s_abort);
-  tc_chain<FP8, SYM>(a, smem, cx, NS, dbl != 0);
+  tc_chain<FP8, SYM>(a, smem, cx, NS, dbl != 0,
+                     vms ? vms + (size_t)blockIdx.x * vm_stride : nullptr);
   tc_teardown(cx);
 }
 
@@ -841,7 +846,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sgd_tc_kernel(TcArgs a, int NS,
 template <bool FP8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     sgd_tc_batched_kernel(const TcArgs* __restrict__ items, int nitems, int* counter, int NS,
-                          int dbl) {
+                          int dbl, float* vms, int vm_stride) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar[NMBAR];
   __shared__ uint32_t tmem_base;
@@ -859,7 +864,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int it = s_item;
     if (it >= nitems) break;
     const TcArgs a = items[it];
-    tc_chain<FP8, true>(a, smem, cx, NS, dbl != 0);
+    tc_chain<FP8, true>(a, smem, cx, NS, dbl != 0,
+                        vms ? vms + (size_t)blockIdx.x * vm_stride : nullptr);
   }
   tc_teardown(cx);
 }
@@ -909,6 +915,7 @@ struct TcPlan {
   int CL, N, NS;
   bool dbl;
   size_t smem;
+  bool vmg;  // needs global scratch for the FP32 master rows: N x 256 floats per CTA
 };
 
 // The first configuration (deepest pipeline, double-buffered V image first)
@@ -928,7 +935,7 @@ bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
     if (dbl && CL == 1) continue;
     const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, o[1], dbl, KPc);
     if (L.total <= lim) {
-      *out = {CL, N, o[1], dbl, L.total};
+      *out = {CL, N, o[1], dbl, L.total, L.vmg};
       return true;
     }
   }
@@ -946,7 +953,7 @@ bool tc_plan_single(int k, bool sym, bool fp8, TcPlan* out) {
 }
 
 template <bool FP8, bool SYM>
-otm_status launch_tc(const TcArgs& args, const TcPlan& P, cudaStream_t st) {
+otm_status launch_tc(const TcArgs& args, const TcPlan& P, cudaStream_t st, float* vms) {
   auto kern = sgd_tc_kernel<FP8, SYM>;
   OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
   if (P.CL > 8)
@@ -963,7 +970,8 @@ otm_status launch_tc(const TcArgs& args, const TcPlan& P, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args, P.NS, (int)P.dbl));
+  float* vm = P.vmg ? vms : nullptr;
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args, P.NS, (int)P.dbl, vm, P.N * 256));
   count_launch();
   return OTM_OK;
 }
@@ -988,7 +996,7 @@ cudaLaunchConfig_t batched_cfg(const TcPlan& P, int nclusters, cudaStream_t st,
 // prepare call, so that the launch itself issues stream work only)
 template <bool FP8>
 otm_status launch_batched(const TcPlan& P, const TcArgs* items, int nitems, int* counter,
-                          int nclusters, cudaStream_t st, bool configure) {
+                          int nclusters, cudaStream_t st, bool configure, float* vms) {
   auto kern = sgd_tc_batched_kernel<FP8>;
   if (configure) {
     OTM_CHECK_CUDA(
@@ -999,7 +1007,9 @@ otm_status launch_batched(const TcPlan& P, const TcArgs* items, int nitems, int*
   if (nitems == 0) return OTM_OK;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = batched_cfg(P, nclusters, st, attr);
-  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, items, nitems, counter, P.NS, (int)P.dbl));
+  float* vm = P.vmg ? vms : nullptr;
+  OTM_CHECK_CUDA(
+      cudaLaunchKernelEx(&cfg, kern, items, nitems, counter, P.NS, (int)P.dbl, vm, P.N * 256));
   count_launch();
   return OTM_OK;
 }
@@ -1059,7 +1069,10 @@ otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precis
   return OTM_OK;
 }
 
-size_t otm_sgd_run_lp_workspace(void) { return 256; }
+// The error flag (256 bytes), then, for k > 128, the FP32 master rows of every
+// CTA of the chain's cluster (at most 16 CTAs x 32 rows x 256 floats).
+constexpr size_t LP_VM_FLOATS = (size_t)16 * 32 * 256;
+size_t otm_sgd_run_lp_workspace(void) { return 256 + LP_VM_FLOATS * sizeof(float); }
 
 otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* YC,
                           const float* sA, const float* sB, const float* sC, int64_t n, int64_t k,
@@ -1112,10 +1125,11 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   args.c3 = (float)(alpha0 * alpha0);
   args.kappa = (float)(0.5 * (1.0 + theta));
   otm_status s_;
+  float* vms = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + 256);
   if (fp8)
-    s_ = sym ? launch_tc<true, true>(args, P, st) : launch_tc<true, false>(args, P, st);
+    s_ = sym ? launch_tc<true, true>(args, P, st, vms) : launch_tc<true, false>(args, P, st, vms);
   else
-    s_ = sym ? launch_tc<false, true>(args, P, st) : launch_tc<false, false>(args, P, st);
+    s_ = sym ? launch_tc<false, true>(args, P, st, vms) : launch_tc<false, false>(args, P, st, vms);
   if (s_ != OTM_OK) return s_;
   int h = 0;
   OTM_CHECK_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1124,10 +1138,36 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   return OTM_OK;
 }
 
+// Batched workspace: header, work list, trial work list, trial V matrices, and
+// the FP32 master rows of the k > 128 group (N x 256 floats for each of at most
+// WIDE_CTAS CTAs).
+constexpr int WIDE_CTAS = 256;
+constexpr size_t WIDE_VM_FLOATS = (size_t)WIDE_CTAS * 32 * 256;
+
+static_assert(WIDE_CTAS > 0, "wide scratch");
+struct BatchedWs {
+  int* hdr;
+  TcArgs* dev_items;
+  TcArgs* trial_items;
+  float* scratchV;
+  float* vm_wide;
+};
+
+static BatchedWs batched_ws(void* ws, size_t ws_bytes, int64_t nitems) {
+  Workspace w(ws, ws_bytes);
+  BatchedWs b;
+  b.hdr = w.take<int>(64);
+  b.dev_items = w.take<TcArgs>(nitems);
+  b.trial_items = w.take<TcArgs>(nitems);
+  b.scratchV = w.take<float>((size_t)std::min<int64_t>(nitems, 512) * TC_KMAX * TC_KMAX);
+  b.vm_wide = w.take<float>(WIDE_VM_FLOATS);
+  return b;
+}
+
 size_t otm_sgd_batched_workspace(int64_t nitems) {
   WorkspaceSize w;
   w.add<int>(64).add<TcArgs>(nitems).add<TcArgs>(nitems).add<float>(
-      (size_t)std::min<int64_t>(nitems, 512) * TC_KMAX * TC_KMAX);
+      (size_t)std::min<int64_t>(nitems, 512) * TC_KMAX * TC_KMAX).add<float>(WIDE_VM_FLOATS);
   return w.bytes();
 }
 
@@ -1182,7 +1222,7 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
               "otm_sgd_batched_prepare: workspace too small (need %zu bytes)",
               otm_sgd_batched_workspace(nitems));
   // two groups, each its own persistent launch: k <= 128 (autotuned cluster) first,
-  // then k > 128 (256 padded coordinates, 16-CTA clusters); longest chains first
+  // then k > 128 (256 padded coordinates, 8- or 16-CTA clusters); longest chains first
   // within a group, so that the tail of each persistent loop holds short ones
   std::vector<int> order(nitems);
   for (int i = 0; i < nitems; ++i) order[i] = i;
@@ -1204,17 +1244,24 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
     }
   }
   const int n_narrow = nitems - n_wide;
-  Workspace w(ws, ws_bytes);
-  int* hdr = w.take<int>(64);
-  TcArgs* dev_items = w.take<TcArgs>(nitems);
-  TcArgs* trial_items = w.take<TcArgs>(nitems);
-  float* scratchV = w.take<float>((size_t)std::min(nitems, 512) * TC_KMAX * TC_KMAX);
+  const BatchedWs bw = batched_ws(ws, ws_bytes, nitems);
+  int* hdr = bw.hdr;
+  TcArgs* dev_items = bw.dev_items;
+  TcArgs* trial_items = bw.trial_items;
+  float* scratchV = bw.scratchV;
   cudaStream_t st = as_stream(stream);
   for (int i = 0; i < nitems; ++i) sorted[i].err = hdr + 1;
-  TcPlan Pw{};
-  if (n_wide > 0)
-    OTM_REQUIRE(tc_plan(max_k_wide, true, fp8, 16, &Pw),
-                "otm_sgd_batched_prepare: k=%d does not fit on chip", max_k_wide);
+  // the k > 128 group: 8- or 16-CTA clusters, whichever fits (and, if both do,
+  // is faster on a trial run below)
+  std::vector<int> cands_w;
+  for (int c : {8, 16}) {
+    TcPlan Pc;
+    if (n_wide > 0 && (c - 1) * own_cols(max_k_wide, c) < round16(max_k_wide) &&
+        tc_plan(max_k_wide, true, fp8, c, &Pc))
+      cands_w.push_back(c);
+  }
+  OTM_REQUIRE(n_wide == 0 || !cands_w.empty(), "otm_sgd_batched_prepare: k=%d does not fit on chip",
+              max_k_wide);
   OTM_CHECK_CUDA(cudaMemcpyAsync(dev_items, sorted.data(), sizeof(TcArgs) * nitems,
                                  cudaMemcpyHostToDevice, st));
   OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 64 * sizeof(int), st));
@@ -1263,15 +1310,15 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
         tc_plan(max_k, true, fp8, c, &Pc);
         float tot = 0.f;
         // set attributes (zero-item launch) before the occupancy query
-        otm_status s1 = fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true)
-                            : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true);
+        otm_status s1 = fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr)
+                            : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr);
         if (s1 != OTM_OK) return s1;
         const int ncl = std::min(batched_clusters(fp8, Pc), ntrial);
         for (int rep = 0; rep < 2; ++rep) {
           OTM_CHECK_CUDA(cudaMemsetAsync(hdr + 8, 0, sizeof(int), st));
           OTM_CHECK_CUDA(cudaEventRecord(e0, st));
-          otm_status s2 = fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false)
-                              : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false);
+          otm_status s2 = fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, nullptr)
+                              : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, nullptr);
           if (s2 != OTM_OK) return s2;
           OTM_CHECK_CUDA(cudaEventRecord(e1, st));
           OTM_CHECK_CUDA(cudaEventSynchronize(e1));
@@ -1290,16 +1337,78 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
       g_tune_cache[key] = chosen;
     }
   }
-  TcPlan Pch{};
+  // the k > 128 group: cluster size by the same trial (cached likewise)
+  int chosen_w = 0;
+  if (n_wide > 0) {
+    chosen_w = cands_w.back();
+    const long long key = (1LL << 62) | ((long long)precision << 40) |
+                          ((long long)max_k_wide << 24) | n_wide;
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto f = g_tune_cache.find(key);
+      if (f != g_tune_cache.end()) {
+        chosen_w = f->second;
+        cached = true;
+      }
+    }
+    if (!cached && cands_w.size() > 1) {
+      const int ntrial = std::min(n_wide, 512);
+      std::vector<TcArgs> trial(sorted.begin() + n_narrow, sorted.begin() + n_narrow + ntrial);
+      for (int i = 0; i < ntrial; ++i) {
+        trial[i].V = scratchV + (size_t)i * TC_KMAX * TC_KMAX;
+        trial[i].total_steps = std::min<int64_t>(trial[i].total_steps, 4);
+      }
+      OTM_CHECK_CUDA(cudaMemsetAsync(scratchV, 0, sizeof(float) * ntrial * TC_KMAX * TC_KMAX, st));
+      OTM_CHECK_CUDA(cudaMemcpyAsync(trial_items, trial.data(), sizeof(TcArgs) * ntrial,
+                                     cudaMemcpyHostToDevice, st));
+      cudaEvent_t e0, e1;
+      OTM_CHECK_CUDA(cudaEventCreate(&e0));
+      OTM_CHECK_CUDA(cudaEventCreate(&e1));
+      float best = 3.0e38f;
+      for (int c : cands_w) {
+        TcPlan Pc;
+        tc_plan(max_k_wide, true, fp8, c, &Pc);
+        otm_status s1 = fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr)
+                            : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr);
+        if (s1 != OTM_OK) return s1;
+        const int ncl = std::min(std::min(batched_clusters(fp8, Pc), WIDE_CTAS / c), ntrial);
+        float tot = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+          OTM_CHECK_CUDA(cudaMemsetAsync(hdr + 8, 0, sizeof(int), st));
+          OTM_CHECK_CUDA(cudaEventRecord(e0, st));
+          otm_status s2 =
+              fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vm_wide)
+                  : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vm_wide);
+          if (s2 != OTM_OK) return s2;
+          OTM_CHECK_CUDA(cudaEventRecord(e1, st));
+          OTM_CHECK_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          OTM_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep == 1) tot = ms;
+        }
+        if (tot < best) {
+          best = tot;
+          chosen_w = c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = chosen_w;
+  }
+  TcPlan Pch{}, Pw{};
   if (n_narrow > 0) {
     OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pch), "otm_sgd_batched_prepare: no plan");
-    otm_status s3 = fp8 ? launch_batched<true>(Pch, dev_items, 0, hdr, 1, st, true)
-                        : launch_batched<false>(Pch, dev_items, 0, hdr, 1, st, true);
+    otm_status s3 = fp8 ? launch_batched<true>(Pch, dev_items, 0, hdr, 1, st, true, nullptr)
+                        : launch_batched<false>(Pch, dev_items, 0, hdr, 1, st, true, nullptr);
     if (s3 != OTM_OK) return s3;
   }
   if (n_wide > 0) {
-    otm_status s4 = fp8 ? launch_batched<true>(Pw, dev_items, 0, hdr, 1, st, true)
-                        : launch_batched<false>(Pw, dev_items, 0, hdr, 1, st, true);
+    OTM_REQUIRE(tc_plan(max_k_wide, true, fp8, chosen_w, &Pw), "otm_sgd_batched_prepare: no plan");
+    otm_status s4 = fp8 ? launch_batched<true>(Pw, dev_items, 0, hdr, 1, st, true, nullptr)
+                        : launch_batched<false>(Pw, dev_items, 0, hdr, 1, st, true, nullptr);
     if (s4 != OTM_OK) return s4;
   }
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -1311,7 +1420,9 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   plan->grid_clusters = n_narrow > 0 ? std::min(batched_clusters(fp8, Pch), n_narrow) : 0;
   plan->nitems_wide = n_wide;
   plan->max_k_wide = max_k_wide;
-  plan->grid_clusters_wide = n_wide > 0 ? std::min(batched_clusters(fp8, Pw), n_wide) : 0;
+  plan->cluster_wide = chosen_w;
+  plan->grid_clusters_wide =
+      n_wide > 0 ? std::min(std::min(batched_clusters(fp8, Pw), WIDE_CTAS / chosen_w), n_wide) : 0;
   plan->ws = ws;
   plan->ws_bytes = ws_bytes;
   return OTM_OK;
@@ -1324,9 +1435,9 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
               "otm_sgd_batched_launch: invalid plan");
   const int n_wide = plan->nitems_wide, n_narrow = plan->nitems - n_wide;
   cudaStream_t st = as_stream(stream);
-  Workspace w(plan->ws, plan->ws_bytes);
-  int* hdr = w.take<int>(64);
-  TcArgs* dev_items = w.take<TcArgs>(plan->nitems);
+  const BatchedWs bw = batched_ws(plan->ws, plan->ws_bytes, plan->nitems);
+  int* hdr = bw.hdr;
+  TcArgs* dev_items = bw.dev_items;
   OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 3 * sizeof(int), st));  // counters and the flag
   const bool fp8 = plan->precision == OTM_PREC_FP8;
   if (n_narrow > 0) {
@@ -1335,18 +1446,20 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
                     (int64_t)P.smem == plan->smem_bytes && plan->grid_clusters >= 1,
                 "otm_sgd_batched_launch: plan does not match this library");
     OTM_TRY(fp8 ? launch_batched<true>(P, dev_items, n_narrow, hdr, plan->grid_clusters, st,
-                                       false)
+                                       false, nullptr)
                 : launch_batched<false>(P, dev_items, n_narrow, hdr, plan->grid_clusters, st,
-                                        false));
+                                        false, nullptr));
   }
   if (n_wide > 0) {
     TcPlan P;
-    OTM_REQUIRE(tc_plan(plan->max_k_wide, true, fp8, 16, &P) && plan->grid_clusters_wide >= 1,
+    OTM_REQUIRE(tc_plan(plan->max_k_wide, true, fp8, plan->cluster_wide, &P) &&
+                    plan->grid_clusters_wide >= 1 &&
+                    plan->grid_clusters_wide * plan->cluster_wide <= WIDE_CTAS,
                 "otm_sgd_batched_launch: plan does not match this library");
     OTM_TRY(fp8 ? launch_batched<true>(P, dev_items + n_narrow, n_wide, hdr + 2,
-                                       plan->grid_clusters_wide, st, false)
+                                       plan->grid_clusters_wide, st, false, bw.vm_wide)
                 : launch_batched<false>(P, dev_items + n_narrow, n_wide, hdr + 2,
-                                        plan->grid_clusters_wide, st, false));
+                                        plan->grid_clusters_wide, st, false, bw.vm_wide));
   }
   return OTM_OK;
 }

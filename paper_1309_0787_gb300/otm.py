@@ -45,7 +45,8 @@ class OtmBatchPlan(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_k", ctypes.c_int32),
                 ("grid_clusters", ctypes.c_int32), ("nitems_wide", ctypes.c_int32),
                 ("grid_clusters_wide", ctypes.c_int32), ("max_k_wide", ctypes.c_int32),
-                ("smem_bytes", c_i64), ("ws", c_vp), ("ws_bytes", c_sz)]
+                ("cluster_wide", ctypes.c_int32), ("smem_bytes", c_i64), ("ws", c_vp),
+                ("ws_bytes", c_sz)]
 
 
 class OtmMlp(ctypes.Structure):
