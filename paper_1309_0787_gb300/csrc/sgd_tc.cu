@@ -126,15 +126,18 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   const size_t b_bytes = (size_t)TILE * N * es;
   // the B images, the H image and the ybar image (16 rows: ybar_A, ybar_B, zeros;
   // rebuilt at the start of every step) share one region: they are live at
-  // different times of a step
+  // different times of a step.  With a single sample stage nothing is loaded
+  // into it between the last tile of a step and the first of the next, which
+  // is when the H and ybar images are live, so they use the stage instead.
+  const size_t h_bytes = (size_t)KP * N * 2;
+  const size_t yb_bytes = (size_t)16 * KP * 2;
+  const bool in_stage = NS == 1 && h_bytes <= L.y_stage && yb_bytes <= L.y_stage;
   L.off_b[0] = al128(L.off_vq + vq_bytes);
   L.off_b[1] = NS >= 4 ? L.off_b[0] + b_bytes : L.off_b[0];
-  L.off_yb = L.off_b[0];
-  L.off_h = L.off_b[0];  // the H image reuses both B images (free by then)
+  L.off_yb = in_stage ? 0 : L.off_b[0];
+  L.off_h = in_stage ? 0 : L.off_b[0];  // the H image reuses both B images (free by then)
   size_t end = L.off_b[1] + b_bytes;
-  const size_t h_bytes = (size_t)KP * N * 2;
   if (L.off_h + h_bytes > end) end = L.off_h + h_bytes;
-  const size_t yb_bytes = (size_t)16 * KP * 2;
   if (L.off_yb + yb_bytes > end) end = L.off_yb + yb_bytes;
   L.off_f = al128(end);
   size_t f = 0;
@@ -1125,6 +1128,8 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   args.c3 = (float)(alpha0 * alpha0);
   args.kappa = (float)(0.5 * (1.0 + theta));
   otm_status s_;
+  OTM_REQUIRE(!P.vmg || (size_t)P.CL * P.N * 256 <= LP_VM_FLOATS,
+              "otm_sgd_run_lp: master-row scratch too small for this plan");
   float* vms = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + 256);
   if (fp8)
     s_ = sym ? launch_tc<true, true>(args, P, st, vms) : launch_tc<true, false>(args, P, st, vms);
@@ -1142,7 +1147,12 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
 // the FP32 master rows of the k > 128 group (N x 256 floats for each of at most
 // WIDE_CTAS CTAs).
 constexpr int WIDE_CTAS = 256;
-constexpr size_t WIDE_VM_FLOATS = (size_t)WIDE_CTAS * 32 * 256;
+constexpr size_t WIDE_VM_FLOATS = (size_t)WIDE_CTAS * 64 * 256;
+
+// Clusters of plan P whose FP32 master rows fit the wide scratch.
+static int wide_clusters_cap(const TcPlan& P) {
+  return (int)(WIDE_VM_FLOATS / ((size_t)P.CL * P.N * 256));
+}
 
 static_assert(WIDE_CTAS > 0, "wide scratch");
 struct BatchedWs {
@@ -1222,7 +1232,7 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
               "otm_sgd_batched_prepare: workspace too small (need %zu bytes)",
               otm_sgd_batched_workspace(nitems));
   // two groups, each its own persistent launch: k <= 128 (autotuned cluster) first,
-  // then k > 128 (256 padded coordinates, 8- or 16-CTA clusters); longest chains first
+  // then k > 128 (256 padded coordinates, 4- to 16-CTA clusters); longest chains first
   // within a group, so that the tail of each persistent loop holds short ones
   std::vector<int> order(nitems);
   for (int i = 0; i < nitems; ++i) order[i] = i;
@@ -1251,10 +1261,10 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   float* scratchV = bw.scratchV;
   cudaStream_t st = as_stream(stream);
   for (int i = 0; i < nitems; ++i) sorted[i].err = hdr + 1;
-  // the k > 128 group: 8- or 16-CTA clusters, whichever fits (and, if both do,
-  // is faster on a trial run below)
+  // the k > 128 group: 4-, 8- or 16-CTA clusters, whichever fit, the fastest on
+  // a trial run below
   std::vector<int> cands_w;
-  for (int c : {8, 16}) {
+  for (int c : {4, 8, 16}) {
     TcPlan Pc;
     if (n_wide > 0 && (c - 1) * own_cols(max_k_wide, c) < round16(max_k_wide) &&
         tc_plan(max_k_wide, true, fp8, c, &Pc))
@@ -1372,7 +1382,7 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
         otm_status s1 = fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr)
                             : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr);
         if (s1 != OTM_OK) return s1;
-        const int ncl = std::min(std::min(batched_clusters(fp8, Pc), WIDE_CTAS / c), ntrial);
+        const int ncl = std::min(std::min(batched_clusters(fp8, Pc), wide_clusters_cap(Pc)), ntrial);
         float tot = 0.f;
         for (int rep = 0; rep < 2; ++rep) {
           OTM_CHECK_CUDA(cudaMemsetAsync(hdr + 8, 0, sizeof(int), st));
@@ -1422,7 +1432,7 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   plan->max_k_wide = max_k_wide;
   plan->cluster_wide = chosen_w;
   plan->grid_clusters_wide =
-      n_wide > 0 ? std::min(std::min(batched_clusters(fp8, Pw), WIDE_CTAS / chosen_w), n_wide) : 0;
+      n_wide > 0 ? std::min(std::min(batched_clusters(fp8, Pw), wide_clusters_cap(Pw)), n_wide) : 0;
   plan->ws = ws;
   plan->ws_bytes = ws_bytes;
   return OTM_OK;
@@ -1454,7 +1464,7 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
     TcPlan P;
     OTM_REQUIRE(tc_plan(plan->max_k_wide, true, fp8, plan->cluster_wide, &P) &&
                     plan->grid_clusters_wide >= 1 &&
-                    plan->grid_clusters_wide * plan->cluster_wide <= WIDE_CTAS,
+                    plan->grid_clusters_wide <= wide_clusters_cap(P),
                 "otm_sgd_batched_launch: plan does not match this library");
     OTM_TRY(fp8 ? launch_batched<true>(P, dev_items + n_narrow, n_wide, hdr + 2,
                                        plan->grid_clusters_wide, st, false, bw.vm_wide)
