@@ -1409,17 +1409,20 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
     g_tune_cache[key] = chosen_w;
   }
   TcPlan Pch{}, Pw{};
-  if (n_narrow > 0) {
+  if (n_narrow > 0)
     OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pch), "otm_sgd_batched_prepare: no plan");
-    otm_status s3 = fp8 ? launch_batched<true>(Pch, dev_items, 0, hdr, 1, st, true, nullptr)
-                        : launch_batched<false>(Pch, dev_items, 0, hdr, 1, st, true, nullptr);
-    if (s3 != OTM_OK) return s3;
-  }
-  if (n_wide > 0) {
+  if (n_wide > 0)
     OTM_REQUIRE(tc_plan(max_k_wide, true, fp8, chosen_w, &Pw), "otm_sgd_batched_prepare: no plan");
-    otm_status s4 = fp8 ? launch_batched<true>(Pw, dev_items, 0, hdr, 1, st, true, nullptr)
-                        : launch_batched<false>(Pw, dev_items, 0, hdr, 1, st, true, nullptr);
-    if (s4 != OTM_OK) return s4;
+  {
+    // both launches run the same kernel: its attributes must admit both plans
+    TcPlan Pmax = n_narrow > 0 ? Pch : Pw;
+    if (n_narrow > 0 && n_wide > 0) {
+      Pmax.smem = std::max(Pch.smem, Pw.smem);
+      Pmax.CL = std::max(Pch.CL, Pw.CL);
+    }
+    otm_status s3 = fp8 ? launch_batched<true>(Pmax, dev_items, 0, hdr, 1, st, true, nullptr)
+                        : launch_batched<false>(Pmax, dev_items, 0, hdr, 1, st, true, nullptr);
+    if (s3 != OTM_OK) return s3;
   }
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
   plan->nitems = nitems;

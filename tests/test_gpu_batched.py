@@ -103,6 +103,23 @@ def test_batched_two_groups_beyond_128(otm):
             assert rel(to_np(p["V"][r]), to_np(Vs)) < 1e-2
 
 
+def test_batched_two_groups_forced_cluster(otm):
+    """Both groups with the narrow cluster size given (1): the kernel's launch
+    attributes must admit the larger of the two plans' shared memory."""
+    prec = otm.PREC_BF16
+    specs = [(81, 128, 1024, 256, 1, 2), (82, 256, 1024, 512, 1, 1), (83, 16, 512, 64, 2, 2)]
+    probs = [_problem(otm, s, k, n, b, e, r, 5e-3, prec) for s, k, n, b, e, r in specs]
+    batch = otm.SgdBatch(probs, prec, cluster=1)
+    assert batch.cluster == 1 and batch.plan.nitems_wide == 1
+    batch.launch()
+    batch.check()
+    for p in probs:
+        for r in range(p["V0"].shape[0]):
+            Vs = _single(otm, p, r, prec)
+            torch.cuda.synchronize()
+            assert rel(to_np(p["V"][r]), to_np(Vs)) < 1e-2
+
+
 def test_batched_tracks_oracle(otm):
     """Batched BF16 chains against the FP64 oracle run of Lemma 3."""
     prec = otm.PREC_BF16
