@@ -243,10 +243,14 @@ otm_status otm_column_mean(const float* Y, int64_t n, int64_t k, double* ybar, v
  * V: k x k column-major float32, updated in place.  YA, YB, YC: b x k float32
  * (may alias each other; equal pointers select the symmetric fast path).
  * ybar3: 3 x k doubles (ybA, ybB, ybC).  1 <= k <= 128, b >= 1.
+ * ws: otm_sgd_workspace(k, b) bytes of scratch for the grid form of the
+ * kernel (see otm_sgd_set_form), or NULL / too small, in which case the
+ * cluster form runs (forcing the grid form then returns OTM_EINVAL).
  */
+size_t otm_sgd_workspace(int64_t k, int64_t b);
 otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float* YC,
                         int64_t b, int64_t k, const double* ybar3, double theta, double beta,
-                        double alpha0, void* stream);
+                        double alpha0, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * otm_sgd_run -- the whole STGD loop in ONE persistent launch (V stays
@@ -256,29 +260,32 @@ otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float*
  * YA, YB, YC: n x k (may alias); perm: epochs x n int32 (NULL = identity order
  * every epoch).  If snapshot_every > 0, V after every snapshot_every-th step
  * is written to V_snap[(t / snapshot_every - 1) * k * k ...] (caller sizes it
- * for floor(total_steps / snapshot_every) matrices).
+ * for floor(total_steps / snapshot_every) matrices).  ws / ws_bytes: as for
+ * otm_sgd_step (otm_sgd_workspace(k, b) bytes).
  */
 otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
                        int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
                        int64_t b, double beta0, double theta, double alpha0,
-                       int64_t snapshot_every, float* V_snap, void* stream);
+                       int64_t snapshot_every, float* V_snap, void* ws, size_t ws_bytes,
+                       void* stream);
 
 /*
  * otm_sgd_set_form -- which FP32 kernel otm_sgd_step / otm_sgd_run use, for
  * the whole process (no paper counterpart; a performance choice with the same
  * results up to FP32 summation order):
  *   0 (default)  chosen by size: the grid form for k <= 128 and
- *                256 <= b <= 32 x (SM count), the cluster form otherwise;
+ *                256 <= b <= 32 x (SM count) when the caller passed its
+ *                workspace, the cluster form otherwise;
  *   1            the cluster form: one thread-block cluster of up to 16 CTAs
  *                keeps V in shared memory, the minibatch split over its CTAs,
  *                partial products reduced through distributed shared memory;
  *   2            the grid form: one cooperative launch of up to one CTA per SM,
  *                the minibatch split over all of them, partial products
  *                reduced through L2 by the owners of the columns, two grid
- *                barriers per step (k <= 128, 16 <= b <= 32 x SMs, else
- *                OTM_EINVAL from the run).  It takes its scratch with
- *                cudaMallocAsync on the stream and frees it after the launch.
- *                On a barrier time-out the affected columns of V are NaN.
+ *                barriers per step (k <= 128, 16 <= b <= 32 x SMs and a
+ *                workspace of otm_sgd_workspace(k, b) bytes, else OTM_EINVAL
+ *                from the run).  On a barrier time-out the affected columns
+ *                of V are NaN.
  * OTM_EINVAL for another value.
  */
 otm_status otm_sgd_set_form(int form);

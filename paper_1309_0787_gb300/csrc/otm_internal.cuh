@@ -107,10 +107,12 @@ otm_status dgemm_small(int ta, int tb, int64_t m, int64_t n, int64_t kk, double 
 // through L2 by the owners of the columns; same arguments and results as
 // otm_sgd_run.  Applicable for k <= 128 and 16 <= b <= 32 x (SM count).
 bool sgd_grid_applicable(int64_t k, int64_t b);
+size_t sgd_grid_workspace(int64_t k, int64_t b);  // 0 where not applicable
 otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
                         int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
                         int64_t b, double beta0, double theta, double alpha0,
-                        int64_t snapshot_every, float* V_snap, cudaStream_t st);
+                        int64_t snapshot_every, float* V_snap, void* ws, size_t ws_bytes,
+                        cudaStream_t st);
 size_t orth_workspace(int64_t m);
 // Device-side failure flags: *dflag is set to 1 (QR: non-finite Gram matrix) or
 // 2 (eigensolver: non-finite eigenvalues) or 3 (eigensolver: the refinement's grid

@@ -567,14 +567,16 @@ constexpr int64_t GRID_AUTO_MIN_B = 256;
 otm_status run(float* V, const float* YA, const float* YB, const float* YC, int64_t n, int64_t k,
                const double* ybar3, const int32_t* perm, int64_t epochs, int64_t b,
                double beta0, double theta, double alpha0, int64_t snapshot_every, float* V_snap,
-               cudaStream_t st) {
+               void* ws, size_t ws_bytes, cudaStream_t st) {
   const int form = g_sgd_form.load();
   const bool grid_ok = sgd_grid_applicable(k, b);
   if (form == 2 && !grid_ok)
     return set_error(OTM_EINVAL, "sgd: the grid form needs k <= 128 and 16 <= b <= 32 x SMs");
-  if (form == 2 || (form == 0 && grid_ok && b >= GRID_AUTO_MIN_B))
+  // the auto choice takes the grid form only when the caller gave it its scratch
+  const bool grid_ws_ok = ws && ws_bytes >= sgd_grid_workspace(k, b);
+  if (form == 2 || (form == 0 && grid_ok && grid_ws_ok && b >= GRID_AUTO_MIN_B))
     return sgd_grid_run(V, YA, YB, YC, n, k, ybar3, perm, epochs, b, beta0, theta, alpha0,
-                        snapshot_every, V_snap, st);
+                        snapshot_every, V_snap, ws, ws_bytes, st);
   SgdArgs args;
   const bool sym = (YA == YB) && (YB == YC);
   args.YA = YA;
@@ -634,15 +636,17 @@ using namespace otm;
 
 extern "C" {
 
+size_t otm_sgd_workspace(int64_t k, int64_t b) { return sgd_grid_workspace(k, b); }
+
 otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float* YC, int64_t b,
                         int64_t k, const double* ybar3, double theta, double beta,
-                        double alpha0, void* stream) {
+                        double alpha0, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
   OTM_REQUIRE(V && YA && YB && YC && ybar3, "otm_sgd_step: null pointer");
   OTM_REQUIRE(k >= 1 && k <= KMAX, "otm_sgd_step: k=%lld outside [1, %d]", (long long)k, KMAX);
   OTM_REQUIRE(b >= 1, "otm_sgd_step: b must be >= 1");
-  return run(V, YA, YB, YC, b, k, ybar3, nullptr, 1, b, beta, theta, alpha0, 0, nullptr,
-             as_stream(stream));
+  return run(V, YA, YB, YC, b, k, ybar3, nullptr, 1, b, beta, theta, alpha0, 0, nullptr, ws,
+             ws_bytes, as_stream(stream));
 }
 
 otm_status otm_sgd_set_form(int form) {
@@ -655,7 +659,8 @@ otm_status otm_sgd_set_form(int form) {
 otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
                        int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
                        int64_t b, double beta0, double theta, double alpha0,
-                       int64_t snapshot_every, float* V_snap, void* stream) {
+                       int64_t snapshot_every, float* V_snap, void* ws, size_t ws_bytes,
+                       void* stream) {
   clear_error();
   OTM_REQUIRE(V && YA && YB && YC && ybar3, "otm_sgd_run: null pointer");
   OTM_REQUIRE(k >= 1 && k <= KMAX, "otm_sgd_run: k=%lld outside [1, %d]", (long long)k, KMAX);
@@ -664,7 +669,7 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
   OTM_REQUIRE(snapshot_every == 0 || V_snap, "otm_sgd_run: V_snap required for snapshots");
   if (epochs == 0) return OTM_OK;
   return run(V, YA, YB, YC, n, k, ybar3, perm, epochs, b, beta0, theta, alpha0, snapshot_every,
-             V_snap, as_stream(stream));
+             V_snap, ws, ws_bytes, as_stream(stream));
 }
 
 }  // extern "C"

@@ -440,6 +440,29 @@ otm_status launch_grid(GridArgs& args, int G, cudaStream_t st) {
 
 }  // namespace
 
+// CTAs of the grid form for minibatch b: about G_SAMPLES samples each, at
+// most one per SM.
+static int grid_ctas(int64_t b) {
+  const int64_t want = (b + G_SAMPLES - 1) / G_SAMPLES;
+  return (int)std::min<int64_t>(std::min<int64_t>(grid_sms(), G_MAXGRID), want);
+}
+
+// Scratch of the grid form: the iterate by step parity and its means, the
+// partial products and sums of every CTA, the barrier counter and a flag.
+static WorkspaceSize grid_ws(int64_t k, int64_t b) {
+  const GLayout L = g_layout((int)k, false, 1);  // kp and ld do not depend on the views
+  const int G = grid_ctas(b);
+  WorkspaceSize w;
+  w.add<float>(2 * (size_t)L.kp * L.ld).add<float>(4 * (size_t)L.kp);
+  w.add<float>((size_t)G * L.kp * L.ld).add<float>((size_t)G * L.kp);
+  w.add<unsigned>(1).add<int>(1);
+  return w;
+}
+
+size_t sgd_grid_workspace(int64_t k, int64_t b) {
+  return sgd_grid_applicable(k, b) ? grid_ws(k, b).bytes() : 0;
+}
+
 bool sgd_grid_applicable(int64_t k, int64_t b) {
   const int64_t gmax = std::min<int64_t>(grid_sms(), G_MAXGRID);
   return k >= 1 && k <= G_KMAX && b >= 16 && b <= (int64_t)G_SMAX * gmax;
@@ -448,11 +471,11 @@ bool sgd_grid_applicable(int64_t k, int64_t b) {
 otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
                         int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
                         int64_t b, double beta0, double theta, double alpha0,
-                        int64_t snapshot_every, float* V_snap, cudaStream_t st) {
+                        int64_t snapshot_every, float* V_snap, void* ws_ptr, size_t ws_bytes,
+                        cudaStream_t st) {
   if (!sgd_grid_applicable(k, b)) return set_error(OTM_EINVAL, "sgd grid form: k or b out of range");
   const bool sym = (YA == YB) && (YB == YC);
-  const int64_t want = (b + G_SAMPLES - 1) / G_SAMPLES;
-  const int G = (int)std::min<int64_t>(std::min<int64_t>(grid_sms(), G_MAXGRID), want);
+  const int G = grid_ctas(b);
   const int S = (int)((b + G - 1) / G);
   if (S > G_SMAX) return set_error(OTM_EINVAL, "sgd grid form: minibatch too large for the grid");
   GridArgs args;
@@ -478,25 +501,18 @@ otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float*
   args.c3 = (float)(alpha0 * alpha0);
   args.kappa = (float)(0.5 * (1.0 + theta));
   const GLayout L = g_layout((int)k, sym, S);
-  WorkspaceSize w;
-  w.add<float>(2 * (size_t)L.kp * L.ld).add<float>(4 * (size_t)L.kp);
-  w.add<float>((size_t)G * L.kp * L.ld).add<float>((size_t)G * L.kp);
-  w.add<unsigned>(1).add<int>(1);
-  void* scratch = nullptr;
-  OTM_CHECK_CUDA(cudaMallocAsync(&scratch, w.bytes(), st));
-  Workspace ws(scratch, w.bytes());
+  if (!ws_ptr || ws_bytes < grid_ws(k, b).bytes())
+    return set_error(OTM_EINVAL, "sgd grid form: workspace too small (need %zu bytes)",
+                     grid_ws(k, b).bytes());
+  Workspace ws(ws_ptr, ws_bytes);
   args.Vg = ws.take<float>(2 * (size_t)L.kp * L.ld);
   args.means = ws.take<float>(4 * (size_t)L.kp);
   args.part = ws.take<float>((size_t)G * L.kp * L.ld);
   args.spart = ws.take<float>((size_t)G * L.kp);
   args.bar = ws.take<unsigned>(1);
   args.flag = ws.take<int>(1);
-  otm_status rc = OTM_OK;
-  if (cudaMemsetAsync(args.bar, 0, sizeof(unsigned), st) != cudaSuccess)
-    rc = set_error(OTM_ECUDA, "sgd grid form: memset failed");
-  if (rc == OTM_OK) rc = sym ? launch_grid<true>(args, G, st) : launch_grid<false>(args, G, st);
-  cudaFreeAsync(scratch, st);
-  return rc;
+  OTM_CHECK_CUDA(cudaMemsetAsync(args.bar, 0, sizeof(unsigned), st));
+  return sym ? launch_grid<true>(args, G, st) : launch_grid<false>(args, G, st);
 }
 
 }  // namespace otm

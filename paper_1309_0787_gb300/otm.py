@@ -82,10 +82,12 @@ _SIGS = {
                              c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
     "otm_project": [_P, c_vp, c_i64, c_vp, c_vp, c_vp],
     "otm_column_mean": [c_vp, c_i64, c_i64, c_vp, c_vp],
-    "otm_sgd_step": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_f64, c_f64, c_f64, c_vp],
+    "otm_sgd_step": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_f64, c_f64, c_f64, c_vp, c_sz,
+                     c_vp],
+    "otm_sgd_workspace": [c_i64, c_i64],
     "otm_sgd_set_form": [ctypes.c_int],
     "otm_sgd_run": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64, c_i64, c_f64,
-                    c_f64, c_f64, c_i64, c_vp, c_vp],
+                    c_f64, c_f64, c_i64, c_vp, c_vp, c_sz, c_vp],
     "otm_quantize_samples": [c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp, c_vp],
     "otm_sgd_run_lp_workspace": [],
     "otm_sgd_run_lp": [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64,
@@ -354,8 +356,10 @@ def sgd_step(V, YA, YB, YC, ybar3, theta: float, beta: float, alpha0: float):
     for nm, Y in (("YA", YA), ("YB", YB), ("YC", YC)):
         _need(Y, torch.float32, (b, k), nm)
     _need(ybar3, torch.float64, (3, k), "ybar3")
+    ws = _ws(_lib.otm_sgd_workspace(k, b), V.device)
     _check(_lib.otm_sgd_step(_ptr(V), _ptr(YA), _ptr(YB), _ptr(YC), b, k, _ptr(ybar3),
-                             float(theta), float(beta), float(alpha0), _stream()))
+                             float(theta), float(beta), float(alpha0), _ptr(ws), ws.numel(),
+                             _stream()))
     return V
 
 
@@ -376,9 +380,11 @@ def sgd_run(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, theta
     if snapshot_every:
         snaps = torch.empty(max(steps // snapshot_every, 1), k, k, dtype=torch.float32,
                             device=V.device)
+    ws = _ws(_lib.otm_sgd_workspace(k, int(b)), V.device)
     _check(_lib.otm_sgd_run(_ptr(V), _ptr(YA), _ptr(YB), _ptr(YC), n, k, _ptr(ybar3),
                             _ptr(perm), int(epochs), int(b), float(beta0), float(theta),
-                            float(alpha0), int(snapshot_every), _ptr(snaps), _stream()))
+                            float(alpha0), int(snapshot_every), _ptr(snaps), _ptr(ws), ws.numel(),
+                            _stream()))
     return snaps
 
 

@@ -56,14 +56,14 @@ def test_host_side_argument_errors(lib):
     vp = ctypes.c_void_p
     f = lib.otm_sgd_step
     f.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_double,
-                  ctypes.c_double, ctypes.c_double, vp]
+                  ctypes.c_double, ctypes.c_double, vp, ctypes.c_size_t, vp]
     # k = 0
-    assert f(vp(16), vp(16), vp(16), vp(16), 8, 0, vp(16), 1.0, 0.1, 1.0, None) == 1
+    assert f(vp(16), vp(16), vp(16), vp(16), 8, 0, vp(16), 1.0, 0.1, 1.0, None, 0, None) == 1
     assert b"k=0" in lib.otm_last_error()
     # k too large for the FP32 kernel
-    assert f(vp(16), vp(16), vp(16), vp(16), 8, 129, vp(16), 1.0, 0.1, 1.0, None) == 1
+    assert f(vp(16), vp(16), vp(16), vp(16), 8, 129, vp(16), 1.0, 0.1, 1.0, None, 0, None) == 1
     # null pointer
-    assert f(None, vp(16), vp(16), vp(16), 8, 4, vp(16), 1.0, 0.1, 1.0, None) == 1
+    assert f(None, vp(16), vp(16), vp(16), 8, 4, vp(16), 1.0, 0.1, 1.0, None, 0, None) == 1
     g = lib.otm_syev
     g.argtypes = [vp, ctypes.c_int64, vp, vp, vp, ctypes.c_size_t, vp]
     assert g(vp(16), 200, vp(16), vp(16), vp(16), 1 << 30, None) == 1
