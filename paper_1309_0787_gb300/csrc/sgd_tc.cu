@@ -1263,13 +1263,18 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   for (int i = 0; i < nitems; ++i) sorted[i].err = hdr + 1;
   // the k > 128 group: 4-, 8- or 16-CTA clusters, whichever fit, the fastest on
   // a trial run below
-  std::vector<int> cands_w;
+  // (cluster sizes that leave a CTA without components of the largest problem
+  // are used only when no other fits)
+  std::vector<int> cands_w, cands_w_idle;
   for (int c : {4, 8, 16}) {
     TcPlan Pc;
-    if (n_wide > 0 && (c - 1) * own_cols(max_k_wide, c) < round16(max_k_wide) &&
-        tc_plan(max_k_wide, true, fp8, c, &Pc))
+    if (n_wide == 0 || !tc_plan(max_k_wide, true, fp8, c, &Pc)) continue;
+    if ((c - 1) * own_cols(max_k_wide, c) < round16(max_k_wide))
       cands_w.push_back(c);
+    else
+      cands_w_idle.push_back(c);
   }
+  if (cands_w.empty()) cands_w = cands_w_idle;
   OTM_REQUIRE(n_wide == 0 || !cands_w.empty(), "otm_sgd_batched_prepare: k=%d does not fit on chip",
               max_k_wide);
   OTM_CHECK_CUDA(cudaMemcpyAsync(dev_items, sorted.data(), sizeof(TcArgs) * nitems,

@@ -103,6 +103,23 @@ def test_batched_two_groups_beyond_128(otm):
             assert rel(to_np(p["V"][r]), to_np(Vs)) < 1e-2
 
 
+def test_batched_two_groups_fp8(otm):
+    """FP8 with chains beyond k = 128 (their master rows in the workspace):
+    every chain matches its own single-chain FP8 run."""
+    prec = otm.PREC_FP8
+    specs = [(91, 64, 800, 128, 2, 2), (92, 200, 1024, 256, 1, 2)]
+    probs = [_problem(otm, s, k, n, b, e, r, 5e-3, prec) for s, k, n, b, e, r in specs]
+    batch = otm.SgdBatch(probs, prec)
+    assert batch.plan.nitems_wide == 2 and batch.plan.cluster_wide in (4, 8, 16)
+    batch.launch()
+    batch.check()
+    for p in probs:
+        for r in range(p["V0"].shape[0]):
+            Vs = _single(otm, p, r, prec)
+            torch.cuda.synchronize()
+            assert rel(to_np(p["V"][r]), to_np(Vs)) < 3e-2
+
+
 def test_batched_two_groups_forced_cluster(otm):
     """Both groups with the narrow cluster size given (1): the kernel's launch
     attributes must admit the larger of the two plans' shared memory."""

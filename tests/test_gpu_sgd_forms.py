@@ -129,3 +129,26 @@ def test_grid_form_limits(otm):
         assert np.isfinite(to_np(Vd)).all()
     finally:
         otm.sgd_set_form(otm.SGD_FORM_AUTO)
+
+
+@pytest.mark.parametrize("form", [1, 2], indirect=True)
+def test_invalid_permutation_entries_read_as_zero_samples(otm, form):
+    """A permutation entry outside [0, n) contributes a zero sample (both forms):
+    the result equals the oracle's run on samples with a zero row appended and
+    those entries pointed at it."""
+    k, n, b, epochs = 24, 600, 256, 2
+    g = np.random.default_rng(17)
+    Ys, yb = _views(g, n, k, False)
+    perm = synth.epoch_permutations(18, n, epochs).copy()
+    perm[0, 5] = -3
+    perm[1, 100] = n + 7
+    V0 = synth.haar_orthonormal(19, k)
+    Vd = _dev(V0.T.copy())
+    otm.sgd_run(Vd, *_dev_views(Ys, False), _dev(yb), _dev(perm), epochs, b, 1e-2, 1.0, 1.0)
+    torch.cuda.synchronize()
+    Yz = [np.vstack([Y, np.zeros((1, k), np.float32)]) for Y in Ys]
+    pz = perm.copy()
+    pz[(pz < 0) | (pz >= n)] = n
+    # the oracle visits perm[e, :n] of the (n + 1)-row sample matrix
+    Vo, _ = ostgd.sgd_run(V0, *Yz, tuple(yb), np.ascontiguousarray(pz), b, 1e-2, 1.0, 1.0)
+    assert rel(to_np(Vd).T, Vo) < 1e-5
