@@ -681,10 +681,12 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
   ghi += pad;
   const float piv_min = 1e-30f + 1e-12f * tnorm;
   // multisection: G lanes per eigenvalue evaluate the Sturm count at G interior
-  // points of the current interval, which then shrinks by G + 1 (9 rounds of
-  // 9 for G = 8, 13 rounds of 5 for G = 4: below 2^-28 of the Gershgorin range)
-  const int G = n <= TE_T / 8 ? 8 : 4;
-  const int rounds = G == 8 ? 9 : 13;
+  // points of the current interval, which then shrinks by G + 1 (13 rounds of
+  // 5 for G = 4: below 2^-28 of the Gershgorin range)
+  // (the Sturm counts are bound by the reciprocal unit's throughput, so the
+  // fewer evaluations of G = 4 beat the fewer rounds of G = 8)
+  const int G = 4;
+  const int rounds = 13;
   if ((warp * 32) / G < n) {  // warps holding at least one eigenvalue (ballots are warp-wide)
     const int i = tid / G, sub = tid % G;
     const int gbase = (lane / G) * G;  // first lane of this eigenvalue's group
