@@ -316,10 +316,13 @@ otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precis
  * symmetric path), V re-quantised every step with one scale per component,
  * B = c1 A_A o A_B - c2 (...) quantised with one scale per component per 128
  * samples, FP32 accumulation in tensor memory; the Gram term V((V^T V) o 2)
- * and a_A = V^T ybar_A, a_B = V^T ybar_B run as BF16 tensor-core products of
- * the BF16 image of V; the master V, the mean terms and the update stay FP32.
- * ybar3 are the FP64 means of the unquantised samples.  1 <= k <= 256
- * (k > 128: symmetric views only).
+ * runs as BF16 tensor-core products of the BF16 image of V, and so do
+ * a_A = V^T ybar_A, a_B = V^T ybar_B for k <= 128 (k > 128: FP32 sums of the
+ * BF16 rows on the CUDA cores); the master V, the mean terms and the update
+ * stay FP32.  ybar3 are the FP64 means of the unquantised samples.
+ * 1 <= k <= 256; for k > 128 every CTA of the cluster keeps only its own rows
+ * of the BF16 image on chip and the whole image is exchanged through two
+ * buffers in the workspace (three distinct views: 16-CTA clusters).
  * Scratch: otm_sgd_run_lp_workspace() bytes.  Synchronises the stream;
  * returns OTM_ETIMEOUT if a bounded wait on the tensor cores expired.
  */
@@ -379,8 +382,9 @@ typedef struct otm_batch_plan {
  *
  * otm_sgd_batched_launch -- one persistent launch running every chain with
  * k <= 128 (and, if the plan has any, a second one for 128 < k <= 256, whose
- * chains use 8- or 16-CTA clusters and keep their FP32 master rows in the
- * workspace instead of shared memory): as many clusters as fit on the GPU take chains
+ * chains use 4- to 16-CTA clusters and keep their FP32 master rows and the
+ * cluster's two BF16 images of V in the workspace instead of shared memory,
+ * chosen by the same trial): as many clusters as fit on the GPU take chains
  * from the work list until it is empty.  Asynchronous and free of host synchronisation, so it can
  * be captured in a CUDA graph.  otm_sgd_batched_check reads the plan's
  * timeout flag (synchronises; OTM_ETIMEOUT if a tensor-core wait expired).

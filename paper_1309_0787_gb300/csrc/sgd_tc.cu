@@ -61,6 +61,7 @@ constexpr int TILE = 128;        // samples per tile (M of the first product)
 constexpr int TC_THREADS = 256;  // 8 warps: two per 32-lane TMEM quarter
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int TC_KMAX = 256;
+constexpr size_t VIMG_BYTES = (size_t)2 * 256 * 256 * 2;  // k > 128: two BF16 images per cluster
 constexpr int NMBAR = 5;         // mbarriers: first product x2, second x2, Gram
 
 struct TcArgs {
@@ -91,7 +92,9 @@ __host__ __device__ inline int own_cols(int k, int cl) {
 struct TcLayout {
   int N, nv, NS, es, KPc, CR, CRb, CBn, CBh;
   bool dbl;
-  bool vmg;  // the FP32 master rows live in global scratch (KPc = 256: shared memory is short)
+  bool vstr; // (KPc = 256) only the owned rows of the BF16 image of V stay in shared memory;
+             // the whole image is streamed from global scratch into the sample stages for
+             // the Gram term, and the FP32 master rows live in tensor memory
   size_t y_view, y_stage, off_v[2], off_vq, off_yb, off_b[2], off_h, off_f;
   size_t vm, ybA, ybB, ybC, aA, aB, vsc, bsc, amax, spw, red, ssc, nfloat;
   size_t total;
@@ -111,16 +114,17 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   L.NS = NS;
   L.es = es;
   L.dbl = dbl;
-  L.vmg = KPc > 128;
+  L.vstr = KPc > 128;
   L.CR = KP * es / 16;
   L.CRb = KP * 2 / 16;
   L.CBn = N * es / 16;
   L.CBh = N * 2 / 16;
   L.y_view = (size_t)TILE * KP * es;
   L.y_stage = L.nv * L.y_view;
-  const size_t v_bytes = (size_t)KP * KP * 2;  // KPc rows (components) x KPc coordinates
+  // KPc rows (components) x KPc coordinates, or only the N owned rows when streamed
+  const size_t v_bytes = (size_t)(L.vstr ? N : KP) * KP * 2;
   L.off_v[0] = NS * L.y_stage;
-  L.off_v[1] = dbl ? L.off_v[0] + v_bytes : L.off_v[0];
+  L.off_v[1] = dbl && !L.vstr ? L.off_v[0] + v_bytes : L.off_v[0];
   L.off_vq = L.off_v[1] + v_bytes;
   const size_t vq_bytes = es == 1 ? (size_t)N * KP : 0;
   const size_t b_bytes = (size_t)TILE * N * es;
@@ -131,7 +135,7 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   // is when the H and ybar images are live, so they use the stage instead.
   const size_t h_bytes = (size_t)KP * N * 2;
   const size_t yb_bytes = (size_t)16 * KP * 2;
-  const bool in_stage = NS == 1 && h_bytes <= L.y_stage && yb_bytes <= L.y_stage;
+  const bool in_stage = NS == 1 && !L.vstr && h_bytes <= L.y_stage && yb_bytes <= L.y_stage;
   L.off_b[0] = al128(L.off_vq + vq_bytes);
   L.off_b[1] = NS >= 4 ? L.off_b[0] + b_bytes : L.off_b[0];
   L.off_yb = in_stage ? 0 : L.off_b[0];
@@ -141,7 +145,7 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   if (L.off_yb + yb_bytes > end) end = L.off_yb + yb_bytes;
   L.off_f = al128(end);
   size_t f = 0;
-  L.vm = f;   f += L.vmg ? 0 : (size_t)N * KP;
+  L.vm = f;   f += L.vstr ? 0 : (size_t)N * KP;
   L.ybA = f;  f += KP;
   L.ybB = f;  f += KP;
   L.ybC = f;  f += KP;
@@ -170,6 +174,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t addr, const float (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(addr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_async_cluster() {
   asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
 }
@@ -181,47 +198,84 @@ struct TcCtx {
   uint32_t ph;     // phase bits: 0-1 first product slots, 2-3 second, 4 Gram
 };
 
+// Samples of a tile handled by a thread: warp w takes samples 16 w .. 16 w + 15,
+// lane l samples 16 w + (l & 7) and 16 w + 8 + (l & 7).
+__device__ __forceinline__ int tile_sample(int j) {
+  return 16 * (threadIdx.x >> 5) + 8 * j + (threadIdx.x & 7);
+}
+
 // Sample tile into ring stage `stage` by cp.async (zero fill outside the
-// minibatch); thread tid copies half of sample tid / 2's coordinates and its
-// scales.  raw: the permutation entry of that sample (-1 outside the
-// minibatch), loaded one issue earlier so that its latency is hidden.
+// minibatch), with the samples' scales.  One warp instruction copies four
+// consecutive 16-byte groups (64 contiguous bytes) of each of eight samples, so
+// that it touches eight rows in global memory and writes four conflict-free
+// 128-byte rows of the K-major image.  raw[j]: the permutation entry of sample
+// tile_sample(j) (-1 outside the minibatch), loaded one issue earlier so that
+// its latency is hidden.
 template <bool FP8, bool SYM>
 __device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, uint8_t* smem,
-                                          float* F, int raw, int stage) {
+                                          float* F, const int (&raw)[2], int stage) {
   constexpr int ES = FP8 ? 1 : 2;
-  const int tid = threadIdx.x;
-  const int t = tid >> 1, hs = tid & 1;
-  const int64_t row = (raw >= 0 && raw < a.n) ? raw : -1;
-  const int half = L.CR / 2;
+  const int lane = threadIdx.x & 31;
+  const int s8 = lane & 7, c4 = lane >> 3;
+  const int nq = L.CR / 4;  // 64-byte quarters of a sample row
   uint8_t* Ys = smem + (size_t)stage * L.y_stage;
-  for (int v = 0; v < L.nv; ++v) {
-    const uint8_t* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
-    uint8_t* dst = Ys + v * L.y_view + ((size_t)(t >> 3) * L.CR << 7) + ((t & 7) << 4);
-    for (int c = 0; c < half; ++c) {
-      const int rg = hs * half + c;
-      const int c0 = rg * (16 / ES);
-      const bool in = row >= 0 && c0 < a.ldq;
-      const uint8_t* src = in ? Yg + ((size_t)row * a.ldq + c0) * ES : Yg;
-      cp_async16(dst + ((size_t)rg << 7), src, in ? 16u : 0u);
-    }
-    if (hs == 0) {
-      const float* sv = v == 0 ? a.sA : (v == 1 ? a.sB : a.sC);
-      float* sd = F + L.ssc + ((size_t)stage * 3 + v) * TILE + t;
-      if (sv)
-        cp_async4(sd, row >= 0 ? sv + row : sv, row >= 0 ? 4u : 0u);
-      else
-        *sd = row >= 0 ? 1.f : 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int t = tile_sample(j);
+    const int64_t row = (raw[j] >= 0 && raw[j] < a.n) ? raw[j] : -1;
+    for (int v = 0; v < L.nv; ++v) {
+      const uint8_t* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+      uint8_t* dst = Ys + v * L.y_view + ((size_t)(t >> 3) * L.CR << 7) + (s8 << 4);
+      for (int m = 0; m < nq; ++m) {
+        const int rg = 4 * m + c4;
+        const int c0 = rg * (16 / ES);
+        const bool in = row >= 0 && c0 < a.ldq;
+        const uint8_t* src = in ? Yg + ((size_t)row * a.ldq + c0) * ES : Yg;
+        cp_async16(dst + ((size_t)rg << 7), src, in ? 16u : 0u);
+      }
+      if (c4 == 0) {
+        const float* sv = v == 0 ? a.sA : (v == 1 ? a.sB : a.sC);
+        float* sd = F + L.ssc + ((size_t)stage * 3 + v) * TILE + t;
+        if (sv)
+          cp_async4(sd, row >= 0 ? sv + row : sv, row >= 0 ? 4u : 0u);
+        else
+          *sd = row >= 0 ? 1.f : 0.f;
+      }
     }
   }
   cp_async_commit();
 }
 
-// One STGD chain (one decomposition), run by one cluster; TMEM and the
+// The owned rows own_lo .. own_lo + N - 1 of V (k x k, component-contiguous)
+// into tensor memory from column base tcol on: lane = coordinate within a
+// 128-row block, column mbk N + i = component own_lo + i (zeros outside k x k).
+// Kept out of line: it runs once per chain and inlining it costs the step loop
+// registers.
+__device__ __noinline__ void tmem_load_rows(const float* __restrict__ V, int k, int own_lo, int N,
+                                            uint32_t tcol) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qd = warp & 3, hf = warp >> 2;
+  for (int c = 0; c < N / 16; ++c)
+    for (int mbk = 0; mbk < 2; ++mbk) {
+      const int r = mbk * 128 + 32 * qd + lane, c0 = 16 * c + 8 * hf;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int comp = own_lo + c0 + j;
+        v[j] = (comp < k && r < k) ? V[(int64_t)comp * k + r] : 0.f;
+      }
+      tmem_st8(tcol + (uint32_t)(mbk * N + c0), v);
+    }
+  tmem_st_wait();
+}
+
+// One STGD chain (one decomposition), run by one cluster (WIDE: k > 128, 256
+// padded coordinates, the code path of the streamed image); TMEM and the
 // mbarriers are set up by the caller.  Ends with a cluster barrier so that the
 // caller may reuse shared memory afterwards.
-template <bool FP8, bool SYM>
+template <bool FP8, bool SYM, bool WIDE>
 __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool dbl,
-                         float* vm_cta) {
+                         uint8_t* vimg_cl) {
   constexpr int ES = FP8 ? 1 : 2;
   constexpr int KSTEP = FP8 ? 32 : 16;            // K of one MMA
   constexpr uint32_t FMT = FP8 ? 0u : 1u;         // E4M3 / BF16
@@ -233,15 +287,19 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int qd = warp & 3, hf = warp >> 2;
   const int k = a.k;
-  const int KPc = k <= 128 ? 128 : 256;  // padded coordinates / components
-  const int MB = KPc / 128;               // 128-row blocks
+  constexpr int KPc = WIDE ? 256 : 128;  // padded coordinates / components
+  constexpr int MB = KPc / 128;           // 128-row blocks
+  if ((k > 128) != WIDE) {  // launched for the other width: report, leave V as it is
+    if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+    return;
+  }
   const int N = own_cols(k, CL);
   const TcLayout L = tc_layout(N, SYM, ES, NS, dbl, KPc);
   const int own_lo = q * N;
   const bool active = own_lo < k;
   const int nch = N / 16;
   float* F = reinterpret_cast<float*>(smem + L.off_f);
-  float* Vm = L.vmg ? vm_cta : F + L.vm;  // owned rows [N][KPc]
+  float* Vm = F + L.vm;  // owned rows [N][KPc] (k <= 128)
   float* ybA = F + L.ybA;
   float* ybB = F + L.ybB;
   float* ybC = F + L.ybC;
@@ -254,6 +312,12 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   float* red = F + L.red;
   uint8_t* Vimg0 = smem + L.off_v[0];
   uint8_t* Vimg1 = smem + L.off_v[1];
+  // streamed image: Vown = the owned rows (local row index), Vfull = the whole image
+  // copied into the sample stages for the Gram term, gimg = the cluster's two global
+  // images (step s reads image s & 1 and writes image (s + 1) & 1)
+  uint8_t* Vown = Vimg0;
+  uint8_t* Vfull = smem;
+  const size_t img_bytes = (size_t)KPc * KPc * 2;
   uint8_t* Vq = smem + L.off_vq;
   uint8_t* Bimg0 = smem + L.off_b[0];
   uint8_t* Bimg1 = smem + L.off_b[1];
@@ -269,18 +333,26 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   const uint32_t colD2b = (uint32_t)(2 * NVD * N);
   const uint32_t d2w = (uint32_t)((FP8 ? 2 : 1) * N);
   const uint32_t colY = colD2b + (uint32_t)MB * d2w;
-  const uint32_t colGGb = MB == 1 ? (uint32_t)N : colY + 16;
+  const uint32_t colGGb = MB == 1 ? (uint32_t)N : colY + (WIDE ? 0u : 16u);
+  // k > 128: the FP32 master rows, lane = coordinate within a 128-row block,
+  // column colVm + mbk N + i = owned component i
+  const uint32_t colVm = colGGb + (uint32_t)(MB * N);
   const int ks1 = (k + KSTEP - 1) / KSTEP;  // coordinate steps of the first product
   const int kg16 = (k + 15) / 16;           // 16-steps of the Gram products
   const size_t own_off = ((size_t)(own_lo >> 3) * L.CRb) << 7;
 
   // ---- initial state: owned FP32 rows, BF16 image of all rows, means ----
-  for (int idx = tid; idx < N * KPc; idx += TC_THREADS) {
-    const int i = idx / KPc, r = idx % KPc, c = own_lo + i;
-    Vm[idx] = (c < k && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
+  if (WIDE) {
+    tmem_load_rows(a.V, k, own_lo, N, tmem + lane_base + colVm);
+  } else {
+    for (int idx = tid; idx < N * KPc; idx += TC_THREADS) {
+      const int i = idx / KPc, r = idx % KPc, c = own_lo + i;
+      Vm[idx] = (c < k && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
+    }
   }
-  for (int idx = tid; idx < KPc * L.CRb; idx += TC_THREADS) {
-    const int c = idx / L.CRb, rg = idx % L.CRb;
+  for (int idx = tid; idx < (WIDE ? N : KPc) * L.CRb; idx += TC_THREADS) {
+    const int c = idx / L.CRb + (WIDE ? own_lo : 0), rg = idx % L.CRb;
+    const int cl = WIDE ? c - own_lo : c;  // row of the shared-memory image
     float v[8];
 #pragma unroll
     for (int z = 0; z < 8; ++z) {
@@ -292,9 +364,21 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     w.y = pack_bf16(v[2], v[3]);
     w.z = pack_bf16(v[4], v[5]);
     w.w = pack_bf16(v[6], v[7]);
-    const size_t off = (((size_t)(c >> 3) * L.CRb + rg) << 7) + ((c & 7) << 4);
+    const size_t off = (((size_t)(cl >> 3) * L.CRb + rg) << 7) + ((cl & 7) << 4);
     *reinterpret_cast<uint4*>(Vimg0 + off) = w;
     if (dbl) *reinterpret_cast<uint4*>(Vimg1 + off) = w;
+  }
+  // streamed image: the owned rows into global image dst (contiguous: N rows x KPc
+  // coordinates from row own_lo on), visible to the cluster after its next barrier
+  auto publish_own = [&](uint8_t* dst) {
+    const uint4* src = reinterpret_cast<const uint4*>(Vown);
+    uint4* d = reinterpret_cast<uint4*>(dst + (size_t)own_lo * KPc * 2);
+    for (int idx = tid; idx < N * KPc / 8; idx += TC_THREADS) d[idx] = src[idx];
+    __threadfence();
+  };
+  if (WIDE && active) {
+    __syncthreads();
+    publish_own(vimg_cl);
   }
   for (int r = tid; r < KPc; r += TC_THREADS) {
     ybA[r] = r < k ? (float)a.ybar3[r] : 0.f;
@@ -326,7 +410,13 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   if (FP8) {
     for (int i = warp; i < N; i += TC_THREADS / 32) {
       float m = 0.f;
-      for (int r = lane; r < KPc; r += 32) m = fmaxf(m, fabsf(Vm[i * KPc + r]));
+      if (WIDE) {
+        if (own_lo + i < k)
+          for (int r = lane; r < k; r += 32)
+            m = fmaxf(m, fabsf(a.V[(int64_t)(own_lo + i) * k + r]));
+      } else {
+        for (int r = lane; r < KPc; r += 32) m = fmaxf(m, fabsf(Vm[i * KPc + r]));
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       if (lane == 0) vsc[i] = m > 0.f ? m / QMAX : 1.f;
@@ -338,6 +428,22 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
 
   // FP8: owned rows of V quantised with one scale per component (K-major)
   auto build_vq = [&]() {
+    if (WIDE) {  // from tensor memory: thread = coordinate r, one byte per component
+      for (int c = 0; c < nch; ++c)
+        for (int mbk = 0; mbk < MB; ++mbk) {
+          const int r = mbk * 128 + 32 * qd + lane, c0 = 16 * c + 8 * hf;
+          float x[8];
+          tmem_ld8(tmem + lane_base + colVm + (uint32_t)(mbk * N + c0), x);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int i = c0 + j;
+            const __nv_fp8_e4m3 q(x[j] * (1.f / vsc[i]));
+            Vq[(((size_t)(i >> 3) * L.CR + (r >> 4)) << 7) + ((i & 7) << 4) + (r & 15)] =
+                *reinterpret_cast<const uint8_t*>(&q);
+          }
+        }
+      return;
+    }
     for (int idx = tid; idx < N * L.CR; idx += TC_THREADS) {
       const int i = idx / L.CR, rg = idx % L.CR;
       const float inv = 1.f / vsc[i];
@@ -353,6 +459,28 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   if (FP8) build_vq();
   fence_async_smem();
   cluster.sync();
+
+  // the owned FP32 rows into dst (k x k, component-contiguous)
+  auto write_rows = [&](float* dst) {
+    if (WIDE) {
+      for (int c = 0; c < nch; ++c)
+        for (int mbk = 0; mbk < MB; ++mbk) {
+          const int r = mbk * 128 + 32 * qd + lane, c0 = 16 * c + 8 * hf;
+          float x[8];
+          tmem_ld8(tmem + lane_base + colVm + (uint32_t)(mbk * N + c0), x);
+          if (r < k) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (own_lo + c0 + j < k) dst[(int64_t)(own_lo + c0 + j) * k + r] = x[j];
+          }
+        }
+      return;
+    }
+    for (int idx = tid; idx < N * k; idx += TC_THREADS) {
+      const int i = idx / k, r = idx % k;
+      if (own_lo + i < k) dst[(int64_t)(own_lo + i) * k + r] = Vm[i * KPc + r];
+    }
+  };
 
   // bounded mbarrier wait by every thread (phases tracked identically)
   auto wait_mb = [&](int idx) {
@@ -375,15 +503,17 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   auto tiles_of = [&](int64_t jb) {
     return (int)((min(a.b, a.n - jb * a.b) + TILE - 1) / TILE);
   };
-  auto row_raw = [&](int64_t e, int64_t jb, int n_tile) {
-    const int t = tid >> 1;
+  auto row_raw = [&](int64_t e, int64_t jb, int n_tile, int t) {
     const int64_t pos0 = jb * a.b;
     const int64_t p = (int64_t)n_tile * TILE + t;
     if (p >= min(a.b, a.n - pos0)) return -1;
     return a.perm ? a.perm[e * a.n + pos0 + p] : (int)(pos0 + p);
   };
   ld_nt = a.total_steps > 0 ? tiles_of(0) : 0;
-  int next_raw = a.total_steps > 0 ? row_raw(0, 0, 0) : -1;
+  int next_raw[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+    next_raw[j] = a.total_steps > 0 ? row_raw(0, 0, 0, tile_sample(j)) : -1;
   auto issue_one = [&]() {
     if (ld_s >= a.total_steps) return;
     load_tile<FP8, SYM>(a, L, smem, F, next_raw, ld_stage);
@@ -398,7 +528,10 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       }
       ld_nt = tiles_of(ld_jb);
     }
-    if (ld_s < a.total_steps) next_raw = row_raw(ld_e, ld_jb, ld_n);
+    if (ld_s < a.total_steps) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) next_raw[j] = row_raw(ld_e, ld_jb, ld_n, tile_sample(j));
+    }
   };
   auto wait_tile = [&](int64_t g) {
     const int64_t pend = issued - 1 - g;
@@ -408,8 +541,10 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     __syncthreads();
     tc_after();
   };
+  // streamed image: the stages hold the image during the Gram term, so no tile of
+  // a later step is issued before that step's Gram products are done
   if (active)
-    for (int i = 0; i < NS - W; ++i) issue_one();
+    for (int i = 0; i < NS - W && (!WIDE || ld_s == 0); ++i) issue_one();
 
   int cur = 0;
   int64_t gbase = 0;
@@ -439,7 +574,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
           for (int j = 0; j < 8; ++j) gacc[u][c][j] = 0.f;
 
       // descriptors (the start address is the low 14-bit field, in 16-byte units)
-      const uint64_t dV_own = sdesc(Vc + own_off, 128, (uint32_t)L.CRb * 128);
+      const uint64_t dV_own = sdesc(WIDE ? Vown : Vc + own_off, 128, (uint32_t)L.CRb * 128);
       const uint64_t dVq = sdesc(Vq, 128, (uint32_t)L.CR * 128);
       const uint32_t id1 = make_idesc(FMT, 0, 0, TILE, (uint32_t)N);
       const uint32_t id2 = make_idesc(FMT, 1, 1, 128, (uint32_t)N);
@@ -497,12 +632,14 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       // a_A = V^T ybar_A, a_B = V^T ybar_B for the 128 components of the block holding
       // the owned ones (one MMA chain, N = 16)
       const int mbo = own_lo >> 7;
-      build_ybar_image();
-      fence_async_smem();
+      if (!WIDE) {
+        build_ybar_image();
+        fence_async_smem();
+      }
       tc_before();
       __syncthreads();
       tc_after();
-      if (tid == 0 && !s_abort) {
+      if (!WIDE && tid == 0 && !s_abort) {
         const uint64_t dA = sdesc(Vc + (((size_t)mbo * 16 * L.CRb) << 7), 128, (uint32_t)L.CRb * 128);
         const uint64_t dB = sdesc(Ybimg, 128, (uint32_t)L.CRb * 128);
         const uint32_t id = make_idesc(1, 0, 0, 128, 16);
@@ -516,14 +653,42 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         wait_tile(gbase);
         if (tid == 0 && !s_abort) gemm1(0, st);
       }
-      wait_mb(4);
-      if (hf == 0) {  // lanes = components: keep the owned ones
-        float x[8];
-        tmem_ld8(tmem + lane_base + colY, x);
-        const int j = mbo * 128 + 32 * qd + lane;
-        if (j >= own_lo && j < own_lo + N) {
-          aA[j - own_lo] = x[0];
-          aB[j - own_lo] = SYM ? x[0] : x[1];
+      if (WIDE) {
+        // from the owned rows' BF16 image: warp w sums components 8w..8w+7, lanes
+        // 8j..8j+7 take coordinate groups j, j + 4, ... (one 128-byte row per group)
+        for (int i8 = warp; i8 < N / 8; i8 += TC_THREADS / 32) {
+          float sa = 0.f, sb = 0.f;
+          for (int rg = lane >> 3; rg < L.CRb; rg += 4) {
+            const uint4 w = *reinterpret_cast<const uint4*>(
+                Vown + (((size_t)i8 * L.CRb + rg) << 7) + ((lane & 7) << 4));
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w);
+#pragma unroll
+            for (int z = 0; z < 4; ++z) {
+              const float2 v = __bfloat1622float2(h[z]);
+              const int r = rg * 8 + 2 * z;
+              sa = fmaf(v.x, ybA[r], fmaf(v.y, ybA[r + 1], sa));
+              if (!SYM) sb = fmaf(v.x, ybB[r], fmaf(v.y, ybB[r + 1], sb));
+            }
+          }
+          sa += __shfl_xor_sync(0xffffffffu, sa, 8);
+          sa += __shfl_xor_sync(0xffffffffu, sa, 16);
+          sb += __shfl_xor_sync(0xffffffffu, sb, 8);
+          sb += __shfl_xor_sync(0xffffffffu, sb, 16);
+          if (lane < 8) {
+            aA[i8 * 8 + lane] = sa;
+            aB[i8 * 8 + lane] = SYM ? sa : sb;
+          }
+        }
+      } else {
+        wait_mb(4);
+        if (hf == 0) {  // lanes = components: keep the owned ones
+          float x[8];
+          tmem_ld8(tmem + lane_base + colY, x);
+          const int j = mbo * 128 + 32 * qd + lane;
+          if (j >= own_lo && j < own_lo + N) {
+            aA[j - own_lo] = x[0];
+            aB[j - own_lo] = SYM ? x[0] : x[1];
+          }
         }
       }
       tc_before();
@@ -542,7 +707,8 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
           wait_mb(2 + ((n - W) & 1));
           if (FP8) epi2(n - W);
         }
-        while (issued <= g + NS - W && ld_s < a.total_steps) issue_one();
+        while (issued <= g + NS - W && ld_s < a.total_steps && (!WIDE || ld_s == s))
+          issue_one();
         if (!early) {
           wait_tile(g);
           if (tid == 0 && !s_abort) gemm1(slot, st);
@@ -635,6 +801,17 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         wait_mb(2 + (n & 1));
         if (FP8) epi2(n);
       }
+      if (WIDE) {
+        // the stages are free: copy this step's image (rows >= k read as zeros)
+        const uint8_t* src = vimg_cl + (size_t)(s & 1) * img_bytes;
+        for (int c16 = tid; c16 < (int)(img_bytes >> 4); c16 += TC_THREADS) {
+          const size_t off = (size_t)c16 << 4;
+          const int comp = (int)((off >> 7) / L.CRb) * 8 + (int)((off >> 4) & 7);
+          const bool in = comp < k;
+          cp_async16(Vfull + off, in ? src + off : src, in ? 16u : 0u);
+        }
+        cp_async_commit();
+      }
 
       // s_i = sum over the minibatch of A_A o A_B (per owned component)
 #pragma unroll
@@ -650,6 +827,11 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         }
       }
       // -- Gram term: H = V^T V_own, then G_gram = V (H o H) --
+      uint8_t* Vg = WIDE ? Vfull : Vc;  // the whole image
+      if (WIDE) {
+        cp_async_wait(0);
+        fence_async_smem();
+      }
       tc_before();
       __syncthreads();
       tc_after();
@@ -657,7 +839,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         const uint32_t id = make_idesc(1, 0, 0, 128, (uint32_t)N);
         for (int mbk = 0; mbk < MB; ++mbk) {  // components j in blocks of 128 rows
           const uint64_t dA =
-              sdesc(Vc + (((size_t)mbk * 16 * L.CRb) << 7), 128, (uint32_t)L.CRb * 128);
+              sdesc(Vg + (((size_t)mbk * 16 * L.CRb) << 7), 128, (uint32_t)L.CRb * 128);
           for (int ks = 0; ks < kg16; ++ks)
             mma<false>(tmem + (uint32_t)(mbk * N), dA + (uint64_t)(16 * ks),
                        dV_own + (uint64_t)(16 * ks), id, ks > 0 ? 1u : 0u);
@@ -691,7 +873,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         const uint64_t dB = sdesc(Himg, (uint32_t)L.CBh * 128, 128);
         const uint32_t id = make_idesc(1, 1, 1, 128, (uint32_t)N);
         for (int mbk = 0; mbk < MB; ++mbk) {  // coordinates in blocks of 128 (2048 bytes)
-          const uint64_t dA = sdesc(Vc + (size_t)mbk * 2048, (uint32_t)L.CRb * 128, 128);
+          const uint64_t dA = sdesc(Vg + (size_t)mbk * 2048, (uint32_t)L.CRb * 128, 128);
           for (int ks = 0; ks < kg16; ++ks)
             mma<false>(tmem + colGGb + (uint32_t)(mbk * N), dA + (uint64_t)(2 * L.CRb * 8 * ks),
                        dB + (uint64_t)(2 * L.CBh * 8 * ks), id, ks > 0 ? 1u : 0u);
@@ -699,6 +881,11 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         mma_commit(&mb[4]);
       }
       wait_mb(4);
+      // streamed image: the stages are free again; the next step's first tiles load
+      // during the update
+      if (WIDE)
+        while (issued < gbase + nt + NS - W && ld_s == s + 1 && ld_s < a.total_steps)
+          issue_one();
 
       // -- update of the owned columns (thread = coordinate r, per 128-row block) --
 #pragma unroll
@@ -710,8 +897,9 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
           for (int j = 0; j < 8; ++j) mcol[j] = 0.f;
           for (int mbk = 0; mbk < MB; ++mbk) {
             const int r = mbk * 128 + 32 * qd + lane;
-            float gg[8], gd[8];
+            float gg[8], gd[8], vm8[8];
             tmem_ld8(tmem + lane_base + colGGb + (uint32_t)(mbk * N + c0), gg);
+            if (WIDE) tmem_ld8(tmem + lane_base + colVm + (uint32_t)(mbk * N + c0), vm8);
             if constexpr (FP8) {
 #pragma unroll
               for (int j = 0; j < 8; ++j) gd[j] = gacc[mbk & 1][c < 4 ? c : 0][j];
@@ -727,15 +915,21 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
                   const float s_i = spw[i] + spw[N + i] + spw[2 * N + i] + spw[3 * N + i];
                   const float gdata =
                       gd[j] * inv_b + ybC[r] * (a.c3 * aA[i] * aB[i] - a.c2 * s_i * inv_b);
-                  vnew = Vm[i * KPc + r] - beta * (a.kappa * gg[j] - gdata);
-                  Vm[i * KPc + r] = vnew;
+                  vnew = (WIDE ? vm8[j] : Vm[i * KPc + r]) - beta * (a.kappa * gg[j] - gdata);
+                  if (WIDE)
+                    vm8[j] = vnew;
+                  else
+                    Vm[i * KPc + r] = vnew;
                 }
+                const int ci = WIDE ? i : comp;  // row of the shared-memory image
                 *reinterpret_cast<__nv_bfloat16*>(
-                    Vn + ((((size_t)(comp >> 3) * L.CRb + (r >> 3)) << 7) + ((comp & 7) << 4) +
-                          ((r & 7) << 1))) = __float2bfloat16_rn(vnew);
+                    (WIDE ? Vown : Vn) + ((((size_t)(ci >> 3) * L.CRb + (r >> 3)) << 7) +
+                                            ((ci & 7) << 4) + ((r & 7) << 1))) =
+                    __float2bfloat16_rn(vnew);
                 mcol[j] = fmaxf(mcol[j], fabsf(vnew));
               }
             }
+            if (WIDE) tmem_st8(tmem + lane_base + colVm + (uint32_t)(mbk * N + c0), vm8);
           }
           if (FP8) {
 #pragma unroll
@@ -748,6 +942,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
           }
         }
       }
+      if (WIDE) tmem_st_wait();
       tc_before();
       __syncthreads();
       tc_after();
@@ -755,19 +950,15 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         const float m = fmaxf(fmaxf(red[tid], red[N + tid]), fmaxf(red[2 * N + tid], red[3 * N + tid]));
         vsc[tid] = m > 0.f ? m / QMAX : 1.f;
       }
-      if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0) {
-        float* dst = a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k;
-        for (int idx = tid; idx < N * k; idx += TC_THREADS) {
-          const int i = idx / k, r = idx % k;
-          if (own_lo + i < k) dst[(int64_t)(own_lo + i) * k + r] = Vm[i * KPc + r];
-        }
-      }
+      if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0)
+        write_rows(a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k);
       __syncthreads();
       if (FP8) build_vq();
+      if (WIDE) publish_own(vimg_cl + (size_t)((s + 1) & 1) * img_bytes);
     }
 
     // -- the new owned rows into every CTA's V image --
-    if (CL > 1) {
+    if (CL > 1 && !WIDE) {
       if (!dbl) cluster.sync();  // single image: every CTA has finished reading it
       if (active) {
         const int nrow = min(N, k - own_lo);
@@ -790,12 +981,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     if (++jb == a.spe) jb = 0;
   }
   cp_async_wait(0);
-  if (active) {
-    for (int idx = tid; idx < N * k; idx += TC_THREADS) {
-      const int i = idx / k, r = idx % k;
-      if (own_lo + i < k) a.V[(int64_t)(own_lo + i) * k + r] = Vm[i * KPc + r];
-    }
-  }
+  if (active) write_rows(a.V);
   cx.ph = ph;
   cluster.sync();
 }
@@ -829,27 +1015,26 @@ __device__ __forceinline__ void tc_teardown(TcCtx& cx) {
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(cx.tmem, TMEM_COLS);
 }
 
-template <bool FP8, bool SYM>
+template <bool FP8, bool SYM, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    sgd_tc_kernel(TcArgs a, int NS, int dbl, float* vms, int vm_stride) {
+    sgd_tc_kernel(TcArgs a, int NS, int dbl, uint8_t* vimg) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar[NMBAR];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   TcCtx cx;
   tc_setup(cx, mbar, &tmem_base, &s_abort);
-  tc_chain<FP8, SYM>(a, smem, cx, NS, dbl != 0,
-                     vms ? vms + (size_t)blockIdx.x * vm_stride : nullptr);
+  tc_chain<FP8, SYM, WIDE>(a, smem, cx, NS, dbl != 0, vimg);
   tc_teardown(cx);
 }
 
 // Persistent batched form: every cluster takes (problem, restart) chains from
 // a cost-ordered work list until it is exhausted.  Cluster rank 0 claims the
 // next item with one atomic and broadcasts it through distributed shared memory.
-template <bool FP8>
+template <bool FP8, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     sgd_tc_batched_kernel(const TcArgs* __restrict__ items, int nitems, int* counter, int NS,
-                          int dbl, float* vms, int vm_stride) {
+                          int dbl, uint8_t* vimg) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar[NMBAR];
   __shared__ uint32_t tmem_base;
@@ -867,8 +1052,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int it = s_item;
     if (it >= nitems) break;
     const TcArgs a = items[it];
-    tc_chain<FP8, true>(a, smem, cx, NS, dbl != 0,
-                        vms ? vms + (size_t)blockIdx.x * vm_stride : nullptr);
+    tc_chain<FP8, true, WIDE>(a, smem, cx, NS, dbl != 0,
+                        vimg ? vimg + (size_t)(blockIdx.x / cluster.num_blocks()) * VIMG_BYTES
+                             : nullptr);
   }
   tc_teardown(cx);
 }
@@ -918,7 +1104,7 @@ struct TcPlan {
   int CL, N, NS;
   bool dbl;
   size_t smem;
-  bool vmg;  // needs global scratch for the FP32 master rows: N x 256 floats per CTA
+  bool wide;  // k > 128: needs VIMG_BYTES of global scratch per cluster (streamed V images)
 };
 
 // The first configuration (deepest pipeline, double-buffered V image first)
@@ -929,7 +1115,9 @@ bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
   if (N > 128 || (fp8 && N > 64)) return false;
   if (MB > 1 && 128 % N != 0) return false;  // owned rows inside one 128-row block
   const int nvd = sym ? 1 : 2;
-  if (2 * nvd * N + MB * (fp8 ? 2 : 1) * N + 16 + (MB > 1 ? MB * N : 0) > (int)TMEM_COLS)
+  // tensor memory columns: first product, second product, then either the means (16)
+  // or, for k > 128, G_gram and the FP32 master rows per 128-row block
+  if (2 * nvd * N + MB * (fp8 ? 2 : 1) * N + (MB > 1 ? 2 * MB * N : 16) > (int)TMEM_COLS)
     return false;
   const size_t lim = (size_t)max_smem_optin() - 1024;  // static shared variables
   const int order[8][2] = {{1, 4}, {1, 3}, {0, 4}, {0, 3}, {1, 2}, {0, 2}, {1, 1}, {0, 1}};
@@ -937,8 +1125,9 @@ bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
     const bool dbl = o[0] != 0;
     if (dbl && CL == 1) continue;
     const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, o[1], dbl, KPc);
+    if (L.vstr && (dbl || (size_t)o[1] * L.y_stage < (size_t)KPc * KPc * 2)) continue;
     if (L.total <= lim) {
-      *out = {CL, N, o[1], dbl, L.total, L.vmg};
+      *out = {CL, N, o[1], dbl, L.total, L.vstr};
       return true;
     }
   }
@@ -956,8 +1145,8 @@ bool tc_plan_single(int k, bool sym, bool fp8, TcPlan* out) {
 }
 
 template <bool FP8, bool SYM>
-otm_status launch_tc(const TcArgs& args, const TcPlan& P, cudaStream_t st, float* vms) {
-  auto kern = sgd_tc_kernel<FP8, SYM>;
+otm_status launch_tc(const TcArgs& args, const TcPlan& P, cudaStream_t st, uint8_t* vimg) {
+  auto kern = P.wide ? sgd_tc_kernel<FP8, SYM, true> : sgd_tc_kernel<FP8, SYM, false>;
   OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
   if (P.CL > 8)
     OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -973,8 +1162,8 @@ otm_status launch_tc(const TcArgs& args, const TcPlan& P, cudaStream_t st, float
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  float* vm = P.vmg ? vms : nullptr;
-  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args, P.NS, (int)P.dbl, vm, P.N * 256));
+  uint8_t* vi = P.wide ? vimg : nullptr;
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args, P.NS, (int)P.dbl, vi));
   count_launch();
   return OTM_OK;
 }
@@ -999,8 +1188,8 @@ cudaLaunchConfig_t batched_cfg(const TcPlan& P, int nclusters, cudaStream_t st,
 // prepare call, so that the launch itself issues stream work only)
 template <bool FP8>
 otm_status launch_batched(const TcPlan& P, const TcArgs* items, int nitems, int* counter,
-                          int nclusters, cudaStream_t st, bool configure, float* vms) {
-  auto kern = sgd_tc_batched_kernel<FP8>;
+                          int nclusters, cudaStream_t st, bool configure, uint8_t* vimg) {
+  auto kern = P.wide ? sgd_tc_batched_kernel<FP8, true> : sgd_tc_batched_kernel<FP8, false>;
   if (configure) {
     OTM_CHECK_CUDA(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
@@ -1010,9 +1199,8 @@ otm_status launch_batched(const TcPlan& P, const TcArgs* items, int nitems, int*
   if (nitems == 0) return OTM_OK;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = batched_cfg(P, nclusters, st, attr);
-  float* vm = P.vmg ? vms : nullptr;
-  OTM_CHECK_CUDA(
-      cudaLaunchKernelEx(&cfg, kern, items, nitems, counter, P.NS, (int)P.dbl, vm, P.N * 256));
+  uint8_t* vi = P.wide ? vimg : nullptr;
+  OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, items, nitems, counter, P.NS, (int)P.dbl, vi));
   count_launch();
   return OTM_OK;
 }
@@ -1034,8 +1222,9 @@ int batched_clusters(bool fp8, const TcPlan& P) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = batched_cfg(P, 1, nullptr, attr);
   int n = 0;
-  const cudaError_t e = fp8 ? cudaOccupancyMaxActiveClusters(&n, sgd_tc_batched_kernel<true>, &cfg)
-                            : cudaOccupancyMaxActiveClusters(&n, sgd_tc_batched_kernel<false>, &cfg);
+  auto kern = fp8 ? (P.wide ? sgd_tc_batched_kernel<true, true> : sgd_tc_batched_kernel<true, false>)
+                  : (P.wide ? sgd_tc_batched_kernel<false, true> : sgd_tc_batched_kernel<false, false>);
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
   if (e != cudaSuccess || n <= 0) {
     cudaGetLastError();
     n = std::max(1, num_sms_tc() / P.CL);
@@ -1072,10 +1261,9 @@ otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precis
   return OTM_OK;
 }
 
-// The error flag (256 bytes), then, for k > 128, the FP32 master rows of every
-// CTA of the chain's cluster (at most 16 CTAs x 32 rows x 256 floats).
-constexpr size_t LP_VM_FLOATS = (size_t)16 * 32 * 256;
-size_t otm_sgd_run_lp_workspace(void) { return 256 + LP_VM_FLOATS * sizeof(float); }
+// The error flag (256 bytes), then, for k > 128, the cluster's two streamed BF16
+// images of V.
+size_t otm_sgd_run_lp_workspace(void) { return 256 + VIMG_BYTES; }
 
 otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* YC,
                           const float* sA, const float* sB, const float* sC, int64_t n, int64_t k,
@@ -1128,13 +1316,11 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   args.c3 = (float)(alpha0 * alpha0);
   args.kappa = (float)(0.5 * (1.0 + theta));
   otm_status s_;
-  OTM_REQUIRE(!P.vmg || (size_t)P.CL * P.N * 256 <= LP_VM_FLOATS,
-              "otm_sgd_run_lp: master-row scratch too small for this plan");
-  float* vms = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + 256);
+  uint8_t* vimg = static_cast<uint8_t*>(ws) + 256;
   if (fp8)
-    s_ = sym ? launch_tc<true, true>(args, P, st, vms) : launch_tc<true, false>(args, P, st, vms);
+    s_ = sym ? launch_tc<true, true>(args, P, st, vimg) : launch_tc<true, false>(args, P, st, vimg);
   else
-    s_ = sym ? launch_tc<false, true>(args, P, st, vms) : launch_tc<false, false>(args, P, st, vms);
+    s_ = sym ? launch_tc<false, true>(args, P, st, vimg) : launch_tc<false, false>(args, P, st, vimg);
   if (s_ != OTM_OK) return s_;
   int h = 0;
   OTM_CHECK_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1144,23 +1330,18 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
 }
 
 // Batched workspace: header, work list, trial work list, trial V matrices, and
-// the FP32 master rows of the k > 128 group (N x 256 floats for each of at most
-// WIDE_CTAS CTAs).
-constexpr int WIDE_CTAS = 256;
-constexpr size_t WIDE_VM_FLOATS = (size_t)WIDE_CTAS * 64 * 256;
+// for the k > 128 group the streamed V images (VIMG_BYTES for each of at most
+// WIDE_CLUSTERS clusters of at least 4 CTAs).
+constexpr int WIDE_CLUSTERS = 64;
 
-// Clusters of plan P whose FP32 master rows fit the wide scratch.
-static int wide_clusters_cap(const TcPlan& P) {
-  return (int)(WIDE_VM_FLOATS / ((size_t)P.CL * P.N * 256));
-}
-
-static_assert(WIDE_CTAS > 0, "wide scratch");
+// Clusters of plan P whose images fit the wide scratch.
+static int wide_clusters_cap(const TcPlan&) { return WIDE_CLUSTERS; }
 struct BatchedWs {
   int* hdr;
   TcArgs* dev_items;
   TcArgs* trial_items;
   float* scratchV;
-  float* vm_wide;
+  uint8_t* vimg_wide;
 };
 
 static BatchedWs batched_ws(void* ws, size_t ws_bytes, int64_t nitems) {
@@ -1170,14 +1351,15 @@ static BatchedWs batched_ws(void* ws, size_t ws_bytes, int64_t nitems) {
   b.dev_items = w.take<TcArgs>(nitems);
   b.trial_items = w.take<TcArgs>(nitems);
   b.scratchV = w.take<float>((size_t)std::min<int64_t>(nitems, 512) * TC_KMAX * TC_KMAX);
-  b.vm_wide = w.take<float>(WIDE_VM_FLOATS);
+  b.vimg_wide = w.take<uint8_t>((size_t)WIDE_CLUSTERS * VIMG_BYTES);
   return b;
 }
 
 size_t otm_sgd_batched_workspace(int64_t nitems) {
   WorkspaceSize w;
   w.add<int>(64).add<TcArgs>(nitems).add<TcArgs>(nitems).add<float>(
-      (size_t)std::min<int64_t>(nitems, 512) * TC_KMAX * TC_KMAX).add<float>(WIDE_VM_FLOATS);
+      (size_t)std::min<int64_t>(nitems, 512) * TC_KMAX * TC_KMAX)
+      .add<uint8_t>((size_t)WIDE_CLUSTERS * VIMG_BYTES);
   return w.bytes();
 }
 
@@ -1393,8 +1575,8 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
           OTM_CHECK_CUDA(cudaMemsetAsync(hdr + 8, 0, sizeof(int), st));
           OTM_CHECK_CUDA(cudaEventRecord(e0, st));
           otm_status s2 =
-              fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vm_wide)
-                  : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vm_wide);
+              fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vimg_wide)
+                  : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vimg_wide);
           if (s2 != OTM_OK) return s2;
           OTM_CHECK_CUDA(cudaEventRecord(e1, st));
           OTM_CHECK_CUDA(cudaEventSynchronize(e1));
@@ -1418,15 +1600,12 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
     OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pch), "otm_sgd_batched_prepare: no plan");
   if (n_wide > 0)
     OTM_REQUIRE(tc_plan(max_k_wide, true, fp8, chosen_w, &Pw), "otm_sgd_batched_prepare: no plan");
-  {
-    // both launches run the same kernel: its attributes must admit both plans
-    TcPlan Pmax = n_narrow > 0 ? Pch : Pw;
-    if (n_narrow > 0 && n_wide > 0) {
-      Pmax.smem = std::max(Pch.smem, Pw.smem);
-      Pmax.CL = std::max(Pch.CL, Pw.CL);
-    }
-    otm_status s3 = fp8 ? launch_batched<true>(Pmax, dev_items, 0, hdr, 1, st, true, nullptr)
-                        : launch_batched<false>(Pmax, dev_items, 0, hdr, 1, st, true, nullptr);
+  // each group's kernel takes its own plan's attributes
+  for (int grp = 0; grp < 2; ++grp) {
+    if ((grp == 0 ? n_narrow : n_wide) == 0) continue;
+    const TcPlan& Pg = grp == 0 ? Pch : Pw;
+    otm_status s3 = fp8 ? launch_batched<true>(Pg, dev_items, 0, hdr, 1, st, true, nullptr)
+                        : launch_batched<false>(Pg, dev_items, 0, hdr, 1, st, true, nullptr);
     if (s3 != OTM_OK) return s3;
   }
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -1475,9 +1654,9 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
                     plan->grid_clusters_wide <= wide_clusters_cap(P),
                 "otm_sgd_batched_launch: plan does not match this library");
     OTM_TRY(fp8 ? launch_batched<true>(P, dev_items + n_narrow, n_wide, hdr + 2,
-                                       plan->grid_clusters_wide, st, false, bw.vm_wide)
+                                       plan->grid_clusters_wide, st, false, bw.vimg_wide)
                 : launch_batched<false>(P, dev_items + n_narrow, n_wide, hdr + 2,
-                                        plan->grid_clusters_wide, st, false, bw.vm_wide));
+                                        plan->grid_clusters_wide, st, false, bw.vimg_wide));
   }
   return OTM_OK;
 }

@@ -104,11 +104,36 @@ def test_tc_gradient_beyond_128_components(otm, k, b, prec_name, tol):
     assert err < tol, err
 
 
-def test_tc_three_views_beyond_128_rejected(otm):
-    k, n = 160, 64
-    Y = torch.zeros(n, k, device="cuda")
-    q = [otm.quantize_samples(Y + i, otm.PREC_BF16) for i in range(3)]
-    V = torch.zeros(k, k, device="cuda")
-    yb = torch.zeros(3, k, dtype=torch.float64, device="cuda")
-    with pytest.raises(otm.OtmError):
-        otm.sgd_run_lp(V, q[0], q[1], q[2], yb, None, 1, 32, 1e-2, 1.0, 1.0, otm.PREC_BF16)
+@pytest.mark.parametrize("prec_name,tol", [("PREC_BF16", 2e-2), ("PREC_FP8", 6e-2)])
+def test_tc_three_views_beyond_128(otm, prec_name, tol):
+    """k > 128 with three distinct views (16-CTA cluster, one sample stage of
+    three views): one step against the oracle's implicit gradient."""
+    err = _grad_err(otm, getattr(otm, prec_name), 160, 512, False, 1.0, 41)
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("prec_name,tol,sym", [("PREC_BF16", 2e-2, True), ("PREC_FP8", 5e-2, True),
+                                               ("PREC_BF16", 2e-2, False)])
+def test_tc_run_beyond_128_tracks_oracle(otm, prec_name, tol, sym):
+    """k > 128 over twelve steps with a partial last minibatch: the cluster's
+    shared V image alternates between two global buffers, read back for the
+    Gram term of every step.  beta0 = 0.2 moves V by about 60 %; a Gram term
+    one step stale would leave the iterate about 9 % from the oracle's, 1 %
+    random gradient noise about 0.3 %."""
+    prec = getattr(otm, prec_name)
+    k, n, b, epochs = 160, 1500, 256, 2
+    g = np.random.default_rng(13)
+    Y = (g.standard_normal((n, k)) * 0.3 + 0.1).astype(np.float32)
+    Ys = [Y] * 3 if sym else [Y, (Y + 0.05 * g.standard_normal(Y.shape)).astype(np.float32),
+                              Y[::-1].copy()]
+    yb = np.stack([Z.astype(np.float64).mean(axis=0) for Z in Ys])
+    perm = synth.epoch_permutations(15, n, epochs)
+    V0 = synth.haar_orthonormal(16, k)
+    qs = [otm.quantize_samples(_dev(Z), prec) for Z in (Ys[:1] if sym else Ys)]
+    if sym:
+        qs = qs * 3
+    Vd = _dev(V0.T.copy().astype(np.float32))
+    otm.sgd_run_lp(Vd, qs[0], qs[1], qs[2], _dev(yb), _dev(perm), epochs, b, 0.2, 1.0, 1.0, prec)
+    torch.cuda.synchronize()
+    Vo, _ = ostgd.sgd_run(V0, *Ys, tuple(yb), perm, b, 0.2, 1.0, 1.0)
+    assert rel(to_np(Vd).T, Vo) < tol
