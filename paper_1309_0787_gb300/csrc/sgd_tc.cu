@@ -208,15 +208,19 @@ __device__ __forceinline__ int tile_sample(int j) {
 // minibatch), with the samples' scales.  One warp instruction copies four
 // consecutive 16-byte groups (64 contiguous bytes) of each of eight samples, so
 // that it touches eight rows in global memory and writes four conflict-free
-// 128-byte rows of the K-major image.  raw[j]: the permutation entry of sample
-// tile_sample(j) (-1 outside the minibatch), loaded one issue earlier so that
-// its latency is hidden.
+// 128-byte rows of the K-major image.  Only the coordinates the first product
+// reads (k rounded up to its K step) are copied: the second product's rows for
+// coordinates beyond k feed update rows that are never formed.  raw[j]: the
+// permutation entry of sample tile_sample(j) (-1 outside the minibatch), loaded
+// one issue earlier so that its latency is hidden.
 template <bool FP8, bool SYM>
 __device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, uint8_t* smem,
                                           float* F, const int (&raw)[2], int stage) {
   constexpr int ES = FP8 ? 1 : 2;
   const int lane = threadIdx.x & 31;
   const int s8 = lane & 7, c4 = lane >> 3;
+  constexpr int KSTEP = FP8 ? 32 : 16;
+  const int kload = (a.k + KSTEP - 1) / KSTEP * KSTEP;  // coordinates read by the first product
   const int nq = L.CR / 4;  // 64-byte quarters of a sample row
   uint8_t* Ys = smem + (size_t)stage * L.y_stage;
 #pragma unroll
@@ -229,6 +233,7 @@ __device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, ui
       for (int m = 0; m < nq; ++m) {
         const int rg = 4 * m + c4;
         const int c0 = rg * (16 / ES);
+        if (c0 >= kload) break;
         const bool in = row >= 0 && c0 < a.ldq;
         const uint8_t* src = in ? Yg + ((size_t)row * a.ldq + c0) * ES : Yg;
         cp_async16(dst + ((size_t)rg << 7), src, in ? 16u : 0u);
