@@ -20,6 +20,15 @@
 // is hidden.  One thread issues every MMA; completion is signalled by
 // tcgen05.commit to mbarriers whose waits are bounded.
 //
+// k > 128 (256 padded coordinates, the WIDE instantiation): a CTA keeps only
+// its own rows of the BF16 image on chip and publishes them after its update
+// to one of two image buffers per cluster in global memory (step s reads
+// buffer s & 1 and writes the other); once the step's last tile is consumed
+// the whole image is copied into the sample stages for the Gram products, and
+// the next step's tiles are issued only after those.  Its FP32 master rows
+// live in tensor memory (lane = coordinate within a 128-row block, one column
+// per owned component), and a_A, a_B are summed on the CUDA cores.
+//
 // Scaling: samples are stored quantised with one scale per sample (FP8; BF16
 // stores scale 1); the owned rows of V are re-quantised every step with one
 // scale per component (FP8); B with one scale per component per 128-sample
