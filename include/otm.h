@@ -356,10 +356,11 @@ typedef struct otm_problem {
 
 /* A prepared batch: filled by otm_sgd_batched_prepare, read by the launch. */
 typedef struct otm_batch_plan {
-  int32_t nitems;         /* chains = sum of restarts */
+  int32_t nitems;         /* work items: restarts, with those of a problem with k <= 64
+                             stacked floor(128 / k) to an item */
   int32_t cluster;        /* CTAs per chain (k <= 128), chosen by the autotuner or given */
   int32_t precision;
-  int32_t max_k;          /* largest k <= 128 */
+  int32_t max_k;          /* most components of an item with k <= 128 (stacked: R k) */
   int32_t grid_clusters;  /* clusters in the persistent grid (k <= 128) */
   int32_t nitems_wide;    /* chains with 128 < k <= 256 (second launch) */
   int32_t grid_clusters_wide;
@@ -371,10 +372,15 @@ typedef struct otm_batch_plan {
 } otm_batch_plan;
 
 /*
- * otm_sgd_batched_prepare -- expands the problems into chains (one per
- * restart), orders them by cost (steps x (b k^2 + k^3), longest first) and
+ * otm_sgd_batched_prepare -- expands the problems into work items, orders them
+ * by cost (steps x (b c k + c^2 k) for c components, longest first) and
  * uploads the work list to the workspace (otm_sgd_batched_workspace(chains)
- * bytes, kept alive until the last launch).  cluster = 0 runs the autotuner:
+ * bytes, chains = the sum of restarts, kept alive until the last launch).  An
+ * item is one restart, or for k <= 64 up to floor(128 / k) restarts of one
+ * problem run together as one chain of R k components: every sample tile is
+ * loaded and multiplied once for all of them, each keeps its own Gram term
+ * (H = V^T V is masked to the restart's block), and the results equal R
+ * separate runs up to FP32 summation order.  cluster = 0 runs the autotuner:
  * a short trial launch (at most 4 steps per chain, on scratch V) for each
  * cluster size whose shared-memory footprint fits the largest k; the fastest
  * is kept (cached per precision, largest k and chain count).  Synchronises
@@ -382,9 +388,9 @@ typedef struct otm_batch_plan {
  *
  * otm_sgd_batched_launch -- one persistent launch running every chain with
  * k <= 128 (and, if the plan has any, a second one for 128 < k <= 256, whose
- * chains use 4- to 16-CTA clusters and keep their FP32 master rows and the
- * cluster's two BF16 images of V in the workspace instead of shared memory,
- * chosen by the same trial): as many clusters as fit on the GPU take chains
+ * chains use 4- to 16-CTA clusters, chosen by the same trial, keep their FP32
+ * master rows in tensor memory and exchange the BF16 image of V through two
+ * buffers per cluster in the workspace): as many clusters as fit on the GPU take chains
  * from the work list until it is empty.  Asynchronous and free of host synchronisation, so it can
  * be captured in a CUDA graph.  otm_sgd_batched_check reads the plan's
  * timeout flag (synchronises; OTM_ETIMEOUT if a tensor-core wait expired).

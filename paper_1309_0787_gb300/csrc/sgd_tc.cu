@@ -87,6 +87,8 @@ struct TcArgs {
   int* err;
   int64_t n, b, spe, total_steps, snapshot_every;
   int k, ldq;
+  int nc;             // components: k, or R k for R restarts of one problem stacked
+                      // (their V matrices contiguous from V on, the Gram term per restart)
   double beta0;
   float c1, c2, c3, kappa;
 };
@@ -300,17 +302,18 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   const int q = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int qd = warp & 3, hf = warp >> 2;
-  const int k = a.k;
+  const int k = a.k;    // coordinates
+  const int nc = a.nc;  // components
   constexpr int KPc = WIDE ? 256 : 128;  // padded coordinates / components
   constexpr int MB = KPc / 128;           // 128-row blocks
   if ((k > 128) != WIDE) {  // launched for the other width: report, leave V as it is
     if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
     return;
   }
-  const int N = own_cols(k, CL);
+  const int N = own_cols(nc, CL);
   const TcLayout L = tc_layout(N, SYM, ES, NS, dbl, KPc);
   const int own_lo = q * N;
-  const bool active = own_lo < k;
+  const bool active = own_lo < nc;
   const int nch = N / 16;
   float* F = reinterpret_cast<float*>(smem + L.off_f);
   float* Vm = F + L.vm;  // owned rows [N][KPc] (k <= 128)
@@ -352,7 +355,8 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   // column colVm + mbk N + i = owned component i
   const uint32_t colVm = colGGb + (uint32_t)(MB * N);
   const int ks1 = (k + KSTEP - 1) / KSTEP;  // coordinate steps of the first product
-  const int kg16 = (k + 15) / 16;           // 16-steps of the Gram products
+  const int kg16 = (k + 15) / 16;           // 16-steps over coordinates (H = V^T V_own)
+  const int kgc = (nc + 15) / 16;           // 16-steps over components (V (H o H))
   const size_t own_off = ((size_t)(own_lo >> 3) * L.CRb) << 7;
 
   // ---- initial state: owned FP32 rows, BF16 image of all rows, means ----
@@ -361,7 +365,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
   } else {
     for (int idx = tid; idx < N * KPc; idx += TC_THREADS) {
       const int i = idx / KPc, r = idx % KPc, c = own_lo + i;
-      Vm[idx] = (c < k && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
+      Vm[idx] = (c < nc && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
     }
   }
   for (int idx = tid; idx < (WIDE ? N : KPc) * L.CRb; idx += TC_THREADS) {
@@ -371,7 +375,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
 #pragma unroll
     for (int z = 0; z < 8; ++z) {
       const int r = rg * 8 + z;
-      v[z] = (c < k && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
+      v[z] = (c < nc && r < k) ? a.V[(int64_t)c * k + r] : 0.f;
     }
     uint4 w;
     w.x = pack_bf16(v[0], v[1]);
@@ -425,7 +429,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     for (int i = warp; i < N; i += TC_THREADS / 32) {
       float m = 0.f;
       if (WIDE) {
-        if (own_lo + i < k)
+        if (own_lo + i < nc)
           for (int r = lane; r < k; r += 32)
             m = fmaxf(m, fabsf(a.V[(int64_t)(own_lo + i) * k + r]));
       } else {
@@ -485,14 +489,14 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
           if (r < k) {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-              if (own_lo + c0 + j < k) dst[(int64_t)(own_lo + c0 + j) * k + r] = x[j];
+              if (own_lo + c0 + j < nc) dst[(int64_t)(own_lo + c0 + j) * k + r] = x[j];
           }
         }
       return;
     }
     for (int idx = tid; idx < N * k; idx += TC_THREADS) {
       const int i = idx / k, r = idx % k;
-      if (own_lo + i < k) dst[(int64_t)(own_lo + i) * k + r] = Vm[i * KPc + r];
+      if (own_lo + i < nc) dst[(int64_t)(own_lo + i) * k + r] = Vm[i * KPc + r];
     }
   };
 
@@ -821,7 +825,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         for (int c16 = tid; c16 < (int)(img_bytes >> 4); c16 += TC_THREADS) {
           const size_t off = (size_t)c16 << 4;
           const int comp = (int)((off >> 7) / L.CRb) * 8 + (int)((off >> 4) & 7);
-          const bool in = comp < k;
+          const bool in = comp < nc;
           cp_async16(Vfull + off, in ? src + off : src, in ? 16u : 0u);
         }
         cp_async_commit();
@@ -863,12 +867,18 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       wait_mb(4);
       for (int mbk = 0; mbk < MB; ++mbk) {
         const int j = mbk * 128 + 32 * qd + lane;
+        const int rj = j / k;  // restart of component j (stacked restarts)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           if (c < nch) {
             const int c0 = 16 * c + 8 * hf;
             float x[8];
             tmem_ld8(tmem + lane_base + (uint32_t)(mbk * N + c0), x);
+            if (nc > k) {  // the Gram term couples only components of the same restart
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj)
+                if ((own_lo + c0 + jj) / k != rj) x[jj] = 0.f;
+            }
             uint4 u;
             u.x = pack_bf16(x[0] * x[0], x[1] * x[1]);
             u.y = pack_bf16(x[2] * x[2], x[3] * x[3]);
@@ -888,7 +898,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         const uint32_t id = make_idesc(1, 1, 1, 128, (uint32_t)N);
         for (int mbk = 0; mbk < MB; ++mbk) {  // coordinates in blocks of 128 (2048 bytes)
           const uint64_t dA = sdesc(Vg + (size_t)mbk * 2048, (uint32_t)L.CRb * 128, 128);
-          for (int ks = 0; ks < kg16; ++ks)
+          for (int ks = 0; ks < kgc; ++ks)
             mma<false>(tmem + colGGb + (uint32_t)(mbk * N), dA + (uint64_t)(2 * L.CRb * 8 * ks),
                        dB + (uint64_t)(2 * L.CBh * 8 * ks), id, ks > 0 ? 1u : 0u);
         }
@@ -923,7 +933,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int i = c0 + j, comp = own_lo + i;
-              if (comp < k) {
+              if (comp < nc) {
                 float vnew = 0.f;
                 if (r < k) {
                   const float s_i = spw[i] + spw[N + i] + spw[2 * N + i] + spw[3 * N + i];
@@ -965,7 +975,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         vsc[tid] = m > 0.f ? m / QMAX : 1.f;
       }
       if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0)
-        write_rows(a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)k * k);
+        write_rows(a.V_snap + ((s + 1) / a.snapshot_every - 1) * (int64_t)nc * k);
       __syncthreads();
       if (FP8) build_vq();
       if (WIDE) publish_own(vimg_cl + (size_t)((s + 1) & 1) * img_bytes);
@@ -975,7 +985,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     if (CL > 1 && !WIDE) {
       if (!dbl) cluster.sync();  // single image: every CTA has finished reading it
       if (active) {
-        const int nrow = min(N, k - own_lo);
+        const int nrow = min(N, nc - own_lo);
         for (int idx = tid; idx < nrow * L.CRb; idx += TC_THREADS) {
           const int i = idx / L.CRb, rg = idx % L.CRb, comp = own_lo + i;
           const size_t off = (((size_t)(comp >> 3) * L.CRb + rg) << 7) + ((comp & 7) << 4);
@@ -1324,6 +1334,7 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   args.snapshot_every = snapshot_every;
   args.k = (int)k;
   args.ldq = (int)((k + 15) & ~15);
+  args.nc = (int)k;
   args.beta0 = beta0;
   args.c1 = (float)((alpha0 + 1.0) * (alpha0 + 2.0) / 2.0);
   args.c2 = (float)(alpha0 * (alpha0 + 1.0) / 2.0);
@@ -1398,7 +1409,12 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
                 "otm_sgd_batched_prepare: problem %d invalid (need 1 <= k <= %d, n, b, "
                 "restarts >= 1, non-null Yq, ybar3, V)", p, TC_KMAX);
     max_k = std::max(max_k, (int)P.k);
-    for (int64_t r = 0; r < P.restarts; ++r) {
+    // restarts of a problem with k <= 64 share samples, permutation and schedule: up to
+    // floor(128 / k) of them run as one chain of R k components, so that each sample tile
+    // is loaded and multiplied once for all of them (the Gram term stays per restart)
+    const int64_t rs = P.k <= 64 ? 128 / P.k : 1;
+    for (int64_t r = 0; r < P.restarts; r += rs) {
+      const int64_t cnt = std::min<int64_t>(rs, P.restarts - r);
       TcArgs a;
       a.YA = a.YB = a.YC = static_cast<const uint8_t*>(P.Yq);
       a.sA = a.sB = a.sC = P.scales;
@@ -1414,13 +1430,15 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
       a.snapshot_every = 0;
       a.k = (int)P.k;
       a.ldq = (int)((P.k + 15) & ~15);
+      a.nc = (int)(cnt * P.k);
       a.beta0 = P.beta0;
       a.c1 = (float)((P.alpha0 + 1.0) * (P.alpha0 + 2.0) / 2.0);
       a.c2 = (float)(P.alpha0 * (P.alpha0 + 1.0) / 2.0);
       a.c3 = (float)(P.alpha0 * P.alpha0);
       a.kappa = (float)(0.5 * (1.0 + P.theta));
       items.push_back(a);
-      cost.push_back((double)a.total_steps * ((double)P.b * P.k * P.k + (double)P.k * P.k * P.k));
+      cost.push_back((double)a.total_steps *
+                     ((double)P.b * a.nc * P.k + (double)a.nc * a.nc * P.k));
     }
   }
   const int nitems = (int)items.size();
@@ -1441,12 +1459,12 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   for (int i = 0; i < nitems; ++i) sorted[i] = items[order[i]];
   int n_wide = 0, max_k_wide = 0;
   max_k = 0;
-  for (const TcArgs& a : sorted) {
+  for (const TcArgs& a : sorted) {  // plans are sized by components (k <= 128: up to 128)
     if (a.k > 128) {
       ++n_wide;
-      max_k_wide = std::max(max_k_wide, a.k);
+      max_k_wide = std::max(max_k_wide, a.nc);
     } else {
-      max_k = std::max(max_k, a.k);
+      max_k = std::max(max_k, a.nc);
     }
   }
   const int n_narrow = nitems - n_wide;

@@ -41,6 +41,13 @@ def _problem(otm, seed, k, n, b, epochs, restarts, beta0, prec, sigma=0.05):
             "epochs": epochs, "b": b, "beta0": beta0, "theta": 1.0, "alpha0": 0.0}
 
 
+def _items(k, restarts):
+    """Work items of one problem: restarts of a problem with k <= 64 run
+    floor(128 / k) to an item."""
+    per = 128 // k if k <= 64 else 1
+    return -(-restarts // per)
+
+
 def _single(otm, p, r, prec):
     Vd = _dev(p["V0"][r].T.copy().astype(np.float32))
     q = (p["Yq"], p["scales"])
@@ -74,7 +81,7 @@ def test_batched_mixed_sizes_autotuned(otm, prec_name):
              (24, 128, 2048, 1024, 2, 1)]
     probs = [_problem(otm, s, k, n, b, e, r, 5e-3, prec) for s, k, n, b, e, r in specs]
     batch = otm.SgdBatch(probs, prec)
-    assert batch.nitems == sum(s[-1] for s in specs)
+    assert batch.nitems == sum(_items(s[1], s[-1]) for s in specs)
     assert batch.cluster in (1, 2, 4, 8, 16)
     batch.launch()
     batch.check()
@@ -86,6 +93,26 @@ def test_batched_mixed_sizes_autotuned(otm, prec_name):
             assert rel(to_np(p["V"][r]), to_np(Vs)) < tol
 
 
+@pytest.mark.parametrize("k,restarts", [(16, 8), (24, 3)])
+def test_batched_stacked_restarts_equal_single(otm, k, restarts):
+    """Restarts of one problem stacked into one chain of R k components (one
+    tile load and one pair of products for all of them, the Gram term masked to
+    each restart's block) give each restart's single-chain result up to FP32
+    summation order; with k = 24 the restart boundaries fall inside 8-component
+    groups."""
+    prec = otm.PREC_BF16
+    p = _problem(otm, 101 + k, k, 1500, 256, 2, restarts, 5e-3, prec)
+    batch = otm.SgdBatch([p], prec, cluster=1)
+    assert batch.nitems == 1
+    batch.launch()
+    batch.check()
+    for r in range(restarts):
+        Vs = _single(otm, p, r, prec)
+        torch.cuda.synchronize()
+        a, s = to_np(p["V"][r]), to_np(Vs)
+        assert np.abs(a - s).max() <= 1e-5 * np.abs(s).max(), (r, np.abs(a - s).max())
+
+
 def test_batched_two_groups_beyond_128(otm):
     """Problems with k <= 128 and k > 128 in one batch (two persistent launches):
     every chain matches its own single-chain run."""
@@ -93,7 +120,7 @@ def test_batched_two_groups_beyond_128(otm):
     specs = [(71, 48, 800, 128, 2, 2), (72, 200, 1024, 256, 1, 2), (73, 256, 1024, 512, 1, 1)]
     probs = [_problem(otm, s, k, n, b, e, r, 5e-3, prec) for s, k, n, b, e, r in specs]
     batch = otm.SgdBatch(probs, prec)
-    assert batch.nitems == 5 and batch.plan.nitems_wide == 3
+    assert batch.nitems == 4 and batch.plan.nitems_wide == 3
     batch.launch()
     batch.check()
     for p in probs:
