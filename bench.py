@@ -419,9 +419,11 @@ def run_batched(args):
     """Whitened orthogonal-tensor problems (y = w_h^{-1/2} u_h + sigma eps, alpha0 = 0),
     k ~ U{16, 32, 64, 128, 256}, b = 2^U{6..12}, a pool of 4 b samples per problem,
     8 epochs, `restarts` Haar-random starts each; all chains in one persistent
-    BF16 tensor-core launch per group (k <= 128; k = 256 with 4- to 16-CTA clusters),
-    captured in a CUDA graph.  Flops per step of one
-    chain (symmetric views): 2 k^2 b (A = Y V) + 2 k^2 b (Y^T B) + 4 k^3 (Gram).
+    BF16 tensor-core launch per group (k <= 128, the restarts of a problem with
+    k <= 64 stacked into one chain; k = 256 with 4- to 16-CTA clusters), captured in
+    a CUDA graph.  Algorithmic flops per step of one chain (symmetric views, counted
+    per restart whether stacked or not): 2 k^2 b (A = Y V) + 2 k^2 b (Y^T B) + 4 k^3
+    (Gram).
     The plain FP32 kernel, looped chain by chain, is timed on the first restart of
     the first problems with k <= 128 (its limit) and extrapolated per sample."""
     import torch
