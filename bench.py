@@ -46,7 +46,7 @@ FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 f
 # DRAM bytes (read + write) per launch of the STGD kernel on this workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command; to be reset to None
 # whenever the kernel changes
-SGD_KERNEL_TRAFFIC = 6989568
+SGD_KERNEL_TRAFFIC = 7125760
 
 
 def make_inputs(cfg, rank=0):

@@ -29,7 +29,7 @@ namespace otm {
 namespace {
 
 constexpr int GT = 256;       // threads per CTA
-constexpr int G_SAMPLES = 6;  // target samples per CTA per step
+constexpr int G_SAMPLES = 8;  // target samples per CTA per step (k = 100, b = 1024: 128 CTAs)
 constexpr int G_SMAX = 32;    // at most this many samples per CTA per step
 constexpr int G_KMAX = 128;
 constexpr int G_MAXGRID = 160;  // CTAs at most (the owners' sums load G / 8 partials at once)
