@@ -180,6 +180,81 @@ __global__ void __launch_bounds__(256) gemm_nn_small_kernel(
   }
 }
 
+// The same product for m and p multiples of 4 and p <= 128 (the whitening's shapes):
+// a CTA computes 32 rows x all p columns (so out may alias A), each thread a 4 x 4
+// block read as float4 from K-major shared tiles, and the next 32-wide K chunk is
+// loaded into registers while the current one is multiplied.
+constexpr int T_R = 32, T_K = 32, T_P = 128;
+__global__ void __launch_bounds__(256) gemm_nn_tile_kernel(
+    const float* A, int64_t rows, int64_t m, const float* __restrict__ C, int64_t p, float* out,
+    const double* __restrict__ r1_u, const double* __restrict__ r1_v, double r1_alpha,
+    const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ __align__(16) float As[T_K][T_R + 4];  // As[kk][row]
+  __shared__ __align__(16) float Cs[T_K][T_P + 4];  // Cs[kk][col]
+  const int tid = threadIdx.x;
+  const int ty = tid >> 5, tx = tid & 31;  // rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3
+  const int64_t r0 = (int64_t)blockIdx.x * T_R;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int ar = tid >> 3, ak = (tid & 7) * 4;  // A chunk: row ar, K columns ak .. ak + 3
+  float4 ra, rc[4];
+  auto load = [&](int64_t k0) {
+    const int64_t gr = r0 + ar, gk = k0 + ak;
+    ra = (gr < rows && gk < m) ? *reinterpret_cast<const float4*>(A + gr * m + gk) : zero;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {  // C chunk: K row ck, columns c4 .. c4 + 3
+      const int idx = tid + 256 * i, ck = idx >> 5, c4 = (idx & 31) * 4;
+      const int64_t gc = k0 + ck;
+      rc[i] = (gc < m && c4 < p) ? __ldg(reinterpret_cast<const float4*>(C + gc * p + c4)) : zero;
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[q][j] = 0.f;
+  load(0);
+  for (int64_t k0 = 0; k0 < m; k0 += T_K) {
+    As[ak][ar] = ra.x;
+    As[ak + 1][ar] = ra.y;
+    As[ak + 2][ar] = ra.z;
+    As[ak + 3][ar] = ra.w;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = tid + 256 * i;
+      *reinterpret_cast<float4*>(&Cs[idx >> 5][(idx & 31) * 4]) = rc[i];
+    }
+    __syncthreads();
+    if (k0 + T_K < m) load(k0 + T_K);
+#pragma unroll 8
+    for (int kk = 0; kk < T_K; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+      const float4 c = *reinterpret_cast<const float4*>(&Cs[kk][4 * tx]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[q][j] = fmaf(av[q], cv[j], acc[q][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t r = r0 + 4 * ty + q;
+    if (r >= rows) continue;
+    const double u = r1_u ? r1_u[r] * r1_alpha : 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t c = 4 * tx + j;
+      if (c < p) {
+        float v = acc[q][j];
+        if (r1_u) v = (float)((double)v - u * r1_v[c]);
+        out[r * p + c] = v;
+      }
+    }
+  }
+}
+
 // out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64), FP64 FMAs.
 constexpr int D_R = 32, D_C = 32, D_K = 32;
 __global__ void __launch_bounds__(256) gemm_nn_f64_kernel(const float* __restrict__ A,
@@ -1332,8 +1407,14 @@ otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const float* C
                          cudaStream_t st, const int* skip) {
   if (p > NN_PMAX) return set_error(OTM_EINVAL, "gemm_nn_small: p=%lld > %d", (long long)p, NN_PMAX);
   if (rows == 0 || p == 0) return OTM_OK;
-  gemm_nn_small_kernel<<<(unsigned)((rows + NN_R - 1) / NN_R), 256, 0, st>>>(
-      A, rows, m, C, p, out, r1_u, r1_v, r1_alpha, skip);
+  const bool a16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0;
+  if (m % 4 == 0 && p % 4 == 0 && p <= T_P && m >= 1 && a16) {
+    gemm_nn_tile_kernel<<<(unsigned)((rows + T_R - 1) / T_R), 256, 0, st>>>(
+        A, rows, m, C, p, out, r1_u, r1_v, r1_alpha, skip);
+  } else {
+    gemm_nn_small_kernel<<<(unsigned)((rows + NN_R - 1) / NN_R), 256, 0, st>>>(
+        A, rows, m, C, p, out, r1_u, r1_v, r1_alpha, skip);
+  }
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }

@@ -106,7 +106,8 @@ def test_pairs_apply(otm):
 # dense kernels of the whitening
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("rows,m,cond", [(5000, 120, 1e2), (500, 30, 1e5), (161, 160, 10.0),
-                                         (40, 1, 1.0), (3000, 77, 1e6)])
+                                         (40, 1, 1.0), (3000, 77, 1e6), (2000, 64, 1e3),
+                                         (1000, 128, 1e2), (33, 4, 1.0)])
 def test_orthonormalize(otm, rows, m, cond):
     g = np.random.default_rng(9)
     U, _ = np.linalg.qr(g.standard_normal((rows, m)))
