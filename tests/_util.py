@@ -22,6 +22,7 @@ def to_np(t):
 
 
 def grad_rel_err(G, G64, V, theta, kappa_gram_data):
-    """Survey tolerance metric: ||G - G64||_F / (||kappa G_gram||_F + ||G_data||_F)."""
+    """Normwise error of a gradient relative to its two terms:
+    ||G - G64||_F / (||kappa G_gram||_F + ||G_data||_F)."""
     gram, data = kappa_gram_data
     return float(np.linalg.norm(G - G64) / (np.linalg.norm(gram) + np.linalg.norm(data)))

@@ -93,7 +93,7 @@ def test_batched_mixed_sizes_autotuned(otm, prec_name):
             assert rel(to_np(p["V"][r]), to_np(Vs)) < tol
 
 
-@pytest.mark.parametrize("k,restarts", [(16, 8), (24, 3)])
+@pytest.mark.parametrize("k,restarts", [(16, 8), (24, 3), (16, 10)])
 def test_batched_stacked_restarts_equal_single(otm, k, restarts):
     """Restarts of one problem stacked into one chain of R k components (one
     tile load and one pair of products for all of them, the Gram term masked to
@@ -103,7 +103,7 @@ def test_batched_stacked_restarts_equal_single(otm, k, restarts):
     prec = otm.PREC_BF16
     p = _problem(otm, 101 + k, k, 1500, 256, 2, restarts, 5e-3, prec)
     batch = otm.SgdBatch([p], prec, cluster=1)
-    assert batch.nitems == 1
+    assert batch.nitems == _items(k, restarts)  # (16, 10): items of 8 and 2 restarts
     batch.launch()
     batch.check()
     for r in range(restarts):

@@ -194,7 +194,7 @@ def test_sgd_step_gradient(otm, k, b, sym, a0):
     G, gram, data = _grad_parts(V0.astype(np.float64), *[Y.astype(np.float64) for Y in Ys],
                                 tuple(yb), theta, a0)
     err = np.linalg.norm(Gk - G) / (np.linalg.norm(gram) + np.linalg.norm(data))
-    # FP32 path, survey tolerance 1e-5 (normwise, relative to the two gradient terms)
+    # FP32 path, tolerance 1e-5 (normwise, relative to the two gradient terms)
     assert err < 1e-5, err
 
 
