@@ -223,6 +223,8 @@ def run_gpu(args, rank, world, local_rank):
     cfg = dict(CFG)
     host = make_inputs(cfg, rank)
     path = GpuPath(otm, torch, cfg, host, dev)
+    otm.sgd_set_form({"auto": otm.SGD_FORM_AUTO, "cluster": otm.SGD_FORM_CLUSTER,
+                      "grid": otm.SGD_FORM_GRID}[args.sgd_form])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     samples = cfg["n_per"] * cfg["epochs"]
     flops, nsteps = sgd_flops(cfg)
@@ -299,16 +301,19 @@ def run_gpu(args, rank, world, local_rank):
                    "theta": cfg["theta"], "beta0": cfg["beta0"],
                    "nnz": [int(host[x].nnz) for x in ("G_XA", "G_XB", "G_XC")],
                    "l2": "flushed between timed steps (256 MiB write)",
+                   "sgd_form": args.sgd_form,
                    "parallelism": "replicas" if world > 1 else "single"},
         "breakdown_ms": {"whiten_project_mean": statistics.mean(pre_ms),
                          "sgd_run": statistics.mean(sgd_ms),
                          "unwhiten": statistics.mean(step_ms) - statistics.mean(pre_ms)
                          - statistics.mean(sgd_ms),
                          "wall_per_step": 1e3 * wall / args.steps},
-        "roofline": {"kernel": "sgd_grid_kernel (one cooperative launch = all 100 STGD steps)",
+        "roofline": {"kernel": ("sgd_cluster_kernel (one 16-CTA cluster launch = all 100 STGD "
+                                "steps)" if args.sgd_form == "cluster" else
+                                "sgd_grid_kernel (one cooperative launch = all 100 STGD steps)"),
                      "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
-                     "traffic": SGD_KERNEL_TRAFFIC,
+                     "traffic": None if args.sgd_form == "cluster" else SGD_KERNEL_TRAFFIC,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "algorithmic_flops_per_launch": flops},
         "e2e": {"value": world * samples * n_e2e / e2e_t, "unit": UNIT,
@@ -316,6 +321,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    otm.sgd_set_form(otm.SGD_FORM_AUTO)  # the full-batch reference needs the cluster form
     line["time_to_1e-3"] = convergence(otm, torch, path, cfg, statistics.mean(sgd_ms) / nsteps)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(cfg, host)
@@ -730,6 +736,8 @@ def main():
     ap.add_argument("--restarts", type=int, default=8)
     ap.add_argument("--cluster", type=int, default=0,
                     help="batched: CTAs per chain (0 = autotune)")
+    ap.add_argument("--sgd-form", default="auto", choices=["auto", "cluster", "grid"],
+                    help="mmsb: form of the FP32 STGD kernel in the pipeline (auto = grid here)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
