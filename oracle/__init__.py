@@ -16,6 +16,9 @@ Modules and the part of the paper each follows:
               stochastic update), Appendix A (gradient, shift operator).
   post     -- Section 3.3 Lemma 4 (eigenvalues, unwhitening, alpha estimate),
               plus the reconstruction error used to measure convergence.
+  community-- Section 3.3 Lemma 4, community case (membership Pi_hat,
+              thresholding) and the validation section (p-value graph,
+              recovery ratio, average error).
   warmstart-- tensor sketches T(I, I, theta_j) and the warm-start MLP
               (forward, backward, Gram-Schmidt), not in the paper.
 
@@ -27,4 +30,4 @@ other than itself (brute-force counts, closed forms, library routines, finite
 differences, exact recovery).  The paper's real-dataset tables are not
 reproduced (their data are absent): parity unpinned for those numbers only.
 """
-from . import moments, whiten, stgd, post, warmstart  # noqa: F401
+from . import moments, whiten, stgd, post, community, warmstart  # noqa: F401
