@@ -8,7 +8,9 @@ p = 0.1 within / q = 0.005 across (Bernoulli), three CSR blocks X->A, B, C.
   whiten (randomised, oversampling 20, 2 power iterations, FP64 eig)
   -> project the three views -> means -> STGD, minibatch 1,024,
   beta_t = 1e-2/sqrt(t), theta = 1, 20 epochs (100 steps, one persistent
-  launch) -> unwhiten.
+  launch) -> unwhiten -> membership of the X nodes (Lemma 4, community case).
+After the timed region the membership is validated against the generator's
+ground truth by p-value testing (recovery ratio, average error).
 Metric: whitened samples processed by the SGD per second of whole-path time
 (100,000 samples per step).  Inputs are resident in HBM before timing; the
 L2 is flushed (256 MiB write) between timed steps.  ``e2e`` repeats the
@@ -47,6 +49,7 @@ FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 f
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command; to be reset to None
 # whenever the kernel changes
 SGD_KERNEL_TRAFFIC = 7125760
+PVALUE_THRESHOLD = 0.01   # significance level of the paired p-value test
 
 
 def make_inputs(cfg, rank=0):
@@ -57,7 +60,8 @@ def make_inputs(cfg, rank=0):
             "S_pairs": synth.gaussian(s + 1, cfg["n_per"], kt),
             "S_w": synth.gaussian(s + 2, cfg["n_per"], kt),
             "perm": synth.epoch_permutations(s + 3, cfg["n_per"], cfg["epochs"]),
-            "V0": synth.haar_orthonormal(s + 4, cfg["k"])}
+            "V0": synth.haar_orthonormal(s + 4, cfg["k"]),
+            "Pi_X": g["Pi"]["X"]}
 
 
 def sgd_flops(cfg, views=3):
@@ -109,6 +113,7 @@ class GpuPath:
         if ev:
             ev["s1"].record()
         out = otm.unwhiten(V, wh["Q"], wh["Cp"], c["theta"], False)
+        out["Pi_hat"] = otm.membership(YA, V, c["theta"])
         return out
 
 
@@ -268,7 +273,8 @@ def run_gpu(args, rank, world, local_rank):
                for nm in ("S_pairs", "S_w", "perm", "V0"))
     res_host = torch.empty(cfg["n_per"], cfg["k"], dtype=torch.float64).pin_memory()
     lam_host = torch.empty(cfg["k"], dtype=torch.float64).pin_memory()
-    d2h = res_host.numel() * 8 + lam_host.numel() * 8
+    pi_host = torch.empty(cfg["k"], cfg["n_per"], dtype=torch.float32).pin_memory()
+    d2h = res_host.numel() * 8 + lam_host.numel() * 8 + pi_host.numel() * 4
     e_start = torch.cuda.Event(enable_timing=True)
     e_end = torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
@@ -279,11 +285,18 @@ def run_gpu(args, rank, world, local_rank):
         out = path.step()
         res_host.copy_(out["comps"], non_blocking=True)
         lam_host.copy_(out["lambda"], non_blocking=True)
+        pi_host.copy_(out["Pi_hat"], non_blocking=True)
         e_end.record()
         torch.cuda.synchronize()
         e2e_ms += e_start.elapsed_time(e_end)
     n_e2e = max(1, args.steps // 2)
     e2e_t = dist_max(e2e_ms / 1e3, world)
+
+    # validation of the last membership estimate (off the timed region)
+    truth = torch.from_numpy(np.ascontiguousarray(host["Pi_X"].T, dtype=np.float32)).to(dev)
+    val = otm.pvalue_match(out["Pi_hat"], truth, PVALUE_THRESHOLD)
+    pv = val["pvalues"].cpu().numpy()
+    scores = val["scores"].cpu().numpy()
 
     if rank != 0:
         return None
@@ -322,6 +335,11 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
     }
     otm.sgd_set_form(otm.SGD_FORM_AUTO)  # the full-batch reference needs the cluster form
+    line["mmsb_validation"] = {
+        "recovery_ratio": float(scores[0]), "average_error": float(scores[1]),
+        "pvalue_threshold": PVALUE_THRESHOLD,
+        "significant_pairs": int((pv <= PVALUE_THRESHOLD).sum()),
+        "against": "the generator's memberships of the 5,000 X nodes"}
     line["time_to_1e-3"] = convergence(otm, torch, path, cfg, statistics.mean(sgd_ms) / nsteps)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(cfg, host)
@@ -349,6 +367,7 @@ def oracle_sample(cfg, host, sgd_steps):
     """Time the oracle on the workload: whitening + projection + means once,
     `sgd_steps` STGD steps, unwhitening.  Returns (seconds per component)."""
     from oracle import moments as om
+    from oracle import community as ocomm
     from oracle import post as opost
     from oracle import stgd as ostgd
     from oracle import whiten as ow
@@ -366,6 +385,7 @@ def oracle_sample(cfg, host, sgd_steps):
                          cfg["theta"], cfg["alpha0"], max_steps=sgd_steps)
     t2 = time.perf_counter()
     opost.unwhiten(V, wh["Wplus"], cfg["theta"], False)
+    ocomm.membership(YA, V, cfg["theta"])
     t3 = time.perf_counter()
     return t1 - t0, (t2 - t1) / sgd_steps, t3 - t2
 
@@ -377,7 +397,7 @@ def cpu_value(cfg, host, sgd_steps=10):
     samples = cfg["n_per"] * cfg["epochs"]
     sample = (f"oracle (FP64 NumPy) on the same workload: whitening+projection once "
               f"({pre:.2f} s), {sgd_steps} of the {nsteps} STGD steps ({per_step * 1e3:.1f} ms "
-              f"each), unwhitening ({post:.2f} s); value = {samples} samples / "
+              f"each), unwhitening + membership ({post:.2f} s); value = {samples} samples / "
               f"(pre + {nsteps} x step + post) = {full:.2f} s")
     return samples / full, sample
 

@@ -9,6 +9,8 @@
  *   projection of samples y_t = W^T c_t (Section 3.1, Section 4.1)
  *   stochastic tensor gradient descent  (Section 3.2, Lemma 3 / Eq. (16))
  *   unwhitening / post-processing       (Section 3.3, Lemma 4)
+ *   community membership and its p-value validation (Lemma 4, community case;
+ *                                        Section "Validation methods")
  *
  * Conventions that hold for every entry point:
  *   - Every pointer argument is a DEVICE pointer owned by the caller, unless the
@@ -591,6 +593,48 @@ size_t otm_recon_error_workspace(int64_t k);
 otm_status otm_recon_error(const float* V, int64_t k, double theta, const double* U_true,
                            const double* lam_true, double* err, void* ws, size_t ws_bytes,
                            void* stream);
+
+/*
+ * otm_membership -- community membership estimate (Section 3.3 Lemma 4,
+ * community case): Pi_hat = diag(gamma)^{1/3} diag(Lambda)^{-1} Phi^T W^T G_{A,X}
+ * for the n nodes X whose whitened view-A rows y_x = W^T G_{A,x} are the rows
+ * of Y.  Phi holds the unit components u_i = v_i / ||v_i||, Lambda the
+ * eigenvalues lambda_i = kappa ||v_i||^3 (kappa = (1 + theta) / 2), and gamma
+ * the scalar of the Dirichlet normalisation, gamma = (sum_i lambda_i^-2)^{-1/2}.
+ * With population moments and exact components the result is the true
+ * membership.  Entries below tau are set to 0 (thresholding; pass -INFINITY
+ * to keep all).
+ *   Y: n x k float32 row-major (the view-A samples, as otm_project writes them);
+ *   V: k x k float32 column-major (the STGD components);
+ *   Pi_hat: k x n float32 row-major, row i = community i over the nodes.
+ * FP32 dot products, FP64 scale.  1 <= k <= 1024; n = 0 is a no-op.
+ * Scratch: otm_membership_workspace(k).  OTM_EINVAL on bad sizes or pointers.
+ */
+size_t otm_membership_workspace(int64_t k);
+otm_status otm_membership(const float* Y, int64_t n, int64_t k, const float* V, double theta,
+                          double tau, float* Pi_hat, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * otm_pvalue_match -- validation of an estimated membership against the
+ * ground truth by p-value testing (Section "Validation methods": p-value
+ * testing, recovery ratio, error function).  For each estimated row i
+ * (k_hat rows) and ground-truth row j (k rows) over n nodes:
+ *   rho(i,j) = Pearson correlation (0 when either row is constant),
+ *   T = rho sqrt(n-2) / sqrt(1 - rho^2),  pvals[i*k + j] = P(t_{n-2} > T),
+ *   l1[i*k + j] = (1/n) sum_x |Pi_hat[i,x] - Pi[j,x]|.
+ * A pair is significant when its p-value is <= threshold (the paper uses
+ * 0.01).  scores[0] = recovery ratio R = fraction of ground-truth rows with at
+ * least one significant pair; scores[1] = average error E = (1/k) * sum of
+ * l1 over the significant pairs.
+ *   Pi_hat: k_hat x n, Pi: k x n, float32 row-major; pvals, l1: k_hat x k FP64
+ *   row-major; scores: 2 doubles (device).  All statistics in FP64; the
+ *   t tail from the continued fraction of the regularised incomplete beta.
+ * Needs n >= 3, 1 <= k <= 1024.  Scratch: otm_pvalue_match_workspace(k_hat, k).
+ */
+size_t otm_pvalue_match_workspace(int64_t k_hat, int64_t k);
+otm_status otm_pvalue_match(const float* Pi_hat, int64_t k_hat, const float* Pi, int64_t k,
+                            int64_t n, double threshold, double* pvals, double* l1,
+                            double* scores, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

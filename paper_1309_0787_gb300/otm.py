@@ -129,6 +129,11 @@ _SIGS = {
                      c_vp, c_vp, c_sz, c_vp],
     "otm_recon_error_workspace": [c_i64],
     "otm_recon_error": [c_vp, c_i64, c_f64, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
+    "otm_membership_workspace": [c_i64],
+    "otm_membership": [c_vp, c_i64, c_i64, c_vp, c_f64, c_f64, c_vp, c_vp, c_sz, c_vp],
+    "otm_pvalue_match_workspace": [c_i64, c_i64],
+    "otm_pvalue_match": [c_vp, c_i64, c_vp, c_i64, c_i64, c_f64, c_vp, c_vp, c_vp, c_vp, c_sz,
+                         c_vp],
 }
 _RESTYPE = {"otm_last_error": ctypes.c_char_p, "otm_version": ctypes.c_int,
             "otm_launch_count": ctypes.c_uint64, "otm_mlp_param_count": c_i64}
@@ -705,6 +710,37 @@ def recon_error(V, U_true, lam_true, theta: float):
     _check(_lib.otm_recon_error(_ptr(V), k, float(theta), _ptr(U_true), _ptr(lam_true), _ptr(err),
                                 _ptr(ws), ws.numel(), _stream()))
     return err
+
+
+def membership(Y, V, theta: float, tau: float = float("-inf")):
+    """otm_membership: Pi_hat (k x n float32) from the view-A samples Y (n x k)
+    and the components V (k x k, V[i] = component i)."""
+    n, k = Y.shape
+    _need(Y, torch.float32, (n, k), "Y")
+    _need(V, torch.float32, (k, k), "V")
+    out = torch.empty(k, n, dtype=torch.float32, device=Y.device)
+    ws = _ws(_lib.otm_membership_workspace(k), Y.device)
+    _check(_lib.otm_membership(_ptr(Y), n, k, _ptr(V), float(theta), float(tau), _ptr(out),
+                               _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def pvalue_match(Pi_hat, Pi, threshold: float = 0.01) -> dict:
+    """otm_pvalue_match: p-values, l1 distances, recovery ratio and average
+    error of Pi_hat (k_hat x n) against Pi (k x n), both float32."""
+    k_hat, n = Pi_hat.shape
+    k = Pi.shape[0]
+    _need(Pi_hat, torch.float32, (k_hat, n), "Pi_hat")
+    _need(Pi, torch.float32, (k, n), "Pi")
+    dev = Pi_hat.device
+    o = {"pvalues": torch.empty(k_hat, k, dtype=torch.float64, device=dev),
+         "l1": torch.empty(k_hat, k, dtype=torch.float64, device=dev),
+         "scores": torch.empty(2, dtype=torch.float64, device=dev)}
+    ws = _ws(_lib.otm_pvalue_match_workspace(k_hat, k), dev)
+    _check(_lib.otm_pvalue_match(_ptr(Pi_hat), k_hat, _ptr(Pi), k, n, float(threshold),
+                                 _ptr(o["pvalues"]), _ptr(o["l1"]), _ptr(o["scores"]), _ptr(ws),
+                                 ws.numel(), _stream()))
+    return o
 
 
 ENTRY_POINTS = tuple(_SIGS)
