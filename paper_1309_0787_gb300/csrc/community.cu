@@ -22,81 +22,95 @@
 namespace otm {
 namespace {
 
-constexpr int kMaxK = 1024;
+constexpr int kMaxK = 1024;  // largest k of otm_membership
 
 // ---- membership ---------------------------------------------------------
 
-// One CTA: scale[i] = gamma^{1/3} / (lambda_i ||v_i||) = gamma^{1/3} / (kappa ||v_i||^4).
-__global__ void membership_scale_kernel(const float* __restrict__ V, int k, double kappa,
-                                        double* __restrict__ scale) {
-  __shared__ double s_norm[kMaxK];
-  __shared__ double s_red[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int i = warp; i < k; i += nwarps) {
-    double acc = 0.0;
-    for (int r = lane; r < k; r += 32) {
-      const double v = V[(int64_t)i * k + r];
-      acc = fma(v, v, acc);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) s_norm[i] = sqrt(acc);
+// One warp per component: norm[i] = ||v_i|| (FP64), eight components per CTA.
+__global__ void component_norms_kernel(const float* __restrict__ V, int k,
+                                       double* __restrict__ norm) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= k) return;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int r = lane; r < k; r += 32) {
+    const double v = V[(int64_t)i * k + r];
+    acc = fma(v, v, acc);
   }
-  __syncthreads();
-  // sum_i lambda_i^-2, in a fixed order (deterministic)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) norm[i] = sqrt(acc);
+}
+
+// Pi_hat (k x n) = diag(scale) Vr Y^T with Vr[i][j] = V[i * k + j] (row i = v_i)
+// and scale[i] = gamma^{1/3} / (lambda_i ||v_i||) = gamma^{1/3} / (kappa ||v_i||^4):
+// a 64 x 64 output tile per CTA, 256 threads with 4 x 4 outputs each, the
+// contraction index staged 32 at a time in shared memory (transposed so that a
+// thread's four rows / four nodes are contiguous), the next chunk loaded into
+// registers while the current one is multiplied.  Every CTA sums
+// sum_i lambda_i^-2 in the same fixed order, so all use the same gamma.
+constexpr int MT = 64, NT = 64, KT = 32;
+constexpr int LD = (MT * KT) / 256;  // elements of each tile a thread loads
+
+__global__ void __launch_bounds__(256)
+membership_kernel(const float* __restrict__ Y, int64_t n, int k, const float* __restrict__ V,
+                  const double* __restrict__ norm, double kappa, double tau,
+                  float* __restrict__ Pi_hat) {
+  __shared__ __align__(16) float sA[KT][MT + 4];
+  __shared__ __align__(16) float sB[KT][NT + 4];
+  __shared__ double s_red[8];
+  __shared__ double s_scale[MT];
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.y * MT;
+  const int64_t x0 = (int64_t)blockIdx.x * NT;
+  const int ty = tid >> 4, tx = tid & 15;  // rows i0 + 4 ty .. +3, nodes x0 + 4 tx .. +3
+
+  float ra[LD], rb[LD];
+  auto load = [&](int j0) {
+#pragma unroll
+    for (int e = 0; e < LD; ++e) {
+      const int idx = tid + e * 256;
+      const int r = idx / KT, c = idx % KT;  // consecutive threads: consecutive j
+      const int j = j0 + c;
+      const int i = i0 + r;
+      const int64_t x = x0 + r;
+      ra[e] = (i < k && j < k) ? V[(int64_t)i * k + j] : 0.0f;
+      rb[e] = (x < n && j < k) ? Y[x * k + j] : 0.0f;
+    }
+  };
+  load(0);
+
+  // gamma^{1/3} and this tile's row scales
   double part = 0.0;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double nv = s_norm[i];
+  for (int i = tid; i < k; i += 256) {
+    const double nv = norm[i];
     const double lam = kappa * nv * nv * nv;
     part += 1.0 / (lam * lam);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (lane == 0) s_red[warp] = part;
+  if ((tid & 31) == 0) s_red[tid >> 5] = part;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid < MT && i0 + tid < k) {
     double tot = 0.0;
-    for (int w = 0; w < nwarps; ++w) tot += s_red[w];
-    s_red[0] = cbrt(1.0 / sqrt(tot));  // gamma^{1/3}
+    for (int w = 0; w < 8; ++w) tot += s_red[w];
+    const double g13 = cbrt(1.0 / sqrt(tot));
+    const double nv = norm[i0 + tid];
+    s_scale[tid] = g13 / (kappa * nv * nv * nv * nv);
   }
-  __syncthreads();
-  const double g13 = s_red[0];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double nv = s_norm[i];
-    scale[i] = g13 / (kappa * nv * nv * nv * nv);
-  }
-}
 
-// Pi_hat (k x n) = diag(scale) Vr Y^T with Vr[i][j] = V[i * k + j] (row i = v_i):
-// a 64 x 64 output tile per CTA, 256 threads with 4 x 4 outputs each, the
-// contraction index staged 16 at a time in shared memory (transposed so that
-// a thread's four rows / four nodes are contiguous).
-constexpr int MT = 64, NT = 64, KT = 16;
-
-__global__ void __launch_bounds__(256)
-membership_kernel(const float* __restrict__ Y, int64_t n, int k, const float* __restrict__ V,
-                  const double* __restrict__ scale, double tau, float* __restrict__ Pi_hat) {
-  __shared__ __align__(16) float sA[KT][MT + 4];
-  __shared__ __align__(16) float sB[KT][NT + 4];
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.y * MT;
-  const int64_t x0 = (int64_t)blockIdx.x * NT;
-  const int ty = tid >> 4, tx = tid & 15;  // rows i0 + 4 ty .. +3, nodes x0 + 4 tx .. +3
   float acc[4][4] = {};
   for (int j0 = 0; j0 < k; j0 += KT) {
-    // 64 x 16 tiles of Vr and of Y, four elements per thread each; consecutive
-    // threads read consecutive j (coalesced within a row).
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < LD; ++e) {
       const int idx = tid + e * 256;
-      const int r = idx >> 4, c = idx & 15;
-      const int j = j0 + c;
-      const int i = i0 + r;
-      sA[c][r] = (i < k && j < k) ? V[(int64_t)i * k + j] : 0.0f;
-      const int64_t x = x0 + r;
-      sB[c][r] = (x < n && j < k) ? Y[x * k + j] : 0.0f;
+      const int r = idx / KT, c = idx % KT;
+      sA[c][r] = ra[e];
+      sB[c][r] = rb[e];
     }
     __syncthreads();
+    if (j0 + KT < k) load(j0 + KT);
 #pragma unroll
     for (int c = 0; c < KT; ++c) {
       const float4 a = *reinterpret_cast<const float4*>(&sA[c][4 * ty]);
@@ -112,15 +126,15 @@ membership_kernel(const float* __restrict__ Y, int64_t n, int k, const float* __
   }
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    const int i = i0 + 4 * ty + p;
-    if (i >= k) continue;
-    const double s = scale[i];
+    const int r = 4 * ty + p;
+    if (i0 + r >= k) continue;
+    const double s = s_scale[r];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t x = x0 + 4 * tx + q;
       if (x >= n) continue;
       const double v = s * (double)acc[p][q];
-      Pi_hat[(int64_t)i * n + x] = v >= tau ? (float)v : 0.0f;
+      Pi_hat[(int64_t)(i0 + r) * n + x] = v >= tau ? (float)v : 0.0f;
     }
   }
 }
@@ -308,11 +322,12 @@ otm_status otm_membership(const float* Y, int64_t n, int64_t k, const float* V, 
   if (n == 0) return OTM_OK;
   cudaStream_t st = as_stream(stream);
   Workspace w(ws, ws_bytes);
-  double* scale = w.take<double>(k);
-  membership_scale_kernel<<<1, 256, 0, st>>>(V, (int)k, 0.5 * (1.0 + theta), scale);
+  double* norm = w.take<double>(k);
+  component_norms_kernel<<<(unsigned)((k + 7) / 8), 256, 0, st>>>(V, (int)k, norm);
   OTM_CHECK_LAUNCH();
   const dim3 grid((unsigned)((n + NT - 1) / NT), (unsigned)((k + MT - 1) / MT));
-  membership_kernel<<<grid, 256, 0, st>>>(Y, n, (int)k, V, scale, tau, Pi_hat);
+  membership_kernel<<<grid, 256, 0, st>>>(Y, n, (int)k, V, norm, 0.5 * (1.0 + theta), tau,
+                                          Pi_hat);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }
