@@ -10,11 +10,20 @@ Readings of the paper used here:
     positive the whitening does not exist (error).
   * Eigenvector signs: the entry of largest magnitude of each eigenvector is
     made positive.
-  * Randomised whitening: the paper's Nystrom form (Algorithm 2, k~ = 2k, no
-    power iteration) is replaced by the randomised range finder with
+  * Randomised whitening, default form: the randomised range finder with
     oversampling p and q power iterations (Q = orth(M2 S), then
     Q <- orth(M2 Q) q times), Rayleigh-Ritz on Omega = Q^T M2 Q, truncation to
     k.  On the GPU the range finder uses the tall-thin QR of Section 4.2.
+  * Randomised whitening, the paper's Nystrom form (Algorithm 2): O = M2 S,
+    Omega = S^T O, W = U_O L_O^{-1} V_O^T V_Omega L_Omega^{1/2} with both
+    decompositions truncated to rank k (O has rank k when M2 has, so its
+    remaining singular values are rounding noise and L_O^{-1} would amplify
+    them), Omega symmetrised and decomposed as a symmetric matrix (its SVD
+    for a positive semi-definite Omega), its k largest eigenvalues required
+    positive (relative to the largest, as for the exact whitening), and the
+    trailing U_Omega^T of the printed formula dropped: it rotates the k
+    columns back into k~ coordinates, and without it W is d x k with
+    W^T M2 W = I_k whenever M2 has rank k.  (W^T)^+ = W (W^T W)^{-1}.
   * Randomised pseudo-inverse (Algorithm 3): its printed formula
     (J^+)^T Psi J^+ is a pseudo-inverse only for symmetric matrices; Pairs is
     not symmetric, so we compute the rank-k SVD P ~ U Sigma V^T by randomised
@@ -29,7 +38,7 @@ from .moments import as_sparse, community_first_moment
 
 __all__ = [
     "NotPositiveDefinite", "sign_fix", "orth", "top_eigh", "whiten_exact",
-    "range_finder_whiten", "randomized_svd", "community_whiten_randomized",
+    "range_finder_whiten", "nystrom_whiten", "randomized_svd", "community_whiten_randomized",
 ]
 
 
@@ -88,6 +97,21 @@ def range_finder_whiten(apply_M2, S: np.ndarray, k: int, power_iters: int) -> di
     Cp = U * np.sqrt(lam)
     return {"W": Q @ Cw, "Wplus": Q @ Cp, "Q": Q, "Cw": Cw, "Cp": Cp, "eig": lam,
             "Omega": 0.5 * (Om + Om.T)}
+
+
+def nystrom_whiten(apply_M2, S: np.ndarray, k: int) -> dict:
+    """Algorithm 2 (randomised tall-thin SVD), read as in the module doc:
+    W (d x k), Wplus = (W^T)^+, eig = the k largest eigenvalues of Omega."""
+    S = np.asarray(S, dtype=np.float64)
+    O = apply_M2(S)                                     # O = M2 S
+    U_O, L_O, Vt_O = np.linalg.svd(O, full_matrices=False)
+    Omega = S.T @ O                                     # Omega = S^T O
+    lam, V_Om = top_eigh(Omega, k)
+    if not lam[-1] > 1e-5 * abs(lam[0]):
+        raise NotPositiveDefinite(f"k-th eigenvalue of Omega is {lam[-1]:.3e}")
+    W = (U_O[:, :k] / L_O[:k]) @ Vt_O[:k] @ (V_Om * np.sqrt(lam))
+    Wplus = W @ np.linalg.inv(W.T @ W)
+    return {"W": W, "Wplus": Wplus, "eig": lam}
 
 
 def randomized_svd(apply_A, apply_AT, S: np.ndarray, k: int, power_iters: int):

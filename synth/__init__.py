@@ -41,7 +41,7 @@ __all__ = [
     "rng", "CSR", "lda_corpus", "mmsb_graph", "orthogonal_samples", "gaussian",
     "haar_orthonormal", "epoch_permutations", "csr_from_dense", "csr_to_dense",
     "philox4x32", "bits_to_unit", "whitened_lda_instances", "whitened_lda_samples",
-    "unit_vectors",
+    "unit_vectors", "signed_column_selection",
 ]
 
 
@@ -184,6 +184,18 @@ def orthogonal_samples(seed: int, k: int, n: int, sigma: float) -> dict:
 
 def gaussian(seed: int, rows: int, cols: int, dtype=np.float32) -> np.ndarray:
     return rng(seed).standard_normal((rows, cols)).astype(dtype)
+
+
+def signed_column_selection(seed: int, rows: int, cols: int, dtype=np.float32) -> np.ndarray:
+    """rows x cols matrix with one entry +-1 per column, in distinct rows chosen
+    uniformly without replacement (the random projection for a sparse second
+    moment, Section 4.2)."""
+    g = rng(seed)
+    idx = g.choice(rows, size=cols, replace=False)
+    sign = np.where(g.random(cols) < 0.5, -1.0, 1.0)
+    S = np.zeros((rows, cols), dtype=dtype)
+    S[idx, np.arange(cols)] = sign
+    return S
 
 
 def _haar(g: np.random.Generator, k: int) -> np.ndarray:

@@ -91,3 +91,46 @@ def test_community_randomized_whitening_on_expected_graph():
     YA = G["A"] @ r["W"]
     np.testing.assert_allclose(G["B"] @ r["W_B"], YA, atol=1e-9)
     np.testing.assert_allclose(G["C"] @ r["W_C"], YA, atol=1e-9)
+
+
+# --- Algorithm 2 (Nystrom form), read as in the oracle's module doc ----------
+
+@pytest.mark.parametrize("kind", ["selection", "gaussian"])
+def test_nystrom_whiten_exact_on_rank_k(kind):
+    """M2 of rank k: the Nystrom approximation O Omega^+ O^T is exact, so W
+    whitens M2 exactly and W W^T is M2's pseudo-inverse (unique, whatever the
+    rotation); Omega's eigenvalues from the library; Wplus = pinv(W^T)."""
+    d, k, kt = 40, 5, 10
+    M2, _, _ = _psd(3, d, k)
+    S = (synth.signed_column_selection(4, d, kt) if kind == "selection"
+         else synth.gaussian(4, d, kt)).astype(np.float64)
+    wh = ow.nystrom_whiten(lambda Z: M2 @ Z, S, k)
+    W = wh["W"]
+    assert W.shape == (d, k)
+    np.testing.assert_allclose(W.T @ M2 @ W, np.eye(k), atol=1e-9)
+    P = np.linalg.pinv(M2, rcond=1e-10)
+    assert np.linalg.norm(W @ W.T - P) < 1e-9 * np.linalg.norm(P)
+    Om = S.T @ M2 @ S
+    ref = scipy.linalg.eigh(0.5 * (Om + Om.T), eigvals_only=True,
+                            subset_by_index=[kt - k, kt - 1])[::-1]
+    np.testing.assert_allclose(wh["eig"], ref, rtol=1e-10)
+    np.testing.assert_allclose(wh["Wplus"], np.linalg.pinv(W.T), atol=1e-9)
+
+
+def test_nystrom_whiten_full_selection_is_exact_whitening():
+    """S a signed permutation (k~ = d): Omega is M2 in permuted coordinates and
+    the Nystrom W equals the exact whitening of the top-k eigenpairs."""
+    d, k = 30, 6
+    M2, _, _ = _psd(5, d, d)                   # full rank, distinct eigenvalues
+    S = synth.signed_column_selection(6, d, d).astype(np.float64)
+    wh = ow.nystrom_whiten(lambda Z: M2 @ Z, S, k)
+    ex = ow.whiten_exact(M2, k)
+    np.testing.assert_allclose(wh["W"] @ wh["W"].T, ex["W"] @ ex["W"].T, atol=1e-10)
+    np.testing.assert_allclose(wh["eig"], ex["eig"], rtol=1e-12)
+
+
+def test_nystrom_whiten_rejects_indefinite():
+    M2, _, _ = _psd(7, 20, 20)
+    S = synth.signed_column_selection(8, 20, 8).astype(np.float64)
+    with pytest.raises(ow.NotPositiveDefinite):
+        ow.nystrom_whiten(lambda Z: -M2 @ Z, S, 3)

@@ -68,3 +68,13 @@ def test_samples_reproducible_by_instance_index():
     a = synth.whitened_lda_samples(inst, 50, 9)
     b = synth.whitened_lda_samples(inst, 50, 9, first=1, count=2)
     np.testing.assert_array_equal(a[1:], b)
+
+
+def test_signed_column_selection_structure():
+    S = synth.signed_column_selection(3, 50, 12)
+    assert S.shape == (50, 12) and S.dtype == np.float32
+    assert (np.count_nonzero(S, axis=0) == 1).all()
+    assert set(np.unique(S[S != 0])) <= {-1.0, 1.0}
+    rows = np.nonzero(S.T)[1]
+    assert len(set(rows.tolist())) == 12                 # distinct rows
+    np.testing.assert_array_equal(S, synth.signed_column_selection(3, 50, 12))
