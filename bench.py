@@ -741,6 +741,70 @@ def dist_max(x, world):
     return float(t.item())
 
 
+WHITEN = dict(workload="lda_30000x20000_k50_whitening", n_docs=30000, d=20000, k=50,
+              alpha_i=0.01, word_conc=0.05, doc_len=300, oversample=20, power_iters=2, seed=0)
+
+
+def run_whitening(args):
+    """Randomised whitening of a topic model's M2, both forms, on one LDA corpus
+    (30,000 documents of Poisson(300) words over 20,000 words, k = 50,
+    alpha0 = 0.5): the range finder (Gaussian S, k + 20 columns, 2 power
+    iterations, tall-thin QR) and the paper's Nystrom form (Algorithm 2,
+    signed column selection, k~ = 2k).  Per form: device time per call (median
+    of `steps`, L2 flushed before each; each call ends with its host-checked
+    eigenvalue flag) and the whitening deviation max |W^T M2 W - I| with M2
+    applied implicitly."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    c = dict(WHITEN)
+    dev = torch.device("cuda", 0)
+    k, d = c["k"], c["d"]
+    alpha0 = k * c["alpha_i"]
+    corpus = synth.lda_corpus(c["seed"], c["n_docs"], d, k, c["alpha_i"], c["word_conc"],
+                              c["doc_len"], poisson_len=True)
+    Xd = otm.DeviceCSR.from_host(corpus["X"], dev)
+    S_rf = torch.from_numpy(synth.gaussian(c["seed"] + 1, d, k + c["oversample"])).to(dev)
+    S_ny = torch.from_numpy(synth.signed_column_selection(c["seed"] + 2, d, 2 * k)).to(dev)
+    forms = {"range_finder": lambda: otm.whiten_topic(Xd, S_rf, k, c["power_iters"], alpha0),
+             "nystrom": lambda: otm.whiten_topic_nystrom(Xd, S_ny, k, alpha0)}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    mom = otm.topic_moments(Xd)
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = {}
+    for name, f in forms.items():
+        for _ in range(args.warmup):
+            f()
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = f()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        W = out["W"]
+        MW = otm.topic_m2_apply(Xd, mom, alpha0, W)
+        dev_max = (W.double().t() @ MW.double() - torch.eye(k, dtype=torch.float64, device=dev))
+        res[name] = {"ms": statistics.median(ms), "ms_all": ms,
+                     "whitening_deviation_max": float(dev_max.abs().max()),
+                     "columns": int(out["Q"].shape[1])}
+    clocks = sampler.stop()
+    return {"metric": "randomised whitening time (ms), Nystrom form (Algorithm 2)",
+            "value": res["nystrom"]["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["nystrom"]["ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": c["workload"], "docs": c["n_docs"], "vocabulary": d, "k": k,
+                       "alpha0": alpha0, "nnz": int(corpus["X"].nnz),
+                       "l2": "flushed before each call (256 MiB write)"},
+            "forms": res, "clocks": clocks,
+            "note": ("the range finder satisfies W^T M2 W = I by construction (Rayleigh-Ritz on "
+                     "its basis), so its deviation is float32 rounding; the Nystrom form's "
+                     "deviation measures how much of M2 its column selection misses")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -748,9 +812,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mmsb", choices=["mmsb", "batched", "warmstart"],
+    ap.add_argument("--workload", default="mmsb",
+                    choices=["mmsb", "batched", "warmstart", "whitening"],
                     help="mmsb: the default pipeline line; batched: the batched form; "
-                         "warmstart: time to 1e-3 with the learned start")
+                         "warmstart: time to 1e-3 with the learned start; whitening: both "
+                         "randomised whitening forms on an LDA corpus")
     ap.add_argument("--k", type=int, default=0, help="warmstart: components (default 64)")
     ap.add_argument("--problems", type=int, default=512)
     ap.add_argument("--restarts", type=int, default=8)
@@ -766,6 +832,8 @@ def main():
         line = run_batched(args) if rank == 0 else None
     elif args.workload == "warmstart":
         line = run_warmstart(args) if rank == 0 else None
+    elif args.workload == "whitening":
+        line = run_whitening(args) if rank == 0 else None
     elif args.impl == "reference":
         line = run_reference(args, rank, world)
     else:

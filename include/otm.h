@@ -189,6 +189,31 @@ otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t
                             float* row_w, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * otm_whiten_topic_nystrom -- the paper's own randomised whitening of the
+ * topic-model M2 (Section 4.2, Algorithm 2 "Randomized Tall-thin SVD"): for a
+ * random S (d x kt; the paper's choice for a sparse M2 is a column selection
+ * with random signs, kt = 2k), O = M2 S, Omega = S^T O, and
+ *   W = U_O L_O^{-1} V_O^T V_Omega L_Omega^{1/2}   (d x k),
+ * with the SVD of O and the symmetric eigendecomposition of Omega both
+ * truncated to rank k (the printed formula's trailing U_Omega^T is dropped so
+ * that W has k columns; W^T M2 W = I_k exactly when M2 has rank k).  The SVD
+ * of O comes from the FP64 eigendecomposition of O^T O.  k < kt <= 160, kt <= d.
+ * Outputs, in the layout of otm_whiten_topic so that otm_project and
+ * otm_unwhiten take them unchanged: W (d x k, float32); O (d x kt, float32,
+ * in the Q slot: not orthonormal); Cw, Cp (kt x k, FP64) with W = O Cw and
+ * (W^T)^+ = W (W^T W)^{-1} = O Cp; eig[k] = the k largest eigenvalues of
+ * Omega (descending); M1, row_invlen, row_w as otm_topic_moments.
+ * OTM_ENOTPSD if the k-th eigenvalue of Omega is not above 1e-5 times the
+ * largest or O has rank < k.  Synchronises the stream.
+ * Scratch: otm_whiten_topic_nystrom_workspace(n, d, k, kt).
+ */
+size_t otm_whiten_topic_nystrom_workspace(int64_t n, int64_t d, int64_t k, int64_t kt);
+otm_status otm_whiten_topic_nystrom(const otm_csr* X, const float* S, int64_t k, int64_t kt,
+                                    double alpha0, float* W, float* O, double* Cw, double* Cp,
+                                    double* eig, double* M1, float* row_invlen, float* row_w,
+                                    void* ws, size_t ws_bytes, void* stream);
+
+/*
  * otm_whiten_community -- randomised whitening of the community-model M2
  * (Eq. (10), Sections 4.1-4.2).  G_XA, G_XB, G_XC: n_X x n_A, n_X x n_B,
  * n_X x n_C adjacency blocks.  S_pairs (n_B x kt) and S_w (n_A x kt) are the

@@ -13,6 +13,10 @@
 //
 // Both then run the same range finder: Q = orth(M2 S); q times Q = orth(M2 Q);
 // Omega = Q^T M2 Q; FP64 eigendecomposition; W = Q U_k Lambda_k^{-1/2}.
+//
+// The topic model also has the paper's own Nystrom form (Algorithm 2): O = M2 S
+// for a signed column selection S, Omega = S^T O, both decomposed at rank k,
+// W = U_O L_O^{-1} V_O^T V_Omega L_Omega^{1/2} (d x k).
 #include "otm_internal.cuh"
 
 namespace otm {
@@ -61,6 +65,35 @@ __global__ void take_cols_kernel(const double* __restrict__ a, int64_t n, int64_
 }
 
 inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Nystrom whitening (Algorithm 2), k x k middle factors.  T1 = V_G,k^T V_Om,k;
+// T2 = diag(1/ev_G) T1 diag(sqrt(ev_Om)); D = diag(ev_G) T2 = T1 diag(sqrt(ev_Om));
+// eig = ev_Om[:k].  Flags the k-th eigenvalue of Omega (relative to the first,
+// as for the range finder) and of G = O^T O not being positive.
+__global__ void nystrom_scale_kernel(const double* __restrict__ T1, const double* __restrict__ evG,
+                                     const double* __restrict__ evO, int64_t k,
+                                     double* __restrict__ T2, double* __restrict__ D,
+                                     double* __restrict__ eig, int* __restrict__ flag) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx == 0 && (!(evO[k - 1] > 1e-5 * fabs(evO[0])) || !(evG[k - 1] > 0.0))) *flag = 1;
+  if (idx < k) eig[idx] = evO[idx];
+  if (idx >= k * k) return;
+  const int64_t a = idx / k, b = idx % k;
+  const double so = evO[b] > 0.0 ? sqrt(evO[b]) : 0.0;
+  const double g = evG[a] > 0.0 ? evG[a] : 1.0;
+  D[idx] = T1[idx] * so;
+  T2[idx] = T1[idx] * so / g;
+}
+
+// E = V diag(1/ev) (k x k, column scaling); flags a non-positive eigenvalue.
+__global__ void inv_scale_cols_kernel(const double* __restrict__ V, const double* __restrict__ ev,
+                                      int64_t k, double* __restrict__ E, int* __restrict__ flag) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx == 0 && !(ev[k - 1] > 0.0)) *flag = 1;
+  if (idx >= k * k) return;
+  const double e = ev[idx % k];
+  E[idx] = e > 0.0 ? V[idx] / e : 0.0;
+}
 
 struct TopicOp {
   const otm_csr* X;
@@ -373,6 +406,87 @@ otm_status otm_whiten_community(const otm_csr* G_XA, const otm_csr* G_XB, const 
   OTM_TRY(gemm_nn_small(U_C, nc, k, LW32, k, W_C, nullptr, nullptr, 0.0, st));
 
   return check_flags(flags, st, "otm_whiten_community");
+}
+
+
+size_t otm_whiten_topic_nystrom_workspace(int64_t n, int64_t d, int64_t k, int64_t kt) {
+  WorkspaceSize w;
+  w.add<double>(d).add<float>(n * kt).add<double>(kt).add<int>(kFlags);
+  w.add<double>(kt * kt).add<double>(kt * kt);                  // G, Omega
+  w.add<double>(kt).add<double>(kt * kt).add<double>(kt).add<double>(kt * kt);  // eigenpairs
+  for (int i = 0; i < 6; ++i) w.add<double>(k * k);             // T1, T2, D, H, E, Hinv
+  w.add<double>(k).add<double>(k * k).add<float>(kt * k);       // evH, vecH, Cw32
+  return w.bytes() + syev_workspace(kt);
+}
+
+otm_status otm_whiten_topic_nystrom(const otm_csr* X, const float* S, int64_t k, int64_t kt,
+                                    double alpha0, float* W, float* O, double* Cw, double* Cp,
+                                    double* eig, double* M1, float* row_invlen, float* row_w,
+                                    void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  OTM_TRY(check_csr(X, "otm_whiten_topic_nystrom"));
+  OTM_REQUIRE(k >= 1 && kt > k && kt <= 160 && kt <= X->cols,
+              "otm_whiten_topic_nystrom: need 1 <= k < kt <= min(160, d) (k=%lld kt=%lld "
+              "d=%lld)", (long long)k, (long long)kt, (long long)X->cols);
+  OTM_REQUIRE(X->rows >= 1, "otm_whiten_topic_nystrom: empty corpus");
+  OTM_REQUIRE(alpha0 >= 0.0, "otm_whiten_topic_nystrom: alpha0 must be >= 0");
+  OTM_REQUIRE(S && W && O && Cw && Cp && eig && M1 && row_invlen && row_w,
+              "otm_whiten_topic_nystrom: null argument");
+  OTM_REQUIRE(S != O, "otm_whiten_topic_nystrom: O must not alias S");
+  const size_t need = otm_whiten_topic_nystrom_workspace(X->rows, X->cols, k, kt);
+  OTM_REQUIRE(ws_bytes >= need, "otm_whiten_topic_nystrom: workspace too small (need %zu bytes)",
+              need);
+  cudaStream_t st = as_stream(stream);
+  const int64_t d = X->cols;
+  Workspace w(ws, ws_bytes);
+  double* delta = w.take<double>(d);
+  float* P = w.take<float>(X->rows * kt);
+  double* u = w.take<double>(kt);
+  int* flags = w.take<int>(kFlags);
+  double* G = w.take<double>(kt * kt);
+  double* Om = w.take<double>(kt * kt);
+  double* evG = w.take<double>(kt);
+  double* vecG = w.take<double>(kt * kt);
+  double* evO = w.take<double>(kt);
+  double* vecO = w.take<double>(kt * kt);
+  double* T1 = w.take<double>(k * k);
+  double* T2 = w.take<double>(k * k);
+  double* D = w.take<double>(k * k);
+  double* H = w.take<double>(k * k);
+  double* E = w.take<double>(k * k);
+  double* Hinv = w.take<double>(k * k);
+  double* evH = w.take<double>(k);
+  double* vecH = w.take<double>(k * k);
+  float* Cw32 = w.take<float>(kt * k);
+  const size_t mark = w.used;
+  OTM_CHECK_CUDA(cudaMemsetAsync(flags, 0, kFlags * sizeof(int), st));
+  OTM_TRY(topic_moments(X, row_invlen, row_w, M1, delta, st));
+  TopicOp op{X, row_w, M1, delta, alpha0, P, u};
+  // O = M2 S; G = O^T O (its eigenpairs give the SVD of O); Omega = S^T O
+  OTM_TRY(op.apply(S, kt, O, st));
+  OTM_TRY(gemm_tn_f64acc(O, O, d, kt, kt, 1.0, G, 0, st));
+  OTM_TRY(gemm_tn_f64acc(S, O, d, kt, kt, 1.0, Om, 0, st));
+  OTM_TRY(syev(G, kt, evG, vecG, w, st, flags + 2));
+  w.used = mark;
+  OTM_TRY(syev(Om, kt, evO, vecO, w, st, flags + 2));
+  w.used = mark;
+  // C = V_G,k diag(1/ev_G) V_G,k^T V_Om,k diag(sqrt(ev_Om)) = U_O L_O^-1 V_O^T V_Om L_Om^1/2
+  // expressed on O (U_O = O V_O L_O^-1), so that W = O C
+  OTM_TRY(dgemm_small(1, 0, k, k, kt, 1.0, vecG, kt, vecO, kt, 0.0, T1, k, st));
+  nystrom_scale_kernel<<<blocks_for(k * k), 256, 0, st>>>(T1, evG, evO, k, T2, D, eig, flags);
+  OTM_CHECK_LAUNCH();
+  OTM_TRY(dgemm_small(0, 0, kt, k, k, 1.0, vecG, kt, T2, k, 0.0, Cw, k, st));
+  // (W^T)^+ = W (W^T W)^-1 = O C H^-1 with H = C^T G C = T2^T diag(ev_G) T2
+  OTM_TRY(dgemm_small(1, 0, k, k, k, 1.0, T2, k, D, k, 0.0, H, k, st));
+  OTM_TRY(syev(H, k, evH, vecH, w, st, flags + 2));
+  w.used = mark;
+  inv_scale_cols_kernel<<<blocks_for(k * k), 256, 0, st>>>(vecH, evH, k, E, flags);
+  OTM_CHECK_LAUNCH();
+  OTM_TRY(dgemm_small(0, 1, k, k, k, 1.0, E, k, vecH, k, 0.0, Hinv, k, st));
+  OTM_TRY(dgemm_small(0, 0, kt, k, k, 1.0, Cw, k, Hinv, k, 0.0, Cp, k, st));
+  OTM_TRY(f64_to_f32(Cw, Cw32, kt * k, st));
+  OTM_TRY(gemm_nn_small(O, d, kt, Cw32, k, W, nullptr, nullptr, 0.0, st));
+  return check_flags(flags, st, "otm_whiten_topic_nystrom");
 }
 
 }  // extern "C"

@@ -77,6 +77,9 @@ _SIGS = {
     "otm_whiten_topic_workspace": [c_i64, c_i64, c_i64, c_i64],
     "otm_whiten_topic": [_P, c_vp, c_i64, c_i64, ctypes.c_int, c_f64, c_vp, c_vp, c_vp, c_vp,
                          c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
+    "otm_whiten_topic_nystrom_workspace": [c_i64, c_i64, c_i64, c_i64],
+    "otm_whiten_topic_nystrom": [_P, c_vp, c_i64, c_i64, c_f64, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                 c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
     "otm_whiten_community_workspace": [c_i64, c_i64, c_i64, c_i64, c_i64, c_i64],
     "otm_whiten_community": [_P, _P, _P, c_vp, c_vp, c_i64, c_i64, ctypes.c_int, c_f64, c_vp,
                              c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
@@ -301,6 +304,26 @@ def whiten_topic(X: DeviceCSR, S, k: int, power_iters: int, alpha0: float) -> di
                                  _ptr(o["W"]), _ptr(o["Q"]), _ptr(o["Cw"]), _ptr(o["Cp"]),
                                  _ptr(o["eig"]), _ptr(o["M1"]), _ptr(o["row_invlen"]),
                                  _ptr(o["row_w"]), _ptr(ws), ws.numel(), _stream()))
+    return o
+
+
+def whiten_topic_nystrom(X: DeviceCSR, S, k: int, alpha0: float) -> dict:
+    """otm_whiten_topic_nystrom (Algorithm 2); "Q" holds O = M2 S."""
+    n, d = X.shape
+    kt = S.shape[1]
+    _need(S, torch.float32, (d, kt), "S")
+    dev = S.device
+    f32, f64 = torch.float32, torch.float64
+    o = {"W": torch.empty(d, k, dtype=f32, device=dev), "Q": torch.empty(d, kt, dtype=f32, device=dev),
+         "Cw": torch.empty(kt, k, dtype=f64, device=dev), "Cp": torch.empty(kt, k, dtype=f64, device=dev),
+         "eig": torch.empty(k, dtype=f64, device=dev), "M1": torch.empty(d, dtype=f64, device=dev),
+         "row_invlen": torch.empty(n, dtype=f32, device=dev),
+         "row_w": torch.empty(n, dtype=f32, device=dev)}
+    ws = _ws(_lib.otm_whiten_topic_nystrom_workspace(n, d, k, kt), dev)
+    _check(_lib.otm_whiten_topic_nystrom(X.ref(), _ptr(S), k, kt, float(alpha0), _ptr(o["W"]),
+                                         _ptr(o["Q"]), _ptr(o["Cw"]), _ptr(o["Cp"]), _ptr(o["eig"]),
+                                         _ptr(o["M1"]), _ptr(o["row_invlen"]), _ptr(o["row_w"]),
+                                         _ptr(ws), ws.numel(), _stream()))
     return o
 
 

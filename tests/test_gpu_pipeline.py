@@ -76,6 +76,44 @@ def test_whiten_topic_rejects_too_large_k(otm):
         otm.whiten_topic(otm.DeviceCSR.from_host(X), _dev(S), 8, 2, 1.0)
 
 
+@pytest.mark.parametrize("kt,kind", [(20, "selection"), (30, "selection"), (20, "gaussian")])
+def test_whiten_topic_nystrom_matches_oracle(otm, lda1, kt, kind):
+    """Algorithm 2 on the GPU against the oracle's, same float32 S.  The float32
+    O = M2 S (SpMM sums, float32 storage) carries ~1e-6 relative error, which
+    the rank-k pseudo-inverse of O^T O (condition ~500 here) amplifies to ~1e-5
+    on W (3e-6 from float32 rounding alone, emulated on the CPU); the bounds
+    below leave two orders of margin."""
+    c, _ = lda1
+    X = c["X"]
+    k = 10
+    S = (synth.signed_column_selection(5, 500, kt) if kind == "selection"
+         else synth.gaussian(6, 500, kt))
+    wh = otm.whiten_topic_nystrom(otm.DeviceCSR.from_host(X), _dev(S), k, 1.0)
+    torch.cuda.synchronize()
+    ref = ow.nystrom_whiten(lambda Z: om.topic_second_moment_apply(X, Z, 1.0),
+                            S.astype(np.float64), k)
+    W = to_np(wh["W"]).astype(np.float64)
+    np.testing.assert_allclose(to_np(wh["eig"]), ref["eig"], rtol=1e-4)
+    assert rel(align_signs(W, ref["W"]), ref["W"]) < 1e-3
+    O = to_np(wh["Q"]).astype(np.float64)
+    O_ref = om.topic_second_moment_apply(X, S.astype(np.float64), 1.0)
+    assert rel(O, O_ref) < 1e-5
+    assert rel(O @ to_np(wh["Cw"]), W) < 1e-6
+    Wp = O @ to_np(wh["Cp"])
+    assert rel(align_signs(Wp, ref["Wplus"]), ref["Wplus"]) < 1e-3
+    # (W^T)^+ is a left inverse of W^T: W^T (W^T)^+ = I
+    assert np.abs(W.T @ Wp - np.eye(k)).max() < 1e-4
+
+
+def test_whiten_topic_nystrom_rejects_too_large_k(otm):
+    dense = np.zeros((40, 20))
+    dense[:, :3] = 5.0
+    X = synth.csr_from_dense(dense)
+    S = synth.signed_column_selection(2, 20, 12)
+    with pytest.raises(otm.OtmError, match="OTM_ENOTPSD"):
+        otm.whiten_topic_nystrom(otm.DeviceCSR.from_host(X), _dev(S), 8, 1.0)
+
+
 def test_topic_pipeline_end_to_end(otm, lda1):
     """Config: d = 500, k = 10, 2,000 x 100-word documents, b = 256, beta = 1e-2/sqrt(t),
     theta = 1, 20 epochs, alpha0 = 1.  Each side runs the whole path itself."""
