@@ -805,6 +805,156 @@ def run_whitening(args):
                      "deviation measures how much of M2 its column selection misses")}
 
 
+LDA3 = dict(workload="lda_300000x100000_k100_precision", n_docs=300000, d=100000, k=100,
+            alpha_i=0.01, word_conc=0.05, doc_len=300, oversample=20, power_iters=2, b=1024,
+            epochs=20, beta0=1e-2, theta=1.0, seed=0, proj_docs=256)
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def lda_oracle_checks(X, W, Y_docs, docs, V0, Yb, yb, c, V1):
+    """FP64 oracle checks of single stages on a sample, each fed the previous
+    stage's GPU output: the projection y_t = W^T c_t / l_t of `docs` (Section
+    3.1), and the update of one STGD step (Lemma 3) on the minibatch Yb from V0
+    (components as columns) for each precision's V1 (same orientation).
+    Returns relative errors (of the rows, and of the update V1 - V0)."""
+    from oracle import moments as om
+    from oracle import stgd as ostgd
+    Xs = om.as_sparse(X)[docs]
+    lens = np.asarray(Xs.sum(axis=1)).ravel()
+    y_ref = (Xs @ np.asarray(W, dtype=np.float64)) / lens[:, None]
+    Yb = np.asarray(Yb, dtype=np.float64)
+    yb = np.asarray(yb, dtype=np.float64)
+    V0 = np.asarray(V0, dtype=np.float64)
+    dV = ostgd.sgd_step(V0, Yb, Yb, Yb, (yb, yb, yb), c["theta"], c["beta0"],
+                        c["k"] * c["alpha_i"]) - V0
+    return {"projection_rel_err": _rel(Y_docs, y_ref),
+            "step_update_rel_err": {p: _rel(np.asarray(v, dtype=np.float64) - V0, dV)
+                                    for p, v in V1.items()}}
+
+
+def run_lda(args):
+    """Precision form on a large LDA corpus: 300,000 documents of Poisson(300)
+    words over 100,000 words with Zipf-skewed Dir(0.05) topics, k = 100,
+    alpha0 = 1 (a synthetic stand-in for the paper's NYTimes corpus).  Per timed
+    iteration: whitening (range finder) + projection + means, then 20 epochs of
+    STGD (b = 1,024) from the same start in FP32, BF16 and FP8 (each with its
+    sample quantisation timed apart).  Medians over `steps` iterations, L2
+    flushed before each.  Errors: each low-precision result against the FP32
+    one (relative reconstruction error of the components, relative error of the
+    unwhitened topics), and FP64 oracle checks of single stages on a sample."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    c = dict(LDA3)
+    dev = torch.device("cuda", 0)
+    k, b, ep = c["k"], c["b"], c["epochs"]
+    alpha0 = k * c["alpha_i"]
+    t0 = time.perf_counter()
+    corpus = synth.lda_corpus(c["seed"], c["n_docs"], c["d"], k, c["alpha_i"], c["word_conc"],
+                              c["doc_len"], poisson_len=True, zipf=True)
+    gen_s = time.perf_counter() - t0
+    X = corpus["X"]
+    n, d = X.shape
+    S = torch.from_numpy(synth.gaussian(c["seed"] + 1, d, k + c["oversample"])).to(dev)
+    perm_h = synth.epoch_permutations(c["seed"] + 3, n, ep)
+    perm = torch.from_numpy(perm_h).to(dev)
+    V0h = synth.haar_orthonormal(c["seed"] + 4, k)            # columns = components
+    V0t = torch.from_numpy(V0h.T.copy()).to(dev)              # V[i] = component i
+    Xd = otm.DeviceCSR.from_host(X, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    precs = {"bf16": otm.PREC_BF16, "fp8": otm.PREC_FP8}
+
+    def one():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        ev[0].record()
+        wh = otm.whiten_topic(Xd, S, k, c["power_iters"], alpha0)
+        Y = otm.project(Xd, wh["W"], wh["row_invlen"])
+        yb3 = torch.stack([otm.column_mean(Y)] * 3)
+        ev[1].record()
+        V = {"fp32": V0t.clone()}
+        otm.sgd_run(V["fp32"], Y, Y, Y, yb3, perm, ep, b, c["beta0"], c["theta"], alpha0)
+        ev[2].record()
+        for j, (nm, pr) in enumerate(precs.items()):
+            q = otm.quantize_samples(Y, pr)
+            ev[3 + 2 * j].record()
+            V[nm] = V0t.clone()
+            otm.sgd_run_lp(V[nm], q, q, q, yb3, perm, ep, b, c["beta0"], c["theta"], alpha0, pr)
+            ev[4 + 2 * j].record()
+        torch.cuda.synchronize()
+        t = {"whiten_project_mean": ev[0].elapsed_time(ev[1]),
+             "sgd_fp32": ev[1].elapsed_time(ev[2]),
+             "quantize_bf16": ev[2].elapsed_time(ev[3]), "sgd_bf16": ev[3].elapsed_time(ev[4]),
+             "quantize_fp8": ev[4].elapsed_time(ev[5]), "sgd_fp8": ev[5].elapsed_time(ev[6])}
+        return t, wh, Y, yb3, V
+
+    for _ in range(args.warmup):
+        one()
+    sampler = ClockSampler(0)
+    sampler.start()
+    runs = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        t, wh, Y, yb3, V = one()
+        runs.append(t)
+    clocks = sampler.stop()
+    med = {key: statistics.median(r[key] for r in runs) for key in runs[0]}
+    samples = n * ep
+
+    # errors of the low-precision results against the FP32 one
+    nr = V["fp32"].double().norm(dim=1)
+    kappa = 0.5 * (1.0 + c["theta"])
+    lam = (kappa * nr ** 3).contiguous()
+    U = (V["fp32"].double() / nr[:, None]).contiguous()
+    topics = {nm: otm.unwhiten(V[nm], wh["Q"], wh["Cp"], c["theta"], True)["comps"]
+              for nm in V}
+    vs32 = {nm: {"recon_rel_err": float(otm.recon_error(V[nm], U, lam, c["theta"])[0]),
+                 "topics_rel_err": float((topics[nm] - topics["fp32"]).norm()
+                                         / topics["fp32"].norm())}
+            for nm in precs}
+    # FP64 oracle checks of single stages on a sample
+    docs = perm_h[0][: c["proj_docs"]]
+    idx = torch.from_numpy(perm_h[0][:b].astype(np.int64)).to(dev)
+    Yb = Y[idx].contiguous()
+    V1 = {"fp32": V0t.clone()}
+    otm.sgd_step(V1["fp32"], Yb, Yb, Yb, yb3, c["theta"], c["beta0"], alpha0)
+    for nm, pr in precs.items():
+        qb = otm.quantize_samples(Yb, pr)
+        V1[nm] = V0t.clone()
+        otm.sgd_run_lp(V1[nm], qb, qb, qb, yb3, None, 1, b, c["beta0"], c["theta"], alpha0, pr)
+    torch.cuda.synchronize()
+    checks = lda_oracle_checks(X, wh["W"].cpu().numpy(), Y[torch.from_numpy(
+        docs.astype(np.int64)).to(dev)].cpu().numpy(), docs, V0h, Yb.cpu().numpy(),
+        yb3[0].cpu().numpy(), c, {nm: v.cpu().numpy().T for nm, v in V1.items()})
+    from oracle import post as opost
+    Qh = wh["Q"].cpu().numpy().astype(np.float64)
+    mu_ref = opost.unwhiten(V["fp32"].cpu().numpy().T.astype(np.float64),
+                            Qh @ wh["Cp"].cpu().numpy(), c["theta"], True)["mu"]
+    checks["unwhiten_fp32_rel_err"] = _rel(topics["fp32"].cpu().numpy(), mu_ref)
+
+    per = {nm: {"sgd_ms": med["sgd_" + nm], "samples_per_s": samples / (med["sgd_" + nm] / 1e3)}
+           for nm in ("fp32", "bf16", "fp8")}
+    for nm in precs:
+        per[nm]["quantize_ms"] = med["quantize_" + nm]
+        per[nm]["vs_fp32"] = vs32[nm]
+    return {"metric": "whitened-sample SGD throughput (samples/s), BF16 precision form",
+            "value": per["bf16"]["samples_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sum(med.values()),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": c["workload"], "docs": n, "vocabulary": d, "k": k,
+                       "nnz": int(X.nnz), "alpha0": alpha0, "minibatch": b, "epochs": ep,
+                       "beta0": c["beta0"], "theta": c["theta"], "samples_per_run": samples,
+                       "l2": "flushed before each iteration (256 MiB write)",
+                       "host_generation_s": round(gen_s, 1)},
+            "whiten_project_mean_ms": med["whiten_project_mean"], "precisions": per,
+            "oracle_checks": checks, "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -813,10 +963,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="mmsb",
-                    choices=["mmsb", "batched", "warmstart", "whitening"],
+                    choices=["mmsb", "batched", "warmstart", "whitening", "lda"],
                     help="mmsb: the default pipeline line; batched: the batched form; "
                          "warmstart: time to 1e-3 with the learned start; whitening: both "
-                         "randomised whitening forms on an LDA corpus")
+                         "randomised whitening forms on an LDA corpus; lda: the precision "
+                         "form on a 300,000-document LDA corpus")
     ap.add_argument("--k", type=int, default=0, help="warmstart: components (default 64)")
     ap.add_argument("--problems", type=int, default=512)
     ap.add_argument("--restarts", type=int, default=8)
@@ -834,6 +985,8 @@ def main():
         line = run_warmstart(args) if rank == 0 else None
     elif args.workload == "whitening":
         line = run_whitening(args) if rank == 0 else None
+    elif args.workload == "lda":
+        line = run_lda(args) if rank == 0 else None
     elif args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
