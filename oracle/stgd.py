@@ -24,16 +24,21 @@ Readings of the paper used here:
     samples (the Gram term once per step); the last, partial minibatch of an
     epoch is kept and averaged over its own size.
   * Step size beta_t = beta0 / sqrt(t), t the global step counted from 1.
+  * grad_implicit_topic_exact keeps the self-token terms of Eq. (3) that the
+    sample tensor of Section 3.2 drops (its bias is O(1/l)): the data tensor is
+    M3(W, W, W) of Eq. (3) estimated on the minibatch documents (per-document
+    normalisation as for the moments, documents too short for a term add zero
+    to it, the average over all b documents), M1 the full-data first moment.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .moments import coefficients
+from .moments import as_sparse, coefficients
 
 __all__ = [
     "kappa", "whitened_tensor", "contract", "loss_explicit", "grad_explicit",
-    "grad_implicit", "sgd_step", "sgd_run", "steps_per_epoch",
+    "grad_implicit", "grad_implicit_topic_exact", "sgd_step", "sgd_run", "steps_per_epoch",
 ]
 
 
@@ -109,6 +114,60 @@ def grad_implicit(V, YA, YB, YC, ybar3, theta: float, alpha0: float) -> np.ndarr
         gram = np.zeros(V.shape[0])
         for j in range(k):
             gram += (V[:, j] @ phi) ** 2 * V[:, j]
+        G[:, i] = kap * gram - data
+    return G
+
+
+def grad_implicit_topic_exact(V, Xb, W, M1, theta: float, alpha0: float) -> np.ndarray:
+    """Implicit gradient (Lemma 3 form, G = kappa V((V^T V)o2) - T(V, V, I)) for
+    the topic model with the exact third moment of Eq. (3) whitened by W
+    (d x k), estimated on the minibatch count rows Xb, without forming it.
+
+    For component v, u = W v, and document t with counts c (length l),
+    y' = W^T c, s = <c, u>, q = sum_j c_j u_j^2, r = W^T (c o u),
+    z = W^T (c o u o u), m = W^T M1, mu = <m, v>:
+      bracket of Eq. (3) at (u, u, W):   s^2 y' - q y' - 2 s r + 2 z
+      pair moment P2 at (u, u):          s^2 - q
+      P2 W v (positions (1,3) and (2,3)): s y' - r
+      T_t(v, v, I) = c1 [s^2 y' - q y' - 2 s r + 2 z] / (l (l-1) (l-2))
+                     - c2 ([s^2 - q] m + 2 mu [s y' - r]) / (l (l-1)),
+    averaged over the b documents, plus c3 mu^2 m.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    m = W.T @ np.asarray(M1, dtype=np.float64)
+    Xs = as_sparse(Xb)
+    n = Xs.shape[0]
+    c1, c2, c3 = coefficients(alpha0)
+    kap = kappa(theta)
+    k = V.shape[1]
+    G = np.empty_like(V)
+    for i in range(k):
+        v = V[:, i]
+        u = W @ v
+        mu = m @ v
+        acc = np.zeros(V.shape[0])
+        for t in range(n):
+            lo, hi = Xs.indptr[t], Xs.indptr[t + 1]
+            idx = Xs.indices[lo:hi]
+            c = Xs.data[lo:hi]
+            l = c.sum()
+            Wt = W[idx]
+            ut = u[idx]
+            yp = Wt.T @ c
+            s_ = yp @ v
+            q = c @ (ut * ut)
+            r = Wt.T @ (c * ut)
+            z = Wt.T @ (c * ut * ut)
+            if l >= 3:
+                acc += c1 * (s_ * s_ * yp - q * yp - 2.0 * s_ * r + 2.0 * z) / (
+                    l * (l - 1.0) * (l - 2.0))
+            if l >= 2:
+                acc -= c2 * ((s_ * s_ - q) * m + 2.0 * mu * (s_ * yp - r)) / (l * (l - 1.0))
+        data = acc / n + c3 * mu * mu * m
+        gram = np.zeros(V.shape[0])
+        for j in range(k):
+            gram += (V[:, j] @ v) ** 2 * V[:, j]
         G[:, i] = kap * gram - data
     return G
 

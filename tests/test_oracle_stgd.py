@@ -186,3 +186,54 @@ def test_match_components_inverts_permutation_and_signs():
     assert err < 1e-12
     np.testing.assert_array_equal(perm, p)
     np.testing.assert_array_equal(signs, s)
+
+
+# --- exact self-token corrections (topic model, Eq. (3) kept whole) ---------
+
+def _tiny_corpus(seed, n, d, lengths):
+    """Count rows with the given document lengths (some below 3 on purpose)."""
+    g = np.random.default_rng(seed)
+    dense = np.zeros((n, d))
+    for t in range(n):
+        words = g.integers(0, d, size=lengths[t % len(lengths)])
+        np.add.at(dense[t], words, 1.0)
+    return synth.csr_from_dense(dense)
+
+
+@pytest.mark.parametrize("alpha0,theta", [(0.0, 1.0), (1.0, 1.0), (0.7, 2.0)])
+def test_exact_topic_gradient_is_third_of_explicit_eq3_gradient(alpha0, theta):
+    """The implicit per-document formula equals (1/3) grad L~ of the explicit
+    whitened tensor M3(W, W, W), with M3 from the brute-force-pinned Eq. (3)
+    moments of the same documents (lengths 1 and 2 included: they add nothing
+    to the terms they are too short for)."""
+    d, k = 9, 4
+    X = _tiny_corpus(3, 25, d, [1, 2, 3, 5, 8, 13])
+    g = np.random.default_rng(4)
+    W = g.standard_normal((d, k))
+    V = g.standard_normal((k, k))
+    M3 = om.topic_third_moment(X, alpha0)
+    T = np.einsum("abc,ai,bj,ck->ijk", M3, W, W, W)
+    G = stgd.grad_implicit_topic_exact(V, X, W, om.topic_first_moment(X), theta, alpha0)
+    np.testing.assert_allclose(3.0 * G, stgd.grad_explicit(V, T, theta), rtol=1e-11,
+                               atol=1e-11)
+
+
+def test_exact_topic_gradient_approaches_sample_tensor_for_long_documents():
+    """The self-token terms are O(1/l): for documents of l words the exact
+    gradient and the sample-tensor gradient of Section 3.2 (y = W^T c / l)
+    differ by a relative amount that shrinks like 1/l."""
+    d, k, alpha0, theta = 30, 4, 1.0, 1.0
+    g = np.random.default_rng(5)
+    W = g.standard_normal((d, k))
+    V = g.standard_normal((k, k))
+    gaps = []
+    for L in (50, 400):
+        X = _tiny_corpus(6, 40, d, [L])
+        M1 = om.topic_first_moment(X)
+        Y = (om.as_sparse(X) @ W) / L
+        yb = W.T @ M1
+        G_exact = stgd.grad_implicit_topic_exact(V, X, W, M1, theta, alpha0)
+        G_samp = stgd.grad_implicit(V, Y, Y, Y, (yb, yb, yb), theta, alpha0)
+        gaps.append(np.linalg.norm(G_exact - G_samp) / np.linalg.norm(G_samp))
+    assert gaps[1] < gaps[0] / 4.0                # 8x longer documents: ~8x smaller
+    assert gaps[1] < 5e-2
