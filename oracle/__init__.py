@@ -13,7 +13,9 @@ Modules and the part of the paper each follows:
   whiten   -- Section 3.1 (whitening W^T M2 W = I), Section 4.2 (randomised
               low-rank whitening and pseudo-inverse, Algorithms 2 and 3).
   stgd     -- Section 3.2 (whitened tensor, loss Eq. (15), Lemma 3 / Eq. (16)
-              stochastic update), Appendix A (gradient, shift operator).
+              stochastic update), Appendix A (gradient, shift operator); the
+              same gradient with the whole Eq. (3) for topics (self-token
+              terms kept).
   post     -- Section 3.3 Lemma 4 (eigenvalues, unwhitening, alpha estimate),
               plus the reconstruction error used to measure convergence.
   community-- Section 3.3 Lemma 4, community case (membership Pi_hat,
