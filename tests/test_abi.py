@@ -88,3 +88,42 @@ def test_workspace_sizes_monotone(lib):
     a = lib.otm_whiten_topic_workspace(100, 50, 5, 10)
     b = lib.otm_whiten_topic_workspace(1000, 500, 5, 10)
     assert 0 < a < b
+
+
+def test_host_side_errors_of_membership_validation_and_nystrom(lib):
+    """The newer entry points reject bad sizes on the host (OTM_EINVAL) before
+    any CUDA call, so these run without a GPU."""
+    from paper_1309_0787_gb300 import otm
+    lib.otm_last_error.restype = ctypes.c_char_p
+    vp, i64, f64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    m = lib.otm_membership
+    m.argtypes = [vp, i64, i64, vp, f64, f64, vp, vp, sz, vp]
+    assert m(vp(16), 10, 0, vp(16), 1.0, 0.0, vp(16), vp(16), 1 << 20, None) == 1   # k = 0
+    assert m(vp(16), 10, 1025, vp(16), 1.0, 0.0, vp(16), vp(16), 1 << 20, None) == 1
+    assert m(vp(16), -1, 4, vp(16), 1.0, 0.0, vp(16), vp(16), 1 << 20, None) == 1
+    assert m(vp(16), 10, 4, None, 1.0, 0.0, vp(16), vp(16), 1 << 20, None) == 1    # V null
+    assert m(vp(16), 10, 4, vp(16), 1.0, 0.0, vp(16), vp(16), 0, None) == 1        # workspace
+    assert b"workspace" in lib.otm_last_error()
+    p = lib.otm_pvalue_match
+    p.argtypes = [vp, i64, vp, i64, i64, f64, vp, vp, vp, vp, sz, vp]
+    assert p(vp(16), 3, vp(16), 3, 2, 0.01, vp(16), vp(16), vp(16), vp(16), 1 << 20, None) == 1
+    assert b"n >= 3" in lib.otm_last_error()
+    assert p(vp(16), 3, vp(16), 1025, 10, 0.01, vp(16), vp(16), vp(16), vp(16), 1 << 20,
+             None) == 1
+    assert p(vp(16), 3, None, 3, 10, 0.01, vp(16), vp(16), vp(16), vp(16), 1 << 20, None) == 1
+    w = lib.otm_whiten_topic_nystrom
+    w.argtypes = [ctypes.POINTER(otm.OtmCsr), vp, i64, i64, f64] + [vp] * 9 + [sz, vp]
+    X = otm.OtmCsr(10, 40, 20, 16, 16, 16)
+    outs = [vp(16)] * 8                          # S (vp(32)) must not alias O
+    assert w(ctypes.byref(X), vp(32), 5, 5, 1.0, *outs, vp(16), 1 << 30, None) == 1   # kt = k
+    assert w(ctypes.byref(X), vp(32), 5, 161, 1.0, *outs, vp(16), 1 << 30, None) == 1
+    assert w(ctypes.byref(X), vp(32), 5, 41, 1.0, *outs, vp(16), 1 << 30, None) == 1  # kt > d
+    assert w(ctypes.byref(X), vp(32), 5, 10, -1.0, *outs, vp(16), 1 << 30, None) == 1
+    assert w(ctypes.byref(X), vp(32), 5, 10, 1.0, *outs, vp(16), 0, None) == 1
+    assert b"workspace" in lib.otm_last_error()
+    assert w(ctypes.byref(X), vp(16), 5, 10, 1.0, *outs, vp(16), 1 << 30, None) == 1
+    assert b"alias" in lib.otm_last_error()
+    lib.otm_whiten_topic_nystrom_workspace.restype = sz
+    lib.otm_whiten_topic_nystrom_workspace.argtypes = [i64] * 4
+    assert 0 < lib.otm_whiten_topic_nystrom_workspace(10, 40, 5, 10) < \
+        lib.otm_whiten_topic_nystrom_workspace(1000, 4000, 5, 10)
