@@ -1,0 +1,51 @@
+"""Host-side logic of bench.py that needs no GPU: the algorithmic flop count
+behind the STGD roofline, the per-rank workload, and the oracle stage checks of
+the LDA precision workload (fed the oracle's own results, they report zero)."""
+import numpy as np
+
+import bench
+import synth
+from oracle import moments as om
+from oracle import stgd as ostgd
+
+
+def test_sgd_flops_closed_form():
+    # per step 6 k^2 b_s (two projections and the data product, three views) + 4 k^3
+    cfg = dict(bench.CFG)
+    flops, steps = bench.sgd_flops(cfg)
+    n, b, k, ep = cfg["n_per"], cfg["b"], cfg["k"], cfg["epochs"]
+    per_epoch = -(-n // b)
+    assert steps == per_epoch * ep
+    assert flops == ep * (6 * k * k * n + per_epoch * 4 * k ** 3)
+    assert flops == 6.4e9                           # the MMSB k = 100 line
+
+
+def test_make_inputs_shapes_and_rank_seeds():
+    cfg = dict(bench.CFG)
+    cfg.update(n_per=80, k=5, oversample=3, epochs=2)
+    a = bench.make_inputs(cfg, 0)
+    b = bench.make_inputs(cfg, 1)
+    assert a["S_pairs"].shape == (80, 8) and a["perm"].shape == (2, 80)
+    assert a["V0"].shape == (5, 5) and a["Pi_X"].shape == (80, 5)
+    np.testing.assert_allclose(a["V0"].T @ a["V0"], np.eye(5), atol=1e-5)
+    assert not np.array_equal(a["S_w"], b["S_w"])
+
+
+def test_lda_oracle_checks_zero_on_oracle_inputs():
+    c = dict(bench.LDA3)
+    c.update(k=6, b=40)
+    corp = synth.lda_corpus(1, 300, 50, 6, 0.1, 0.1, 30)
+    X = corp["X"]
+    W = np.random.default_rng(2).standard_normal((50, 6))
+    Xs = om.as_sparse(X)
+    Y = (Xs @ W) / np.asarray(Xs.sum(axis=1)).ravel()[:, None]
+    docs = np.arange(0, 300, 11).astype(np.int32)
+    V0 = synth.haar_orthonormal(3, 6).astype(np.float64)
+    Yb, yb = Y[:40], Y.mean(axis=0)
+    V1 = ostgd.sgd_step(V0, Yb, Yb, Yb, (yb, yb, yb), c["theta"], c["beta0"],
+                        6 * c["alpha_i"])
+    out = bench.lda_oracle_checks(X, W, Y[docs], docs, V0, Yb, yb, c,
+                                  {"fp32": V1, "off": V0 + 1.1 * (V1 - V0)})
+    assert out["projection_rel_err"] < 1e-14
+    assert out["step_update_rel_err"]["fp32"] < 1e-12
+    assert abs(out["step_update_rel_err"]["off"] - 0.1) < 1e-9
