@@ -838,6 +838,13 @@ def lda_oracle_checks(X, W, Y_docs, docs, V0, Yb, yb, c, V1):
                                     for p, v in V1.items()}}
 
 
+def sym_sgd_flops(n, b, k, epochs):
+    """Algorithmic flops of an STGD run with symmetric views: per step
+    2k^2 b_s (A = V^T Y) + 2k^2 b_s (Y^T B^T) + 4k^3 (Gram term)."""
+    sizes = [min(b, n - s) for s in range(0, n, b)] * epochs
+    return sum(4 * k * k * bs + 4 * k ** 3 for bs in sizes)
+
+
 def run_lda(args):
     """Precision form on a large LDA corpus: 300,000 documents of Poisson(300)
     words over 100,000 words with Zipf-skewed Dir(0.05) topics, k = 100,
@@ -936,6 +943,7 @@ def run_lda(args):
                             Qh @ wh["Cp"].cpu().numpy(), c["theta"], True)["mu"]
     checks["unwhiten_fp32_rel_err"] = _rel(topics["fp32"].cpu().numpy(), mu_ref)
 
+    flops = sym_sgd_flops(n, b, k, ep)
     per = {nm: {"sgd_ms": med["sgd_" + nm], "samples_per_s": samples / (med["sgd_" + nm] / 1e3)}
            for nm in ("fp32", "bf16", "fp8")}
     for nm in precs:
@@ -953,6 +961,15 @@ def run_lda(args):
                        "l2": "flushed before each iteration (256 MiB write)",
                        "host_generation_s": round(gen_s, 1)},
             "whiten_project_mean_ms": med["whiten_project_mean"], "precisions": per,
+            "roofline": {"kernel": "sgd_tc_kernel (BF16, one launch = all 5,860 STGD steps)",
+                         "bound": "tensor", "achieved": flops / (med["sgd_bf16"] / 1e3) / 1e12,
+                         "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops / (med["sgd_bf16"] / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+                         "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops",
+                         "algorithmic_flops_per_launch": flops,
+                         "fp32_grid_form_frac_of_fp32_peak":
+                             flops / (med["sgd_fp32"] / 1e3) / 1e12 / FP32_FMA_PEAK_TFLOPS,
+                         "note": "one chain: latency-bound per step in every form"},
             "oracle_checks": checks, "clocks": clocks}
 
 

@@ -49,3 +49,9 @@ def test_lda_oracle_checks_zero_on_oracle_inputs():
     assert out["projection_rel_err"] < 1e-14
     assert out["step_update_rel_err"]["fp32"] < 1e-12
     assert abs(out["step_update_rel_err"]["off"] - 0.1) < 1e-9
+
+
+def test_sym_sgd_flops_closed_form():
+    # 300,000 samples, b = 1,024: 292 full minibatches and one of 992 per epoch
+    f = bench.sym_sgd_flops(300000, 1024, 100, 20)
+    assert f == 20 * (4 * 100 ** 2 * 300000 + 293 * 4 * 100 ** 3)
