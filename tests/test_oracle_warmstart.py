@@ -150,3 +150,25 @@ def test_canonical_frame_diagonalises_first_sketch():
     x, E2 = ws.canonical_input(S)
     np.testing.assert_array_equal(E, E2)
     np.testing.assert_allclose(np.linalg.norm(x), np.linalg.norm(ws.mlp_input(S)), rtol=1e-12)
+
+
+def test_sketches_match_implicit_formula():
+    """The sketches built from the explicit whitened tensor equal the implicit
+    form S_j = (1/n) Y^T diag(c1 Y th_j - c2 <th_j, yb>) Y - c2 (m_j yb^T + yb m_j^T)
+    + c3 <th_j, yb> yb yb^T with m_j = (1/n) Y^T (Y th_j) (Section 3.2's tensor
+    contracted in its third mode; no k^3 tensor)."""
+    from oracle.moments import coefficients
+    g = np.random.default_rng(9)
+    n, k, alpha0 = 60, 5, 0.8
+    Y = g.standard_normal((n, k)) + 0.2
+    yb = Y.mean(axis=0)
+    th = g.standard_normal((3, k))
+    c1, c2, c3 = coefficients(alpha0)
+    S = ws.sketches(Y, yb, alpha0, th)
+    for j in range(3):
+        a = Y @ th[j]
+        m = Y.T @ a / n
+        p = th[j] @ yb
+        want = (Y.T * (c1 * a - c2 * p)) @ Y / n - c2 * (np.outer(m, yb) + np.outer(yb, m)) \
+            + c3 * p * np.outer(yb, yb)
+        np.testing.assert_allclose(S[j], want, rtol=1e-12, atol=1e-12)
