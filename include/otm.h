@@ -63,7 +63,7 @@ typedef struct otm_csr {
   const float* val;        /* nnz */
 } otm_csr;
 
-/* Library version (major * 10000 + minor * 100 + patch). */
+/* Library version (major * 10000 + minor * 100 + patch); no paper counterpart. */
 int otm_version(void);
 
 /* Message describing the calling thread's last error ("" if none). */
@@ -607,7 +607,8 @@ otm_status otm_unwhiten(const float* V, int64_t k, const float* Q, int64_t d, in
                         void* stream);
 
 /*
- * otm_recon_error -- relative reconstruction error of the components in V
+ * otm_recon_error -- (not in the paper: the convergence measure of the
+ * benchmark) relative reconstruction error of the components in V
  * against reference components (lam_true[k], U_true: k x k column-major FP64,
  * unit columns):
  *   err = || kappa sum_i v_i^(x)3 - sum_j lam_j u_j^(x)3 ||_F / || sum_j lam_j u_j^(x)3 ||_F,
