@@ -154,3 +154,31 @@ def test_match_scores_false_pairing_counts_in_error():
 def test_pvalue_matrix_needs_three_nodes():
     with pytest.raises(ValueError):
         oc.pvalue_matrix(np.ones((1, 2)), np.ones((1, 2)))
+
+
+def test_pvalue_graph_of_the_papers_figure():
+    """The paper's example graph (golden fixture, 1-based indices as printed):
+    estimated rows 2, 3, 6 pair with ground truth 1; 1 with 2; 4, 5 with 4;
+    ground truth 3 has no partner, so R = 3/4.  Memberships realising it:
+    disjoint blocks of nodes for the ground truth, each estimated row an affine
+    copy 0.9 Pi_j + 0.05 of its partner (rho = 1, p = 0; against the other
+    blocks rho < 0, p > 1/2), so every pair's l1 / n is 0.05 and E = 6 x 0.05 / 4."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden",
+                           "pvalue_graph_figure.json")) as f:
+        fig = json.load(f)
+    k, k_hat, blk = fig["ground_truth_communities"], fig["estimated_communities"], 50
+    n = k * blk
+    Pi = np.zeros((k, n))
+    for j in range(k):
+        Pi[j, j * blk:(j + 1) * blk] = 1.0
+    est = np.zeros((k_hat, n))
+    for i, j in fig["edges_estimated_to_truth"]:
+        est[i - 1] = 0.9 * Pi[j - 1] + 0.05
+    s = oc.match_scores(est, Pi, 0.01)
+    edges = {(int(i) + 1, int(j) + 1) for i, j in zip(*np.nonzero(s["edges"]))}
+    assert edges == {tuple(e) for e in fig["edges_estimated_to_truth"]}
+    np.testing.assert_array_equal(s["degree"], fig["degrees_of_truth"])
+    assert s["recovery"] == fig["recovery_ratio"]
+    assert abs(s["error"] - 6 * 0.05 / 4) < 1e-12
