@@ -134,3 +134,26 @@ def test_nystrom_whiten_rejects_indefinite():
     S = synth.signed_column_selection(8, 20, 8).astype(np.float64)
     with pytest.raises(ow.NotPositiveDefinite):
         ow.nystrom_whiten(lambda Z: -M2 @ Z, S, 3)
+
+
+def test_nystrom_gram_form_equals_printed_product():
+    """The GPU evaluates Algorithm 2 from the eigenpairs of the small Gram
+    matrix O^T O instead of an SVD of the tall O: W = O V_G,k diag(1/ev_G)
+    V_G,k^T V_Om,k L_Om,k^{1/2} (U_O = O V_O L_O^{-1}), and (W^T)^+ = O C H^{-1}
+    with H = C^T (O^T O) C.  Checked here in FP64 against the oracle's printed
+    product on an indefinite, full-rank M2 (the general case)."""
+    d, k, kt = 60, 6, 14
+    g = np.random.default_rng(12)
+    A = g.standard_normal((d, d))
+    M2 = A @ A.T / d - 0.3 * np.eye(d)
+    S = synth.signed_column_selection(13, d, kt).astype(np.float64)
+    ref = ow.nystrom_whiten(lambda Z: M2 @ Z, S, k)
+    O = M2 @ S
+    evG, VG = np.linalg.eigh(O.T @ O)
+    evG, VG = evG[::-1][:k], VG[:, ::-1][:, :k]
+    lam, VO = ow.top_eigh(S.T @ O, k)
+    C = VG @ np.diag(1.0 / evG) @ VG.T @ VO * np.sqrt(lam)
+    W = O @ C
+    np.testing.assert_allclose(W, ref["W"], rtol=1e-9, atol=1e-12)
+    H = C.T @ (O.T @ O) @ C
+    np.testing.assert_allclose(O @ C @ np.linalg.inv(H), ref["Wplus"], rtol=1e-8, atol=1e-10)
