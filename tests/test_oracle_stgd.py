@@ -237,3 +237,44 @@ def test_exact_topic_gradient_approaches_sample_tensor_for_long_documents():
         gaps.append(np.linalg.norm(G_exact - G_samp) / np.linalg.norm(G_samp))
     assert gaps[1] < gaps[0] / 4.0                # 8x longer documents: ~8x smaller
     assert gaps[1] < 5e-2
+
+
+def test_exact_topic_gradient_in_gathered_gemm_form():
+    """The form a kernel would evaluate (all word occurrences e = (t, j) of the
+    minibatch at once): gathered rows W_g (nnz x k), U_e = W_j V, per-document
+    S = Y' V and q; then the self-token terms are ONE product W_g^T Coef with
+    Coef_e = c_e U_e (2 w2_t mu - 2 w3_t S_t) + 2 w3_t c_e U_e^2, the sample terms
+    Y'^T A with A_t = w3_t (S_t^2 - q_t) - 2 w2_t mu S_t, plus m terms.  Checked
+    against the oracle's per-document loop (FP64)."""
+    from oracle.moments import coefficients
+    d, k, alpha0, theta = 20, 5, 0.8, 1.5
+    X = _tiny_corpus(8, 30, d, [1, 2, 4, 7, 12])
+    g = np.random.default_rng(9)
+    W = g.standard_normal((d, k))
+    V = g.standard_normal((k, k))
+    M1 = om.topic_first_moment(X) + 0.01
+    c1, c2, c3 = coefficients(alpha0)
+    Xs = om.as_sparse(X)
+    b = Xs.shape[0]
+    rows = np.repeat(np.arange(b), np.diff(Xs.indptr))       # document of each occurrence
+    cols, cnt = Xs.indices, Xs.data
+    l = np.asarray(Xs.sum(axis=1)).ravel()
+    w3 = np.where(l >= 3, c1 / np.maximum(l * (l - 1) * (l - 2), 1), 0.0)
+    w2 = np.where(l >= 2, c2 / np.maximum(l * (l - 1), 1), 0.0)
+    Wg = W[cols]                                              # nnz x k
+    U = Wg @ V                                                # U_e[i] = <W_j, v_i>
+    Yp = Xs @ W                                               # b x k, rows y'_t
+    S = Yp @ V                                                # S[t, i] = <y'_t, v_i>
+    q = np.zeros((b, k))
+    np.add.at(q, rows, cnt[:, None] * U * U)
+    m = W.T @ M1
+    mu = m @ V                                                # mu_i = <m, v_i>
+    coef = (cnt[:, None] * U * (2 * w2[rows, None] * mu - 2 * w3[rows, None] * S[rows])
+            + 2 * w3[rows, None] * cnt[:, None] * U * U)
+    A = w3[:, None] * (S * S - q) - 2 * w2[:, None] * mu * S
+    data = (Wg.T @ coef + Yp.T @ A - np.outer(m, (w2[:, None] * (S * S - q)).sum(axis=0))) / b
+    data += c3 * m[:, None] * mu ** 2
+    Gm = V.T @ V
+    G = stgd.kappa(theta) * V @ (Gm ** 2) - data
+    np.testing.assert_allclose(G, stgd.grad_implicit_topic_exact(V, X, W, M1, theta, alpha0),
+                               rtol=1e-11, atol=1e-11)
