@@ -157,11 +157,10 @@ otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, vo
  * Scratch: a fixed 2 MiB array inside the library, present on every GPU on
  * which the library is loaded until the process exits.  The call allocates
  * nothing.  The first call on a device looks up the array's address on that
- * device (the current device; `stream` must belong to it); make that first
- * call before any stream capture begins.  All calls on one device share the
- * array: calls whose work overlaps on the GPU (other streams, other host
- * threads) race and give wrong results, so serialise them.  Synchronises the
- * stream.
+ * device (the current device; `stream` must belong to it).  All calls on one
+ * device share the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and give wrong results, so serialise them.
+ * Every call copies a status flag to the host and synchronises the stream.
  */
 otm_status otm_syev_noalloc(const double* A, int64_t n, double* evals, double* evecs,
                             void* stream);

@@ -181,6 +181,11 @@ def _ptr(t):
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
+    # the library launches on the current device and stream: a tensor that lives
+    # on another GPU would be dereferenced by a kernel on this one
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"tensor on {t.device}, but the current CUDA device is "
+                         f"cuda:{torch.cuda.current_device()}")
     return c_vp(t.data_ptr())
 
 
@@ -221,6 +226,9 @@ class DeviceCSR:
         return self.row_ptr.device
 
     def ref(self):
+        if not self.row_ptr.is_cuda or self.row_ptr.device.index != torch.cuda.current_device():
+            raise ValueError(f"CSR on {self.row_ptr.device}, but the current CUDA device is "
+                             f"cuda:{torch.cuda.current_device()}")
         return ctypes.byref(self._desc)
 
 

@@ -42,6 +42,26 @@ def test_syev_noalloc_matches_syev_two_calls():
         assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-11
 
 
+def test_syev_noalloc_allocates_nothing():
+    """The point of the entry point: once a warm-up call has loaded its kernels,
+    a further call takes no device memory (neither from the driver nor from
+    torch's caching allocator)."""
+    from paper_1309_0787_gb300 import otm
+    n = 120
+    A = torch.as_tensor(_matrix(7, n)).cuda()
+    ev = torch.empty(n, dtype=torch.float64, device="cuda")
+    vec = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    otm.syev_noalloc(A, ev, vec)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    torch0 = torch.cuda.memory_reserved()
+    otm.syev_noalloc(A, ev, vec)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert torch.cuda.memory_reserved() == torch0
+
+
 def test_syev_noalloc_rejects_too_large():
     from paper_1309_0787_gb300 import otm
     n = 161
