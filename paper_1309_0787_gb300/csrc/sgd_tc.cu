@@ -35,6 +35,14 @@
 // tile (FP8).  Scales are applied to the FP32 accumulators in the epilogues.
 // The Gram term always uses the BF16 image of V.
 //
+// FP8 keeps V as two e4m3 terms with the same per-component scale s_i:
+// V_hi = e4m3(V / s_i) and V_lo = e4m3(V / s_i - V_hi), and issues the first
+// product once for each into the same accumulator, so that Y (V_hi + V_lo) s_i
+// carries about seven significant bits of V instead of four.  V's rounding is
+// common to every sample of a minibatch and does not average out over the
+// minibatch the way the per-sample rounding of the samples and of B does;
+// it was the largest error of the single-term form.
+//
 // Operand layouts in shared memory (no swizzle; 8-row x 16-byte core
 // matrices; LBO = stride between cores along K, SBO = along M/N):
 //   sample tile: core (tg, rg) = 8 samples x 16 B of coordinates at
@@ -137,7 +145,8 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   L.off_v[0] = NS * L.y_stage;
   L.off_v[1] = dbl && !L.vstr ? L.off_v[0] + v_bytes : L.off_v[0];
   L.off_vq = L.off_v[1] + v_bytes;
-  const size_t vq_bytes = es == 1 ? (size_t)N * KP : 0;
+  // FP8: two e4m3 images of the owned rows, V_hi and the residual V_lo (same scales)
+  const size_t vq_bytes = es == 1 ? (size_t)2 * N * KP : 0;
   const size_t b_bytes = (size_t)TILE * N * es;
   // the B images, the H image and the ybar image (16 rows: ybar_A, ybar_B, zeros;
   // rebuilt at the start of every step) share one region: they are live at
@@ -455,9 +464,13 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int i = c0 + j;
-            const __nv_fp8_e4m3 q(x[j] * (1.f / vsc[i]));
-            Vq[(((size_t)(i >> 3) * L.CR + (r >> 4)) << 7) + ((i & 7) << 4) + (r & 15)] =
-                *reinterpret_cast<const uint8_t*>(&q);
+            const float z = x[j] * (1.f / vsc[i]);
+            const __nv_fp8_e4m3 qh(z);
+            const __nv_fp8_e4m3 ql(z - float(qh));
+            const size_t off =
+                (((size_t)(i >> 3) * L.CR + (r >> 4)) << 7) + ((i & 7) << 4) + (r & 15);
+            Vq[off] = *reinterpret_cast<const uint8_t*>(&qh);
+            Vq[(size_t)N * KPc + off] = *reinterpret_cast<const uint8_t*>(&ql);
           }
         }
       return;
@@ -466,12 +479,14 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       const int i = idx / L.CR, rg = idx % L.CR;
       const float inv = 1.f / vsc[i];
       const float* vr = Vm + i * KPc + rg * 16;
-      uint4 w;
-      w.x = pack_e4m3(vr[0] * inv, vr[1] * inv, vr[2] * inv, vr[3] * inv);
-      w.y = pack_e4m3(vr[4] * inv, vr[5] * inv, vr[6] * inv, vr[7] * inv);
-      w.z = pack_e4m3(vr[8] * inv, vr[9] * inv, vr[10] * inv, vr[11] * inv);
-      w.w = pack_e4m3(vr[12] * inv, vr[13] * inv, vr[14] * inv, vr[15] * inv);
-      *reinterpret_cast<uint4*>(Vq + (((size_t)(i >> 3) * L.CR + rg) << 7) + ((i & 7) << 4)) = w;
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int z = 0; z < 4; ++z)
+        split_e4m3(vr[4 * z] * inv, vr[4 * z + 1] * inv, vr[4 * z + 2] * inv,
+                   vr[4 * z + 3] * inv, hi[z], lo[z]);
+      const size_t off = (((size_t)(i >> 3) * L.CR + rg) << 7) + ((i & 7) << 4);
+      *reinterpret_cast<uint4*>(Vq + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(Vq + (size_t)N * KPc + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
   };
   if (FP8) build_vq();
@@ -594,6 +609,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
       // descriptors (the start address is the low 14-bit field, in 16-byte units)
       const uint64_t dV_own = sdesc(WIDE ? Vown : Vc + own_off, 128, (uint32_t)L.CRb * 128);
       const uint64_t dVq = sdesc(Vq, 128, (uint32_t)L.CR * 128);
+      const uint64_t dVq_lo = sdesc(Vq + (size_t)N * KPc, 128, (uint32_t)L.CR * 128);
       const uint32_t id1 = make_idesc(FMT, 0, 0, TILE, (uint32_t)N);
       const uint32_t id2 = make_idesc(FMT, 1, 1, 128, (uint32_t)N);
 
@@ -603,9 +619,13 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         for (int v = 0; v < NVD; ++v) {
           const uint64_t dY = sdesc(Ys + v * L.y_view, 128, (uint32_t)L.CR * 128);
           const uint64_t dB = FP8 ? dVq : dV_own;
-          for (int ks = 0; ks < ks1; ++ks)
+          for (int ks = 0; ks < ks1; ++ks) {
             mma<FP8>(tmem + (uint32_t)((slot * NVD + v) * N), dY + (uint64_t)(16 * ks),
                      dB + (uint64_t)(16 * ks), id1, ks > 0 ? 1u : 0u);
+            if (FP8)  // the residual term of V into the same accumulator
+              mma<FP8>(tmem + (uint32_t)((slot * NVD + v) * N), dY + (uint64_t)(16 * ks),
+                       dVq_lo + (uint64_t)(16 * ks), id1, 1u);
+          }
         }
         mma_commit(&mb[slot]);
       };

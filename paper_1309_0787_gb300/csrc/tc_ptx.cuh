@@ -174,6 +174,15 @@ __device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d
   const __nv_fp8x4_e4m3 q(make_float4(a, b, c, d));
   return *reinterpret_cast<const uint32_t*>(&q);
 }
+// Two-term e4m3 rounding of four values: hi = e4m3(x), lo = e4m3(x - hi).
+__device__ __forceinline__ void split_e4m3(float a, float b, float c, float d, uint32_t& hi,
+                                           uint32_t& lo) {
+  const __nv_fp8x4_e4m3 h(make_float4(a, b, c, d));
+  const float4 hf = static_cast<float4>(h);
+  const __nv_fp8x4_e4m3 l(make_float4(a - hf.x, b - hf.y, c - hf.z, d - hf.w));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
 
 }  // namespace tc
 }  // namespace otm

@@ -4,7 +4,8 @@ many independent decompositions).
 Each chain of the batch runs the same Lemma 3 schedule as a single
 otm_sgd_run_lp call; with the same cluster size the two are bit-identical, with
 another cluster size they differ only in FP32 summation order.  Against the
-FP64 oracle the BF16 tolerance of the single-chain tests (2e-2 relative) holds.
+FP64 oracle the tolerance of the single-chain tests (2e-2 relative) holds for BF16
+and FP8.
 """
 import numpy as np
 import pytest
@@ -85,7 +86,7 @@ def test_batched_mixed_sizes_autotuned(otm, prec_name):
     assert batch.cluster in (1, 2, 4, 8, 16)
     batch.launch()
     batch.check()
-    tol = 1e-2 if prec == otm.PREC_BF16 else 3e-2
+    tol = 1e-2 if prec == otm.PREC_BF16 else 2e-2
     for p in probs:
         for r in range(p["V0"].shape[0]):
             Vs = _single(otm, p, r, prec)
@@ -144,7 +145,7 @@ def test_batched_two_groups_fp8(otm):
         for r in range(p["V0"].shape[0]):
             Vs = _single(otm, p, r, prec)
             torch.cuda.synchronize()
-            assert rel(to_np(p["V"][r]), to_np(Vs)) < 3e-2
+            assert rel(to_np(p["V"][r]), to_np(Vs)) < 2e-2
 
 
 def test_batched_two_groups_forced_cluster(otm):
@@ -164,9 +165,10 @@ def test_batched_two_groups_forced_cluster(otm):
             assert rel(to_np(p["V"][r]), to_np(Vs)) < 1e-2
 
 
-def test_batched_tracks_oracle(otm):
-    """Batched BF16 chains against the FP64 oracle run of Lemma 3."""
-    prec = otm.PREC_BF16
+@pytest.mark.parametrize("prec_name", ["PREC_BF16", "PREC_FP8"])
+def test_batched_tracks_oracle(otm, prec_name):
+    """Batched BF16 and FP8 chains against the FP64 oracle run of Lemma 3."""
+    prec = getattr(otm, prec_name)
     probs = [_problem(otm, 31, 16, 2000, 256, 4, 2, 5e-3, prec),
              _problem(otm, 41, 24, 1200, 128, 3, 2, 5e-3, prec)]
     batch = otm.SgdBatch(probs, prec)

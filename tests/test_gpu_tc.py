@@ -1,17 +1,19 @@
 """GPU parity of the tensor-core (BF16 / FP8) STGD against the FP64 oracle.
 
 The low-precision path quantises the samples, V and B (per-sample and
-per-component scales) and accumulates in FP32; the oracle computes Lemma 3 in
-FP64 from the unquantised samples.  Tolerance: 2e-2 normwise relative
-(||G - G64||_F / (||kappa G_gram||_F + ||G_data||_F)) for BF16; FP8 e4m3
-(3 mantissa bits) is measured and held to 6e-2.
+per-component scales) and accumulates in FP32; FP8 keeps V as two e4m3 terms.
+The oracle computes Lemma 3 in FP64 from the unquantised samples.  Tolerance
+for both precisions: 2e-2 normwise relative,
+||G - G64||_F / (||kappa G_gram||_F + ||G_data||_F), and the same ratio for
+every column (component) of G on its own, so that one wrong component or tile
+cannot hide inside the Frobenius norm.
 """
 import numpy as np
 import pytest
 
 import synth
 from oracle import stgd as ostgd
-from tests._util import rel, to_np
+from tests._util import grad_errs, rel, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -42,24 +44,67 @@ def _grad_err(otm, prec, k, b, sym, a0, seed):
     torch.cuda.synchronize()
     V64 = V0.astype(np.float64)
     G = ostgd.grad_implicit(V64, *[Y.astype(np.float64) for Y in Ys], tuple(yb), 1.0, a0)
-    gram = V64 @ (V64.T @ V64) ** 2
-    Gk = V64 - to_np(Vd).T.astype(np.float64)
-    return np.linalg.norm(Gk - G) / (np.linalg.norm(gram) + np.linalg.norm(gram - G))
+    return _errs(V64, V64 - to_np(Vd).T.astype(np.float64), G)
+
+
+def _errs(V64, Gk, G):
+    """(Frobenius, worst column) error of Gk against the oracle's G; theta = 1."""
+    return grad_errs(Gk, G, ostgd.kappa(1.0) * V64 @ (V64.T @ V64) ** 2)
 
 
 @pytest.mark.parametrize("k,b,sym,a0", [(100, 1024, False, 1.0), (100, 1024, True, 1.0),
                                         (10, 256, True, 1.0), (17, 100, False, 0.5),
                                         (64, 2000, True, 0.0), (128, 512, True, 1.0)])
 def test_tc_bf16_gradient(otm, k, b, sym, a0):
-    err = _grad_err(otm, otm.PREC_BF16, k, b, sym, a0, 3 * k + b)
-    assert err < 2e-2, err
+    frob, col = _grad_err(otm, otm.PREC_BF16, k, b, sym, a0, 3 * k + b)
+    assert frob < 2e-2 and col < 2e-2, (frob, col)
 
 
 @pytest.mark.parametrize("k,b,sym,a0", [(100, 1024, False, 1.0), (100, 1024, True, 1.0),
                                         (33, 300, False, 1.0), (128, 1024, True, 1.0)])
 def test_tc_fp8_gradient(otm, k, b, sym, a0):
-    err = _grad_err(otm, otm.PREC_FP8, k, b, sym, a0, 5 * k + b)
-    assert err < 6e-2, err
+    frob, col = _grad_err(otm, otm.PREC_FP8, k, b, sym, a0, 5 * k + b)
+    assert frob < 2e-2 and col < 2e-2, (frob, col)
+
+
+@pytest.fixture(scope="module")
+def lda_samples():
+    """Whitened samples of a synthetic LDA corpus (6,000 documents of Poisson(300)
+    words over 2,000 words, Zipf-skewed Dir(0.05) topics, k = 50, alpha0 = 0.5),
+    whitened and projected by the oracle (FP64), stored as float32."""
+    from oracle import moments as om
+    from oracle import whiten as ow
+    n, d, k = 6000, 2000, 50
+    c = synth.lda_corpus(0, n, d, k, 0.01, 0.05, 300, poisson_len=True, zipf=True)
+    a0 = 0.01 * k
+    S = synth.gaussian(1, d, k + 20).astype(np.float64)
+    wh = ow.range_finder_whiten(lambda Z: om.topic_second_moment_apply(c["X"], Z, a0), S, k, 2)
+    Xs = om.as_sparse(c["X"])
+    Y = ((Xs @ wh["W"]) / om.doc_lengths(Xs)[:, None]).astype(np.float32)
+    return Y, a0
+
+
+@pytest.mark.parametrize("prec_name", ["PREC_BF16", "PREC_FP8"])
+def test_tc_gradient_on_lda_samples(otm, lda_samples, prec_name):
+    """One step on a minibatch of whitened LDA samples (Section 3.1): the whitened
+    documents share a large mean and carry word-sampling noise, so the
+    alpha0-corrected terms of Lemma 3 cancel much more than on Gaussian samples.
+    Full-data means, Haar-random V."""
+    Y, a0 = lda_samples
+    k, b = Y.shape[1], 1024
+    prec = getattr(otm, prec_name)
+    yb = np.stack([Y.astype(np.float64).mean(axis=0)] * 3)
+    Yb = np.ascontiguousarray(Y[:b])
+    V0 = synth.haar_orthonormal(4, k).astype(np.float32)
+    q = otm.quantize_samples(_dev(Yb), prec)
+    Vd = _dev(V0.T.copy())
+    otm.sgd_run_lp(Vd, q, q, q, _dev(yb), None, 1, b, 1.0, 1.0, a0, prec)
+    torch.cuda.synchronize()
+    V64 = V0.astype(np.float64)
+    Y64 = Yb.astype(np.float64)
+    G = ostgd.grad_implicit(V64, Y64, Y64, Y64, tuple(yb), 1.0, a0)
+    frob, col = _errs(V64, V64 - to_np(Vd).T.astype(np.float64), G)
+    assert frob < 2e-2 and col < 2e-2, (frob, col)
 
 
 def test_tc_bf16_run_tracks_fp32_run(otm):
@@ -95,25 +140,25 @@ def test_quantize_samples_roundtrip(otm):
     assert np.all(to_np(qb)[:, 74:] == 0) and np.all(to_np(qf)[:, 37:] == 0)
 
 
-@pytest.mark.parametrize("k,b,prec_name,tol", [(200, 512, "PREC_BF16", 2e-2),
-                                               (256, 1024, "PREC_BF16", 2e-2),
-                                               (256, 512, "PREC_FP8", 6e-2)])
-def test_tc_gradient_beyond_128_components(otm, k, b, prec_name, tol):
+@pytest.mark.parametrize("k,b,prec_name", [(200, 512, "PREC_BF16"), (256, 1024, "PREC_BF16"),
+                                           (256, 512, "PREC_FP8"), (200, 1024, "PREC_FP8")])
+def test_tc_gradient_beyond_128_components(otm, k, b, prec_name):
     """k > 128: 256 padded coordinates, products per 128-row block (symmetric views)."""
-    err = _grad_err(otm, getattr(otm, prec_name), k, b, True, 1.0, 7 * k + b)
-    assert err < tol, err
+    frob, col = _grad_err(otm, getattr(otm, prec_name), k, b, True, 1.0, 7 * k + b)
+    assert frob < 2e-2 and col < 2e-2, (frob, col)
 
 
-@pytest.mark.parametrize("prec_name,tol", [("PREC_BF16", 2e-2), ("PREC_FP8", 6e-2)])
-def test_tc_three_views_beyond_128(otm, prec_name, tol):
+@pytest.mark.parametrize("prec_name", ["PREC_BF16", "PREC_FP8"])
+def test_tc_three_views_beyond_128(otm, prec_name):
     """k > 128 with three distinct views (16-CTA cluster, one sample stage of
     three views): one step against the oracle's implicit gradient."""
-    err = _grad_err(otm, getattr(otm, prec_name), 160, 512, False, 1.0, 41)
-    assert err < tol, err
+    frob, col = _grad_err(otm, getattr(otm, prec_name), 160, 512, False, 1.0, 41)
+    assert frob < 2e-2 and col < 2e-2, (frob, col)
 
 
-@pytest.mark.parametrize("prec_name,tol,sym", [("PREC_BF16", 2e-2, True), ("PREC_FP8", 5e-2, True),
-                                               ("PREC_BF16", 2e-2, False)])
+@pytest.mark.parametrize("prec_name,tol,sym", [("PREC_BF16", 2e-2, True), ("PREC_FP8", 2e-2, True),
+                                               ("PREC_BF16", 2e-2, False),
+                                               ("PREC_FP8", 2e-2, False)])
 def test_tc_run_beyond_128_tracks_oracle(otm, prec_name, tol, sym):
     """k > 128 over twelve steps with a partial last minibatch: the cluster's
     shared V image alternates between two global buffers, read back for the
