@@ -38,7 +38,8 @@ from .moments import as_sparse, coefficients
 
 __all__ = [
     "kappa", "whitened_tensor", "contract", "loss_explicit", "grad_explicit",
-    "grad_implicit", "grad_implicit_topic_exact", "sgd_step", "sgd_run", "steps_per_epoch",
+    "grad_implicit", "grad_implicit_gemm", "grad_implicit_topic_exact", "sgd_step", "sgd_run",
+    "steps_per_epoch",
 ]
 
 
@@ -118,6 +119,30 @@ def grad_implicit(V, YA, YB, YC, ybar3, theta: float, alpha0: float) -> np.ndarr
     return G
 
 
+def grad_implicit_gemm(V, YA, YB, YC, ybar3, theta: float, alpha0: float) -> np.ndarray:
+    """Lemma 3 (Eq. (16)) for all components at once: the same sums as
+    grad_implicit, grouped into products of the minibatch matrices (b x k):
+      A_A = Y_A V, A_B = Y_B V, a_A = V^T ybar_A, a_B = V^T ybar_B,
+      B = c1 A_A o A_B - c2 (A_A diag(a_B) + A_B diag(a_A)),
+      data = Y_C^T B / b + ybar_C (c3 a_A o a_B - c2 mean_t (A_A o A_B))^T,
+      G = kappa V ((V^T V) o (V^T V)) - data.
+    Column i of every matrix is component i."""
+    V = np.asarray(V, dtype=np.float64)
+    YA, YB, YC = (np.asarray(Y, dtype=np.float64) for Y in (YA, YB, YC))
+    ybA, ybB, ybC = (np.asarray(y, dtype=np.float64) for y in ybar3)
+    c1, c2, c3 = coefficients(alpha0)
+    b = YA.shape[0]
+    AA = YA @ V
+    AB = AA if YB is YA else YB @ V
+    aA = V.T @ ybA
+    aB = V.T @ ybB
+    P = AA * AB
+    B = c1 * P - c2 * (AA * aB[None, :] + AB * aA[None, :])
+    data = YC.T @ B / b + np.outer(ybC, c3 * aA * aB - c2 * P.mean(axis=0))
+    H = V.T @ V
+    return kappa(theta) * V @ (H * H) - data
+
+
 def grad_implicit_topic_exact(V, Xb, W, M1, theta: float, alpha0: float) -> np.ndarray:
     """Implicit gradient (Lemma 3 form, G = kappa V((V^T V)o2) - T(V, V, I)) for
     the topic model with the exact third moment of Eq. (3) whitened by W
@@ -172,10 +197,12 @@ def grad_implicit_topic_exact(V, Xb, W, M1, theta: float, alpha0: float) -> np.n
     return G
 
 
-def sgd_step(V, YA, YB, YC, ybar3, theta: float, beta: float, alpha0: float) -> np.ndarray:
-    """One update of Lemma 3 over a minibatch: V <- V - beta G."""
-    return np.asarray(V, dtype=np.float64) - beta * grad_implicit(V, YA, YB, YC, ybar3,
-                                                                   theta, alpha0)
+def sgd_step(V, YA, YB, YC, ybar3, theta: float, beta: float, alpha0: float,
+             gemm: bool = False) -> np.ndarray:
+    """One update of Lemma 3 over a minibatch: V <- V - beta G (G per component,
+    or in the matrix form of grad_implicit_gemm when gemm is set)."""
+    grad = grad_implicit_gemm if gemm else grad_implicit
+    return np.asarray(V, dtype=np.float64) - beta * grad(V, YA, YB, YC, ybar3, theta, alpha0)
 
 
 def steps_per_epoch(n: int, b: int) -> int:
@@ -183,12 +210,14 @@ def steps_per_epoch(n: int, b: int) -> int:
 
 
 def sgd_run(V0, YA, YB, YC, ybar3, perm: np.ndarray, b: int, beta0: float,
-            theta: float, alpha0: float, snapshot_every: int = 0, max_steps: int = -1):
+            theta: float, alpha0: float, snapshot_every: int = 0, max_steps: int = -1,
+            gemm: bool = False):
     """The STGD loop (Section 3.2): for each epoch e the samples are visited in the
     order perm[e], in minibatches of b; beta_t = beta0/sqrt(t).
 
     Returns the final V and, if snapshot_every > 0, the list of V after every
     snapshot_every-th step.  max_steps >= 0 stops early (bounded CPU samples).
+    gemm selects the matrix form of the gradient (grad_implicit_gemm).
     """
     V = np.asarray(V0, dtype=np.float64).copy()
     YA, YB, YC = (np.asarray(Y, dtype=np.float64) for Y in (YA, YB, YC))
@@ -202,7 +231,7 @@ def sgd_run(V0, YA, YB, YC, ybar3, perm: np.ndarray, b: int, beta0: float,
             idx = order[s:s + b]
             t += 1
             V = sgd_step(V, YA[idx], YB[idx], YC[idx], ybar3, theta,
-                         beta0 / np.sqrt(t), alpha0)
+                         beta0 / np.sqrt(t), alpha0, gemm=gemm)
             if snapshot_every and t % snapshot_every == 0:
                 snaps.append(V.copy())
     return V, snaps

@@ -57,6 +57,29 @@ def test_three_view_data_term_contracts_modes_one_and_two():
     np.testing.assert_allclose(gram - G0, stgd.contract(T, V), rtol=1e-11, atol=1e-11)
 
 
+@pytest.mark.parametrize("views,alpha0,theta", [(1, 1.0, 1.0), (3, 0.8, 1.0), (3, 0.0, 2.0),
+                                               (1, 2.5, 0.5)])
+def test_matrix_form_gradient_equals_explicit_tensor_contraction(views, alpha0, theta):
+    """The matrix form of Lemma 3 (all components at once, products of the
+    minibatch matrices) equals kappa V (V^T V)^o2 - T(V, V, I) with T formed
+    explicitly by einsum; its SGD run equals the per-component one."""
+    g = np.random.default_rng(21 + views)
+    Ys = [g.standard_normal((30, 5)) + s for s in (0.2, -0.1, 0.4)]
+    if views == 1:
+        Ys = [Ys[0]] * 3
+    yb = tuple(Y.mean(axis=0) for Y in Ys)
+    V = g.standard_normal((5, 5))
+    T = stgd.whitened_tensor(*Ys, yb, alpha0)
+    G = stgd.grad_implicit_gemm(V, *Ys, yb, theta, alpha0)
+    ref = stgd.kappa(theta) * V @ (V.T @ V) ** 2 - stgd.contract(T, V)
+    np.testing.assert_allclose(G, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    perm = synth.epoch_permutations(3, 30, 2)
+    V1, s1 = stgd.sgd_run(V, *Ys, yb, perm, 8, 0.01, theta, alpha0, snapshot_every=3)
+    V2, s2 = stgd.sgd_run(V, *Ys, yb, perm, 8, 0.01, theta, alpha0, snapshot_every=3, gemm=True)
+    np.testing.assert_allclose(V2, V1, rtol=1e-12, atol=1e-12)
+    assert len(s1) == len(s2) == 2
+
+
 def _orthogonal_atoms(seed, k):
     """Samples whose empirical third moment is exactly sum_i lam_i u_i^(x)3."""
     g = np.random.default_rng(seed)
