@@ -1,23 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the online tensor method's hot path on one GB300 (or N replicas).
 
-Workload (one "step" = one pass of the whole hot path over one synthetic
-input): mixed-membership stochastic blockmodel, four parts X, A, B, C of
-5,000 nodes, k = 100 communities, pi ~ Dir(0.01 * 1_100) (alpha0 = 1),
-p = 0.1 within / q = 0.005 across (Bernoulli), three CSR blocks X->A, B, C.
-  whiten (randomised, oversampling 20, 2 power iterations, FP64 eig)
-  -> project the three views -> means -> STGD, minibatch 1,024,
-  beta_t = 1e-2/sqrt(t), theta = 1, 20 epochs (100 steps, one persistent
-  launch) -> unwhiten -> membership of the X nodes (Lemma 4, community case).
-After the timed region the membership is validated against the generator's
-ground truth by p-value testing (recovery ratio, average error).
+Default workload (one "step" = one pass of the whole hot path over one
+synthetic input): latent Dirichlet allocation, 300,000 documents of
+Poisson(300) words over a vocabulary of 100,000 (topic-word distributions
+Dir(0.05) with Zipf-skewed concentrations), k = 100 topics, alpha0 = 1 -- a
+synthetic stand-in for the paper's NYTimes corpus.
+  whiten (randomised range finder, oversampling 20, 2 power iterations, FP64
+  eigendecomposition) -> project (y_t = W^T c_t / l_t) -> means -> STGD,
+  minibatch 1,024, beta_t = 1e-2/sqrt(t), theta = 1, 20 epochs (5,860 steps in
+  one persistent launch) -> unwhiten (topics normalised to the simplex).
 Metric: whitened samples processed by the SGD per second of whole-path time
-(100,000 samples per step).  Inputs are resident in HBM before timing; the
-L2 is flushed (256 MiB write) between timed steps.  ``e2e`` repeats the
-measurement with the inputs in pinned host memory and the copies inside the
-timed region.
+(6,000,000 samples per step).  Inputs are resident in HBM before timing
+(larger than L2); the L2 is flushed (256 MiB write) between timed steps.
+``e2e`` repeats the measurement with the inputs in pinned host memory and the
+copies (CSR, projection, permutations, start) and the read-back of the topics
+inside the timed region.  After the timed region: the BF16 and FP8 forms of
+the STGD on the same samples with their errors against the FP64 oracle, the
+time to 1e-3 reconstruction error of plain FP32 STGD and of the warm-started
+forms, and the FP64 oracle timed on the host cores (matrix-form STGD run to
+completion).
 
-``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+Other workloads: --workload mmsb (the community-model pipeline, 4 x 5,000
+nodes, k = 100), batched, warmstart, whitening.
+``--impl reference`` times the FP64 CPU oracle on the default workload.
 Multi-GPU: replicas only (one independent decomposition per rank, no
 collective on the data path); value = samples of all ranks / max rank time.
 """
@@ -45,10 +51,11 @@ CFG = dict(workload="mmsb_4x5000_k100_b1024_fp32", n_per=5000, k=100, alpha_i=0.
            q=0.005, oversample=20, power_iters=2, b=1024, epochs=20, beta0=1e-2, theta=1.0,
            alpha0=1.0, seed=0)
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
-# DRAM bytes (read + write) per launch of the STGD kernel on this workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of this command; to be reset to None
-# whenever the kernel changes
-SGD_KERNEL_TRAFFIC = 7125760
+# the persistent STGD kernel the library runs for each choice of otm_sgd_set_form
+SGD_KERNEL_NAME = {"auto": "sgd_split_kernel (one persistent launch = all STGD steps)",
+                   "split": "sgd_split_kernel (one persistent launch = all STGD steps)",
+                   "grid": "sgd_grid_kernel (one cooperative launch = all STGD steps)",
+                   "cluster": "sgd_cluster_kernel (one cluster launch = all STGD steps)"}
 PVALUE_THRESHOLD = 0.01   # significance level of the paired p-value test
 
 
@@ -220,7 +227,12 @@ def convergence(otm, torch, path, cfg, fp32_step_ms):
             "fp32": report(snap32, fp32_step_ms), "bf16": report(snap16, bf16_step_ms)}
 
 
-def run_gpu(args, rank, world, local_rank):
+def sgd_form_code(otm, name):
+    return {"auto": otm.SGD_FORM_AUTO, "cluster": otm.SGD_FORM_CLUSTER,
+            "grid": otm.SGD_FORM_GRID, "split": otm.SGD_FORM_SPLIT}[name]
+
+
+def run_mmsb(args, rank, world, local_rank):
     import torch
     from paper_1309_0787_gb300 import otm
     dev = torch.device("cuda", local_rank)
@@ -228,8 +240,7 @@ def run_gpu(args, rank, world, local_rank):
     cfg = dict(CFG)
     host = make_inputs(cfg, rank)
     path = GpuPath(otm, torch, cfg, host, dev)
-    otm.sgd_set_form({"auto": otm.SGD_FORM_AUTO, "cluster": otm.SGD_FORM_CLUSTER,
-                      "grid": otm.SGD_FORM_GRID}[args.sgd_form])
+    otm.sgd_set_form(sgd_form_code(otm, args.sgd_form))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     samples = cfg["n_per"] * cfg["epochs"]
     flops, nsteps = sgd_flops(cfg)
@@ -321,12 +332,10 @@ def run_gpu(args, rank, world, local_rank):
                          "unwhiten": statistics.mean(step_ms) - statistics.mean(pre_ms)
                          - statistics.mean(sgd_ms),
                          "wall_per_step": 1e3 * wall / args.steps},
-        "roofline": {"kernel": ("sgd_cluster_kernel (one 16-CTA cluster launch = all 100 STGD "
-                                "steps)" if args.sgd_form == "cluster" else
-                                "sgd_grid_kernel (one cooperative launch = all 100 STGD steps)"),
+        "roofline": {"kernel": SGD_KERNEL_NAME[args.sgd_form],
                      "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
-                     "traffic": None if args.sgd_form == "cluster" else SGD_KERNEL_TRAFFIC,
+                     "traffic": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "algorithmic_flops_per_launch": flops},
         "e2e": {"value": world * samples * n_e2e / e2e_t, "unit": UNIT,
@@ -806,36 +815,10 @@ def run_whitening(args):
                      "deviation measures how much of M2 its column selection misses")}
 
 
-LDA3 = dict(workload="lda_300000x100000_k100_precision", n_docs=300000, d=100000, k=100,
-            alpha_i=0.01, word_conc=0.05, doc_len=300, oversample=20, power_iters=2, b=1024,
-            epochs=20, beta0=1e-2, theta=1.0, seed=0, proj_docs=256)
-
-
 def _rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def lda_oracle_checks(X, W, Y_docs, docs, V0, Yb, yb, c, V1):
-    """FP64 oracle checks of single stages on a sample, each fed the previous
-    stage's GPU output: the projection y_t = W^T c_t / l_t of `docs` (Section
-    3.1), and the update of one STGD step (Lemma 3) on the minibatch Yb from V0
-    (components as columns) for each precision's V1 (same orientation).
-    Returns relative errors (of the rows, and of the update V1 - V0)."""
-    from oracle import moments as om
-    from oracle import stgd as ostgd
-    Xs = om.as_sparse(X)[docs]
-    lens = np.asarray(Xs.sum(axis=1)).ravel()
-    y_ref = (Xs @ np.asarray(W, dtype=np.float64)) / lens[:, None]
-    Yb = np.asarray(Yb, dtype=np.float64)
-    yb = np.asarray(yb, dtype=np.float64)
-    V0 = np.asarray(V0, dtype=np.float64)
-    dV = ostgd.sgd_step(V0, Yb, Yb, Yb, (yb, yb, yb), c["theta"], c["beta0"],
-                        c["k"] * c["alpha_i"]) - V0
-    return {"projection_rel_err": _rel(Y_docs, y_ref),
-            "step_update_rel_err": {p: _rel(np.asarray(v, dtype=np.float64) - V0, dV)
-                                    for p, v in V1.items()}}
 
 
 def sym_sgd_flops(n, b, k, epochs):
@@ -845,132 +828,561 @@ def sym_sgd_flops(n, b, k, epochs):
     return sum(4 * k * k * bs + 4 * k ** 3 for bs in sizes)
 
 
-def run_lda(args):
-    """Precision form on a large LDA corpus: 300,000 documents of Poisson(300)
-    words over 100,000 words with Zipf-skewed Dir(0.05) topics, k = 100,
-    alpha0 = 1 (a synthetic stand-in for the paper's NYTimes corpus).  Per timed
-    iteration: whitening (range finder) + projection + means, then 20 epochs of
-    STGD (b = 1,024) from the same start in FP32, BF16 and FP8 (each with its
-    sample quantisation timed apart).  Medians over `steps` iterations, L2
-    flushed before each.  Errors: each low-precision result against the FP32
-    one (relative reconstruction error of the components, relative error of the
-    unwhitened topics), and FP64 oracle checks of single stages on a sample."""
-    import torch
-    from paper_1309_0787_gb300 import otm
-    c = dict(LDA3)
-    dev = torch.device("cuda", 0)
-    k, b, ep = c["k"], c["b"], c["epochs"]
-    alpha0 = k * c["alpha_i"]
-    t0 = time.perf_counter()
-    corpus = synth.lda_corpus(c["seed"], c["n_docs"], c["d"], k, c["alpha_i"], c["word_conc"],
+# ----------------------------------------------------------------------------
+# The default line: the whole hot path on a large synthetic LDA corpus
+# ----------------------------------------------------------------------------
+LDA = dict(workload="lda_300000x100000_k100_b1024_fp32", n_docs=300000, d=100000, k=100,
+           alpha_i=0.01, word_conc=0.05, doc_len=300, oversample=20, power_iters=2, b=1024,
+           epochs=20, beta0=1e-2, theta=1.0, seed=0, check_docs=256)
+
+
+def lda_corpus_cached(c, seed):
+    """The synthetic corpus (about 17 s to draw on one core), cached as an .npz in
+    the system temp directory so that a second process on the same machine (the
+    reference arm) loads it instead.  The cache holds only what synth drew."""
+    import tempfile
+    key = (f"otm_lda_{c['n_docs']}x{c['d']}_k{c['k']}_a{c['alpha_i']}_w{c['word_conc']}"
+           f"_l{c['doc_len']}_s{seed}.npz")
+    path = os.path.join(tempfile.gettempdir(), "otm_bench_cache", key)
+    if os.path.exists(path):
+        try:
+            z = np.load(path)
+            X = synth.CSR(z["row_ptr"], z["col"], z["val"], tuple(int(v) for v in z["shape"]))
+            return {"X": X, "mu": z["mu"], "cached": True}
+        except Exception:
+            pass
+    corpus = synth.lda_corpus(seed, c["n_docs"], c["d"], c["k"], c["alpha_i"], c["word_conc"],
                               c["doc_len"], poisson_len=True, zipf=True)
-    gen_s = time.perf_counter() - t0
     X = corpus["X"]
-    n, d = X.shape
-    S = torch.from_numpy(synth.gaussian(c["seed"] + 1, d, k + c["oversample"])).to(dev)
-    perm_h = synth.epoch_permutations(c["seed"] + 3, n, ep)
-    perm = torch.from_numpy(perm_h).to(dev)
-    V0h = synth.haar_orthonormal(c["seed"] + 4, k)            # columns = components
-    V0t = torch.from_numpy(V0h.T.copy()).to(dev)              # V[i] = component i
-    Xd = otm.DeviceCSR.from_host(X, dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, row_ptr=X.row_ptr, col=X.col, val=X.val, shape=np.array(X.shape),
+                 mu=corpus["mu"])
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return {"X": X, "mu": corpus["mu"], "cached": False}
+
+
+def lda_inputs(c, rank=0):
+    """Seeded inputs of one decomposition (rank r draws seed + 1000 r): the corpus,
+    the range finder's Gaussian projection S (d x (k + oversample)), the epoch
+    permutations and a Haar-random start V0 (columns = components)."""
+    s = c["seed"] + 1000 * rank
+    t0 = time.perf_counter()
+    corpus = lda_corpus_cached(c, s)
+    gen_s = time.perf_counter() - t0
+    d, k = c["d"], c["k"]
+    n = corpus["X"].shape[0]
+    return {"X": corpus["X"], "mu": corpus["mu"], "gen_s": gen_s, "cached": corpus["cached"],
+            "S": synth.gaussian(s + 1, d, k + c["oversample"]),
+            "perm": synth.epoch_permutations(s + 3, n, c["epochs"]),
+            "V0": synth.haar_orthonormal(s + 4, k)}
+
+
+class LdaPath:
+    """The hot path on the GPU: topic-model whitening (range finder) ->
+    projection -> means -> FP32 STGD (one persistent launch) -> unwhitening."""
+
+    def __init__(self, otm, torch, c, host, device):
+        self.otm, self.torch, self.c, self.dev, self.host = otm, torch, c, device, host
+        self.upload()
+
+    def upload(self, pinned=None):
+        t, otm = self.torch, self.otm
+        if pinned is None:
+            self.Xd = otm.DeviceCSR.from_host(self.host["X"], self.dev)
+            self.S = t.from_numpy(self.host["S"]).to(self.dev)
+            self.perm = t.from_numpy(self.host["perm"]).to(self.dev)
+            self.V0t = t.from_numpy(self.host["V0"].T.copy()).to(self.dev)
+        else:
+            self.Xd = otm.DeviceCSR(*(a.to(self.dev, non_blocking=True) for a in pinned["X"]),
+                                    self.host["X"].shape)
+            self.S = pinned["S"].to(self.dev, non_blocking=True)
+            self.perm = pinned["perm"].to(self.dev, non_blocking=True)
+            self.V0t = pinned["V0t"].to(self.dev, non_blocking=True)
+
+    def front(self):
+        c, otm = self.c, self.otm
+        wh = otm.whiten_topic(self.Xd, self.S, c["k"], c["power_iters"], c["k"] * c["alpha_i"])
+        Y = otm.project(self.Xd, wh["W"], wh["row_invlen"])
+        yb3 = self.torch.stack([otm.column_mean(Y)] * 3)
+        return wh, Y, yb3
+
+    def step(self, ev=None):
+        c, otm = self.c, self.otm
+        if ev:
+            ev["w0"].record()
+        wh, Y, yb3 = self.front()
+        V = self.V0t.clone()
+        if ev:
+            ev["s0"].record()
+        otm.sgd_run(V, Y, Y, Y, yb3, self.perm, c["epochs"], c["b"], c["beta0"], c["theta"],
+                    c["k"] * c["alpha_i"])
+        if ev:
+            ev["s1"].record()
+        out = otm.unwhiten(V, wh["Q"], wh["Cp"], c["theta"], True)
+        self.last = (wh, Y, yb3, V)
+        return out
+
+
+def lda_oracle_checks(c, X, W, Y_docs, docs, Yb, yb, V0, V1):
+    """FP64 oracle checks of single stages on a sample, each fed the previous
+    stage's GPU output: the projection y_t = W^T c_t / l_t of the documents
+    `docs` (Section 3.1), and one STGD step (Lemma 3) on the minibatch Yb from V0
+    (columns = components) for each precision's result V1 (same orientation).
+    Step errors: G = (V0 - V1) / beta0 against the oracle's G64, as
+    ||G - G64|| / (||kappa G_gram|| + ||G_data||) over the whole matrix and for
+    the worst component, and the update relative to its own norm."""
+    from oracle import moments as om
+    from oracle import stgd as ostgd
+    Xs = om.as_sparse(X)[docs]
+    lens = np.asarray(Xs.sum(axis=1)).ravel()
+    y_ref = (Xs @ np.asarray(W, dtype=np.float64)) / lens[:, None]
+    Yb = np.asarray(Yb, dtype=np.float64)
+    yb = np.asarray(yb, dtype=np.float64)
+    V0 = np.asarray(V0, dtype=np.float64)
+    a0 = c["k"] * c["alpha_i"]
+    G = ostgd.grad_implicit(V0, Yb, Yb, Yb, (yb, yb, yb), c["theta"], a0)
+    gram = ostgd.kappa(c["theta"]) * V0 @ (V0.T @ V0) ** 2
+    den = np.linalg.norm(gram) + np.linalg.norm(gram - G)
+    den_col = np.linalg.norm(gram, axis=0) + np.linalg.norm(gram - G, axis=0)
+    step = {}
+    for p, v in V1.items():
+        Gk = (V0 - np.asarray(v, dtype=np.float64)) / c["beta0"]
+        step[p] = {"grad_rel_err": float(np.linalg.norm(Gk - G) / den),
+                   "grad_rel_err_worst_component":
+                       float((np.linalg.norm(Gk - G, axis=0) / den_col).max()),
+                   "update_rel_err": _rel(Gk, G)}
+    return {"projection_rows_rel_err": _rel(Y_docs, y_ref), "step": step}
+
+
+def lda_precisions(otm, torch, path, c, host, fp32_sgd_ms):
+    """The precision form on the same whitened samples: sample quantisation, then
+    the 20 epochs of STGD from the same start in BF16 and in FP8 (tensor cores,
+    FP32 accumulation; medians of three runs).  Errors: one step of each
+    precision against the FP64 oracle (lda_oracle_checks), and the 20-epoch
+    results against the FP32 one (relative reconstruction error of the
+    components, relative error of the unwhitened topics)."""
+    from oracle import post as opost
+    wh, Y, yb3, V32 = path.last
+    k, b, ep, th = c["k"], c["b"], c["epochs"], c["theta"]
+    a0 = k * c["alpha_i"]
+    n = Y.shape[0]
+    dev = Y.device
+    res = {"fp32": {"sgd_ms": fp32_sgd_ms, "samples_per_s": n * ep / (fp32_sgd_ms / 1e3)}}
+    V = {"fp32": V32}
     precs = {"bf16": otm.PREC_BF16, "fp8": otm.PREC_FP8}
+    for nm, pr in precs.items():
+        tq, ts = [], []
+        for _ in range(3):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            q = otm.quantize_samples(Y, pr)
+            e[1].record()
+            Vp = path.V0t.clone()
+            otm.sgd_run_lp(Vp, q, q, q, yb3, path.perm, ep, b, c["beta0"], th, a0, pr)
+            e[2].record()
+            torch.cuda.synchronize()
+            tq.append(e[0].elapsed_time(e[1]))
+            ts.append(e[1].elapsed_time(e[2]))
+        V[nm] = Vp
+        res[nm] = {"quantize_ms": statistics.median(tq), "sgd_ms": statistics.median(ts),
+                   "samples_per_s": n * ep / (statistics.median(ts) / 1e3)}
+    nr = V32.double().norm(dim=1)
+    kappa = 0.5 * (1.0 + th)
+    lam = (kappa * nr ** 3).contiguous()
+    U = (V32.double() / nr[:, None]).contiguous()
+    topics = {nm: otm.unwhiten(v, wh["Q"], wh["Cp"], th, True)["comps"] for nm, v in V.items()}
+    for nm in precs:
+        res[nm]["after_run_vs_fp32"] = {
+            "recon_rel_err": float(otm.recon_error(V[nm], U, lam, th)[0]),
+            "topics_rel_err": float((topics[nm] - topics["fp32"]).norm() / topics["fp32"].norm())}
+    # one step of each precision from the Haar start on the first minibatch
+    docs = host["perm"][0][:b].astype(np.int64)
+    idx = torch.from_numpy(docs).to(dev)
+    Yb = Y[idx].contiguous()
+    V1 = {"fp32": path.V0t.clone()}
+    otm.sgd_step(V1["fp32"], Yb, Yb, Yb, yb3, th, c["beta0"], a0)
+    for nm, pr in precs.items():
+        qb = otm.quantize_samples(Yb, pr)
+        V1[nm] = path.V0t.clone()
+        otm.sgd_run_lp(V1[nm], qb, qb, qb, yb3, None, 1, b, c["beta0"], th, a0, pr)
+    torch.cuda.synchronize()
+    cd = docs[: c["check_docs"]]
+    checks = lda_oracle_checks(c, host["X"], wh["W"].cpu().numpy(), Y[idx[: c["check_docs"]]]
+                               .cpu().numpy(), cd, Yb.cpu().numpy(), yb3[0].cpu().numpy(),
+                               host["V0"], {nm: v.cpu().numpy().T for nm, v in V1.items()})
+    for nm in res:
+        res[nm]["one_step_vs_fp64_oracle"] = checks["step"][nm]
+    Qh = wh["Q"].cpu().numpy().astype(np.float64)
+    mu_ref = opost.unwhiten(V32.cpu().numpy().T.astype(np.float64),
+                            Qh @ wh["Cp"].cpu().numpy(), th, True)["mu"]
+    res["stage_checks_vs_fp64_oracle"] = {
+        "projection_rows_rel_err": checks["projection_rows_rel_err"],
+        "unwhiten_rel_err": _rel(topics["fp32"].cpu().numpy(), mu_ref),
+        "sample": f"projection of {len(cd)} documents; one STGD step on the first minibatch "
+                  f"({b} documents) from the Haar start; unwhitening of the FP32 result"}
+    return res
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def lda_oracle_sample(c, host, fracs, stgd_steps, project_frac=1.0):
+    """Times the oracle (FP64 NumPy/SciPy) on the host cores, on the line's inputs:
+      whitening (range finder, Section 4.2) of the first f n documents for each f
+      in `fracs`; its full-corpus time by a linear fit in f (a dense part that
+      does not depend on the documents plus a part proportional to them);
+      projection and means (Section 3.1) of the first project_frac n documents,
+      scaled to all of them;
+      `stgd_steps` steps of the matrix-form implicit STGD (Lemma 3) with the
+      line's schedule (None: the whole schedule, run to completion);
+      unwhitening (Lemma 4).
+    Returns the seconds of each part, for the whole workload."""
+    from oracle import moments as om
+    from oracle import post as opost
+    from oracle import stgd as ostgd
+    from oracle import whiten as ow
+    X = host["X"]
+    n = X.shape[0]
+    k, a0 = c["k"], c["k"] * c["alpha_i"]
+    S = host["S"].astype(np.float64)
+    t_wh, wh = [], None
+    for f in fracs:
+        Xf = X.row_slice(0, max(1, int(round(f * n))))
+        t0 = time.perf_counter()
+        wh = ow.range_finder_whiten(lambda Z, Xf=Xf: om.topic_second_moment_apply(Xf, Z, a0), S,
+                                    k, c["power_iters"])
+        t_wh.append(time.perf_counter() - t0)
+    if len(fracs) > 1:
+        slope = (t_wh[-1] - t_wh[0]) / (fracs[-1] - fracs[0])
+        whiten_s = max(t_wh[-1] + slope * (1.0 - fracs[-1]), t_wh[-1])
+    else:
+        whiten_s = t_wh[0] / fracs[0]
+    npj = max(1, int(round(project_frac * n)))
+    t0 = time.perf_counter()
+    Xs = om.as_sparse(X.row_slice(0, npj))
+    Y = (Xs @ wh["W"]) / om.doc_lengths(Xs)[:, None]
+    yb = Y.mean(axis=0)
+    project_s = (time.perf_counter() - t0) * n / npj
+    if npj < n:   # the STGD reads every document: tile the projected rows
+        Y = np.resize(Y, (n, k))
+    total = ostgd.steps_per_epoch(n, c["b"]) * c["epochs"]
+    steps = total if stgd_steps is None else min(stgd_steps, total)
+    t0 = time.perf_counter()
+    V, _ = ostgd.sgd_run(host["V0"].astype(np.float64), Y, Y, Y, (yb, yb, yb), host["perm"],
+                         c["b"], c["beta0"], c["theta"], a0, max_steps=steps, gemm=True)
+    stgd_s = (time.perf_counter() - t0) * total / steps
+    t0 = time.perf_counter()
+    opost.unwhiten(V, wh["Wplus"], c["theta"], True)
+    post_s = time.perf_counter() - t0
+    return {"whiten_s": whiten_s, "whiten_sample_s": t_wh, "project_means_s": project_s,
+            "stgd_s": stgd_s, "stgd_steps_run": steps, "stgd_steps_total": total,
+            "unwhiten_s": post_s}
+
+
+def lda_cpu_baseline(c, host):
+    """The CPU baseline of the default line: lda_oracle_sample with the STGD run
+    to completion (all 5,860 steps) and the whitening extrapolated from 5 % and
+    10 % of the documents."""
+    r = lda_oracle_sample(c, host, (0.05, 0.10), None)
+    n = host["X"].shape[0]
+    tot = r["whiten_s"] + r["project_means_s"] + r["stgd_s"] + r["unwhiten_s"]
+    return {"value": n * c["epochs"] / tot, "unit": UNIT, "cores": blas_threads(),
+            "kind": "oracle", "cpu": cpu_model(),
+            "sample": (f"FP64 oracle on the host cores: the matrix-form implicit STGD run to "
+                       f"completion ({r['stgd_steps_total']} steps, {r['stgd_s']:.1f} s); the "
+                       f"range-finder whitening timed on 5 % and 10 % of the documents "
+                       f"({r['whiten_sample_s'][0]:.1f} s, {r['whiten_sample_s'][1]:.1f} s) and "
+                       f"extrapolated linearly to all ({r['whiten_s']:.1f} s); projection and "
+                       f"means of all documents ({r['project_means_s']:.1f} s); unwhitening "
+                       f"({r['unwhiten_s']:.2f} s); value = samples / total "
+                       f"({tot:.1f} s)"),
+            "seconds": r}
+
+
+def run_lda_reference(args, rank, world):
+    """The reference arm of the default line: the oracle on the host cores (rank 0
+    only), every step a bounded sample of the workload: the whitening on 1 % and
+    2 % of the documents (extrapolated), the projection of 2 % (scaled), 100 of
+    the 5,860 STGD steps (scaled), the unwhitening."""
+    if rank != 0:
+        return None
+    c = dict(LDA)
+    host = lda_inputs(c, 0)
+    n = host["X"].shape[0]
 
     def one():
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
-        ev[0].record()
-        wh = otm.whiten_topic(Xd, S, k, c["power_iters"], alpha0)
-        Y = otm.project(Xd, wh["W"], wh["row_invlen"])
-        yb3 = torch.stack([otm.column_mean(Y)] * 3)
-        ev[1].record()
-        V = {"fp32": V0t.clone()}
-        otm.sgd_run(V["fp32"], Y, Y, Y, yb3, perm, ep, b, c["beta0"], c["theta"], alpha0)
-        ev[2].record()
-        for j, (nm, pr) in enumerate(precs.items()):
-            q = otm.quantize_samples(Y, pr)
-            ev[3 + 2 * j].record()
-            V[nm] = V0t.clone()
-            otm.sgd_run_lp(V[nm], q, q, q, yb3, perm, ep, b, c["beta0"], c["theta"], alpha0, pr)
-            ev[4 + 2 * j].record()
-        torch.cuda.synchronize()
-        t = {"whiten_project_mean": ev[0].elapsed_time(ev[1]),
-             "sgd_fp32": ev[1].elapsed_time(ev[2]),
-             "quantize_bf16": ev[2].elapsed_time(ev[3]), "sgd_bf16": ev[3].elapsed_time(ev[4]),
-             "quantize_fp8": ev[4].elapsed_time(ev[5]), "sgd_fp8": ev[5].elapsed_time(ev[6])}
-        return t, wh, Y, yb3, V
+        r = lda_oracle_sample(c, host, (0.01, 0.02), 100, project_frac=0.02)
+        return r, r["whiten_s"] + r["project_means_s"] + r["stgd_s"] + r["unwhiten_s"]
 
     for _ in range(args.warmup):
         one()
-    sampler = ClockSampler(0)
-    sampler.start()
-    runs = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        t, wh, Y, yb3, V = one()
-        runs.append(t)
-    clocks = sampler.stop()
-    med = {key: statistics.median(r[key] for r in runs) for key in runs[0]}
-    samples = n * ep
+    vals, r = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, tot = one()
+        vals.append(n * c["epochs"] / tot)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    sample = (f"FP64 oracle on the host cores, per step: whitening on 1 % and 2 % of the "
+              f"documents extrapolated to all ({r['whiten_s']:.1f} s), projection and means of "
+              f"2 % scaled ({r['project_means_s']:.1f} s), {r['stgd_steps_run']} of the "
+              f"{r['stgd_steps_total']} matrix-form STGD steps scaled ({r['stgd_s']:.1f} s), "
+              f"unwhitening ({r['unwhiten_s']:.2f} s)")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": c["workload"], "docs": n, "vocabulary": c["d"],
+                       "k": c["k"], "minibatch": c["b"], "epochs": c["epochs"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(),
+                             "kind": "oracle", "cpu": cpu_model(), "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
 
-    # errors of the low-precision results against the FP32 one
-    nr = V["fp32"].double().norm(dim=1)
-    kappa = 0.5 * (1.0 + c["theta"])
-    lam = (kappa * nr ** 3).contiguous()
-    U = (V["fp32"].double() / nr[:, None]).contiguous()
-    topics = {nm: otm.unwhiten(V[nm], wh["Q"], wh["Cp"], c["theta"], True)["comps"]
-              for nm in V}
-    vs32 = {nm: {"recon_rel_err": float(otm.recon_error(V[nm], U, lam, c["theta"])[0]),
-                 "topics_rel_err": float((topics[nm] - topics["fp32"]).norm()
-                                         / topics["fp32"].norm())}
-            for nm in precs}
-    # FP64 oracle checks of single stages on a sample
-    docs = perm_h[0][: c["proj_docs"]]
-    idx = torch.from_numpy(perm_h[0][:b].astype(np.int64)).to(dev)
-    Yb = Y[idx].contiguous()
-    V1 = {"fp32": V0t.clone()}
-    otm.sgd_step(V1["fp32"], Yb, Yb, Yb, yb3, c["theta"], c["beta0"], alpha0)
-    for nm, pr in precs.items():
-        qb = otm.quantize_samples(Yb, pr)
-        V1[nm] = V0t.clone()
-        otm.sgd_run_lp(V1[nm], qb, qb, qb, yb3, None, 1, b, c["beta0"], c["theta"], alpha0, pr)
+
+T2T = dict(k=64, n=300000, b=1024, sigma=1e-2, conc=20.0, beta0=1e-3, epochs=60, J=4,
+           polish_steps=300, polish_beta=2e-3, seed=0)
+
+
+def time_to_target(otm, torch, dev):
+    """Time to 1e-3 reconstruction error on a decomposition with a known answer,
+    at the default line's sample count and minibatch: whitened samples of an
+    orthogonal tensor (y = w_h^{-1/2} u_h + sigma eps, h ~ Cat(w), w ~ Dir(20 1_k),
+    alpha0 = 0, so Lemma 3 reduces to the plain third moment), k = 64,
+    n = 300,000, b = 1,024, sigma = 1e-2.  Its sample tensor is orthogonally
+    decomposable up to O(sigma^2): components u_h, eigenvalues
+    lambda_h = (n_h / n) w_h^{-3/2}.  The reference is that decomposition polished
+    by full-batch FP32 steps; its residual gradient is measured by the FP64
+    oracle on the CPU.  Arms (each timed on the GPU, error of the epoch
+    snapshots against the reference):
+      plain_fp32  -- the paper's method: Haar-random start, FP32 STGD;
+      warm_fp32   -- the warm start (sketch T(I, I, theta_1) of the samples, its
+                     eigenvectors as directions, scaled by T(u, u, u)^(1/3)), then FP32 STGD;
+      warm_bf16   -- the same start, BF16 tensor-core STGD.
+    Time to 1e-3 = warm-start time + (first epoch whose snapshot is within 1e-3)
+    x the run's time per epoch."""
+    from oracle import stgd as ostgd
+    c = dict(T2T)
+    k, n, b, ep = c["k"], c["n"], c["b"], c["epochs"]
+    spe = (n + b - 1) // b
+    o = synth.orthogonal_samples(c["seed"] + 17, k, n, c["sigma"], conc=c["conc"])
+    cnt = np.bincount(o["h"], minlength=k)
+    lam0 = (cnt / n) * o["w"] ** -1.5
+    Y = torch.from_numpy(o["Y"]).to(dev)
+    yb = Y.double().mean(0)
+    yb3 = torch.stack([yb] * 3).contiguous()
+    perm = torch.from_numpy(synth.epoch_permutations(c["seed"] + 18, n, ep)).to(dev)
+    # reference: the closed form, then full-batch FP32 steps (one call per step keeps
+    # the step size constant)
+    Vref = torch.from_numpy((o["U"] * lam0 ** (1.0 / 3.0)).T.astype(np.float32).copy()).to(dev)
+    Vcf = Vref.clone()
+    for _ in range(c["polish_steps"]):
+        otm.sgd_run(Vref, Y, Y, Y, yb3, None, 1, n, c["polish_beta"], 1.0, 0.0)
     torch.cuda.synchronize()
-    checks = lda_oracle_checks(X, wh["W"].cpu().numpy(), Y[torch.from_numpy(
-        docs.astype(np.int64)).to(dev)].cpu().numpy(), docs, V0h, Yb.cpu().numpy(),
-        yb3[0].cpu().numpy(), c, {nm: v.cpu().numpy().T for nm, v in V1.items()})
-    from oracle import post as opost
-    Qh = wh["Q"].cpu().numpy().astype(np.float64)
-    mu_ref = opost.unwhiten(V["fp32"].cpu().numpy().T.astype(np.float64),
-                            Qh @ wh["Cp"].cpu().numpy(), c["theta"], True)["mu"]
-    checks["unwhiten_fp32_rel_err"] = _rel(topics["fp32"].cpu().numpy(), mu_ref)
+    Y64 = o["Y"].astype(np.float64)
+    ybh = Y64.mean(axis=0)
 
+    def resid(Vt):
+        V = Vt.cpu().numpy().T.astype(np.float64)
+        G = ostgd.grad_implicit_gemm(V, Y64, Y64, Y64, (ybh, ybh, ybh), 1.0, 0.0)
+        return float(np.linalg.norm(G) / np.linalg.norm(V))
+    nr = Vref.double().norm(dim=1)
+    lam = (nr ** 3).contiguous()
+    U = (Vref.double() / nr[:, None]).contiguous()
+
+    def run(V0, prec):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        V = V0.clone()
+        q = otm.quantize_samples(Y, prec) if prec is not None else None
+        torch.cuda.synchronize()
+        e0.record()
+        if prec is None:
+            sn = otm.sgd_run(V, Y, Y, Y, yb3, perm, ep, b, c["beta0"], 1.0, 0.0,
+                             snapshot_every=spe)
+        else:
+            sn = otm.sgd_run_lp(V, q, q, q, yb3, perm, ep, b, c["beta0"], 1.0, 0.0, prec,
+                                snapshot_every=spe)
+        e1.record()
+        torch.cuda.synchronize()
+        return sn, e0.elapsed_time(e1) / ep
+
+    def report(sn, epoch_ms, start_ms):
+        errs = [float(otm.recon_error(sn[i].contiguous(), U, lam, 1.0)[0])
+                for i in range(sn.shape[0])]
+        hit = next((i + 1 for i, e in enumerate(errs) if e <= 1e-3), None)
+        return {"epochs_to_1e-3": hit,
+                "seconds_to_1e-3": None if hit is None else (start_ms + hit * epoch_ms) / 1e3,
+                "start_ms": start_ms, "epoch_ms": epoch_ms, "final_error": errs[-1],
+                "error_by_epoch": [float(f"{e:.4g}") for e in errs[::3]] + [float(f"{errs[-1]:.4g}")]}
+
+    V0h = torch.from_numpy(synth.haar_orthonormal(c["seed"] + 19, k).T.copy()).to(dev)
+    out = {}
+    sn, ms = run(V0h, None)
+    out["plain_fp32"] = report(sn, ms, 0.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    th = torch.from_numpy(synth.unit_vectors(c["seed"] + 20, c["J"], k)).to(dev)
+    a0 = torch.zeros(1, dtype=torch.float64, device=dev)
+    e0.record()
+    S, _ = otm.ws_sketch(Y[None], a0, th)
+    E, _, _ = otm.ws_canonicalize(S)
+    Vw = otm.ws_init_components(E, Y[None], a0, 1.0)[0].contiguous()
+    e1.record()
+    torch.cuda.synchronize()
+    warm_ms = e0.elapsed_time(e1)
+    sn, ms = run(Vw, None)
+    out["warm_fp32"] = report(sn, ms, warm_ms)
+    sn, ms = run(Vw, otm.PREC_BF16)
+    out["warm_bf16"] = report(sn, ms, warm_ms)
+    best = min((v["seconds_to_1e-3"] for v in out.values() if v["seconds_to_1e-3"] is not None),
+               default=None)
+    plain = out["plain_fp32"]["seconds_to_1e-3"]
+    return {"problem": (f"whitened orthogonal tensor, k = {k}, n = {n}, b = {b}, sigma = "
+                        f"{c['sigma']}, w ~ Dir({c['conc']:g} 1_k), alpha0 = 0, theta = 1, "
+                        f"beta_t = {c['beta0']:g}/sqrt(t), {ep} epochs, seed {c['seed']}"),
+            "reference": (f"closed-form decomposition (u_h, lambda_h = (n_h/n) w_h^-1.5) "
+                          f"polished by {c['polish_steps']} full-batch FP32 steps "
+                          f"(beta {c['polish_beta']:g})"),
+            "reference_grad_rel": resid(Vref), "closed_form_grad_rel": resid(Vcf),
+            "closed_form_vs_reference_error": float(otm.recon_error(Vcf, U, lam, 1.0)[0]),
+            "arms": out, "best_seconds_to_1e-3": best,
+            "plain_fp32_seconds_to_1e-3": plain}
+
+
+def run_lda(args, rank, world, local_rank):
+    """The default line (see the module docstring)."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    c = dict(LDA)
+    k, b, ep = c["k"], c["b"], c["epochs"]
+    a0 = k * c["alpha_i"]
+    host = lda_inputs(c, rank)
+    n = host["X"].shape[0]
+    path = LdaPath(otm, torch, c, host, dev)
+    otm.sgd_set_form(sgd_form_code(otm, args.sgd_form))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    samples = n * ep
     flops = sym_sgd_flops(n, b, k, ep)
-    per = {nm: {"sgd_ms": med["sgd_" + nm], "samples_per_s": samples / (med["sgd_" + nm] / 1e3)}
-           for nm in ("fp32", "bf16", "fp8")}
-    for nm in precs:
-        per[nm]["quantize_ms"] = med["quantize_" + nm]
-        per[nm]["vs_fp32"] = vs32[nm]
-    return {"metric": "whitened-sample SGD throughput (samples/s), BF16 precision form",
-            "value": per["bf16"]["samples_per_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": sum(med.values()),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-            "data": "synthetic",
-            "config": {"workload": c["workload"], "docs": n, "vocabulary": d, "k": k,
-                       "nnz": int(X.nnz), "alpha0": alpha0, "minibatch": b, "epochs": ep,
-                       "beta0": c["beta0"], "theta": c["theta"], "samples_per_run": samples,
-                       "l2": "flushed before each iteration (256 MiB write)",
-                       "host_generation_s": round(gen_s, 1)},
-            "whiten_project_mean_ms": med["whiten_project_mean"], "precisions": per,
-            "roofline": {"kernel": "sgd_tc_kernel (BF16, one launch = all 5,860 STGD steps)",
-                         "bound": "tensor", "achieved": flops / (med["sgd_bf16"] / 1e3) / 1e12,
-                         "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": flops / (med["sgd_bf16"] / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
-                         "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops",
-                         "algorithmic_flops_per_launch": flops,
-                         "fp32_grid_form_frac_of_fp32_peak":
-                             flops / (med["sgd_fp32"] / 1e3) / 1e12 / FP32_FMA_PEAK_TFLOPS,
-                         "note": "one chain: latency-bound per step in every form"},
-            "oracle_checks": checks, "clocks": clocks}
+    nsteps = ((n + b - 1) // b) * ep
+
+    for _ in range(args.warmup):
+        path.step()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ev = [{nm: torch.cuda.Event(enable_timing=True) for nm in ("w0", "s0", "s1", "e1")}
+          for _ in range(args.steps)]
+    l0 = otm.launch_count()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                       # evict the L2 (129 MB) between steps
+        path.step(ev[i])
+        ev[i]["e1"].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    dist_barrier(world)
+    launches = otm.launch_count() - l0
+    clocks = sampler.stop()
+    step_ms = [e["w0"].elapsed_time(e["e1"]) for e in ev]
+    sgd_ms = [e["s0"].elapsed_time(e["s1"]) for e in ev]
+    pre_ms = [e["w0"].elapsed_time(e["s0"]) for e in ev]
+    t_max = dist_max(sum(step_ms) / 1e3, world)
+
+    # end to end: inputs in pinned host memory, copies inside the timed region
+    X = host["X"]
+    pinned = {"X": tuple(torch.from_numpy(a).pin_memory() for a in (X.row_ptr, X.col, X.val)),
+              "S": torch.from_numpy(host["S"]).pin_memory(),
+              "perm": torch.from_numpy(host["perm"]).pin_memory(),
+              "V0t": torch.from_numpy(host["V0"].T.copy()).pin_memory()}
+    h2d = sum(a.numel() * a.element_size() for a in pinned["X"])
+    h2d += sum(pinned[nm].numel() * pinned[nm].element_size() for nm in ("S", "perm", "V0t"))
+    mu_host = torch.empty(c["d"], k, dtype=torch.float64).pin_memory()
+    lam_host = torch.empty(k, dtype=torch.float64).pin_memory()
+    al_host = torch.empty(k, dtype=torch.float64).pin_memory()
+    d2h = (mu_host.numel() + lam_host.numel() + al_host.numel()) * 8
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(1, args.steps // 2)
+    e2e_ms = 0.0
+    for i in range(n_e2e):
+        flush.fill_(float(i))
+        e_start.record()
+        path.upload(pinned)
+        out = path.step()
+        mu_host.copy_(out["comps"], non_blocking=True)
+        lam_host.copy_(out["lambda"], non_blocking=True)
+        al_host.copy_(out["alpha_hat"], non_blocking=True)
+        e_end.record()
+        torch.cuda.synchronize()
+        e2e_ms += e_start.elapsed_time(e_end)
+    e2e_t = dist_max(e2e_ms / 1e3, world)
+    path.upload()
+
+    if rank != 0:
+        return None
+    sgd_avg_s = statistics.mean(sgd_ms) / 1e3
+    achieved = flops / sgd_avg_s / 1e12
+    line = {
+        "metric": METRIC, "value": world * samples * args.steps / t_max, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": c["workload"], "docs": n, "vocabulary": c["d"], "k": k,
+                   "nnz": int(X.nnz), "doc_len": "Poisson(300)",
+                   "topics": "Dir(0.05) with Zipf skew", "alpha0": a0, "minibatch": b,
+                   "epochs": ep, "sgd_steps": nsteps, "samples_per_step": samples,
+                   "oversample": c["oversample"], "power_iters": c["power_iters"],
+                   "beta0": c["beta0"], "theta": c["theta"],
+                   "l2": "flushed between timed steps (256 MiB write); inputs larger than L2",
+                   "sgd_form": args.sgd_form,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "host_generation_s": round(host["gen_s"], 1),
+                   "corpus_from_cache": host["cached"]},
+        "breakdown_ms": {"whiten_project_mean": statistics.mean(pre_ms),
+                         "sgd_run": statistics.mean(sgd_ms),
+                         "unwhiten": statistics.mean(step_ms) - statistics.mean(pre_ms)
+                         - statistics.mean(sgd_ms),
+                         "wall_per_step": 1e3 * wall / args.steps},
+        "roofline": {"kernel": SGD_KERNEL_NAME.get(args.sgd_form, SGD_KERNEL_NAME["auto"]),
+                     "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "algorithmic_flops_per_launch": flops,
+                     "launch_ms": statistics.mean(sgd_ms)},
+        "e2e": {"value": world * samples * n_e2e / e2e_t, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    line["precisions"] = lda_precisions(otm, torch, path, c, host, statistics.mean(sgd_ms))
+    line["time_to_1e-3"] = time_to_target(otm, torch, dev)
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = lda_cpu_baseline(c, host)
+    return line
 
 
 def main():
@@ -980,19 +1392,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mmsb",
-                    choices=["mmsb", "batched", "warmstart", "whitening", "lda"],
-                    help="mmsb: the default pipeline line; batched: the batched form; "
+    ap.add_argument("--workload", default="lda",
+                    choices=["lda", "mmsb", "batched", "warmstart", "whitening"],
+                    help="lda: the default line (300,000-document LDA corpus, whole path); "
+                         "mmsb: the community-model pipeline; batched: the batched form; "
                          "warmstart: time to 1e-3 with the learned start; whitening: both "
-                         "randomised whitening forms on an LDA corpus; lda: the precision "
-                         "form on a 300,000-document LDA corpus")
+                         "randomised whitening forms on an LDA corpus")
     ap.add_argument("--k", type=int, default=0, help="warmstart: components (default 64)")
     ap.add_argument("--problems", type=int, default=512)
     ap.add_argument("--restarts", type=int, default=8)
     ap.add_argument("--cluster", type=int, default=0,
                     help="batched: CTAs per chain (0 = autotune)")
-    ap.add_argument("--sgd-form", default="auto", choices=["auto", "cluster", "grid"],
-                    help="mmsb: form of the FP32 STGD kernel in the pipeline (auto = grid here)")
+    ap.add_argument("--sgd-form", default="auto", choices=["auto", "split", "grid", "cluster"],
+                    help="lda / mmsb: form of the FP32 STGD kernel")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -1003,17 +1415,17 @@ def main():
         line = run_warmstart(args) if rank == 0 else None
     elif args.workload == "whitening":
         line = run_whitening(args) if rank == 0 else None
-    elif args.workload == "lda":
-        line = run_lda(args) if rank == 0 else None
     elif args.impl == "reference":
-        line = run_reference(args, rank, world)
+        line = (run_lda_reference(args, rank, world) if args.workload == "lda"
+                else run_reference(args, rank, world))
     else:
         if world > 1:
             import torch
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
-        line = run_gpu(args, rank, world, local_rank)
+        fn = run_lda if args.workload == "lda" else run_mmsb
+        line = fn(args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

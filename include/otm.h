@@ -299,9 +299,9 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
  * otm_sgd_set_form -- which FP32 kernel otm_sgd_step / otm_sgd_run use, for
  * the whole process (no paper counterpart; a performance choice with the same
  * results up to FP32 summation order):
- *   0 (default)  chosen by size: the grid form for k <= 128 and
- *                256 <= b <= 32 x (SM count) when the caller passed its
- *                workspace, the cluster form otherwise;
+ *   0 (default)  chosen by size: for b >= 256 and a caller workspace, the split
+ *                form where it applies, else the grid form for k <= 128 and
+ *                b <= 32 x (SM count); the cluster form otherwise;
  *   1            the cluster form: one thread-block cluster of up to 16 CTAs
  *                keeps V in shared memory, the minibatch split over its CTAs,
  *                partial products reduced through distributed shared memory;
@@ -311,7 +311,17 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
  *                barriers per step (k <= 128, 16 <= b <= 32 x SMs and a
  *                workspace of otm_sgd_workspace(k, b) bytes, else OTM_EINVAL
  *                from the run).  On a barrier time-out the affected columns
- *                of V are NaN.
+ *                of V are NaN;
+ *   3            the split form: one launch of C thread-block clusters; the
+ *                components are cut into C blocks (one per cluster) and every
+ *                minibatch into slices (one per CTA of a cluster); each CTA
+ *                forms its slice's products for its cluster's block, the
+ *                partial columns are summed by their owners through
+ *                distributed shared memory, and one grid barrier per step
+ *                publishes the new V (k <= 128, all clusters resident at once,
+ *                a workspace of otm_sgd_workspace(k, b) bytes, else OTM_EINVAL
+ *                from the run).  On a barrier time-out the owners' columns of
+ *                V are NaN.
  * OTM_EINVAL for another value.
  */
 otm_status otm_sgd_set_form(int form);

@@ -113,6 +113,18 @@ otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float*
                         int64_t b, double beta0, double theta, double alpha0,
                         int64_t snapshot_every, float* V_snap, void* ws, size_t ws_bytes,
                         cudaStream_t st);
+// FP32 STGD, split form (sgd_split.cu): clusters own blocks of components, the
+// CTAs of a cluster split every minibatch, partial columns reduced through
+// distributed shared memory, one grid barrier per step; same arguments and
+// results as otm_sgd_run.  Applicable for k <= 128 when all its clusters can be
+// resident at once.
+bool sgd_split_applicable(int64_t k, int64_t b, bool sym);
+size_t sgd_split_workspace(int64_t k);  // 0 where k is out of range
+otm_status sgd_split_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
+                         int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
+                         int64_t b, double beta0, double theta, double alpha0,
+                         int64_t snapshot_every, float* V_snap, void* ws, size_t ws_bytes,
+                         cudaStream_t st);
 size_t orth_workspace(int64_t m);
 // Device-side failure flags: *dflag is set to 1 (QR: non-finite Gram matrix) or
 // 2 (eigensolver: non-finite eigenvalues) or 3 (eigensolver: the refinement's grid

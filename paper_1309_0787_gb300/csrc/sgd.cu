@@ -22,6 +22,7 @@
 // cluster, adds the Gram and mean terms and broadcasts the new columns into
 // every CTA's next-V buffer together with their means a_A, a_B.  Two cluster
 // barriers per step; no global memory traffic besides the samples.
+#include <algorithm>
 #include <atomic>
 
 #include <cooperative_groups.h>
@@ -559,9 +560,10 @@ int pick_cluster(int k, bool sym, int64_t b, int max_cl, int* nbuf) {
 }
 
 // Which form runs otm_sgd_step / otm_sgd_run: 0 = chosen by size, 1 = the
-// cluster form (this file), 2 = the grid form (sgd_grid.cu).
+// cluster form (this file), 2 = the grid form (sgd_grid.cu), 3 = the split
+// form (sgd_split.cu).
 std::atomic<int> g_sgd_form{0};
-// The grid form is chosen for minibatches of at least this many samples.
+// The grid and split forms are chosen for minibatches of at least this many samples.
 constexpr int64_t GRID_AUTO_MIN_B = 256;
 
 otm_status run(float* V, const float* YA, const float* YB, const float* YC, int64_t n, int64_t k,
@@ -569,6 +571,17 @@ otm_status run(float* V, const float* YA, const float* YB, const float* YC, int6
                double beta0, double theta, double alpha0, int64_t snapshot_every, float* V_snap,
                void* ws, size_t ws_bytes, cudaStream_t st) {
   const int form = g_sgd_form.load();
+  const bool sym_views = (YA == YB) && (YB == YC);
+  if (form == 3 || (form == 0 && b >= GRID_AUTO_MIN_B && ws &&
+                    ws_bytes >= sgd_split_workspace(k))) {
+    const bool split_ok = sgd_split_applicable(k, b, sym_views);
+    if (form == 3 && !split_ok)
+      return set_error(OTM_EINVAL, "sgd: the split form needs k <= 128 and all of its clusters "
+                                   "resident at once");
+    if (split_ok)
+      return sgd_split_run(V, YA, YB, YC, n, k, ybar3, perm, epochs, b, beta0, theta, alpha0,
+                           snapshot_every, V_snap, ws, ws_bytes, st);
+  }
   const bool grid_ok = sgd_grid_applicable(k, b);
   if (form == 2 && !grid_ok)
     return set_error(OTM_EINVAL, "sgd: the grid form needs k <= 128 and 16 <= b <= 32 x SMs");
@@ -636,7 +649,9 @@ using namespace otm;
 
 extern "C" {
 
-size_t otm_sgd_workspace(int64_t k, int64_t b) { return sgd_grid_workspace(k, b); }
+size_t otm_sgd_workspace(int64_t k, int64_t b) {
+  return std::max(sgd_grid_workspace(k, b), sgd_split_workspace(k));
+}
 
 otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float* YC, int64_t b,
                         int64_t k, const double* ybar3, double theta, double beta,
@@ -651,7 +666,7 @@ otm_status otm_sgd_step(float* V, const float* YA, const float* YB, const float*
 
 otm_status otm_sgd_set_form(int form) {
   clear_error();
-  OTM_REQUIRE(form >= 0 && form <= 2, "otm_sgd_set_form: form must be 0, 1 or 2");
+  OTM_REQUIRE(form >= 0 && form <= 3, "otm_sgd_set_form: form must be 0, 1, 2 or 3");
   g_sgd_form.store(form);
   return OTM_OK;
 }

@@ -1,0 +1,652 @@
+// Stochastic tensor gradient descent on the implicit whitened tensor
+// (Section 3.2, Lemma 3 / Eq. (16)), FP32, "split" form: ONE launch of C
+// thread-block clusters of CL CTAs that runs every step of the schedule.
+//
+// The k components are cut into C blocks of Nc (Nc <= CL) and every minibatch
+// into CL slices of Sb samples.  Cluster c owns block c; CTA s of the cluster
+// owns slice s and, for the update, component i = c Nc + s.  Per step:
+//   every CTA, for its slice and its cluster's block (in chunks of SC samples):
+//     A_A = Y_A V_c, A_B = Y_B V_c          (samples x block components)
+//     B   = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B)
+//     part[i] = sum_t y_C,t B[t, i],  part[i][kp] = sum_t (A_A o A_B)[t, i]
+//   cluster barrier;
+//   the owner of component i sums the CL partial columns of i through
+//   distributed shared memory and forms
+//     G_data = part / b + ybar_C (c3 a_A a_B - c2 s / b),
+//     G_gram = sum_j <v_j, v_i>^2 v_j      (from its copy of all of V),
+//     v_i   <- v_i - beta_t (kappa G_gram - G_data),
+//   and writes v_i and its means a_A, a_B to the iterate buffer of the next
+//   step in global memory;
+//   grid barrier (hierarchical: cluster barrier, one arrival per cluster on a
+//   global counter, cluster barrier), then every CTA copies the new V into
+//   shared memory (cp.async through L2) while the samples of the next chunk are
+//   already in flight.
+// Compared with the grid form (sgd_grid.cu), which reduces one k x k partial
+// per CTA through L2 and needs two grid barriers per step, each CTA here
+// produces only k x Nc partial sums, the reduction stays inside the cluster,
+// and a step has one grid barrier.  The partial sums are added in a fixed
+// order, so the result does not depend on timing.
+//
+// Every wait is bounded: a global-counter wait that times out sets a flag,
+// the decision is shared by the whole cluster through distributed shared
+// memory, and every CTA of the cluster leaves the kernel at the same point;
+// the owners then write NaN into their columns of V.
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
+#include "grid_sync.cuh"
+#include "otm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace otm {
+namespace {
+
+constexpr int ST = 256;          // threads per CTA
+constexpr int SP_KMAX = 128;
+constexpr int SP_CLMAX = 16;
+
+struct SplitArgs {
+  const float* YA;
+  const float* YB;
+  const float* YC;
+  const int32_t* perm;
+  const double* ybar3;
+  float* V;        // k x k, component-major (row i = v_i); initial and final iterate
+  float* V_snap;
+  float* Vg;       // 2 x kp x ld: the iterate of the next step, by step parity
+  float* Mg;       // 2 x 2 x kp: its means a_A, a_B, by step parity
+  unsigned* bar;   // global arrival counter (zero on entry)
+  int* flag;       // wait time-out
+  int64_t n, b, spe, total_steps, snapshot_every;
+  int k, Nc, Sb, SC;
+  int vec;         // sample rows are 16-byte aligned (k % 4 == 0, aligned bases)
+  double beta0;
+  float c1, c2, c3, kappa;
+};
+
+struct SLayout {
+  int kp, ld, nview, Nc4, kpp, SC;
+  size_t off_v, off_y, off_b, off_p, off_part, off_yb, off_a, off_h, off_red, total;
+};
+
+// Shared memory (floats).  Rows of V and of the samples have stride ld, an odd
+// number of float4s, so that float4 reads of consecutive rows fall in
+// different bank groups.
+__host__ __device__ inline SLayout s_layout(int k, bool sym, int Nc, int SC) {
+  SLayout L;
+  L.kp = (k + 3) & ~3;
+  L.ld = ((L.kp / 4) & 1) ? L.kp : L.kp + 4;
+  L.nview = sym ? 1 : 3;
+  L.Nc4 = (Nc + 3) & ~3;
+  L.kpp = L.kp + 4;  // a partial column: kp coordinates, then the sum of A_A o A_B
+  L.SC = SC;
+  size_t f = 0;
+  L.off_v = f;    f += (size_t)L.kp * L.ld;              // all of V, component rows
+  L.off_y = f;    f += 2 * (size_t)L.nview * SC * L.ld;  // sample chunks [buf][view][t]
+  L.off_b = f;    f += (size_t)SC * L.Nc4;               // B [t][i]
+  L.off_p = f;    f += (size_t)SC * L.Nc4;               // A_A o A_B [t][i]
+  L.off_part = f; f += (size_t)L.Nc4 * L.kpp;            // partial columns [i][r]
+  L.off_yb = f;   f += 3 * (size_t)L.ld;                 // ybar_A, ybar_B, ybar_C
+  L.off_a = f;    f += 2 * (size_t)L.Nc4;                // a_A, a_B of the block
+  L.off_h = f;    f += (size_t)L.kp;                     // <v_j, v_i>^2 of the owned i
+  L.off_red = f;  f += 2 * (ST / 32) + 4;
+  L.total = f;
+  return L;
+}
+
+__device__ __forceinline__ float dot4(const float4& a, const float4& b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
+__device__ __forceinline__ void fma4(float4& acc, float s, const float4& v) {
+  acc.x = fmaf(s, v.x, acc.x);
+  acc.y = fmaf(s, v.y, acc.y);
+  acc.z = fmaf(s, v.z, acc.z);
+  acc.w = fmaf(s, v.w, acc.w);
+}
+__device__ __forceinline__ void cp16(float* dst, const float* src, bool in) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(in ? 16u : 0u)
+               : "memory");
+}
+__device__ __forceinline__ void cp4(float* dst, const float* src, bool in) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(in ? 4u : 0u)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Grid-wide barrier of the cooperative cluster launch.  Every CTA of a cluster
+// arrives at a cluster barrier; thread 0 of cluster rank 0 then arrives on the
+// global counter (release) and waits (acquire, bounded) for the other
+// clusters; a second cluster barrier releases the cluster, whose CTAs read the
+// outcome from rank 0's shared memory, so that all of them leave or continue
+// together.  Returns false on a time-out (*flag set).
+__device__ __forceinline__ bool cluster_grid_barrier(cg::cluster_group& cluster, unsigned* count,
+                                                     int* flag, int* s_ok) {
+  cluster.sync();
+  if (cluster.block_rank() == 0 && threadIdx.x == 0) {
+    const unsigned nclusters = gridDim.x / cluster.num_blocks();
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nclusters - 1) : 1u;
+    unsigned old, v;
+    int ok = 1;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(count), "r"(add) : "memory");
+    const long long t0 = clock64();
+    do {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (((v ^ old) & 0x80000000u) != 0u) break;
+      if (clock64() - t0 > GRID_WAIT_CYCLES) {
+        atomicExch(flag, 1);
+        ok = 0;
+        break;
+      }
+    } while (true);
+    *s_ok = ok;
+  }
+  cluster.sync();
+  return *cluster.map_shared_rank(s_ok, 0) != 0;
+}
+
+template <bool SYM>
+__global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_ok;
+  __shared__ float s_si;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int sl = (int)cluster.block_rank();       // sample slice of this CTA
+  const int cb = (int)(blockIdx.x / CL);          // component block of its cluster
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = a.k, Nc = a.Nc, Sb = a.Sb;
+  const SLayout L = s_layout(k, SYM, Nc, a.SC);
+  const int kp = L.kp, ld = L.ld, kq = kp / 4, SC = L.SC, Nc4 = L.Nc4, kpp = L.kpp;
+  float* Vs = sm + L.off_v;
+  float* Ysb = sm + L.off_y;
+  float* Bs = sm + L.off_b;
+  float* Ps = sm + L.off_p;
+  float* part = sm + L.off_part;
+  float* ybA = sm + L.off_yb;
+  float* ybB = ybA + ld;
+  float* ybC = ybB + ld;
+  float* aA = sm + L.off_a;
+  float* aB = aA + Nc4;
+  float* hs = sm + L.off_h;
+  float* red = sm + L.off_red;
+  const int c0 = cb * Nc;                          // first component of the block
+  const int own = c0 + sl;                         // component owned by this CTA
+  const bool owner = sl < Nc && own < k;
+  const int nchunk = (Sb + SC - 1) / SC;
+
+  for (int r = tid; r < ld; r += ST) {
+    ybA[r] = r < k ? (float)a.ybar3[r] : 0.f;
+    ybB[r] = r < k ? (float)a.ybar3[k + r] : 0.f;
+    ybC[r] = r < k ? (float)a.ybar3[2 * k + r] : 0.f;
+  }
+  for (int idx = tid; idx < kp * ld; idx += ST) {
+    const int i = idx / ld, r = idx % ld;
+    Vs[idx] = (i < k && r < k) ? a.V[(int64_t)i * k + r] : 0.f;
+  }
+  // padding rows and columns of both iterate buffers stay zero (the owners
+  // write rows < k, columns < kp)
+  if (blockIdx.x == 0) {
+    for (int bsel = 0; bsel < 2; ++bsel) {
+      float* Vb = a.Vg + (size_t)bsel * kp * ld;
+      for (int idx = tid; idx < kp * ld; idx += ST) {
+        const int i = idx / ld, r = idx % ld;
+        if (i >= k || r >= kp) Vb[idx] = 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  // a_A, a_B of the block's components from the initial V
+  for (int i = warp; i < Nc4; i += ST / 32) {
+    float x = 0.f, y = 0.f;
+    const int gi = c0 + i;
+    if (i < Nc && gi < k)
+      for (int r = lane; r < kp; r += 32) {
+        x = fmaf(Vs[gi * ld + r], ybA[r], x);
+        y = fmaf(Vs[gi * ld + r], ybB[r], y);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) {
+      aA[i] = x;
+      aB[i] = y;
+    }
+  }
+
+  // sample chunk g (global chunk sequence: step g / nchunk, chunk g % nchunk)
+  // into buffer g & 1; rows outside the minibatch or the data read as zeros.
+  // Every call commits one cp.async group (an empty one past the last step),
+  // so that "all but the newest group complete" always means chunk g - 1 landed.
+  auto issue_chunk = [&](int64_t g) {
+    const int64_t s = g / nchunk;
+    if (s >= a.total_steps) {
+      cp_commit();
+      return;
+    }
+    const int q = (int)(g % nchunk);
+    const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
+    const int64_t beff = min(a.b, a.n - pos0);
+    float* Yb = Ysb + (size_t)(g & 1) * L.nview * SC * ld;
+    const int per_row = a.vec ? kq : kp;
+    const int items = L.nview * SC * per_row;
+    for (int idx = tid; idx < items; idx += ST) {
+      const int v = idx / (SC * per_row), rem = idx % (SC * per_row);
+      const int t = rem / per_row, u = rem % per_row;
+      const int pl = q * SC + t;
+      const int64_t p = (int64_t)sl * Sb + pl;
+      int64_t row = -1;
+      if (pl < Sb && p < beff) {
+        row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
+        if (row < 0 || row >= a.n) row = -1;
+      }
+      const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+      float* dst = Yb + ((size_t)v * SC + t) * ld;
+      if (a.vec) {
+        cp16(dst + 4 * u, row >= 0 ? Yg + row * k + 4 * u : Yg, row >= 0);
+      } else {
+        const bool in = row >= 0 && u < k;
+        cp4(dst + u, in ? Yg + row * k + u : Yg, in);
+      }
+    }
+    cp_commit();
+  };
+
+  int64_t g = 0;  // next chunk to consume
+  issue_chunk(0);
+  for (int64_t s = 0; s < a.total_steps; ++s) {
+    const int par = (int)(s & 1);
+    const int64_t pos0 = (s % a.spe) * a.b;
+    const int64_t beff = min(a.b, a.n - pos0);
+    float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    float ssum = 0.f;
+    for (int q = 0; q < nchunk; ++q, ++g) {
+      issue_chunk(g + 1);
+      cp_wait_one();
+      __syncthreads();
+      const float* Yb = Ysb + (size_t)(g & 1) * L.nview * SC * ld;
+      // first product: A_A, A_B for 4 block components x 1 sample per item
+      for (int item = tid; item < SC * (Nc4 / 4); item += ST) {
+        const int t = item % SC, i0 = 4 * (item / SC);
+        const float* ya = Yb + (size_t)t * ld;
+        const float* yb = SYM ? ya : Yb + ((size_t)SC + t) * ld;
+        float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* vr[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gi = c0 + i0 + j;
+          vr[j] = (i0 + j < Nc && gi < k) ? Vs + (size_t)gi * ld : nullptr;
+        }
+        for (int r = 0; r < kp; r += 4) {
+          const float4 yA = *reinterpret_cast<const float4*>(ya + r);
+          const float4 yB = SYM ? yA : *reinterpret_cast<const float4*>(yb + r);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (vr[j]) {
+              const float4 v = *reinterpret_cast<const float4*>(vr[j] + r);
+              xa[j] = dot4(v, yA, xa[j]);
+              if (!SYM) xb[j] = dot4(v, yB, xb[j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int i = i0 + j;
+          const float xA = xa[j], xB = SYM ? xa[j] : xb[j];
+          const float pr = xA * xB;
+          Ps[t * Nc4 + i] = pr;
+          Bs[t * Nc4 + i] = a.c1 * pr - a.c2 * (aB[i] * xA + aA[i] * xB);
+        }
+      }
+      __syncthreads();
+      if (tid < Nc4)
+        for (int t = 0; t < SC; ++t) ssum += Ps[t * Nc4 + tid];
+      // second product: partial columns sum_t y_C,t B[t, i] (float4 of coordinates)
+      {
+        const float* yc = SYM ? Yb : Yb + 2 * (size_t)SC * ld;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int item = tid + u * ST;
+          if (item < Nc * kq) {
+            const int i = item / kq, r0 = 4 * (item % kq);
+            float4 acc_u = acc[u];
+            for (int t = 0; t < SC; ++t)
+              fma4(acc_u, Bs[t * Nc4 + i], *reinterpret_cast<const float4*>(yc + (size_t)t * ld + r0));
+            acc[u] = acc_u;
+          }
+        }
+      }
+      __syncthreads();  // the chunk buffer and B are reused by the next chunk
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int item = tid + u * ST;
+      if (item < Nc * kq) {
+        const int i = item / kq, r0 = 4 * (item % kq);
+        *reinterpret_cast<float4*>(part + (size_t)i * kpp + r0) = acc[u];
+      }
+    }
+    if (tid < Nc4) part[(size_t)tid * kpp + kp] = ssum;
+    cluster.sync();
+
+    // owner: sum the partial columns of component `own`, Gram term, update
+    float* Vnext = a.Vg + (size_t)(par ^ 1) * kp * ld;
+    float* Mnext = a.Mg + (size_t)(par ^ 1) * 2 * kp;
+    if (owner) {
+      const float beta = (float)a.beta0 / sqrtf((float)(s + 1));
+      const float inv_b = 1.f / (float)beff;
+      // the CL partial columns (and sums) through distributed shared memory: all
+      // loads issued before the Gram term, which needs only V
+      const int r = tid;  // coordinate (r == kp: the sum of A_A o A_B)
+      float dsum = 0.f;
+      if (r <= kp) {
+        float pv[SP_CLMAX];
+#pragma unroll
+        for (int c = 0; c < SP_CLMAX; ++c)
+          if (c < CL) pv[c] = *cluster.map_shared_rank(part + (size_t)sl * kpp + r, c);
+#pragma unroll
+        for (int c = 0; c < SP_CLMAX; ++c)
+          if (c < CL) dsum += pv[c];
+      }
+      if (r == kp) s_si = dsum;
+      if (r < k) {  // (v_j . v_own)^2
+        const float* vi = Vs + (size_t)own * ld;
+        const float* vj = Vs + (size_t)r * ld;
+        float h0 = 0.f, h1 = 0.f;
+        for (int q = 0; q < kp; q += 8) {
+          h0 = dot4(*reinterpret_cast<const float4*>(vi + q), *reinterpret_cast<const float4*>(vj + q), h0);
+          if (q + 4 < kp)
+            h1 = dot4(*reinterpret_cast<const float4*>(vi + q + 4),
+                      *reinterpret_cast<const float4*>(vj + q + 4), h1);
+        }
+        const float hv = h0 + h1;
+        hs[r] = hv * hv;
+      }
+      __syncthreads();
+      float x = 0.f, y = 0.f;
+      if (r < kp) {
+        float gg = 0.f;
+        for (int j = 0; j < k; ++j) gg = fmaf(hs[j], Vs[(size_t)j * ld + r], gg);
+        const float ai = aA[sl], bi = aB[sl];
+        const float gdata = dsum * inv_b + ybC[r] * (a.c3 * ai * bi - a.c2 * s_si * inv_b);
+        const float v = r < k ? Vs[(size_t)own * ld + r] - beta * (a.kappa * gg - gdata) : 0.f;
+        Vnext[(size_t)own * ld + r] = v;
+        x = v * ybA[r];
+        y = v * ybB[r];
+        if (r < k) {
+          if (a.snapshot_every > 0 && (s + 1) % a.snapshot_every == 0)
+            a.V_snap[((s + 1) / a.snapshot_every - 1) * (int64_t)k * k + (int64_t)own * k + r] = v;
+          if (s + 1 == a.total_steps) a.V[(int64_t)own * k + r] = v;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane == 0) {
+        red[warp] = x;
+        red[ST / 32 + warp] = y;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float tx = 0.f, ty = 0.f;
+#pragma unroll
+        for (int w = 0; w < ST / 32; ++w) {
+          tx += red[w];
+          ty += red[ST / 32 + w];
+        }
+        Mnext[own] = tx;
+        Mnext[kp + own] = ty;
+      }
+    }
+    __threadfence();
+    if (!cluster_grid_barrier(cluster, a.bar, a.flag, &s_ok)) {
+      // the whole cluster leaves here together; its peers read rank 0's flag
+      // before the final cluster barrier
+      if (owner)
+        for (int r = tid; r < k; r += ST) a.V[(int64_t)own * k + r] = __int_as_float(0x7fc00000);
+      cp_wait_all();
+      cluster.sync();
+      return;
+    }
+    if (s + 1 < a.total_steps) {
+      // the new V (all components) and the block's means; the next chunk's
+      // samples are already in flight
+      for (int idx = tid; idx < kp * ld / 4; idx += ST) cp16(Vs + 4 * idx, Vnext + 4 * idx, true);
+      cp_commit();
+      for (int i = tid; i < Nc4; i += ST) {
+        const int gi = c0 + i;
+        aA[i] = (i < Nc && gi < k) ? __ldcg(Mnext + gi) : 0.f;
+        aB[i] = (i < Nc && gi < k) ? __ldcg(Mnext + kp + gi) : 0.f;
+      }
+      cp_wait_all();  // V (and the prefetched chunk, issued long before)
+      __syncthreads();
+    }
+  }
+  cp_wait_all();
+  cluster.sync();  // no CTA leaves while a peer may still read its shared memory
+}
+
+int split_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (sms[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = v > 0 ? v : 1;
+  }
+  return sms[dev];
+}
+
+int split_smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (v <= 0) v = 227 * 1024;
+  }
+  return v;
+}
+
+// Launch shape: cluster size CL, components per block Nc (<= CL), samples per
+// CTA and step Sb, chunk SC; false if none fits.
+struct SplitPlan {
+  int CL, Nc, C, Sb, SC;
+  size_t smem;
+};
+
+bool split_plan(int64_t k, int64_t b, bool sym, int CL, SplitPlan* out) {
+  if (k < 1 || k > SP_KMAX || b < 1) return false;
+  const int C = (int)((k + CL - 1) / CL);  // blocks
+  const int Nc = (int)((k + C - 1) / C);   // components per block (<= CL)
+  if (C * CL > split_sms()) return false;
+  const int Sb = (int)((b + CL - 1) / CL);
+  for (int SC : {64, 32, 16}) {
+    const int sc = std::min(SC, std::max(Sb, 1));
+    const SLayout L = s_layout((int)k, sym, Nc, sc);
+    const size_t bytes = L.total * sizeof(float);
+    if (bytes + 1024 <= (size_t)split_smem_optin()) {
+      // each thread accumulates at most two float4 partial outputs
+      if (Nc * (L.kp / 4) > 2 * ST) return false;
+      *out = {CL, Nc, C, Sb, sc, bytes};
+      return true;
+    }
+  }
+  return false;
+}
+
+template <bool SYM>
+cudaLaunchConfig_t split_cfg(const SplitPlan& P, cudaStream_t st, cudaLaunchAttribute* attr,
+                             bool cooperative) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P.C * P.CL, 1, 1);
+  cfg.blockDim = dim3(ST, 1, 1);
+  cfg.dynamicSmemBytes = P.smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P.CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = cooperative ? 2 : 1;
+  return cfg;
+}
+
+// Whether all C clusters of plan P can be resident at once (so that the grid
+// barrier can complete); sets the kernel's attributes.
+template <bool SYM>
+bool split_fits(const SplitPlan& P) {
+  auto kern = sgd_split_kernel<SYM>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (P.CL > 8 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = split_cfg<SYM>(P, nullptr, attr, false);
+  int n = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (const void*)kern, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= P.C;
+}
+
+// The plan for (k, b, views), cached per (k, b, sym): 8-CTA clusters, else 16.
+bool split_choose(int64_t k, int64_t b, bool sym, SplitPlan* out) {
+  struct Entry {
+    int64_t k, b;
+    bool sym, ok;
+    SplitPlan P;
+  };
+  static Entry cache[32];
+  static int ncache = 0;
+  for (int i = 0; i < ncache; ++i)
+    if (cache[i].k == k && cache[i].b == b && cache[i].sym == sym) {
+      *out = cache[i].P;
+      return cache[i].ok;
+    }
+  bool ok = false;
+  SplitPlan P{};
+  for (int CL : {8, 16}) {
+    SplitPlan Q;
+    if (!split_plan(k, b, sym, CL, &Q)) continue;
+    if (sym ? split_fits<true>(Q) : split_fits<false>(Q)) {
+      P = Q;
+      ok = true;
+      break;
+    }
+  }
+  if (ncache < 32) cache[ncache++] = {k, b, sym, ok, P};
+  *out = P;
+  return ok;
+}
+
+template <bool SYM>
+otm_status launch_split(SplitArgs& args, const SplitPlan& P, cudaStream_t st) {
+  auto kern = sgd_split_kernel<SYM>;
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = split_cfg<SYM>(P, st, attr, true);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
+  if (e != cudaSuccess) {
+    // the cooperative attribute is not accepted with clusters here: residency
+    // was checked by split_fits, every wait is bounded
+    cudaGetLastError();
+    cfg = split_cfg<SYM>(P, st, attr, false);
+    OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
+  }
+  count_launch();
+  return OTM_OK;
+}
+
+WorkspaceSize split_ws(int64_t k) {
+  const int kp = (int)((k + 3) & ~3);
+  const int ld = ((kp / 4) & 1) ? kp : kp + 4;
+  WorkspaceSize w;
+  w.add<float>(2 * (size_t)kp * ld).add<float>(4 * (size_t)kp).add<unsigned>(1).add<int>(1);
+  return w;
+}
+
+}  // namespace
+
+bool sgd_split_applicable(int64_t k, int64_t b, bool sym) {
+  SplitPlan P;
+  return split_choose(k, b, sym, &P);
+}
+
+size_t sgd_split_workspace(int64_t k) { return (k >= 1 && k <= SP_KMAX) ? split_ws(k).bytes() : 0; }
+
+otm_status sgd_split_run(float* V, const float* YA, const float* YB, const float* YC, int64_t n,
+                         int64_t k, const double* ybar3, const int32_t* perm, int64_t epochs,
+                         int64_t b, double beta0, double theta, double alpha0,
+                         int64_t snapshot_every, float* V_snap, void* ws_ptr, size_t ws_bytes,
+                         cudaStream_t st) {
+  const bool sym = (YA == YB) && (YB == YC);
+  SplitPlan P;
+  if (!split_choose(k, b, sym, &P))
+    return set_error(OTM_EINVAL, "sgd split form: k=%lld, b=%lld does not fit", (long long)k,
+                     (long long)b);
+  if (!ws_ptr || ws_bytes < split_ws(k).bytes())
+    return set_error(OTM_EINVAL, "sgd split form: workspace too small (need %zu bytes)",
+                     split_ws(k).bytes());
+  SplitArgs args;
+  args.YA = YA;
+  args.YB = YB;
+  args.YC = YC;
+  args.perm = perm;
+  args.ybar3 = ybar3;
+  args.V = V;
+  args.V_snap = V_snap;
+  args.n = n;
+  args.b = b;
+  args.spe = (n + b - 1) / b;
+  args.total_steps = args.spe * epochs;
+  args.snapshot_every = snapshot_every;
+  args.k = (int)k;
+  args.Nc = P.Nc;
+  args.Sb = P.Sb;
+  args.SC = P.SC;
+  args.vec = (k % 4 == 0) && ((reinterpret_cast<uintptr_t>(YA) | reinterpret_cast<uintptr_t>(YB) |
+                                reinterpret_cast<uintptr_t>(YC)) & 15) == 0;
+  args.beta0 = beta0;
+  args.c1 = (float)((alpha0 + 1.0) * (alpha0 + 2.0) / 2.0);
+  args.c2 = (float)(alpha0 * (alpha0 + 1.0) / 2.0);
+  args.c3 = (float)(alpha0 * alpha0);
+  args.kappa = (float)(0.5 * (1.0 + theta));
+  const int kp = (int)((k + 3) & ~3);
+  const int ld = ((kp / 4) & 1) ? kp : kp + 4;
+  Workspace ws(ws_ptr, ws_bytes);
+  args.Vg = ws.take<float>(2 * (size_t)kp * ld);
+  args.Mg = ws.take<float>(4 * (size_t)kp);
+  args.bar = ws.take<unsigned>(1);
+  args.flag = ws.take<int>(1);
+  OTM_CHECK_CUDA(cudaMemsetAsync(args.bar, 0, sizeof(unsigned), st));
+  return sym ? launch_split<true>(args, P, st) : launch_split<false>(args, P, st);
+}
+
+}  // namespace otm

@@ -377,7 +377,7 @@ def column_mean(Y):
     return yb
 
 
-SGD_FORM_AUTO, SGD_FORM_CLUSTER, SGD_FORM_GRID = 0, 1, 2
+SGD_FORM_AUTO, SGD_FORM_CLUSTER, SGD_FORM_GRID, SGD_FORM_SPLIT = 0, 1, 2, 3
 
 
 def sgd_set_form(form: int) -> None:

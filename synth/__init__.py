@@ -167,15 +167,15 @@ def mmsb_graph(seed: int, n_per: int, k: int, alpha_i: float, p: float, q: float
     return {**blocks, "Pi": Pi, "P": P, "alpha": alpha}
 
 
-def orthogonal_samples(seed: int, k: int, n: int, sigma: float) -> dict:
+def orthogonal_samples(seed: int, k: int, n: int, sigma: float, conc: float = 1.0) -> dict:
     """Whitened samples of an orthogonal tensor plus Gaussian noise.
 
-    w ~ Dir(1_k), U a Haar-random orthonormal k x k matrix, h_t ~ Cat(w),
+    w ~ Dir(conc 1_k), U a Haar-random orthonormal k x k matrix, h_t ~ Cat(w),
     y_t = w_h^{-1/2} u_h + sigma * eps_t.  Returns Y (n x k, float32) and the
-    ground truth (U: columns u_h, w).
+    ground truth (U: columns u_h, w, the draws h).
     """
     g = rng(seed)
-    w = g.dirichlet(np.ones(k))
+    w = g.dirichlet(np.full(k, float(conc)))
     U = _haar(g, k)
     h = g.choice(k, size=n, p=w)
     Y = (U[:, h] / np.sqrt(w[h])).T + sigma * g.standard_normal((n, k))

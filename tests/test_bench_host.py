@@ -32,7 +32,7 @@ def test_make_inputs_shapes_and_rank_seeds():
 
 
 def test_lda_oracle_checks_zero_on_oracle_inputs():
-    c = dict(bench.LDA3)
+    c = dict(bench.LDA)
     c.update(k=6, b=40)
     corp = synth.lda_corpus(1, 300, 50, 6, 0.1, 0.1, 30)
     X = corp["X"]
@@ -44,11 +44,45 @@ def test_lda_oracle_checks_zero_on_oracle_inputs():
     Yb, yb = Y[:40], Y.mean(axis=0)
     V1 = ostgd.sgd_step(V0, Yb, Yb, Yb, (yb, yb, yb), c["theta"], c["beta0"],
                         6 * c["alpha_i"])
-    out = bench.lda_oracle_checks(X, W, Y[docs], docs, V0, Yb, yb, c,
+    out = bench.lda_oracle_checks(c, X, W, Y[docs], docs, Yb, yb, V0,
                                   {"fp32": V1, "off": V0 + 1.1 * (V1 - V0)})
-    assert out["projection_rel_err"] < 1e-14
-    assert out["step_update_rel_err"]["fp32"] < 1e-12
-    assert abs(out["step_update_rel_err"]["off"] - 0.1) < 1e-9
+    assert out["projection_rows_rel_err"] < 1e-14
+    st = out["step"]
+    assert st["fp32"]["update_rel_err"] < 1e-12 and st["fp32"]["grad_rel_err"] < 1e-12
+    assert st["fp32"]["grad_rel_err_worst_component"] < 1e-12
+    assert abs(st["off"]["update_rel_err"] - 0.1) < 1e-9
+    # the gradient error is relative to the two terms, never above the update error
+    assert 0 < st["off"]["grad_rel_err"] <= st["off"]["update_rel_err"]
+
+
+def test_lda_inputs_shapes_and_rank_seeds(tmp_path, monkeypatch):
+    import tempfile
+    monkeypatch.setattr(tempfile, "gettempdir", lambda: str(tmp_path))
+    c = dict(bench.LDA)
+    c.update(n_docs=200, d=60, k=5, epochs=2, doc_len=20)
+    a = bench.lda_inputs(c, 0)
+    assert not a["cached"]
+    a2 = bench.lda_inputs(c, 0)           # second call loads the cached corpus
+    assert a2["cached"]
+    for f in ("row_ptr", "col", "val"):
+        np.testing.assert_array_equal(getattr(a["X"], f), getattr(a2["X"], f))
+    b = bench.lda_inputs(c, 1)
+    assert a["S"].shape == (60, 25) and a["perm"].shape == (2, 200) and a["V0"].shape == (5, 5)
+    assert not np.array_equal(a["S"], b["S"])
+
+
+def test_cpu_oracle_sample_extrapolates_whitening(tmp_path, monkeypatch):
+    """The oracle timing leg runs on a small corpus and returns positive times;
+    the whitening estimate is at least the largest sampled fraction's time."""
+    import tempfile
+    monkeypatch.setattr(tempfile, "gettempdir", lambda: str(tmp_path))
+    c = dict(bench.LDA)
+    c.update(n_docs=400, d=80, k=4, epochs=1, doc_len=30, b=64)
+    host = bench.lda_inputs(c, 0)
+    r = bench.lda_oracle_sample(c, host, (0.25, 0.5), None)
+    assert r["stgd_steps_run"] == r["stgd_steps_total"] == 7
+    assert r["whiten_s"] >= r["whiten_sample_s"][-1] > 0
+    assert r["project_means_s"] > 0 and r["stgd_s"] > 0
 
 
 def test_sym_sgd_flops_closed_form():

@@ -1,9 +1,11 @@
-"""GPU tests of the two FP32 kernels of the fused STGD step (Lemma 3): the
-cluster form (one thread-block cluster, V in shared memory) and the grid form
-(one cooperative launch over many SMs, partial products reduced through L2).
-Both are checked against the FP64 oracle at the FP32 tolerance (1e-5) and
-against each other; the form is a process-wide setting, restored to the
-default after every test."""
+"""GPU tests of the three FP32 kernels of the fused STGD step (Lemma 3): the
+cluster form (one thread-block cluster, V in shared memory), the grid form
+(one cooperative launch over many SMs, partial products reduced through L2)
+and the split form (clusters own blocks of components, their CTAs split the
+minibatch, partial columns reduced through distributed shared memory, one
+grid barrier per step).  All are checked against the FP64 oracle at the FP32
+tolerance (1e-5) and against each other; the form is a process-wide setting,
+restored to the default after every test."""
 import numpy as np
 import pytest
 
@@ -45,7 +47,7 @@ def _dev_views(Ys, sym):
     return [Yd[0]] * 3 if sym else Yd
 
 
-@pytest.mark.parametrize("form", [1, 2], indirect=True)
+@pytest.mark.parametrize("form", [1, 2, 3], indirect=True)
 @pytest.mark.parametrize("k,b,sym,a0", [(100, 1024, False, 1.0), (128, 2000, True, 2.0),
                                         (17, 300, False, 0.7), (1, 64, True, 1.0),
                                         (64, 4096, False, 0.0), (33, 16, False, 1.0)])
@@ -66,7 +68,7 @@ def test_step_gradient_both_forms(otm, form, k, b, sym, a0):
     assert frob < 1e-5 and col < 1e-5, (frob, col)
 
 
-@pytest.mark.parametrize("form", [1, 2], indirect=True)
+@pytest.mark.parametrize("form", [1, 2, 3], indirect=True)
 @pytest.mark.parametrize("k,n,b,epochs,sym", [(12, 700, 128, 3, True), (100, 3000, 1024, 2, False),
                                               (40, 2500, 512, 2, False)])
 def test_run_schedule_both_forms(otm, form, k, n, b, epochs, sym):
@@ -91,7 +93,7 @@ def test_run_schedule_both_forms(otm, form, k, n, b, epochs, sym):
 
 
 def test_forms_agree(otm):
-    """The two forms on the same run differ only by FP32 summation order."""
+    """The three forms on the same run differ only by FP32 summation order."""
     k, n, b, epochs = 100, 5000, 1024, 3
     g = np.random.default_rng(5)
     Ys, yb = _views(g, n, k, False)
@@ -99,7 +101,7 @@ def test_forms_agree(otm):
     V0 = synth.haar_orthonormal(7, k).astype(np.float32)
     out = {}
     try:
-        for f in (otm.SGD_FORM_CLUSTER, otm.SGD_FORM_GRID):
+        for f in (otm.SGD_FORM_CLUSTER, otm.SGD_FORM_GRID, otm.SGD_FORM_SPLIT):
             otm.sgd_set_form(f)
             Vd = _dev(V0.T.copy())
             otm.sgd_run(Vd, *_dev_views(Ys, False), _dev(yb), _dev(perm), epochs, b, 1e-2, 1.0,
@@ -109,6 +111,7 @@ def test_forms_agree(otm):
     finally:
         otm.sgd_set_form(otm.SGD_FORM_AUTO)
     assert rel(out[otm.SGD_FORM_GRID], out[otm.SGD_FORM_CLUSTER]) < 1e-5
+    assert rel(out[otm.SGD_FORM_SPLIT], out[otm.SGD_FORM_CLUSTER]) < 1e-5
 
 
 def test_grid_form_limits(otm):
@@ -122,7 +125,7 @@ def test_grid_form_limits(otm):
         with pytest.raises(otm.OtmError):   # b = 8 < 16
             otm.sgd_step(Vd, *_dev_views(Ys, True), _dev(yb), 1.0, 1e-3, 1.0)
         with pytest.raises(otm.OtmError):
-            otm.sgd_set_form(3)
+            otm.sgd_set_form(4)
         otm.sgd_set_form(otm.SGD_FORM_AUTO)
         otm.sgd_step(Vd, *_dev_views(Ys, True), _dev(yb), 1.0, 1e-3, 1.0)
         torch.cuda.synchronize()
@@ -131,7 +134,7 @@ def test_grid_form_limits(otm):
         otm.sgd_set_form(otm.SGD_FORM_AUTO)
 
 
-@pytest.mark.parametrize("form", [1, 2], indirect=True)
+@pytest.mark.parametrize("form", [1, 2, 3], indirect=True)
 def test_invalid_permutation_entries_read_as_zero_samples(otm, form):
     """A permutation entry outside [0, n) contributes a zero sample (both forms):
     the result equals the oracle's run on samples with a zero row appended and
@@ -152,3 +155,38 @@ def test_invalid_permutation_entries_read_as_zero_samples(otm, form):
     # the oracle visits perm[e, :n] of the (n + 1)-row sample matrix
     Vo, _ = ostgd.sgd_run(V0, *Yz, tuple(yb), np.ascontiguousarray(pz), b, 1e-2, 1.0, 1.0)
     assert rel(to_np(Vd).T, Vo) < 1e-5
+
+
+@pytest.mark.parametrize("k,n,b,sym,offset", [(100, 45000, 20000, False, 0), (64, 30000, 30000, True, 0),
+                                              (37, 9000, 4000, False, 0), (128, 20000, 7000, True, 1)])
+def test_split_form_large_minibatches(otm, k, n, b, sym, offset):
+    """The split form with minibatches far larger than one chunk per CTA
+    (several chunks per step, the last one partial), up to a full-batch step,
+    a partial last minibatch, k = 37 and views that are not 16-byte aligned
+    (scalar copies), against the oracle's run at the FP32 tolerance."""
+    g = np.random.default_rng(k + b)
+    Ys = [(g.standard_normal((n, k)) * 0.05 + 0.1 * g.standard_normal(k)).astype(np.float32)
+          for _ in range(3)]
+    if sym:
+        Ys = [Ys[0]] * 3
+    yb = np.stack([Y.astype(np.float64).mean(axis=0) for Y in Ys])
+    epochs = 1
+    perm = synth.epoch_permutations(k + 5, n, epochs)
+    V0 = synth.haar_orthonormal(k + 6, k)
+    views = []
+    for Y in (Ys[:1] if sym else Ys):
+        buf = torch.zeros(n * k + offset, device="cuda", dtype=torch.float32)
+        buf[offset:] = _dev(Y).reshape(-1)
+        views.append(buf[offset:].view(n, k))
+    if sym:
+        views = views * 3
+    Vd = _dev(V0.T.copy())
+    try:
+        otm.sgd_set_form(otm.SGD_FORM_SPLIT)
+        otm.sgd_run(Vd, *views, _dev(yb), _dev(perm), epochs, b, 5e-2, 1.0, 1.0)
+        torch.cuda.synchronize()
+    finally:
+        otm.sgd_set_form(otm.SGD_FORM_AUTO)
+    Vo, _ = ostgd.sgd_run(V0, *Ys, tuple(yb), perm, b, 5e-2, 1.0, 1.0, gemm=True)
+    assert rel(to_np(Vd).T, Vo) < 1e-5
+
