@@ -1358,6 +1358,7 @@ def run_lda(args, rank, world, local_rank):
                    "beta0": c["beta0"], "theta": c["theta"],
                    "l2": "flushed between timed steps (256 MiB write); inputs larger than L2",
                    "sgd_form": args.sgd_form,
+                   "sgd_split_shape": "%d clusters x %d CTAs" % otm.sgd_split_shape(k, b, True),
                    "parallelism": "replicas" if world > 1 else "single",
                    "host_generation_s": round(host["gen_s"], 1),
                    "corpus_from_cache": host["cached"]},

@@ -326,6 +326,15 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
  */
 otm_status otm_sgd_set_form(int form);
 
+/*
+ * otm_sgd_split_shape -- the launch shape the split form (form 3) takes for
+ * k components, minibatch b and symmetric (sym != 0) or three distinct views:
+ * *clusters thread-block clusters of *cluster_size CTAs, or 0 and 0 where the
+ * split form does not apply on the current device.  No paper counterpart (a
+ * diagnostic of the performance choice above).  OTM_EINVAL on a null pointer.
+ */
+otm_status otm_sgd_split_shape(int64_t k, int64_t b, int sym, int* clusters, int* cluster_size);
+
 /* ------------------------------------------------------------------------ */
 /* Precision form of the STGD (not in the paper: BF16 / FP8 tensor cores)     */
 /* ------------------------------------------------------------------------ */

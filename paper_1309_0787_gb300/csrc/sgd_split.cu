@@ -2,9 +2,11 @@
 // (Section 3.2, Lemma 3 / Eq. (16)), FP32, "split" form: ONE launch of C
 // thread-block clusters of CL CTAs that runs every step of the schedule.
 //
-// The k components are cut into C blocks of Nc (Nc <= CL) and every minibatch
-// into CL slices of Sb samples.  Cluster c owns block c; CTA s of the cluster
-// owns slice s and, for the update, component i = c Nc + s.  Per step:
+// The k components are cut into C blocks of Nc and every minibatch into CL
+// slices of Sb samples.  Cluster c owns block c; CTA s of the cluster owns
+// slice s and, for the update, components i = c Nc + s, c Nc + s + CL, ...
+// (one or two).  C is the largest count whose clusters can all be resident.
+// Per step:
 //   every CTA, for its slice and its cluster's block (in chunks of SC samples):
 //     A_A = Y_A V_c, A_B = Y_B V_c          (samples x block components)
 //     B   = c1 A_A o A_B - c2 (a_B o A_A + a_A o A_B)
@@ -182,8 +184,6 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
   float* hs = sm + L.off_h;
   float* red = sm + L.off_red;
   const int c0 = cb * Nc;                          // first component of the block
-  const int own = c0 + sl;                         // component owned by this CTA
-  const bool owner = sl < Nc && own < k;
   const int nchunk = (Sb + SC - 1) / SC;
 
   for (int r = tid; r < ld; r += ST) {
@@ -342,12 +342,13 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     if (tid < Nc4) part[(size_t)tid * kpp + kp] = ssum;
     cluster.sync();
 
-    // owner: sum the partial columns of component `own`, Gram term, update
+    // owners: sum the partial columns of each owned component, Gram term, update
     float* Vnext = a.Vg + (size_t)(par ^ 1) * kp * ld;
     float* Mnext = a.Mg + (size_t)(par ^ 1) * 2 * kp;
-    if (owner) {
-      const float beta = (float)a.beta0 / sqrtf((float)(s + 1));
-      const float inv_b = 1.f / (float)beff;
+    const float beta = (float)a.beta0 / sqrtf((float)(s + 1));
+    const float inv_b = 1.f / (float)beff;
+    for (int lc = sl; lc < Nc && c0 + lc < k; lc += CL) {
+      const int own = c0 + lc;
       // the CL partial columns (and sums) through distributed shared memory: all
       // loads issued before the Gram term, which needs only V
       const int r = tid;  // coordinate (r == kp: the sum of A_A o A_B)
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
         float pv[SP_CLMAX];
 #pragma unroll
         for (int c = 0; c < SP_CLMAX; ++c)
-          if (c < CL) pv[c] = *cluster.map_shared_rank(part + (size_t)sl * kpp + r, c);
+          if (c < CL) pv[c] = *cluster.map_shared_rank(part + (size_t)lc * kpp + r, c);
 #pragma unroll
         for (int c = 0; c < SP_CLMAX; ++c)
           if (c < CL) dsum += pv[c];
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
       if (r < kp) {
         float gg = 0.f;
         for (int j = 0; j < k; ++j) gg = fmaf(hs[j], Vs[(size_t)j * ld + r], gg);
-        const float ai = aA[sl], bi = aB[sl];
+        const float ai = aA[lc], bi = aB[lc];
         const float gdata = dsum * inv_b + ybC[r] * (a.c3 * ai * bi - a.c2 * s_si * inv_b);
         const float v = r < k ? Vs[(size_t)own * ld + r] - beta * (a.kappa * gg - gdata) : 0.f;
         Vnext[(size_t)own * ld + r] = v;
@@ -412,13 +413,14 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
         Mnext[own] = tx;
         Mnext[kp + own] = ty;
       }
+      __syncthreads();  // hs, s_si and red are reused by the next owned component
     }
     __threadfence();
     if (!cluster_grid_barrier(cluster, a.bar, a.flag, &s_ok)) {
       // the whole cluster leaves here together; its peers read rank 0's flag
       // before the final cluster barrier
-      if (owner)
-        for (int r = tid; r < k; r += ST) a.V[(int64_t)own * k + r] = __int_as_float(0x7fc00000);
+      for (int lc = sl; lc < Nc && c0 + lc < k; lc += CL)
+        for (int r = tid; r < k; r += ST) a.V[(int64_t)(c0 + lc) * k + r] = __int_as_float(0x7fc00000);
       cp_wait_all();
       cluster.sync();
       return;
@@ -465,26 +467,25 @@ int split_smem_optin() {
   return v;
 }
 
-// Launch shape: cluster size CL, components per block Nc (<= CL), samples per
-// CTA and step Sb, chunk SC; false if none fits.
+// Launch shape: cluster size CL, C clusters, components per block Nc (at most
+// two per CTA), samples per CTA and step Sb, chunk SC.
 struct SplitPlan {
   int CL, Nc, C, Sb, SC;
   size_t smem;
 };
 
-bool split_plan(int64_t k, int64_t b, bool sym, int CL, SplitPlan* out) {
-  if (k < 1 || k > SP_KMAX || b < 1) return false;
-  const int C = (int)((k + CL - 1) / CL);  // blocks
-  const int Nc = (int)((k + C - 1) / C);   // components per block (<= CL)
-  if (C * CL > split_sms()) return false;
+bool split_plan(int64_t k, int64_t b, bool sym, int CL, int C, SplitPlan* out) {
+  if (k < 1 || k > SP_KMAX || b < 1 || C < 1) return false;
+  const int Nc = (int)((k + C - 1) / C);
+  if (Nc > 2 * CL || C * CL > split_sms()) return false;
+  const int kq = (int)((k + 3) & ~3) / 4;
+  if (Nc * kq > 2 * ST) return false;  // each thread accumulates at most two float4 outputs
   const int Sb = (int)((b + CL - 1) / CL);
   for (int SC : {64, 32, 16}) {
     const int sc = std::min(SC, std::max(Sb, 1));
     const SLayout L = s_layout((int)k, sym, Nc, sc);
     const size_t bytes = L.total * sizeof(float);
     if (bytes + 1024 <= (size_t)split_smem_optin()) {
-      // each thread accumulates at most two float4 partial outputs
-      if (Nc * (L.kp / 4) > 2 * ST) return false;
       *out = {CL, Nc, C, Sb, sc, bytes};
       return true;
     }
@@ -511,10 +512,10 @@ cudaLaunchConfig_t split_cfg(const SplitPlan& P, cudaStream_t st, cudaLaunchAttr
   return cfg;
 }
 
-// Whether all C clusters of plan P can be resident at once (so that the grid
-// barrier can complete); sets the kernel's attributes.
+// Sets the kernel's launch attributes for plan P (before every launch or
+// occupancy query: plans of different shared-memory size share the kernel).
 template <bool SYM>
-bool split_fits(const SplitPlan& P) {
+bool split_attrs(const SplitPlan& P) {
   auto kern = sgd_split_kernel<SYM>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem) !=
       cudaSuccess) {
@@ -526,56 +527,73 @@ bool split_fits(const SplitPlan& P) {
     cudaGetLastError();
     return false;
   }
+  return true;
+}
+
+// Clusters of plan P that can be resident at once.
+template <bool SYM>
+int split_resident(const SplitPlan& P) {
+  if (!split_attrs<SYM>(P)) return 0;
   cudaLaunchAttribute attr[2];
   cudaLaunchConfig_t cfg = split_cfg<SYM>(P, nullptr, attr, false);
   int n = 0;
-  const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (const void*)kern, &cfg);
-  if (e != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)sgd_split_kernel<SYM>, &cfg) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return n >= P.C;
+  return n;
 }
 
-// The plan for (k, b, views), cached per (k, b, sym): 8-CTA clusters, else 16.
+// The plan for (k, b, views), cached per (device, k, b, sym): for 8- and
+// 16-CTA clusters the largest C whose clusters are all resident at once; of
+// those, the one with more CTAs (the smaller cluster on a tie).
 bool split_choose(int64_t k, int64_t b, bool sym, SplitPlan* out) {
   struct Entry {
+    int dev;
     int64_t k, b;
     bool sym, ok;
     SplitPlan P;
   };
-  static Entry cache[32];
+  static Entry cache[64];
   static int ncache = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
   for (int i = 0; i < ncache; ++i)
-    if (cache[i].k == k && cache[i].b == b && cache[i].sym == sym) {
+    if (cache[i].dev == dev && cache[i].k == k && cache[i].b == b && cache[i].sym == sym) {
       *out = cache[i].P;
       return cache[i].ok;
     }
   bool ok = false;
-  SplitPlan P{};
+  SplitPlan best{};
   for (int CL : {8, 16}) {
-    SplitPlan Q;
-    if (!split_plan(k, b, sym, CL, &Q)) continue;
-    if (sym ? split_fits<true>(Q) : split_fits<false>(Q)) {
-      P = Q;
-      ok = true;
-      break;
+    for (int C = (int)((k + CL - 1) / CL); C >= 1; --C) {
+      if ((k + C - 1) / C > 2 * CL) break;  // more than two components per CTA
+      SplitPlan Q;
+      if (!split_plan(k, b, sym, CL, C, &Q)) continue;
+      const int res = sym ? split_resident<true>(Q) : split_resident<false>(Q);
+      if (res >= C) {
+        if (!ok || C * CL > best.C * best.CL) best = Q;
+        ok = true;
+        break;
+      }
     }
   }
-  if (ncache < 32) cache[ncache++] = {k, b, sym, ok, P};
-  *out = P;
+  if (ncache < 64) cache[ncache++] = {dev, k, b, sym, ok, best};
+  *out = best;
   return ok;
 }
 
 template <bool SYM>
 otm_status launch_split(SplitArgs& args, const SplitPlan& P, cudaStream_t st) {
   auto kern = sgd_split_kernel<SYM>;
+  if (!split_attrs<SYM>(P))
+    return set_error(OTM_ECUDA, "sgd split form: cannot set the kernel's launch attributes");
   cudaLaunchAttribute attr[2];
   cudaLaunchConfig_t cfg = split_cfg<SYM>(P, st, attr, true);
   cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
   if (e != cudaSuccess) {
     // the cooperative attribute is not accepted with clusters here: residency
-    // was checked by split_fits, every wait is bounded
+    // was checked by split_choose, every wait is bounded
     cudaGetLastError();
     cfg = split_cfg<SYM>(P, st, attr, false);
     OTM_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
@@ -650,3 +668,20 @@ otm_status sgd_split_run(float* V, const float* YA, const float* YB, const float
 }
 
 }  // namespace otm
+
+using namespace otm;
+
+extern "C" otm_status otm_sgd_split_shape(int64_t k, int64_t b, int sym, int* clusters,
+                                          int* cluster_size) {
+  clear_error();
+  OTM_REQUIRE(clusters && cluster_size, "otm_sgd_split_shape: null pointer");
+  SplitPlan P;
+  if (!split_choose(k, b, sym != 0, &P)) {
+    *clusters = 0;
+    *cluster_size = 0;
+    return OTM_OK;
+  }
+  *clusters = P.C;
+  *cluster_size = P.CL;
+  return OTM_OK;
+}

@@ -89,6 +89,8 @@ _SIGS = {
                      c_vp],
     "otm_sgd_workspace": [c_i64, c_i64],
     "otm_sgd_set_form": [ctypes.c_int],
+    "otm_sgd_split_shape": [c_i64, c_i64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int)],
     "otm_sgd_run": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64, c_i64, c_f64,
                     c_f64, c_f64, c_i64, c_vp, c_vp, c_sz, c_vp],
     "otm_quantize_samples": [c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp, c_vp],
@@ -383,6 +385,15 @@ SGD_FORM_AUTO, SGD_FORM_CLUSTER, SGD_FORM_GRID, SGD_FORM_SPLIT = 0, 1, 2, 3
 def sgd_set_form(form: int) -> None:
     """otm_sgd_set_form: which FP32 kernel sgd_step / sgd_run use (process-wide)."""
     _check(_lib.otm_sgd_set_form(int(form)))
+
+
+def sgd_split_shape(k: int, b: int, sym: bool):
+    """(clusters, CTAs per cluster) of the split form for k, b and the views, or
+    (0, 0) where it does not apply on the current device."""
+    c, cl = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.otm_sgd_split_shape(int(k), int(b), int(bool(sym)), ctypes.byref(c),
+                                    ctypes.byref(cl)))
+    return c.value, cl.value
 
 
 def sgd_step(V, YA, YB, YC, ybar3, theta: float, beta: float, alpha0: float):
