@@ -447,7 +447,19 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 BATCHED = dict(ks=(16, 32, 64, 128, 256), b_exp=(6, 12), pool=4, epochs=8, sigma=1e-2, beta0=5e-3,
                theta=1.0, seed=0)
-BF16_PEAK_TFLOPS = 1891.5   # MEASURED_PEAKS.json bf16_tflops (burst; cuBLAS 8192^3)
+def _measured_peaks():
+    """HBM copy bandwidth (GB/s) and BF16 GEMM throughput (TFLOP/s) measured on
+    the GB300s (MEASURED_PEAKS.json beside this file), else the values
+    it held when this file was written."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 6789.0, 1888.6
+
+
+HBM_PEAK_GBS, BF16_PEAK_TFLOPS = _measured_peaks()
 
 
 def run_batched(args):
@@ -1386,6 +1398,59 @@ def run_lda(args, rank, world, local_rank):
     return line
 
 
+def run_projection(args):
+    """The projection y_t = W^T c_t / l_t (Section 3.1) alone, on the default
+    line's corpus with a random W (d x k, float32): the gather SpMM's time and
+    its achieved bandwidth on the algorithmic HBM bytes 8 nnz (column index and
+    count) + 4 (n + 1) (row pointers) + 4 n (row scales) + 4 k n (the output
+    rows), against the measured copy bandwidth; the W-row gathers (4 k nnz
+    bytes) are served by the L2 and counted apart.  L2 flushed before each call."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    c = dict(LDA)
+    dev = torch.device("cuda", 0)
+    host = lda_inputs(c, 0)
+    X = host["X"]
+    n, d = X.shape
+    k = c["k"]
+    Xd = otm.DeviceCSR.from_host(X, dev)
+    W = torch.from_numpy(synth.gaussian(c["seed"] + 9, d, k)).to(dev)
+    invlen = otm.topic_moments(Xd)["row_invlen"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        otm.project(Xd, W, invlen)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        otm.project(Xd, W, invlen)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    t = statistics.median(ms) / 1e3
+    nnz = int(X.nnz)
+    alg = 8 * nnz + 4 * (n + 1) + 4 * n + 4 * k * n
+    gathers = 4 * k * nnz
+    return {"metric": "projection throughput (documents/s), gather SpMM", "value": n / t,
+            "unit": "documents/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "projection_300000x100000_k100", "docs": n, "vocabulary": d,
+                       "k": k, "nnz": nnz, "l2": "flushed before each call (256 MiB write)"},
+            "roofline": {"kernel": "spmm_gather_v4_kernel", "bound": "hbm",
+                         "achieved": alg / t / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                         "frac": alg / t / 1e9 / HBM_PEAK_GBS, "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                         "algorithmic_bytes_per_launch": alg},
+            "l2_gather_bytes_per_launch": gathers, "l2_gather_gbs": gathers / t / 1e9,
+            "gpu_launches": args.steps, "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1394,7 +1459,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="lda",
-                    choices=["lda", "mmsb", "batched", "warmstart", "whitening"],
+                    choices=["lda", "mmsb", "batched", "warmstart", "whitening", "projection"],
                     help="lda: the default line (300,000-document LDA corpus, whole path); "
                          "mmsb: the community-model pipeline; batched: the batched form; "
                          "warmstart: time to 1e-3 with the learned start; whitening: both "
@@ -1416,6 +1481,8 @@ def main():
         line = run_warmstart(args) if rank == 0 else None
     elif args.workload == "whitening":
         line = run_whitening(args) if rank == 0 else None
+    elif args.workload == "projection":
+        line = run_projection(args) if rank == 0 else None
     elif args.impl == "reference":
         line = (run_lda_reference(args, rank, world) if args.workload == "lda"
                 else run_reference(args, rank, world))

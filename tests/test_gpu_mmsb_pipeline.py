@@ -64,7 +64,8 @@ def run():
            "Pi_hat": to_np(Pi_hat).astype(np.float64), "pvalues": to_np(val["pvalues"]),
            "scores": to_np(val["scores"])}
     return {"g": g, "S_pairs": S_pairs, "S_w": S_w, "perm": perm, "V0": V0,
-            "truth": g["Pi"]["X"].T.astype(np.float64), "gpu": gpu}
+            # the memberships exactly as the GPU received them (float32)
+            "truth": g["Pi"]["X"].T.astype(np.float32).astype(np.float64), "gpu": gpu}
 
 
 def _colwise(a, b):
