@@ -1077,13 +1077,22 @@ def lda_oracle_sample(c, host, fracs, stgd_steps, project_frac=1.0):
     n = X.shape[0]
     k, a0 = c["k"], c["k"] * c["alpha_i"]
     S = host["S"].astype(np.float64)
-    t_wh, wh = [], None
+    t_wh, wh, passed = [], None, []
     for f in fracs:
         Xf = X.row_slice(0, max(1, int(round(f * n))))
         t0 = time.perf_counter()
-        wh = ow.range_finder_whiten(lambda Z, Xf=Xf: om.topic_second_moment_apply(Xf, Z, a0), S,
-                                    k, c["power_iters"])
+        try:
+            wh = ow.range_finder_whiten(lambda Z, Xf=Xf: om.topic_second_moment_apply(Xf, Z, a0),
+                                        S, k, c["power_iters"])
+            passed.append(True)
+        except ow.NotPositiveDefinite:
+            # a small share of the documents may leave fewer than k positive
+            # eigenvalues; the check is the whitening's last step, so the time
+            # is that of the whole whitening
+            passed.append(False)
         t_wh.append(time.perf_counter() - t0)
+    if wh is None:   # stand-ins of the same shapes for the timing of the later stages
+        wh = {"W": S[:, :k].copy(), "Wplus": S[:, :k].copy()}
     if len(fracs) > 1:
         slope = (t_wh[-1] - t_wh[0]) / (fracs[-1] - fracs[0])
         whiten_s = max(t_wh[-1] + slope * (1.0 - fracs[-1]), t_wh[-1])
@@ -1106,7 +1115,8 @@ def lda_oracle_sample(c, host, fracs, stgd_steps, project_frac=1.0):
     t0 = time.perf_counter()
     opost.unwhiten(V, wh["Wplus"], c["theta"], True)
     post_s = time.perf_counter() - t0
-    return {"whiten_s": whiten_s, "whiten_sample_s": t_wh, "project_means_s": project_s,
+    return {"whiten_s": whiten_s, "whiten_sample_s": t_wh, "whiten_sample_positive": passed,
+            "project_means_s": project_s,
             "stgd_s": stgd_s, "stgd_steps_run": steps, "stgd_steps_total": total,
             "unwhiten_s": post_s}
 
@@ -1391,11 +1401,75 @@ def run_lda(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    print(f"bench: timed {args.steps} steps, {1e3 * t_max / args.steps:.2f} ms/step",
+          file=sys.stderr, flush=True)
     line["precisions"] = lda_precisions(otm, torch, path, c, host, statistics.mean(sgd_ms))
+    print("bench: precision forms done", file=sys.stderr, flush=True)
     line["time_to_1e-3"] = time_to_target(otm, torch, dev)
+    print("bench: time to 1e-3 done", file=sys.stderr, flush=True)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = lda_cpu_baseline(c, host)
     return line
+
+
+def run_stgd(args):
+    """The STGD launch alone (one persistent launch = the 20 epochs of the default
+    line, 5,860 steps) on the default line's whitened samples, in the FP32 form
+    --sgd-form selects: time per launch, samples/s, algorithmic FP32 throughput
+    (4 k^2 per sample + 4 k^3 per step) against the derived FP32 peak.  Whitening
+    and projection run once, untimed; L2 flushed before each launch."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    c = dict(LDA)
+    dev = torch.device("cuda", 0)
+    host = lda_inputs(c, 0)
+    path = LdaPath(otm, torch, c, host, dev)
+    otm.sgd_set_form(sgd_form_code(otm, args.sgd_form))
+    wh, Y, yb3 = path.front()
+    n, k, b, ep = Y.shape[0], c["k"], c["b"], c["epochs"]
+    a0 = k * c["alpha_i"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one():
+        V = path.V0t.clone()
+        otm.sgd_run(V, Y, Y, Y, yb3, path.perm, ep, b, c["beta0"], c["theta"], a0)
+        return V
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    otm.sgd_set_form(otm.SGD_FORM_AUTO)
+    t = statistics.median(ms) / 1e3
+    flops = sym_sgd_flops(n, b, k, ep)
+    nsteps = ((n + b - 1) // b) * ep
+    return {"metric": "whitened-sample SGD throughput (samples/s), STGD launch alone",
+            "value": n * ep / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "stgd_lda_300000_k100_b1024_fp32", "docs": n, "k": k,
+                       "minibatch": b, "epochs": ep, "sgd_steps": nsteps,
+                       "sgd_form": args.sgd_form,
+                       "sgd_split_shape": "%d clusters x %d CTAs" % otm.sgd_split_shape(k, b, True),
+                       "l2": "flushed before each launch (256 MiB write)"},
+            "us_per_sgd_step": 1e6 * t / nsteps,
+            "roofline": {"kernel": SGD_KERNEL_NAME[args.sgd_form], "bound": "alu",
+                         "achieved": flops / t / 1e12, "peak": FP32_FMA_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP32_FMA_PEAK_TFLOPS,
+                         "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                         "algorithmic_flops_per_launch": flops},
+            "gpu_launches": args.steps, "clocks": clocks}
 
 
 def run_projection(args):
@@ -1459,7 +1533,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="lda",
-                    choices=["lda", "mmsb", "batched", "warmstart", "whitening", "projection"],
+                    choices=["lda", "mmsb", "batched", "warmstart", "whitening", "projection",
+                             "stgd"],
                     help="lda: the default line (300,000-document LDA corpus, whole path); "
                          "mmsb: the community-model pipeline; batched: the batched form; "
                          "warmstart: time to 1e-3 with the learned start; whitening: both "
@@ -1483,6 +1558,8 @@ def main():
         line = run_whitening(args) if rank == 0 else None
     elif args.workload == "projection":
         line = run_projection(args) if rank == 0 else None
+    elif args.workload == "stgd":
+        line = run_stgd(args) if rank == 0 else None
     elif args.impl == "reference":
         line = (run_lda_reference(args, rank, world) if args.workload == "lda"
                 else run_reference(args, rank, world))
