@@ -335,6 +335,38 @@ otm_status otm_sgd_set_form(int form);
  */
 otm_status otm_sgd_split_shape(int64_t k, int64_t b, int sym, int* clusters, int* cluster_size);
 
+/*
+ * otm_sgd_run_topic_exact -- STGD for the topic model on the whole third
+ * moment of Section 2.1, Eq. (3) (its self-token terms kept), whitened by W,
+ * instead of the sample tensor of Section 3.2; the implicit form of Lemma 3:
+ *   G = kappa V ((V^T V) o (V^T V)) - T(V, V, I),   V <- V - beta_t G,
+ * where column i of T(V, V, I) is the minibatch mean over documents t of
+ *   c1 [s^2 y' - q y' - 2 s r + 2 z] / (l (l-1) (l-2))
+ *   - c2 ([s^2 - q] m + 2 mu [s y' - r]) / (l (l-1))
+ * plus c3 mu^2 m, with y' = W^T c_t, u = W v_i, s = <c_t, u>, q = sum_j c_j u_j^2,
+ * r = W^T (c_t o u), z = W^T (c_t o u o u), m = W^T M1, mu = <m, v_i>, l the
+ * document's length (a term is dropped for documents shorter than its
+ * order).  The tensor is never formed: per minibatch the rows of W of its word
+ * occurrences are gathered, U = W_g V^T, the per-document sums and
+ * coefficients are formed, and the data term is W_g^T Coef + Y'^T A (FP32
+ * tiles, FP64 accumulation).
+ * X: the corpus (n documents x d words, CSR counts); W: d x k float32
+ * row-major; M1: d doubles (the first moment of Eq. (1)); V: k x k float32,
+ * component i contiguous, updated in place; perm: epochs x n int32 (NULL =
+ * identity order); minibatches of b documents, beta_t = beta0 / sqrt(t).
+ * nnz_b_max: the most word occurrences (CSR entries) any minibatch holds; a
+ * larger minibatch is not processed and makes the call return OTM_EINVAL.
+ * Snapshots as for otm_sgd_run.  1 <= k <= 128.
+ * Scratch: otm_sgd_topic_exact_workspace(k, b, nnz_b_max) bytes.  The host
+ * drives the steps (about ten launches each); synchronises the stream at the end.
+ */
+size_t otm_sgd_topic_exact_workspace(int64_t k, int64_t b, int64_t nnz_b_max);
+otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, const double* M1,
+                                   int64_t k, const int32_t* perm, int64_t epochs, int64_t b,
+                                   int64_t nnz_b_max, double beta0, double theta, double alpha0,
+                                   float* V_snap, int64_t snapshot_every, void* ws,
+                                   size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Precision form of the STGD (not in the paper: BF16 / FP8 tensor cores)     */
 /* ------------------------------------------------------------------------ */

@@ -33,13 +33,14 @@ Readings of the paper used here:
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 
 from .moments import as_sparse, coefficients
 
 __all__ = [
     "kappa", "whitened_tensor", "contract", "loss_explicit", "grad_explicit",
     "grad_implicit", "grad_implicit_gemm", "grad_implicit_topic_exact", "sgd_step", "sgd_run",
-    "steps_per_epoch",
+    "sgd_run_topic_exact", "steps_per_epoch",
 ]
 
 
@@ -235,3 +236,28 @@ def sgd_run(V0, YA, YB, YC, ybar3, perm: np.ndarray, b: int, beta0: float,
             if snapshot_every and t % snapshot_every == 0:
                 snaps.append(V.copy())
     return V, snaps
+
+
+def sgd_run_topic_exact(V0, X, W, M1, perm: np.ndarray, b: int, beta0: float, theta: float,
+                        alpha0: float, snapshot_every: int = 0):
+    """The STGD loop of sgd_run (same visiting order, minibatches, partial last
+    batch and beta_t = beta0/sqrt(t)) with the gradient of
+    grad_implicit_topic_exact: the minibatch is the count rows perm[e][s:s+b] of
+    X; an index outside [0, n) is an empty document."""
+    V = np.asarray(V0, dtype=np.float64).copy()
+    Xs = as_sparse(X)
+    n = Xs.shape[0]
+    Xz = sp.vstack([Xs, sp.csr_matrix((1, Xs.shape[1]))]).tocsr()  # row n: an empty document
+    snaps = []
+    t = 0
+    for order in perm:
+        for s in range(0, n, b):
+            idx = np.asarray(order[s:s + b], dtype=np.int64)
+            idx = np.where((idx >= 0) & (idx < n), idx, n)
+            t += 1
+            V = V - (beta0 / np.sqrt(t)) * grad_implicit_topic_exact(V, Xz[idx], W, M1, theta,
+                                                                     alpha0)
+            if snapshot_every and t % snapshot_every == 0:
+                snaps.append(V.copy())
+    return V, snaps
+

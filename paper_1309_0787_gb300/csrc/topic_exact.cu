@@ -1,0 +1,340 @@
+// STGD for the topic model with the whole third moment of Section 2.1, Eq. (3)
+// -- the self-token terms kept -- instead of the sample tensor of Section 3.2,
+// in the implicit form of Lemma 3: G = kappa V ((V^T V) o (V^T V)) - T(V, V, I),
+// T the minibatch estimate of M3(W, W, W) (per-document normalisation, as for
+// the moments), M1 the full-data first moment.  The tensor is never formed.
+//
+// For component v = v_i, document t with counts c_j over its distinct words j
+// (length l), u_j = W_j . v (W_j row j of the whitening), y' = W^T c:
+//   s = <y', v> = sum_j c_j u_j,   q = sum_j c_j u_j^2,   mu = <W^T M1, v>,
+//   T_t(v, v, I) = a y' + sum_j c_j u_j (b + g u_j) W_j + e m,   m = W^T M1,
+//   a = c1 (s^2 - q) / L3 - 2 c2 mu s / L2,    b = -2 c1 s / L3 + 2 c2 mu / L2,
+//   g = 2 c1 / L3,                             e = -c2 (s^2 - q) / L2,
+// L3 = l (l-1) (l-2) and L2 = l (l-1) (a term whose L is zero is dropped: a
+// document too short for a term adds nothing to it).  Over the minibatch of
+// b documents (its nnz word occurrences gathered into W_g, nnz x k):
+//   U     = W_g V^T                        (nnz x k; U[e, i] = W_j(e) . v_i)
+//   Coef  = c o U o (b_t(e) + g_t(e) U)     (elementwise, per occurrence)
+//   data  = (W_g^T Coef + Y'^T A) / b + m (sum_t e_t / b + c3 mu o mu)^T
+//   V    <- V - beta_t (kappa V ((V^T V) o (V^T V)) - data)
+// The two large products are FP32 tiles accumulated in FP64 (gemm_tn_f64acc).
+// One step is a short sequence of launches; the host drives the steps.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "otm_internal.cuh"
+
+namespace otm {
+namespace {
+
+constexpr int TE_KMAX = 128;
+
+// Per-step preparation (one block): mu_i = <m, v_i> and the transpose of V
+// (Vt[r][i] = v_i[r]) for the product U = W_g Vt.
+__global__ void __launch_bounds__(256) te_prep_kernel(const float* __restrict__ V, int k,
+                                                      const double* __restrict__ m,
+                                                      double* __restrict__ mu,
+                                                      float* __restrict__ Vt) {
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int i = idx / k, r = idx % k;
+    Vt[r * k + i] = V[idx];
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double acc = 0.0;
+    for (int r = 0; r < k; ++r) acc += m[r] * (double)V[i * k + r];
+    mu[i] = acc;
+  }
+}
+
+// Occurrences of each minibatch document (one thread per document) and their
+// exclusive prefix sums (one block, sequential over chunks of 1,024).  doc[t]
+// is the corpus row of minibatch position t (-1: outside the corpus, an empty
+// document).  *flag |= 1 when the minibatch holds more than cap occurrences.
+__global__ void __launch_bounds__(1024) te_offsets_kernel(const int32_t* __restrict__ row_ptr,
+                                                          const int32_t* __restrict__ doc,
+                                                          int64_t nb, int64_t cap,
+                                                          int64_t* __restrict__ off,
+                                                          int* __restrict__ flag) {
+  __shared__ int64_t part[1024];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t t = base + threadIdx.x;
+    int64_t c = 0;
+    if (t < nb && doc[t] >= 0) c = row_ptr[doc[t] + 1] - row_ptr[doc[t]];
+    part[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan
+      const int64_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    if (t < nb) off[t] = carry + part[threadIdx.x] - c;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    off[nb] = carry;
+    if (carry > cap) atomicOr(flag, 1);
+  }
+}
+
+// One warp per minibatch document: its occurrences' rows of W into W_g and
+// their counts into cnt, y'_t = W^T c_t into Yp (FP32 sums), l_t into len.
+// Writes nothing past cap occurrences.
+__global__ void __launch_bounds__(256) te_gather_kernel(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const float* __restrict__ val, const int32_t* __restrict__ doc, int64_t nb,
+    const float* __restrict__ W, int k, const int64_t* __restrict__ off, int64_t cap,
+    float* __restrict__ Wg, float* __restrict__ cnt, float* __restrict__ Yp,
+    float* __restrict__ len) {
+  const int lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (t >= nb) return;
+  float acc[TE_KMAX / 32];
+#pragma unroll
+  for (int q = 0; q < TE_KMAX / 32; ++q) acc[q] = 0.f;
+  float l = 0.f;
+  if (doc[t] >= 0) {
+    const int32_t e0 = row_ptr[doc[t]], e1 = row_ptr[doc[t] + 1];
+    const int64_t o = off[t];
+    for (int32_t e = e0; e < e1; ++e) {
+      const int32_t j = col[e];
+      const float c = val[e];
+      const int64_t g = o + (e - e0);
+      l += c;
+      const bool keep = g < cap;
+      if (keep && lane == 0) cnt[g] = c;
+#pragma unroll
+      for (int q = 0; q < TE_KMAX / 32; ++q) {
+        const int r = lane + 32 * q;
+        if (r < k) {
+          const float w = W[(int64_t)j * k + r];
+          acc[q] = fmaf(c, w, acc[q]);
+          if (keep) Wg[g * k + r] = w;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < TE_KMAX / 32; ++q) {
+    const int r = lane + 32 * q;
+    if (r < k) Yp[t * k + r] = acc[q];
+  }
+  if (lane == 0) len[t] = l;
+}
+
+// One block per minibatch document, one thread per component: s, q, the
+// coefficients a (into A), e (summed into esum, FP64), and U -> Coef in place.
+__global__ void __launch_bounds__(TE_KMAX) te_coef_kernel(
+    const int64_t* __restrict__ off, int64_t cap, const float* __restrict__ cnt,
+    const float* __restrict__ Yp, const float* __restrict__ len, const float* __restrict__ V,
+    const double* __restrict__ mu, int k, float c1, float c2, float* __restrict__ U,
+    float* __restrict__ A, double* __restrict__ esum) {
+  const int64_t t = blockIdx.x;
+  const int i = threadIdx.x;
+  if (i >= k) return;
+  const int64_t e0 = off[t], e1 = min(off[t + 1], cap);
+  const double l = (double)len[t];
+  const double L2 = l >= 2.0 ? l * (l - 1.0) : 0.0;
+  const double L3 = l >= 3.0 ? l * (l - 1.0) * (l - 2.0) : 0.0;
+  // s = <y'_t, v_i> and q over the document's occurrences, summed in FP64: s^2 - q
+  // (the pairs of distinct tokens) cancels the self-pairs
+  double sd = 0.0;
+  for (int r = 0; r < k; ++r) sd += (double)Yp[t * k + r] * (double)V[i * k + r];
+  double qd = 0.0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const double u = U[e * k + i];
+    qd += (double)cnt[e] * u * u;
+  }
+  const double mi = mu[i];
+  const double i3 = L3 > 0.0 ? 1.0 / L3 : 0.0, i2 = L2 > 0.0 ? 1.0 / L2 : 0.0;
+  const double a = c1 * (sd * sd - qd) * i3 - 2.0 * c2 * mi * sd * i2;
+  const double bc = -2.0 * c1 * sd * i3 + 2.0 * c2 * mi * i2;
+  const double g = 2.0 * c1 * i3;
+  const double ec = -c2 * (sd * sd - qd) * i2;
+  A[t * k + i] = (float)a;
+  atomicAdd(&esum[i], ec);
+  const float bf = (float)bc, gf = (float)g;
+  for (int64_t e = e0; e < e1; ++e) {
+    const float u = U[e * k + i];
+    U[e * k + i] = cnt[e] * u * fmaf(gf, u, bf);
+  }
+}
+
+// One block per component i: the Gram term from V, the data term from the FP64
+// products (Gd[r][i], already divided by b) and the m terms, the update into Vn.
+__global__ void __launch_bounds__(TE_KMAX) te_finish_kernel(
+    const float* __restrict__ V, int k, const double* __restrict__ Gd,
+    const double* __restrict__ m, const double* __restrict__ mu,
+    const double* __restrict__ esum, double inv_b, float c3, float kappa, float beta,
+    float* __restrict__ Vn) {
+  __shared__ float h[TE_KMAX];
+  const int i = blockIdx.x, r = threadIdx.x;
+  if (r < k) {
+    float acc = 0.f;
+    for (int c = 0; c < k; ++c) acc = fmaf(V[r * k + c], V[i * k + c], acc);
+    h[r] = acc * acc;
+  }
+  __syncthreads();
+  if (r < k) {
+    float gg = 0.f;
+    for (int j = 0; j < k; ++j) gg = fmaf(h[j], V[j * k + r], gg);
+    const double data = Gd[(int64_t)r * k + i] + m[r] * (esum[i] * inv_b + (double)c3 * mu[i] * mu[i]);
+    Vn[i * k + r] = V[i * k + r] - beta * (kappa * gg - (float)data);
+  }
+}
+
+// Rows of W_g from this minibatch's last occurrence (off[nb], on the device) to
+// the capacity are zeroed, so that the products over all cap rows see only
+// this minibatch: U and Coef of those rows are then zero as well.
+__global__ void te_zero_tail_kernel(const int64_t* __restrict__ off_end, int64_t cap, int k,
+                                    float* __restrict__ Wg) {
+  const int64_t start = min(*off_end, cap) * k, end = cap * k;
+  for (int64_t i = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+       i += (int64_t)gridDim.x * blockDim.x)
+    Wg[i] = 0.f;
+}
+
+__global__ void te_docs_kernel(const int32_t* __restrict__ perm, int64_t n, int64_t pos0,
+                               int64_t nb, int32_t* __restrict__ doc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb) return;
+  const int64_t row = perm ? (int64_t)perm[pos0 + t] : pos0 + t;
+  doc[t] = (row >= 0 && row < n) ? (int32_t)row : -1;
+}
+
+struct TeWs {
+  int32_t* doc;
+  int64_t* off;
+  float *Wg, *cnt, *Yp, *len, *U, *A, *Vt, *Vn;
+  double *m, *mu, *esum, *Gd;
+  int* flag;
+};
+
+TeWs te_take(Workspace& w, int64_t k, int64_t b, int64_t cap) {
+  TeWs s;
+  s.doc = w.take<int32_t>(b);
+  s.off = w.take<int64_t>(b + 1);
+  s.Wg = w.take<float>((size_t)cap * k);
+  s.cnt = w.take<float>(cap);
+  s.Yp = w.take<float>((size_t)b * k);
+  s.len = w.take<float>(b);
+  s.U = w.take<float>((size_t)cap * k);
+  s.A = w.take<float>((size_t)b * k);
+  s.Vt = w.take<float>((size_t)k * k);
+  s.Vn = w.take<float>((size_t)k * k);
+  s.m = w.take<double>(k);
+  s.mu = w.take<double>(k);
+  s.esum = w.take<double>(k);
+  s.Gd = w.take<double>((size_t)k * k);
+  s.flag = w.take<int>(1);
+  return s;
+}
+
+// Gd = (W_g^T Coef + Y'^T A) / nb, FP32 tiles accumulated in FP64
+otm_status te_products(const TeWs& s, int64_t k, int64_t nb, int64_t cap, cudaStream_t st) {
+  OTM_TRY(gemm_tn_f64acc(s.Wg, s.U, cap, k, k, 1.0 / (double)nb, s.Gd, 0, st));
+  OTM_TRY(gemm_tn_f64acc(s.Yp, s.A, nb, k, k, 1.0 / (double)nb, s.Gd, 1, st));
+  return OTM_OK;
+}
+
+WorkspaceSize te_size(int64_t k, int64_t b, int64_t cap) {
+  WorkspaceSize w;
+  w.add<int32_t>(b).add<int64_t>(b + 1).add<float>((size_t)cap * k).add<float>(cap);
+  w.add<float>((size_t)b * k).add<float>(b).add<float>((size_t)cap * k).add<float>((size_t)b * k);
+  w.add<float>((size_t)k * k).add<float>((size_t)k * k);
+  w.add<double>(k).add<double>(k).add<double>(k).add<double>((size_t)k * k).add<int>(1);
+  return w;
+}
+
+}  // namespace
+}  // namespace otm
+
+using namespace otm;
+
+extern "C" {
+
+size_t otm_sgd_topic_exact_workspace(int64_t k, int64_t b, int64_t nnz_b_max) {
+  if (k < 1 || k > TE_KMAX || b < 1 || nnz_b_max < 0) return 0;
+  return te_size(k, b, nnz_b_max).bytes();
+}
+
+otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, const double* M1,
+                                   int64_t k, const int32_t* perm, int64_t epochs, int64_t b,
+                                   int64_t nnz_b_max, double beta0, double theta, double alpha0,
+                                   float* V_snap, int64_t snapshot_every, void* ws,
+                                   size_t ws_bytes, void* stream) {
+  clear_error();
+  OTM_TRY(check_csr(X, "otm_sgd_run_topic_exact: X"));
+  OTM_REQUIRE(V && W && M1, "otm_sgd_run_topic_exact: null pointer");
+  OTM_REQUIRE(k >= 1 && k <= TE_KMAX, "otm_sgd_run_topic_exact: k=%lld outside [1, %d]",
+              (long long)k, TE_KMAX);
+  OTM_REQUIRE(X->rows >= 1 && b >= 1 && epochs >= 0 && nnz_b_max >= 0,
+              "otm_sgd_run_topic_exact: need n >= 1, b >= 1, epochs >= 0, nnz_b_max >= 0");
+  OTM_REQUIRE(snapshot_every >= 0 && (snapshot_every == 0 || V_snap),
+              "otm_sgd_run_topic_exact: V_snap required for snapshots");
+  const int64_t n = X->rows, d = X->cols;
+  const int64_t nb_max = std::min(b, n);
+  OTM_REQUIRE(ws && ws_bytes >= te_size(k, nb_max, nnz_b_max).bytes(),
+              "otm_sgd_run_topic_exact: workspace too small (need %zu bytes)",
+              te_size(k, nb_max, nnz_b_max).bytes());
+  if (epochs == 0) return OTM_OK;
+  cudaStream_t st = as_stream(stream);
+  Workspace w(ws, ws_bytes);
+  const TeWs s = te_take(w, k, nb_max, nnz_b_max);
+  OTM_CHECK_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int), st));
+  OTM_TRY(vec_tn(M1, W, d, k, s.m, st));  // m = W^T M1
+  const double a0 = alpha0;
+  const float c1 = (float)((a0 + 1.0) * (a0 + 2.0) / 2.0), c2 = (float)(a0 * (a0 + 1.0) / 2.0),
+              c3 = (float)(a0 * a0), kappa = (float)(0.5 * (1.0 + theta));
+  const int64_t spe = (n + b - 1) / b;
+  int64_t t = 0;
+  for (int64_t e = 0; e < epochs; ++e)
+    for (int64_t jb = 0; jb < spe; ++jb) {
+      ++t;
+      const int64_t pos0 = jb * b, nb = std::min(b, n - pos0);
+      const float beta = (float)(beta0 / std::sqrt((double)t));
+      te_docs_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
+          perm ? perm + e * n : nullptr, n, pos0, nb, s.doc);
+      OTM_CHECK_LAUNCH();
+      te_prep_kernel<<<1, 256, 0, st>>>(V, (int)k, s.m, s.mu, s.Vt);
+      OTM_CHECK_LAUNCH();
+      te_offsets_kernel<<<1, 1024, 0, st>>>(X->row_ptr, s.doc, nb, nnz_b_max, s.off, s.flag);
+      OTM_CHECK_LAUNCH();
+      te_gather_kernel<<<(unsigned)((nb + 7) / 8), 256, 0, st>>>(
+          X->row_ptr, X->col, X->val, s.doc, nb, W, (int)k, s.off, nnz_b_max, s.Wg, s.cnt,
+          s.Yp, s.len);
+      OTM_CHECK_LAUNCH();
+      te_zero_tail_kernel<<<256, 256, 0, st>>>(s.off + nb, nnz_b_max, (int)k, s.Wg);
+      OTM_CHECK_LAUNCH();
+      // U = W_g V^T over every row the workspace holds (a minibatch past the
+      // capacity has set the flag; its occurrences beyond it are not read)
+      OTM_TRY(gemm_nn_small(s.Wg, nnz_b_max, k, s.Vt, k, s.U, nullptr, nullptr, 0.0, st));
+      OTM_CHECK_CUDA(cudaMemsetAsync(s.esum, 0, sizeof(double) * k, st));
+      te_coef_kernel<<<(unsigned)nb, TE_KMAX, 0, st>>>(s.off, nnz_b_max, s.cnt, s.Yp, s.len, V,
+                                                        s.mu, (int)k, c1, c2, s.U, s.A, s.esum);
+      OTM_CHECK_LAUNCH();
+      OTM_TRY(te_products(s, k, nb, nnz_b_max, st));
+      te_finish_kernel<<<(unsigned)k, TE_KMAX, 0, st>>>(V, (int)k, s.Gd, s.m, s.mu, s.esum,
+                                                        1.0 / (double)nb, c3, kappa, beta, s.Vn);
+      OTM_CHECK_LAUNCH();
+      OTM_CHECK_CUDA(cudaMemcpyAsync(V, s.Vn, sizeof(float) * k * k, cudaMemcpyDeviceToDevice, st));
+      if (snapshot_every > 0 && t % snapshot_every == 0)
+        OTM_CHECK_CUDA(cudaMemcpyAsync(V_snap + (t / snapshot_every - 1) * k * k, V,
+                                       sizeof(float) * k * k, cudaMemcpyDeviceToDevice, st));
+    }
+  int h = 0;
+  OTM_CHECK_CUDA(cudaMemcpyAsync(&h, s.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OTM_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (h)
+    return set_error(OTM_EINVAL, "otm_sgd_run_topic_exact: a minibatch holds more than "
+                                 "nnz_b_max = %lld word occurrences", (long long)nnz_b_max);
+  return OTM_OK;
+}
+
+}  // extern "C"

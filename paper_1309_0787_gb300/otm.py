@@ -10,6 +10,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -93,6 +95,9 @@ _SIGS = {
                             ctypes.POINTER(ctypes.c_int)],
     "otm_sgd_run": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64, c_i64, c_f64,
                     c_f64, c_f64, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_sgd_topic_exact_workspace": [c_i64, c_i64, c_i64],
+    "otm_sgd_run_topic_exact": [c_vp, _P, c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_f64,
+                                c_f64, c_f64, c_vp, c_i64, c_vp, c_sz, c_vp],
     "otm_quantize_samples": [c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp, c_vp],
     "otm_sgd_run_lp_workspace": [],
     "otm_sgd_run_lp": [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64,
@@ -437,6 +442,44 @@ def sgd_run(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, theta
 
 PREC_BF16 = 1
 PREC_FP8 = 2
+
+
+def sgd_run_topic_exact(V, X: DeviceCSR, W, M1, perm, epochs: int, b: int, beta0: float,
+                        theta: float, alpha0: float, snapshot_every: int = 0):
+    """otm_sgd_run_topic_exact: STGD on the whole third moment of Eq. (3) (the
+    self-token terms kept).  V: k x k (V[i] = component i), W: d x k float32,
+    M1: d float64, perm: epochs x n int32 or None.  The workspace is sized by
+    the most word occurrences any minibatch holds (from the row pointers)."""
+    k = V.shape[0]
+    n, d = X.shape
+    _need(V, torch.float32, (k, k), "V")
+    _need(W, torch.float32, (d, k), "W")
+    _need(M1, torch.float64, (d,), "M1")
+    if perm is not None:
+        _need(perm, torch.int32, (epochs, n), "perm")
+    # the workspace holds the largest minibatch's word occurrences (host-side
+    # sizing from the row pointers and the visiting order)
+    per = np.diff(X.row_ptr.cpu().numpy().astype(np.int64))
+    order = (perm.cpu().numpy().astype(np.int64) if perm is not None
+             else np.tile(np.arange(n, dtype=np.int64), (max(epochs, 1), 1)))
+    starts = np.arange(0, n, b)
+    ends = np.minimum(starts + b, n)
+    cap = 0
+    for e in range(epochs):
+        valid = (order[e] >= 0) & (order[e] < n)
+        cs = np.concatenate([[0], np.cumsum(np.where(valid, per[np.clip(order[e], 0, n - 1)], 0))])
+        cap = max(cap, int((cs[ends] - cs[starts]).max()))
+    steps = ((n + b - 1) // b) * epochs
+    snaps = None
+    if snapshot_every:
+        snaps = torch.empty(max(steps // snapshot_every, 1), k, k, dtype=torch.float32,
+                            device=V.device)
+    ws = _ws(_lib.otm_sgd_topic_exact_workspace(k, min(b, n), cap), V.device)
+    _check(_lib.otm_sgd_run_topic_exact(_ptr(V), X.ref(), _ptr(W), _ptr(M1), k, _ptr(perm),
+                                        int(epochs), int(b), cap, float(beta0), float(theta),
+                                        float(alpha0), _ptr(snaps), int(snapshot_every),
+                                        _ptr(ws), ws.numel(), _stream()))
+    return snaps
 
 
 def quantize_samples(Y, precision: int):

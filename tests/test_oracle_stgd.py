@@ -301,3 +301,30 @@ def test_exact_topic_gradient_in_gathered_gemm_form():
     G = stgd.kappa(theta) * V @ (Gm ** 2) - data
     np.testing.assert_allclose(G, stgd.grad_implicit_topic_exact(V, X, W, M1, theta, alpha0),
                                rtol=1e-11, atol=1e-11)
+
+
+def test_exact_topic_run_is_the_schedule_over_the_exact_gradient():
+    """sgd_run_topic_exact visits perm[e][s:s+b] with beta0/sqrt(t) and the
+    gradient of grad_implicit_topic_exact; an index outside [0, n) is an empty
+    document (it counts in the minibatch mean and adds nothing)."""
+    corp = synth.lda_corpus(31, 30, 20, 3, 0.3, 0.3, 6, poisson_len=True)
+    X = corp["X"]
+    g = np.random.default_rng(32)
+    W = g.standard_normal((20, 3))
+    M1 = om.topic_first_moment(X)
+    V0 = g.standard_normal((3, 3))
+    perm = synth.epoch_permutations(33, 30, 2).copy()
+    perm[1, 4] = -1
+    V, snaps = stgd.sgd_run_topic_exact(V0, X, W, M1, perm, 8, 0.05, 1.0, 0.7, snapshot_every=4)
+    Xs = om.as_sparse(X)
+    Vm, t = V0.copy(), 0
+    for e in range(2):
+        for s in range(0, 30, 8):
+            t += 1
+            idx = perm[e][s:s + 8]
+            rows = [Xs[i] if 0 <= i < 30 else None for i in idx]
+            Xb = om.as_sparse(np.vstack([r.toarray() if r is not None else np.zeros((1, 20))
+                                         for r in rows]))
+            Vm = Vm - 0.05 / np.sqrt(t) * stgd.grad_implicit_topic_exact(Vm, Xb, W, M1, 1.0, 0.7)
+    np.testing.assert_allclose(V, Vm, rtol=1e-12, atol=1e-12)
+    assert len(snaps) == 2
