@@ -38,7 +38,8 @@ import scipy.sparse as sp
 from .moments import as_sparse, coefficients
 
 __all__ = [
-    "kappa", "whitened_tensor", "contract", "loss_explicit", "grad_explicit",
+    "kappa", "whitened_tensor", "whitened_tensor_chunked", "contract", "contract_all",
+    "loss_explicit", "grad_explicit",
     "grad_implicit", "grad_implicit_gemm", "grad_implicit_topic_exact", "sgd_step", "sgd_run",
     "sgd_run_topic_exact", "steps_per_epoch",
 ]
@@ -61,6 +62,36 @@ def whitened_tensor(YA, YB, YC, ybar3, alpha0: float) -> np.ndarray:
     S = (np.einsum("ti,tj,k->ijk", YA, YB, ybC) + np.einsum("ti,j,tk->ijk", YA, ybB, YC)
          + np.einsum("i,tj,tk->ijk", ybA, YB, YC)) / n
     return c1 * E - c2 * S + c3 * np.einsum("i,j,k->ijk", ybA, ybB, ybC)
+
+
+def whitened_tensor_chunked(YA, YB, YC, ybar3, alpha0: float, chunk: int = 8192) -> np.ndarray:
+    """The tensor of whitened_tensor for many samples: the three sample sums of
+    Section 3.2 formed chunk by chunk as matrix products, e.g.
+    sum_t yA_t (x) yB_t (x) yC_t = reshape(YA^T [YB (row-wise x) YC]), and the mean
+    terms from the full-data sums; same definition, other summation order."""
+    YA, YB, YC = (np.asarray(Y, dtype=np.float64) for Y in (YA, YB, YC))
+    ybA, ybB, ybC = (np.asarray(y, dtype=np.float64) for y in ybar3)
+    n, k = YA.shape
+    c1, c2, c3 = coefficients(alpha0)
+    E = np.zeros((k, k * k))
+    for t0 in range(0, n, chunk):
+        a, bb, c = YA[t0:t0 + chunk], YB[t0:t0 + chunk], YC[t0:t0 + chunk]
+        E += a.T @ (bb[:, :, None] * c[:, None, :]).reshape(len(a), k * k)
+    E = E.reshape(k, k, k) / n
+    AB = YA.T @ YB / n
+    AC = YA.T @ YC / n
+    BC = YB.T @ YC / n
+    S = (np.einsum("ij,k->ijk", AB, ybC) + np.einsum("ik,j->ijk", AC, ybB)
+         + np.einsum("jk,i->ijk", BC, ybA))
+    return c1 * E - c2 * S + c3 * np.einsum("i,j,k->ijk", ybA, ybB, ybC)
+
+
+def contract_all(T: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """contract(T, V) as one matrix product: column i = T_(3)^T (v_i (x) v_i), with
+    T_(3) the k^2 x k unfolding of T and the Khatri-Rao columns v_i (x) v_i."""
+    k = T.shape[0]
+    KR = (V[:, None, :] * V[None, :, :]).reshape(k * k, V.shape[1])
+    return T.reshape(k * k, k).T @ KR
 
 
 def contract(T: np.ndarray, V: np.ndarray) -> np.ndarray:

@@ -314,7 +314,8 @@ otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, c
       OTM_CHECK_LAUNCH();
       // U = W_g V^T over every row the workspace holds (a minibatch past the
       // capacity has set the flag; its occurrences beyond it are not read)
-      OTM_TRY(gemm_nn_small(s.Wg, nnz_b_max, k, s.Vt, k, s.U, nullptr, nullptr, 0.0, st));
+      if (nnz_b_max > 0)
+        OTM_TRY(gemm_nn_small(s.Wg, nnz_b_max, k, s.Vt, k, s.U, nullptr, nullptr, 0.0, st));
       OTM_CHECK_CUDA(cudaMemsetAsync(s.esum, 0, sizeof(double) * k, st));
       te_coef_kernel<<<(unsigned)nb, TE_KMAX, 0, st>>>(s.off, nnz_b_max, s.cnt, s.Yp, s.len, V,
                                                         s.mu, (int)k, c1, c2, s.U, s.A, s.esum);

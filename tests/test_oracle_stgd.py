@@ -328,3 +328,20 @@ def test_exact_topic_run_is_the_schedule_over_the_exact_gradient():
             Vm = Vm - 0.05 / np.sqrt(t) * stgd.grad_implicit_topic_exact(Vm, Xb, W, M1, 1.0, 0.7)
     np.testing.assert_allclose(V, Vm, rtol=1e-12, atol=1e-12)
     assert len(snaps) == 2
+
+
+@pytest.mark.parametrize("views,alpha0", [(1, 1.0), (3, 0.6), (1, 0.0)])
+def test_chunked_tensor_and_matrix_contraction_equal_the_definitions(views, alpha0):
+    """whitened_tensor_chunked (matrix products over sample chunks) equals the
+    einsum definition; contract_all (Khatri-Rao form) equals contract."""
+    g = np.random.default_rng(41 + views)
+    Ys = [g.standard_normal((77, 6)) + s for s in (0.2, -0.3, 0.1)]
+    if views == 1:
+        Ys = [Ys[0]] * 3
+    yb = tuple(Y.mean(axis=0) for Y in Ys)
+    T = stgd.whitened_tensor(*Ys, yb, alpha0)
+    np.testing.assert_allclose(stgd.whitened_tensor_chunked(*Ys, yb, alpha0, chunk=10), T,
+                               rtol=1e-12, atol=1e-12)
+    V = g.standard_normal((6, 6))
+    np.testing.assert_allclose(stgd.contract_all(T, V), stgd.contract(T, V), rtol=1e-12,
+                               atol=1e-12)
