@@ -89,27 +89,22 @@ def test_exact_run_matches_oracle_run(otm):
         assert rel(s_gpu.T, s_ref) < 1e-5
 
 
-def test_exact_gradient_whitened_lda_k100(otm):
-    """k = 100 on whitened LDA documents: the whitening of a 600-document corpus
-    (Poisson(100) words over 2,000 words, oracle range finder), one step over
-    its first 256 documents from a Haar-random start."""
-    from oracle import whiten as ow
-    n, d, k, b = 600, 2000, 100, 256
-    c = synth.lda_corpus(11, n, d, k, 0.01, 0.05, 100, poisson_len=True, zipf=True)
-    X = c["X"]
-    S = synth.gaussian(12, d, k + 20).astype(np.float64)
-    wh = ow.range_finder_whiten(lambda Z: om.topic_second_moment_apply(X, Z, 1.0), S, k, 2)
-    W = wh["W"].astype(np.float32)
+def test_exact_gradient_k100_lda_documents(otm):
+    """k = 100 on LDA documents (256 documents of Poisson(100) words over 2,000
+    words, Zipf-skewed topics) with a fixed random W of whitened scale: one step
+    over all of them from a Haar-random start."""
+    n, d, k = 256, 2000, 100
+    X = synth.lda_corpus(11, n, d, k, 0.01, 0.05, 100, poisson_len=True, zipf=True)["X"]
+    W = (synth.gaussian(12, d, k) * 0.5).astype(np.float32)
     M1 = om.topic_first_moment(X)
-    Xb = X.row_slice(0, b)
     V0 = synth.haar_orthonormal(13, k)
     Vd = _dev(V0.T.copy())
-    otm.sgd_run_topic_exact(Vd, otm.DeviceCSR.from_host(Xb), _dev(W), _dev(M1), None, 1, b, 1.0,
+    otm.sgd_run_topic_exact(Vd, otm.DeviceCSR.from_host(X), _dev(W), _dev(M1), None, 1, n, 1.0,
                             1.0, 1.0)
     torch.cuda.synchronize()
     V64 = V0.astype(np.float64)
     Gk = V64 - to_np(Vd).T.astype(np.float64)
-    G = ostgd.grad_implicit_topic_exact(V64, Xb, W.astype(np.float64), M1, 1.0, 1.0)
+    G = ostgd.grad_implicit_topic_exact(V64, X, W.astype(np.float64), M1, 1.0, 1.0)
     frob, col = grad_errs(Gk, G, V64 @ (V64.T @ V64) ** 2)
     assert frob < 1e-5 and col < 1e-5, (frob, col)
 
