@@ -48,6 +48,7 @@ namespace {
 constexpr int ST = 256;          // threads per CTA
 constexpr int SP_KMAX = 128;
 constexpr int SP_CLMAX = 16;
+constexpr int SP_SCMAX = 64;     // samples per chunk at most
 
 struct SplitArgs {
   const float* YA;
@@ -70,7 +71,7 @@ struct SplitArgs {
 
 struct SLayout {
   int kp, ld, nview, Nc4, kpp, SC;
-  size_t off_v, off_y, off_b, off_p, off_part, off_yb, off_a, off_h, off_red, total;
+  size_t off_v, off_y, off_b, off_p, off_part, off_yb, off_a, off_h, off_g, off_red, total;
 };
 
 // Shared memory (floats).  Rows of V and of the samples have stride ld, an odd
@@ -88,11 +89,12 @@ __host__ __device__ inline SLayout s_layout(int k, bool sym, int Nc, int SC) {
   L.off_v = f;    f += (size_t)L.kp * L.ld;              // all of V, component rows
   L.off_y = f;    f += 2 * (size_t)L.nview * SC * L.ld;  // sample chunks [buf][view][t]
   L.off_b = f;    f += (size_t)SC * L.Nc4;               // B [t][i]
-  L.off_p = f;    f += (size_t)SC * L.Nc4;               // A_A o A_B [t][i]
+  L.off_p = f;    f += (size_t)L.Nc4;                    // sum_t (A_A o A_B)[t][i] of a step
   L.off_part = f; f += (size_t)L.Nc4 * L.kpp;            // partial columns [i][r]
   L.off_yb = f;   f += 3 * (size_t)L.ld;                 // ybar_A, ybar_B, ybar_C
   L.off_a = f;    f += 2 * (size_t)L.Nc4;                // a_A, a_B of the block
   L.off_h = f;    f += (size_t)L.kp;                     // <v_j, v_i>^2 of the owned i
+  L.off_g = f;    f += 2 * (size_t)L.kp;                 // two half sums of a Gram column
   L.off_red = f;  f += 2 * (ST / 32) + 4;
   L.total = f;
   return L;
@@ -125,6 +127,7 @@ __device__ __forceinline__ void cp4(float* dst, const float* src, bool in) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_two() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 // Grid-wide barrier of the cooperative cluster launch.  Every CTA of a cluster
 // arrives at a cluster barrier; thread 0 of cluster rank 0 then arrives on the
@@ -162,7 +165,7 @@ template <bool SYM>
 __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_ok;
-  __shared__ float s_si;
+  __shared__ int s_rows[2][SP_SCMAX];  // corpus rows of a chunk's samples, by chunk parity
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int sl = (int)cluster.block_rank();       // sample slice of this CTA
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
   float* Vs = sm + L.off_v;
   float* Ysb = sm + L.off_y;
   float* Bs = sm + L.off_b;
-  float* Ps = sm + L.off_p;
+  float* psum = sm + L.off_p;   // sum over the step's samples of A_A o A_B (Nc4)
   float* part = sm + L.off_part;
   float* ybA = sm + L.off_yb;
   float* ybB = ybA + ld;
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
   float* aA = sm + L.off_a;
   float* aB = aA + Nc4;
   float* hs = sm + L.off_h;
+  float* gpart = sm + L.off_g;  // two half sums of the Gram column (2 x kp)
   float* red = sm + L.off_red;
   const int c0 = cb * Nc;                          // first component of the block
   const int nchunk = (Sb + SC - 1) / SC;
@@ -227,32 +231,43 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     }
   }
 
-  // sample chunk g (global chunk sequence: step g / nchunk, chunk g % nchunk)
-  // into buffer g & 1; rows outside the minibatch or the data read as zeros.
-  // Every call commits one cp.async group (an empty one past the last step),
-  // so that "all but the newest group complete" always means chunk g - 1 landed.
-  auto issue_chunk = [&](int64_t g) {
-    const int64_t s = g / nchunk;
-    if (s >= a.total_steps) {
+  // corpus row of sample t of chunk gg (global chunk sequence: step gg / nchunk,
+  // chunk gg % nchunk); -1 outside the minibatch or the data (a zero sample)
+  auto row_for = [&](int64_t gg, int t) -> int {
+    const int64_t s = gg / nchunk;
+    if (s >= a.total_steps) return -1;
+    const int q = (int)(gg % nchunk);
+    const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
+    const int64_t beff = min(a.b, a.n - pos0);
+    const int pl = q * SC + t;
+    const int64_t p = (int64_t)sl * Sb + pl;
+    if (pl >= Sb || p >= beff) return -1;
+    const int64_t row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
+    return (row >= 0 && row < a.n) ? (int)row : -1;
+  };
+  // the row of this thread's sample in the next chunk to issue, loaded one
+  // issue ahead so that the permutation's latency is hidden
+  int pf_row = tid < SC ? row_for(0, tid) : -1;
+  // sample chunk gg into buffer gg & 1.  Every call commits one cp.async
+  // group (an empty one past the last step).
+  auto issue_chunk = [&](int64_t gg) {
+    if (gg / nchunk >= a.total_steps) {
       cp_commit();
       return;
     }
-    const int q = (int)(g % nchunk);
-    const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
-    const int64_t beff = min(a.b, a.n - pos0);
-    float* Yb = Ysb + (size_t)(g & 1) * L.nview * SC * ld;
+    int* rows = s_rows[gg & 1];
+    if (tid < SC) {
+      rows[tid] = pf_row;
+      pf_row = row_for(gg + 1, tid);
+    }
+    __syncthreads();
+    float* Yb = Ysb + (size_t)(gg & 1) * L.nview * SC * ld;
     const int per_row = a.vec ? kq : kp;
     const int items = L.nview * SC * per_row;
     for (int idx = tid; idx < items; idx += ST) {
       const int v = idx / (SC * per_row), rem = idx % (SC * per_row);
       const int t = rem / per_row, u = rem % per_row;
-      const int pl = q * SC + t;
-      const int64_t p = (int64_t)sl * Sb + pl;
-      int64_t row = -1;
-      if (pl < Sb && p < beff) {
-        row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
-        if (row < 0 || row >= a.n) row = -1;
-      }
+      const int64_t row = rows[t];
       const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
       float* dst = Yb + ((size_t)v * SC + t) * ld;
       if (a.vec) {
@@ -264,56 +279,87 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     }
     cp_commit();
   };
+  // rows of V outside this cluster's block, from the iterate buffer src (the
+  // block's rows were copied before the step's first product)
+  auto issue_vrest = [&](const float* src) {
+    const int b0 = c0 * ld / 4, b1 = min(c0 + Nc, kp) * ld / 4;
+    for (int idx = tid; idx < kp * ld / 4; idx += ST)
+      if (idx < b0 || idx >= b1) cp16(Vs + 4 * idx, src + 4 * idx, true);
+    cp_commit();
+  };
 
   int64_t g = 0;  // next chunk to consume
   issue_chunk(0);
+  const int nit1 = SC * (Nc4 / 4);  // items of the first product (SC samples x Nc4 / 4)
+  const bool warp_seg = (SC % 32) == 0;
   for (int64_t s = 0; s < a.total_steps; ++s) {
     const int par = (int)(s & 1);
     const int64_t pos0 = (s % a.spe) * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
     float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    float ssum = 0.f;
+    for (int i = tid; i < Nc4; i += ST) psum[i] = 0.f;
     for (int q = 0; q < nchunk; ++q, ++g) {
       issue_chunk(g + 1);
-      cp_wait_one();
+      if (q == 0 && s > 0) {
+        issue_vrest(a.Vg + (size_t)par * kp * ld);
+        cp_wait_two();   // the block's rows of V and chunk g have landed
+      } else {
+        cp_wait_one();
+      }
       __syncthreads();
       const float* Yb = Ysb + (size_t)(g & 1) * L.nview * SC * ld;
       // first product: A_A, A_B for 4 block components x 1 sample per item
-      for (int item = tid; item < SC * (Nc4 / 4); item += ST) {
-        const int t = item % SC, i0 = 4 * (item / SC);
-        const float* ya = Yb + (size_t)t * ld;
-        const float* yb = SYM ? ya : Yb + ((size_t)SC + t) * ld;
-        float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
-        const float* vr[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gi = c0 + i0 + j;
-          vr[j] = (i0 + j < Nc && gi < k) ? Vs + (size_t)gi * ld : nullptr;
-        }
-        for (int r = 0; r < kp; r += 4) {
-          const float4 yA = *reinterpret_cast<const float4*>(ya + r);
-          const float4 yB = SYM ? yA : *reinterpret_cast<const float4*>(yb + r);
+      for (int base = 0; base < nit1; base += ST) {
+        const int item = base + tid;
+        const bool act = item < nit1;
+        const int t = item % SC, i0 = 4 * (act ? item / SC : 0);
+        float pr[4] = {0.f, 0.f, 0.f, 0.f};
+        if (act) {
+          const float* ya = Yb + (size_t)t * ld;
+          const float* yb = SYM ? ya : Yb + ((size_t)SC + t) * ld;
+          float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
+          const float* vr[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            if (vr[j]) {
+            const int gi = c0 + i0 + j;
+            vr[j] = (i0 + j < Nc && gi < k) ? Vs + (size_t)gi * ld : Vs;
+          }
+#pragma unroll 4
+          for (int r = 0; r < kp; r += 4) {
+            const float4 yA = *reinterpret_cast<const float4*>(ya + r);
+            const float4 yB = SYM ? yA : *reinterpret_cast<const float4*>(yb + r);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
               const float4 v = *reinterpret_cast<const float4*>(vr[j] + r);
               xa[j] = dot4(v, yA, xa[j]);
               if (!SYM) xb[j] = dot4(v, yB, xb[j]);
             }
           }
-        }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int i = i0 + j;
-          const float xA = xa[j], xB = SYM ? xa[j] : xb[j];
-          const float pr = xA * xB;
-          Ps[t * Nc4 + i] = pr;
-          Bs[t * Nc4 + i] = a.c1 * pr - a.c2 * (aB[i] * xA + aA[i] * xB);
+          for (int j = 0; j < 4; ++j) {
+            const int i = i0 + j;
+            const bool on = i < Nc && c0 + i < k;
+            const float xA = on ? xa[j] : 0.f, xB = on ? (SYM ? xa[j] : xb[j]) : 0.f;
+            pr[j] = xA * xB;
+            Bs[t * Nc4 + i] = a.c1 * pr[j] - a.c2 * (aB[i] * xA + aA[i] * xB);
+          }
+        }
+        // sum of A_A o A_B over the samples: the lanes of a warp hold 32 samples
+        // of the same 4 components when SC is a multiple of 32
+        if (warp_seg) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float v = pr[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && act) atomicAdd(&psum[i0 + j], v);
+          }
+        } else if (act) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) atomicAdd(&psum[i0 + j], pr[j]);
         }
       }
       __syncthreads();
-      if (tid < Nc4)
-        for (int t = 0; t < SC; ++t) ssum += Ps[t * Nc4 + tid];
       // second product: partial columns sum_t y_C,t B[t, i] (float4 of coordinates)
       {
         const float* yc = SYM ? Yb : Yb + 2 * (size_t)SC * ld;
@@ -323,6 +369,7 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
           if (item < Nc * kq) {
             const int i = item / kq, r0 = 4 * (item % kq);
             float4 acc_u = acc[u];
+#pragma unroll 8
             for (int t = 0; t < SC; ++t)
               fma4(acc_u, Bs[t * Nc4 + i], *reinterpret_cast<const float4*>(yc + (size_t)t * ld + r0));
             acc[u] = acc_u;
@@ -339,7 +386,8 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
         *reinterpret_cast<float4*>(part + (size_t)i * kpp + r0) = acc[u];
       }
     }
-    if (tid < Nc4) part[(size_t)tid * kpp + kp] = ssum;
+    if (tid < Nc4) part[(size_t)tid * kpp + kp] = psum[tid];
+    cp_wait_all();   // all of V has landed (the owners' Gram term reads it)
     cluster.sync();
 
     // owners: sum the partial columns of each owned component, Gram term, update
@@ -362,27 +410,37 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
         for (int c = 0; c < SP_CLMAX; ++c)
           if (c < CL) dsum += pv[c];
       }
-      if (r == kp) s_si = dsum;
-      if (r < k) {  // (v_j . v_own)^2
-        const float* vi = Vs + (size_t)own * ld;
-        const float* vj = Vs + (size_t)r * ld;
-        float h0 = 0.f, h1 = 0.f;
-        for (int q = 0; q < kp; q += 8) {
-          h0 = dot4(*reinterpret_cast<const float4*>(vi + q), *reinterpret_cast<const float4*>(vj + q), h0);
-          if (q + 4 < kp)
-            h1 = dot4(*reinterpret_cast<const float4*>(vi + q + 4),
-                      *reinterpret_cast<const float4*>(vj + q + 4), h1);
+      {  // (v_j . v_own)^2: two threads per component j, alternate float4 of coordinates
+        const int j = tid >> 1, h = tid & 1;
+        float hv = 0.f;
+        if (j < k) {
+          const float* vi = Vs + (size_t)own * ld;
+          const float* vj = Vs + (size_t)j * ld;
+#pragma unroll 4
+          for (int q = 4 * h; q < kp; q += 8)
+            hv = dot4(*reinterpret_cast<const float4*>(vi + q), *reinterpret_cast<const float4*>(vj + q), hv);
         }
-        const float hv = h0 + h1;
-        hs[r] = hv * hv;
+        hv += __shfl_xor_sync(0xffffffffu, hv, 1);
+        if (h == 0 && j < kp) hs[j] = j < k ? hv * hv : 0.f;
       }
+      __syncthreads();
+      {  // Gram column: two halves of the components, one coordinate per thread
+        const int rr = tid & 127, hh = tid >> 7;
+        if (rr < kp) {
+          const int kh = (k + 1) / 2, j0 = hh * kh, j1 = min(k, j0 + kh);
+          float gg = 0.f;
+#pragma unroll 4
+          for (int j = j0; j < j1; ++j) gg = fmaf(hs[j], Vs[(size_t)j * ld + rr], gg);
+          gpart[hh * kp + rr] = gg;
+        }
+      }
+      if (r == kp) red[2 * (ST / 32)] = dsum;  // s_i
       __syncthreads();
       float x = 0.f, y = 0.f;
       if (r < kp) {
-        float gg = 0.f;
-        for (int j = 0; j < k; ++j) gg = fmaf(hs[j], Vs[(size_t)j * ld + r], gg);
-        const float ai = aA[lc], bi = aB[lc];
-        const float gdata = dsum * inv_b + ybC[r] * (a.c3 * ai * bi - a.c2 * s_si * inv_b);
+        const float gg = gpart[r] + gpart[kp + r];
+        const float ai = aA[lc], bi = aB[lc], si = red[2 * (ST / 32)];
+        const float gdata = dsum * inv_b + ybC[r] * (a.c3 * ai * bi - a.c2 * si * inv_b);
         const float v = r < k ? Vs[(size_t)own * ld + r] - beta * (a.kappa * gg - gdata) : 0.f;
         Vnext[(size_t)own * ld + r] = v;
         x = v * ybA[r];
@@ -413,7 +471,7 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
         Mnext[own] = tx;
         Mnext[kp + own] = ty;
       }
-      __syncthreads();  // hs, s_si and red are reused by the next owned component
+      __syncthreads();  // hs, gpart and red are reused by the next owned component
     }
     __threadfence();
     if (!cluster_grid_barrier(cluster, a.bar, a.flag, &s_ok)) {
@@ -426,17 +484,16 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
       return;
     }
     if (s + 1 < a.total_steps) {
-      // the new V (all components) and the block's means; the next chunk's
-      // samples are already in flight
-      for (int idx = tid; idx < kp * ld / 4; idx += ST) cp16(Vs + 4 * idx, Vnext + 4 * idx, true);
+      // the block's rows of the new V (the products need only these; the other
+      // rows are copied while the first product runs) and the block's means
+      const int b0 = c0 * ld / 4, b1 = min(c0 + Nc, kp) * ld / 4;
+      for (int idx = b0 + tid; idx < b1; idx += ST) cp16(Vs + 4 * idx, Vnext + 4 * idx, true);
       cp_commit();
       for (int i = tid; i < Nc4; i += ST) {
         const int gi = c0 + i;
         aA[i] = (i < Nc && gi < k) ? __ldcg(Mnext + gi) : 0.f;
         aB[i] = (i < Nc && gi < k) ? __ldcg(Mnext + kp + gi) : 0.f;
       }
-      cp_wait_all();  // V (and the prefetched chunk, issued long before)
-      __syncthreads();
     }
   }
   cp_wait_all();
