@@ -106,12 +106,6 @@ __device__ __forceinline__ float dot4(const float4& a, const float4& b, float ac
   acc = fmaf(a.z, b.z, acc);
   return fmaf(a.w, b.w, acc);
 }
-__device__ __forceinline__ void fma4(float4& acc, float s, const float4& v) {
-  acc.x = fmaf(s, v.x, acc.x);
-  acc.y = fmaf(s, v.y, acc.y);
-  acc.z = fmaf(s, v.z, acc.z);
-  acc.w = fmaf(s, v.w, acc.w);
-}
 __device__ __forceinline__ void cp16(float* dst, const float* src, bool in) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
                    (uint32_t)__cvta_generic_to_shared(dst)),
@@ -290,13 +284,20 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
 
   int64_t g = 0;  // next chunk to consume
   issue_chunk(0);
-  const int nit1 = SC * (Nc4 / 4);  // items of the first product (SC samples x Nc4 / 4)
-  const bool warp_seg = (SC % 32) == 0;
+  // tiles of the two products and the lanes that share one (a power of two)
+  const int nt1 = (SC / 4) * (Nc4 / 4), nt2 = kq * (Nc4 / 4);
+  int KS1 = 1, KS2 = 1;
+  while (KS1 < 8 && nt1 * KS1 * 2 <= ST && KS1 * 2 <= kq) KS1 *= 2;
+  while (KS2 < 8 && nt2 * KS2 * 2 <= ST && KS2 * 2 <= SC) KS2 *= 2;
   for (int64_t s = 0; s < a.total_steps; ++s) {
     const int par = (int)(s & 1);
     const int64_t pos0 = (s % a.spe) * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
-    float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    float g2[4][4];  // this lane's part of a tile of the partial columns
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) g2[c][u] = 0.f;
     for (int i = tid; i < Nc4; i += ST) psum[i] = 0.f;
     for (int q = 0; q < nchunk; ++q, ++g) {
       issue_chunk(g + 1);
@@ -308,82 +309,108 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
       }
       __syncthreads();
       const float* Yb = Ysb + (size_t)(g & 1) * L.nview * SC * ld;
-      // first product: A_A, A_B for 4 block components x 1 sample per item
-      for (int base = 0; base < nit1; base += ST) {
-        const int item = base + tid;
-        const bool act = item < nit1;
-        const int t = item % SC, i0 = 4 * (act ? item / SC : 0);
-        float pr[4] = {0.f, 0.f, 0.f, 0.f};
+      // first product A = Y V_c^T: 4 samples x 4 block components per tile, the
+      // coordinates split over KS1 neighbouring lanes, summed by shuffles
+      {
+        float xa[4][4], xb[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) xa[u][c] = xb[u][c] = 0.f;
+        const int tile = tid / KS1, ks = tid % KS1;
+        const bool act = tile < nt1;
+        const int t0 = 4 * (tile % (SC / 4)), i0 = 4 * (act ? tile / (SC / 4) : 0);
         if (act) {
-          const float* ya = Yb + (size_t)t * ld;
-          const float* yb = SYM ? ya : Yb + ((size_t)SC + t) * ld;
-          float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
           const float* vr[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int gi = c0 + i0 + j;
-            vr[j] = (i0 + j < Nc && gi < k) ? Vs + (size_t)gi * ld : Vs;
+          for (int c = 0; c < 4; ++c) {
+            const int gi = c0 + i0 + c;
+            vr[c] = Vs + (size_t)((i0 + c < Nc && gi < k) ? gi : 0) * ld;
           }
-#pragma unroll 4
-          for (int r = 0; r < kp; r += 4) {
-            const float4 yA = *reinterpret_cast<const float4*>(ya + r);
-            const float4 yB = SYM ? yA : *reinterpret_cast<const float4*>(yb + r);
+#pragma unroll 2
+          for (int r = 4 * ks; r < kp; r += 4 * KS1) {
+            float4 v[4], ya[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float4 v = *reinterpret_cast<const float4*>(vr[j] + r);
-              xa[j] = dot4(v, yA, xa[j]);
-              if (!SYM) xb[j] = dot4(v, yB, xb[j]);
+            for (int c = 0; c < 4; ++c) v[c] = *reinterpret_cast<const float4*>(vr[c] + r);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              ya[u] = *reinterpret_cast<const float4*>(Yb + (size_t)(t0 + u) * ld + r);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) xa[u][c] = dot4(v[c], ya[u], xa[u][c]);
+            if (!SYM) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float4 yb4 =
+                    *reinterpret_cast<const float4*>(Yb + ((size_t)SC + t0 + u) * ld + r);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xb[u][c] = dot4(v[c], yb4, xb[u][c]);
+              }
             }
           }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int i = i0 + j;
-            const bool on = i < Nc && c0 + i < k;
-            const float xA = on ? xa[j] : 0.f, xB = on ? (SYM ? xa[j] : xb[j]) : 0.f;
-            pr[j] = xA * xB;
-            Bs[t * Nc4 + i] = a.c1 * pr[j] - a.c2 * (aB[i] * xA + aA[i] * xB);
-          }
         }
-        // sum of A_A o A_B over the samples: the lanes of a warp hold 32 samples
-        // of the same 4 components when SC is a multiple of 32
-        if (warp_seg) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            float v = pr[j];
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && act) atomicAdd(&psum[i0 + j], v);
+          for (int c = 0; c < 4; ++c)
+            for (int o = KS1 / 2; o > 0; o >>= 1) {
+              xa[u][c] += __shfl_xor_sync(0xffffffffu, xa[u][c], o);
+              if (!SYM) xb[u][c] += __shfl_xor_sync(0xffffffffu, xb[u][c], o);
+            }
+        if (act && ks == 0) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = i0 + c;
+            const bool on = i < Nc && c0 + i < k;
+            float ps = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float xA = on ? xa[u][c] : 0.f, xB = on ? (SYM ? xa[u][c] : xb[u][c]) : 0.f;
+              const float pr = xA * xB;
+              ps += pr;
+              Bs[(t0 + u) * Nc4 + i] = a.c1 * pr - a.c2 * (aB[i] * xA + aA[i] * xB);
+            }
+            atomicAdd(&psum[i], ps);
           }
-        } else if (act) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) atomicAdd(&psum[i0 + j], pr[j]);
         }
       }
       __syncthreads();
-      // second product: partial columns sum_t y_C,t B[t, i] (float4 of coordinates)
+      // second product: the partial columns sum_t y_C,t B[t, i], 4 coordinates x 4
+      // block components per tile, the samples split over KS2 neighbouring lanes
+      // (per-lane sums carried over the step's chunks)
       {
         const float* yc = SYM ? Yb : Yb + 2 * (size_t)SC * ld;
+        const int tile = tid / KS2, ks = tid % KS2;
+        if (tile < nt2) {
+          const int r0 = 4 * (tile % kq), i0 = 4 * (tile / kq);
+#pragma unroll 4
+          for (int t = ks; t < SC; t += KS2) {
+            const float4 y4 = *reinterpret_cast<const float4*>(yc + (size_t)t * ld + r0);
+            const float4 b4 = *reinterpret_cast<const float4*>(Bs + t * Nc4 + i0);
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int item = tid + u * ST;
-          if (item < Nc * kq) {
-            const int i = item / kq, r0 = 4 * (item % kq);
-            float4 acc_u = acc[u];
-#pragma unroll 8
-            for (int t = 0; t < SC; ++t)
-              fma4(acc_u, Bs[t * Nc4 + i], *reinterpret_cast<const float4*>(yc + (size_t)t * ld + r0));
-            acc[u] = acc_u;
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) g2[c][u] = fmaf(bv[c], yv[u], g2[c][u]);
           }
         }
       }
       __syncthreads();  // the chunk buffer and B are reused by the next chunk
     }
+    {  // the step's partial columns: sum the KS2 lanes of each tile, store
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int item = tid + u * ST;
-      if (item < Nc * kq) {
-        const int i = item / kq, r0 = 4 * (item % kq);
-        *reinterpret_cast<float4*>(part + (size_t)i * kpp + r0) = acc[u];
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          for (int o = KS2 / 2; o > 0; o >>= 1) g2[c][u] += __shfl_xor_sync(0xffffffffu, g2[c][u], o);
+      const int tile = tid / KS2, ks = tid % KS2;
+      if (tile < nt2 && ks == 0) {
+        const int r0 = 4 * (tile % kq), i0 = 4 * (tile / kq);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          *reinterpret_cast<float4*>(part + (size_t)(i0 + c) * kpp + r0) =
+              make_float4(g2[c][0], g2[c][1], g2[c][2], g2[c][3]);
       }
     }
     if (tid < Nc4) part[(size_t)tid * kpp + kp] = psum[tid];
@@ -539,7 +566,9 @@ bool split_plan(int64_t k, int64_t b, bool sym, int CL, int C, SplitPlan* out) {
   if (Nc * kq > 2 * ST) return false;  // each thread accumulates at most two float4 outputs
   const int Sb = (int)((b + CL - 1) / CL);
   for (int SC : {64, 32, 16}) {
-    const int sc = std::min(SC, std::max(Sb, 1));
+    // chunks of a multiple of 4 samples (the products' tiles); samples past the
+    // slice are zero rows
+    const int sc = std::min(SC, (std::max(Sb, 1) + 3) & ~3);
     const SLayout L = s_layout((int)k, sym, Nc, sc);
     const size_t bytes = L.total * sizeof(float);
     if (bytes + 1024 <= (size_t)split_smem_optin()) {
