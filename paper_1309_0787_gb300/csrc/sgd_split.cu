@@ -225,13 +225,15 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     }
   }
 
-  // corpus row of sample t of chunk gg (global chunk sequence: step gg / nchunk,
-  // chunk gg % nchunk); -1 outside the minibatch or the data (a zero sample)
-  auto row_for = [&](int64_t gg, int t) -> int {
-    const int64_t s = gg / nchunk;
+  // Position of the next chunk to issue (step, chunk within the step, epoch,
+  // minibatch within the epoch), advanced without divisions.  The row of this
+  // thread's sample (t = tid < SC) in the chunk after it is loaded one issue
+  // ahead, so that the permutation's latency is hidden.
+  int64_t is_s = 0, is_e = 0, is_jb = 0;
+  int is_q = 0;
+  auto row_at = [&](int64_t s, int64_t e, int64_t jb, int q, int t) -> int {
     if (s >= a.total_steps) return -1;
-    const int q = (int)(gg % nchunk);
-    const int64_t e = s / a.spe, pos0 = (s % a.spe) * a.b;
+    const int64_t pos0 = jb * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
     const int pl = q * SC + t;
     const int64_t p = (int64_t)sl * Sb + pl;
@@ -239,36 +241,54 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     const int64_t row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
     return (row >= 0 && row < a.n) ? (int)row : -1;
   };
-  // the row of this thread's sample in the next chunk to issue, loaded one
-  // issue ahead so that the permutation's latency is hidden
-  int pf_row = tid < SC ? row_for(0, tid) : -1;
-  // sample chunk gg into buffer gg & 1.  Every call commits one cp.async
-  // group (an empty one past the last step).
+  auto advance = [&](int64_t& s, int64_t& e, int64_t& jb, int& q) {
+    if (++q == nchunk) {
+      q = 0;
+      ++s;
+      if (++jb == a.spe) {
+        jb = 0;
+        ++e;
+      }
+    }
+  };
+  int pf_row = tid < SC ? row_at(0, 0, 0, 0, tid) : -1;
+  // the next chunk into buffer gg & 1 (gg counts issues).  Every call commits
+  // one cp.async group (an empty one past the last step).  One warp per sample
+  // row, its lanes over the row's 16-byte (or 4-byte) pieces.
   auto issue_chunk = [&](int64_t gg) {
-    if (gg / nchunk >= a.total_steps) {
+    if (is_s >= a.total_steps) {
       cp_commit();
       return;
     }
     int* rows = s_rows[gg & 1];
-    if (tid < SC) {
-      rows[tid] = pf_row;
-      pf_row = row_for(gg + 1, tid);
+    {
+      int64_t ns = is_s, ne = is_e, njb = is_jb;
+      int nq = is_q;
+      advance(ns, ne, njb, nq);
+      if (tid < SC) {
+        rows[tid] = pf_row;
+        pf_row = row_at(ns, ne, njb, nq, tid);
+      }
+      is_s = ns;
+      is_e = ne;
+      is_jb = njb;
+      is_q = nq;
     }
     __syncthreads();
     float* Yb = Ysb + (size_t)(gg & 1) * L.nview * SC * ld;
     const int per_row = a.vec ? kq : kp;
-    const int items = L.nview * SC * per_row;
-    for (int idx = tid; idx < items; idx += ST) {
-      const int v = idx / (SC * per_row), rem = idx % (SC * per_row);
-      const int t = rem / per_row, u = rem % per_row;
+    for (int vt = warp; vt < L.nview * SC; vt += ST / 32) {
+      const int v = vt / SC, t = vt - v * SC;
       const int64_t row = rows[t];
       const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
       float* dst = Yb + ((size_t)v * SC + t) * ld;
-      if (a.vec) {
-        cp16(dst + 4 * u, row >= 0 ? Yg + row * k + 4 * u : Yg, row >= 0);
-      } else {
-        const bool in = row >= 0 && u < k;
-        cp4(dst + u, in ? Yg + row * k + u : Yg, in);
+      for (int u = lane; u < per_row; u += 32) {
+        if (a.vec) {
+          cp16(dst + 4 * u, row >= 0 ? Yg + row * k + 4 * u : Yg, row >= 0);
+        } else {
+          const bool in = row >= 0 && u < k;
+          cp4(dst + u, in ? Yg + row * k + u : Yg, in);
+        }
       }
     }
     cp_commit();
@@ -284,10 +304,11 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
 
   int64_t g = 0;  // next chunk to consume
   issue_chunk(0);
-  // tiles of the two products and the lanes that share one (a power of two)
-  const int nt1 = (SC / 4) * (Nc4 / 4), nt2 = kq * (Nc4 / 4);
-  int KS1 = 1, KS2 = 1;
-  while (KS1 < 8 && nt1 * KS1 * 2 <= ST && KS1 * 2 <= kq) KS1 *= 2;
+  const int nit1 = SC * (Nc4 / 4);  // items of the first product (SC samples x Nc4 / 4)
+  const bool warp_seg = (SC % 32) == 0;
+  // tiles of the second product and the lanes that share one (a power of two)
+  const int nt2 = kq * (Nc4 / 4);
+  int KS2 = 1;
   while (KS2 < 8 && nt2 * KS2 * 2 <= ST && KS2 * 2 <= SC) KS2 *= 2;
   for (int64_t s = 0; s < a.total_steps; ++s) {
     const int par = (int)(s & 1);
@@ -309,70 +330,55 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
       }
       __syncthreads();
       const float* Yb = Ysb + (size_t)(g & 1) * L.nview * SC * ld;
-      // first product A = Y V_c^T: 4 samples x 4 block components per tile, the
-      // coordinates split over KS1 neighbouring lanes, summed by shuffles
-      {
-        float xa[4][4], xb[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) xa[u][c] = xb[u][c] = 0.f;
-        const int tile = tid / KS1, ks = tid % KS1;
-        const bool act = tile < nt1;
-        const int t0 = 4 * (tile % (SC / 4)), i0 = 4 * (act ? tile / (SC / 4) : 0);
+      // first product: A_A, A_B for 4 block components x 1 sample per item
+      for (int base = 0; base < nit1; base += ST) {
+        const int item = base + tid;
+        const bool act = item < nit1;
+        const int t = item % SC, i0 = 4 * (act ? item / SC : 0);
+        float pr[4] = {0.f, 0.f, 0.f, 0.f};
         if (act) {
+          const float* ya = Yb + (size_t)t * ld;
+          const float* yb = SYM ? ya : Yb + ((size_t)SC + t) * ld;
+          float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
           const float* vr[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int gi = c0 + i0 + c;
-            vr[c] = Vs + (size_t)((i0 + c < Nc && gi < k) ? gi : 0) * ld;
+          for (int j = 0; j < 4; ++j) {
+            const int gi = c0 + i0 + j;
+            vr[j] = (i0 + j < Nc && gi < k) ? Vs + (size_t)gi * ld : Vs;
           }
-#pragma unroll 2
-          for (int r = 4 * ks; r < kp; r += 4 * KS1) {
-            float4 v[4], ya[4];
+#pragma unroll 4
+          for (int r = 0; r < kp; r += 4) {
+            const float4 yA = *reinterpret_cast<const float4*>(ya + r);
+            const float4 yB = SYM ? yA : *reinterpret_cast<const float4*>(yb + r);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = *reinterpret_cast<const float4*>(vr[c] + r);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              ya[u] = *reinterpret_cast<const float4*>(Yb + (size_t)(t0 + u) * ld + r);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) xa[u][c] = dot4(v[c], ya[u], xa[u][c]);
-            if (!SYM) {
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const float4 yb4 =
-                    *reinterpret_cast<const float4*>(Yb + ((size_t)SC + t0 + u) * ld + r);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) xb[u][c] = dot4(v[c], yb4, xb[u][c]);
-              }
+            for (int j = 0; j < 4; ++j) {
+              const float4 v = *reinterpret_cast<const float4*>(vr[j] + r);
+              xa[j] = dot4(v, yA, xa[j]);
+              if (!SYM) xb[j] = dot4(v, yB, xb[j]);
             }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int i = i0 + j;
+            const bool on = i < Nc && c0 + i < k;
+            const float xA = on ? xa[j] : 0.f, xB = on ? (SYM ? xa[j] : xb[j]) : 0.f;
+            pr[j] = xA * xB;
+            Bs[t * Nc4 + i] = a.c1 * pr[j] - a.c2 * (aB[i] * xA + aA[i] * xB);
           }
         }
+        // sum of A_A o A_B over the samples: the lanes of a warp hold 32 samples
+        // of the same 4 components when SC is a multiple of 32
+        if (warp_seg) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+          for (int j = 0; j < 4; ++j) {
+            float v = pr[j];
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            for (int o = KS1 / 2; o > 0; o >>= 1) {
-              xa[u][c] += __shfl_xor_sync(0xffffffffu, xa[u][c], o);
-              if (!SYM) xb[u][c] += __shfl_xor_sync(0xffffffffu, xb[u][c], o);
-            }
-        if (act && ks == 0) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int i = i0 + c;
-            const bool on = i < Nc && c0 + i < k;
-            float ps = 0.f;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float xA = on ? xa[u][c] : 0.f, xB = on ? (SYM ? xa[u][c] : xb[u][c]) : 0.f;
-              const float pr = xA * xB;
-              ps += pr;
-              Bs[(t0 + u) * Nc4 + i] = a.c1 * pr - a.c2 * (aB[i] * xA + aA[i] * xB);
-            }
-            atomicAdd(&psum[i], ps);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && act) atomicAdd(&psum[i0 + j], v);
           }
+        } else if (act) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) atomicAdd(&psum[i0 + j], pr[j]);
         }
       }
       __syncthreads();
