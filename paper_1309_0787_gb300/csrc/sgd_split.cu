@@ -39,6 +39,7 @@
 
 #include "grid_sync.cuh"
 #include "otm_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -122,6 +123,18 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_two() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+// One-dimensional bulk copy (TMA) of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) from global to this CTA's shared memory, completing on mbar.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc::smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 // Grid-wide barrier of the cooperative cluster launch.  Every CTA of a cluster
 // arrives at a cluster barrier; thread 0 of cluster rank 0 then arrives on the
@@ -160,6 +173,9 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_ok;
   __shared__ int s_rows[2][SP_SCMAX];  // corpus rows of a chunk's samples, by chunk parity
+  // bulk-copy completion (16-byte aligned rows): the two chunk buffers, the
+  // block's rows of V, the other rows of V
+  __shared__ __align__(8) uint64_t s_mb[4];
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int sl = (int)cluster.block_rank();       // sample slice of this CTA
@@ -203,6 +219,10 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
         if (i >= k || r >= kp) Vb[idx] = 0.f;
       }
     }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) tc::mbar_init(&s_mb[i], 1);
+    tc::mbar_fence_init();
   }
   __syncthreads();
   // a_A, a_B of the block's components from the initial V
@@ -255,9 +275,20 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
   // the next chunk into buffer gg & 1 (gg counts issues).  Every call commits
   // one cp.async group (an empty one past the last step).  One warp per sample
   // row, its lanes over the row's 16-byte (or 4-byte) pieces.
+  // completion parities of the four barriers, an unwaited chunk, a failed wait
+  uint32_t mph = 0;
+  int64_t out_g = -1;
+  bool bad = false;
+  auto mwait = [&](int i) {
+    if (!tc::mbar_wait(&s_mb[i], (mph >> i) & 1u)) {
+      if (tid == 0) atomicExch(a.flag, 2);
+      bad = true;
+    }
+    mph ^= 1u << i;
+  };
   auto issue_chunk = [&](int64_t gg) {
     if (is_s >= a.total_steps) {
-      cp_commit();
+      if (!a.vec) cp_commit();
       return;
     }
     int* rows = s_rows[gg & 1];
@@ -274,21 +305,38 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
       is_jb = njb;
       is_q = nq;
     }
-    __syncthreads();
     float* Yb = Ysb + (size_t)(gg & 1) * L.nview * SC * ld;
-    const int per_row = a.vec ? kq : kp;
+    if (a.vec) {
+      // one bulk copy per sample row and view; rows outside the data are zeroed
+      const int valid = __syncthreads_count(tid < SC && rows[tid] >= 0);
+      if (tid == 0) tc::mbar_expect_tx(&s_mb[gg & 1], (uint32_t)(valid * L.nview * k * 4));
+      __syncthreads();
+      if (tid < SC) {
+        const int row = rows[tid];
+        tc::fence_async_smem();  // earlier reads of the buffer precede the copy
+        for (int v = 0; v < L.nview; ++v) {
+          const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+          float* dst = Yb + ((size_t)v * SC + tid) * ld;
+          if (row >= 0)
+            bulk_g2s(dst, Yg + (int64_t)row * k, (uint32_t)(k * 4), &s_mb[gg & 1]);
+          else
+            for (int r = 0; r < kp; r += 4)
+              *reinterpret_cast<float4*>(dst + r) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      out_g = gg;
+      return;
+    }
+    __syncthreads();
+    const int per_row = kp;
     for (int vt = warp; vt < L.nview * SC; vt += ST / 32) {
       const int v = vt / SC, t = vt - v * SC;
       const int64_t row = rows[t];
       const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
       float* dst = Yb + ((size_t)v * SC + t) * ld;
       for (int u = lane; u < per_row; u += 32) {
-        if (a.vec) {
-          cp16(dst + 4 * u, row >= 0 ? Yg + row * k + 4 * u : Yg, row >= 0);
-        } else {
-          const bool in = row >= 0 && u < k;
-          cp4(dst + u, in ? Yg + row * k + u : Yg, in);
-        }
+        const bool in = row >= 0 && u < k;
+        cp4(dst + u, in ? Yg + row * k + u : Yg, in);
       }
     }
     cp_commit();
@@ -296,7 +344,18 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
   // rows of V outside this cluster's block, from the iterate buffer src (the
   // block's rows were copied before the step's first product)
   auto issue_vrest = [&](const float* src) {
-    const int b0 = c0 * ld / 4, b1 = min(c0 + Nc, kp) * ld / 4;
+    const int r1 = min(c0 + Nc, kp);
+    if (a.vec) {
+      if (tid == 0) {
+        tc::mbar_expect_tx(&s_mb[3], (uint32_t)((kp - (r1 - c0)) * ld * 4));
+        if (c0 > 0) bulk_g2s(Vs, src, (uint32_t)(c0 * ld * 4), &s_mb[3]);
+        if (r1 < kp)
+          bulk_g2s(Vs + (size_t)r1 * ld, src + (size_t)r1 * ld, (uint32_t)((kp - r1) * ld * 4),
+                   &s_mb[3]);
+      }
+      return;
+    }
+    const int b0 = c0 * ld / 4, b1 = r1 * ld / 4;
     for (int idx = tid; idx < kp * ld / 4; idx += ST)
       if (idx < b0 || idx >= b1) cp16(Vs + 4 * idx, src + 4 * idx, true);
     cp_commit();
@@ -322,8 +381,12 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     for (int i = tid; i < Nc4; i += ST) psum[i] = 0.f;
     for (int q = 0; q < nchunk; ++q, ++g) {
       issue_chunk(g + 1);
-      if (q == 0 && s > 0) {
-        issue_vrest(a.Vg + (size_t)par * kp * ld);
+      if (q == 0 && s > 0) issue_vrest(a.Vg + (size_t)par * kp * ld);
+      if (a.vec) {  // chunk g and, at a step's first chunk, the block's rows of V
+        mwait((int)(g & 1));
+        if (out_g == g) out_g = -1;
+        if (q == 0 && s > 0) mwait(2);
+      } else if (q == 0 && s > 0) {
         cp_wait_two();   // the block's rows of V and chunk g have landed
       } else {
         cp_wait_one();
@@ -420,7 +483,11 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
       }
     }
     if (tid < Nc4) part[(size_t)tid * kpp + kp] = psum[tid];
-    cp_wait_all();   // all of V has landed (the owners' Gram term reads it)
+    if (a.vec) {     // all of V has landed (the owners' Gram term reads it)
+      if (s > 0) mwait(3);
+    } else {
+      cp_wait_all();
+    }
     cluster.sync();
 
     // owners: sum the partial columns of each owned component, Gram term, update
@@ -507,11 +574,13 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
       __syncthreads();  // hs, gpart and red are reused by the next owned component
     }
     __threadfence();
+    fence_async_global();  // the new rows are read by bulk copies on other SMs
     if (!cluster_grid_barrier(cluster, a.bar, a.flag, &s_ok)) {
       // the whole cluster leaves here together; its peers read rank 0's flag
-      // before the final cluster barrier
+      // before the final cluster barrier; no bulk copy is left in flight
       for (int lc = sl; lc < Nc && c0 + lc < k; lc += CL)
         for (int r = tid; r < k; r += ST) a.V[(int64_t)(c0 + lc) * k + r] = __int_as_float(0x7fc00000);
+      if (a.vec && out_g >= 0) mwait((int)(out_g & 1));
       cp_wait_all();
       cluster.sync();
       return;
@@ -519,9 +588,20 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     if (s + 1 < a.total_steps) {
       // the block's rows of the new V (the products need only these; the other
       // rows are copied while the first product runs) and the block's means
-      const int b0 = c0 * ld / 4, b1 = min(c0 + Nc, kp) * ld / 4;
-      for (int idx = b0 + tid; idx < b1; idx += ST) cp16(Vs + 4 * idx, Vnext + 4 * idx, true);
-      cp_commit();
+      const int r1 = min(c0 + Nc, kp);
+      if (a.vec) {
+        if (tid == 0) {
+          fence_async_global();
+          tc::fence_async_smem();
+          tc::mbar_expect_tx(&s_mb[2], (uint32_t)((r1 - c0) * ld * 4));
+          bulk_g2s(Vs + (size_t)c0 * ld, Vnext + (size_t)c0 * ld, (uint32_t)((r1 - c0) * ld * 4),
+                   &s_mb[2]);
+        }
+      } else {
+        for (int idx = c0 * ld / 4 + tid; idx < r1 * ld / 4; idx += ST)
+          cp16(Vs + 4 * idx, Vnext + 4 * idx, true);
+        cp_commit();
+      }
       for (int i = tid; i < Nc4; i += ST) {
         const int gi = c0 + i;
         aA[i] = (i < Nc && gi < k) ? __ldcg(Mnext + gi) : 0.f;
@@ -530,6 +610,9 @@ __global__ void __launch_bounds__(ST, 1) sgd_split_kernel(SplitArgs a) {
     }
   }
   cp_wait_all();
+  if (bad)  // a bounded wait on a bulk copy gave up: the result is not to be used
+    for (int lc = sl; lc < Nc && c0 + lc < k; lc += CL)
+      for (int r = tid; r < k; r += ST) a.V[(int64_t)(c0 + lc) * k + r] = __int_as_float(0x7fc00000);
   cluster.sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
