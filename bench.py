@@ -52,7 +52,7 @@ CFG = dict(workload="mmsb_4x5000_k100_b1024_fp32", n_per=5000, k=100, alpha_i=0.
            alpha0=1.0, seed=0)
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
 # the persistent STGD kernel the library runs for each choice of otm_sgd_set_form
-SGD_KERNEL_NAME = {"auto": "sgd_split_kernel (one persistent launch = all STGD steps)",
+SGD_KERNEL_NAME = {"auto": "sgd_grid_kernel (one cooperative launch = all STGD steps)",
                    "split": "sgd_split_kernel (one persistent launch = all STGD steps)",
                    "grid": "sgd_grid_kernel (one cooperative launch = all STGD steps)",
                    "cluster": "sgd_cluster_kernel (one cluster launch = all STGD steps)"}

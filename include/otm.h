@@ -299,9 +299,9 @@ otm_status otm_sgd_run(float* V, const float* YA, const float* YB, const float* 
  * otm_sgd_set_form -- which FP32 kernel otm_sgd_step / otm_sgd_run use, for
  * the whole process (no paper counterpart; a performance choice with the same
  * results up to FP32 summation order):
- *   0 (default)  chosen by size: for b >= 256 and a caller workspace, the split
- *                form where it applies, else the grid form for k <= 128 and
- *                b <= 32 x (SM count); the cluster form otherwise;
+ *   0 (default)  chosen by size: with a caller workspace, the grid form for
+ *                k <= 128 and 256 <= b <= 32 x (SM count), the split form for
+ *                larger minibatches where it applies; the cluster form otherwise;
  *   1            the cluster form: one thread-block cluster of up to 16 CTAs
  *                keeps V in shared memory, the minibatch split over its CTAs,
  *                partial products reduced through distributed shared memory;

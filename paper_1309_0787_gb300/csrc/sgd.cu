@@ -572,7 +572,11 @@ otm_status run(float* V, const float* YA, const float* YB, const float* YC, int6
                void* ws, size_t ws_bytes, cudaStream_t st) {
   const int form = g_sgd_form.load();
   const bool sym_views = (YA == YB) && (YB == YC);
-  if (form == 3 || (form == 0 && b >= GRID_AUTO_MIN_B && ws &&
+  const bool grid_ok = sgd_grid_applicable(k, b);
+  // auto: the grid form where it applies (the fastest per step at b = 1,024,
+  // k = 100); beyond its minibatch limit the split form, which spreads a large
+  // minibatch over all clusters instead of one
+  if (form == 3 || (form == 0 && !grid_ok && b >= GRID_AUTO_MIN_B && ws &&
                     ws_bytes >= sgd_split_workspace(k))) {
     const bool split_ok = sgd_split_applicable(k, b, sym_views);
     if (form == 3 && !split_ok)
@@ -582,7 +586,6 @@ otm_status run(float* V, const float* YA, const float* YB, const float* YC, int6
       return sgd_split_run(V, YA, YB, YC, n, k, ybar3, perm, epochs, b, beta0, theta, alpha0,
                            snapshot_every, V_snap, ws, ws_bytes, st);
   }
-  const bool grid_ok = sgd_grid_applicable(k, b);
   if (form == 2 && !grid_ok)
     return set_error(OTM_EINVAL, "sgd: the grid form needs k <= 128 and 16 <= b <= 32 x SMs");
   // the auto choice takes the grid form only when the caller gave it its scratch
