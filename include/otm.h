@@ -442,7 +442,11 @@ typedef struct otm_batch_plan {
   int32_t nitems_wide;    /* chains with 128 < k <= 256 (second launch) */
   int32_t grid_clusters_wide;
   int32_t max_k_wide;
-  int32_t cluster_wide;   /* CTAs per chain with k > 128: 8 or 16, by the same trial */
+  int32_t cluster_wide;   /* CTAs per chain with k > 128: 4, 8 or 16, by the same trial */
+  int32_t stages;         /* sample stages (1-4) of the k <= 128 group's schedule */
+  int32_t vimg2;          /* its V image double-buffered (1) or single (0) */
+  int32_t stages_wide;    /* the same for the k > 128 group */
+  int32_t vimg2_wide;
   int64_t smem_bytes;
   void* ws;
   size_t ws_bytes;
@@ -457,11 +461,15 @@ typedef struct otm_batch_plan {
  * problem run together as one chain of R k components: every sample tile is
  * loaded and multiplied once for all of them, each keeps its own Gram term
  * (H = V^T V is masked to the restart's block), and the results equal R
- * separate runs up to FP32 summation order.  cluster = 0 runs the autotuner:
- * a short trial launch (at most 4 steps per chain, on scratch V) for each
- * cluster size whose shared-memory footprint fits the largest k; the fastest
- * is kept (cached per precision, largest k and chain count).  Synchronises
- * the stream.  Each chain runs the Lemma 3 schedule of otm_sgd_run_lp.
+ * separate runs up to FP32 summation order.  cluster = 0 runs the autotuner
+ * for each group (k <= 128, 128 < k <= 256): a short trial launch (at most 4
+ * steps per chain, on scratch V) for every schedule that fits the group's
+ * largest k -- the cluster size (CTAs per chain, i.e. the width of a CTA's tile
+ * of components), the number of sample stages (1 to 4) and a single or double
+ * V image; the fastest is kept (cached per group, precision, largest k and
+ * chain count) and recorded in the plan.  A given cluster size (k <= 128 group)
+ * takes its first fitting schedule.  Synchronises the stream.  Each chain runs
+ * the Lemma 3 schedule of otm_sgd_run_lp.
  *
  * otm_sgd_batched_launch -- one persistent launch running every chain with
  * k <= 128 (and, if the plan has any, a second one for 128 < k <= 256, whose

@@ -1151,9 +1151,9 @@ struct TcPlan {
   bool wide;  // k > 128: needs VIMG_BYTES of global scratch per cluster (streamed V images)
 };
 
-// The first configuration (deepest pipeline, double-buffered V image first)
-// whose tensor memory, registers and shared memory fit; false if none does.
-bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
+// Whether the schedule (CL CTAs per chain, NS sample stages, single or double V
+// image) fits tensor memory, registers and shared memory for k components.
+bool tc_plan_fits(int k, bool sym, bool fp8, int CL, bool dbl, int NS, TcPlan* out) {
   const int N = own_cols(k, CL);
   const int KPc = k <= 128 ? 128 : 256, MB = KPc / 128;
   if (N > 128 || (fp8 && N > 64)) return false;
@@ -1163,18 +1163,23 @@ bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
   // or, for k > 128, G_gram and the FP32 master rows per 128-row block
   if (2 * nvd * N + MB * (fp8 ? 2 : 1) * N + (MB > 1 ? 2 * MB * N : 16) > (int)TMEM_COLS)
     return false;
+  if (dbl && CL == 1) return false;
   const size_t lim = (size_t)max_smem_optin() - 1024;  // static shared variables
-  const int order[8][2] = {{1, 4}, {1, 3}, {0, 4}, {0, 3}, {1, 2}, {0, 2}, {1, 1}, {0, 1}};
-  for (const auto& o : order) {
-    const bool dbl = o[0] != 0;
-    if (dbl && CL == 1) continue;
-    const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, o[1], dbl, KPc);
-    if (L.vstr && (dbl || (size_t)o[1] * L.y_stage < (size_t)KPc * KPc * 2)) continue;
-    if (L.total <= lim) {
-      *out = {CL, N, o[1], dbl, L.total, L.vstr};
-      return true;
-    }
-  }
+  const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, NS, dbl, KPc);
+  if (L.vstr && (dbl || (size_t)NS * L.y_stage < (size_t)KPc * KPc * 2)) return false;
+  if (L.total > lim) return false;
+  *out = {CL, N, NS, dbl, L.total, L.vstr};
+  return true;
+}
+
+// The schedules tried for a cluster size, deepest pipeline and double-buffered V
+// image first.
+constexpr int kSchedules[8][2] = {{1, 4}, {1, 3}, {0, 4}, {0, 3}, {1, 2}, {0, 2}, {1, 1}, {0, 1}};
+
+// The first schedule of kSchedules that fits; false if none does.
+bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
+  for (const auto& o : kSchedules)
+    if (tc_plan_fits(k, sym, fp8, CL, o[0] != 0, o[1], out)) return true;
   return false;
 }
 
@@ -1235,10 +1240,12 @@ otm_status launch_batched(const TcPlan& P, const TcArgs* items, int nitems, int*
                           int nclusters, cudaStream_t st, bool configure, uint8_t* vimg) {
   auto kern = P.wide ? sgd_tc_batched_kernel<FP8, true> : sgd_tc_batched_kernel<FP8, false>;
   if (configure) {
-    OTM_CHECK_CUDA(
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
-    if (P.CL > 8)
-      OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    // the device's largest shared-memory size and non-portable clusters: every
+    // plan of this kernel launches under the same attributes, so a later prepare
+    // (another schedule) never invalidates an earlier plan
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        max_smem_optin() - 1024));
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   }
   if (nitems == 0) return OTM_OK;
   cudaLaunchAttribute attr[1];
@@ -1276,9 +1283,16 @@ int batched_clusters(bool fp8, const TcPlan& P) {
   return n;
 }
 
-// autotuner cache: (precision, max k, chains) -> chosen cluster size
+// A schedule of a batched group: CTAs per chain, single or double V image, sample stages.
+struct Sched {
+  int CL;
+  bool dbl;
+  int NS;
+};
+
+// autotuner cache: (group, precision, largest k, chains) -> chosen schedule
 std::mutex g_tune_mu;
-std::map<long long, int> g_tune_cache;
+std::map<long long, Sched> g_tune_cache;
 
 }  // namespace
 }  // namespace otm
@@ -1495,115 +1509,48 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   float* scratchV = bw.scratchV;
   cudaStream_t st = as_stream(stream);
   for (int i = 0; i < nitems; ++i) sorted[i].err = hdr + 1;
-  // the k > 128 group: 4-, 8- or 16-CTA clusters, whichever fit, the fastest on
-  // a trial run below
-  // (cluster sizes that leave a CTA without components of the largest problem
-  // are used only when no other fits)
-  std::vector<int> cands_w, cands_w_idle;
-  for (int c : {4, 8, 16}) {
-    TcPlan Pc;
-    if (n_wide == 0 || !tc_plan(max_k_wide, true, fp8, c, &Pc)) continue;
-    if ((c - 1) * own_cols(max_k_wide, c) < round16(max_k_wide))
-      cands_w.push_back(c);
-    else
-      cands_w_idle.push_back(c);
-  }
-  if (cands_w.empty()) cands_w = cands_w_idle;
-  OTM_REQUIRE(n_wide == 0 || !cands_w.empty(), "otm_sgd_batched_prepare: k=%d does not fit on chip",
-              max_k_wide);
   OTM_CHECK_CUDA(cudaMemcpyAsync(dev_items, sorted.data(), sizeof(TcArgs) * nitems,
                                  cudaMemcpyHostToDevice, st));
   OTM_CHECK_CUDA(cudaMemsetAsync(hdr, 0, 64 * sizeof(int), st));
-  // feasible cluster sizes: shared memory for the largest k
-  std::vector<int> cands;
-  for (int c : {1, 2, 4, 8, 16}) {
-    TcPlan Pc;
-    if (n_narrow == 0) break;
-    // every CTA of the cluster must own components of the largest problem
-    if ((c - 1) * own_cols(max_k, c) >= round16(max_k)) continue;
-    if (tc_plan(max_k, true, fp8, c, &Pc)) cands.push_back(c);
-  }
-  OTM_REQUIRE(n_narrow == 0 || !cands.empty() || cluster != 0,
-              "otm_sgd_batched_prepare: k=%d does not fit shared memory", max_k);
-  int chosen = n_narrow == 0 ? 16 : cluster;
-  if (n_narrow == 0) {
-  } else if (chosen != 0) {
-    TcPlan Pc;
-    OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pc),
-                "otm_sgd_batched_prepare: cluster %d does not fit k=%d", chosen, max_k);
-  } else {
-    // autotune: time a short trial (<= 4 steps per chain, on scratch V) for every
-    // feasible cluster size; the choice is cached per (precision, max k, items)
-    const long long key = ((long long)precision << 40) | ((long long)max_k << 24) | nitems;
-    {
-      std::lock_guard<std::mutex> lk(g_tune_mu);
-      auto f = g_tune_cache.find(key);
-      if (f != g_tune_cache.end()) chosen = f->second;
-    }
-    if (chosen == 0) {
-      const int ntrial = std::min(n_narrow, 512);
-      std::vector<TcArgs> trial(sorted.begin(), sorted.begin() + ntrial);
-      for (int i = 0; i < ntrial; ++i) {
-        trial[i].V = scratchV + (size_t)i * TC_KMAX * TC_KMAX;
-        trial[i].total_steps = std::min<int64_t>(trial[i].total_steps, 4);
-      }
-      OTM_CHECK_CUDA(cudaMemsetAsync(scratchV, 0, sizeof(float) * ntrial * TC_KMAX * TC_KMAX, st));
-      OTM_CHECK_CUDA(cudaMemcpyAsync(trial_items, trial.data(), sizeof(TcArgs) * ntrial,
-                                     cudaMemcpyHostToDevice, st));
-      cudaEvent_t e0, e1;
-      OTM_CHECK_CUDA(cudaEventCreate(&e0));
-      OTM_CHECK_CUDA(cudaEventCreate(&e1));
-      float best = 3.0e38f;
-      for (int c : cands) {
+  // Schedules of a group: the cluster size (CTAs per chain: the width of a CTA's
+  // tile of components), the number of sample stages and a single or double V
+  // image.  Cluster sizes that leave a CTA without components of the group's
+  // largest chain are used only when no other fits.
+  auto schedules = [&](int kmax, bool wide, int only_cl) {
+    std::vector<Sched> full, idle;
+    const int cls[5] = {1, 2, 4, 8, 16};
+    for (int c : cls) {
+      if (wide && c < 4) continue;
+      if (only_cl && c != only_cl) continue;
+      const bool busy = (c - 1) * own_cols(kmax, c) < round16(kmax);
+      for (const auto& o : kSchedules) {
         TcPlan Pc;
-        tc_plan(max_k, true, fp8, c, &Pc);
-        float tot = 0.f;
-        // set attributes (zero-item launch) before the occupancy query
-        otm_status s1 = fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr)
-                            : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr);
-        if (s1 != OTM_OK) return s1;
-        const int ncl = std::min(batched_clusters(fp8, Pc), ntrial);
-        for (int rep = 0; rep < 2; ++rep) {
-          OTM_CHECK_CUDA(cudaMemsetAsync(hdr + 8, 0, sizeof(int), st));
-          OTM_CHECK_CUDA(cudaEventRecord(e0, st));
-          otm_status s2 = fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, nullptr)
-                              : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, nullptr);
-          if (s2 != OTM_OK) return s2;
-          OTM_CHECK_CUDA(cudaEventRecord(e1, st));
-          OTM_CHECK_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          OTM_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (rep == 1) tot = ms;  // second run: code and caches warm
-        }
-        if (tot < best) {
-          best = tot;
-          chosen = c;
-        }
+        if (!tc_plan_fits(kmax, true, fp8, c, o[0] != 0, o[1], &Pc)) continue;
+        (busy ? full : idle).push_back({c, o[0] != 0, o[1]});
       }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      std::lock_guard<std::mutex> lk(g_tune_mu);
-      g_tune_cache[key] = chosen;
     }
-  }
-  // the k > 128 group: cluster size by the same trial (cached likewise)
-  int chosen_w = 0;
-  if (n_wide > 0) {
-    chosen_w = cands_w.back();
-    const long long key = (1LL << 62) | ((long long)precision << 40) |
-                          ((long long)max_k_wide << 24) | n_wide;
-    bool cached = false;
+    return full.empty() ? idle : full;
+  };
+  // The autotuner: a short trial of the group's chains (at most 512, at most 4
+  // steps each, on scratch V) for each schedule, the fastest of two timed
+  // repetitions kept; cached per (precision, group, largest k, chains).
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto tune = [&](const std::vector<Sched>& cands, int kmax, int first, int count, bool wide,
+                  Sched* best_out) -> otm_status {
+    const long long key = ((long long)wide << 62) | ((long long)precision << 40) |
+                          ((long long)kmax << 24) | count;
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto f = g_tune_cache.find(key);
       if (f != g_tune_cache.end()) {
-        chosen_w = f->second;
-        cached = true;
+        *best_out = f->second;
+        return OTM_OK;
       }
     }
-    if (!cached && cands_w.size() > 1) {
-      const int ntrial = std::min(n_wide, 512);
-      std::vector<TcArgs> trial(sorted.begin() + n_narrow, sorted.begin() + n_narrow + ntrial);
+    Sched best = cands.front();
+    if (cands.size() > 1) {
+      const int ntrial = std::min(count, 512);
+      std::vector<TcArgs> trial(sorted.begin() + first, sorted.begin() + first + ntrial);
       for (int i = 0; i < ntrial; ++i) {
         trial[i].V = scratchV + (size_t)i * TC_KMAX * TC_KMAX;
         trial[i].total_steps = std::min<int64_t>(trial[i].total_steps, 4);
@@ -1611,48 +1558,76 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
       OTM_CHECK_CUDA(cudaMemsetAsync(scratchV, 0, sizeof(float) * ntrial * TC_KMAX * TC_KMAX, st));
       OTM_CHECK_CUDA(cudaMemcpyAsync(trial_items, trial.data(), sizeof(TcArgs) * ntrial,
                                      cudaMemcpyHostToDevice, st));
-      cudaEvent_t e0, e1;
-      OTM_CHECK_CUDA(cudaEventCreate(&e0));
-      OTM_CHECK_CUDA(cudaEventCreate(&e1));
-      float best = 3.0e38f;
-      for (int c : cands_w) {
+      if (!e0) {
+        OTM_CHECK_CUDA(cudaEventCreate(&e0));
+        OTM_CHECK_CUDA(cudaEventCreate(&e1));
+      }
+      float best_ms = 3.0e38f;
+      for (const Sched& c : cands) {
         TcPlan Pc;
-        tc_plan(max_k_wide, true, fp8, c, &Pc);
-        otm_status s1 = fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr)
-                            : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr);
-        if (s1 != OTM_OK) return s1;
-        const int ncl = std::min(std::min(batched_clusters(fp8, Pc), wide_clusters_cap(Pc)), ntrial);
-        float tot = 0.f;
+        tc_plan_fits(kmax, true, fp8, c.CL, c.dbl, c.NS, &Pc);
+        OTM_TRY(fp8 ? launch_batched<true>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr)
+                    : launch_batched<false>(Pc, trial_items, 0, hdr + 8, 1, st, true, nullptr));
+        int ncl = std::min(batched_clusters(fp8, Pc), ntrial);
+        if (wide) ncl = std::min(ncl, wide_clusters_cap(Pc));
+        float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {
           OTM_CHECK_CUDA(cudaMemsetAsync(hdr + 8, 0, sizeof(int), st));
           OTM_CHECK_CUDA(cudaEventRecord(e0, st));
-          otm_status s2 =
-              fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vimg_wide)
-                  : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false, bw.vimg_wide);
-          if (s2 != OTM_OK) return s2;
+          OTM_TRY(fp8 ? launch_batched<true>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false,
+                                             wide ? bw.vimg_wide : nullptr)
+                      : launch_batched<false>(Pc, trial_items, ntrial, hdr + 8, ncl, st, false,
+                                              wide ? bw.vimg_wide : nullptr));
           OTM_CHECK_CUDA(cudaEventRecord(e1, st));
           OTM_CHECK_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          OTM_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (rep == 1) tot = ms;
+          OTM_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));  // the second: code and caches warm
         }
-        if (tot < best) {
-          best = tot;
-          chosen_w = c;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
         }
       }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = chosen_w;
+    g_tune_cache[key] = best;
+    *best_out = best;
+    return OTM_OK;
+  };
+  Sched sn{16, false, 1}, sw{16, false, 1};
+  otm_status tuned = OTM_OK;
+  if (n_narrow > 0) {
+    // a given cluster size keeps its first fitting schedule (the single-chain one)
+    const std::vector<Sched> cands = schedules(max_k, false, cluster);
+    if (cands.empty()) {
+      tuned = set_error(OTM_EINVAL, cluster ? "otm_sgd_batched_prepare: cluster %d does not fit k=%d"
+                                            : "otm_sgd_batched_prepare: k=%d does not fit shared memory",
+                        cluster ? cluster : max_k, max_k);
+    } else if (cluster) {
+      sn = cands.front();
+    } else {
+      tuned = tune(cands, max_k, 0, n_narrow, false, &sn);
+    }
   }
+  if (tuned == OTM_OK && n_wide > 0) {
+    const std::vector<Sched> cands = schedules(max_k_wide, true, 0);
+    if (cands.empty())
+      tuned = set_error(OTM_EINVAL, "otm_sgd_batched_prepare: k=%d does not fit on chip", max_k_wide);
+    else
+      tuned = tune(cands, max_k_wide, n_narrow, n_wide, true, &sw);
+  }
+  if (e0) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (tuned != OTM_OK) return tuned;
   TcPlan Pch{}, Pw{};
   if (n_narrow > 0)
-    OTM_REQUIRE(tc_plan(max_k, true, fp8, chosen, &Pch), "otm_sgd_batched_prepare: no plan");
+    OTM_REQUIRE(tc_plan_fits(max_k, true, fp8, sn.CL, sn.dbl, sn.NS, &Pch),
+                "otm_sgd_batched_prepare: no plan");
   if (n_wide > 0)
-    OTM_REQUIRE(tc_plan(max_k_wide, true, fp8, chosen_w, &Pw), "otm_sgd_batched_prepare: no plan");
-  // each group's kernel takes its own plan's attributes
+    OTM_REQUIRE(tc_plan_fits(max_k_wide, true, fp8, sw.CL, sw.dbl, sw.NS, &Pw),
+                "otm_sgd_batched_prepare: no plan");
+  // each group's kernel takes the launch attributes
   for (int grp = 0; grp < 2; ++grp) {
     if ((grp == 0 ? n_narrow : n_wide) == 0) continue;
     const TcPlan& Pg = grp == 0 ? Pch : Pw;
@@ -1662,16 +1637,20 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
   }
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
   plan->nitems = nitems;
-  plan->cluster = chosen;
+  plan->cluster = n_narrow > 0 ? sn.CL : 0;
   plan->precision = precision;
   plan->max_k = max_k;
   plan->smem_bytes = (int64_t)Pch.smem;
   plan->grid_clusters = n_narrow > 0 ? std::min(batched_clusters(fp8, Pch), n_narrow) : 0;
   plan->nitems_wide = n_wide;
   plan->max_k_wide = max_k_wide;
-  plan->cluster_wide = chosen_w;
+  plan->cluster_wide = n_wide > 0 ? sw.CL : 0;
   plan->grid_clusters_wide =
       n_wide > 0 ? std::min(std::min(batched_clusters(fp8, Pw), wide_clusters_cap(Pw)), n_wide) : 0;
+  plan->stages = n_narrow > 0 ? sn.NS : 0;
+  plan->vimg2 = n_narrow > 0 ? (int32_t)sn.dbl : 0;
+  plan->stages_wide = n_wide > 0 ? sw.NS : 0;
+  plan->vimg2_wide = n_wide > 0 ? (int32_t)sw.dbl : 0;
   plan->ws = ws;
   plan->ws_bytes = ws_bytes;
   return OTM_OK;
@@ -1691,7 +1670,8 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
   const bool fp8 = plan->precision == OTM_PREC_FP8;
   if (n_narrow > 0) {
     TcPlan P;
-    OTM_REQUIRE(tc_plan(plan->max_k, true, fp8, plan->cluster, &P) &&
+    OTM_REQUIRE(tc_plan_fits(plan->max_k, true, fp8, plan->cluster, plan->vimg2 != 0,
+                             plan->stages, &P) &&
                     (int64_t)P.smem == plan->smem_bytes && plan->grid_clusters >= 1,
                 "otm_sgd_batched_launch: plan does not match this library");
     OTM_TRY(fp8 ? launch_batched<true>(P, dev_items, n_narrow, hdr, plan->grid_clusters, st,
@@ -1701,7 +1681,8 @@ otm_status otm_sgd_batched_launch(const otm_batch_plan* plan, void* stream) {
   }
   if (n_wide > 0) {
     TcPlan P;
-    OTM_REQUIRE(tc_plan(plan->max_k_wide, true, fp8, plan->cluster_wide, &P) &&
+    OTM_REQUIRE(tc_plan_fits(plan->max_k_wide, true, fp8, plan->cluster_wide,
+                             plan->vimg2_wide != 0, plan->stages_wide, &P) &&
                     plan->grid_clusters_wide >= 1 &&
                     plan->grid_clusters_wide <= wide_clusters_cap(P),
                 "otm_sgd_batched_launch: plan does not match this library");

@@ -47,7 +47,9 @@ class OtmBatchPlan(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_k", ctypes.c_int32),
                 ("grid_clusters", ctypes.c_int32), ("nitems_wide", ctypes.c_int32),
                 ("grid_clusters_wide", ctypes.c_int32), ("max_k_wide", ctypes.c_int32),
-                ("cluster_wide", ctypes.c_int32), ("smem_bytes", c_i64), ("ws", c_vp),
+                ("cluster_wide", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("vimg2", ctypes.c_int32), ("stages_wide", ctypes.c_int32),
+                ("vimg2_wide", ctypes.c_int32), ("smem_bytes", c_i64), ("ws", c_vp),
                 ("ws_bytes", c_sz)]
 
 

@@ -84,6 +84,9 @@ def test_batched_mixed_sizes_autotuned(otm, prec_name):
     batch = otm.SgdBatch(probs, prec)
     assert batch.nitems == sum(_items(s[1], s[-1]) for s in specs)
     assert batch.cluster in (1, 2, 4, 8, 16)
+    # the tuned schedule: sample stages and V-image buffering recorded in the plan
+    assert 1 <= batch.plan.stages <= 4 and batch.plan.vimg2 in (0, 1)
+    assert batch.plan.vimg2 == 0 or batch.cluster > 1
     batch.launch()
     batch.check()
     tol = 1e-2 if prec == otm.PREC_BF16 else 2e-2
@@ -139,6 +142,7 @@ def test_batched_two_groups_fp8(otm):
     probs = [_problem(otm, s, k, n, b, e, r, 5e-3, prec) for s, k, n, b, e, r in specs]
     batch = otm.SgdBatch(probs, prec)
     assert batch.plan.nitems_wide == 2 and batch.plan.cluster_wide in (4, 8, 16)
+    assert 1 <= batch.plan.stages_wide <= 4 and batch.plan.vimg2_wide in (0, 1)
     batch.launch()
     batch.check()
     for p in probs:
