@@ -271,3 +271,103 @@ def test_training_lowers_loss_and_beats_random_init(otm):
     print(f"held-out -L: network {-l_net:.4f}, canonical frame {-l_frame:.4f}, random {-l_rand:.4f}")
     assert l_net < l_rand - 0.5
     assert l_net < l_frame + 0.01
+
+
+def _steps_to_1e3(otm, Y, a0, V0, U_ref, lam_ref, beta0, max_steps):
+    """First full-batch STGD step (b = n) whose iterate is within 1e-3 relative
+    reconstruction error of the reference, or None."""
+    yb = torch.stack([Y.double().mean(0)] * 3).contiguous()
+    V = V0.clone()
+    sn = otm.sgd_run(V, Y, Y, Y, yb, None, max_steps, Y.shape[0], beta0, 1.0, a0,
+                     snapshot_every=1)
+    for j in range(sn.shape[0]):
+        if float(otm.recon_error(sn[j].contiguous(), U_ref, lam_ref, 1.0)[0]) <= 1e-3:
+            return j + 1
+    return None
+
+
+def test_trained_network_beats_frame_on_held_out(otm):
+    """The learned start against the canonical frame alone and a Haar-random start
+    (k = 8), after training on 65,536 generated instances (8 epochs, batch 256):
+      * captured mass -L on 1,000 held-out instances: the network's mean exceeds
+        the frame's by at least 0.005 and by at least four standard errors of the
+        paired differences;
+      * full-batch STGD (b = n = 4,000, beta0 = 0.1) to 1e-3 of a converged
+        reference (6,000 steps from the frame start) on 200 of them: the network's
+        start reaches 1e-3 on at least 99 % of the instances, in at most 0.9 times
+        the frame start's mean number of steps and by at least two standard errors
+        of the paired differences; the random start reaches it within 600 steps on
+        fewer than half of them."""
+    k, J, h, n_train, ntr, B, epochs = 8, 4, 256, 1000, 65536, 256, 8
+    nte, n_test, nsgd, beta0 = 1000, 4000, 200, 0.1
+    din, dout = J * k * k, k * k
+    inst = synth.whitened_lda_instances(300, ntr + nte, k)
+    th = _dev(synth.unit_vectors(301, J, k))
+    m, al = _dev(inst["m"]), _dev(inst["alpha32"])
+    a0 = _dev(inst["alpha0"])
+    Us = _dev(inst["U"].astype(np.float32))
+    lam = _dev(inst["lam"].astype(np.float32))
+    X = torch.empty(ntr, din, dtype=torch.bfloat16, device="cuda")
+    E = torch.empty(ntr, k, k, dtype=torch.float32, device="cuda")
+    for c0 in range(0, ntr, 1024):
+        c1 = min(c0 + 1024, ntr)
+        Yc = otm.ws_generate(m[c0:c1].contiguous(), al[c0:c1].contiguous(), n_train, 302,
+                             first=c0)
+        S, _ = otm.ws_sketch(Yc, a0[c0:c1].contiguous(), th)
+        Ec, _, Xc = otm.ws_canonicalize(S)
+        X[c0:c1], E[c0:c1] = Xc, Ec
+    Ut = otm.ws_rotate(E, Us[:ntr].contiguous(), transpose=True)
+    p0 = ows.init_params(303, din, h, dout)
+    p0["W3"] *= 0.01
+    p0["b3"] = np.eye(k).reshape(-1)
+    net = otm.Mlp(din, h, dout, _flat(p0).astype(np.float32))
+    steps = epochs * ntr // B
+    for st in range(steps):
+        i0 = (st * B) % ntr
+        net.train_step(X[i0:i0 + B], Ut[i0:i0 + B], lam[i0:i0 + B], k,
+                       1e-3 if st < 0.7 * steps else 2e-4)
+    net.check(B)
+    lo = ntr
+    Yt = otm.ws_generate(m[lo:].contiguous(), al[lo:].contiguous(), n_test, 304, first=lo)
+    St, _ = otm.ws_sketch(Yt, a0[lo:].contiguous(), th)
+    Et, _, Xt = otm.ws_canonicalize(St)
+    U0 = otm.ws_rotate(Et, net.infer(Xt, k).contiguous())
+    Ur = _dev(np.stack([synth.haar_orthonormal(5000 + b, k) for b in range(nte)]))
+
+    def captured(U):
+        return -to_np(otm.ws_loss_grad(U.contiguous(), Us[lo:].contiguous(),
+                                       lam[lo:].contiguous())[0]).astype(np.float64)
+    cn, cf, cr = captured(U0), captured(Et), captured(Ur)
+    d = cn - cf
+    sem = d.std() / np.sqrt(nte)
+    print(f"held-out -L: network {cn.mean():.4f}, frame {cf.mean():.4f}, random {cr.mean():.4f}; "
+          f"network - frame {d.mean():.4f} +- {sem:.4f}")
+    assert d.mean() >= 0.005 and d.mean() >= 4 * sem
+
+    a0t = a0[lo:].contiguous()
+    starts = {"net": otm.ws_init_components(U0, Yt, a0t, 1.0),
+              "frame": otm.ws_init_components(Et.contiguous(), Yt, a0t, 1.0),
+              "random": otm.ws_init_components(Ur, Yt, a0t, 1.0)}
+    res = {nm: [] for nm in starts}
+    for i in range(nsgd):
+        Y = Yt[i].contiguous()
+        a0i = float(a0t[i])
+        yb = torch.stack([Y.double().mean(0)] * 3).contiguous()
+        Vref = starts["frame"][i].clone()
+        otm.sgd_run(Vref, Y, Y, Y, yb, None, 6000, n_test, beta0, 1.0, a0i)
+        nr = Vref.double().norm(dim=1)
+        lam_ref, U_ref = (nr ** 3).contiguous(), (Vref.double() / nr[:, None]).contiguous()
+        for nm, V0 in starts.items():
+            res[nm].append(_steps_to_1e3(otm, Y, a0i, V0[i], U_ref, lam_ref, beta0,
+                                         600 if nm == "random" else 1000))
+    reached = {nm: np.mean([s is not None for s in v]) for nm, v in res.items()}
+    both = [(a, b) for a, b in zip(res["net"], res["frame"]) if a is not None and b is not None]
+    sn = np.array([a for a, _ in both], dtype=float)
+    sf = np.array([b for _, b in both], dtype=float)
+    dd = sn - sf
+    print(f"steps to 1e-3: reached {reached}; mean network {sn.mean():.1f}, frame {sf.mean():.1f}; "
+          f"paired {dd.mean():.2f} +- {dd.std() / np.sqrt(len(dd)):.2f}")
+    assert reached["net"] >= 0.99
+    assert sn.mean() <= 0.9 * sf.mean()
+    assert dd.mean() <= -2 * dd.std() / np.sqrt(len(dd))
+    assert reached["random"] < 0.5
