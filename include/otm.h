@@ -88,16 +88,34 @@ otm_status otm_topic_moments(const otm_csr* X, float* row_invlen, float* row_w,
                              double* M1, double* delta, void* stream);
 
 /*
+ * otm_csr_transpose -- the CSR of X^T (d x n): colptr[d + 1], rowT[nnz] (the
+ * document of each entry), valT[nnz], all caller-owned device arrays.  X must
+ * have distinct columns within each row (a word counted once per document).
+ * A counting sort by word over blocks of rows (per-block counts in shared
+ * memory) where d fits, else one atomic position per entry; within a word the
+ * documents come in no fixed order, colptr is exact.  Scratch:
+ * otm_csr_transpose_workspace(n, d) bytes.  Used by the topic M2 products
+ * (Eq. (2)): X^T P becomes a gather over the transpose.
+ */
+size_t otm_csr_transpose_workspace(int64_t n, int64_t d);
+otm_status otm_csr_transpose(const otm_csr* X, int32_t* colptr, int32_t* rowT, float* valT,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/*
  * otm_topic_m2_apply -- O = M2 S for Eq. (2) without forming M2:
  *   M2 S = (alpha0+1) [ (1/n) X^T diag(row_w) (X S) - diag(delta) S ]
  *          - alpha0 M1 (M1^T S).
- * S: d x m, O: d x m (float32, row-major; O must not alias S).
+ * S: d x m, O: d x m (float32, row-major; O must not alias S).  Xt: the
+ * transpose of X from otm_csr_transpose, or NULL.  With Xt, X^T P is a gather
+ * over it (m at most 384); without, a scatter with one atomic per nonzero and
+ * column.
  * Scratch: otm_topic_m2_workspace(n, m) bytes.
  */
 size_t otm_topic_m2_workspace(int64_t n, int64_t m);
-otm_status otm_topic_m2_apply(const otm_csr* X, const float* row_w, const double* M1,
-                              const double* delta, double alpha0, const float* S,
-                              int64_t m, float* O, void* ws, size_t ws_bytes, void* stream);
+otm_status otm_topic_m2_apply(const otm_csr* X, const otm_csr* Xt, const float* row_w,
+                              const double* M1, const double* delta, double alpha0,
+                              const float* S, int64_t m, float* O, void* ws, size_t ws_bytes,
+                              void* stream);
 
 /*
  * otm_pairs_apply -- O = Pairs(Y1, Y2) S = (1/n_X) G_{X,Y1}^T (G_{X,Y2} S)
@@ -179,9 +197,15 @@ otm_status otm_syev_noalloc(const double* A, int64_t n, double* evals, double* e
  * row_invlen[n], row_w[n] (as otm_topic_moments).  Returns OTM_ENOTPSD if the
  * k-th eigenvalue is not above 1e-5 times the largest (not positive, or not
  * resolvable at the float32 accuracy of the range finder).  Synchronises the
- * stream (the eigenvalue check).  Scratch: otm_whiten_topic_workspace(n, d, k, kt).
+ * stream (the eigenvalue check).  Scratch: otm_whiten_topic_workspace(n, d,
+ * nnz, k, kt); it holds, among the rest, the transpose of X (the CSR of X^T,
+ * formed once per call, 8 nnz + 8 d bytes), through which X^T P and the
+ * first moments are gathered.  The order of a word's documents in that
+ * transpose comes from atomic positions, so FP32 sums over them (X^T P) vary
+ * in the last bits from call to call; M1 and the other FP64 outputs of the
+ * moments do not depend on it beyond FP64 rounding.
  */
-size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t k, int64_t kt);
+size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t nnz, int64_t k, int64_t kt);
 otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t kt,
                             int power_iters, double alpha0, float* W, float* Q, double* Cw,
                             double* Cp, double* eig, double* M1, float* row_invlen,
@@ -671,7 +695,8 @@ otm_status otm_unwhiten(const float* V, int64_t k, const float* Q, int64_t d, in
  * unit columns):
  *   err = || kappa sum_i v_i^(x)3 - sum_j lam_j u_j^(x)3 ||_F / || sum_j lam_j u_j^(x)3 ||_F,
  * evaluated in closed form from Gram matrices (<x^(x)3, y^(x)3> = <x,y>^3), FP64.
- * Writes one double to err (device).  Scratch: otm_recon_error_workspace(k).
+ * Writes one double to err (device): NaN if V holds a non-finite value (a
+ * diverged run), never a clamped zero.  Scratch: otm_recon_error_workspace(k).
  */
 size_t otm_recon_error_workspace(int64_t k);
 otm_status otm_recon_error(const float* V, int64_t k, double theta, const double* U_true,

@@ -80,6 +80,22 @@ otm_status spmm_scatter(const otm_csr* X, const float* P, int64_t m, const float
                         float alpha, float* out, cudaStream_t st);
 otm_status topic_moments(const otm_csr* X, float* row_invlen, float* row_w, double* M1,
                          double* delta, cudaStream_t st);
+// The CSR of X^T: colptr (cols + 1), rowT, valT (nnz each); scratch of
+// csr_transpose_workspace(rows, cols) bytes (256-byte aligned).  A counting sort
+// by word over row blocks where a word's count per block fits shared memory,
+// else one global atomic position per entry.  The order of the entries within
+// a column is not fixed.  X must have distinct columns within each row.
+size_t csr_transpose_workspace(int64_t n, int64_t d);
+otm_status csr_transpose(const otm_csr* X, int32_t* colptr, int32_t* rowT, float* valT,
+                         void* scratch, cudaStream_t st);
+// topic_moments over the transpose; wa, wb (rows, FP64) are scratch.
+otm_status topic_moments_csc(const otm_csr* X, const int32_t* colptr, const int32_t* rowT,
+                             const float* valT, double* wa, double* wb, float* row_invlen,
+                             float* row_w, double* M1, double* delta, cudaStream_t st);
+// out (d x m) += alpha * X^T P over the transpose of X (out pre-zeroed; m <= 384).
+otm_status spmm_csc(const int32_t* colptr, const int32_t* rowT, const float* valT, int64_t d,
+                    int64_t nnz, const float* P, int64_t m, float alpha, float* out,
+                    cudaStream_t st);
 // M1[c] = (1/rows) sum_r X[r, c]  (community first moment, Eq. (9))
 otm_status column_sums_scaled(const otm_csr* X, double scale, double* out, cudaStream_t st);
 

@@ -121,7 +121,8 @@ __global__ void recon_final_kernel(const double* __restrict__ part, int64_t k, d
     tt += part[3 * i + 2];
   }
   const double num = kappa * kappa * hh - 2.0 * kappa * ht + tt;
-  *err = sqrt((num > 0.0 ? num : 0.0) / tt);
+  // a rounding-negative num is zero; a non-finite V (a diverged run) gives NaN
+  *err = isfinite(hh) && isfinite(ht) ? sqrt((num < 0.0 ? 0.0 : num) / tt) : nan("");
 }
 
 }  // namespace

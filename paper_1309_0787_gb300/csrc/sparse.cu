@@ -7,6 +7,16 @@
 // One warp per CSR row; the dense rows move as float4 (coalesced 16-byte
 // loads), the row's (col, val) pairs are loaded once per warp and broadcast
 // with shuffles.
+//
+// The topic whitening instead transposes the counts once (the CSR of X^T:
+// per-word counts, an exclusive scan, a scatter of (document, count) pairs)
+// and forms X^T P as a gather over that transpose: each warp takes a fixed
+// run of nonzeros in word order (so a word of 300,000 documents is spread over
+// many warps), sums the P rows of each word's documents in registers, and
+// writes a word it holds whole with plain stores, a word it shares with
+// another warp with vector atomics.  That replaces one vector atomic per
+// nonzero by at most two per warp.  The first moments become per-word sums in
+// FP64 over the same transpose, without atomics.
 #include "otm_internal.cuh"
 
 namespace otm {
@@ -19,6 +29,9 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// Nonzeros per warp of the gather over the transpose.
+constexpr int kCscChunk = 256;
 
 // l_t, 1/l_t, 1/(l_t(l_t-1)) and the FP64 first-moment scatters.
 __global__ void topic_stats_kernel(const int32_t* __restrict__ row_ptr,
@@ -192,6 +205,336 @@ __global__ void __launch_bounds__(256) spmm_scatter_scalar_kernel(
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// ---- transpose of the counts and the products over it ----
+
+__global__ void csc_count_kernel(const int32_t* __restrict__ col, int64_t nnz,
+                                 int32_t* __restrict__ cnt) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[col[e]], 1);
+}
+
+// ptr[0..d] = exclusive prefix sums of cnt[0..d-1] (ptr[d] = total), cursor = ptr[0..d-1].
+// One block: each thread sums a contiguous range, the block scans the range
+// sums, each thread writes its range.
+// cnt and cursor may be the same array (each thread reads an entry before writing it).
+__global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int32_t* cnt, int64_t d,
+                                                              int32_t* __restrict__ ptr,
+                                                              int32_t* cursor) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (d + 1023) / 1024;
+  const int64_t b = t * per, e = b + per < d ? b + per : d;
+  int64_t sum = 0;
+  for (int64_t i = b; i < e; ++i) sum += cnt[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int64_t v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = part[t] - sum;
+  for (int64_t i = b; i < e; ++i) {
+    const int32_t ci = cnt[i];
+    ptr[i] = (int32_t)run;
+    cursor[i] = (int32_t)run;
+    run += ci;
+  }
+  if (t == 1023) ptr[d] = (int32_t)part[1023];
+}
+
+// Scatter of (row, value) pairs into the transpose (one warp per CSR row).
+__global__ void __launch_bounds__(256) csc_fill_kernel(const int32_t* __restrict__ row_ptr,
+                                                       const int32_t* __restrict__ col,
+                                                       const float* __restrict__ val, int64_t rows,
+                                                       int32_t* __restrict__ cursor,
+                                                       int32_t* __restrict__ rowT,
+                                                       float* __restrict__ valT) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  for (int32_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
+    const int32_t pos = atomicAdd(&cursor[col[e]], 1);
+    rowT[pos] = (int32_t)r;
+    valT[pos] = val[e];
+  }
+}
+
+// Document lengths l_t (exact in float32), 1/l_t and 1/(l_t(l_t-1)) in float32
+// and, scaled by 1/n, in FP64 (wa, wb) for the first-moment sums.
+__global__ void __launch_bounds__(256) topic_rows_kernel(const int32_t* __restrict__ row_ptr,
+                                                         const float* __restrict__ val,
+                                                         int64_t rows, double inv_n,
+                                                         double* __restrict__ wa,
+                                                         double* __restrict__ wb,
+                                                         float* __restrict__ row_invlen,
+                                                         float* __restrict__ row_w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  float l = 0.f;
+  for (int32_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) l += val[e];
+  l = warp_sum(l);
+  if (lane == 0) {
+    const double ld = (double)l;
+    const double a = ld > 0.0 ? 1.0 / ld : 0.0, b = ld >= 2.0 ? 1.0 / (ld * (ld - 1.0)) : 0.0;
+    wa[r] = a * inv_n;
+    wb[r] = b * inv_n;
+    row_invlen[r] = (float)a;
+    row_w[r] = (float)b;
+  }
+}
+
+// M1[c] += sum_t X[t, c] wa[t] and delta[c] += sum_t X[t, c] wb[t] over the
+// transpose (M1, delta pre-zeroed), FP64.  Each warp takes kCscChunk nonzeros in
+// column order; a column it holds whole is stored, a shared one added atomically.
+__global__ void __launch_bounds__(256) topic_cols_kernel(const int32_t* __restrict__ colptr,
+                                                         const int32_t* __restrict__ rowT,
+                                                         const float* __restrict__ valT,
+                                                         int64_t d, int64_t nnz,
+                                                         const double* __restrict__ wa,
+                                                         const double* __restrict__ wb,
+                                                         double* __restrict__ M1,
+                                                         double* __restrict__ delta) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kCscChunk;
+  if (e0 >= nnz) return;
+  const int64_t e1 = e0 + kCscChunk < nnz ? e0 + kCscChunk : nnz;
+  int64_t lo = 0, hi = d - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (colptr[mid] <= e0) lo = mid; else hi = mid - 1;
+  }
+  int64_t c = lo, e = e0;
+  while (e < e1) {
+    const int64_t cb = colptr[c], ce = colptr[c + 1];
+    const int64_t se = ce < e1 ? ce : e1;
+    double a = 0.0, b = 0.0;
+    for (int64_t x = e + lane; x < se; x += 32) {
+      const int32_t r = rowT[x];
+      const double v = (double)valT[x];
+      a = fma(v, wa[r], a);
+      b = fma(v, wb[r], b);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      if (cb >= e0 && ce <= e1) {
+        M1[c] = a;
+        delta[c] = b;
+      } else {
+        atomicAdd(&M1[c], a);
+        atomicAdd(&delta[c], b);
+      }
+    }
+    e = se;
+    ++c;
+    while (c < d && colptr[c + 1] <= e) ++c;
+  }
+}
+
+// ---- blocked transpose: counting sort by word, one row block per CTA ----
+// Row block b = rows [b R, (b + 1) R), R <= 65535, so a word's count within a
+// block fits 16 bits: the CTA keeps one 16-bit counter per word in shared
+// memory (two per 32-bit word), d <= 2 x (shared memory / 4).  Pass 1 writes
+// the block's counts to bc[b][w]; a scan over blocks turns them into the
+// block's offsets within each word; pass 2 places the entries at
+// colptr[w] + bc[b][w] + (rank within the block).
+__global__ void __launch_bounds__(1024) csc_block_count_kernel(const int32_t* __restrict__ row_ptr,
+                                                               const int32_t* __restrict__ col,
+                                                               int64_t rows, int64_t R, int64_t d,
+                                                               int32_t* __restrict__ bc) {
+  extern __shared__ uint32_t cnt2[];
+  const int64_t dh = (d + 1) >> 1;
+  for (int64_t i = threadIdx.x; i < dh; i += blockDim.x) cnt2[i] = 0u;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int64_t r1 = r0 + R < rows ? r0 + R : rows;
+  const int64_t e0 = row_ptr[r0], e1 = row_ptr[r1];
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int32_t w = col[e];
+    atomicAdd(&cnt2[w >> 1], 1u << ((w & 1) * 16));
+  }
+  __syncthreads();
+  int32_t* out = bc + (int64_t)blockIdx.x * d;
+  for (int64_t w = threadIdx.x; w < d; w += blockDim.x)
+    out[w] = (int32_t)((cnt2[w >> 1] >> ((w & 1) * 16)) & 0xFFFFu);
+}
+
+// For each word: bc[b][w] <- sum_{b' < b} bc[b'][w] (in place), total[w] = the sum over all b.
+__global__ void csc_block_scan_kernel(int32_t* __restrict__ bc, int64_t nblocks, int64_t d,
+                                      int32_t* __restrict__ total) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= d) return;
+  int32_t run = 0;
+  for (int64_t b = 0; b < nblocks; ++b) {
+    const int32_t c = bc[b * d + w];
+    bc[b * d + w] = run;
+    run += c;
+  }
+  total[w] = run;
+}
+
+__global__ void __launch_bounds__(1024) csc_block_fill_kernel(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const float* __restrict__ val, int64_t rows, int64_t R, int64_t d,
+    const int32_t* __restrict__ colptr, const int32_t* __restrict__ bc, int64_t nnz,
+    int32_t* __restrict__ rowT, float* __restrict__ valT) {
+  extern __shared__ uint32_t cnt2[];
+  const int64_t dh = (d + 1) >> 1;
+  for (int64_t i = threadIdx.x; i < dh; i += blockDim.x) cnt2[i] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int64_t r1 = r0 + R < rows ? r0 + R : rows;
+  const int32_t* off = bc + (int64_t)blockIdx.x * d;
+  for (int64_t r = r0 + warp; r < r1; r += nw) {
+    for (int32_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
+      const int32_t w = col[e];
+      const uint32_t sh = (w & 1) * 16;
+      const uint32_t rank = (atomicAdd(&cnt2[w >> 1], 1u << sh) >> sh) & 0xFFFFu;
+      const int64_t pos = (int64_t)colptr[w] + off[w] + rank;
+      if (pos < nnz) {  // always, for distinct columns within each row
+        rowT[pos] = (int32_t)r;
+        valT[pos] = val[e];
+      }
+    }
+  }
+}
+
+// out[c, :] += alpha * sum_{e in column c} valT[e] * P[rowT[e], :]  (out pre-zeroed),
+// P and out with a row stride of ld4 float4, m4 float4 columns.  Warp w takes the
+// nonzeros [w kCscChunk, (w + 1) kCscChunk) in column order.
+template <int NV>
+__global__ void __launch_bounds__(256) spmm_csc_v4_kernel(
+    const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowT,
+    const float* __restrict__ valT, int64_t d, int64_t nnz, const float4* __restrict__ P,
+    int m4, int64_t ld4, float alpha, float4* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kCscChunk;
+  if (e0 >= nnz) return;
+  const int64_t e1 = e0 + kCscChunk < nnz ? e0 + kCscChunk : nnz;
+  // the column holding e0: the largest c with colptr[c] <= e0 (it is not empty)
+  int64_t lo = 0, hi = d - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (colptr[mid] <= e0) lo = mid; else hi = mid - 1;
+  }
+  int64_t c = lo, e = e0;
+  while (e < e1) {
+    const int64_t cb = colptr[c], ce = colptr[c + 1];
+    const int64_t se = ce < e1 ? ce : e1;
+    float4 acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t base = e; base < se; base += 32) {
+      const int cnt = se - base < 32 ? (int)(se - base) : 32;
+      int32_t my_r = 0;
+      float my_v = 0.f;
+      if (lane < cnt) {
+        my_r = rowT[base + lane];
+        my_v = valT[base + lane];
+      }
+#pragma unroll 4
+      for (int j = 0; j < cnt; ++j) {
+        const int32_t r = __shfl_sync(0xffffffffu, my_r, j);
+        const float v = __shfl_sync(0xffffffffu, my_v, j);
+        const float4* prow = P + (int64_t)r * ld4;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const int idx = lane + 32 * q;
+          if (idx < m4) {
+            const float4 b = __ldg(prow + idx);
+            acc[q].x = fmaf(v, b.x, acc[q].x);
+            acc[q].y = fmaf(v, b.y, acc[q].y);
+            acc[q].z = fmaf(v, b.z, acc[q].z);
+            acc[q].w = fmaf(v, b.w, acc[q].w);
+          }
+        }
+      }
+    }
+    const bool whole = cb >= e0 && ce <= e1;  // no other warp touches column c
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int idx = lane + 32 * q;
+      if (idx < m4) {
+        float4 a = acc[q];
+        a.x *= alpha; a.y *= alpha; a.z *= alpha; a.w *= alpha;
+        if (whole)
+          out[c * ld4 + idx] = a;
+        else
+          atomicAdd(out + c * ld4 + idx, a);
+      }
+    }
+    e = se;
+    ++c;
+    while (c < d && colptr[c + 1] <= e) ++c;  // skip empty columns
+  }
+}
+
+// The same over scalar columns (any m <= 32 NV): lane j holds columns j, j + 32, ...
+template <int NV>
+__global__ void __launch_bounds__(256) spmm_csc_scalar_kernel(
+    const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowT,
+    const float* __restrict__ valT, int64_t d, int64_t nnz, const float* __restrict__ P,
+    int m, float alpha, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e0 = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kCscChunk;
+  if (e0 >= nnz) return;
+  const int64_t e1 = e0 + kCscChunk < nnz ? e0 + kCscChunk : nnz;
+  int64_t lo = 0, hi = d - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (colptr[mid] <= e0) lo = mid; else hi = mid - 1;
+  }
+  int64_t c = lo, e = e0;
+  while (e < e1) {
+    const int64_t cb = colptr[c], ce = colptr[c + 1];
+    const int64_t se = ce < e1 ? ce : e1;
+    float acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.f;
+    for (int64_t base = e; base < se; base += 32) {
+      const int cnt = se - base < 32 ? (int)(se - base) : 32;
+      int32_t my_r = 0;
+      float my_v = 0.f;
+      if (lane < cnt) {
+        my_r = rowT[base + lane];
+        my_v = valT[base + lane];
+      }
+      for (int j = 0; j < cnt; ++j) {
+        const int32_t r = __shfl_sync(0xffffffffu, my_r, j);
+        const float v = __shfl_sync(0xffffffffu, my_v, j);
+        const float* prow = P + (int64_t)r * m;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const int idx = lane + 32 * q;
+          if (idx < m) acc[q] = fmaf(v, __ldg(prow + idx), acc[q]);
+        }
+      }
+    }
+    const bool whole = cb >= e0 && ce <= e1;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int idx = lane + 32 * q;
+      if (idx < m) {
+        if (whole)
+          out[c * m + idx] = alpha * acc[q];
+        else
+          atomicAdd(out + c * m + idx, alpha * acc[q]);
+      }
+    }
+    e = se;
+    ++c;
+    while (c < d && colptr[c + 1] <= e) ++c;
+  }
+}
+
 inline unsigned row_blocks(int64_t rows) {
   return (unsigned)((rows + kWarpsPerBlock - 1) / kWarpsPerBlock);
 }
@@ -280,6 +623,123 @@ otm_status spmm_scatter(const otm_csr* X, const float* P, int64_t m, const float
     spmm_scatter_scalar_kernel<<<g, T, 0, st>>>(X->row_ptr, X->col, X->val, X->rows, P, m,
                                                 row_scale, alpha, out);
   }
+  OTM_CHECK_LAUNCH();
+  return OTM_OK;
+}
+
+int smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+int64_t csc_block_rows(int64_t n) {
+  const int64_t r = (n + 1023) / 1024;  // at most 1,024 row blocks
+  return r < 2048 ? 2048 : (r > 65535 ? 65535 : r);
+}
+
+bool csc_blocked_fits(int64_t n, int64_t d) {
+  if (n > 1024 * 65535) return false;
+  return (size_t)((d + 1) / 2) * 4 + 1024 <= (size_t)smem_optin();
+}
+
+size_t csr_transpose_workspace(int64_t n, int64_t d) {
+  WorkspaceSize w;
+  w.add<int32_t>(d > 0 ? d : 1);
+  if (csc_blocked_fits(n, d)) w.add<int32_t>(((n + csc_block_rows(n) - 1) / csc_block_rows(n)) * d);
+  return w.bytes();
+}
+
+otm_status csr_transpose(const otm_csr* X, int32_t* colptr, int32_t* rowT, float* valT,
+                         void* scratch, cudaStream_t st) {
+  const int64_t d = X->cols, nnz = X->nnz, n = X->rows;
+  int32_t* cursor = static_cast<int32_t*>(scratch);
+  int32_t* bc = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(scratch) +
+                                           ((sizeof(int32_t) * (d > 0 ? d : 1) + 255) & ~size_t(255)));
+  if (n > 0 && d > 0 && nnz > 0 && csc_blocked_fits(n, d)) {
+    const int64_t R = csc_block_rows(n), nb = (n + R - 1) / R;
+    const size_t smem = (size_t)((d + 1) / 2) * 4;
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(csc_block_count_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(csc_block_fill_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    csc_block_count_kernel<<<(unsigned)nb, 1024, smem, st>>>(X->row_ptr, X->col, n, R, d, bc);
+    OTM_CHECK_LAUNCH();
+    csc_block_scan_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(bc, nb, d, cursor);
+    OTM_CHECK_LAUNCH();
+    exclusive_scan_kernel<<<1, 1024, 0, st>>>(cursor, d, colptr, cursor);
+    OTM_CHECK_LAUNCH();
+    csc_block_fill_kernel<<<(unsigned)nb, 1024, smem, st>>>(X->row_ptr, X->col, X->val, n, R, d,
+                                                            colptr, bc, nnz, rowT, valT);
+    OTM_CHECK_LAUNCH();
+    return OTM_OK;
+  }
+  OTM_CHECK_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (d > 0 ? d : 1), st));
+  if (nnz > 0) {
+    const int64_t g = (nnz + 255) / 256 < 4096 ? (nnz + 255) / 256 : 4096;
+    csc_count_kernel<<<(unsigned)g, 256, 0, st>>>(X->col, nnz, cursor);
+    OTM_CHECK_LAUNCH();
+  }
+  exclusive_scan_kernel<<<1, 1024, 0, st>>>(cursor, d, colptr, cursor);
+  OTM_CHECK_LAUNCH();
+  if (X->rows > 0 && nnz > 0) {
+    csc_fill_kernel<<<row_blocks(X->rows), 32 * kWarpsPerBlock, 0, st>>>(
+        X->row_ptr, X->col, X->val, X->rows, cursor, rowT, valT);
+    OTM_CHECK_LAUNCH();
+  }
+  return OTM_OK;
+}
+
+otm_status topic_moments_csc(const otm_csr* X, const int32_t* colptr, const int32_t* rowT,
+                             const float* valT, double* wa, double* wb, float* row_invlen,
+                             float* row_w, double* M1, double* delta, cudaStream_t st) {
+  OTM_CHECK_CUDA(cudaMemsetAsync(M1, 0, sizeof(double) * X->cols, st));
+  OTM_CHECK_CUDA(cudaMemsetAsync(delta, 0, sizeof(double) * X->cols, st));
+  if (X->rows == 0) return OTM_OK;
+  topic_rows_kernel<<<row_blocks(X->rows), 32 * kWarpsPerBlock, 0, st>>>(
+      X->row_ptr, X->val, X->rows, 1.0 / (double)X->rows, wa, wb, row_invlen, row_w);
+  OTM_CHECK_LAUNCH();
+  if (X->cols > 0 && X->nnz > 0) {
+    const int64_t warps = (X->nnz + kCscChunk - 1) / kCscChunk;
+    topic_cols_kernel<<<(unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock),
+                        32 * kWarpsPerBlock, 0, st>>>(colptr, rowT, valT, X->cols, X->nnz, wa,
+                                                      wb, M1, delta);
+    OTM_CHECK_LAUNCH();
+  }
+  return OTM_OK;
+}
+
+otm_status spmm_csc(const int32_t* colptr, const int32_t* rowT, const float* valT, int64_t d,
+                    int64_t nnz, const float* P, int64_t m, float alpha, float* out,
+                    cudaStream_t st) {
+  OTM_REQUIRE(m <= 384, "spmm_csc: m=%lld > 384", (long long)m);
+  if (nnz == 0 || m == 0 || d == 0) return OTM_OK;
+  const int64_t warps = (nnz + kCscChunk - 1) / kCscChunk;
+  const unsigned g = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const int T = 32 * kWarpsPerBlock;
+  if (m % 4 != 0 || !aligned16(P) || !aligned16(out)) {
+    const int mi = (int)m;
+    if (m <= 32)
+      spmm_csc_scalar_kernel<1><<<g, T, 0, st>>>(colptr, rowT, valT, d, nnz, P, mi, alpha, out);
+    else if (m <= 64)
+      spmm_csc_scalar_kernel<2><<<g, T, 0, st>>>(colptr, rowT, valT, d, nnz, P, mi, alpha, out);
+    else if (m <= 128)
+      spmm_csc_scalar_kernel<4><<<g, T, 0, st>>>(colptr, rowT, valT, d, nnz, P, mi, alpha, out);
+    else
+      spmm_csc_scalar_kernel<12><<<g, T, 0, st>>>(colptr, rowT, valT, d, nnz, P, mi, alpha, out);
+    OTM_CHECK_LAUNCH();
+    return OTM_OK;
+  }
+  const int m4 = (int)(m / 4);
+  auto* P4 = reinterpret_cast<const float4*>(P);
+  auto* O4 = reinterpret_cast<float4*>(out);
+  if (m4 <= 32)
+    spmm_csc_v4_kernel<1><<<g, T, 0, st>>>(colptr, rowT, valT, d, nnz, P4, m4, m4, alpha, O4);
+  else if (m4 <= 64)
+    spmm_csc_v4_kernel<2><<<g, T, 0, st>>>(colptr, rowT, valT, d, nnz, P4, m4, m4, alpha, O4);
+  else
+    spmm_csc_v4_kernel<3><<<g, T, 0, st>>>(colptr, rowT, valT, d, nnz, P4, m4, m4, alpha, O4);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }

@@ -1,9 +1,10 @@
 // Whitening (Section 3.1) by the randomised low-rank method of Section 4.2.
 //
 // Topic model: M2 of Eq. (2) is applied implicitly, M2 S = (a0+1)[(1/n) X^T
-// diag(w) (X S) - diag(delta) S] - a0 M1 (M1^T S), i.e. one gather SpMM, one
-// scatter SpMM and a fused diagonal/rank-one epilogue; the d x d matrix is
-// never formed.
+// diag(w) (X S) - diag(delta) S] - a0 M1 (M1^T S), i.e. one gather SpMM over
+// the counts, one over their transpose (formed once per call; the scatter
+// SpMM where no transpose is given) and a fused diagonal/rank-one epilogue;
+// the d x d matrix is never formed.
 //
 // Community model: Pairs(C,B) = (1/n_X) G_XC^T G_XB gets a rank-k randomised
 // SVD (the pseudo-inverses of Eqs. (7)-(8)); Z_B, Z_C and M2 of Eq. (10) are
@@ -12,7 +13,11 @@
 //   sym(M2) X = L [ (a0+1)/2 K (L_B^T X) ; (a0+1)/2 K^T (L_C^T X) ] - a0 M1 (M1^T X).
 //
 // Both then run the same range finder: Q = orth(M2 S); q times Q = orth(M2 Q);
-// Omega = Q^T M2 Q; FP64 eigendecomposition; W = Q U_k Lambda_k^{-1/2}.
+// Omega = Q^T M2 Q; FP64 eigendecomposition; W = Q U_k Lambda_k^{-1/2}.  For the
+// topic model Omega is formed as a Gram matrix, without the scatter product:
+//   Omega = (a0+1)[(1/n) R^T R - D^T D] - a0 (Q^T M1)(M1^T Q),
+//   R = diag(sqrt(w)) X Q (n x m, one gather SpMM),  D = diag(sqrt(delta)) Q,
+// symmetric by construction (w and delta are non-negative).
 //
 // The topic model also has the paper's own Nystrom form (Algorithm 2): O = M2 S
 // for a signed column selection S, Omega = S^T O, both decomposed at rank k,
@@ -32,6 +37,28 @@ __global__ void topic_m2_epilogue_kernel(float* __restrict__ O, const float* __r
   const int64_t r = idx / m, j = idx % m;
   const double v = (a0 + 1.0) * ((double)O[idx] - delta[r] * (double)S[idx]) - a0 * M1[r] * u[j];
   O[idx] = (float)v;
+}
+
+// out = diag(sqrt(delta)) Q (d x m).
+__global__ void scale_rows_sqrt_kernel(const float* __restrict__ Q, const double* __restrict__ delta,
+                                       int64_t d, int64_t m, float* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d * m) return;
+  const double w = delta[idx / m];
+  out[idx] = (float)(sqrt(w > 0.0 ? w : 0.0) * (double)Q[idx]);
+}
+
+__global__ void sqrt_f32_kernel(const float* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = sqrtf(a[i] > 0.f ? a[i] : 0.f);
+}
+
+// Om (m x m) -= a0 u u^T.
+__global__ void rank1_sub_kernel(double* __restrict__ Om, const double* __restrict__ u, int64_t m,
+                                 double a0) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  Om[idx] -= a0 * u[idx / m] * u[idx % m];
 }
 
 __global__ void concat2_kernel(const float* __restrict__ A, const float* __restrict__ B,
@@ -101,15 +128,37 @@ struct TopicOp {
   const double* M1;
   const double* delta;
   double a0;
-  float* P;   // n x m scratch
-  double* u;  // m scratch
+  float* P;    // n x m scratch
+  double* u;   // m scratch
+  float* sqw;  // n: sqrt(row_w), for rayleigh (may be null if rayleigh is not used)
+  // the transpose of X (CSR of X^T), or null: X^T P by the scatter SpMM
+  const int32_t* colptr;
+  const int32_t* rowT;
+  const float* valT;
   otm_status apply(const float* S, int64_t m, float* O, cudaStream_t st) const {
     const int64_t n = X->rows, d = X->cols;
+    const float inv_n = (float)(1.0 / (double)(n > 0 ? n : 1));
     OTM_TRY(spmm_gather(X, S, m, row_w, P, st));
     OTM_CHECK_CUDA(cudaMemsetAsync(O, 0, sizeof(float) * d * m, st));
-    OTM_TRY(spmm_scatter(X, P, m, nullptr, (float)(1.0 / (double)(n > 0 ? n : 1)), O, st));
+    if (colptr)
+      OTM_TRY(spmm_csc(colptr, rowT, valT, d, X->nnz, P, m, inv_n, O, st));
+    else
+      OTM_TRY(spmm_scatter(X, P, m, nullptr, inv_n, O, st));
     OTM_TRY(vec_tn(M1, S, d, m, u, st));
     topic_m2_epilogue_kernel<<<blocks_for(d * m), 256, 0, st>>>(O, S, delta, M1, u, d, m, a0);
+    OTM_CHECK_LAUNCH();
+    return OTM_OK;
+  }
+  // Om = Q^T M2 Q (m x m, FP64) in the Gram form; D (d x m) is scratch.
+  otm_status rayleigh(const float* Q, int64_t m, double* Om, float* D, cudaStream_t st) const {
+    const int64_t n = X->rows, d = X->cols;
+    OTM_TRY(spmm_gather(X, Q, m, sqw, P, st));
+    OTM_TRY(gemm_tn_f64acc(P, P, n, m, m, (a0 + 1.0) / (double)(n > 0 ? n : 1), Om, 0, st));
+    scale_rows_sqrt_kernel<<<blocks_for(d * m), 256, 0, st>>>(Q, delta, d, m, D);
+    OTM_CHECK_LAUNCH();
+    OTM_TRY(gemm_tn_f64acc(D, D, d, m, m, -(a0 + 1.0), Om, 1, st));
+    OTM_TRY(vec_tn(M1, Q, d, m, u, st));
+    rank1_sub_kernel<<<blocks_for(m * m), 256, 0, st>>>(Om, u, m, a0);
     OTM_CHECK_LAUNCH();
     return OTM_OK;
   }
@@ -135,6 +184,11 @@ struct CommunityOp {
     OTM_TRY(f64_to_f32(coef, coef32, 2 * k * m, st));
     OTM_TRY(gemm_nn_small(L, n_a, 2 * k, coef32, m, O, M1, u, a0, st));
     return OTM_OK;
+  }
+  // Om = Q^T (M2 Q); O (n_A x m) is scratch.
+  otm_status rayleigh(const float* Q, int64_t m, double* Om, float* O, cudaStream_t st) const {
+    OTM_TRY(apply(Q, m, O, st));
+    return gemm_tn_f64acc(Q, O, n_a, m, m, 1.0, Om, 0, st);
   }
 };
 
@@ -163,8 +217,7 @@ otm_status range_finder(const Op& op, int64_t d, const float* S, int64_t k, int6
     OTM_TRY(orthonormalize(Q, d, kt, ws, st, flags + 2, it + 1 < power_iters ? 1 : 4));
     ws.used = mark;
   }
-  OTM_TRY(op.apply(Q, kt, O, st));
-  OTM_TRY(gemm_tn_f64acc(Q, O, d, kt, kt, 1.0, Om, 0, st));
+  OTM_TRY(op.rayleigh(Q, kt, Om, O, st));
   OTM_TRY(syev(Om, kt, ev, evec, ws, st, flags + 2));
   ws.used = mark;
   OTM_TRY(whitening_factors(ev, evec, kt, k, Cw, Cp, eig, flags, st, Cw32));
@@ -218,15 +271,39 @@ size_t otm_topic_m2_workspace(int64_t n, int64_t m) {
   return w.bytes();
 }
 
-otm_status otm_topic_m2_apply(const otm_csr* X, const float* row_w, const double* M1,
-                              const double* delta, double alpha0, const float* S, int64_t m,
-                              float* O, void* ws, size_t ws_bytes, void* stream) {
+size_t otm_csr_transpose_workspace(int64_t n, int64_t d) {
+  return csr_transpose_workspace(n, d) + 256;
+}
+
+otm_status otm_csr_transpose(const otm_csr* X, int32_t* colptr, int32_t* rowT, float* valT,
+                             void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  OTM_TRY(check_csr(X, "otm_csr_transpose"));
+  OTM_REQUIRE(colptr && (X->nnz == 0 || (rowT && valT)), "otm_csr_transpose: null output");
+  Workspace w(ws, ws_bytes);
+  uint8_t* scratch = w.take<uint8_t>(csr_transpose_workspace(X->rows, X->cols));
+  OTM_REQUIRE(scratch, "otm_csr_transpose: workspace too small (need %zu bytes)",
+              otm_csr_transpose_workspace(X->rows, X->cols));
+  return csr_transpose(X, colptr, rowT, valT, scratch, as_stream(stream));
+}
+
+otm_status otm_topic_m2_apply(const otm_csr* X, const otm_csr* Xt, const float* row_w,
+                              const double* M1, const double* delta, double alpha0,
+                              const float* S, int64_t m, float* O, void* ws, size_t ws_bytes,
+                              void* stream) {
   clear_error();
   OTM_TRY(check_csr(X, "otm_topic_m2_apply"));
   OTM_REQUIRE(m >= 1 && row_w && M1 && delta && S && O, "otm_topic_m2_apply: bad arguments");
   OTM_REQUIRE(S != O, "otm_topic_m2_apply: O must not alias S");
+  if (Xt) {
+    OTM_TRY(check_csr(Xt, "otm_topic_m2_apply (Xt)"));
+    OTM_REQUIRE(Xt->rows == X->cols && Xt->cols == X->rows && Xt->nnz == X->nnz,
+                "otm_topic_m2_apply: Xt is not the transpose of X (shape or nnz)");
+    OTM_REQUIRE(m <= 384, "otm_topic_m2_apply: with Xt, m must be at most 384");
+  }
   Workspace w(ws, ws_bytes);
-  TopicOp op{X, row_w, M1, delta, alpha0, w.take<float>(X->rows * m), w.take<double>(m)};
+  TopicOp op{X, row_w, M1, delta, alpha0, w.take<float>(X->rows * m), w.take<double>(m), nullptr,
+             Xt ? Xt->row_ptr : nullptr, Xt ? Xt->col : nullptr, Xt ? Xt->val : nullptr};
   OTM_REQUIRE(op.P && op.u, "otm_topic_m2_apply: workspace too small (need %zu bytes)",
               otm_topic_m2_workspace(X->rows, m));
   return op.apply(S, m, O, as_stream(stream));
@@ -251,10 +328,12 @@ otm_status otm_pairs_apply(const otm_csr* G1, const otm_csr* G2, const float* S,
   return pairs_apply_ws(G1, G2, S, m, O, tmp, as_stream(stream));
 }
 
-size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t k, int64_t kt) {
+size_t otm_whiten_topic_workspace(int64_t n, int64_t d, int64_t nnz, int64_t k, int64_t kt) {
   (void)k;
   WorkspaceSize w;
-  w.add<double>(d).add<float>(n * kt).add<double>(kt).add<int>(kFlags);
+  w.add<double>(d).add<float>(n * kt).add<double>(kt).add<int>(kFlags).add<float>(n);
+  w.add<int32_t>(d + 1).add<int32_t>(nnz).add<float>(nnz);                  // transpose
+  w.add<uint8_t>(csr_transpose_workspace(n, d)).add<double>(n).add<double>(n);  // its scratch, wa, wb
   return w.bytes() + range_finder_ws(d, kt);
 }
 
@@ -272,18 +351,28 @@ otm_status otm_whiten_topic(const otm_csr* X, const float* S, int64_t k, int64_t
   OTM_REQUIRE(alpha0 >= 0.0, "otm_whiten_topic: alpha0 must be >= 0");
   OTM_REQUIRE(S && W && Q && Cw && Cp && eig && M1 && row_invlen && row_w,
               "otm_whiten_topic: null output");
-  OTM_REQUIRE(ws_bytes >= otm_whiten_topic_workspace(X->rows, X->cols, k, kt),
+  OTM_REQUIRE(ws_bytes >= otm_whiten_topic_workspace(X->rows, X->cols, X->nnz, k, kt),
               "otm_whiten_topic: workspace too small (need %zu bytes)",
-              otm_whiten_topic_workspace(X->rows, X->cols, k, kt));
+              otm_whiten_topic_workspace(X->rows, X->cols, X->nnz, k, kt));
   cudaStream_t st = as_stream(stream);
   Workspace w(ws, ws_bytes);
   double* delta = w.take<double>(X->cols);
   float* P = w.take<float>(X->rows * kt);
   double* u = w.take<double>(kt);
   int* flags = w.take<int>(kFlags);
+  float* sqw = w.take<float>(X->rows);
+  int32_t* colptr = w.take<int32_t>(X->cols + 1);
+  int32_t* rowT = w.take<int32_t>(X->nnz);
+  float* valT = w.take<float>(X->nnz);
+  uint8_t* tscratch = w.take<uint8_t>(csr_transpose_workspace(X->rows, X->cols));
+  double* wa = w.take<double>(X->rows);
+  double* wb = w.take<double>(X->rows);
   OTM_CHECK_CUDA(cudaMemsetAsync(flags, 0, kFlags * sizeof(int), st));
-  OTM_TRY(topic_moments(X, row_invlen, row_w, M1, delta, st));
-  TopicOp op{X, row_w, M1, delta, alpha0, P, u};
+  OTM_TRY(csr_transpose(X, colptr, rowT, valT, tscratch, st));
+  OTM_TRY(topic_moments_csc(X, colptr, rowT, valT, wa, wb, row_invlen, row_w, M1, delta, st));
+  sqrt_f32_kernel<<<blocks_for(X->rows), 256, 0, st>>>(row_w, sqw, X->rows);
+  OTM_CHECK_LAUNCH();
+  TopicOp op{X, row_w, M1, delta, alpha0, P, u, sqw, colptr, rowT, valT};
   OTM_TRY(range_finder(op, X->cols, S, k, kt, power_iters, W, Q, Cw, Cp, eig, w, st, flags));
   return check_flags(flags, st, "otm_whiten_topic");
 }

@@ -70,7 +70,10 @@ _SIGS = {
     "otm_launch_count": [],
     "otm_topic_moments": [_P, c_vp, c_vp, c_vp, c_vp, c_vp],
     "otm_topic_m2_workspace": [c_i64, c_i64],
-    "otm_topic_m2_apply": [_P, c_vp, c_vp, c_vp, c_f64, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp],
+    "otm_topic_m2_apply": [_P, _P, c_vp, c_vp, c_vp, c_f64, c_vp, c_i64, c_vp, c_vp, c_sz,
+                           c_vp],
+    "otm_csr_transpose_workspace": [c_i64, c_i64],
+    "otm_csr_transpose": [_P, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
     "otm_pairs_workspace": [c_i64, c_i64],
     "otm_pairs_apply": [_P, _P, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp],
     "otm_orth_workspace": [c_i64],
@@ -78,7 +81,7 @@ _SIGS = {
     "otm_syev_workspace": [c_i64],
     "otm_syev": [c_vp, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp],
     "otm_syev_noalloc": [c_vp, c_i64, c_vp, c_vp, c_vp],
-    "otm_whiten_topic_workspace": [c_i64, c_i64, c_i64, c_i64],
+    "otm_whiten_topic_workspace": [c_i64, c_i64, c_i64, c_i64, c_i64],
     "otm_whiten_topic": [_P, c_vp, c_i64, c_i64, ctypes.c_int, c_f64, c_vp, c_vp, c_vp, c_vp,
                          c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp],
     "otm_whiten_topic_nystrom_workspace": [c_i64, c_i64, c_i64, c_i64],
@@ -254,13 +257,27 @@ def topic_moments(X: DeviceCSR) -> dict:
     return out
 
 
-def topic_m2_apply(X: DeviceCSR, moments: dict, alpha0: float, S):
+def csr_transpose(X: DeviceCSR) -> DeviceCSR:
+    """The CSR of X^T (d x n); within a word the documents come in no fixed order."""
+    n, d = X.shape
+    dev = X.device
+    colptr = torch.empty(d + 1, dtype=torch.int32, device=dev)
+    rowT = torch.empty(X.nnz, dtype=torch.int32, device=dev)
+    valT = torch.empty(X.nnz, dtype=torch.float32, device=dev)
+    ws = _ws(_lib.otm_csr_transpose_workspace(n, d), dev)
+    _check(_lib.otm_csr_transpose(X.ref(), _ptr(colptr), _ptr(rowT), _ptr(valT), _ptr(ws),
+                                  ws.numel(), _stream()))
+    return DeviceCSR(colptr, rowT, valT, (d, n))
+
+
+def topic_m2_apply(X: DeviceCSR, moments: dict, alpha0: float, S, Xt: DeviceCSR = None):
     n, d = X.shape
     m = S.shape[1]
     _need(S, torch.float32, (d, m), "S")
     O = torch.empty_like(S)
     ws = _ws(_lib.otm_topic_m2_workspace(n, m), S.device)
-    _check(_lib.otm_topic_m2_apply(X.ref(), _ptr(moments["row_w"]), _ptr(moments["M1"]),
+    _check(_lib.otm_topic_m2_apply(X.ref(), Xt.ref() if Xt is not None else None,
+                                   _ptr(moments["row_w"]), _ptr(moments["M1"]),
                                    _ptr(moments["delta"]), float(alpha0), _ptr(S), m, _ptr(O),
                                    _ptr(ws), ws.numel(), _stream()))
     return O
@@ -316,7 +333,7 @@ def whiten_topic(X: DeviceCSR, S, k: int, power_iters: int, alpha0: float) -> di
          "eig": torch.empty(k, dtype=f64, device=dev), "M1": torch.empty(d, dtype=f64, device=dev),
          "row_invlen": torch.empty(n, dtype=f32, device=dev),
          "row_w": torch.empty(n, dtype=f32, device=dev)}
-    ws = _ws(_lib.otm_whiten_topic_workspace(n, d, k, kt), dev)
+    ws = _ws(_lib.otm_whiten_topic_workspace(n, d, X.nnz, k, kt), dev)
     _check(_lib.otm_whiten_topic(X.ref(), _ptr(S), k, kt, int(power_iters), float(alpha0),
                                  _ptr(o["W"]), _ptr(o["Q"]), _ptr(o["Cw"]), _ptr(o["Cp"]),
                                  _ptr(o["eig"]), _ptr(o["M1"]), _ptr(o["row_invlen"]),

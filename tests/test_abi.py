@@ -84,10 +84,11 @@ def test_csr_validation(lib):
 
 def test_workspace_sizes_monotone(lib):
     lib.otm_whiten_topic_workspace.restype = ctypes.c_size_t
-    lib.otm_whiten_topic_workspace.argtypes = [ctypes.c_int64] * 4
-    a = lib.otm_whiten_topic_workspace(100, 50, 5, 10)
-    b = lib.otm_whiten_topic_workspace(1000, 500, 5, 10)
-    assert 0 < a < b
+    lib.otm_whiten_topic_workspace.argtypes = [ctypes.c_int64] * 5
+    a = lib.otm_whiten_topic_workspace(100, 50, 400, 5, 10)
+    b = lib.otm_whiten_topic_workspace(1000, 500, 400, 5, 10)
+    c = lib.otm_whiten_topic_workspace(1000, 500, 4000, 5, 10)
+    assert 0 < a < b < c
 
 
 def test_host_side_errors_of_membership_validation_and_nystrom(lib):

@@ -92,6 +92,58 @@ def test_topic_m2_apply(otm, m):
     assert rel(to_np(O), ref) < 1e-5
 
 
+@pytest.mark.parametrize("m", [32, 120, 200])
+def test_topic_m2_apply_over_transpose(otm, m):
+    """X^T P as a gather over the transpose (the form the topic whitening uses)
+    against the oracle: 3,000 documents with word 0 in every one (a column
+    spread over a dozen warps of 256 nonzeros, summed with atomics), words 1-9
+    in none (empty columns), empty and one-word documents, m of one to two
+    float4 per lane."""
+    c = _corpus(15, 3000, 400, 8, 40)
+    dense = synth.csr_to_dense(c["X"])
+    dense[:, 0] += 2.0
+    dense[:, 1:10] = 0.0
+    dense[5] = 0.0
+    dense[6] = 0.0
+    dense[6, 17] = 1.0
+    X = synth.csr_from_dense(dense)
+    S = synth.gaussian(16, 400, m)
+    Xd = otm.DeviceCSR.from_host(X)
+    mom = otm.topic_moments(Xd)
+    Xt = otm.csr_transpose(Xd)
+    O = otm.topic_m2_apply(Xd, mom, 1.0, _dev(S), Xt=Xt)
+    torch.cuda.synchronize()
+    ref = om.topic_second_moment_apply(X, S.astype(np.float64), 1.0)
+    assert rel(to_np(O), ref) < 1e-5
+    # every row (word) on its own, the empty ones included
+    err = np.linalg.norm(to_np(O) - ref, axis=1)
+    assert np.all(err <= 1e-5 * np.linalg.norm(ref, axis=1) + 1e-6 * np.linalg.norm(ref) / 20)
+
+
+def test_csr_transpose_matches_scipy(otm):
+    """colptr exact; per word the (document, count) pairs as a set (their order
+    within a word is not fixed)."""
+    sp = pytest.importorskip("scipy.sparse")
+    c = _corpus(17, 2000, 300, 6, 50)
+    dense = synth.csr_to_dense(c["X"])
+    dense[:, 3] = 1.0          # a word in every document
+    dense[:, 7] = 0.0          # a word in none
+    dense[11] = 0.0            # an empty document
+    X = synth.csr_from_dense(dense)
+    Xt = otm.csr_transpose(otm.DeviceCSR.from_host(X))
+    torch.cuda.synchronize()
+    ref = sp.csr_matrix((X.val, X.col, X.row_ptr), shape=X.shape).T.tocsr()
+    ref.sort_indices()
+    cp, rt, vt = to_np(Xt.row_ptr), to_np(Xt.col), to_np(Xt.val)
+    assert Xt.shape == (300, 2000)
+    np.testing.assert_array_equal(cp, ref.indptr)
+    for w in range(300):
+        a, b = cp[w], cp[w + 1]
+        o = np.argsort(rt[a:b], kind="stable")
+        np.testing.assert_array_equal(rt[a:b][o], ref.indices[a:b])
+        np.testing.assert_array_equal(vt[a:b][o], ref.data[a:b])
+
+
 def test_pairs_apply(otm):
     g = synth.mmsb_graph(7, 600, 8, 0.05, 0.3, 0.02)
     S = synth.gaussian(8, 600, 28)
@@ -287,3 +339,17 @@ def test_recon_error(otm, k):
     torch.cuda.synchronize()
     ref = opost.recon_error_from_V(V.astype(np.float64), 1.0, lam, U)
     assert abs(float(to_np(err)[0]) - ref) < 1e-9 * max(ref, 1e-3)
+
+
+def test_recon_error_of_diverged_components_is_nan(otm):
+    """A diverged iterate (inf or NaN in V) reports NaN, not a clamped zero."""
+    k = 8
+    g = np.random.default_rng(3)
+    U = np.linalg.qr(g.standard_normal((k, k)))[0]
+    lam = g.uniform(1, 3, k)
+    for bad in (np.inf, np.nan):
+        V = (lam ** (1 / 3) * U).astype(np.float32)
+        V[2, 5] = bad
+        err = otm.recon_error(_dev(V.T.copy()), _dev(U.T.copy()), _dev(lam), 1.0)
+        torch.cuda.synchronize()
+        assert np.isnan(float(to_np(err)[0]))

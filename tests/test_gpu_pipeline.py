@@ -60,6 +60,10 @@ def test_whiten_topic_matches_oracle(otm, lda1):
     assert np.abs(W.T @ M2 @ W - np.eye(10)).max() < 1e-3
     assert _subspace_gap(to_np(wh["Q"]).astype(np.float64), ref["Q"]) < 1e-3
     np.testing.assert_allclose(to_np(wh["M1"]), om.topic_first_moment(X), rtol=1e-12)
+    # the per-document weights of the whitening's moments equal the standalone call's
+    mom = otm.topic_moments(otm.DeviceCSR.from_host(X))
+    np.testing.assert_array_equal(to_np(wh["row_invlen"]), to_np(mom["row_invlen"]))
+    np.testing.assert_array_equal(to_np(wh["row_w"]), to_np(mom["row_w"]))
     # factored forms: W = Q Cw and (W^T)^+ = Q Cp
     Q = to_np(wh["Q"]).astype(np.float64)
     assert rel(Q @ to_np(wh["Cw"]), W) < 1e-6
