@@ -395,10 +395,12 @@ def project(X: DeviceCSR, W, row_scale=None):
     return Y
 
 
-def column_mean(Y):
+def column_mean(Y, out=None):
+    """ybar (k, float64); written into `out` (a contiguous float64 k-vector) if given."""
     n, k = Y.shape
     _need(Y, torch.float32, (n, k), "Y")
-    yb = torch.empty(k, dtype=torch.float64, device=Y.device)
+    yb = torch.empty(k, dtype=torch.float64, device=Y.device) if out is None else out
+    _need(yb, torch.float64, (k,), "out")
     _check(_lib.otm_column_mean(_ptr(Y), n, k, _ptr(yb), _stream()))
     return yb
 
