@@ -21,9 +21,12 @@
 // a_A, a_B) to the iterate buffer of the next step.  Grid barrier.  Every CTA
 // reloads V from that buffer at the start of the next step.  Two grid
 // barriers per step; the partial sums are added in a fixed order, so the
-// result does not depend on timing.
+// result does not depend on timing.  The samples of step s + 1 do not depend
+// on V: they are copied (cp.async) into a second buffer at the start of step
+// s and land while step s computes and waits at its barriers.
 #include "grid_sync.cuh"
 #include "otm_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace otm {
 namespace {
@@ -34,7 +37,6 @@ constexpr int G_SMAX = 32;    // at most this many samples per CTA per step
 constexpr int G_KMAX = 128;
 constexpr int G_MAXGRID = 160;  // CTAs at most (the owners' sums load G / 8 partials at once)
 constexpr int VQ = (G_KMAX * (G_KMAX + 4) / 4 + GT - 1) / GT;  // float4 of V per thread
-constexpr int YQ = (3 * G_SMAX * (G_KMAX / 4) + GT - 1) / GT;  // float4 of samples per thread
 constexpr int RQ = G_MAXGRID / 8;                              // partials per thread
 
 struct GridArgs {
@@ -74,7 +76,7 @@ __host__ __device__ inline GLayout g_layout(int k, bool sym, int S) {
   L.S = S;
   size_t f = 0;
   L.off_v = f;   f += (size_t)L.kp * L.ld;          // V, component rows
-  L.off_y = f;   f += (size_t)L.nview * S * L.ld;   // this CTA's samples [view][t]
+  L.off_y = f;   f += 2 * (size_t)L.nview * S * L.ld;  // this CTA's samples [step parity][view][t]
   L.off_b = f;   f += (size_t)S * L.kp;             // B [t][i]
   L.off_p = f;   f += (size_t)S * L.kp;             // A_A o A_B [t][i]
   L.off_yb = f;  f += 3 * (size_t)L.ld;             // ybar_A, ybar_B, ybar_C
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
   // on a barrier time-out the owned columns of V are set to NaN (the caller
   // sees the failure in the result) and the CTA returns
   auto fail = [&]() {
+    tc::cp_async_wait(0);  // no copy into shared memory outlives the CTA
     for (int i = g; i < k; i += G)
       for (int r = tid; r < k; r += GT) a.V[(int64_t)i * k + r] = __int_as_float(0x7fc00000);
   };
@@ -157,8 +160,33 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     const int64_t row = a.perm ? (int64_t)a.perm[e * a.n + pos0 + p] : pos0 + p;
     return (row >= 0 && row < a.n) ? (int)row : -1;
   };
+  // copies of the samples of a step into buffer `buf` (zero rows outside the
+  // minibatch); one cp.async group per call
+  const size_t ybuf = (size_t)L.nview * S * ld;
+  auto issue_samples = [&](int buf) {
+    float* dstb = Ys + (size_t)buf * ybuf;
+    const int ny = L.nview * S * kq;
+#pragma unroll 1
+    for (int idx = tid; idx < ny; idx += GT) {
+      const int v = idx / (S * kq), rem = idx % (S * kq), t = rem / kq, r = 4 * (rem % kq);
+      const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
+      const int row = s_row[buf][t];
+      float* dst = dstb + ((size_t)v * S + t) * ld + r;
+      const float* src = row >= 0 ? Yg + (int64_t)row * k + r : Yg;
+      if (a.vec) {
+        tc::cp_async16(dst, src, row >= 0 ? 16u : 0u);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          tc::cp_async4(dst + j, row >= 0 && r + j < k ? src + j : Yg,
+                        row >= 0 && r + j < k ? 4u : 0u);
+      }
+    }
+    tc::cp_async_commit();
+  };
   if (tid < S) s_row[0][tid] = row_of(0, tid);
   __syncthreads();
+  issue_samples(0);
   for (int i = warp; i < kp; i += GT / 32) {  // a_A, a_B of the initial V
     float x = 0.f, y = 0.f;
     for (int r = lane; r < kp; r += 32) {
@@ -182,38 +210,17 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     float* Mnext = a.means + (size_t)(par ^ 1) * 2 * kp;
     const int64_t pos0 = (s % a.spe) * a.b;
     const int64_t beff = min(a.b, a.n - pos0);
-    // the iterate the owners wrote in the previous step, its means and this
-    // CTA's samples: every load is issued before any store
+    // rows of the next step's samples; the iterate the owners wrote in the
+    // previous step and its means (every load issued before any store)
+    if (tid < S) s_row[par ^ 1][tid] = row_of(s + 1, tid);
     {
-      float4 vv[VQ], yy[YQ];
+      float4 vv[VQ];
       const int nv4 = s > 0 ? kp * ld / 4 : 0;
       const float4* src = reinterpret_cast<const float4*>(a.Vg + (size_t)par * kp * ld);
 #pragma unroll
       for (int c = 0; c < VQ; ++c) {
         const int idx = tid + c * GT;
         if (idx < nv4) vv[c] = __ldcg(src + idx);
-      }
-      const int ny = L.nview * S * kq;
-#pragma unroll
-      for (int c = 0; c < YQ; ++c) {
-        const int idx = tid + c * GT;
-        yy[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < ny) {
-          const int v = idx / (S * kq), rem = idx % (S * kq), t = rem / kq, r = 4 * (rem % kq);
-          const float* Yg = v == 0 ? a.YA : (v == 1 ? a.YB : a.YC);
-          const int row = s_row[par][t];
-          if (row >= 0) {
-            const float* src_y = Yg + (int64_t)row * k + r;
-            if (a.vec) {
-              yy[c] = __ldg(reinterpret_cast<const float4*>(src_y));
-            } else {
-              yy[c].x = __ldg(src_y);
-              yy[c].y = r + 1 < k ? __ldg(src_y + 1) : 0.f;
-              yy[c].z = r + 2 < k ? __ldg(src_y + 2) : 0.f;
-              yy[c].w = r + 3 < k ? __ldg(src_y + 3) : 0.f;
-            }
-          }
-        }
       }
       if (s > 0) {
         const float* msrc = a.means + (size_t)par * 2 * kp;
@@ -225,23 +232,19 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
         const int idx = tid + c * GT;
         if (idx < nv4) dst[idx] = vv[c];
       }
-#pragma unroll
-      for (int c = 0; c < YQ; ++c) {
-        const int idx = tid + c * GT;
-        if (idx < ny) {
-          const int v = idx / (S * kq), rem = idx % (S * kq), t = rem / kq, r = 4 * (rem % kq);
-          *reinterpret_cast<float4*>(Ys + ((size_t)v * S + t) * ld + r) = yy[c];
-        }
-      }
     }
+    __syncthreads();  // s_row of the next step
+    issue_samples(par ^ 1);
+    tc::cp_async_wait(1);  // this step's samples (issued one step earlier) have landed
     __syncthreads();
+    const float* Yst = Ys + (size_t)par * ybuf;
 
     // A_A, A_B for 4 components x 1 sample per item (consecutive threads take
     // consecutive samples), then B and A_A o A_B
     for (int item = tid; item < S * kq; item += GT) {
       const int t = item % S, i0 = 4 * (item / S);
-      const float* ya = Ys + (size_t)t * ld;
-      const float* yb = SYM ? ya : Ys + ((size_t)S + t) * ld;
+      const float* ya = Yst + (size_t)t * ld;
+      const float* yb = SYM ? ya : Yst + ((size_t)S + t) * ld;
       float xa[4] = {0.f, 0.f, 0.f, 0.f}, xb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
       for (int r = 0; r < kp; r += 4) {
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     }
     {
       float* pg = a.part + (size_t)g * kp * ld;
-      const float* yc = SYM ? Ys : Ys + 2 * (size_t)S * ld;
+      const float* yc = SYM ? Yst : Yst + 2 * (size_t)S * ld;
       for (int tile = tid; tile < kq * kq; tile += GT) {
         const int r0 = 4 * (tile % kq), i0 = 4 * (tile / kq);
         float4 acc[4];
@@ -405,12 +408,12 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
         __syncthreads();  // shared scratch is reused by the next owned column
       }
     }
-    if (tid < S) s_row[par ^ 1][tid] = row_of(s + 1, tid);
     if (!grid_barrier(a.bar, a.flag, 1)) {
       fail();
       return;
     }
   }
+  tc::cp_async_wait(0);  // the last (empty) prefetch
 }
 
 unsigned grid_sms() {
