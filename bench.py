@@ -1647,6 +1647,69 @@ def run_stgd(args):
             "gpu_launches": args.steps, "clocks": clocks}
 
 
+def run_topic_exact(args):
+    """The STGD on the whole third moment of Eq. (3) (self-token terms kept) on the
+    default line's corpus, W and M1 from its whitening (untimed), one epoch of
+    b = 1,024 documents from the default line's start; L2 flushed before each
+    run.  Algorithmic FP32 work per step: 2 k^2 per word occurrence for U = W_g V^T,
+    2 k^2 per occurrence and 2 k^2 per document for W_g^T Coef + Y'^T A, plus the
+    Gram term 4 k^3 (the sample tensor's 4 k^2 per document for comparison)."""
+    import torch
+    from paper_1309_0787_gb300 import otm
+    c = dict(LDA)
+    dev = torch.device("cuda", 0)
+    host = lda_inputs(c, 0)
+    path = LdaPath(otm, torch, c, host, dev)
+    wh, Y, yb3 = path.front()
+    n, k, b = Y.shape[0], c["k"], c["b"]
+    a0 = k * c["alpha_i"]
+    perm = path.perm[:1].contiguous()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one():
+        V = path.V0t.clone()
+        otm.sgd_run_topic_exact(V, path.Xd, wh["W"], wh["M1"], perm, 1, b, c["beta0"],
+                                c["theta"], a0)
+        return V
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        V = one()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    t = statistics.median(ms) / 1e3
+    nnz = int(host["X"].row_ptr[-1])
+    nsteps = (n + b - 1) // b
+    flops = 4.0 * k * k * nnz + 2.0 * k * k * n + nsteps * 4.0 * k ** 3
+    finite = bool(torch.isfinite(V).all())
+    return {"metric": "exact-topic STGD throughput (documents/s), whole Eq. (3)",
+            "value": n / t, "unit": "documents/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 accumulation)",
+            "data": "synthetic",
+            "config": {"workload": "stgd_exact_topic_lda_300000x100000_k100_b1024", "docs": n,
+                       "nnz": nnz, "k": k, "minibatch": b, "epochs": 1, "sgd_steps": nsteps,
+                       "l2": "flushed before each run (256 MiB write)"},
+            "us_per_sgd_step": 1e6 * t / nsteps, "result_finite": finite,
+            "roofline": {"kernel": "sgd_run_topic_exact (gather, U = W_g V^T, coefficients, "
+                                   "W_g^T Coef + Y'^T A, update per step)",
+                         "bound": "alu", "achieved": flops / t / 1e12,
+                         "peak": FP32_FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops / t / 1e12 / FP32_FMA_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                         "algorithmic_flops_per_run": flops},
+            "clocks": clocks}
+
+
 def run_projection(args):
     """The projection y_t = W^T c_t / l_t (Section 3.1) alone, on the default
     line's corpus with a random W (d x k, float32): the gather SpMM's time and
@@ -1711,6 +1774,7 @@ def main():
                     help="batched: skip the time-to-1e-3 comparison")
     ap.add_argument("--workload", default="lda",
                     choices=["lda", "mmsb", "batched", "warmstart", "whitening", "projection",
+                             "topic_exact",
                              "stgd"],
                     help="lda: the default line (300,000-document LDA corpus, whole path); "
                          "mmsb: the community-model pipeline; batched: the batched form; "
@@ -1735,6 +1799,8 @@ def main():
         line = run_whitening(args) if rank == 0 else None
     elif args.workload == "projection":
         line = run_projection(args) if rank == 0 else None
+    elif args.workload == "topic_exact":
+        line = run_topic_exact(args) if rank == 0 else None
     elif args.workload == "stgd":
         line = run_stgd(args) if rank == 0 else None
     elif args.impl == "reference":
