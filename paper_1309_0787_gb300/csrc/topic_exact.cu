@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(1024) te_offsets_kernel(const int32_t* __restr
 
 // One warp per minibatch document: its occurrences' rows of W into W_g and
 // their counts into cnt, y'_t = W^T c_t into Yp (FP32 sums), l_t into len.
+// The (word, count) pairs come 32 at a time (one coalesced load, broadcast by
+// shuffles), so the W-row loads of consecutive occurrences are independent.
 // Writes nothing past cap occurrences.
 __global__ void __launch_bounds__(256) te_gather_kernel(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -102,20 +104,31 @@ __global__ void __launch_bounds__(256) te_gather_kernel(
   if (doc[t] >= 0) {
     const int32_t e0 = row_ptr[doc[t]], e1 = row_ptr[doc[t] + 1];
     const int64_t o = off[t];
-    for (int32_t e = e0; e < e1; ++e) {
-      const int32_t j = col[e];
-      const float c = val[e];
-      const int64_t g = o + (e - e0);
-      l += c;
-      const bool keep = g < cap;
-      if (keep && lane == 0) cnt[g] = c;
+    for (int32_t base = e0; base < e1; base += 32) {
+      const int cntb = e1 - base < 32 ? e1 - base : 32;
+      int32_t my_j = 0;
+      float my_c = 0.f;
+      if (lane < cntb) {
+        my_j = col[base + lane];
+        my_c = val[base + lane];
+        const int64_t g = o + (base + lane - e0);
+        if (g < cap) cnt[g] = my_c;
+      }
+#pragma unroll 4
+      for (int x = 0; x < cntb; ++x) {
+        const int32_t j = __shfl_sync(0xffffffffu, my_j, x);
+        const float c = __shfl_sync(0xffffffffu, my_c, x);
+        const int64_t g = o + (base + x - e0);
+        l += c;
+        const bool keep = g < cap;
 #pragma unroll
-      for (int q = 0; q < TE_KMAX / 32; ++q) {
-        const int r = lane + 32 * q;
-        if (r < k) {
-          const float w = W[(int64_t)j * k + r];
-          acc[q] = fmaf(c, w, acc[q]);
-          if (keep) Wg[g * k + r] = w;
+        for (int q = 0; q < TE_KMAX / 32; ++q) {
+          const int r = lane + 32 * q;
+          if (r < k) {
+            const float w = __ldg(W + (int64_t)j * k + r);
+            acc[q] = fmaf(c, w, acc[q]);
+            if (keep) Wg[g * k + r] = w;
+          }
         }
       }
     }
@@ -143,14 +156,31 @@ __global__ void __launch_bounds__(TE_KMAX) te_coef_kernel(
   const double L2 = l >= 2.0 ? l * (l - 1.0) : 0.0;
   const double L3 = l >= 3.0 ? l * (l - 1.0) * (l - 2.0) : 0.0;
   // s = <y'_t, v_i> and q over the document's occurrences, summed in FP64: s^2 - q
-  // (the pairs of distinct tokens) cancels the self-pairs
-  double sd = 0.0;
-  for (int r = 0; r < k; ++r) sd += (double)Yp[t * k + r] * (double)V[i * k + r];
-  double qd = 0.0;
-  for (int64_t e = e0; e < e1; ++e) {
-    const double u = U[e * k + i];
-    qd += (double)cnt[e] * u * u;
+  // (the pairs of distinct tokens) cancels the self-pairs.  Four partial sums
+  // each, so that the dependent FP64 chains and the loads overlap.
+  double s4[4] = {0.0, 0.0, 0.0, 0.0};
+  int r = 0;
+  for (; r + 4 <= k; r += 4) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+      s4[x] = fma((double)Yp[t * k + r + x], (double)V[i * k + r + x], s4[x]);
   }
+  for (; r < k; ++r) s4[0] = fma((double)Yp[t * k + r], (double)V[i * k + r], s4[0]);
+  const double sd = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+  double q4[4] = {0.0, 0.0, 0.0, 0.0};
+  int64_t e = e0;
+  for (; e + 4 <= e1; e += 4) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const double u = U[(e + x) * k + i];
+      q4[x] = fma((double)cnt[e + x] * u, u, q4[x]);
+    }
+  }
+  for (; e < e1; ++e) {
+    const double u = U[e * k + i];
+    q4[0] = fma((double)cnt[e] * u, u, q4[0]);
+  }
+  const double qd = (q4[0] + q4[1]) + (q4[2] + q4[3]);
   const double mi = mu[i];
   const double i3 = L3 > 0.0 ? 1.0 / L3 : 0.0, i2 = L2 > 0.0 ? 1.0 / L2 : 0.0;
   const double a = c1 * (sd * sd - qd) * i3 - 2.0 * c2 * mi * sd * i2;
@@ -160,9 +190,10 @@ __global__ void __launch_bounds__(TE_KMAX) te_coef_kernel(
   A[t * k + i] = (float)a;
   atomicAdd(&esum[i], ec);
   const float bf = (float)bc, gf = (float)g;
-  for (int64_t e = e0; e < e1; ++e) {
-    const float u = U[e * k + i];
-    U[e * k + i] = cnt[e] * u * fmaf(gf, u, bf);
+#pragma unroll 4
+  for (int64_t x = e0; x < e1; ++x) {
+    const float u = U[x * k + i];
+    U[x * k + i] = cnt[x] * u * fmaf(gf, u, bf);
   }
 }
 

@@ -120,28 +120,48 @@ def test_topic_m2_apply_over_transpose(otm, m):
     assert np.all(err <= 1e-5 * np.linalg.norm(ref, axis=1) + 1e-6 * np.linalg.norm(ref) / 20)
 
 
-def test_csr_transpose_matches_scipy(otm):
-    """colptr exact; per word the (document, count) pairs as a set (their order
-    within a word is not fixed)."""
+def _check_transpose(otm, X):
     sp = pytest.importorskip("scipy.sparse")
-    c = _corpus(17, 2000, 300, 6, 50)
+    Xt = otm.csr_transpose(otm.DeviceCSR.from_host(X))
+    torch.cuda.synchronize()
+    n, d = X.shape
+    ref = sp.csr_matrix((X.val, X.col, X.row_ptr), shape=X.shape).T.tocsr()
+    ref.sort_indices()
+    cp, rt, vt = to_np(Xt.row_ptr), to_np(Xt.col), to_np(Xt.val)
+    assert Xt.shape == (d, n)
+    np.testing.assert_array_equal(cp, ref.indptr)
+    # per word the (document, count) pairs as a set: order them by document
+    key = np.repeat(np.arange(d, dtype=np.int64), np.diff(cp)) * (n + 1) + rt
+    o = np.argsort(key, kind="stable")
+    np.testing.assert_array_equal(rt[o], ref.indices)
+    np.testing.assert_array_equal(vt[o], ref.data)
+
+
+@pytest.mark.parametrize("n", [2000, 5000])
+def test_csr_transpose_matches_scipy(otm, n):
+    """colptr exact; per word the (document, count) pairs as a set (their order
+    within a word is not fixed); 5,000 documents span three row blocks of the
+    counting sort."""
+    c = _corpus(17, n, 300, 6, 50)
     dense = synth.csr_to_dense(c["X"])
     dense[:, 3] = 1.0          # a word in every document
     dense[:, 7] = 0.0          # a word in none
     dense[11] = 0.0            # an empty document
-    X = synth.csr_from_dense(dense)
-    Xt = otm.csr_transpose(otm.DeviceCSR.from_host(X))
-    torch.cuda.synchronize()
-    ref = sp.csr_matrix((X.val, X.col, X.row_ptr), shape=X.shape).T.tocsr()
-    ref.sort_indices()
-    cp, rt, vt = to_np(Xt.row_ptr), to_np(Xt.col), to_np(Xt.val)
-    assert Xt.shape == (300, 2000)
-    np.testing.assert_array_equal(cp, ref.indptr)
-    for w in range(300):
-        a, b = cp[w], cp[w + 1]
-        o = np.argsort(rt[a:b], kind="stable")
-        np.testing.assert_array_equal(rt[a:b][o], ref.indices[a:b])
-        np.testing.assert_array_equal(vt[a:b][o], ref.data[a:b])
+    _check_transpose(otm, synth.csr_from_dense(dense))
+
+
+def test_csr_transpose_wide_vocabulary(otm):
+    """A vocabulary too wide for the per-block counts in shared memory (150,000
+    words): the transpose takes one atomic position per entry, same result."""
+    g = np.random.default_rng(19)
+    n, d, per = 3000, 150000, 40
+    cols = np.sort(np.stack([g.choice(d, per, replace=False) for _ in range(n)]), axis=1)
+    cols[:, 0] = 0             # a word in every document
+    cols = np.sort(cols, axis=1)
+    row_ptr = np.arange(n + 1, dtype=np.int64) * per
+    X = synth.CSR(row_ptr, cols.reshape(-1), g.integers(1, 4, n * per).astype(np.float64),
+                  (n, d))
+    _check_transpose(otm, X)
 
 
 def test_pairs_apply(otm):
