@@ -29,20 +29,30 @@ namespace otm {
 namespace {
 
 constexpr int TE_KMAX = 128;
+constexpr int TE_WPD = 4;  // warps per document in the gather
 
-// Per-step preparation (one block): mu_i = <m, v_i> and the transpose of V
-// (Vt[r][i] = v_i[r]) for the product U = W_g Vt.
-__global__ void __launch_bounds__(256) te_prep_kernel(const float* __restrict__ V, int k,
-                                                      const double* __restrict__ m,
-                                                      double* __restrict__ mu,
-                                                      float* __restrict__ Vt) {
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
-    const int i = idx / k, r = idx % k;
-    Vt[r * k + i] = V[idx];
+// Per-step preparation, one block per component i: mu_i = <m, v_i> and column
+// i of the transpose of V (Vt[r][i] = v_i[r]) for the product U = W_g Vt.
+__global__ void __launch_bounds__(TE_KMAX) te_prep_kernel(const float* __restrict__ V, int k,
+                                                          const double* __restrict__ m,
+                                                          double* __restrict__ mu,
+                                                          float* __restrict__ Vt) {
+  __shared__ double red[TE_KMAX / 32];
+  const int i = blockIdx.x, r = threadIdx.x;
+  double x = 0.0;
+  if (r < k) {
+    const float v = V[i * k + r];
+    Vt[r * k + i] = v;
+    x = m[r] * (double)v;
   }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((r & 31) == 0) red[r >> 5] = x;
+  __syncthreads();
+  if (r == 0) {
     double acc = 0.0;
-    for (int r = 0; r < k; ++r) acc += m[r] * (double)V[i * k + r];
+#pragma unroll
+    for (int w = 0; w < TE_KMAX / 32; ++w) acc += red[w];
     mu[i] = acc;
   }
 }
@@ -83,27 +93,34 @@ __global__ void __launch_bounds__(1024) te_offsets_kernel(const int32_t* __restr
   }
 }
 
-// One warp per minibatch document: its occurrences' rows of W into W_g and
-// their counts into cnt, y'_t = W^T c_t into Yp (FP32 sums), l_t into len.
-// The (word, count) pairs come 32 at a time (one coalesced load, broadcast by
+// TE_WPD warps per minibatch document, each over a contiguous part of its
+// occurrences: their rows of W into W_g and their counts into cnt, and the
+// part's sums of c_j W_j (Ypp[t][w], FP32) and of the counts (lenp[t][w]); the
+// coefficient kernel adds the parts in a fixed order into y'_t and l_t.  The
+// (word, count) pairs come 32 at a time (one coalesced load, broadcast by
 // shuffles), so the W-row loads of consecutive occurrences are independent.
 // Writes nothing past cap occurrences.
 __global__ void __launch_bounds__(256) te_gather_kernel(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     const float* __restrict__ val, const int32_t* __restrict__ doc, int64_t nb,
     const float* __restrict__ W, int k, const int64_t* __restrict__ off, int64_t cap,
-    float* __restrict__ Wg, float* __restrict__ cnt, float* __restrict__ Yp,
-    float* __restrict__ len) {
+    float* __restrict__ Wg, float* __restrict__ cnt, float* __restrict__ Ypp,
+    float* __restrict__ lenp) {
   const int lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t wid = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t t = wid / TE_WPD;
+  const int part = (int)(wid % TE_WPD);
   if (t >= nb) return;
   float acc[TE_KMAX / 32];
 #pragma unroll
   for (int q = 0; q < TE_KMAX / 32; ++q) acc[q] = 0.f;
   float l = 0.f;
   if (doc[t] >= 0) {
-    const int32_t e0 = row_ptr[doc[t]], e1 = row_ptr[doc[t] + 1];
-    const int64_t o = off[t];
+    const int32_t d0 = row_ptr[doc[t]], d1 = row_ptr[doc[t] + 1];
+    const int32_t per = (d1 - d0 + TE_WPD - 1) / TE_WPD;
+    const int32_t e0 = d0 + part * per < d1 ? d0 + part * per : d1;
+    const int32_t e1 = e0 + per < d1 ? e0 + per : d1;
+    const int64_t o = off[t] + (e0 - d0);
     for (int32_t base = e0; base < e1; base += 32) {
       const int cntb = e1 - base < 32 ? e1 - base : 32;
       int32_t my_j = 0;
@@ -136,51 +153,77 @@ __global__ void __launch_bounds__(256) te_gather_kernel(
 #pragma unroll
   for (int q = 0; q < TE_KMAX / 32; ++q) {
     const int r = lane + 32 * q;
-    if (r < k) Yp[t * k + r] = acc[q];
+    if (r < k) Ypp[wid * k + r] = acc[q];
   }
-  if (lane == 0) len[t] = l;
+  if (lane == 0) lenp[wid] = l;
 }
 
-// One block per minibatch document, one thread per component: s, q, the
-// coefficients a (into A), e (summed into esum, FP64), and U -> Coef in place.
+// One block per minibatch document, one thread per component: y'_t and l_t from
+// the gather's parts, then s, q, the coefficients a (into A), e (summed into
+// esum, FP64), and U -> Coef in place.
 __global__ void __launch_bounds__(TE_KMAX) te_coef_kernel(
     const int64_t* __restrict__ off, int64_t cap, const float* __restrict__ cnt,
-    const float* __restrict__ Yp, const float* __restrict__ len, const float* __restrict__ V,
-    const double* __restrict__ mu, int k, float c1, float c2, float* __restrict__ U,
-    float* __restrict__ A, double* __restrict__ esum) {
+    const float* __restrict__ Ypp, const float* __restrict__ lenp, float* __restrict__ Yp,
+    const float* __restrict__ V, const double* __restrict__ mu, int k, float c1, float c2,
+    float* __restrict__ U, float* __restrict__ A, double* __restrict__ esum) {
+  __shared__ float s_len;
   const int64_t t = blockIdx.x;
   const int i = threadIdx.x;
+  if (i < k) {
+    float y = 0.f;
+#pragma unroll
+    for (int w = 0; w < TE_WPD; ++w) y += Ypp[(t * TE_WPD + w) * k + i];
+    Yp[t * k + i] = y;
+  }
+  if (i == 0) {
+    float l = 0.f;
+#pragma unroll
+    for (int w = 0; w < TE_WPD; ++w) l += lenp[t * TE_WPD + w];
+    s_len = l;
+  }
+  __syncthreads();
   if (i >= k) return;
   const int64_t e0 = off[t], e1 = min(off[t + 1], cap);
-  const double l = (double)len[t];
+  const double l = (double)s_len;
   const double L2 = l >= 2.0 ? l * (l - 1.0) : 0.0;
   const double L3 = l >= 3.0 ? l * (l - 1.0) * (l - 2.0) : 0.0;
-  // s = <y'_t, v_i> and q over the document's occurrences, summed in FP64: s^2 - q
-  // (the pairs of distinct tokens) cancels the self-pairs.  Four partial sums
-  // each, so that the dependent FP64 chains and the loads overlap.
-  double s4[4] = {0.0, 0.0, 0.0, 0.0};
+  // s = <y'_t, v_i> and q over the document's occurrences, accumulated in FP64
+  // from FP32 partial sums of 4 (s) and 8 (q, all terms non-negative) terms, so
+  // that s^2 - q (the pairs of distinct tokens) keeps the cancellation of the
+  // self-pairs to the accuracy of the FP32 inputs while the FP64 pipe does
+  // one addition per partial sum.
+  double s2[2] = {0.0, 0.0};
   int r = 0;
-  for (; r + 4 <= k; r += 4) {
+  for (; r + 8 <= k; r += 8) {
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
-      s4[x] = fma((double)Yp[t * k + r + x], (double)V[i * k + r + x], s4[x]);
+    for (int x = 0; x < 2; ++x) {
+      float p = Yp[t * k + r + 4 * x] * V[i * k + r + 4 * x];
+#pragma unroll
+      for (int y = 1; y < 4; ++y) p = fmaf(Yp[t * k + r + 4 * x + y], V[i * k + r + 4 * x + y], p);
+      s2[x] += (double)p;
+    }
   }
-  for (; r < k; ++r) s4[0] = fma((double)Yp[t * k + r], (double)V[i * k + r], s4[0]);
-  const double sd = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-  double q4[4] = {0.0, 0.0, 0.0, 0.0};
+  for (; r < k; ++r) s2[0] = fma((double)Yp[t * k + r], (double)V[i * k + r], s2[0]);
+  const double sd = s2[0] + s2[1];
+  double q2[2] = {0.0, 0.0};
   int64_t e = e0;
-  for (; e + 4 <= e1; e += 4) {
+  for (; e + 16 <= e1; e += 16) {
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      const double u = U[(e + x) * k + i];
-      q4[x] = fma((double)cnt[e + x] * u, u, q4[x]);
+    for (int x = 0; x < 2; ++x) {
+      float p = 0.f;
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const float u = U[(e + 8 * x + y) * k + i];
+        p = fmaf(cnt[e + 8 * x + y] * u, u, p);
+      }
+      q2[x] += (double)p;
     }
   }
   for (; e < e1; ++e) {
     const double u = U[e * k + i];
-    q4[0] = fma((double)cnt[e] * u, u, q4[0]);
+    q2[0] = fma((double)cnt[e] * u, u, q2[0]);
   }
-  const double qd = (q4[0] + q4[1]) + (q4[2] + q4[3]);
+  const double qd = q2[0] + q2[1];
   const double mi = mu[i];
   const double i3 = L3 > 0.0 ? 1.0 / L3 : 0.0, i2 = L2 > 0.0 ? 1.0 / L2 : 0.0;
   const double a = c1 * (sd * sd - qd) * i3 - 2.0 * c2 * mi * sd * i2;
@@ -242,7 +285,7 @@ __global__ void te_docs_kernel(const int32_t* __restrict__ perm, int64_t n, int6
 struct TeWs {
   int32_t* doc;
   int64_t* off;
-  float *Wg, *cnt, *Yp, *len, *U, *A, *Vt, *Vn;
+  float *Wg, *cnt, *Yp, *Ypp, *lenp, *U, *A, *Vt, *Vn;
   double *m, *mu, *esum, *Gd;
   int* flag;
 };
@@ -254,7 +297,8 @@ TeWs te_take(Workspace& w, int64_t k, int64_t b, int64_t cap) {
   s.Wg = w.take<float>((size_t)cap * k);
   s.cnt = w.take<float>(cap);
   s.Yp = w.take<float>((size_t)b * k);
-  s.len = w.take<float>(b);
+  s.Ypp = w.take<float>((size_t)b * TE_WPD * k);
+  s.lenp = w.take<float>((size_t)b * TE_WPD);
   s.U = w.take<float>((size_t)cap * k);
   s.A = w.take<float>((size_t)b * k);
   s.Vt = w.take<float>((size_t)k * k);
@@ -277,7 +321,8 @@ otm_status te_products(const TeWs& s, int64_t k, int64_t nb, int64_t cap, cudaSt
 WorkspaceSize te_size(int64_t k, int64_t b, int64_t cap) {
   WorkspaceSize w;
   w.add<int32_t>(b).add<int64_t>(b + 1).add<float>((size_t)cap * k).add<float>(cap);
-  w.add<float>((size_t)b * k).add<float>(b).add<float>((size_t)cap * k).add<float>((size_t)b * k);
+  w.add<float>((size_t)b * k).add<float>((size_t)b * TE_WPD * k).add<float>((size_t)b * TE_WPD);
+  w.add<float>((size_t)cap * k).add<float>((size_t)b * k);
   w.add<float>((size_t)k * k).add<float>((size_t)k * k);
   w.add<double>(k).add<double>(k).add<double>(k).add<double>((size_t)k * k).add<int>(1);
   return w;
@@ -333,13 +378,13 @@ otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, c
       te_docs_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
           perm ? perm + e * n : nullptr, n, pos0, nb, s.doc);
       OTM_CHECK_LAUNCH();
-      te_prep_kernel<<<1, 256, 0, st>>>(V, (int)k, s.m, s.mu, s.Vt);
+      te_prep_kernel<<<(unsigned)k, TE_KMAX, 0, st>>>(V, (int)k, s.m, s.mu, s.Vt);
       OTM_CHECK_LAUNCH();
       te_offsets_kernel<<<1, 1024, 0, st>>>(X->row_ptr, s.doc, nb, nnz_b_max, s.off, s.flag);
       OTM_CHECK_LAUNCH();
-      te_gather_kernel<<<(unsigned)((nb + 7) / 8), 256, 0, st>>>(
+      te_gather_kernel<<<(unsigned)((nb * TE_WPD + 7) / 8), 256, 0, st>>>(
           X->row_ptr, X->col, X->val, s.doc, nb, W, (int)k, s.off, nnz_b_max, s.Wg, s.cnt,
-          s.Yp, s.len);
+          s.Ypp, s.lenp);
       OTM_CHECK_LAUNCH();
       te_zero_tail_kernel<<<256, 256, 0, st>>>(s.off + nb, nnz_b_max, (int)k, s.Wg);
       OTM_CHECK_LAUNCH();
@@ -348,7 +393,7 @@ otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, c
       if (nnz_b_max > 0)
         OTM_TRY(gemm_nn_small(s.Wg, nnz_b_max, k, s.Vt, k, s.U, nullptr, nullptr, 0.0, st));
       OTM_CHECK_CUDA(cudaMemsetAsync(s.esum, 0, sizeof(double) * k, st));
-      te_coef_kernel<<<(unsigned)nb, TE_KMAX, 0, st>>>(s.off, nnz_b_max, s.cnt, s.Yp, s.len, V,
+      te_coef_kernel<<<(unsigned)nb, TE_KMAX, 0, st>>>(s.off, nnz_b_max, s.cnt, s.Ypp, s.lenp, s.Yp, V,
                                                         s.mu, (int)k, c1, c2, s.U, s.A, s.esum);
       OTM_CHECK_LAUNCH();
       OTM_TRY(te_products(s, k, nb, nnz_b_max, st));
