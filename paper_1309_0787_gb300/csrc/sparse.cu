@@ -440,7 +440,9 @@ __global__ void __launch_bounds__(256) spmm_csc_v4_kernel(
         my_r = rowT[base + lane];
         my_v = valT[base + lane];
       }
-#pragma unroll 4
+      // 16 row loads in flight per warp: the P rows (n x m, larger than L2 for the
+      // topic whitening) come partly from HBM
+#pragma unroll 16
       for (int j = 0; j < cnt; ++j) {
         const int32_t r = __shfl_sync(0xffffffffu, my_r, j);
         const float v = __shfl_sync(0xffffffffu, my_v, j);
