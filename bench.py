@@ -1666,27 +1666,51 @@ def run_topic_exact(args):
     perm = path.perm[:1].contiguous()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def one():
+    def one(prec):
         V = path.V0t.clone()
         otm.sgd_run_topic_exact(V, path.Xd, wh["W"], wh["M1"], perm, 1, b, c["beta0"],
-                                c["theta"], a0)
+                                c["theta"], a0, precision=prec)
         return V
-    for _ in range(args.warmup):
-        one()
-    torch.cuda.synchronize()
+
+    def timed(prec):
+        for _ in range(args.warmup):
+            one(prec)
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            V = one(prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms) / 1e3, V
     sampler = ClockSampler(0)
     sampler.start()
-    ms = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        V = one()
-        e1.record()
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
+    t, V = timed(0)
+    t16, V16 = timed(otm.PREC_BF16)
     clocks = sampler.stop()
-    t = statistics.median(ms) / 1e3
+    # one step on the first minibatch from the start, each form against the FP64 oracle
+    from oracle import stgd as ostgd
+    docs = host["perm"][0][:b].astype(np.int64)
+    Xb = synth.CSR(*_csr_rows(host["X"], docs), (len(docs), host["X"].shape[1]))
+    W64 = wh["W"].cpu().numpy().astype(np.float64)
+    M164 = wh["M1"].cpu().numpy()
+    V0 = host["V0"].astype(np.float64)
+    G = ostgd.grad_implicit_topic_exact(V0, Xb, W64, M164, c["theta"], a0)
+    gram = ostgd.kappa(c["theta"]) * V0 @ (V0.T @ V0) ** 2
+    den = np.linalg.norm(gram) + np.linalg.norm(gram - G)
+    step = {}
+    for nm, prec in (("fp32", 0), ("bf16", otm.PREC_BF16)):
+        V1 = path.V0t.clone()
+        otm.sgd_run_topic_exact(V1, otm.DeviceCSR.from_host(Xb, dev), wh["W"], wh["M1"], None, 1,
+                                b, c["beta0"], c["theta"], a0, precision=prec)
+        Gk = (V0 - V1.cpu().numpy().T.astype(np.float64)) / c["beta0"]
+        step[nm] = {"grad_rel_err": float(np.linalg.norm(Gk - G) / den),
+                    "grad_rel_err_worst_component": float(
+                        (np.linalg.norm(Gk - G, axis=0) /
+                         (np.linalg.norm(gram, axis=0) + np.linalg.norm(gram - G, axis=0))).max())}
     nnz = int(host["X"].row_ptr[-1])
     nsteps = (n + b - 1) // b
     flops = 4.0 * k * k * nnz + 2.0 * k * k * n + nsteps * 4.0 * k ** 3
@@ -1700,6 +1724,10 @@ def run_topic_exact(args):
                        "nnz": nnz, "k": k, "minibatch": b, "epochs": 1, "sgd_steps": nsteps,
                        "l2": "flushed before each run (256 MiB write)"},
             "us_per_sgd_step": 1e6 * t / nsteps, "result_finite": finite,
+            "bf16": {"ms_per_step": 1e3 * t16, "us_per_sgd_step": 1e6 * t16 / nsteps,
+                     "documents_per_s": n / t16, "result_finite": bool(torch.isfinite(V16).all()),
+                     "achieved_tflops": flops / t16 / 1e12},
+            "one_step_vs_fp64_oracle": step,
             "roofline": {"kernel": "sgd_run_topic_exact (gather, U = W_g V^T, coefficients, "
                                    "W_g^T Coef + Y'^T A, update per step)",
                          "bound": "alu", "achieved": flops / t / 1e12,
@@ -1708,6 +1736,14 @@ def run_topic_exact(args):
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                          "algorithmic_flops_per_run": flops},
             "clocks": clocks}
+
+
+def _csr_rows(X, rows):
+    """(row_ptr, col, val) of the rows `rows` of the CSR X, in that order."""
+    lens = (X.row_ptr[rows + 1] - X.row_ptr[rows]).astype(np.int64)
+    rp = np.concatenate([[0], np.cumsum(lens)])
+    idx = np.concatenate([np.arange(X.row_ptr[r], X.row_ptr[r + 1]) for r in rows])
+    return rp, X.col[idx], X.val[idx]
 
 
 def run_projection(args):

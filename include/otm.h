@@ -372,8 +372,12 @@ otm_status otm_sgd_split_shape(int64_t k, int64_t b, int sym, int* clusters, int
  * document's length (a term is dropped for documents shorter than its
  * order).  The tensor is never formed: per minibatch the rows of W of its word
  * occurrences are gathered, U = W_g V^T, the per-document sums and
- * coefficients are formed, and the data term is W_g^T Coef + Y'^T A (FP32
- * tiles, FP64 accumulation).
+ * coefficients are formed, and the data term is W_g^T Coef + Y'^T A.
+ * precision 0: the products in FP32 tiles with FP64 accumulation; precision 1
+ * (OTM_PREC_BF16): U = W_g V^T and W_g^T Coef on the tensor cores (tcgen05,
+ * BF16 operands, FP32 accumulation; W_g^T Coef as slices of 1,536 occurrences
+ * whose partials are added in FP64), the per-document sums and coefficients
+ * as in FP32; about 3e-3 relative error in the gradient.
  * X: the corpus (n documents x d words, CSR counts); W: d x k float32
  * row-major; M1: d doubles (the first moment of Eq. (1)); V: k x k float32,
  * component i contiguous, updated in place; perm: epochs x n int32 (NULL =
@@ -381,14 +385,16 @@ otm_status otm_sgd_split_shape(int64_t k, int64_t b, int sym, int* clusters, int
  * nnz_b_max: the most word occurrences (CSR entries) any minibatch holds; a
  * larger minibatch is not processed and makes the call return OTM_EINVAL.
  * Snapshots as for otm_sgd_run.  1 <= k <= 128.
- * Scratch: otm_sgd_topic_exact_workspace(k, b, nnz_b_max) bytes.  The host
- * drives the steps (about ten launches each); synchronises the stream at the end.
+ * Scratch: otm_sgd_topic_exact_workspace(k, b, nnz_b_max, precision) bytes (0
+ * for arguments out of range).  The host drives the steps (about ten launches
+ * each); synchronises the stream at the end.  OTM_ETIMEOUT if a tensor-core
+ * product's bounded wait expired.
  */
-size_t otm_sgd_topic_exact_workspace(int64_t k, int64_t b, int64_t nnz_b_max);
+size_t otm_sgd_topic_exact_workspace(int64_t k, int64_t b, int64_t nnz_b_max, int precision);
 otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, const double* M1,
                                    int64_t k, const int32_t* perm, int64_t epochs, int64_t b,
                                    int64_t nnz_b_max, double beta0, double theta, double alpha0,
-                                   float* V_snap, int64_t snapshot_every, void* ws,
+                                   int precision, float* V_snap, int64_t snapshot_every, void* ws,
                                    size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */

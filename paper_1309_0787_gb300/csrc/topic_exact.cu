@@ -17,11 +17,18 @@
 //   Coef  = c o U o (b_t(e) + g_t(e) U)     (elementwise, per occurrence)
 //   data  = (W_g^T Coef + Y'^T A) / b + m (sum_t e_t / b + c3 mu o mu)^T
 //   V    <- V - beta_t (kappa V ((V^T V) o (V^T V)) - data)
-// The two large products are FP32 tiles accumulated in FP64 (gemm_tn_f64acc).
+// The two large products are FP32 tiles accumulated in FP64 (gemm_tn_f64acc),
+// or, in the BF16 form, tcgen05 products of BF16 operands with FP32
+// accumulation: U = W_g V^T in one TMA-fed GEMM, and W_g^T Coef as a batch of
+// GEMMs over slices of TE_KC occurrences (transposed BF16 copies of W_g and
+// Coef), whose FP32 partials are added in FP64.  The per-document sums and
+// coefficients stay as in the FP32 form.
 // One step is a short sequence of launches; the host drives the steps.
 #include <algorithm>
 #include <cmath>
 #include <vector>
+
+#include <cuda_bf16.h>
 
 #include "otm_internal.cuh"
 
@@ -30,6 +37,7 @@ namespace {
 
 constexpr int TE_KMAX = 128;
 constexpr int TE_WPD = 4;  // warps per document in the gather
+constexpr int TE_KC = 1536;  // occurrences per slice of the BF16 W_g^T Coef product
 
 // Per-step preparation, one block per component i: mu_i = <m, v_i> and column
 // i of the transpose of V (Vt[r][i] = v_i[r]) for the product U = W_g Vt.
@@ -100,12 +108,15 @@ __global__ void __launch_bounds__(1024) te_offsets_kernel(const int32_t* __restr
 // (word, count) pairs come 32 at a time (one coalesced load, broadcast by
 // shuffles), so the W-row loads of consecutive occurrences are independent.
 // Writes nothing past cap occurrences.
+// BF: W_g as BF16 rows of kpad columns (zero beyond k) in Wg16, else FP32 rows
+// of k columns in Wg.
+template <bool BF>
 __global__ void __launch_bounds__(256) te_gather_kernel(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     const float* __restrict__ val, const int32_t* __restrict__ doc, int64_t nb,
-    const float* __restrict__ W, int k, const int64_t* __restrict__ off, int64_t cap,
-    float* __restrict__ Wg, float* __restrict__ cnt, float* __restrict__ Ypp,
-    float* __restrict__ lenp) {
+    const float* __restrict__ W, int k, int kpad, const int64_t* __restrict__ off, int64_t cap,
+    float* __restrict__ Wg, __nv_bfloat16* __restrict__ Wg16, float* __restrict__ cnt,
+    float* __restrict__ Ypp, float* __restrict__ lenp) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int64_t t = wid / TE_WPD;
@@ -144,7 +155,14 @@ __global__ void __launch_bounds__(256) te_gather_kernel(
           if (r < k) {
             const float w = __ldg(W + (int64_t)j * k + r);
             acc[q] = fmaf(c, w, acc[q]);
-            if (keep) Wg[g * k + r] = w;
+            if (keep) {
+              if constexpr (BF)
+                Wg16[g * kpad + r] = __float2bfloat16(w);
+              else
+                Wg[g * k + r] = w;
+            }
+          } else if (BF && r < kpad && keep) {
+            Wg16[g * kpad + r] = __float2bfloat16(0.f);
           }
         }
       }
@@ -161,11 +179,14 @@ __global__ void __launch_bounds__(256) te_gather_kernel(
 // One block per minibatch document, one thread per component: y'_t and l_t from
 // the gather's parts, then s, q, the coefficients a (into A), e (summed into
 // esum, FP64), and U -> Coef in place.
+// BF: Coef into C16 (BF16, rows of kpad), else into U in place.
+template <bool BF>
 __global__ void __launch_bounds__(TE_KMAX) te_coef_kernel(
     const int64_t* __restrict__ off, int64_t cap, const float* __restrict__ cnt,
     const float* __restrict__ Ypp, const float* __restrict__ lenp, float* __restrict__ Yp,
-    const float* __restrict__ V, const double* __restrict__ mu, int k, float c1, float c2,
-    float* __restrict__ U, float* __restrict__ A, double* __restrict__ esum) {
+    const float* __restrict__ V, const double* __restrict__ mu, int k, int kpad, float c1,
+    float c2, float* __restrict__ U, __nv_bfloat16* __restrict__ C16, float* __restrict__ A,
+    double* __restrict__ esum) {
   __shared__ float s_len;
   const int64_t t = blockIdx.x;
   const int i = threadIdx.x;
@@ -236,7 +257,11 @@ __global__ void __launch_bounds__(TE_KMAX) te_coef_kernel(
 #pragma unroll 4
   for (int64_t x = e0; x < e1; ++x) {
     const float u = U[x * k + i];
-    U[x * k + i] = cnt[x] * u * fmaf(gf, u, bf);
+    const float cf = cnt[x] * u * fmaf(gf, u, bf);
+    if constexpr (BF)
+      C16[x * kpad + i] = __float2bfloat16(cf);
+    else
+      U[x * k + i] = cf;
   }
 }
 
@@ -274,6 +299,59 @@ __global__ void te_zero_tail_kernel(const int64_t* __restrict__ off_end, int64_t
     Wg[i] = 0.f;
 }
 
+// BF16 rows [*off_end, capp) of W_g and Coef are zeroed (this minibatch only).
+__global__ void te_zero_tail16_kernel(const int64_t* __restrict__ off_end, int64_t cap,
+                                      int64_t capp, int kpad, __nv_bfloat16* __restrict__ a,
+                                      __nv_bfloat16* __restrict__ b) {
+  const int64_t start = min(*off_end, cap) * kpad, end = capp * kpad;
+  const __nv_bfloat16 z = __float2bfloat16(0.f);
+  for (int64_t i = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a[i] = z;
+    b[i] = z;
+  }
+}
+
+// V16[i][r] = bf16(V[i][r]) for r < k, zero for k <= r < kpad (one block per i).
+__global__ void te_v16_kernel(const float* __restrict__ V, int k, int kpad,
+                              __nv_bfloat16* __restrict__ V16) {
+  const int i = blockIdx.x;
+  for (int r = threadIdx.x; r < kpad; r += blockDim.x)
+    V16[i * kpad + r] = __float2bfloat16(r < k ? V[i * k + r] : 0.f);
+}
+
+// out[c][r] = in[r][c] for r < rows, c < cols (in: rows x ld_in, out: cols x ld_out),
+// 32 x 32 tiles through shared memory.
+__global__ void te_transpose16_kernel(const __nv_bfloat16* __restrict__ in, int64_t rows,
+                                      int cols, int ld_in, __nv_bfloat16* __restrict__ out,
+                                      int64_t ld_out) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int y = ty; y < 32; y += 8) {
+    const int64_t r = r0 + y;
+    const int c = c0 + tx;
+    tile[y][tx] = (r < rows && c < cols) ? in[r * ld_in + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  for (int y = ty; y < 32; y += 8) {
+    const int c = c0 + y;
+    const int64_t r = r0 + tx;
+    if (c < cols && r < rows) out[(int64_t)c * ld_out + r] = tile[tx][y];
+  }
+}
+
+// Gd[e] = scale * sum_z part[z][e] in FP64, e < kk.
+__global__ void te_reduce_kernel(const float* __restrict__ part, int64_t nz, int64_t kk,
+                                 double scale, double* __restrict__ Gd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kk) return;
+  double acc = 0.0;
+  for (int64_t z = 0; z < nz; ++z) acc += (double)part[z * kk + e];
+  Gd[e] = acc * scale;
+}
+
 __global__ void te_docs_kernel(const int32_t* __restrict__ perm, int64_t n, int64_t pos0,
                                int64_t nb, int32_t* __restrict__ doc) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,18 +366,25 @@ struct TeWs {
   float *Wg, *cnt, *Yp, *Ypp, *lenp, *U, *A, *Vt, *Vn;
   double *m, *mu, *esum, *Gd;
   int* flag;
+  // BF16 form
+  __nv_bfloat16 *Wg16, *C16, *Wt16, *Ct16, *V16;
+  float* part;
 };
 
-TeWs te_take(Workspace& w, int64_t k, int64_t b, int64_t cap) {
+// The BF16 form's row count: the capacity rounded up to whole slices.
+inline int64_t te_capp(int64_t cap) { return (cap + TE_KC - 1) / TE_KC * TE_KC; }
+inline int te_kpad(int64_t k) { return (int)((k + 7) / 8 * 8); }
+
+TeWs te_take(Workspace& w, int64_t k, int64_t b, int64_t cap, int bf) {
   TeWs s;
   s.doc = w.take<int32_t>(b);
   s.off = w.take<int64_t>(b + 1);
-  s.Wg = w.take<float>((size_t)cap * k);
+  s.Wg = w.take<float>(bf ? 1 : (size_t)cap * k);
   s.cnt = w.take<float>(cap);
   s.Yp = w.take<float>((size_t)b * k);
   s.Ypp = w.take<float>((size_t)b * TE_WPD * k);
   s.lenp = w.take<float>((size_t)b * TE_WPD);
-  s.U = w.take<float>((size_t)cap * k);
+  s.U = w.take<float>((size_t)(bf ? te_capp(cap) : cap) * k);
   s.A = w.take<float>((size_t)b * k);
   s.Vt = w.take<float>((size_t)k * k);
   s.Vn = w.take<float>((size_t)k * k);
@@ -307,8 +392,40 @@ TeWs te_take(Workspace& w, int64_t k, int64_t b, int64_t cap) {
   s.mu = w.take<double>(k);
   s.esum = w.take<double>(k);
   s.Gd = w.take<double>((size_t)k * k);
-  s.flag = w.take<int>(1);
+  s.flag = w.take<int>(2);
+  s.Wg16 = s.C16 = s.Wt16 = s.Ct16 = s.V16 = nullptr;
+  s.part = nullptr;
+  if (bf) {
+    const int64_t capp = te_capp(cap), kpad = te_kpad(k);
+    s.Wg16 = w.take<__nv_bfloat16>((size_t)capp * kpad);
+    s.C16 = w.take<__nv_bfloat16>((size_t)capp * kpad);
+    s.Wt16 = w.take<__nv_bfloat16>((size_t)k * capp);
+    s.Ct16 = w.take<__nv_bfloat16>((size_t)k * capp);
+    s.V16 = w.take<__nv_bfloat16>((size_t)k * kpad);
+    s.part = w.take<float>((size_t)(capp / TE_KC) * k * k);
+  }
   return s;
+}
+
+// Gd = (W_g^T Coef + Y'^T A) / nb with BF16 tensor-core slices of W_g^T Coef.
+otm_status te_products16(const TeWs& s, int64_t k, int64_t nb, int64_t cap, cudaStream_t st) {
+  const int64_t capp = te_capp(cap), nz = capp / TE_KC;
+  const int kpad = te_kpad(k);
+  if (nz > 0) {
+    const dim3 tg((unsigned)(capp / 32), (unsigned)((k + 31) / 32));
+    te_transpose16_kernel<<<tg, 256, 0, st>>>(s.Wg16, capp, (int)k, kpad, s.Wt16, capp);
+    OTM_CHECK_LAUNCH();
+    te_transpose16_kernel<<<tg, 256, 0, st>>>(s.C16, capp, (int)k, kpad, s.Ct16, capp);
+    OTM_CHECK_LAUNCH();
+    OTM_TRY(gemm_bf16_nt(s.Wt16, s.Ct16, k, k, TE_KC, nz, capp, capp, TE_KC, TE_KC, 0, 1.f,
+                         nullptr, s.part, k, k * k, nullptr, 0, 0, s.flag + 1, st));
+    te_reduce_kernel<<<(unsigned)((k * k + 255) / 256), 256, 0, st>>>(s.part, nz, k * k,
+                                                                    1.0 / (double)nb, s.Gd);
+    OTM_CHECK_LAUNCH();
+  } else {
+    OTM_CHECK_CUDA(cudaMemsetAsync(s.Gd, 0, sizeof(double) * k * k, st));
+  }
+  return gemm_tn_f64acc(s.Yp, s.A, nb, k, k, 1.0 / (double)nb, s.Gd, 1, st);
 }
 
 // Gd = (W_g^T Coef + Y'^T A) / nb, FP32 tiles accumulated in FP64
@@ -318,13 +435,19 @@ otm_status te_products(const TeWs& s, int64_t k, int64_t nb, int64_t cap, cudaSt
   return OTM_OK;
 }
 
-WorkspaceSize te_size(int64_t k, int64_t b, int64_t cap) {
+WorkspaceSize te_size(int64_t k, int64_t b, int64_t cap, int bf) {
   WorkspaceSize w;
-  w.add<int32_t>(b).add<int64_t>(b + 1).add<float>((size_t)cap * k).add<float>(cap);
+  w.add<int32_t>(b).add<int64_t>(b + 1).add<float>(bf ? 1 : (size_t)cap * k).add<float>(cap);
   w.add<float>((size_t)b * k).add<float>((size_t)b * TE_WPD * k).add<float>((size_t)b * TE_WPD);
-  w.add<float>((size_t)cap * k).add<float>((size_t)b * k);
+  w.add<float>((size_t)(bf ? te_capp(cap) : cap) * k).add<float>((size_t)b * k);
   w.add<float>((size_t)k * k).add<float>((size_t)k * k);
-  w.add<double>(k).add<double>(k).add<double>(k).add<double>((size_t)k * k).add<int>(1);
+  w.add<double>(k).add<double>(k).add<double>(k).add<double>((size_t)k * k).add<int>(2);
+  if (bf) {
+    const int64_t capp = te_capp(cap), kpad = te_kpad(k);
+    w.add<__nv_bfloat16>((size_t)capp * kpad).add<__nv_bfloat16>((size_t)capp * kpad);
+    w.add<__nv_bfloat16>((size_t)k * capp).add<__nv_bfloat16>((size_t)k * capp);
+    w.add<__nv_bfloat16>((size_t)k * kpad).add<float>((size_t)(capp / TE_KC) * k * k);
+  }
   return w;
 }
 
@@ -335,17 +458,20 @@ using namespace otm;
 
 extern "C" {
 
-size_t otm_sgd_topic_exact_workspace(int64_t k, int64_t b, int64_t nnz_b_max) {
-  if (k < 1 || k > TE_KMAX || b < 1 || nnz_b_max < 0) return 0;
-  return te_size(k, b, nnz_b_max).bytes();
+size_t otm_sgd_topic_exact_workspace(int64_t k, int64_t b, int64_t nnz_b_max, int precision) {
+  if (k < 1 || k > TE_KMAX || b < 1 || nnz_b_max < 0 || precision < 0 || precision > 1) return 0;
+  return te_size(k, b, nnz_b_max, precision).bytes();
 }
 
 otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, const double* M1,
                                    int64_t k, const int32_t* perm, int64_t epochs, int64_t b,
                                    int64_t nnz_b_max, double beta0, double theta, double alpha0,
-                                   float* V_snap, int64_t snapshot_every, void* ws,
+                                   int precision, float* V_snap, int64_t snapshot_every, void* ws,
                                    size_t ws_bytes, void* stream) {
   clear_error();
+  OTM_REQUIRE(precision == 0 || precision == 1,
+              "otm_sgd_run_topic_exact: precision %d is not 0 (FP32) or 1 (BF16)", precision);
+  const int bf = precision;
   OTM_TRY(check_csr(X, "otm_sgd_run_topic_exact: X"));
   OTM_REQUIRE(V && W && M1, "otm_sgd_run_topic_exact: null pointer");
   OTM_REQUIRE(k >= 1 && k <= TE_KMAX, "otm_sgd_run_topic_exact: k=%lld outside [1, %d]",
@@ -356,14 +482,16 @@ otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, c
               "otm_sgd_run_topic_exact: V_snap required for snapshots");
   const int64_t n = X->rows, d = X->cols;
   const int64_t nb_max = std::min(b, n);
-  OTM_REQUIRE(ws && ws_bytes >= te_size(k, nb_max, nnz_b_max).bytes(),
+  OTM_REQUIRE(ws && ws_bytes >= te_size(k, nb_max, nnz_b_max, bf).bytes(),
               "otm_sgd_run_topic_exact: workspace too small (need %zu bytes)",
-              te_size(k, nb_max, nnz_b_max).bytes());
+              te_size(k, nb_max, nnz_b_max, bf).bytes());
   if (epochs == 0) return OTM_OK;
   cudaStream_t st = as_stream(stream);
   Workspace w(ws, ws_bytes);
-  const TeWs s = te_take(w, k, nb_max, nnz_b_max);
-  OTM_CHECK_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int), st));
+  const TeWs s = te_take(w, k, nb_max, nnz_b_max, bf);
+  const int kpad = te_kpad(k);
+  const int64_t capp = te_capp(nnz_b_max);
+  OTM_CHECK_CUDA(cudaMemsetAsync(s.flag, 0, 2 * sizeof(int), st));
   OTM_TRY(vec_tn(M1, W, d, k, s.m, st));  // m = W^T M1
   const double a0 = alpha0;
   const float c1 = (float)((a0 + 1.0) * (a0 + 2.0) / 2.0), c2 = (float)(a0 * (a0 + 1.0) / 2.0),
@@ -382,21 +510,44 @@ otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, c
       OTM_CHECK_LAUNCH();
       te_offsets_kernel<<<1, 1024, 0, st>>>(X->row_ptr, s.doc, nb, nnz_b_max, s.off, s.flag);
       OTM_CHECK_LAUNCH();
-      te_gather_kernel<<<(unsigned)((nb * TE_WPD + 7) / 8), 256, 0, st>>>(
-          X->row_ptr, X->col, X->val, s.doc, nb, W, (int)k, s.off, nnz_b_max, s.Wg, s.cnt,
-          s.Ypp, s.lenp);
-      OTM_CHECK_LAUNCH();
-      te_zero_tail_kernel<<<256, 256, 0, st>>>(s.off + nb, nnz_b_max, (int)k, s.Wg);
-      OTM_CHECK_LAUNCH();
-      // U = W_g V^T over every row the workspace holds (a minibatch past the
-      // capacity has set the flag; its occurrences beyond it are not read)
-      if (nnz_b_max > 0)
-        OTM_TRY(gemm_nn_small(s.Wg, nnz_b_max, k, s.Vt, k, s.U, nullptr, nullptr, 0.0, st));
+      const unsigned gg = (unsigned)((nb * TE_WPD + 7) / 8);
+      if (bf) {
+        te_gather_kernel<true><<<gg, 256, 0, st>>>(X->row_ptr, X->col, X->val, s.doc, nb, W,
+                                                   (int)k, kpad, s.off, nnz_b_max, nullptr,
+                                                   s.Wg16, s.cnt, s.Ypp, s.lenp);
+        OTM_CHECK_LAUNCH();
+        te_zero_tail16_kernel<<<256, 256, 0, st>>>(s.off + nb, nnz_b_max, capp, kpad, s.Wg16,
+                                                   s.C16);
+        OTM_CHECK_LAUNCH();
+        te_v16_kernel<<<(unsigned)k, 128, 0, st>>>(V, (int)k, kpad, s.V16);
+        OTM_CHECK_LAUNCH();
+        // U = W_g V^T (tcgen05, BF16 operands, FP32 accumulation) over every row held
+        if (capp > 0)
+          OTM_TRY(gemm_bf16_nt(s.Wg16, s.V16, capp, k, kpad, 1, kpad, kpad, 0, 0, 0, 1.f, nullptr,
+                               s.U, k, 0, nullptr, 0, 0, s.flag + 1, st));
+      } else {
+        te_gather_kernel<false><<<gg, 256, 0, st>>>(X->row_ptr, X->col, X->val, s.doc, nb, W,
+                                                    (int)k, kpad, s.off, nnz_b_max, s.Wg,
+                                                    nullptr, s.cnt, s.Ypp, s.lenp);
+        OTM_CHECK_LAUNCH();
+        te_zero_tail_kernel<<<256, 256, 0, st>>>(s.off + nb, nnz_b_max, (int)k, s.Wg);
+        OTM_CHECK_LAUNCH();
+        // U = W_g V^T over every row the workspace holds (a minibatch past the
+        // capacity has set the flag; its occurrences beyond it are not read)
+        if (nnz_b_max > 0)
+          OTM_TRY(gemm_nn_small(s.Wg, nnz_b_max, k, s.Vt, k, s.U, nullptr, nullptr, 0.0, st));
+      }
       OTM_CHECK_CUDA(cudaMemsetAsync(s.esum, 0, sizeof(double) * k, st));
-      te_coef_kernel<<<(unsigned)nb, TE_KMAX, 0, st>>>(s.off, nnz_b_max, s.cnt, s.Ypp, s.lenp, s.Yp, V,
-                                                        s.mu, (int)k, c1, c2, s.U, s.A, s.esum);
+      if (bf)
+        te_coef_kernel<true><<<(unsigned)nb, TE_KMAX, 0, st>>>(
+            s.off, nnz_b_max, s.cnt, s.Ypp, s.lenp, s.Yp, V, s.mu, (int)k, kpad, c1, c2, s.U,
+            s.C16, s.A, s.esum);
+      else
+        te_coef_kernel<false><<<(unsigned)nb, TE_KMAX, 0, st>>>(
+            s.off, nnz_b_max, s.cnt, s.Ypp, s.lenp, s.Yp, V, s.mu, (int)k, kpad, c1, c2, s.U,
+            nullptr, s.A, s.esum);
       OTM_CHECK_LAUNCH();
-      OTM_TRY(te_products(s, k, nb, nnz_b_max, st));
+      OTM_TRY(bf ? te_products16(s, k, nb, nnz_b_max, st) : te_products(s, k, nb, nnz_b_max, st));
       te_finish_kernel<<<(unsigned)k, TE_KMAX, 0, st>>>(V, (int)k, s.Gd, s.m, s.mu, s.esum,
                                                         1.0 / (double)nb, c3, kappa, beta, s.Vn);
       OTM_CHECK_LAUNCH();
@@ -405,10 +556,12 @@ otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, c
         OTM_CHECK_CUDA(cudaMemcpyAsync(V_snap + (t / snapshot_every - 1) * k * k, V,
                                        sizeof(float) * k * k, cudaMemcpyDeviceToDevice, st));
     }
-  int h = 0;
-  OTM_CHECK_CUDA(cudaMemcpyAsync(&h, s.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int h[2] = {0, 0};
+  OTM_CHECK_CUDA(cudaMemcpyAsync(h, s.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   OTM_CHECK_CUDA(cudaStreamSynchronize(st));
-  if (h)
+  if (h[1])
+    return set_error(OTM_ETIMEOUT, "otm_sgd_run_topic_exact: a tensor-core product's wait timed out");
+  if (h[0])
     return set_error(OTM_EINVAL, "otm_sgd_run_topic_exact: a minibatch holds more than "
                                  "nnz_b_max = %lld word occurrences", (long long)nnz_b_max);
   return OTM_OK;

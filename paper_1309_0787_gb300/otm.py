@@ -100,9 +100,9 @@ _SIGS = {
                             ctypes.POINTER(ctypes.c_int)],
     "otm_sgd_run": [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64, c_i64, c_f64,
                     c_f64, c_f64, c_i64, c_vp, c_vp, c_sz, c_vp],
-    "otm_sgd_topic_exact_workspace": [c_i64, c_i64, c_i64],
+    "otm_sgd_topic_exact_workspace": [c_i64, c_i64, c_i64, ctypes.c_int],
     "otm_sgd_run_topic_exact": [c_vp, _P, c_vp, c_vp, c_i64, c_vp, c_i64, c_i64, c_i64, c_f64,
-                                c_f64, c_f64, c_vp, c_i64, c_vp, c_sz, c_vp],
+                                c_f64, c_f64, ctypes.c_int, c_vp, c_i64, c_vp, c_sz, c_vp],
     "otm_quantize_samples": [c_vp, c_i64, c_i64, ctypes.c_int, c_vp, c_vp, c_vp],
     "otm_sgd_run_lp_workspace": [],
     "otm_sgd_run_lp": [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_i64,
@@ -466,11 +466,14 @@ PREC_FP8 = 2
 
 
 def sgd_run_topic_exact(V, X: DeviceCSR, W, M1, perm, epochs: int, b: int, beta0: float,
-                        theta: float, alpha0: float, snapshot_every: int = 0):
+                        theta: float, alpha0: float, snapshot_every: int = 0,
+                        precision: int = 0):
     """otm_sgd_run_topic_exact: STGD on the whole third moment of Eq. (3) (the
     self-token terms kept).  V: k x k (V[i] = component i), W: d x k float32,
-    M1: d float64, perm: epochs x n int32 or None.  The workspace is sized by
-    the most word occurrences any minibatch holds (from the row pointers)."""
+    M1: d float64, perm: epochs x n int32 or None; precision 0 (FP32) or
+    PREC_BF16 (the two large products on the tensor cores).  The workspace is
+    sized by the most word occurrences any minibatch holds (from the row
+    pointers)."""
     k = V.shape[0]
     n, d = X.shape
     _need(V, torch.float32, (k, k), "V")
@@ -495,11 +498,11 @@ def sgd_run_topic_exact(V, X: DeviceCSR, W, M1, perm, epochs: int, b: int, beta0
     if snapshot_every:
         snaps = torch.empty(max(steps // snapshot_every, 1), k, k, dtype=torch.float32,
                             device=V.device)
-    ws = _ws(_lib.otm_sgd_topic_exact_workspace(k, min(b, n), cap), V.device)
+    ws = _ws(_lib.otm_sgd_topic_exact_workspace(k, min(b, n), cap, int(precision)), V.device)
     _check(_lib.otm_sgd_run_topic_exact(_ptr(V), X.ref(), _ptr(W), _ptr(M1), k, _ptr(perm),
                                         int(epochs), int(b), cap, float(beta0), float(theta),
-                                        float(alpha0), _ptr(snaps), int(snapshot_every),
-                                        _ptr(ws), ws.numel(), _stream()))
+                                        float(alpha0), int(precision), _ptr(snaps),
+                                        int(snapshot_every), _ptr(ws), ws.numel(), _stream()))
     return snaps
 
 

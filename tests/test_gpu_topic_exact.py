@@ -120,9 +120,55 @@ def test_exact_rejects_too_small_capacity(otm):
     M1 = _dev(om.topic_first_moment(X))
     V = _dev(np.eye(k, dtype=np.float32))
     cap = int(X.nnz) // 2
-    ws = torch.empty(int(otm._lib.otm_sgd_topic_exact_workspace(k, n, cap)), dtype=torch.uint8,
-                     device="cuda")
-    st = otm._lib.otm_sgd_run_topic_exact(otm._ptr(V), Xd.ref(), otm._ptr(W), otm._ptr(M1), k,
-                                          None, 1, n, cap, 1e-3, 1.0, 1.0, None, 0, otm._ptr(ws),
-                                          ws.numel(), otm._stream())
-    assert st == 1 and b"nnz_b_max" in otm._lib.otm_last_error()
+    for prec in (0, otm.PREC_BF16):
+        ws = torch.empty(int(otm._lib.otm_sgd_topic_exact_workspace(k, n, cap, prec)),
+                         dtype=torch.uint8, device="cuda")
+        st = otm._lib.otm_sgd_run_topic_exact(otm._ptr(V), Xd.ref(), otm._ptr(W), otm._ptr(M1),
+                                              k, None, 1, n, cap, 1e-3, 1.0, 1.0, prec, None, 0,
+                                              otm._ptr(ws), ws.numel(), otm._stream())
+        assert st == 1 and b"nnz_b_max" in otm._lib.otm_last_error()
+
+
+@pytest.mark.parametrize("n,d,k,L,a0,theta", [(90, 60, 6, 12, 1.0, 1.0), (400, 300, 17, 40, 0.0, 1.0),
+                                              (3000, 2000, 100, 100, 1.0, 1.0)])
+def test_exact_gradient_one_step_bf16(otm, n, d, k, L, a0, theta):
+    """The BF16 tensor-core form (U = W_g V^T and W_g^T Coef on tcgen05): one
+    full-batch step within the 2e-2 of the low-precision paths, whole matrix and
+    every component; 3,000 documents of 100 words hold about 3e5 occurrences,
+    more than 190 slices of the W_g^T Coef product."""
+    X = _corpus(n + d, n, d, k, L, short=(n < 1000))
+    g = np.random.default_rng(n + k)
+    W = (g.standard_normal((d, k)) * (0.3 if k < 50 else 0.05)).astype(np.float32)
+    M1 = om.topic_first_moment(X)
+    V0 = (0.7 * g.standard_normal((k, k))).astype(np.float32)
+    Vd = _dev(V0.T.copy())
+    otm.sgd_run_topic_exact(Vd, otm.DeviceCSR.from_host(X), _dev(W), _dev(M1), None, 1, n, 1.0,
+                            theta, a0, precision=otm.PREC_BF16)
+    torch.cuda.synchronize()
+    V64 = V0.astype(np.float64)
+    Gk = V64 - to_np(Vd).T.astype(np.float64)
+    G = ostgd.grad_implicit_topic_exact(V64, X, W.astype(np.float64), M1, theta, a0)
+    frob, col = grad_errs(Gk, G, ostgd.kappa(theta) * V64 @ (V64.T @ V64) ** 2)
+    assert frob < 2e-2 and col < 2e-2, (frob, col)
+
+
+def test_exact_run_bf16_tracks_fp32(otm):
+    """Two epochs with permutations and snapshots in BF16 against the FP32 form
+    and the oracle's run: both within 2e-2 of the oracle."""
+    n, d, k, b, epochs = 150, 80, 5, 48, 2
+    X = _corpus(5, n, d, k, 20)
+    g = np.random.default_rng(6)
+    W = (g.standard_normal((d, k)) * 0.4).astype(np.float32)
+    M1 = om.topic_first_moment(X)
+    V0 = synth.haar_orthonormal(7, k)
+    perm = synth.epoch_permutations(8, n, epochs)
+    Vd = _dev(V0.T.copy())
+    snaps = otm.sgd_run_topic_exact(Vd, otm.DeviceCSR.from_host(X), _dev(W), _dev(M1),
+                                    _dev(perm), epochs, b, 0.05, 1.0, 1.0, snapshot_every=4,
+                                    precision=otm.PREC_BF16)
+    torch.cuda.synchronize()
+    Vo, so = ostgd.sgd_run_topic_exact(V0, X, W.astype(np.float64), M1, perm, b, 0.05, 1.0, 1.0,
+                                       snapshot_every=4)
+    assert rel(to_np(Vd).T, Vo) < 2e-2
+    for s_gpu, s_ref in zip(to_np(snaps), so):
+        assert rel(s_gpu.T, s_ref) < 2e-2
