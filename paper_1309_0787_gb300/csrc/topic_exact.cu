@@ -320,36 +320,56 @@ __global__ void te_v16_kernel(const float* __restrict__ V, int k, int kpad,
     V16[i * kpad + r] = __float2bfloat16(r < k ? V[i * k + r] : 0.f);
 }
 
-// out[c][r] = in[r][c] for r < rows, c < cols (in: rows x ld_in, out: cols x ld_out),
-// 32 x 32 tiles through shared memory.
+// out[c][r] = in[r][c] for r < rows, c < cols (in: rows x ld_in, out: cols x ld_out;
+// rows a multiple of 64, ld_in and ld_out even, cols <= ld_in), 64 x 64 tiles
+// through shared memory moved as BF16 pairs.
 __global__ void te_transpose16_kernel(const __nv_bfloat16* __restrict__ in, int64_t rows,
                                       int cols, int ld_in, __nv_bfloat16* __restrict__ out,
                                       int64_t ld_out) {
-  __shared__ __nv_bfloat16 tile[32][34];
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
-  const int c0 = blockIdx.y * 32;
+  __shared__ __nv_bfloat16 tile[64][66];
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int y = ty; y < 32; y += 8) {
+  const __nv_bfloat16 z = __float2bfloat16(0.f);
+  for (int y = ty; y < 64; y += 8) {
     const int64_t r = r0 + y;
-    const int c = c0 + tx;
-    tile[y][tx] = (r < rows && c < cols) ? in[r * ld_in + c] : __float2bfloat16(0.f);
+    const int c = c0 + 2 * tx;
+    __nv_bfloat162 v;
+    v.x = z;
+    v.y = z;
+    if (r < rows && c < ld_in)
+      v = *reinterpret_cast<const __nv_bfloat162*>(in + r * ld_in + c);
+    tile[y][2 * tx] = v.x;
+    tile[y][2 * tx + 1] = v.y;
   }
   __syncthreads();
-  for (int y = ty; y < 32; y += 8) {
+  for (int y = ty; y < 64; y += 8) {
     const int c = c0 + y;
-    const int64_t r = r0 + tx;
-    if (c < cols && r < rows) out[(int64_t)c * ld_out + r] = tile[tx][y];
+    const int64_t r = r0 + 2 * tx;
+    if (c < cols && r < rows) {
+      __nv_bfloat162 v;
+      v.x = tile[2 * tx][y];
+      v.y = tile[2 * tx + 1][y];
+      *reinterpret_cast<__nv_bfloat162*>(out + (int64_t)c * ld_out + r) = v;
+    }
   }
 }
 
-// Gd[e] = scale * sum_z part[z][e] in FP64, e < kk.
+// Gd[e] = scale * sum_z part[z][e] in FP64, e < kk (eight slices in flight per
+// thread, added in a fixed order).
 __global__ void te_reduce_kernel(const float* __restrict__ part, int64_t nz, int64_t kk,
                                  double scale, double* __restrict__ Gd) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= kk) return;
-  double acc = 0.0;
-  for (int64_t z = 0; z < nz; ++z) acc += (double)part[z * kk + e];
-  Gd[e] = acc * scale;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int64_t z = 0;
+  for (; z + 8 <= nz; z += 8) {
+#pragma unroll
+    for (int x = 0; x < 8; ++x) acc[x] += (double)part[(z + x) * kk + e];
+  }
+  for (; z < nz; ++z) acc[0] += (double)part[z * kk + e];
+  Gd[e] = (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]))) *
+          scale;
 }
 
 __global__ void te_docs_kernel(const int32_t* __restrict__ perm, int64_t n, int64_t pos0,
@@ -412,7 +432,7 @@ otm_status te_products16(const TeWs& s, int64_t k, int64_t nb, int64_t cap, cuda
   const int64_t capp = te_capp(cap), nz = capp / TE_KC;
   const int kpad = te_kpad(k);
   if (nz > 0) {
-    const dim3 tg((unsigned)(capp / 32), (unsigned)((k + 31) / 32));
+    const dim3 tg((unsigned)(capp / 64), (unsigned)((k + 63) / 64));
     te_transpose16_kernel<<<tg, 256, 0, st>>>(s.Wg16, capp, (int)k, kpad, s.Wt16, capp);
     OTM_CHECK_LAUNCH();
     te_transpose16_kernel<<<tg, 256, 0, st>>>(s.C16, capp, (int)k, kpad, s.Ct16, capp);
