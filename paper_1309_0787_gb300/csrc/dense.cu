@@ -839,57 +839,39 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
     for (int k = 0; k < n; ++k) Z[k * ldn + tid] *= inv;
   }
   __syncthreads();
-  // Gram-Schmidt inside groups of close eigenvalues (closer than 1e-4 ||T||:
-  // a spectrum with one dominant eigenvalue makes nearly all of them one
-  // group), by the whole block: for vector i, classical Gram-Schmidt twice --
-  // the warps form its dot products with the group's earlier vectors, then
-  // thread k updates element k.  A repeated eigenvalue makes the twisted
-  // factorisation return the same vector for every member; when Gram-Schmidt
-  // leaves less than half of a vector, it is regenerated by two
-  // inverse-iteration solves with the stored LDL^T factors of T - lambda I
-  // from a fixed pseudo-random start, and orthogonalised again.
-  {
+  // Gram-Schmidt inside groups of close eigenvalues (warp 0; groups are rare).
+  // A repeated eigenvalue makes the twisted factorisation return the same
+  // vector for every member; when Gram-Schmidt leaves less than half of a
+  // vector, it is regenerated by two inverse-iteration solves with the stored
+  // LDL^T factors of T - lambda I from a fixed pseudo-random start, and
+  // orthogonalised again.
+  if (warp == 0) {
     const float ctol = 1e-4f * tnorm;
-    float* sdot = P;  // free after the eigenvectors of T
     for (int i = 1; i < n; ++i) {
-      if (lam[i] - lam[i - 1] > ctol) continue;  // the same decision in every thread
       int j0 = i - 1;
+      if (lam[i] - lam[j0] > ctol) continue;
       while (j0 > 0 && lam[i] - lam[j0 - 1] <= ctol) --j0;
       for (int attempt = 0; attempt < 2; ++attempt) {
-        for (int pass = 0; pass < 2; ++pass) {
-          for (int jj = j0 + warp; jj < i; jj += NW) {
-            float dot = 0.f;
-            for (int k = lane; k < n; k += 32) dot = fmaf(Z[k * ldn + jj], Z[k * ldn + i], dot);
+        for (int jj = j0; jj < i; ++jj) {
+          float dot = 0.f;
+          for (int k = lane; k < n; k += 32) dot = fmaf(Z[k * ldn + jj], Z[k * ldn + i], dot);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-            if (lane == 0) sdot[jj - j0] = dot;
-          }
-          __syncthreads();
-          if (tid < n) {
-            float z = Z[tid * ldn + i];
-            for (int jj = j0; jj < i; ++jj) z = fmaf(-sdot[jj - j0], Z[tid * ldn + jj], z);
-            Z[tid * ldn + i] = z;
-          }
-          __syncthreads();
+          for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          for (int k = lane; k < n; k += 32) Z[k * ldn + i] -= dot * Z[k * ldn + jj];
+          __syncwarp();
         }
-        if (warp == 0) {
-          float nn = 0.f;
-          for (int k = lane; k < n; k += 32) nn = fmaf(Z[k * ldn + i], Z[k * ldn + i], nn);
+        float nn = 0.f;
+        for (int k = lane; k < n; k += 32) nn = fmaf(Z[k * ldn + i], Z[k * ldn + i], nn);
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-          if (lane == 0) red[0][0] = nn;
-        }
-        __syncthreads();
-        const float nn = red[0][0];
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
         if (nn > 0.25f || attempt == 1) {
           const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
-          if (tid < n) Z[tid * ldn + i] *= inv;
-          __syncthreads();
+          for (int k = lane; k < n; k += 32) Z[k * ldn + i] *= inv;
+          __syncwarp();
           break;
         }
         // regenerate: x = (L D L^T)^{-2} r, L D L^T = T - lambda_i I (forward factors of column i)
-        if (tid == 0) {
+        if (lane == 0) {
           const float* Dp = fac;
           for (int k = 0; k < n; ++k)
             Z[k * ldn + i] = sinf(12.9898f * (float)(k + 1) + 78.233f * (float)(i + 1));
@@ -912,7 +894,7 @@ __global__ void __launch_bounds__(TE_T) tridiag_eig_kernel(const double* __restr
             for (int k = 0; k < n; ++k) Z[k * ldn + i] *= inv;
           }
         }
-        __syncthreads();
+        __syncwarp();
       }
     }
   }
