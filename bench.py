@@ -1135,8 +1135,8 @@ def lda_oracle_checks(c, X, W, Y_docs, docs, Yb, yb, V0, V1):
 
 def lda_precisions(otm, torch, path, c, host, fp32_sgd_ms):
     """The precision form on the same whitened samples: sample quantisation, then
-    the 20 epochs of STGD from the same start in BF16 and in FP8 (tensor cores,
-    FP32 accumulation; medians of three runs).  Errors: one step of each
+    the 20 epochs of STGD from the same start in BF16, in FP8 and in FP8 with
+    two-term samples (tensor cores, FP32 accumulation; medians of three runs).  Errors: one step of each
     precision against the FP64 oracle (lda_oracle_checks), and the 20-epoch
     results against the FP32 one (relative reconstruction error of the
     components, relative error of the unwhitened topics)."""
@@ -1148,7 +1148,7 @@ def lda_precisions(otm, torch, path, c, host, fp32_sgd_ms):
     dev = Y.device
     res = {"fp32": {"sgd_ms": fp32_sgd_ms, "samples_per_s": n * ep / (fp32_sgd_ms / 1e3)}}
     V = {"fp32": V32}
-    precs = {"bf16": otm.PREC_BF16, "fp8": otm.PREC_FP8}
+    precs = {"bf16": otm.PREC_BF16, "fp8": otm.PREC_FP8, "fp8x2": otm.PREC_FP8X2}
     for nm, pr in precs.items():
         tq, ts = [], []
         for _ in range(3):

@@ -43,6 +43,14 @@
 // minibatch the way the per-sample rounding of the samples and of B does;
 // it was the largest error of the single-term form.
 //
+// Precision 3 (FP8 with two-term samples) also keeps every sample as two e4m3
+// terms at its one scale (Y_hi, Y_lo: a second plane of the sample image, n
+// rows after the first), and issues Y_hi V_hi + Y_hi V_lo + Y_lo V_hi for the
+// first product and Y_hi^T B + Y_lo^T B for the second.  On long whitened
+// samples the samples' own three-bit rounding is what remains above the
+// tolerance of the low-precision forms; two terms bring it to the level of
+// BF16 at BF16's bytes.
+//
 // Operand layouts in shared memory (no swizzle; 8-row x 16-byte core
 // matrices; LBO = stride between cores along K, SBO = along M/N):
 //   sample tile: core (tg, rg) = 8 samples x 16 B of coordinates at
@@ -93,6 +101,7 @@ struct TcArgs {
   float* V;
   float* V_snap;
   int* err;
+  int64_t lo_off;     // bytes from a sample's first e4m3 term to its second (0: one term)
   int64_t n, b, spe, total_steps, snapshot_every;
   int k, ldq;
   int nc;             // components: k, or R k for R restarts of one problem stacked
@@ -124,7 +133,7 @@ __host__ __device__ inline size_t al128(size_t x) { return (x + 127) & ~(size_t)
 // KPc: 128 or 256 padded coordinates; the second B image exists only with four
 // stages (where the second product is waited for two tiles later)
 __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, bool dbl,
-                                              int KPc) {
+                                              int KPc, int planes = 1) {
   TcLayout L;
   const int KP = KPc;
   L.KPc = KPc;
@@ -139,7 +148,7 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   L.CBn = N * es / 16;
   L.CBh = N * 2 / 16;
   L.y_view = (size_t)TILE * KP * es;
-  L.y_stage = L.nv * L.y_view;
+  L.y_stage = (size_t)planes * L.nv * L.y_view;  // second terms of the views after the first
   // KPc rows (components) x KPc coordinates, or only the N owned rows when streamed
   const size_t v_bytes = (size_t)(L.vstr ? N : KP) * KP * 2;
   L.off_v[0] = NS * L.y_stage;
@@ -257,6 +266,9 @@ __device__ __forceinline__ void load_tile(const TcArgs& a, const TcLayout& L, ui
         const bool in = row >= 0 && c0 < a.ldq;
         const uint8_t* src = in ? Yg + ((size_t)row * a.ldq + c0) * ES : Yg;
         cp_async16(dst + ((size_t)rg << 7), src, in ? 16u : 0u);
+        if (FP8 && a.lo_off)  // the second terms, into the views after the first
+          cp_async16(dst + (size_t)L.nv * L.y_view + ((size_t)rg << 7), in ? src + a.lo_off : Yg,
+                     in ? 16u : 0u);
       }
       if (c4 == 0) {
         const float* sv = v == 0 ? a.sA : (v == 1 ? a.sB : a.sC);
@@ -320,7 +332,8 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
     return;
   }
   const int N = own_cols(nc, CL);
-  const TcLayout L = tc_layout(N, SYM, ES, NS, dbl, KPc);
+  const TcLayout L = tc_layout(N, SYM, ES, NS, dbl, KPc, FP8 && a.lo_off ? 2 : 1);
+  const bool two_y = FP8 && a.lo_off != 0;
   const int own_lo = q * N;
   const bool active = own_lo < nc;
   const int nch = N / 16;
@@ -625,6 +638,11 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
             if (FP8)  // the residual term of V into the same accumulator
               mma<FP8>(tmem + (uint32_t)((slot * NVD + v) * N), dY + (uint64_t)(16 * ks),
                        dVq_lo + (uint64_t)(16 * ks), id1, 1u);
+            if (two_y)  // the samples' second term times V_hi
+              mma<FP8>(tmem + (uint32_t)((slot * NVD + v) * N),
+                       sdesc(Ys + (L.nv + v) * L.y_view, 128, (uint32_t)L.CR * 128) +
+                           (uint64_t)(16 * ks),
+                       dB + (uint64_t)(16 * ks), id1, 1u);
           }
         }
         mma_commit(&mb[slot]);
@@ -639,9 +657,15 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         for (int mbk = 0; mbk < MB; ++mbk) {  // 128 coordinates = 1024 ES bytes along M
           const uint64_t dA = sdesc(YC + (size_t)mbk * 1024 * ES, (uint32_t)L.CR * 128, 128);
           const uint32_t col = colD2b + (uint32_t)mbk * d2w + (FP8 ? (uint32_t)(slot * N) : 0u);
-          for (int ks = 0; ks < TILE / KSTEP; ++ks)
+          for (int ks = 0; ks < TILE / KSTEP; ++ks) {
             mma<FP8>(tmem + col, dA + stepA * ks, dB + stepB * ks, id2,
                      (FP8 ? ks > 0 : (n > 0 || ks > 0)) ? 1u : 0u);
+            if (two_y)  // Y_lo^T B into the same accumulator
+              mma<FP8>(tmem + col,
+                       sdesc(YC + (size_t)L.nv * L.y_view + (size_t)mbk * 1024 * ES,
+                             (uint32_t)L.CR * 128, 128) + stepA * ks,
+                       dB + stepB * ks, id2, 1u);
+          }
         }
         mma_commit(&mb[2 + slot]);
       };
@@ -1104,10 +1128,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // quantise rows: FP8 -> per-row scale amax/448; BF16 -> scale 1.  Output row
-// stride ldq (zero padded).
+// stride ldq (zero padded).  two (FP8 only): the rounding residual's e4m3 term
+// into a second plane n rows after the first, at the same scale.
 template <bool FP8>
 __global__ void quantize_rows_kernel(const float* __restrict__ Y, int64_t n, int k, int ldq,
-                                     uint8_t* __restrict__ Yq, float* __restrict__ scale) {
+                                     uint8_t* __restrict__ Yq, float* __restrict__ scale,
+                                     int two) {
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= n) return;
@@ -1123,6 +1149,10 @@ __global__ void quantize_rows_kernel(const float* __restrict__ Y, int64_t n, int
     if constexpr (FP8) {
       const __nv_fp8_e4m3 q(v);
       Yq[r * ldq + c] = *reinterpret_cast<const uint8_t*>(&q);
+      if (two) {
+        const __nv_fp8_e4m3 q2(v - (float)q);
+        Yq[(n + r) * ldq + c] = *reinterpret_cast<const uint8_t*>(&q2);
+      }
     } else {
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       reinterpret_cast<__nv_bfloat16*>(Yq)[r * ldq + c] = h;
@@ -1153,7 +1183,8 @@ struct TcPlan {
 
 // Whether the schedule (CL CTAs per chain, NS sample stages, single or double V
 // image) fits tensor memory, registers and shared memory for k components.
-bool tc_plan_fits(int k, bool sym, bool fp8, int CL, bool dbl, int NS, TcPlan* out) {
+bool tc_plan_fits(int k, bool sym, bool fp8, int CL, bool dbl, int NS, TcPlan* out,
+                  int planes = 1) {
   const int N = own_cols(k, CL);
   const int KPc = k <= 128 ? 128 : 256, MB = KPc / 128;
   if (N > 128 || (fp8 && N > 64)) return false;
@@ -1165,7 +1196,7 @@ bool tc_plan_fits(int k, bool sym, bool fp8, int CL, bool dbl, int NS, TcPlan* o
     return false;
   if (dbl && CL == 1) return false;
   const size_t lim = (size_t)max_smem_optin() - 1024;  // static shared variables
-  const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, NS, dbl, KPc);
+  const TcLayout L = tc_layout(N, sym, fp8 ? 1 : 2, NS, dbl, KPc, planes);
   if (L.vstr && (dbl || (size_t)NS * L.y_stage < (size_t)KPc * KPc * 2)) return false;
   if (L.total > lim) return false;
   *out = {CL, N, NS, dbl, L.total, L.vstr};
@@ -1177,19 +1208,19 @@ bool tc_plan_fits(int k, bool sym, bool fp8, int CL, bool dbl, int NS, TcPlan* o
 constexpr int kSchedules[8][2] = {{1, 4}, {1, 3}, {0, 4}, {0, 3}, {1, 2}, {0, 2}, {1, 1}, {0, 1}};
 
 // The first schedule of kSchedules that fits; false if none does.
-bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out) {
+bool tc_plan(int k, bool sym, bool fp8, int CL, TcPlan* out, int planes = 1) {
   for (const auto& o : kSchedules)
-    if (tc_plan_fits(k, sym, fp8, CL, o[0] != 0, o[1], out)) return true;
+    if (tc_plan_fits(k, sym, fp8, CL, o[0] != 0, o[1], out, planes)) return true;
   return false;
 }
 
 // Single chain: the smallest power-of-two cluster giving every CTA at most 16
 // components (more CTAs per chain shorten each step), growing if needed.
-bool tc_plan_single(int k, bool sym, bool fp8, TcPlan* out) {
+bool tc_plan_single(int k, bool sym, bool fp8, TcPlan* out, int planes = 1) {
   int CL = 1;
   while (CL < 16 && CL * 16 < round16(k)) CL *= 2;
   for (; CL <= 16; CL *= 2)
-    if (tc_plan(k, sym, fp8, CL, out)) return true;
+    if (tc_plan(k, sym, fp8, CL, out, planes)) return true;
   return false;
 }
 
@@ -1305,16 +1336,19 @@ otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precis
                                 float* scales, void* stream) {
   clear_error();
   OTM_REQUIRE(Y && Yq && n >= 1 && k >= 1 && k <= TC_KMAX, "otm_quantize_samples: bad arguments");
-  OTM_REQUIRE(precision == OTM_PREC_BF16 || precision == OTM_PREC_FP8,
-              "otm_quantize_samples: precision must be OTM_PREC_BF16 or OTM_PREC_FP8");
+  OTM_REQUIRE(precision == OTM_PREC_BF16 || precision == OTM_PREC_FP8 ||
+                  precision == OTM_PREC_FP8X2,
+              "otm_quantize_samples: precision must be OTM_PREC_BF16, OTM_PREC_FP8 or "
+              "OTM_PREC_FP8X2");
   OTM_REQUIRE(precision == OTM_PREC_BF16 || scales, "otm_quantize_samples: FP8 needs scales");
   const int ldq = (int)((k + 15) & ~15);
   cudaStream_t st = as_stream(stream);
   const unsigned grid = (unsigned)((n + 7) / 8);
-  if (precision == OTM_PREC_FP8)
-    quantize_rows_kernel<true><<<grid, 256, 0, st>>>(Y, n, (int)k, ldq, (uint8_t*)Yq, scales);
+  if (precision != OTM_PREC_BF16)
+    quantize_rows_kernel<true><<<grid, 256, 0, st>>>(Y, n, (int)k, ldq, (uint8_t*)Yq, scales,
+                                                     precision == OTM_PREC_FP8X2);
   else
-    quantize_rows_kernel<false><<<grid, 256, 0, st>>>(Y, n, (int)k, ldq, (uint8_t*)Yq, scales);
+    quantize_rows_kernel<false><<<grid, 256, 0, st>>>(Y, n, (int)k, ldq, (uint8_t*)Yq, scales, 0);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }
@@ -1334,22 +1368,24 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   OTM_REQUIRE(k >= 1 && k <= TC_KMAX, "otm_sgd_run_lp: k=%lld outside [1, %d]", (long long)k,
               TC_KMAX);
   OTM_REQUIRE(n >= 1 && b >= 1 && epochs >= 0, "otm_sgd_run_lp: need n >= 1, b >= 1, epochs >= 0");
-  OTM_REQUIRE(precision == OTM_PREC_BF16 || precision == OTM_PREC_FP8,
-              "otm_sgd_run_lp: precision must be OTM_PREC_BF16 or OTM_PREC_FP8");
+  OTM_REQUIRE(precision == OTM_PREC_BF16 || precision == OTM_PREC_FP8 ||
+                  precision == OTM_PREC_FP8X2,
+              "otm_sgd_run_lp: precision must be OTM_PREC_BF16, OTM_PREC_FP8 or OTM_PREC_FP8X2");
   OTM_REQUIRE(snapshot_every >= 0 && (snapshot_every == 0 || V_snap),
               "otm_sgd_run_lp: V_snap required for snapshots");
   OTM_REQUIRE(ws && ws_bytes >= otm_sgd_run_lp_workspace(), "otm_sgd_run_lp: workspace too small");
   if (epochs == 0) return OTM_OK;
-  const bool fp8 = precision == OTM_PREC_FP8;
+  const bool fp8 = precision != OTM_PREC_BF16;
+  const bool two_y = precision == OTM_PREC_FP8X2;
   const bool sym = (YA == YB) && (YB == YC);
   TcPlan P;
-  OTM_REQUIRE(tc_plan_single((int)k, sym, fp8, &P),
+  OTM_REQUIRE(tc_plan_single((int)k, sym, fp8, &P, two_y ? 2 : 1),
               "otm_sgd_run_lp: k=%lld does not fit on chip with %s views", (long long)k,
               sym ? "one" : "three");
   cudaStream_t st = as_stream(stream);
   int* err = static_cast<int*>(ws);
   OTM_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  TcArgs args;
+  TcArgs args{};
   args.YA = static_cast<const uint8_t*>(YA);
   args.YB = static_cast<const uint8_t*>(YB);
   args.YC = static_cast<const uint8_t*>(YC);
@@ -1368,6 +1404,7 @@ otm_status otm_sgd_run_lp(float* V, const void* YA, const void* YB, const void* 
   args.snapshot_every = snapshot_every;
   args.k = (int)k;
   args.ldq = (int)((k + 15) & ~15);
+  args.lo_off = two_y ? n * args.ldq : 0;
   args.nc = (int)k;
   args.beta0 = beta0;
   args.c1 = (float)((alpha0 + 1.0) * (alpha0 + 2.0) / 2.0);
@@ -1449,8 +1486,9 @@ otm_status otm_sgd_batched_prepare(const otm_problem* probs, int nprob, int prec
     const int64_t rs = P.k <= 64 ? 128 / P.k : 1;
     for (int64_t r = 0; r < P.restarts; r += rs) {
       const int64_t cnt = std::min<int64_t>(rs, P.restarts - r);
-      TcArgs a;
+      TcArgs a{};
       a.YA = a.YB = a.YC = static_cast<const uint8_t*>(P.Yq);
+      a.lo_off = 0;  // one e4m3 term per sample (two-term samples: single chains only)
       a.sA = a.sB = a.sC = P.scales;
       a.perm = P.perm;
       a.ybar3 = P.ybar3;

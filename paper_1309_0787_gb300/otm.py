@@ -463,6 +463,7 @@ def sgd_run(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, theta
 
 PREC_BF16 = 1
 PREC_FP8 = 2
+PREC_FP8X2 = 3  # e4m3 with two terms per sample (sgd_run_lp only)
 
 
 def sgd_run_topic_exact(V, X: DeviceCSR, W, M1, perm, epochs: int, b: int, beta0: float,
@@ -508,12 +509,14 @@ def sgd_run_topic_exact(V, X: DeviceCSR, W, M1, perm, epochs: int, b: int, beta0
 
 def quantize_samples(Y, precision: int):
     """Samples for the tensor-core STGD: returns (Yq, scales), Yq n x ldq
-    (ldq = k rounded up to 16) BF16 or FP8 e4m3 stored as bytes, scales n."""
+    (ldq = k rounded up to 16) BF16 or FP8 e4m3 stored as bytes (2 n rows for
+    PREC_FP8X2: the second e4m3 terms after the first), scales n."""
     n, k = Y.shape
     _need(Y, torch.float32, (n, k), "Y")
     ldq = (k + 15) // 16 * 16
     es = 2 if precision == PREC_BF16 else 1
-    Yq = torch.empty(n, ldq * es, dtype=torch.uint8, device=Y.device)
+    rows = 2 * n if precision == PREC_FP8X2 else n
+    Yq = torch.empty(rows, ldq * es, dtype=torch.uint8, device=Y.device)
     sc = torch.empty(n, dtype=torch.float32, device=Y.device)
     _check(_lib.otm_quantize_samples(_ptr(Y), n, k, int(precision), _ptr(Yq), _ptr(sc), _stream()))
     return Yq, sc
@@ -524,7 +527,7 @@ def sgd_run_lp(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, th
     """Tensor-core STGD.  YA/YB/YC are (Yq, scales) pairs from quantize_samples
     (pass the same pair three times for symmetric views)."""
     k = V.shape[0]
-    n = YA[0].shape[0]
+    n = YA[1].shape[0]  # the scales: one per sample (Yq has 2 n rows for PREC_FP8X2)
     _need(V, torch.float32, (k, k), "V")
     _need(ybar3, torch.float64, (3, k), "ybar3")
     if perm is not None:

@@ -67,6 +67,37 @@ def test_tc_fp8_gradient(otm, k, b, sym, a0):
     assert frob < 2e-2 and col < 2e-2, (frob, col)
 
 
+@pytest.mark.parametrize("k,b,sym,a0", [(100, 1024, False, 1.0), (100, 1024, True, 1.0),
+                                        (33, 300, False, 1.0), (128, 1024, True, 1.0),
+                                        (200, 512, True, 1.0), (256, 512, True, 0.5)])
+def test_tc_fp8x2_gradient(otm, k, b, sym, a0):
+    """FP8 with two-term samples: within 2e-2, and closer to the oracle than the
+    one-term FP8 on the same inputs."""
+    frob, col = _grad_err(otm, otm.PREC_FP8X2, k, b, sym, a0, 7 * k + b)
+    assert frob < 2e-2 and col < 2e-2, (frob, col)
+    frob1, _ = _grad_err(otm, otm.PREC_FP8, k, b, sym, a0, 7 * k + b)
+    assert frob < frob1, (frob, frob1)
+
+
+def test_quantize_samples_two_terms(otm):
+    """PREC_FP8X2 stores the e4m3 residual in a second plane at the same scale:
+    hi + lo reproduces the row within the two-term rounding (about 2^-8 of the
+    row's largest entry), and the first plane equals the one-term FP8 rows."""
+    g = np.random.default_rng(41)
+    Y = (g.standard_normal((300, 70)) * np.exp(g.standard_normal((300, 1)))).astype(np.float32)
+    q2, s2 = otm.quantize_samples(_dev(Y), otm.PREC_FP8X2)
+    q1, s1 = otm.quantize_samples(_dev(Y), otm.PREC_FP8)
+    torch.cuda.synchronize()
+    assert tuple(q2.shape) == (600, 80)
+    np.testing.assert_array_equal(to_np(q2[:300]), to_np(q1))
+    np.testing.assert_array_equal(to_np(s2), to_np(s1))
+    f8 = lambda q: q.view(torch.float8_e4m3fn).float().cpu().numpy().astype(np.float64)  # noqa: E731
+    rec = (f8(q2[:300]) + f8(q2[300:]))[:, :70] * to_np(s2)[:, None]
+    amax = np.abs(Y).max(axis=1, keepdims=True)
+    assert np.all(np.abs(rec - Y) <= amax * 2.0 ** -8 + 1e-30)
+    assert np.abs(rec - Y).max() < np.abs(f8(q1)[:, :70] * to_np(s1)[:, None] - Y).max()
+
+
 @pytest.fixture(scope="module")
 def lda_samples():
     """Whitened samples of a synthetic LDA corpus (6,000 documents of Poisson(300)
@@ -84,7 +115,7 @@ def lda_samples():
     return Y, a0
 
 
-@pytest.mark.parametrize("prec_name", ["PREC_BF16", "PREC_FP8"])
+@pytest.mark.parametrize("prec_name", ["PREC_BF16", "PREC_FP8", "PREC_FP8X2"])
 def test_tc_gradient_on_lda_samples(otm, lda_samples, prec_name):
     """One step on a minibatch of whitened LDA samples (Section 3.1): the whitened
     documents share a large mean and carry word-sampling noise, so the
