@@ -403,7 +403,7 @@ otm_status otm_sgd_run_topic_exact(float* V, const otm_csr* X, const float* W, c
 
 #define OTM_PREC_BF16 1
 #define OTM_PREC_FP8 2 /* e4m3 */
-#define OTM_PREC_FP8X2 3 /* e4m3 with two terms per sample (otm_sgd_run_lp only) */
+#define OTM_PREC_FP8X2 3 /* e4m3, samples and B as two terms (otm_sgd_run_lp only) */
 
 /*
  * otm_quantize_samples -- store whitened samples for the low-precision STGD.
@@ -431,8 +431,9 @@ otm_status otm_quantize_samples(const float* Y, int64_t n, int64_t k, int precis
  * a_A = V^T ybar_A, a_B = V^T ybar_B for k <= 128 (k > 128: FP32 sums of the
  * BF16 rows on the CUDA cores); the master V, the mean terms and the update
  * stay FP32.  ybar3 are the FP64 means of the unquantised samples.
- * OTM_PREC_FP8X2 (samples stored as two e4m3 terms): the first product takes
- * Y_hi V_hi + Y_hi V_lo + Y_lo V_hi and the second Y_hi^T B + Y_lo^T B, which
+ * OTM_PREC_FP8X2 (samples stored as two e4m3 terms; B split the same way at
+ * its per-tile scales): the first product takes Y_hi V_hi + Y_hi V_lo +
+ * Y_lo V_hi and the second Y_hi^T B_hi + Y_lo^T B_hi + Y_hi^T B_lo, which
  * brings long whitened samples (those of a 300-word LDA corpus) within 2e-2.
  * 1 <= k <= 256; for k > 128 every CTA of the cluster keeps only its own rows
  * of the BF16 image on chip and the whole image is exchanged through two

@@ -43,13 +43,14 @@
 // minibatch the way the per-sample rounding of the samples and of B does;
 // it was the largest error of the single-term form.
 //
-// Precision 3 (FP8 with two-term samples) also keeps every sample as two e4m3
-// terms at its one scale (Y_hi, Y_lo: a second plane of the sample image, n
-// rows after the first), and issues Y_hi V_hi + Y_hi V_lo + Y_lo V_hi for the
-// first product and Y_hi^T B + Y_lo^T B for the second.  On long whitened
-// samples the samples' own three-bit rounding is what remains above the
-// tolerance of the low-precision forms; two terms bring it to the level of
-// BF16 at BF16's bytes.
+// Precision 3 (FP8 with two-term operands) also keeps every sample as two
+// e4m3 terms at its one scale (Y_hi, Y_lo: a second plane of the sample image,
+// n rows after the first) and B as two terms at its per-tile scales (B_hi,
+// B_lo: a second plane of the B image), and issues Y_hi V_hi + Y_hi V_lo +
+// Y_lo V_hi for the first product and Y_hi^T B_hi + Y_lo^T B_hi + Y_hi^T B_lo
+// for the second.  On long whitened samples the three-bit rounding of the
+// samples and of B is what remains above the tolerance of the low-precision
+// forms once V has two terms.
 //
 // Operand layouts in shared memory (no swizzle; 8-row x 16-byte core
 // matrices; LBO = stride between cores along K, SBO = along M/N):
@@ -124,6 +125,7 @@ struct TcLayout {
              // the whole image is streamed from global scratch into the sample stages for
              // the Gram term, and the FP32 master rows live in tensor memory
   size_t y_view, y_stage, off_v[2], off_vq, off_yb, off_b[2], off_h, off_f;
+  size_t blo;  // bytes from a B image to its second e4m3 plane (two-term operands; else 0)
   size_t vm, ybA, ybB, ybC, aA, aB, vsc, bsc, amax, spw, red, ssc, nfloat;
   size_t total;
 };
@@ -167,9 +169,11 @@ __host__ __device__ inline TcLayout tc_layout(int N, bool sym, int es, int NS, b
   const bool in_stage = NS == 1 && !L.vstr && h_bytes <= L.y_stage && yb_bytes <= L.y_stage;
   L.off_b[0] = al128(L.off_vq + vq_bytes);
   L.off_b[1] = NS >= 4 ? L.off_b[0] + b_bytes : L.off_b[0];
+  // two-term operands: the second planes of the B images after both first planes
+  L.blo = planes > 1 ? L.off_b[1] + b_bytes - L.off_b[0] : 0;
   L.off_yb = in_stage ? 0 : L.off_b[0];
   L.off_h = in_stage ? 0 : L.off_b[0];  // the H image reuses both B images (free by then)
-  size_t end = L.off_b[1] + b_bytes;
+  size_t end = L.off_b[1] + b_bytes + L.blo;
   if (L.off_h + h_bytes > end) end = L.off_h + h_bytes;
   if (L.off_yb + yb_bytes > end) end = L.off_yb + yb_bytes;
   L.off_f = al128(end);
@@ -652,6 +656,7 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
         const int slot = n & 1;
         const uint8_t* YC = smem + (size_t)st * L.y_stage + (SYM ? 0 : 2 * L.y_view);
         const uint64_t dB = sdesc(slot ? Bimg1 : Bimg0, (uint32_t)L.CBn * 128, 128);
+        const uint64_t dBl = sdesc((slot ? Bimg1 : Bimg0) + L.blo, (uint32_t)L.CBn * 128, 128);
         const uint64_t stepA = (uint64_t)((KSTEP / 8) * L.CR * 8);   // (KSTEP/8) core groups
         const uint64_t stepB = (uint64_t)((KSTEP / 8) * L.CBn * 8);  // in 16-byte units
         for (int mbk = 0; mbk < MB; ++mbk) {  // 128 coordinates = 1024 ES bytes along M
@@ -660,11 +665,13 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
           for (int ks = 0; ks < TILE / KSTEP; ++ks) {
             mma<FP8>(tmem + col, dA + stepA * ks, dB + stepB * ks, id2,
                      (FP8 ? ks > 0 : (n > 0 || ks > 0)) ? 1u : 0u);
-            if (two_y)  // Y_lo^T B into the same accumulator
+            if (two_y) {  // Y_lo^T B_hi and Y_hi^T B_lo into the same accumulator
               mma<FP8>(tmem + col,
                        sdesc(YC + (size_t)L.nv * L.y_view + (size_t)mbk * 1024 * ES,
                              (uint32_t)L.CR * 128, 128) + stepA * ks,
                        dB + stepB * ks, id2, 1u);
+              mma<FP8>(tmem + col, dA + stepA * ks, dBl + stepB * ks, id2, 1u);
+            }
           }
         }
         mma_commit(&mb[2 + slot]);
@@ -835,11 +842,18 @@ __device__ void tc_chain(const TcArgs& a, uint8_t* smem, TcCtx& cx, int NS, bool
                 w[j] = FP8 ? b / bsc[slot * N + i] : b;
               }
               if constexpr (FP8) {
+                const size_t off = (((size_t)(t >> 3) * L.CBn + c) << 7) + ((t & 7) << 4) + 8 * hf;
                 uint2 u;
-                u.x = pack_e4m3(w[0], w[1], w[2], w[3]);
-                u.y = pack_e4m3(w[4], w[5], w[6], w[7]);
-                *reinterpret_cast<uint2*>(Bi + ((((size_t)(t >> 3) * L.CBn + c) << 7) +
-                                                ((t & 7) << 4) + 8 * hf)) = u;
+                if (two_y) {  // B_hi and the residual B_lo, one scale
+                  uint2 ul;
+                  split_e4m3(w[0], w[1], w[2], w[3], u.x, ul.x);
+                  split_e4m3(w[4], w[5], w[6], w[7], u.y, ul.y);
+                  *reinterpret_cast<uint2*>(Bi + L.blo + off) = ul;
+                } else {
+                  u.x = pack_e4m3(w[0], w[1], w[2], w[3]);
+                  u.y = pack_e4m3(w[4], w[5], w[6], w[7]);
+                }
+                *reinterpret_cast<uint2*>(Bi + off) = u;
               } else {
                 uint4 u;
                 u.x = pack_bf16(w[0], w[1]);

@@ -463,7 +463,7 @@ def sgd_run(V, YA, YB, YC, ybar3, perm, epochs: int, b: int, beta0: float, theta
 
 PREC_BF16 = 1
 PREC_FP8 = 2
-PREC_FP8X2 = 3  # e4m3 with two terms per sample (sgd_run_lp only)
+PREC_FP8X2 = 3  # e4m3, samples and B as two terms (sgd_run_lp only)
 
 
 def sgd_run_topic_exact(V, X: DeviceCSR, W, M1, perm, epochs: int, b: int, beta0: float,

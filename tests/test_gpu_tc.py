@@ -71,8 +71,8 @@ def test_tc_fp8_gradient(otm, k, b, sym, a0):
                                         (33, 300, False, 1.0), (128, 1024, True, 1.0),
                                         (200, 512, True, 1.0), (256, 512, True, 0.5)])
 def test_tc_fp8x2_gradient(otm, k, b, sym, a0):
-    """FP8 with two-term samples: within 2e-2, and closer to the oracle than the
-    one-term FP8 on the same inputs."""
+    """FP8 with two-term samples and B: within 2e-2, and closer to the oracle than
+    the one-term FP8 on the same inputs."""
     frob, col = _grad_err(otm, otm.PREC_FP8X2, k, b, sym, a0, 7 * k + b)
     assert frob < 2e-2 and col < 2e-2, (frob, col)
     frob1, _ = _grad_err(otm, otm.PREC_FP8, k, b, sym, a0, 7 * k + b)
