@@ -1,9 +1,10 @@
 """GPU parity of the tensor-core (BF16 / FP8) STGD against the FP64 oracle.
 
 The low-precision path quantises the samples, V and B (per-sample and
-per-component scales) and accumulates in FP32; FP8 keeps V as two e4m3 terms.
-The oracle computes Lemma 3 in FP64 from the unquantised samples.  Tolerance
-for both precisions: 2e-2 normwise relative,
+per-component scales) and accumulates in FP32; FP8 keeps V as two e4m3 terms,
+and the two-term FP8 form the samples and B as well.  The oracle computes
+Lemma 3 in FP64 from the unquantised samples.  Tolerance for every precision:
+2e-2 normwise relative,
 ||G - G64||_F / (||kappa G_gram||_F + ||G_data||_F), and the same ratio for
 every column (component) of G on its own, so that one wrong component or tile
 cannot hide inside the Frobenius norm.
