@@ -255,36 +255,69 @@ __global__ void __launch_bounds__(256) gemm_nn_tile_kernel(
   }
 }
 
-// out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64), FP64 FMAs.
-constexpr int D_R = 32, D_C = 32, D_K = 32;
+// out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64) to about 2^-48
+// relative to sum_j |A[r][j] C[j][c]|, on the FP32 units (FP64 issues at 1/64 of
+// the FP32 rate on this part).  Each C entry is split into two float32 terms,
+// c = c_hi + c_lo (c_hi = fl32(c), c_lo = fl32(c - c_hi)); a * c_hi is formed
+// exactly as the pair (p, e) with one FMA (Dekker's product, FMA form); a * c_lo
+// is rounded (its error is 2^-24 of a term already 2^-24 below a * c).  The sum
+// is a double-float (hi, lo): hi takes p by Knuth's branch-free TwoSum, whose
+// rounding error joins lo together with e and a * c_lo, and (hi, lo) is
+// renormalised by a second TwoSum after every term (cancellation can leave
+// |lo| > |hi|).  The _rn intrinsics keep the compiler from contracting the
+// product into the following add, which the exact-error steps rely on.  Tile:
+// 64 rows x 32 columns per 256 threads, 8 rows per thread; the row of A is a
+// shared-memory broadcast.
+constexpr int D_R = 64, D_C = 32, D_K = 32;
 __global__ void __launch_bounds__(256) gemm_nn_f64_kernel(const float* __restrict__ A,
                                                           int64_t rows, int64_t m,
                                                           const double* __restrict__ C,
                                                           int64_t p, double* __restrict__ out) {
-  __shared__ double As[D_R][D_K + 1];
-  __shared__ double Cs[D_K][D_C];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 4 rows per thread
+  __shared__ float As[D_R][D_K + 1];
+  __shared__ float Ch[D_K][D_C];
+  __shared__ float Cl[D_K][D_C];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows per thread
   const int64_t r0 = (int64_t)blockIdx.x * D_R, c0 = (int64_t)blockIdx.y * D_C;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float hi[8], lo[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0.f;
   for (int64_t k0 = 0; k0 < m; k0 += D_K) {
     for (int idx = threadIdx.x; idx < D_R * D_K; idx += 256) {
       const int rr = idx / D_K, kk = idx % D_K;
-      As[rr][kk] = (r0 + rr < rows && k0 + kk < m) ? (double)A[(r0 + rr) * m + k0 + kk] : 0.0;
-      Cs[rr][kk] = (k0 + rr < m && c0 + kk < p) ? C[(k0 + rr) * p + c0 + kk] : 0.0;
+      As[rr][kk] = (r0 + rr < rows && k0 + kk < m) ? A[(r0 + rr) * m + k0 + kk] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < D_K * D_C; idx += 256) {
+      const int kk = idx / D_C, cc = idx % D_C;
+      const double c = (k0 + kk < m && c0 + cc < p) ? C[(k0 + kk) * p + c0 + cc] : 0.0;
+      const float ch = (float)c;
+      Ch[kk][cc] = ch;
+      Cl[kk][cc] = (float)(c - (double)ch);
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int kk = 0; kk < D_K; ++kk) {
-      const double c = Cs[kk][tx];
+      const float ch = Ch[kk][tx], cl = Cl[kk][tx];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty * 4 + q][kk], c, acc[q]);
+      for (int q = 0; q < 8; ++q) {
+        const float a = As[ty * 8 + q][kk];
+        const float pr = __fmul_rn(a, ch);
+        const float e = fmaf(a, ch, -pr);  // a * ch = pr + e exactly
+        const float s = __fadd_rn(hi[q], pr);  // TwoSum(hi, pr)
+        const float bv = __fsub_rn(s, hi[q]);
+        const float err = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(s, bv)), __fsub_rn(pr, bv));
+        const float l = __fadd_rn(lo[q], __fadd_rn(err, fmaf(a, cl, e)));
+        const float h2 = __fadd_rn(s, l);      // TwoSum(s, l)
+        const float b2 = __fsub_rn(h2, s);
+        lo[q] = __fadd_rn(__fsub_rn(s, __fsub_rn(h2, b2)), __fsub_rn(l, b2));
+        hi[q] = h2;
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t r = r0 + ty * 4 + q, c = c0 + tx;
-    if (r < rows && c < p) out[r * p + c] = acc[q];
+  for (int q = 0; q < 8; ++q) {
+    const int64_t r = r0 + ty * 8 + q, c = c0 + tx;
+    if (r < rows && c < p) out[r * p + c] = (double)hi[q] + (double)lo[q];
   }
 }
 

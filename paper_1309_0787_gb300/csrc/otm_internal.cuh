@@ -111,7 +111,8 @@ otm_status gemm_nn_small(const float* A, int64_t rows, int64_t m, const float* C
                          float* out, const double* r1_u, const double* r1_v, double r1_alpha,
                          cudaStream_t st, const int* skip = nullptr);
 otm_status f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
-// out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64), FP64 accumulation.
+// out (rows x p, FP64) = A (rows x m, float32) * C (m x p, FP64), sums accurate to
+// about 2^-48 (double-float arithmetic on the FP32 units).
 otm_status gemm_nn_f64(const float* A, int64_t rows, int64_t m, const double* C, int64_t p,
                        double* out, cudaStream_t st);
 // Small FP64 GEMM: C (m x n) = op(A) op(B), op = transpose if flag set.

@@ -349,6 +349,29 @@ def test_unwhiten(otm, d, k, kt, normalize):
     np.testing.assert_allclose(to_np(out["alpha_hat"]), ref["alpha_hat"], rtol=1e-12)
 
 
+def test_unwhiten_product_elementwise(otm):
+    """The d x k product Q M of the unwhitening is summed in double-float on the
+    FP32 units: every entry within 2^-44 of the sum of its absolute terms
+    (|Q| |M|), which a float32 accumulation (about 2^-24 of it) misses by far.
+    M = Cp (V / ||v_i||) diag(lambda) in FP64 (Lemma 4); columns of M of very
+    different scales and the signs of Q make the sums cancel."""
+    g = np.random.default_rng(77)
+    d, k, kt = 3000, 30, 40
+    Q = np.linalg.qr(g.standard_normal((d, kt)))[0].astype(np.float32)
+    Cp = g.standard_normal((kt, k)) * np.exp(3.0 * g.standard_normal((1, k)))
+    V = (g.standard_normal((k, k)) + 2 * np.eye(k)).astype(np.float32)
+    out = otm.unwhiten(_dev(V.T.copy()), _dev(Q), _dev(Cp), 1.0, False)
+    torch.cuda.synchronize()
+    Q64, V64 = Q.astype(np.float64), V.astype(np.float64)
+    norms = np.linalg.norm(V64, axis=0)
+    M = Cp @ (V64 / norms) * (0.5 * (1.0 + 1.0) * norms ** 3)
+    ref = Q64 @ M
+    np.testing.assert_allclose(ref, opost.unwhiten(V64, Q64 @ Cp, 1.0, False)["mu"],
+                               rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    bound = 2.0 ** -44 * (np.abs(Q64) @ np.abs(M)) + 1e-300
+    assert np.all(np.abs(to_np(out["comps"]) - ref) <= bound)
+
+
 @pytest.mark.parametrize("k", [4, 64, 100])
 def test_recon_error(otm, k):
     g = np.random.default_rng(k)
