@@ -380,30 +380,121 @@ __global__ void csc_block_scan_kernel(int32_t* __restrict__ bc, int64_t nblocks,
   total[w] = run;
 }
 
+// Pass 2 in phases over ranges of consecutive words [wl, wh), each holding at
+// most `quota` entries (or one word) and at most W words: in a phase the CTA
+// keeps one 32-bit cursor per word of the range, colptr[w] + bc[b][w], and
+// places the block's entries of those words at the cursor (atomic increment).
+// Every CTA derives the same ranges from colptr and runs them in the same
+// order, so the output being written at a time is the one contiguous slice
+// colptr[wl] .. colptr[wh]: small enough for L2 to hold its partly written
+// sectors until they are complete, instead of evicting them half written (a
+// read-modify-write in DRAM for each) as one pass over all words does.  The
+// ranges follow the entry counts, not the word indices: under Zipf-skewed word
+// frequencies the first eighth of the words holds three quarters of the
+// entries.  The block's column indices are read once per phase, streamed:
+// where col is 16-byte aligned, warp w takes the w-th contiguous share of the
+// block's 128-entry slabs (one int4 per lane per slab, four slabs in flight),
+// and each lane follows the row of its entries with a cursor that only moves
+// forward (one binary search per warp and phase); the few unaligned entries at
+// the ends, or all of them otherwise, are placed one by one with a search each.
 __global__ void __launch_bounds__(1024) csc_block_fill_kernel(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     const float* __restrict__ val, int64_t rows, int64_t R, int64_t d,
-    const int32_t* __restrict__ colptr, const int32_t* __restrict__ bc, int64_t nnz,
-    int32_t* __restrict__ rowT, float* __restrict__ valT) {
-  extern __shared__ uint32_t cnt2[];
-  const int64_t dh = (d + 1) >> 1;
-  for (int64_t i = threadIdx.x; i < dh; i += blockDim.x) cnt2[i] = 0u;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int32_t* __restrict__ colptr, const int32_t* __restrict__ bc, int64_t nnz, int64_t W,
+    int64_t quota, int vec, int32_t* __restrict__ rowT, float* __restrict__ valT) {
+  extern __shared__ int32_t cur[];
+  __shared__ int64_t s_wh;
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int64_t r1 = r0 + R < rows ? r0 + R : rows;
   const int32_t* off = bc + (int64_t)blockIdx.x * d;
-  for (int64_t r = r0 + warp; r < r1; r += nw) {
-    for (int32_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
-      const int32_t w = col[e];
-      const uint32_t sh = (w & 1) * 16;
-      const uint32_t rank = (atomicAdd(&cnt2[w >> 1], 1u << sh) >> sh) & 0xFFFFu;
-      const int64_t pos = (int64_t)colptr[w] + off[w] + rank;
-      if (pos < nnz) {  // always, for distinct columns within each row
-        rowT[pos] = (int32_t)r;
-        valT[pos] = val[e];
+  const int64_t E0 = row_ptr[r0], E1 = row_ptr[r1];
+  // aligned body [A0, A1) read as int4, the head and the tail one by one
+  int64_t A0 = vec ? (E0 + 3) & ~(int64_t)3 : E1, A1 = vec ? E1 & ~(int64_t)3 : E1;
+  if (A0 > A1) A0 = A1 = E1;
+  auto row_of = [&](int64_t e) {  // the largest r in [r0, r1) with row_ptr[r] <= e
+    int64_t lo = r0, hi = r1 - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if ((int64_t)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t nslab = (A1 - A0 + 127) >> 7;
+  const int64_t s0 = nslab * warp / nw, s1 = nslab * (warp + 1) / nw;
+  const int64_t rstart = s0 < s1 ? row_of(A0 + (s0 << 7)) : r0;
+  auto place = [&](int64_t e, int32_t w, int64_t wl) {
+    const int64_t lo = row_of(e);
+    const int32_t pos = atomicAdd(&cur[w - wl], 1);
+    if (pos >= 0 && pos < nnz) {  // always, for distinct columns within each row
+      rowT[pos] = (int32_t)lo;
+      valT[pos] = val[e];
+    }
+  };
+  for (int64_t wl = 0; wl < d;) {
+    __syncthreads();  // the previous phase's cursors and s_wh are no longer used
+    if (threadIdx.x == 0) {
+      // the largest wh <= min(wl + W, d) with colptr[wh] - colptr[wl] <= quota, at least wl + 1
+      int64_t lo = wl + 1, hi = wl + W < d ? wl + W : d;
+      const int64_t lim = (int64_t)colptr[wl] + quota;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)colptr[mid] <= lim) lo = mid; else hi = mid - 1;
+      }
+      s_wh = lo;
+    }
+    __syncthreads();
+    const int64_t wh = s_wh;
+    for (int64_t w = wl + threadIdx.x; w < wh; w += blockDim.x) cur[w - wl] = colptr[w] + off[w];
+    __syncthreads();
+    for (int64_t e = E0 + threadIdx.x; e < A0; e += blockDim.x) {
+      const int32_t w = __ldcs(col + e);
+      if (w >= wl && w < wh) place(e, w, wl);
+    }
+    for (int64_t e = A1 + threadIdx.x; e < E1; e += blockDim.x) {
+      const int32_t w = __ldcs(col + e);
+      if (w >= wl && w < wh) place(e, w, wl);
+    }
+    if (s0 < s1) {
+      const int4* c4p = reinterpret_cast<const int4*>(col) + (A0 >> 2);
+      const int64_t q1 = (A1 - A0) >> 2;  // int4 of the body
+      int64_t r = rstart;                 // row cursor of this lane
+      for (int64_t sl = s0; sl < s1; sl += 4) {
+        int4 c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t q = (sl + u) * 32 + lane;
+          c[u] = (sl + u < s1 && q < q1) ? __ldcs(c4p + q) : make_int4(-1, -1, -1, -1);
+        }
+        // the values of the matching entries, all loads issued before any is used
+        float v[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t e = A0 + 4 * ((sl + u) * 32 + lane);
+          const int32_t cw[4] = {c[u].x, c[u].y, c[u].z, c[u].w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            v[u][j] = (cw[j] >= wl && cw[j] < wh) ? __ldcs(val + e + j) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t e = A0 + 4 * ((sl + u) * 32 + lane);
+          const int32_t cw[4] = {c[u].x, c[u].y, c[u].z, c[u].w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (cw[j] >= wl && cw[j] < wh) {
+              while ((int64_t)row_ptr[r + 1] <= e + j) ++r;
+              const int32_t pos = atomicAdd(&cur[cw[j] - wl], 1);
+              if (pos >= 0 && pos < nnz) {
+                rowT[pos] = (int32_t)r;
+                valT[pos] = v[u][j];
+              }
+            }
+          }
+        }
       }
     }
+    wl = wh;
   }
 }
 
@@ -664,16 +755,21 @@ otm_status csr_transpose(const otm_csr* X, int32_t* colptr, int32_t* rowT, float
     const size_t smem = (size_t)((d + 1) / 2) * 4;
     OTM_CHECK_CUDA(cudaFuncSetAttribute(csc_block_count_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    OTM_CHECK_CUDA(cudaFuncSetAttribute(csc_block_fill_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     csc_block_count_kernel<<<(unsigned)nb, 1024, smem, st>>>(X->row_ptr, X->col, n, R, d, bc);
     OTM_CHECK_LAUNCH();
     csc_block_scan_kernel<<<(unsigned)((d + 255) / 256), 256, 0, st>>>(bc, nb, d, cursor);
     OTM_CHECK_LAUNCH();
     exclusive_scan_kernel<<<1, 1024, 0, st>>>(cursor, d, colptr, cursor);
     OTM_CHECK_LAUNCH();
-    csc_block_fill_kernel<<<(unsigned)nb, 1024, smem, st>>>(X->row_ptr, X->col, X->val, n, R, d,
-                                                            colptr, bc, nnz, rowT, valT);
+    // word ranges of at most 96 MB of output (8 bytes per entry) and 49,152 cursors
+    const int64_t W = d < 49152 ? d : 49152, quota = (96ll << 20) / 8;
+    const int vec = (reinterpret_cast<uintptr_t>(X->col) & 15) == 0;
+    const size_t fsmem = (size_t)W * sizeof(int32_t);
+    OTM_CHECK_CUDA(cudaFuncSetAttribute(csc_block_fill_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    csc_block_fill_kernel<<<(unsigned)nb, 1024, fsmem, st>>>(X->row_ptr, X->col, X->val, n, R, d,
+                                                             colptr, bc, nnz, W, quota, vec,
+                                                             rowT, valT);
     OTM_CHECK_LAUNCH();
     return OTM_OK;
   }

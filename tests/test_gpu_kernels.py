@@ -150,6 +150,43 @@ def test_csr_transpose_matches_scipy(otm, n):
     _check_transpose(otm, synth.csr_from_dense(dense))
 
 
+def test_csr_transpose_in_word_phases(otm):
+    """A corpus whose transpose (8 bytes per entry) is larger than 96 MB, so that
+    the placement pass runs in two phases over ranges of words: 100,000
+    documents of Poisson(150) words over 20,000 words (about 14 M entries), word 3
+    in every document, word 7 in none, document 11 empty."""
+    sp = pytest.importorskip("scipy.sparse")
+    n, d = 100000, 20000
+    X = _corpus(23, n, d, 8, 150)["X"]
+    Xs = sp.csr_matrix((X.val.astype(np.float64), X.col, X.row_ptr), shape=(n, d))
+    Xs = Xs + sp.csr_matrix((np.ones(n), (np.arange(n), np.full(n, 3))), shape=(n, d))
+    cmask = np.ones(d)
+    cmask[7] = 0.0
+    rmask = np.ones(n)
+    rmask[11] = 0.0
+    Xs = (sp.diags(rmask) @ Xs @ sp.diags(cmask)).tocsr()
+    Xs.eliminate_zeros()
+    Xs.sort_indices()
+    assert Xs.nnz * 8 > 96 << 20
+    _check_transpose(otm, synth.CSR(Xs.indptr, Xs.indices, Xs.data, (n, d)))
+
+
+def test_csr_transpose_word_ranges_capped(otm):
+    """60,000 words, more than the 49,152 cursors of one placement phase: two
+    phases by the word cap although the corpus is small (4,000 documents of 50
+    words, uniform over the vocabulary; words 0, 49,151, 49,152 and 59,999, the
+    edges of the phases, in every document)."""
+    g = np.random.default_rng(29)
+    n, d, per = 4000, 60000, 50
+    edges = np.array([0, 49151, 49152, 59999])
+    pool = np.setdiff1d(np.arange(d), edges)
+    cols = np.stack([np.sort(np.concatenate([edges, g.choice(pool, per - 4, replace=False)]))
+                     for _ in range(n)])
+    row_ptr = np.arange(n + 1, dtype=np.int64) * per
+    X = synth.CSR(row_ptr, cols.reshape(-1), g.integers(1, 5, n * per).astype(np.float64), (n, d))
+    _check_transpose(otm, X)
+
+
 def test_csr_transpose_wide_vocabulary(otm):
     """A vocabulary too wide for the per-block counts in shared memory (150,000
     words): the transpose takes one atomic position per entry, same result."""
