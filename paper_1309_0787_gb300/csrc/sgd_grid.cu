@@ -19,7 +19,8 @@
 // owns components i = g, g + G, ...: it sums the G partials of its columns,
 // adds the Gram and mean terms, and writes the new column (and its means
 // a_A, a_B) to the iterate buffer of the next step.  Grid barrier.  Every CTA
-// reloads V from that buffer at the start of the next step.  Two grid
+// reloads V from that buffer at the start of the next step (one bulk copy,
+// completing on an mbarrier, where the buffers are 16-byte aligned).  Two grid
 // barriers per step; the partial sums are added in a fixed order, so the
 // result does not depend on timing.  The samples of step s + 1 do not depend
 // on V: they are copied (cp.async) into a second buffer at the start of step
@@ -56,6 +57,7 @@ struct GridArgs {
   int64_t n, b, spe, total_steps, snapshot_every;
   int k, S;
   int vec;        // sample rows are 16-byte aligned (k % 4 == 0, aligned bases)
+  int bulkv;      // Vg and means are 16-byte aligned: V and its means reload by bulk copy
   double beta0;
   float c1, c2, c3, kappa;
 };
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
   __shared__ float s_red[2][GT / 32];
   __shared__ float s_si;
   __shared__ int s_row[2][G_SMAX];  // sample rows of this CTA, by step parity (-1: none)
+  __shared__ __align__(8) uint64_t s_vb;  // completion of the bulk reload of V and its means
   const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k;
   const GLayout L = g_layout(k, SYM, a.S);
@@ -185,8 +188,14 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     tc::cp_async_commit();
   };
   if (tid < S) s_row[0][tid] = row_of(0, tid);
+  if (tid == 0) {
+    tc::mbar_init(&s_vb, 1);
+    tc::mbar_fence_init();
+  }
   __syncthreads();
   issue_samples(0);
+  uint32_t vph = 0;  // phase of s_vb
+  const uint32_t vbytes = (uint32_t)(kp * ld * sizeof(float)), mbytes = (uint32_t)(2 * kp * sizeof(float));
   for (int i = warp; i < kp; i += GT / 32) {  // a_A, a_B of the initial V
     float x = 0.f, y = 0.f;
     for (int r = lane; r < kp; r += 32) {
@@ -213,7 +222,16 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     // rows of the next step's samples; the iterate the owners wrote in the
     // previous step and its means (every load issued before any store)
     if (tid < S) s_row[par ^ 1][tid] = row_of(s + 1, tid);
-    {
+    if (a.bulkv) {
+      // every generic access of Vs and aA of the last step is behind the grid
+      // barrier's CTA barrier; the owners fenced their writes for the async proxy
+      if (s > 0 && tid == 0) {
+        tc::fence_async_smem();
+        tc::mbar_expect_tx(&s_vb, vbytes + mbytes);
+        tc::bulk_g2s(Vs, a.Vg + (size_t)par * kp * ld, vbytes, &s_vb);
+        tc::bulk_g2s(aA, a.means + (size_t)par * 2 * kp, mbytes, &s_vb);
+      }
+    } else {
       float4 vv[VQ];
       const int nv4 = s > 0 ? kp * ld / 4 : 0;
       const float4* src = reinterpret_cast<const float4*>(a.Vg + (size_t)par * kp * ld);
@@ -235,6 +253,15 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
     }
     __syncthreads();  // s_row of the next step
     issue_samples(par ^ 1);
+    if (a.bulkv && s > 0) {
+      const bool ok = tc::mbar_wait(&s_vb, vph);
+      vph ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.flag, 1);
+        fail();
+        return;
+      }
+    }
     tc::cp_async_wait(1);  // this step's samples (issued one step earlier) have landed
     __syncthreads();
     const float* Yst = Ys + (size_t)par * ybuf;
@@ -408,6 +435,7 @@ __global__ void __launch_bounds__(GT, 1) sgd_grid_kernel(GridArgs a) {
         __syncthreads();  // shared scratch is reused by the next owned column
       }
     }
+    if (a.bulkv) tc::fence_async_global();  // the new columns are read by bulk copies
     if (!grid_barrier(a.bar, a.flag, 1)) {
       fail();
       return;
@@ -514,6 +542,8 @@ otm_status sgd_grid_run(float* V, const float* YA, const float* YB, const float*
   args.spart = ws.take<float>((size_t)G * L.kp);
   args.bar = ws.take<unsigned>(1);
   args.flag = ws.take<int>(1);
+  args.bulkv = ((reinterpret_cast<uintptr_t>(args.Vg) | reinterpret_cast<uintptr_t>(args.means)) &
+                15) == 0;
   OTM_CHECK_CUDA(cudaMemsetAsync(args.bar, 0, sizeof(unsigned), st));
   return sym ? launch_grid<true>(args, G, st) : launch_grid<false>(args, G, st);
 }
