@@ -178,7 +178,9 @@ otm_status otm_syev(const double* A, int64_t n, double* evals, double* evecs, vo
  * device (the current device; `stream` must belong to it).  All calls on one
  * device share the array: calls whose work overlaps on the GPU (other streams,
  * other host threads) race and give wrong results, so serialise them.
- * Every call copies a status flag to the host and synchronises the stream.
+ * Every call copies a status flag to the host and synchronises the stream, so
+ * no call can be captured in a CUDA graph: do not call it while its stream, or
+ * any stream in global capture mode, is being captured.
  */
 otm_status otm_syev_noalloc(const double* A, int64_t n, double* evals, double* evecs,
                             void* stream);
