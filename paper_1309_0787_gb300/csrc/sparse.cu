@@ -215,34 +215,69 @@ __global__ void csc_count_kernel(const int32_t* __restrict__ col, int64_t nnz,
 }
 
 // ptr[0..d] = exclusive prefix sums of cnt[0..d-1] (ptr[d] = total), cursor = ptr[0..d-1].
-// One block: each thread sums a contiguous range, the block scans the range
-// sums, each thread writes its range.
-// cnt and cursor may be the same array (each thread reads an entry before writing it).
+// One block: warp w takes the w-th contiguous share of the entries, read in
+// batches of 256 (eight coalesced loads in flight per lane); the warps' sums are
+// scanned, and each warp then writes its share's prefix sums, one warp-wide
+// scan of 32 entries at a time.
+// cnt and cursor may be the same array (each lane reads an entry before writing it).
 __global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int32_t* cnt, int64_t d,
                                                               int32_t* __restrict__ ptr,
                                                               int32_t* cursor) {
-  __shared__ int64_t part[1024];
-  const int t = threadIdx.x;
-  const int64_t per = (d + 1023) / 1024;
-  const int64_t b = t * per, e = b + per < d ? b + per : d;
+  __shared__ int64_t wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t share = ((d + 31) / 32 + 255) & ~(int64_t)255;
+  const int64_t b = warp * share, e = b + share < d ? b + share : d;
   int64_t sum = 0;
-  for (int64_t i = b; i < e; ++i) sum += cnt[i];
-  part[t] = sum;
+  for (int64_t base = b; base < e; base += 256) {
+    int32_t c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t i = base + 32 * j + lane;
+      c[j] = i < e ? cnt[i] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sum += c[j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) wsum[warp] = sum;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const int64_t v = t >= off ? part[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  if (warp == 0) {  // exclusive scan of the 32 warp sums
+    const int64_t v = wsum[lane];
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x - v;
+    if (lane == 31) ptr[d] = (int32_t)x;
   }
-  int64_t run = part[t] - sum;
-  for (int64_t i = b; i < e; ++i) {
-    const int32_t ci = cnt[i];
-    ptr[i] = (int32_t)run;
-    cursor[i] = (int32_t)run;
-    run += ci;
+  __syncthreads();
+  int64_t run = wsum[warp];
+  for (int64_t base = b; base < e; base += 256) {
+    int32_t c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t i = base + 32 * j + lane;
+      c[j] = i < e ? cnt[i] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int64_t x = c[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const int64_t i = base + 32 * j + lane;
+      if (i < e) {
+        ptr[i] = (int32_t)(run + x - c[j]);
+        cursor[i] = (int32_t)(run + x - c[j]);
+      }
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
   }
-  if (t == 1023) ptr[d] = (int32_t)part[1023];
 }
 
 // Scatter of (row, value) pairs into the transpose (one warp per CSR row).
@@ -367,15 +402,22 @@ __global__ void __launch_bounds__(1024) csc_block_count_kernel(const int32_t* __
 }
 
 // For each word: bc[b][w] <- sum_{b' < b} bc[b'][w] (in place), total[w] = the sum over all b.
+// Eight blocks' counts are loaded before any is used, so that a thread keeps
+// eight loads in flight instead of one.
 __global__ void csc_block_scan_kernel(int32_t* __restrict__ bc, int64_t nblocks, int64_t d,
                                       int32_t* __restrict__ total) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= d) return;
   int32_t run = 0;
-  for (int64_t b = 0; b < nblocks; ++b) {
-    const int32_t c = bc[b * d + w];
-    bc[b * d + w] = run;
-    run += c;
+  for (int64_t b0 = 0; b0 < nblocks; b0 += 8) {
+    int32_t c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j] = b0 + j < nblocks ? bc[(b0 + j) * d + w] : 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (b0 + j < nblocks) bc[(b0 + j) * d + w] = run;
+      run += c[j];
+    }
   }
   total[w] = run;
 }
