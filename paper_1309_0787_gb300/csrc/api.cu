@@ -13,14 +13,24 @@ namespace {
 thread_local char g_err[512] = {0};
 std::atomic<uint64_t> g_launches{0};
 
-// ybar[j] = (1/n) sum_t Y[t, j]; row blocks of 64, FP64 partial sums, FP64 atomics.
+// ybar[j] = (1/n) sum_t Y[t, j]; row blocks of 512, per column a compensated
+// float32 sum (Knuth's TwoSum: the rounding error of every addition kept in a
+// second float, about 2^-48 relative on the FP32 units), added in FP64 with
+// FP64 atomics.
 __global__ void column_mean_kernel(const float* __restrict__ Y, int64_t n, int64_t k,
                                    double inv_n, double* __restrict__ ybar) {
-  const int64_t r0 = (int64_t)blockIdx.x * 64, r1 = min(n, r0 + 64);
+  const int64_t r0 = (int64_t)blockIdx.x * 512, r1 = min(n, r0 + 512);
   for (int64_t j = threadIdx.x; j < k; j += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t r = r0; r < r1; ++r) acc += (double)Y[r * k + j];
-    atomicAdd(&ybar[j], acc * inv_n);
+    float h = 0.f, l = 0.f;
+#pragma unroll 8
+    for (int64_t r = r0; r < r1; ++r) {
+      const float y = Y[r * k + j];
+      const float s = __fadd_rn(h, y);
+      const float bv = __fsub_rn(s, h);
+      l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(y, bv)));
+      h = s;
+    }
+    atomicAdd(&ybar[j], ((double)h + (double)l) * inv_n);
   }
 }
 
@@ -73,7 +83,7 @@ otm_status otm_column_mean(const float* Y, int64_t n, int64_t k, double* ybar, v
   OTM_REQUIRE(n >= 1 && k >= 1 && Y && ybar, "otm_column_mean: bad arguments");
   cudaStream_t st = as_stream(stream);
   OTM_CHECK_CUDA(cudaMemsetAsync(ybar, 0, sizeof(double) * k, st));
-  column_mean_kernel<<<(unsigned)((n + 63) / 64), 128, 0, st>>>(Y, n, k, 1.0 / (double)n, ybar);
+  column_mean_kernel<<<(unsigned)((n + 511) / 512), 128, 0, st>>>(Y, n, k, 1.0 / (double)n, ybar);
   OTM_CHECK_LAUNCH();
   return OTM_OK;
 }

@@ -74,12 +74,21 @@ __global__ void colsum_f64_kernel(const double* __restrict__ A, int64_t rows, in
   }
 }
 
-__global__ void divide_cols_kernel(double* __restrict__ A, int64_t rows, int64_t k,
-                                   const double* __restrict__ s) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * k) return;
-  const double d = s[idx % k];
-  A[idx] = d != 0.0 ? A[idx] / d : A[idx];
+// A[:, j] /= s[j] (s[j] = 0: unchanged), as a multiply by the reciprocal (one
+// FP64 division per column and block, not per entry); blocks take 64 rows at a
+// time, so that the column of an entry is a 32-bit remainder.
+__global__ void __launch_bounds__(256) divide_cols_kernel(double* __restrict__ A, int64_t rows,
+                                                          int64_t k, const double* __restrict__ s) {
+  extern __shared__ double rinv[];
+  for (int64_t j = threadIdx.x; j < k; j += blockDim.x) rinv[j] = s[j] != 0.0 ? 1.0 / s[j] : 1.0;
+  __syncthreads();
+  const int kk = (int)k;
+  for (int64_t r0 = (int64_t)blockIdx.x * 64; r0 < rows; r0 += (int64_t)gridDim.x * 64) {
+    const int64_t r1 = r0 + 64 < rows ? r0 + 64 : rows;
+    const int cnt = (int)((r1 - r0) * k);
+    double* base = A + r0 * k;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) base[e] *= rinv[e % kk];
+  }
 }
 
 // Block i: row i of the three Gram matrices -> partial sums of the error terms.
@@ -161,7 +170,9 @@ otm_status otm_unwhiten(const float* V, int64_t k, const float* Q, int64_t d, in
     OTM_CHECK_CUDA(cudaMemsetAsync(csum, 0, sizeof(double) * k, st));
     colsum_f64_kernel<<<(unsigned)((d + 63) / 64), 128, 0, st>>>(comps, d, k, csum);
     OTM_CHECK_LAUNCH();
-    divide_cols_kernel<<<(unsigned)((d * k + 255) / 256), 256, 0, st>>>(comps, d, k, csum);
+    const int64_t rb = (d + 63) / 64;
+    divide_cols_kernel<<<(unsigned)(rb < 152 * 4 ? rb : 152 * 4), 256, sizeof(double) * k, st>>>(
+        comps, d, k, csum);
     OTM_CHECK_LAUNCH();
   }
   return OTM_OK;

@@ -27,25 +27,66 @@
 namespace otm {
 namespace {
 
-__global__ void topic_m2_epilogue_kernel(float* __restrict__ O, const float* __restrict__ S,
-                                         const double* __restrict__ delta,
-                                         const double* __restrict__ M1,
-                                         const double* __restrict__ u, int64_t d, int64_t m,
-                                         double a0) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= d * m) return;
-  const int64_t r = idx / m, j = idx % m;
-  const double v = (a0 + 1.0) * ((double)O[idx] - delta[r] * (double)S[idx]) - a0 * M1[r] * u[j];
-  O[idx] = (float)v;
+// O <- (a0 + 1)(O - diag(delta) S) - a0 M1 u^T (d x m), one warp per row in
+// FP32 (FP64 issues at 1/64 of the FP32 rate on this part): the row's FP64
+// values are converted once, delta_r = dh + dl as two floats so that
+// delta_r S = dh S + dl S with dh S formed exactly (Dekker's product, FMA form);
+// O - delta_r S then carries one float32 rounding, as the FP64 form does before
+// its final rounding.  u (m values) is converted once per block (shared memory).
+__global__ void __launch_bounds__(256) topic_m2_epilogue_kernel(
+    float* __restrict__ O, const float* __restrict__ S, const double* __restrict__ delta,
+    const double* __restrict__ M1, const double* __restrict__ u, int64_t d, int64_t m,
+    double a0) {
+  extern __shared__ float uf[];
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) uf[j] = (float)u[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const float c1 = (float)(a0 + 1.0);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < d; r += nw) {
+    float dh = 0.f, dl = 0.f, am = 0.f;
+    if (lane == 0) {
+      const double dr = delta[r];
+      dh = (float)dr;
+      dl = (float)(dr - (double)dh);
+      am = (float)(a0 * M1[r]);
+    }
+    dh = __shfl_sync(0xffffffffu, dh, 0);
+    dl = __shfl_sync(0xffffffffu, dl, 0);
+    am = __shfl_sync(0xffffffffu, am, 0);
+    for (int64_t j = lane; j < m; j += 32) {
+      const int64_t idx = r * m + j;
+      const float sv = S[idx];
+      const float p = __fmul_rn(dh, sv);
+      const float e = fmaf(dh, sv, -p);  // dh sv = p + e exactly
+      const float t = __fsub_rn(__fsub_rn(O[idx], p), fmaf(dl, sv, e));
+      O[idx] = fmaf(c1, t, -am * uf[j]);
+    }
+  }
 }
 
-// out = diag(sqrt(delta)) Q (d x m).
-__global__ void scale_rows_sqrt_kernel(const float* __restrict__ Q, const double* __restrict__ delta,
-                                       int64_t d, int64_t m, float* __restrict__ out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= d * m) return;
-  const double w = delta[idx / m];
-  out[idx] = (float)(sqrt(w > 0.0 ? w : 0.0) * (double)Q[idx]);
+// out = diag(sqrt(delta)) Q (d x m): one warp per row, the square root once per row.
+__global__ void __launch_bounds__(256) scale_rows_sqrt_kernel(const float* __restrict__ Q,
+                                                              const double* __restrict__ delta,
+                                                              int64_t d, int64_t m,
+                                                              float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < d; r += nw) {
+    float sr = 0.f;
+    if (lane == 0) {
+      const double w = delta[r];
+      sr = (float)sqrt(w > 0.0 ? w : 0.0);
+    }
+    sr = __shfl_sync(0xffffffffu, sr, 0);
+    for (int64_t j = lane; j < m; j += 32) out[r * m + j] = sr * Q[r * m + j];
+  }
+}
+
+// Grid of the one-warp-per-row kernels: up to eight resident blocks per SM.
+inline unsigned row_warp_blocks(int64_t rows) {
+  const int64_t want = (rows + 7) / 8;
+  return (unsigned)(want < 152 * 8 ? (want > 0 ? want : 1) : 152 * 8);
 }
 
 __global__ void sqrt_f32_kernel(const float* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -145,7 +186,8 @@ struct TopicOp {
     else
       OTM_TRY(spmm_scatter(X, P, m, nullptr, inv_n, O, st));
     OTM_TRY(vec_tn(M1, S, d, m, u, st));
-    topic_m2_epilogue_kernel<<<blocks_for(d * m), 256, 0, st>>>(O, S, delta, M1, u, d, m, a0);
+    topic_m2_epilogue_kernel<<<row_warp_blocks(d), 256, sizeof(float) * m, st>>>(O, S, delta, M1,
+                                                                                 u, d, m, a0);
     OTM_CHECK_LAUNCH();
     return OTM_OK;
   }
@@ -154,7 +196,7 @@ struct TopicOp {
     const int64_t n = X->rows, d = X->cols;
     OTM_TRY(spmm_gather(X, Q, m, sqw, P, st));
     OTM_TRY(gemm_tn_f64acc(P, P, n, m, m, (a0 + 1.0) / (double)(n > 0 ? n : 1), Om, 0, st));
-    scale_rows_sqrt_kernel<<<blocks_for(d * m), 256, 0, st>>>(Q, delta, d, m, D);
+    scale_rows_sqrt_kernel<<<row_warp_blocks(d), 256, 0, st>>>(Q, delta, d, m, D);
     OTM_CHECK_LAUNCH();
     OTM_TRY(gemm_tn_f64acc(D, D, d, m, m, -(a0 + 1.0), Om, 1, st));
     OTM_TRY(vec_tn(M1, Q, d, m, u, st));
