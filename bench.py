@@ -30,6 +30,7 @@ collective on the data path); value = samples of all ranks / max rank time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -57,6 +58,28 @@ SGD_KERNEL_NAME = {"auto": "sgd_grid_kernel (one cooperative launch = all STGD s
                    "grid": "sgd_grid_kernel (one cooperative launch = all STGD steps)",
                    "cluster": "sgd_cluster_kernel (one cluster launch = all STGD steps)"}
 PVALUE_THRESHOLD = 0.01   # significance level of the paired p-value test
+# DRAM bytes (read + write) of one grid-form STGD launch on the default corpus
+# (300,000 documents, k = 100, b = 1,024, 20 epochs), from the ncu capture summarised
+# in profiles/sgd_grid_kernel_lda_300000_k100.md; reported only while the kernel's
+# source is the one that was captured (its SHA-256), else null.
+SGD_GRID_TRAFFIC = {"bytes": 1732604000 + 4984320,
+                    "source": "paper_1309_0787_gb300/csrc/sgd_grid.cu",
+                    "sha256": "9d85a56ee0c025275d1d7c646b533cefacd2e083523fce18116f542c012ff265",
+                    "capture": "profiles/sgd_grid_kernel_lda_300000_k100.md"}
+
+
+def sgd_grid_traffic(form, c):
+    """The captured DRAM bytes of the grid-form launch, for the captured workload
+    and an unchanged kernel source; None otherwise."""
+    if form not in ("auto", "grid") or (c["n_docs"], c["k"], c["b"], c["epochs"]) != (
+            300000, 100, 1024, 20):
+        return None
+    try:
+        with open(os.path.join(ROOT, SGD_GRID_TRAFFIC["source"]), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return SGD_GRID_TRAFFIC["bytes"] if h == SGD_GRID_TRAFFIC["sha256"] else None
 
 
 def make_inputs(cfg, rank=0):
@@ -1567,7 +1590,9 @@ def run_lda(args, rank, world, local_rank):
         "roofline": {"kernel": SGD_KERNEL_NAME.get(args.sgd_form, SGD_KERNEL_NAME["auto"]),
                      "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": sgd_grid_traffic(args.sgd_form, c),
+                     "traffic_source": SGD_GRID_TRAFFIC["capture"] + " (ncu, kernel source "
+                                       "SHA-256 " + SGD_GRID_TRAFFIC["sha256"][:12] + ")",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "algorithmic_flops_per_launch": flops,
                      "launch_ms": statistics.mean(sgd_ms)},
@@ -1641,7 +1666,9 @@ def run_stgd(args):
             "roofline": {"kernel": SGD_KERNEL_NAME[args.sgd_form], "bound": "alu",
                          "achieved": flops / t / 1e12, "peak": FP32_FMA_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP32_FMA_PEAK_TFLOPS,
-                         "traffic": None,
+                         "traffic": sgd_grid_traffic(args.sgd_form, c),
+                         "traffic_source": SGD_GRID_TRAFFIC["capture"] + " (ncu, kernel "
+                                           "source SHA-256 " + SGD_GRID_TRAFFIC["sha256"][:12] + ")",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                          "algorithmic_flops_per_launch": flops},
             "gpu_launches": args.steps, "clocks": clocks}

@@ -89,3 +89,19 @@ def test_sym_sgd_flops_closed_form():
     # 300,000 samples, b = 1,024: 292 full minibatches and one of 992 per epoch
     f = bench.sym_sgd_flops(300000, 1024, 100, 20)
     assert f == 20 * (4 * 100 ** 2 * 300000 + 293 * 4 * 100 ** 3)
+
+
+def test_sgd_grid_traffic_only_for_the_captured_kernel_and_workload(tmp_path, monkeypatch):
+    """The captured DRAM bytes are reported for the grid form on the default corpus
+    while the kernel source hashes as captured; otherwise null."""
+    c = dict(bench.LDA)
+    assert bench.sgd_grid_traffic("auto", c) == bench.SGD_GRID_TRAFFIC["bytes"]
+    assert bench.sgd_grid_traffic("split", c) is None
+    c2 = dict(c)
+    c2["k"] = 50
+    assert bench.sgd_grid_traffic("grid", c2) is None
+    src = tmp_path / bench.SGD_GRID_TRAFFIC["source"]
+    src.parent.mkdir(parents=True)
+    src.write_text("// another kernel\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.sgd_grid_traffic("auto", c) is None
