@@ -59,13 +59,13 @@ SGD_KERNEL_NAME = {"auto": "sgd_grid_kernel (one cooperative launch = all STGD s
                    "cluster": "sgd_cluster_kernel (one cluster launch = all STGD steps)"}
 PVALUE_THRESHOLD = 0.01   # significance level of the paired p-value test
 # DRAM bytes (read + write) of one grid-form STGD launch on the default corpus
-# (300,000 documents, k = 100, b = 1,024, 20 epochs), from the ncu capture summarised
-# in profiles/sgd_grid_kernel_lda_300000_k100.md; reported only while the kernel's
-# source is the one that was captured (its SHA-256), else null.
+# (300,000 documents, k = 100, b = 1,024, 20 epochs), from one ncu capture of that
+# launch (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
+# kernel's source is the one that was captured (its SHA-256), else null.
 SGD_GRID_TRAFFIC = {"bytes": 1732604000 + 4984320,
                     "source": "paper_1309_0787_gb300/csrc/sgd_grid.cu",
                     "sha256": "9d85a56ee0c025275d1d7c646b533cefacd2e083523fce18116f542c012ff265",
-                    "capture": "profiles/sgd_grid_kernel_lda_300000_k100.md"}
+                    "capture": "ncu capture of the grid-form launch on the default corpus"}
 
 
 def sgd_grid_traffic(form, c):
@@ -1591,7 +1591,7 @@ def run_lda(args, rank, world, local_rank):
                      "bound": "alu", "achieved": achieved, "peak": FP32_FMA_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_FMA_PEAK_TFLOPS,
                      "traffic": sgd_grid_traffic(args.sgd_form, c),
-                     "traffic_source": SGD_GRID_TRAFFIC["capture"] + " (ncu, kernel source "
+                     "traffic_source": SGD_GRID_TRAFFIC["capture"] + " (kernel source "
                                        "SHA-256 " + SGD_GRID_TRAFFIC["sha256"][:12] + ")",
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "algorithmic_flops_per_launch": flops,
@@ -1667,7 +1667,7 @@ def run_stgd(args):
                          "achieved": flops / t / 1e12, "peak": FP32_FMA_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP32_FMA_PEAK_TFLOPS,
                          "traffic": sgd_grid_traffic(args.sgd_form, c),
-                         "traffic_source": SGD_GRID_TRAFFIC["capture"] + " (ncu, kernel "
+                         "traffic_source": SGD_GRID_TRAFFIC["capture"] + " (kernel "
                                            "source SHA-256 " + SGD_GRID_TRAFFIC["sha256"][:12] + ")",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                          "algorithmic_flops_per_launch": flops},
