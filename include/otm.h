@@ -695,7 +695,10 @@ otm_status otm_gemm_bf16(const void* A, const void* B, int64_t M, int64_t N, int
  * normalize != 0 each column is sign-flipped to a non-negative sum and divided
  * by its sum (topic-word distributions).  alpha_hat_i = lambda_i^-2 / sum_j
  * lambda_j^-2.  V: k x k column-major float32; Q: d x kt float32; Cp: kt x k
- * FP64; comps: d x k FP64 row-major; lambda, alpha_hat: k doubles.
+ * FP64; comps: d x k FP64 row-major; lambda, alpha_hat: k doubles.  The k x k
+ * factors, the normalisation and alpha_hat are FP64; the d x kt by kt x k
+ * product runs in double-float arithmetic on the FP32 units (every entry
+ * within about 2^-48 of the sum of its absolute terms).
  * Scratch: otm_unwhiten_workspace(d, k, kt).
  */
 size_t otm_unwhiten_workspace(int64_t d, int64_t k, int64_t kt);
