@@ -275,8 +275,10 @@ otm_status otm_project(const otm_csr* X, const float* W, int64_t k, const float*
                        float* Y, void* stream);
 
 /*
- * otm_column_mean -- ybar = (1/n) sum_t Y[t, :] in FP64 (the means y-bar of
- * Section 3.2).  Y: n x k float32; ybar: k doubles.
+ * otm_column_mean -- ybar = (1/n) sum_t Y[t, :] (the means y-bar of Section
+ * 3.2), to FP64-class accuracy: compensated float32 sums over blocks of 512
+ * rows (the rounding error of every addition kept), added in FP64.  Y: n x k
+ * float32; ybar: k doubles.
  */
 otm_status otm_column_mean(const float* Y, int64_t n, int64_t k, double* ybar, void* stream);
 
